@@ -1,0 +1,337 @@
+"""Benchmark: (H2O)64-like exact-exchange applications per second on GB300.
+
+One step = one pass of the whole path on one synthetic configuration:
+sea_apply_vxx (domain boxes, pair selection, per-pair Poisson CG with
+multipole boundaries, far field, accumulation of V_xx phi and E_xx),
+sea_build_ace (M, Cholesky, L^-1) and sea_apply_ace on 256 trial vectors.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``value``: steps/s with inputs resident in HBM (CUDA events on the
+library's stream).  ``e2e``: the same through the C ABI with pinned host
+buffers, host<->device copies inside the timed region.  ``--impl
+reference`` times the CPU oracle (the plain FP64 reference of the method)
+on the host cores.  For N > 1 (torchrun) every rank runs an independent
+replica of the workload (the path has no exchange step between
+configurations); value = all ranks' steps / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "(H2O)64 V_xx applications/s, plain FP64 vs chosen form, same |dExx| bound"
+UNIT = "applications/s"
+CONFIG = "h2o64_96"
+N_TRIAL = 256
+
+# Algorithmic FP64 flops per CG unknown and iteration: the symmetric 37-point
+# stencil as 18 pair sums, 18 multiply-adds and the centre product (55), plus
+# two dot products and three vector updates (10).
+CG_FLOPS_PER_UNKNOWN_ITER = 65
+# FP64 peak from the part's unit counts and clock: 152 SMs x 2 FP64 FMA/clk x
+# 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 figure).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _clock_sampler(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=open(path, "w"),
+                                stderr=subprocess.DEVNULL)
+    except (OSError, FileNotFoundError):
+        return None
+
+
+def _clock_summary(path, index):
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or not f[0].isdigit() or int(f[0]) != index:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_2208_06097_gb300 import build as B
+    from paper_2208_06097_gb300 import sea, synth
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    s = synth.make_config(CONFIG)
+    psi_h = synth.random_trial_vectors(N_TRIAL, s.grid, 2024)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = sea.Context(s.cell, s.grid, stream=stream.cuda_stream)
+
+    phi = torch.from_numpy(s.phi).to(dev)
+    psi = torch.from_numpy(psi_h).to(dev)
+    vxx = torch.empty_like(phi)
+    y = torch.empty_like(psi)
+    torch.cuda.synchronize()
+    ctx.set_orbitals(phi)
+
+    def step():
+        ctx.apply_vxx(vxx)
+        ctx.build_ace()
+        ctx.apply_ace(psi, y)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clk_path = os.path.join(tempfile.gettempdir(), f"sea_clocks_{os.getpid()}.csv")
+    sampler = _clock_sampler(clk_path) if rank == 0 else None
+    time.sleep(0.5 if sampler else 0)
+    st0 = ctx.stats()
+    ms = {"plan": 0.0, "setup": 0.0, "cg": 0.0, "acc": 0.0, "ace_b": 0.0, "ace_a": 0.0}
+    cg_work = 0
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ea = torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply_vxx(vxx)
+        ctx.build_ace()
+        ea.record(stream)
+        ctx.apply_ace(psi, y)
+        eb.record(stream)
+        st = ctx.stats()
+        eb.synchronize()
+        ms["plan"] += st["ms_plan"]
+        ms["setup"] += st["ms_setup"]
+        ms["cg"] += st["ms_cg"]
+        ms["acc"] += st["ms_accumulate"]
+        ms["ace_b"] += st["ms_ace_build"]
+        ms["ace_a"] += ea.elapsed_time(eb)
+        cg_work += st["cg_unknown_iters"]
+    e1.record(stream)
+    barrier()
+    t_ms = e0.elapsed_time(e1)
+    st1 = ctx.stats()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clock_summary(clk_path, local) if rank == 0 else None
+
+    # e2e: host buffers through the C ABI, copies inside the timed region
+    phi_pin = torch.from_numpy(s.phi).pin_memory().numpy()
+    psi_pin = torch.from_numpy(psi_h).pin_memory().numpy()
+    out_pin = torch.empty(s.phi.shape, dtype=torch.float64).pin_memory().numpy()
+    y_pin = torch.empty(psi_h.shape, dtype=torch.float64).pin_memory().numpy()
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def step_host():
+        ctx.set_orbitals(phi_pin)
+        ctx.apply_vxx(out_pin)
+        ctx.build_ace()
+        ctx.apply_ace(psi_pin, y_pin)
+
+    step_host()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    barrier()
+    t_e2e = time.perf_counter() - t0
+
+    ts = torch.tensor([t_ms, t_e2e], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(ts, op=dist.ReduceOp.MAX)
+    t_ms, t_e2e = float(ts[0]), float(ts[1])
+    if rank != 0:
+        ctx.close()
+        return None
+
+    value = ws * args.steps / (t_ms / 1e3)
+    e2e_value = ws * e2e_steps / t_e2e
+    K = args.steps
+    cg_ms = ms["cg"] / K
+    cg_flops = CG_FLOPS_PER_UNKNOWN_ITER * (cg_work / K)
+    achieved = cg_flops / (cg_ms / 1e3) / 1e12
+    stats = ctx.stats()
+    cpu = cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": t_ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded water-like localized orbitals, see synth.py)",
+        "config": {
+            "workload": "(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, "
+                        "eps=10^-3.5, delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; "
+                        "ACE build + apply to 256 trial vectors",
+            "form": "plain FP64",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "inputs larger than L2 (Phi and psi 1.81 GB each)",
+            "n_pairs": stats["n_pairs"],
+            "cg_unknowns": stats["n_unknowns"],
+            "cg_iters_mean": stats["cg_iters_mean"],
+            "stage_ms": {k: v / K for k, v in ms.items()},
+        },
+        "e2e": {
+            "value": e2e_value,
+            "unit": UNIT,
+            "h2d_bytes_per_step": int(s.phi.nbytes + psi_h.nbytes),
+            "d2h_bytes_per_step": int(s.phi.nbytes + psi_h.nbytes + 8),
+        },
+        "gpu_launches": int(st1["n_launches"] - st0["n_launches"]),
+        "roofline": {
+            "kernel": "k_cg (persistent FP64 CG, all pairs)",
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": None,
+            "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
+                         "65 algorithmic flops per unknown per CG iteration",
+        },
+        "clocks": clocks,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return line
+
+
+def oracle_step(s, psi_h):
+    """One full step of the CPU oracle (test infrastructure, timed only)."""
+    from oracle import ace as OA
+    from oracle import oracle as O
+    r = O.apply_vxx(s.phi, s.cell, O.Params())
+    F = s.phi.reshape(s.n_orb, -1)
+    a = OA.build_ace(F, r["vxx"].reshape(s.n_orb, -1), s.dV)
+    OA.apply_ace(a["Xi"], psi_h.reshape(psi_h.shape[0], -1), s.dV)
+    return r
+
+
+def cpu_baseline(s, psi_h):
+    """The oracle as it stands, timed on the host cores: one full step of the
+    same workload (about 10-30 s on the GPU machine's host)."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    oracle_step(s, psi_h)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "one full step (V_xx + ACE build + ACE apply to 256 vectors) of the "
+                      "same (H2O)64-like 96^3 workload; C oracle with OpenMP over pairs, "
+                      "numpy/BLAS ACE"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    from paper_2208_06097_gb300 import synth
+    O.build()
+    s = synth.make_config(CONFIG)
+    psi_h = synth.random_trial_vectors(N_TRIAL, s.grid, 2024)
+    for _ in range(min(args.warmup, 1)):
+        oracle_step(s, psi_h)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(s, psi_h)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": min(args.warmup, 1), "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded water-like localized orbitals, see synth.py)",
+        "config": {"workload": "(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, "
+                               "eps=10^-3.5, delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; "
+                               "ACE build + apply to 256 trial vectors",
+                   "form": "CPU oracle (plain FP64 reference of the method)"},
+        "impl": "reference",
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": "full steps of the same workload on the host cores"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * sea.h -- C ABI of the GB300 exact-exchange engine for SCDM+exx+ACE
+ * (arXiv 2208.06097).
+ *
+ * The library applies the exact-exchange operator V_xx to a set of localized,
+ * orthonormal, real (Gamma-point) occupied orbitals on the real-space grid of
+ * an orthorhombic periodic cell, and builds and applies the adaptively
+ * compressed exchange (ACE) operator from the result:
+ *
+ *   sea_apply_vxx   Sec. II B: domain truncation (Eq. oii), pair selection
+ *                   (Eq. sij), per-pair Poisson problem (Eq. pe) with
+ *                   multipole boundary values (Eqs. me, mepole), local
+ *                   D^i (Eq. tDxx) and E_xx (Eq. exxGen_mlwf);
+ *                   V_xx phi_i = -D^i (Eq. DxxVxx).
+ *   sea_build_ace   Sec. II C, Eq. Vace, App. A: M = Phi^T W dV with
+ *                   W = V_xx Phi, Mbar = (M + M^T)/2, -Mbar = L L^T,
+ *                   Xi = W L^-T.
+ *   sea_apply_ace   V^ACE psi = -Xi (Xi^T psi dV) (Eq. Vace).
+ *
+ * Units: bohr and hartree.  Grid functions are float64 arrays laid out
+ * [n][nz][ny][nx] (x fastest); point (x, y, z) sits at (x hx, y hy, z hz)
+ * with h = cell / grid, and every inner product carries dV = hx hy hz.
+ *
+ * Ownership: the caller owns every buffer it passes and every buffer the
+ * library writes into; the library keeps its own device copy of the
+ * orbitals and its own workspace, released by sea_destroy.  Pointers marked
+ * "host or device" are device pointers when on_device != 0, else pageable or
+ * pinned host pointers.
+ *
+ * Errors: every call returns a sea_status; nothing is thrown across the ABI.
+ * A CUDA error poisons the context: later calls return SEA_ERR_STATE.
+ * sea_last_error gives a one-line message for the last failure.
+ *
+ * Streams: all work is ordered on the stream given to sea_create (NULL: the
+ * legacy default stream).  Calls that return numbers to the host
+ * (sea_apply_vxx's E_xx, status words) synchronize that stream.
+ */
+#ifndef SEA_H
+#define SEA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SEA_OK = 0,
+  SEA_ERR_ARG = 1,              /* bad argument (NULL, size, unsupported option) */
+  SEA_ERR_STATE = 2,            /* call order violated, or context poisoned      */
+  SEA_ERR_CUDA = 3,             /* a CUDA runtime call failed                    */
+  SEA_ERR_OOM = 4,              /* device allocation failed                      */
+  SEA_ERR_CG_NOT_CONVERGED = 5, /* a pair's CG hit cg_max_iter (result kept)     */
+  SEA_ERR_NOT_PD = 6,           /* -Mbar not positive definite (Cholesky pivot)  */
+  SEA_ERR_TIMEOUT = 7,          /* reserved                                      */
+  SEA_ERR_INPUT = 8             /* orbitals not finite                           */
+} sea_status;
+
+/* Method knobs.  Defaults (sea_default_params): eps = 10^-3.5 (Eq. oii),
+ * delta = 1e-3 (Eq. sij), cg_tol = 1e-8, cg_tol_mode = 0 (stop when
+ * ||r||_2 <= cg_tol ||b||_2; 1: stop when rms(r)/(4 pi) <= cg_tol, a
+ * residual density in bohr^-3 as App. C states it), cg_max_iter = 5000,
+ * lmax = 6 (App. C), fd_order = 12 (App. C, O(h^12) Laplacian; the only
+ * supported value), self_scale = 2 (Omega^D_ii = scale_2x Omega_ii, the only
+ * supported value), precision = 0 (FP64 everywhere), warm_start = 0. */
+typedef struct {
+  double eps;
+  double delta;
+  double cg_tol;
+  int cg_tol_mode;
+  int cg_max_iter;
+  int lmax;       /* 0..6 */
+  int fd_order;   /* 12 */
+  double self_scale;
+  int precision;  /* 0: FP64 */
+  int warm_start; /* 0: none */
+  double timeout_ms; /* reserved, 0 */
+} sea_params;
+
+/* Per-call statistics of the last sea_apply_vxx / sea_build_ace /
+ * sea_apply_ace on a context. */
+typedef struct {
+  int n_orb;
+  int n_pairs;        /* selected pairs <ij>, i <= j                       */
+  int n_proto_pairs;  /* pairs with Omega_ij non-empty before screening    */
+  long long n_unknowns; /* sum over pairs of |Omega_ij| (CG unknowns)      */
+  long long n_window_points; /* sum over accumulation windows (Eq. tDxx)   */
+  int cg_iters_min, cg_iters_max;
+  double cg_iters_mean;
+  long long cg_unknown_iters; /* sum over pairs of |Omega_ij| x iterations */
+  double exx;         /* last E_xx from sea_apply_vxx                      */
+  double ms_plan, ms_setup, ms_cg, ms_accumulate; /* device time, last apply_vxx */
+  double ms_ace_build, ms_ace_apply;
+  long long ace_support_points; /* sum over orbitals of tile-rounded support */
+  long long n_launches;  /* kernels this context has launched since creation */
+} sea_stats;
+
+typedef struct sea_ctx sea_ctx;
+
+/* Fill *p with the defaults listed above. */
+void sea_default_params(sea_params* p);
+
+/* Create a context for an orthorhombic cell.  cell[3]: edge lengths (bohr,
+ * > 0); grid[3]: points per axis (nx, ny, nz), each in [8, 1024];
+ * p: NULL for defaults; cuda_stream: a cudaStream_t or NULL.  The context
+ * selects no device: the current device at creation is used for its life. */
+sea_status sea_create(const double cell[3], const int grid[3], const sea_params* p,
+                      void* cuda_stream, sea_ctx** out);
+
+/* Copy n_orb orbitals ([n_orb][nz][ny][nx], host or device) into the
+ * context.  Any earlier exchange/ACE result is invalidated.  Returns
+ * SEA_ERR_INPUT if a value is not finite. */
+sea_status sea_set_orbitals(sea_ctx* ctx, const double* phi, int n_orb, int on_device);
+
+/* Apply V_xx to every orbital: vxx_phi[n_orb][nz][ny][nx] (host or device,
+ * caller-owned) receives V_xx phi_i = -D^i; *exx (may be NULL) receives E_xx.
+ * Synchronizes the context stream once to read E_xx and the status word.
+ * Returns SEA_ERR_CG_NOT_CONVERGED (results still written) if any pair's CG
+ * reached cg_max_iter. */
+sea_status sea_apply_vxx(sea_ctx* ctx, double* vxx_phi, int on_device, double* exx);
+
+/* Build the ACE operator from the orbitals and the last sea_apply_vxx
+ * result.  Returns SEA_ERR_STATE if no sea_apply_vxx result is current and
+ * SEA_ERR_NOT_PD when -Mbar has a non-positive Cholesky pivot. */
+sea_status sea_build_ace(sea_ctx* ctx);
+
+/* out[n_vec][nz][ny][nx] = V^ACE psi for psi[n_vec][nz][ny][nx] (host or
+ * device, same flag for both).  Requires a successful sea_build_ace. */
+sea_status sea_apply_ace(sea_ctx* ctx, const double* psi, int n_vec, double* out,
+                         int on_device);
+
+/* Optional exports of the last results (host or device destination).
+ *   sea_get_ace_matrices: M[n][n] (M_ij = <phi_i|W_j>), L[n][n] (lower,
+ *     zero above the diagonal); either pointer may be NULL.
+ *   sea_get_ace_vectors: xi[n][nz][ny][nx], the ACE vectors Xi = W L^-T
+ *     (materialized on demand; the operator itself is applied in the
+ *     factored form W L^-T L^-1 W^T).
+ *   sea_get_plan: box[n][6] (start x,y,z then extent x,y,z of Omega_ii),
+ *     pairs[P][2], lo[P][3], ext[P][3] (Omega_ij in i's unwrapped frame),
+ *     S[P] (Eq. sij), iters[P] (CG iterations, negative if capped),
+ *     epair[P] (sum over Omega_ij of rho v dV); host pointers, any may be
+ *     NULL; *n_pairs receives P (required). */
+sea_status sea_get_ace_matrices(sea_ctx* ctx, double* M, double* L, int on_device);
+sea_status sea_get_ace_vectors(sea_ctx* ctx, double* xi, int on_device);
+sea_status sea_get_plan(sea_ctx* ctx, int* box, int* n_pairs, int max_pairs, int* pairs,
+                        int* lo, int* ext, double* S, int* iters, double* epair);
+
+sea_status sea_get_stats(const sea_ctx* ctx, sea_stats* s);
+
+/* Message for the last failing call on ctx (static text; never NULL). */
+const char* sea_last_error(const sea_ctx* ctx);
+
+/* Release everything the context owns.  NULL is ignored. */
+void sea_destroy(sea_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SEA_H */

@@ -1,0 +1,300 @@
+// accum.cu -- far field and deterministic accumulation of D (Eq. tDxx),
+// V_xx phi = -D (Eq. DxxVxx) and E_xx (Eq. exxGen_mlwf).
+//
+// Every selected pair p = (i, j) makes one or two entries:
+//   orbital i receives v_ij phi_j on Omega^D_ij (Omega_jj if j != i,
+//   scale_2x Omega_ii if j == i), and for j != i orbital j receives
+//   v_ij phi_i on Omega_ii (v_ji = v_ij).
+// v_ij is the CG solution inside Omega_ij and the multipole expansion
+// (Eq. me) outside it.
+//   k_contrib   (grid over entries x chunks): c = v * phi_partner on the
+//               entry's window, stored per entry; no accumulation here.
+//   k_accumulate (CTA per orbital x z-slab): the slab of the output is
+//               zeroed, then each entry of the orbital is subtracted in
+//               pair order (a fixed order: no floating-point atomics).
+#include <algorithm>
+
+#include "sea_internal.cuh"
+
+namespace sea {
+
+// Window of orbital o's box [s, s+L) for a pair whose domain is [lo, lo+ext)
+// on an axis of n points: the box shifted by kshift*n, or, for a box that
+// spans the whole axis, the n-point window centred on the pair domain.
+__device__ __forceinline__ void box_window(int s, int L, int kshift, int n, int lo, int ext,
+                                           int* ws, int* wl) {
+  if (L >= n) {
+    *ws = lo - (n - ext) / 2;
+    *wl = n;
+  } else {
+    *ws = s + kshift * n;
+    *wl = L;
+  }
+}
+
+// scale_2x: the extent doubled about the interval centre, rounded outward
+// (even L: [s - L/2, s + 3L/2); odd L: [c - L, c + L] with c = s + (L-1)/2),
+// capped at n points centred on the interval (ties low).
+__device__ __forceinline__ void scale_twice(int s, int L, int n, int* ws, int* wl) {
+  int lo2, len2;
+  if ((L & 1) == 0) {
+    lo2 = s - L / 2;
+    len2 = 2 * L;
+  } else {
+    lo2 = s + (L - 1) / 2 - L;
+    len2 = 2 * L + 1;
+  }
+  if (len2 >= n) {
+    lo2 += (len2 - n) / 2;
+    len2 = n;
+  }
+  *ws = lo2;
+  *wl = len2;
+}
+
+// Thread per orbital: count (mode 0) or write (mode 1) its entries in pair
+// order.  eptr must hold the exclusive scan of the counts for mode 1.
+__global__ void k_entries(const PairInfo* __restrict__ pinfo, const int* __restrict__ npairs,
+                          const int* __restrict__ box, int n_orb, int nx, int ny, int nz,
+                          int mode, int* __restrict__ ecount, const int* __restrict__ eptr,
+                          Entry* __restrict__ ent) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_orb) return;
+  const int P = *npairs;
+  const int N[3] = {nx, ny, nz};
+  int cnt = 0;
+  int pos = mode ? eptr[o] : 0;
+  for (int p = 0; p < P; ++p) {
+    const PairInfo I = pinfo[p];
+    int role;
+    if (I.i == o)
+      role = 0;
+    else if (I.j == o)
+      role = 1;
+    else
+      continue;
+    ++cnt;
+    if (!mode) continue;
+    Entry e;
+    e.pair = p;
+    e.o = o;
+    e.partner = role == 0 ? I.j : I.i;
+    for (int a = 0; a < 3; ++a) {
+      if (role == 0 && I.i == I.j) {
+        int s0, l0;
+        box_window(box[I.i * 6 + a], box[I.i * 6 + 3 + a], 0, N[a], I.lo[a], I.ext[a], &s0, &l0);
+        scale_twice(s0, l0, N[a], &e.ws[a], &e.wl[a]);
+      } else if (role == 0) {
+        box_window(box[I.j * 6 + a], box[I.j * 6 + 3 + a], I.k[a], N[a], I.lo[a], I.ext[a],
+                   &e.ws[a], &e.wl[a]);
+      } else {
+        box_window(box[I.i * 6 + a], box[I.i * 6 + 3 + a], 0, N[a], I.lo[a], I.ext[a], &e.ws[a],
+                   &e.wl[a]);
+      }
+    }
+    ent[pos++] = e;
+  }
+  if (!mode) ecount[o] = cnt;
+}
+
+// Single-CTA exclusive scan of n ints (n small); total into *tot.
+__global__ void k_scan_int(const int* __restrict__ in, int n, int* __restrict__ out,
+                           int* __restrict__ tot) {
+  __shared__ long long part[1024];
+  const int T = blockDim.x, chunk = (n + T - 1) / T;
+  const int b = chunk * threadIdx.x, e = min(n, b + chunk);
+  long long s = 0;
+  for (int x = b; x < e; ++x) s += in[x];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int t = 0; t < T; ++t) {
+      long long v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    *tot = (int)acc;
+  }
+  __syncthreads();
+  long long pos = part[threadIdx.x];
+  for (int x = b; x < e; ++x) {
+    out[x] = (int)pos;
+    pos += in[x];
+  }
+  if (threadIdx.x == T - 1) out[n] = (int)pos;
+}
+
+// Window sizes of all entries, then their exclusive scan (64-bit).
+__global__ void k_entry_offsets(const Entry* __restrict__ ent, const int* __restrict__ E_dev,
+                                long long* __restrict__ coff, long long* __restrict__ tot,
+                                long long* __restrict__ maxwin) {
+  __shared__ long long part[1024];
+  __shared__ long long pmax[1024];
+  const int E = *E_dev;
+  const int T = blockDim.x, chunk = (E + T - 1) / T;
+  const int b = chunk * threadIdx.x, e = min(E, b + chunk);
+  long long s = 0, mx = 0;
+  for (int x = b; x < e; ++x) {
+    const long long w = (long long)ent[x].wl[0] * ent[x].wl[1] * ent[x].wl[2];
+    s += w;
+    mx = w > mx ? w : mx;
+  }
+  part[threadIdx.x] = s;
+  pmax[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0, m = 0;
+    for (int t = 0; t < T; ++t) {
+      long long v = part[t];
+      part[t] = acc;
+      acc += v;
+      m = pmax[t] > m ? pmax[t] : m;
+    }
+    *tot = acc;
+    *maxwin = m;
+  }
+  __syncthreads();
+  long long pos = part[threadIdx.x];
+  for (int x = b; x < e; ++x) {
+    coff[x] = pos;
+    pos += (long long)ent[x].wl[0] * ent[x].wl[1] * ent[x].wl[2];
+  }
+}
+
+#define SEA_CHUNK 1024
+
+__global__ void __launch_bounds__(256)
+    k_contrib(const double* __restrict__ phi, int nx, int ny, int nz, const Entry* __restrict__ ent,
+              const long long* __restrict__ coff, const PairInfo* __restrict__ pinfo,
+              const long long* __restrict__ voff, const double* __restrict__ vbuf,
+              const double* __restrict__ Qg, double hx, double hy, double hz,
+              double* __restrict__ cbuf) {
+  const Entry e = ent[blockIdx.y];
+  const int nw = e.wl[0] * e.wl[1] * e.wl[2];
+  const int t0 = blockIdx.x * SEA_CHUNK;
+  if (t0 >= nw) return;
+  const PairInfo P = pinfo[e.pair];
+  __shared__ double Qs[SEA_NQ];
+  if (threadIdx.x < SEA_NQ) Qs[threadIdx.x] = Qg[(size_t)e.pair * SEA_NQ + threadIdx.x];
+  __syncthreads();
+  const double* v = vbuf + voff[e.pair];
+  const size_t ng = (size_t)nx * ny * nz;
+  const double* fp = phi + (size_t)e.partner * ng;
+  double* out = cbuf + coff[blockIdx.y];
+  const double cx = 0.5 * (P.ext[0] - 1), cy = 0.5 * (P.ext[1] - 1), cz = 0.5 * (P.ext[2] - 1);
+  const int t1 = min(nw, t0 + SEA_CHUNK);
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const int tx = t % e.wl[0], ty = (t / e.wl[0]) % e.wl[1], tz = t / (e.wl[0] * e.wl[1]);
+    const int ux = e.ws[0] + tx, uy = e.ws[1] + ty, uz = e.ws[2] + tz;
+    const int lx = ux - P.lo[0], ly = uy - P.lo[1], lz = uz - P.lo[2];
+    double val;
+    if (lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2])
+      val = v[(lz * P.ext[1] + ly) * P.ext[0] + lx];
+    else
+      val = me_potential(Qs, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
+    const size_t g = ((size_t)wrapi(uz, nz) * ny + wrapi(uy, ny)) * nx + wrapi(ux, nx);
+    out[t] = __dmul_rn(val, fp[g]);
+  }
+}
+
+// CTA per (orbital, slab of SLAB z-planes).
+#define SEA_SLAB 4
+__global__ void __launch_bounds__(256)
+    k_accumulate(int nx, int ny, int nz, const int* __restrict__ eptr,
+                 const Entry* __restrict__ ent, const long long* __restrict__ coff,
+                 const double* __restrict__ cbuf, double* __restrict__ out) {
+  const int o = blockIdx.x;
+  const int z0 = blockIdx.y * SEA_SLAB, z1 = min(nz, z0 + SEA_SLAB);
+  const size_t plane = (size_t)nx * ny;
+  double* Do = out + (size_t)o * plane * nz;
+  for (size_t g = z0 * plane + threadIdx.x; g < (size_t)z1 * plane; g += blockDim.x) Do[g] = 0.0;
+  const int e0 = eptr[o], e1 = eptr[o + 1];
+  for (int k = e0; k < e1; ++k) {
+    __syncthreads();
+    const Entry e = ent[k];
+    const double* c = cbuf + coff[k];
+    const int wx = e.wl[0], wy = e.wl[1];
+    const int rowpts = wx * wy;
+    for (int tz = 0; tz < e.wl[2]; ++tz) {
+      const int gz = wrapi(e.ws[2] + tz, nz);
+      if (gz < z0 || gz >= z1) continue;
+      for (int r = threadIdx.x; r < rowpts; r += blockDim.x) {
+        const int tx = r % wx, ty = r / wx;
+        const size_t g = ((size_t)gz * ny + wrapi(e.ws[1] + ty, ny)) * nx + wrapi(e.ws[0] + tx, nx);
+        Do[g] = __dsub_rn(Do[g], c[(size_t)tz * rowpts + r]);
+      }
+    }
+  }
+}
+
+// E_xx = -sum_p (2 - delta_ij) e_p in pair order, plus CG statistics:
+// res[0] = E_xx, res[1] = sum |Omega_ij| x iterations, res[2..4] = min,
+// max, mean iterations.
+__global__ void k_exx(const PairInfo* __restrict__ pinfo, const int* __restrict__ npairs,
+                      const double* __restrict__ epair, const int* __restrict__ iters,
+                      double* __restrict__ res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int P = *npairs;
+  double e = 0.0, ui = 0.0, sum = 0.0;
+  int mn = 0x7fffffff, mx = 0;
+  for (int p = 0; p < P; ++p) {
+    e += (pinfo[p].i == pinfo[p].j ? 1.0 : 2.0) * epair[p];
+    const int it = iters[p] < 0 ? -iters[p] : iters[p];
+    ui += (double)pinfo[p].n * it;
+    sum += it;
+    mn = min(mn, it);
+    mx = max(mx, it);
+  }
+  res[0] = -e;
+  res[1] = ui;
+  res[2] = P ? mn : 0;
+  res[3] = mx;
+  res[4] = P ? sum / P : 0.0;
+}
+
+cudaError_t launch_entries(sea_ctx* c) {
+  const int n = c->n_orb;
+  int* counts = (int*)c->counts.p;
+  k_entries<<<(n + 127) / 128, 128, 0, c->stream>>>((const PairInfo*)c->pinfo.p, counts + 1,
+                                                    (const int*)c->box.p, n, c->N[0], c->N[1],
+                                                    c->N[2], 0, (int*)c->eent.p, nullptr,
+                                                    nullptr);
+  // counts were written into the start of eent as scratch: scan them into eptr
+  k_scan_int<<<1, 1024, 0, c->stream>>>((const int*)c->eent.p, n, (int*)c->eptr.p, counts + 2);
+  k_entries<<<(n + 127) / 128, 128, 0, c->stream>>>((const PairInfo*)c->pinfo.p, counts + 1,
+                                                    (const int*)c->box.p, n, c->N[0], c->N[1],
+                                                    c->N[2], 1, nullptr, (const int*)c->eptr.p,
+                                                    (Entry*)c->ewin.p);
+  k_entry_offsets<<<1, 1024, 0, c->stream>>>((const Entry*)c->ewin.p, counts + 2,
+                                             (long long*)c->coff.p, (long long*)(counts + 6),
+                                             (long long*)(counts + 8));
+  c->launches += 4;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(sea_ctx* c, double* out) {
+  if (c->E > 0) {
+    const int chunks = (int)((c->max_window + SEA_CHUNK - 1) / SEA_CHUNK);
+    for (int e0 = 0; e0 < c->E; e0 += 65535) {
+      const int ne = std::min(65535, c->E - e0);
+      k_contrib<<<dim3(chunks, ne), 256, 0, c->stream>>>(
+          (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const Entry*)c->ewin.p + e0,
+          (const long long*)c->coff.p + e0, (const PairInfo*)c->pinfo.p,
+          (const long long*)c->voff.p, (const double*)c->vbuf.p, (const double*)c->Q.p, c->h[0],
+          c->h[1], c->h[2], (double*)c->cbuf.p);
+    }
+  }
+  k_accumulate<<<dim3(c->n_orb, (c->N[2] + SEA_SLAB - 1) / SEA_SLAB), 256, 0, c->stream>>>(
+      c->N[0], c->N[1], c->N[2], (const int*)c->eptr.p, (const Entry*)c->ewin.p,
+      (const long long*)c->coff.p, (const double*)c->cbuf.p, out);
+  k_exx<<<1, 32, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const int*)c->counts.p + 1,
+                                 (const double*)c->epair.p, (const int*)c->iters.p,
+                                 (double*)c->exx_dev.p);
+  c->launches += 2 + (c->E > 0 ? (c->E + 65534) / 65535 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t upload_harmonics_accum() { return upload_harmonics_here(); }
+
+}  // namespace sea

@@ -1,0 +1,475 @@
+// api.cu -- the C ABI of libsea.so (declared in include/sea.h): context,
+// parameters, workspace and the order of the device steps.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sea_internal.cuh"
+
+namespace sea {
+
+// Real solid-harmonic recurrence coefficients (Racah normalization).
+HarmCoef make_harmonic_coefficients() {
+  HarmCoef h;
+  memset(&h, 0, sizeof(h));
+  for (int l = 0; l < SEA_LMAX; ++l) {
+    h.top[l] = std::sqrt((l == 0 ? 2.0 : 1.0) * (2.0 * l + 1.0) / (2.0 * l + 2.0));
+    for (int m = -l; m <= l; ++m) {
+      const double d = std::sqrt((double)(l + m + 1) * (double)(l - m + 1));
+      h.mid_b[l][m + SEA_LMAX] = (2.0 * l + 1.0) / d;
+      h.mid_c[l][m + SEA_LMAX] = std::sqrt((double)(l + m) * (double)(l - m)) / d;
+    }
+  }
+  return h;
+}
+
+__global__ void k_check_finite(const double* __restrict__ f, size_t n, unsigned* __restrict__ st) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(f[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(st, SEA_FLAG_NONFINITE);
+}
+
+cudaError_t launch_plan_boxes(sea_ctx* c);
+cudaError_t launch_plan_pairs(sea_ctx* c);
+}  // namespace sea
+
+// Second-derivative weights of the symmetric 13-point stencil by Fornberg's
+// recursion (B. Fornberg, Math. Comp. 51, 699 (1988)) for nodes
+// 0, 1, -1, ..., 6, -6; returns w[k], k = 0..6 (symmetric).
+static void fornberg_second_derivative(double* w) {
+  const int np = 2 * SEA_FDP + 1, M = 2;
+  double x[2 * SEA_FDP + 1];
+  x[0] = 0.0;
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    x[2 * k - 1] = k;
+    x[2 * k] = -k;
+  }
+  double C[2 * SEA_FDP + 1][3];
+  memset(C, 0, sizeof(C));
+  C[0][0] = 1.0;
+  double c1 = 1.0, c4 = x[0];
+  for (int i = 1; i < np; ++i) {
+    const int mn = i < M ? i : M;
+    double c2 = 1.0;
+    const double c5 = c4;
+    c4 = x[i];
+    for (int j = 0; j < i; ++j) {
+      const double c3 = x[i] - x[j];
+      c2 *= c3;
+      if (j == i - 1) {
+        for (int k = mn; k >= 1; --k) C[i][k] = c1 * (k * C[i - 1][k - 1] - c5 * C[i - 1][k]) / c2;
+        C[i][0] = -c1 * c5 * C[i - 1][0] / c2;
+      }
+      for (int k = mn; k >= 1; --k) C[j][k] = (c4 * C[j][k] - k * C[j][k - 1]) / c3;
+      C[j][0] = c4 * C[j][0] / c3;
+    }
+    c1 = c2;
+  }
+  w[0] = C[0][2];
+  for (int k = 1; k <= SEA_FDP; ++k) w[k] = 0.5 * (C[2 * k - 1][2] + C[2 * k][2]);
+}
+
+sea_status sea_fail(sea_ctx* c, sea_status s, const char* msg) {
+  if (c) {
+    snprintf(c->err, sizeof(c->err), "%s", msg);
+    if (s == SEA_ERR_CUDA) c->poisoned = true;
+  }
+  return s;
+}
+
+bool sea_ensure(sea_ctx* c, SeaBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return true;
+  if (b.p) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return false;
+  }
+  b.bytes = want;
+  return true;
+}
+
+static void release(SeaBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+#define SEA_CK(call, msg)                                                        \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      char b_[256];                                                              \
+      snprintf(b_, sizeof(b_), "%s: %s", msg, cudaGetErrorString(e_));           \
+      return sea_fail(c, SEA_ERR_CUDA, b_);                                      \
+    }                                                                            \
+  } while (0)
+
+#define SEA_ALLOC(buf, bytes)                                                    \
+  do {                                                                           \
+    if (!sea_ensure(c, c->buf, (bytes))) return sea_fail(c, SEA_ERR_OOM, "device allocation failed: " #buf); \
+  } while (0)
+
+extern "C" {
+
+void sea_default_params(sea_params* p) {
+  if (!p) return;
+  p->eps = std::pow(10.0, -3.5);
+  p->delta = 1e-3;
+  p->cg_tol = 1e-8;
+  p->cg_tol_mode = 0;
+  p->cg_max_iter = 5000;
+  p->lmax = 6;
+  p->fd_order = 12;
+  p->self_scale = 2.0;
+  p->precision = 0;
+  p->warm_start = 0;
+  p->timeout_ms = 0.0;
+}
+
+sea_status sea_create(const double cell[3], const int grid[3], const sea_params* p,
+                      void* cuda_stream, sea_ctx** out) {
+  if (!out || !cell || !grid) return SEA_ERR_ARG;
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a) {
+    if (!(cell[a] > 0.0) || !std::isfinite(cell[a])) return SEA_ERR_ARG;
+    if (grid[a] < 8 || grid[a] > 1024) return SEA_ERR_ARG;
+  }
+  sea_params prm;
+  sea_default_params(&prm);
+  if (p) prm = *p;
+  if (!(prm.eps >= 0.0 && prm.eps < 1.0) || !(prm.delta >= 0.0) || !(prm.cg_tol > 0.0) ||
+      prm.cg_max_iter < 1 || prm.lmax < 0 || prm.lmax > SEA_LMAX || prm.fd_order != 12 ||
+      prm.self_scale != 2.0 || prm.precision != 0 || prm.warm_start != 0 ||
+      (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1))
+    return SEA_ERR_ARG;
+  sea_ctx* c = new (std::nothrow) sea_ctx();
+  if (!c) return SEA_ERR_OOM;
+  c->prm = prm;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return SEA_ERR_CUDA;
+  }
+  c->stream = (cudaStream_t)cuda_stream;
+  for (int a = 0; a < 3; ++a) {
+    c->cell[a] = cell[a];
+    c->N[a] = grid[a];
+    c->h[a] = cell[a] / grid[a];
+  }
+  c->dV = c->h[0] * c->h[1] * c->h[2];
+  c->ng = (size_t)grid[0] * grid[1] * grid[2];
+  double w[SEA_FDP + 1];
+  fornberg_second_derivative(w);
+  c->w_center = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double ih2 = 1.0 / (c->h[a] * c->h[a]);
+    for (int k = 0; k <= SEA_FDP; ++k) c->w_ax[a][k] = -w[k] * ih2;
+    c->w_center += -w[0] * ih2;
+  }
+  if (sea::upload_harmonics_pair() != cudaSuccess || sea::upload_harmonics_accum() != cudaSuccess) {
+    delete c;
+    return SEA_ERR_CUDA;
+  }
+  for (int k = 0; k < 10; ++k)
+    if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
+      delete c;
+      return SEA_ERR_CUDA;
+    }
+  if (!sea_ensure(c, c->status, 64) || !sea_ensure(c, c->counts, 128) ||
+      !sea_ensure(c, c->exx_dev, 64) || !sea_ensure(c, c->queue, 64)) {
+    sea_destroy(c);
+    return SEA_ERR_OOM;
+  }
+  *out = c;
+  return SEA_OK;
+}
+
+sea_status sea_set_orbitals(sea_ctx* c, const double* phi, int n_orb, int on_device) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
+  if (!phi || n_orb < 1 || n_orb > 4096) return sea_fail(c, SEA_ERR_ARG, "bad orbitals");
+  c->have_phi = c->have_vxx = c->have_ace = false;
+  const size_t bytes = (size_t)n_orb * c->ng * sizeof(double);
+  SEA_ALLOC(phi, bytes);
+  SEA_ALLOC(vxx_dev, bytes);
+  c->n_orb = n_orb;
+  const long long ncand = (long long)n_orb * (n_orb + 1) / 2;
+  const int Nmax = std::max(c->N[0], std::max(c->N[1], c->N[2]));
+  SEA_ALLOC(rowsum, (size_t)n_orb * c->N[2] * std::max(c->N[0], c->N[1]) * sizeof(double));
+  SEA_ALLOC(colsum, (size_t)n_orb * c->N[2] * c->N[0] * sizeof(double));
+  SEA_ALLOC(marg, (size_t)n_orb * 3 * Nmax * sizeof(double));
+  SEA_ALLOC(box, (size_t)n_orb * 6 * sizeof(int));
+  SEA_ALLOC(cand_flag, ncand * sizeof(int));
+  SEA_ALLOC(cand_geom, ncand * 9 * sizeof(int));
+  SEA_ALLOC(list_a, ncand * sizeof(int));
+  SEA_ALLOC(list_b, ncand * sizeof(int));
+  SEA_ALLOC(cand_S, ncand * sizeof(double));
+  SEA_ALLOC(pinfo, ncand * sizeof(PairInfo));
+  SEA_ALLOC(pS, ncand * sizeof(double));
+  SEA_ALLOC(psize, ncand * sizeof(int));
+  SEA_ALLOC(voff, ncand * sizeof(long long));
+  SEA_ALLOC(order, ncand * sizeof(int));
+  SEA_ALLOC(eent, (size_t)(n_orb + 1) * sizeof(int));
+  SEA_ALLOC(eptr, (size_t)(n_orb + 1) * sizeof(int));
+  SEA_ALLOC(ewin, (size_t)2 * ncand * sizeof(Entry));
+  SEA_ALLOC(coff, (size_t)2 * ncand * sizeof(long long));
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  SEA_CK(cudaMemcpyAsync(c->phi.p, phi, bytes, kind, c->stream), "copy orbitals");
+  SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
+  sea::k_check_finite<<<1024, 256, 0, c->stream>>>((const double*)c->phi.p, n_orb * c->ng,
+                                                   (unsigned*)c->status.p);
+  c->launches += 1;
+  SEA_CK(cudaGetLastError(), "finite check");
+  unsigned st = 0;
+  SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+         "status");
+  SEA_CK(cudaStreamSynchronize(c->stream), "set_orbitals");
+  if (st & SEA_FLAG_NONFINITE) return sea_fail(c, SEA_ERR_INPUT, "orbitals hold non-finite values");
+  c->have_phi = true;
+  c->stats.n_orb = n_orb;
+  return SEA_OK;
+}
+
+sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
+  if (!c->have_phi) return sea_fail(c, SEA_ERR_STATE, "sea_set_orbitals first");
+  if (!vxx_phi) return sea_fail(c, SEA_ERR_ARG, "vxx_phi is NULL");
+  c->have_vxx = c->have_ace = false;
+  SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
+  SEA_CK(cudaEventRecord(c->ev[0], c->stream), "event");
+  SEA_CK(sea::launch_plan_boxes(c), "domain boxes");
+  SEA_CK(sea::launch_plan_pairs(c), "pair selection");
+  SEA_CK(sea::launch_entries(c), "accumulation entries");
+  int hc[16];
+  SEA_CK(cudaMemcpyAsync(hc, c->counts.p, sizeof(hc), cudaMemcpyDeviceToHost, c->stream), "counts");
+  SEA_CK(cudaStreamSynchronize(c->stream), "plan");
+  c->Pproto = hc[0];
+  c->P = hc[1];
+  c->E = hc[2];
+  memcpy(&c->U, hc + 4, sizeof(long long));
+  memcpy(&c->WC, hc + 6, sizeof(long long));
+  memcpy(&c->max_window, hc + 8, sizeof(long long));
+  SEA_CK(cudaEventRecord(c->ev[1], c->stream), "event");
+  const size_t U = (size_t)std::max<long long>(c->U, 1);
+  SEA_ALLOC(vbuf, U * sizeof(double));
+  SEA_ALLOC(bbuf, U * sizeof(double));
+  SEA_ALLOC(rbuf, U * sizeof(double));
+  SEA_ALLOC(pbuf, U * sizeof(double));
+  SEA_ALLOC(qbuf, U * sizeof(double));
+  SEA_ALLOC(cbuf, (size_t)std::max<long long>(c->WC, 1) * sizeof(double));
+  SEA_ALLOC(Q, (size_t)std::max(c->P, 1) * SEA_NQ * sizeof(double));
+  SEA_ALLOC(epair, (size_t)std::max(c->P, 1) * sizeof(double));
+  SEA_ALLOC(iters, (size_t)std::max(c->P, 1) * sizeof(int));
+  SEA_CK(sea::launch_pair_setup(c), "pair setup");
+  SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
+  SEA_CK(sea::launch_cg(c), "cg");
+  SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
+  SEA_CK(sea::launch_accumulate(c, (double*)c->vxx_dev.p), "accumulate");
+  SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
+  const size_t bytes = (size_t)c->n_orb * c->ng * sizeof(double);
+  SEA_CK(cudaMemcpyAsync(vxx_phi, c->vxx_dev.p, bytes,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+         "copy V_xx phi");
+  struct {
+    double res[5];
+    unsigned st;
+  } r;
+  SEA_CK(cudaMemcpyAsync(r.res, c->exx_dev.p, sizeof(r.res), cudaMemcpyDeviceToHost, c->stream),
+         "exx");
+  SEA_CK(cudaMemcpyAsync(&r.st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+         "status");
+  SEA_CK(cudaStreamSynchronize(c->stream), "apply_vxx");
+  float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
+  cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]);
+  cudaEventElapsedTime(&t23, c->ev[2], c->ev[3]);
+  cudaEventElapsedTime(&t34, c->ev[3], c->ev[4]);
+  c->stats.ms_plan = t01;
+  c->stats.ms_setup = t12;
+  c->stats.ms_cg = t23;
+  c->stats.ms_accumulate = t34;
+  c->stats.n_pairs = c->P;
+  c->stats.n_proto_pairs = c->Pproto;
+  c->stats.n_unknowns = c->U;
+  c->stats.n_window_points = c->WC;
+  c->stats.exx = r.res[0];
+  c->stats.cg_unknown_iters = (long long)r.res[1];
+  c->stats.cg_iters_min = (int)r.res[2];
+  c->stats.cg_iters_max = (int)r.res[3];
+  c->stats.cg_iters_mean = r.res[4];
+  if (exx) *exx = r.res[0];
+  c->have_vxx = true;
+  if (r.st & SEA_FLAG_CG_CAP)
+    return sea_fail(c, SEA_ERR_CG_NOT_CONVERGED, "a pair's CG reached cg_max_iter");
+  return SEA_OK;
+}
+
+sea_status sea_build_ace(sea_ctx* c) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
+  if (!c->have_vxx) return sea_fail(c, SEA_ERR_STATE, "sea_apply_vxx first");
+  c->have_ace = false;
+  SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
+  SEA_CK(cudaEventRecord(c->ev[5], c->stream), "event");
+  cudaError_t e = sea::launch_ace_build(c);
+  if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE workspace");
+  SEA_CK(e, "ace build");
+  SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
+  unsigned st = 0;
+  SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+         "status");
+  SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
+  float t = 0;
+  cudaEventElapsedTime(&t, c->ev[5], c->ev[6]);
+  c->stats.ms_ace_build = t;
+  c->stats.ace_support_points = (long long)c->tile_inc * 512;
+  if (st & SEA_FLAG_NOT_PD) return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is not positive definite");
+  c->have_ace = true;
+  return SEA_OK;
+}
+
+sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, int on_device) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
+  if (!c->have_ace) return sea_fail(c, SEA_ERR_STATE, "sea_build_ace first");
+  if (!psi || !out || n_vec < 1) return sea_fail(c, SEA_ERR_ARG, "bad psi/out");
+  const size_t bytes = (size_t)n_vec * c->ng * sizeof(double);
+  const double* src = psi;
+  double* dst = out;
+  if (!on_device) {
+    SEA_ALLOC(psi_dev, bytes);
+    SEA_ALLOC(out_dev, bytes);
+    SEA_CK(cudaMemcpyAsync(c->psi_dev.p, psi, bytes, cudaMemcpyHostToDevice, c->stream), "copy psi");
+    src = (const double*)c->psi_dev.p;
+    dst = (double*)c->out_dev.p;
+  }
+  SEA_CK(cudaEventRecord(c->ev[7], c->stream), "event");
+  cudaError_t e = sea::launch_ace_apply(c, src, n_vec, dst);
+  if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE apply workspace");
+  SEA_CK(e, "ace apply");
+  SEA_CK(cudaEventRecord(c->ev[8], c->stream), "event");
+  if (!on_device) {
+    SEA_CK(cudaMemcpyAsync(out, c->out_dev.p, bytes, cudaMemcpyDeviceToHost, c->stream), "copy out");
+    SEA_CK(cudaStreamSynchronize(c->stream), "apply_ace");
+    float t = 0;
+    cudaEventElapsedTime(&t, c->ev[7], c->ev[8]);
+    c->stats.ms_ace_apply = t;
+  }
+  return SEA_OK;
+}
+
+sea_status sea_get_ace_matrices(sea_ctx* c, double* M, double* L, int on_device) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned");
+  if (!c->have_ace) return sea_fail(c, SEA_ERR_STATE, "sea_build_ace first");
+  const size_t bytes = (size_t)c->n_orb * c->n_orb * sizeof(double);
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (M) SEA_CK(cudaMemcpyAsync(M, c->Mbuf.p, bytes, k, c->stream), "copy M");
+  if (L) SEA_CK(cudaMemcpyAsync(L, c->Lbuf.p, bytes, k, c->stream), "copy L");
+  SEA_CK(cudaStreamSynchronize(c->stream), "get_ace_matrices");
+  return SEA_OK;
+}
+
+sea_status sea_get_ace_vectors(sea_ctx* c, double* xi, int on_device) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned");
+  if (!c->have_ace) return sea_fail(c, SEA_ERR_STATE, "sea_build_ace first");
+  if (!xi) return sea_fail(c, SEA_ERR_ARG, "xi is NULL");
+  const size_t bytes = (size_t)c->n_orb * c->ng * sizeof(double);
+  double* dst = xi;
+  if (!on_device) {
+    SEA_ALLOC(out_dev, bytes);
+    dst = (double*)c->out_dev.p;
+  }
+  SEA_CK(sea::launch_ace_vectors(c, dst), "ace vectors");
+  if (!on_device) SEA_CK(cudaMemcpyAsync(xi, dst, bytes, cudaMemcpyDeviceToHost, c->stream), "copy xi");
+  SEA_CK(cudaStreamSynchronize(c->stream), "get_ace_vectors");
+  return SEA_OK;
+}
+
+sea_status sea_get_plan(sea_ctx* c, int* box, int* n_pairs, int max_pairs, int* pairs, int* lo,
+                        int* ext, double* S, int* iters, double* epair) {
+  if (!c || !n_pairs) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned");
+  if (!c->have_vxx) return sea_fail(c, SEA_ERR_STATE, "sea_apply_vxx first");
+  *n_pairs = c->P;
+  if (box)
+    SEA_CK(cudaMemcpyAsync(box, c->box.p, (size_t)c->n_orb * 6 * sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream),
+           "copy box");
+  const int m = std::min(max_pairs, c->P);
+  if (m > 0) {
+    PairInfo* pi = (PairInfo*)malloc((size_t)m * sizeof(PairInfo));
+    if (!pi) return sea_fail(c, SEA_ERR_OOM, "host allocation");
+    cudaError_t e = cudaMemcpyAsync(pi, c->pinfo.p, (size_t)m * sizeof(PairInfo),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && S)
+      e = cudaMemcpyAsync(S, c->pS.p, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && iters)
+      e = cudaMemcpyAsync(iters, c->iters.p, (size_t)m * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && epair)
+      e = cudaMemcpyAsync(epair, c->epair.p, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      free(pi);
+      SEA_CK(e, "copy plan");
+    }
+    for (int p = 0; p < m; ++p) {
+      if (pairs) {
+        pairs[2 * p] = pi[p].i;
+        pairs[2 * p + 1] = pi[p].j;
+      }
+      for (int a = 0; a < 3; ++a) {
+        if (lo) lo[3 * p + a] = pi[p].lo[a];
+        if (ext) ext[3 * p + a] = pi[p].ext[a];
+      }
+    }
+    free(pi);
+  }
+  SEA_CK(cudaStreamSynchronize(c->stream), "get_plan");
+  return SEA_OK;
+}
+
+sea_status sea_get_stats(const sea_ctx* c, sea_stats* s) {
+  if (!c || !s) return SEA_ERR_ARG;
+  *s = c->stats;
+  s->n_launches = c->launches;
+  return SEA_OK;
+}
+
+const char* sea_last_error(const sea_ctx* c) {
+  if (!c) return "NULL context";
+  return c->err[0] ? c->err : "no error";
+}
+
+void sea_destroy(sea_ctx* c) {
+  if (!c) return;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  SeaBuf* all[] = {&c->phi, &c->vxx_dev, &c->psi_dev, &c->out_dev, &c->rowsum, &c->colsum,
+                   &c->marg, &c->box, &c->cand_flag, &c->cand_geom, &c->list_a, &c->list_b,
+                   &c->cand_S, &c->counts, &c->pinfo, &c->pS, &c->psize, &c->voff, &c->order,
+                   &c->Q, &c->epair, &c->iters, &c->vbuf, &c->bbuf, &c->rbuf, &c->pbuf,
+                   &c->qbuf, &c->eptr, &c->eent, &c->ewin, &c->coff, &c->cbuf, &c->status,
+                   &c->exx_dev, &c->queue, &c->tmask, &c->tptr_o, &c->tlist_o, &c->tslot_o,
+                   &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf,
+                   &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2};
+  for (SeaBuf* b : all) release(*b);
+  for (int k = 0; k < 10; ++k)
+    if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,373 @@
+// plan.cu -- domain truncation (Eq. oii) and pair selection (Eq. sij).
+//
+// Both steps end in integer decisions taken on FP64 sums.  Every sum here
+// has a fixed order and no fused multiply-add (__dmul_rn/__dadd_rn), so the
+// decisions do not depend on the launch shape:
+//   rows R[z][y] = sum_x phi^2 (x ascending), columns C[z][x] = sum_y phi^2
+//   (y ascending); marginals m_z = (sum_y R) dV, m_y = (sum_z R) dV,
+//   m_x = (sum_z C) dV (ascending); the box of each axis is the shortest
+//   cyclic interval whose outside mass T - inside <= eps/3, inside summed
+//   from the interval start upward, T the ascending total (ties: lowest
+//   start); S_|ij| sums |phi_i phi_j| over each (z, y) row of Omega_ij in x
+//   order, then the rows in (z, y) order, then multiplies by dV.
+#include "sea_internal.cuh"
+
+namespace sea {
+
+// One CTA per (z-plane, orbital): row sums (thread per y) and column sums
+// (thread per x) of phi^2 over the plane.
+__global__ void k_row_col_sums(const double* __restrict__ phi, int nx, int ny, int nz,
+                               double* __restrict__ R, double* __restrict__ C) {
+  const int z = blockIdx.x, i = blockIdx.y;
+  const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
+  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
+    const double* row = plane + (size_t)y * nx;
+    double s = 0.0;
+    for (int x = 0; x < nx; ++x) {
+      double v = row[x];
+      s = __dadd_rn(s, __dmul_rn(v, v));
+    }
+    R[((size_t)i * nz + z) * ny + y] = s;
+  }
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    double s = 0.0;
+    for (int y = 0; y < ny; ++y) {
+      double v = plane[(size_t)y * nx + x];
+      s = __dadd_rn(s, __dmul_rn(v, v));
+    }
+    C[((size_t)i * nz + z) * nx + x] = s;
+  }
+}
+
+// Thread per (orbital, axis, coordinate): the three marginals of |phi|^2 dV.
+// marg layout: [n][3][Nmax].
+__global__ void k_marginals(const double* __restrict__ R, const double* __restrict__ C,
+                            int n, int nx, int ny, int nz, int Nmax, double dV,
+                            double* __restrict__ marg) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int total = n * 3 * Nmax;
+  if (t >= total) return;
+  const int coord = t % Nmax, axis = (t / Nmax) % 3, i = t / (3 * Nmax);
+  double s = 0.0;
+  if (axis == 2) {
+    if (coord >= nz) return;
+    const double* r = R + ((size_t)i * nz + coord) * ny;
+    for (int y = 0; y < ny; ++y) s = __dadd_rn(s, r[y]);
+  } else if (axis == 1) {
+    if (coord >= ny) return;
+    for (int z = 0; z < nz; ++z) s = __dadd_rn(s, R[((size_t)i * nz + z) * ny + coord]);
+  } else {
+    if (coord >= nx) return;
+    for (int z = 0; z < nz; ++z) s = __dadd_rn(s, C[((size_t)i * nz + z) * nx + coord]);
+  }
+  marg[t] = __dmul_rn(s, dV);
+}
+
+// One CTA per (orbital, axis): shortest cyclic interval with outside mass
+// <= tail.  Thread per start s finds its shortest length (the condition is
+// monotone in the length: inside only grows); then the lexicographic
+// minimum of (length, start).  No interval at all (possible only for
+// tail = 0 under rounding): the whole axis from 0.
+__global__ void k_box_fit(const double* __restrict__ marg, int nx, int ny, int nz, int Nmax,
+                          double tail, int* __restrict__ box) {
+  extern __shared__ double sm[];
+  const int axis = blockIdx.x % 3, i = blockIdx.x / 3;
+  const int n = axis == 0 ? nx : (axis == 1 ? ny : nz);
+  const double* m = marg + ((size_t)i * 3 + axis) * Nmax;
+  for (int x = threadIdx.x; x < n; x += blockDim.x) sm[x] = m[x];
+  __shared__ double sT;
+  __shared__ long long sbest[32];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double T = 0.0;
+    for (int x = 0; x < n; ++x) T = __dadd_rn(T, sm[x]);
+    sT = T;
+  }
+  __syncthreads();
+  const double T = sT;
+  long long best = 0x7fffffffffffffffLL;
+  for (int s = threadIdx.x; s < n; s += blockDim.x) {
+    double inside = 0.0;
+    int L = 0, found = 0;
+    while (L < n) {
+      int x = s + L;
+      if (x >= n) x -= n;
+      inside = __dadd_rn(inside, sm[x]);
+      ++L;
+      if (__dsub_rn(T, inside) <= tail) {
+        found = 1;
+        break;
+      }
+    }
+    if (found) {
+      long long key = (long long)L * 4096 + s;
+      if (key < best) best = key;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long other = __shfl_xor_sync(0xffffffffu, best, o);
+    if (other < best) best = other;
+  }
+  if ((threadIdx.x & 31) == 0) sbest[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long b = sbest[0];
+    for (int w = 1; w < (int)((blockDim.x + 31) >> 5); ++w)
+      if (sbest[w] < b) b = sbest[w];
+    int s0 = 0, L0 = n;
+    if (b != 0x7fffffffffffffffLL) {
+      L0 = (int)(b / 4096);
+      s0 = (int)(b % 4096);
+    }
+    box[i * 6 + axis] = s0;
+    box[i * 6 + 3 + axis] = L0;
+  }
+}
+
+// Intersection of cyclic intervals (reading of the wrap-around case): j's
+// interval shifted by k n, k in {-1, 0, 1}; keep the largest overlap (first
+// k on ties); a full-axis interval leaves the other one as it is.
+__device__ bool interval_meet(int s1, int L1, int s2, int L2, int n, int* lo, int* ext,
+                              int* kk) {
+  if (L1 >= n && L2 >= n) { *lo = s1; *ext = n; *kk = 0; return true; }
+  if (L1 >= n) { *lo = s2; *ext = L2; *kk = 0; return true; }
+  if (L2 >= n) { *lo = s1; *ext = L1; *kk = 0; return true; }
+  int best = 0, bk = 0, blo = 0;
+  for (int k = -1; k <= 1; ++k) {
+    int a0 = max(s1, s2 + k * n);
+    int a1 = min(s1 + L1, s2 + k * n + L2);
+    if (a1 - a0 > best) { best = a1 - a0; bk = k; blo = a0; }
+  }
+  if (best <= 0) return false;
+  *lo = blo; *ext = best; *kk = bk;
+  return true;
+}
+
+// Candidate c enumerates i <= j row by row: c = i n - i(i-1)/2 + (j - i).
+__device__ __forceinline__ void decode_pair(long long c, int n, int* pi, int* pj) {
+  // row i starts at off(i) = i n - i(i-1)/2; find the last row with off <= c
+  double b = 2.0 * n + 1.0;
+  int i = (int)floor((b - sqrt(b * b - 8.0 * (double)c)) * 0.5);
+  if (i < 0) i = 0;
+  if (i > n - 1) i = n - 1;
+  while (i > 0 && (long long)i * n - (long long)i * (i - 1) / 2 > c) --i;
+  while (i + 1 < n && (long long)(i + 1) * n - (long long)(i + 1) * i / 2 <= c) ++i;
+  *pi = i;
+  *pj = i + (int)(c - ((long long)i * n - (long long)i * (i - 1) / 2));
+}
+
+// geom layout per candidate: lo[3], ext[3], k[3].
+__global__ void k_proto_pairs(const int* __restrict__ box, int n, int nx, int ny, int nz,
+                              long long ncand, int* __restrict__ flag, int* __restrict__ geom) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncand) return;
+  int i, j;
+  decode_pair(c, n, &i, &j);
+  const int N[3] = {nx, ny, nz};
+  int g[9];
+  bool ok = true;
+  for (int a = 0; a < 3 && ok; ++a)
+    ok = interval_meet(box[i * 6 + a], box[i * 6 + 3 + a], box[j * 6 + a], box[j * 6 + 3 + a],
+                       N[a], &g[a], &g[3 + a], &g[6 + a]);
+  flag[c] = ok ? 1 : 0;
+  if (ok)
+    for (int q = 0; q < 9; ++q) geom[c * 9 + q] = g[q];
+}
+
+// Single-CTA stable compaction: out[k] = index of the k-th set flag;
+// *count = number of set flags.  Each thread scans a contiguous chunk.
+__global__ void k_compact(const int* __restrict__ flag, long long n_host,
+                          const int* __restrict__ n_dev, int* __restrict__ out,
+                          int* __restrict__ count) {
+  __shared__ long long part[1024];
+  const long long n = n_dev ? (long long)*n_dev : n_host;
+  const int T = blockDim.x;
+  const long long chunk = (n + T - 1) / T;
+  const long long b = chunk * threadIdx.x;
+  const long long e = min(n, b + chunk);
+  long long s = 0;
+  for (long long x = b; x < e; ++x) s += flag[x] != 0;
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int t = 0; t < T; ++t) {
+      long long v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    *count = (int)acc;
+  }
+  __syncthreads();
+  long long pos = part[threadIdx.x];
+  for (long long x = b; x < e; ++x)
+    if (flag[x]) out[pos++] = (int)x;
+}
+
+// One CTA per proto-pair: S_|ij| in the fixed row order, keep decision.
+__global__ void k_screen(const double* __restrict__ phi, int n, int nx, int ny, int nz,
+                         const int* __restrict__ proto_list, const int* __restrict__ nproto,
+                         const int* __restrict__ geom, double dV, double delta,
+                         int* __restrict__ keep, double* __restrict__ Sout) {
+  const int q = blockIdx.x;
+  if (q >= *nproto) return;
+  const long long c = proto_list[q];
+  int i, j;
+  decode_pair(c, n, &i, &j);
+  const int* g = geom + c * 9;
+  const int ex = g[3], ey = g[4], ez = g[5];
+  const size_t ng = (size_t)nx * ny * nz;
+  const double* fi = phi + (size_t)i * ng;
+  const double* fj = phi + (size_t)j * ng;
+  __shared__ double rows[1024];
+  __shared__ double tot;
+  if (threadIdx.x == 0) tot = 0.0;
+  const int nrows = ey * ez;
+  for (int r0 = 0; r0 < nrows; r0 += 1024) {
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < min(nrows, r0 + 1024); r += blockDim.x) {
+      const int y = r % ey, z = r / ey;
+      const int gz = wrapi(g[2] + z, nz), gy = wrapi(g[1] + y, ny);
+      const size_t base = ((size_t)gz * ny + gy) * nx;
+      double row = 0.0;
+      for (int x = 0; x < ex; ++x) {
+        const int gx = wrapi(g[0] + x, nx);
+        row = __dadd_rn(row, fabs(__dmul_rn(fi[base + gx], fj[base + gx])));
+      }
+      rows[r - r0] = row;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = tot;
+      for (int r = r0; r < min(nrows, r0 + 1024); ++r) t = __dadd_rn(t, rows[r - r0]);
+      tot = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double S = __dmul_rn(tot, dV);
+    Sout[q] = S;
+    keep[q] = (i == j || S >= delta) ? 1 : 0;
+  }
+}
+
+// Build the pair records in (i, j) order from the kept proto-pairs.
+__global__ void k_fill_pairs(const int* __restrict__ kept, const int* __restrict__ npairs,
+                             const int* __restrict__ proto_list, const int* __restrict__ geom,
+                             const double* __restrict__ Sproto, int n, PairInfo* __restrict__ pinfo,
+                             double* __restrict__ S, int* __restrict__ pn) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= *npairs) return;
+  const int q = kept[p];
+  const long long c = proto_list[q];
+  int i, j;
+  decode_pair(c, n, &i, &j);
+  const int* g = geom + c * 9;
+  PairInfo P;
+  P.i = i;
+  P.j = j;
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = g[a];
+    P.ext[a] = g[3 + a];
+    P.k[a] = g[6 + a];
+  }
+  P.n = P.ext[0] * P.ext[1] * P.ext[2];
+  pinfo[p] = P;
+  S[p] = Sproto[q];
+  pn[p] = P.n;
+}
+
+// Single-CTA exclusive scan of P sizes into 64-bit offsets; total in *tot.
+__global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__ count,
+                             long long* __restrict__ off, long long* __restrict__ tot) {
+  __shared__ long long part[1024];
+  const int n = *count;
+  const int T = blockDim.x;
+  const int chunk = (n + T - 1) / T;
+  const int b = chunk * threadIdx.x, e = min(n, b + chunk);
+  long long s = 0;
+  for (int x = b; x < e; ++x) s += sz[x];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int t = 0; t < T; ++t) {
+      long long v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    *tot = acc;
+  }
+  __syncthreads();
+  long long pos = part[threadIdx.x];
+  for (int x = b; x < e; ++x) {
+    off[x] = pos;
+    pos += sz[x];
+  }
+}
+
+// Longest-first processing order for the CG queue: rank by (size desc,
+// index asc).
+__global__ void k_lpt_order(const int* __restrict__ sz, const int* __restrict__ count,
+                            int* __restrict__ order) {
+  const int n = *count;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int mine = sz[p];
+  int rank = 0;
+  for (int q = 0; q < n; ++q) {
+    const int o = sz[q];
+    rank += (o > mine) || (o == mine && q < p);
+  }
+  order[rank] = p;
+}
+
+cudaError_t launch_plan_boxes(sea_ctx* c) {
+  const int n = c->n_orb, nx = c->N[0], ny = c->N[1], nz = c->N[2];
+  const int Nmax = max(nx, max(ny, nz));
+  k_row_col_sums<<<dim3(nz, n), 128, 0, c->stream>>>((const double*)c->phi.p, nx, ny, nz,
+                                                     (double*)c->rowsum.p, (double*)c->colsum.p);
+  const int tot = n * 3 * Nmax;
+  k_marginals<<<(tot + 255) / 256, 256, 0, c->stream>>>(
+      (const double*)c->rowsum.p, (const double*)c->colsum.p, n, nx, ny, nz, Nmax, c->dV,
+      (double*)c->marg.p);
+  k_box_fit<<<n * 3, 128, Nmax * sizeof(double), c->stream>>>(
+      (const double*)c->marg.p, nx, ny, nz, Nmax, c->prm.eps / 3.0, (int*)c->box.p);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+// Candidates, proto-pair compaction, screening and kept compaction.  Leaves
+// the kept count in counts[1] and the proto count in counts[0] (device).
+// Candidates, proto-pair compaction, screening, kept compaction, pair
+// records, unknown offsets and the CG order, all with device-side counts:
+// counts[0] = proto pairs, counts[1] = pairs, *(long long*)(counts + 4) =
+// total unknowns.  Grids are sized for the worst case (every candidate).
+cudaError_t launch_plan_pairs(sea_ctx* c) {
+  const int n = c->n_orb;
+  const long long ncand = (long long)n * (n + 1) / 2;
+  const unsigned gc = (unsigned)((ncand + 255) / 256);
+  int* counts = (int*)c->counts.p;
+  k_proto_pairs<<<gc, 256, 0, c->stream>>>((const int*)c->box.p, n, c->N[0], c->N[1], c->N[2],
+                                           ncand, (int*)c->cand_flag.p, (int*)c->cand_geom.p);
+  k_compact<<<1, 1024, 0, c->stream>>>((const int*)c->cand_flag.p, ncand, nullptr,
+                                       (int*)c->list_a.p, counts + 0);
+  k_screen<<<(unsigned)ncand, 256, 0, c->stream>>>(
+      (const double*)c->phi.p, n, c->N[0], c->N[1], c->N[2], (const int*)c->list_a.p, counts + 0,
+      (const int*)c->cand_geom.p, c->dV, c->prm.delta, (int*)c->cand_flag.p,
+      (double*)c->cand_S.p);
+  k_compact<<<1, 1024, 0, c->stream>>>((const int*)c->cand_flag.p, 0, counts + 0,
+                                       (int*)c->list_b.p, counts + 1);
+  k_fill_pairs<<<gc, 256, 0, c->stream>>>((const int*)c->list_b.p, counts + 1,
+                                          (const int*)c->list_a.p, (const int*)c->cand_geom.p,
+                                          (const double*)c->cand_S.p, n, (PairInfo*)c->pinfo.p,
+                                          (double*)c->pS.p, (int*)c->psize.p);
+  k_scan_sizes<<<1, 1024, 0, c->stream>>>((const int*)c->psize.p, counts + 1,
+                                          (long long*)c->voff.p, (long long*)(counts + 4));
+  k_lpt_order<<<gc, 256, 0, c->stream>>>((const int*)c->psize.p, counts + 1, (int*)c->order.p);
+  c->launches += 7;
+  return cudaGetLastError();
+}
+
+}  // namespace sea

@@ -1,0 +1,212 @@
+"""Python binding of libsea.so (argument marshalling only).
+
+Every step of the exchange path runs in the CUDA library; this module only
+passes pointers and sizes through the C ABI declared in ``include/sea.h``.
+Device buffers are torch CUDA tensors (float64, contiguous); host buffers
+are numpy float64 arrays.  There is no CPU fallback: if the library is
+missing the import of :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsea.so")
+
+SEA_OK = 0
+STATUS = {0: "SEA_OK", 1: "SEA_ERR_ARG", 2: "SEA_ERR_STATE", 3: "SEA_ERR_CUDA",
+          4: "SEA_ERR_OOM", 5: "SEA_ERR_CG_NOT_CONVERGED", 6: "SEA_ERR_NOT_PD",
+          7: "SEA_ERR_TIMEOUT", 8: "SEA_ERR_INPUT"}
+
+EXPORTS = ["sea_default_params", "sea_create", "sea_set_orbitals", "sea_apply_vxx",
+           "sea_build_ace", "sea_apply_ace", "sea_get_ace_matrices", "sea_get_ace_vectors",
+           "sea_get_plan", "sea_get_stats", "sea_last_error", "sea_destroy"]
+
+
+class SeaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("delta", ctypes.c_double),
+                ("cg_tol", ctypes.c_double), ("cg_tol_mode", ctypes.c_int),
+                ("cg_max_iter", ctypes.c_int), ("lmax", ctypes.c_int),
+                ("fd_order", ctypes.c_int), ("self_scale", ctypes.c_double),
+                ("precision", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("timeout_ms", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_orb", ctypes.c_int), ("n_pairs", ctypes.c_int),
+                ("n_proto_pairs", ctypes.c_int), ("n_unknowns", ctypes.c_longlong),
+                ("n_window_points", ctypes.c_longlong), ("cg_iters_min", ctypes.c_int),
+                ("cg_iters_max", ctypes.c_int), ("cg_iters_mean", ctypes.c_double),
+                ("cg_unknown_iters", ctypes.c_longlong), ("exx", ctypes.c_double),
+                ("ms_plan", ctypes.c_double), ("ms_setup", ctypes.c_double),
+                ("ms_cg", ctypes.c_double), ("ms_accumulate", ctypes.c_double),
+                ("ms_ace_build", ctypes.c_double), ("ms_ace_apply", ctypes.c_double),
+                ("ace_support_points", ctypes.c_longlong), ("n_launches", ctypes.c_longlong)]
+
+
+_LIB = None
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsea.so (build it first with ``build.build()``)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        L.sea_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.sea_default_params.restype = None
+        L.sea_create.argtypes = [_p, _p, ctypes.POINTER(Params), _p, ctypes.POINTER(_p)]
+        L.sea_set_orbitals.argtypes = [_p, _p, _i, _i]
+        L.sea_apply_vxx.argtypes = [_p, _p, _i, _p]
+        L.sea_build_ace.argtypes = [_p]
+        L.sea_apply_ace.argtypes = [_p, _p, _i, _p, _i]
+        L.sea_get_ace_matrices.argtypes = [_p, _p, _p, _i]
+        L.sea_get_ace_vectors.argtypes = [_p, _p, _i]
+        L.sea_get_plan.argtypes = [_p, _p, _p, _i, _p, _p, _p, _p, _p, _p]
+        L.sea_get_stats.argtypes = [_p, ctypes.POINTER(Stats)]
+        L.sea_last_error.argtypes = [_p]
+        L.sea_last_error.restype = ctypes.c_char_p
+        L.sea_destroy.argtypes = [_p]
+        L.sea_destroy.restype = None
+        for f in EXPORTS:
+            if f not in ("sea_default_params", "sea_last_error", "sea_destroy"):
+                getattr(L, f).restype = _i
+        _LIB = L
+    return _LIB
+
+
+def default_params(**over) -> Params:
+    p = Params()
+    lib().sea_default_params(ctypes.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """(pointer, on_device) of a torch CUDA tensor or a numpy array."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data, 0
+    if getattr(a, "is_cuda", False):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous float64")
+        return a.data_ptr(), 1
+    raise TypeError("expected a numpy array or a CUDA torch tensor")
+
+
+class Context:
+    """One exchange engine on the current CUDA device (see include/sea.h)."""
+
+    def __init__(self, cell, grid, params: Params | None = None, stream=None, **over):
+        self._h = _p()
+        c = (ctypes.c_double * 3)(*cell)
+        g = (ctypes.c_int * 3)(*grid)
+        prm = params if params is not None else default_params(**over)
+        self.grid = tuple(int(x) for x in grid)
+        self.cell = tuple(float(x) for x in cell)
+        s = _p(stream) if stream is not None else None
+        self._check(lib().sea_create(c, g, ctypes.byref(prm), s, ctypes.byref(self._h)), "create")
+        self.n_orb = 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, rc, what):
+        if rc != SEA_OK:
+            msg = lib().sea_last_error(self._h).decode() if self._h else what
+            raise SeaError(rc, f"{what}: {msg}")
+
+    def set_orbitals(self, phi):
+        ptr, dev = _ptr(phi)
+        n = int(phi.shape[0])
+        self._check(lib().sea_set_orbitals(self._h, _p(ptr), n, dev), "set_orbitals")
+        self.n_orb = n
+
+    def apply_vxx(self, out, allow_cap: bool = False):
+        """out <- V_xx phi (same kind as out: torch CUDA tensor or numpy)."""
+        ptr, dev = _ptr(out)
+        e = ctypes.c_double(0.0)
+        rc = lib().sea_apply_vxx(self._h, _p(ptr), dev, ctypes.byref(e))
+        if not (allow_cap and rc == 5):
+            self._check(rc, "apply_vxx")
+        return e.value
+
+    def build_ace(self):
+        self._check(lib().sea_build_ace(self._h), "build_ace")
+
+    def apply_ace(self, psi, out):
+        p1, d1 = _ptr(psi)
+        p2, d2 = _ptr(out)
+        if d1 != d2:
+            raise ValueError("psi and out must both be host or both device")
+        self._check(lib().sea_apply_ace(self._h, _p(p1), int(psi.shape[0]), _p(p2), d1),
+                    "apply_ace")
+
+    def ace_matrices(self):
+        n = self.n_orb
+        M = np.zeros((n, n))
+        L = np.zeros((n, n))
+        self._check(lib().sea_get_ace_matrices(self._h, _p(M.ctypes.data), _p(L.ctypes.data), 0),
+                    "get_ace_matrices")
+        return M, L
+
+    def ace_vectors(self, out):
+        ptr, dev = _ptr(out)
+        self._check(lib().sea_get_ace_vectors(self._h, _p(ptr), dev), "get_ace_vectors")
+
+    def plan(self) -> dict:
+        n = self.n_orb
+        np_ = ctypes.c_int(0)
+        self._check(lib().sea_get_plan(self._h, None, ctypes.byref(np_), 0, None, None, None,
+                                       None, None, None), "get_plan")
+        P = np_.value
+        box = np.zeros((n, 6), np.int32)
+        pairs = np.zeros((P, 2), np.int32)
+        lo = np.zeros((P, 3), np.int32)
+        ext = np.zeros((P, 3), np.int32)
+        S = np.zeros(P)
+        it = np.zeros(P, np.int32)
+        ep = np.zeros(P)
+        c = lambda a: _p(a.ctypes.data)  # noqa: E731
+        self._check(lib().sea_get_plan(self._h, c(box), ctypes.byref(np_), P, c(pairs), c(lo),
+                                       c(ext), c(S), c(it), c(ep)), "get_plan")
+        return dict(box=box, pair=pairs, lo=lo, ext=ext, S=S, iters=it, epair=ep)
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(lib().sea_get_stats(self._h, ctypes.byref(s)), "get_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().sea_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
