@@ -107,7 +107,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    s = synth.make_config(CONFIG)
+    s = synth.make_config(args.config)
     psi_h = synth.random_trial_vectors(N_TRIAL, s.grid, 2024)
     stream = torch.cuda.Stream(device=dev)
     ctx = sea.Context(s.cell, s.grid, stream=stream.cuda_stream)
@@ -175,7 +175,7 @@ def run_ours(args, ws, rank, local):
     psi_pin = torch.from_numpy(psi_h).pin_memory().numpy()
     out_pin = torch.empty(s.phi.shape, dtype=torch.float64).pin_memory().numpy()
     y_pin = torch.empty(psi_h.shape, dtype=torch.float64).pin_memory().numpy()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
 
     def step_host():
         ctx.set_orbitals(phi_pin)
@@ -183,7 +183,8 @@ def run_ours(args, ws, rank, local):
         ctx.build_ace()
         ctx.apply_ace(psi_pin, y_pin)
 
-    step_host()
+    if e2e_steps:
+        step_host()
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -201,7 +202,7 @@ def run_ours(args, ws, rank, local):
         return None
 
     value = ws * args.steps / (t_ms / 1e3)
-    e2e_value = ws * e2e_steps / t_e2e
+    e2e_value = ws * e2e_steps / t_e2e if e2e_steps else None
     K = args.steps
     cg_ms = ms["cg"] / K
     cg_flops = CG_FLOPS_PER_UNKNOWN_ITER * (cg_work / K)
@@ -231,6 +232,8 @@ def run_ours(args, ws, rank, local):
             "n_pairs": stats["n_pairs"],
             "cg_unknowns": stats["n_unknowns"],
             "cg_iters_mean": stats["cg_iters_mean"],
+            "cg_unknown_iters": stats["cg_unknown_iters"],
+            "ace_support_points": stats["ace_support_points"],
             "stage_ms": {k: v / K for k, v in ms.items()},
         },
         "e2e": {
@@ -325,6 +328,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default=CONFIG, help="workload name in synth.CONFIGS "
+                    "(default: the (H2O)64 96^3 benchmark workload; smaller ones for profiling)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
