@@ -110,7 +110,8 @@ def run_ours(args, ws, rank, local):
     s = synth.make_config(args.config)
     psi_h = synth.random_trial_vectors(N_TRIAL, s.grid, 2024)
     stream = torch.cuda.Stream(device=dev)
-    ctx = sea.Context(s.cell, s.grid, stream=stream.cuda_stream)
+    ctx = sea.Context(s.cell, s.grid, stream=stream.cuda_stream,
+                      precision=1 if args.form == "mixed" else 0)
 
     phi = torch.from_numpy(s.phi).to(dev)
     psi = torch.from_numpy(psi_h).to(dev)
@@ -226,7 +227,8 @@ def run_ours(args, ws, rank, local):
             "workload": "(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, "
                         "eps=10^-3.5, delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; "
                         "ACE build + apply to 256 trial vectors",
-            "form": "plain FP64",
+            "form": "plain FP64" if args.form == "plain" else
+                    "mixed: FP32 CG sweeps/vectors inside FP64 refinement",
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
             "l2": "inputs larger than L2 (Phi and psi 1.81 GB each)",
             "n_pairs": stats["n_pairs"],
@@ -331,6 +333,8 @@ def main():
     ap.add_argument("--config", default=CONFIG, help="workload name in synth.CONFIGS "
                     "(default: the (H2O)64 96^3 benchmark workload; smaller ones for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
+    ap.add_argument("--form", choices=["plain", "mixed"], default="plain",
+                    help="plain FP64, or FP32 CG sweeps inside FP64 refinement")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

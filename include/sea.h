@@ -60,7 +60,10 @@ typedef enum {
  * residual density in bohr^-3 as App. C states it), cg_max_iter = 5000,
  * lmax = 6 (App. C), fd_order = 12 (App. C, O(h^12) Laplacian; the only
  * supported value), self_scale = 2 (Omega^D_ii = scale_2x Omega_ii, the only
- * supported value), precision = 0 (FP64 everywhere), warm_start = 0. */
+ * supported value), precision = 0 (FP64 everywhere; 1: the mixed form --
+ * FP32 stencil sweeps and CG vectors inside an FP64 iterative refinement of
+ * each pair's solve: true residual, its norm, the stopping rule, dot
+ * products across the block, E_xx and the ACE stay FP64), warm_start = 0. */
 typedef struct {
   double eps;
   double delta;
@@ -70,7 +73,7 @@ typedef struct {
   int lmax;       /* 0..6 */
   int fd_order;   /* 12 */
   double self_scale;
-  int precision;  /* 0: FP64 */
+  int precision;  /* 0: FP64, 1: mixed (FP32 CG inside FP64 refinement) */
   int warm_start; /* 0: none */
   double timeout_ms; /* reserved, 0 */
 } sea_params;
@@ -144,6 +147,22 @@ sea_status sea_get_plan(sea_ctx* ctx, int* box, int* n_pairs, int max_pairs, int
                         int* lo, int* ext, double* S, int* iters, double* epair);
 
 sea_status sea_get_stats(const sea_ctx* ctx, sea_stats* s);
+
+/* The per-pair Poisson solver on its own (Eq. pe with the O(h^12)
+ * Laplacian of App. C): solve -Lap_h x_b = rhs_b on each of n_box boxes with
+ * zero values outside the box (boundary values, if any, already moved into
+ * rhs), by CG from x = 0 with the stopping rule of sea_params (tol,
+ * tol_mode, max_iter).  h[3]: grid spacing (bohr); ext[n_box][3] (host):
+ * box extents (x, y, z), each in [1, 1024]; rhs, x (device): the boxes'
+ * values concatenated in order, each box [ez][ey][ex]; iters (host, may be
+ * NULL) receives the iteration counts (negative: capped).  Allocates and
+ * frees its own device scratch (3 vectors of the total length) on every
+ * call and synchronizes the stream.  Returns SEA_ERR_CG_NOT_CONVERGED if a
+ * box reached max_iter (x still written). */
+sea_status sea_poisson_batch(const double h[3], int n_box, const int* ext, const double* rhs,
+                             double* x, double tol, int tol_mode, int max_iter, int* iters,
+                             void* cuda_stream);
+
 
 /* Message for the last failing call on ctx (static text; never NULL). */
 const char* sea_last_error(const sea_ctx* ctx);

@@ -265,7 +265,9 @@ int ora_cg(const double* b, double* x, int ex, int ey, int ez, const double h[3]
 /* Per-axis marginals of |phi|^2 dV, each summed in a fixed order:
  *   R[z][y] = sum_x phi^2 (x ascending)   C[z][x] = sum_y phi^2 (y ascending)
  *   mz[z] = (sum_y R[z][y]) dV           my[y] = (sum_z R[z][y]) dV
- *   mx[x] = (sum_z C[z][x]) dV            (outer sums ascending). */
+ *   mx[x] = (sum_z C[z][x]) dV            (outer sums ascending).
+ * Each square is accumulated with one fused multiply-add, s = fma(v, v, s)
+ * (one rounding per term; the paper fixes no rounding for Eq. oii). */
 void ora_marginals(const double* f, const int N[3], double dV, double* mx,
                    double* my, double* mz) {
   int nx = N[0], ny = N[1], nz = N[2];
@@ -276,7 +278,7 @@ void ora_marginals(const double* f, const int N[3], double dV, double* mx,
       double s = 0.0;
       for (int x = 0; x < nx; ++x) {
         double v = f[((size_t)z * ny + y) * nx + x];
-        s = s + v * v;
+        s = fma(v, v, s);
       }
       R[(size_t)z * ny + y] = s;
     }
@@ -285,7 +287,7 @@ void ora_marginals(const double* f, const int N[3], double dV, double* mx,
       double s = 0.0;
       for (int y = 0; y < ny; ++y) {
         double v = f[((size_t)z * ny + y) * nx + x];
-        s = s + v * v;
+        s = fma(v, v, s);
       }
       C[(size_t)z * nx + x] = s;
     }

@@ -2,7 +2,7 @@
 //
 // W = V_xx Phi is exactly zero outside the accumulation windows of each
 // orbital (Eq. tDxx), so every contraction with W runs over the grid tiles
-// (16 x 8 x 4 points) that those windows touch; the result is the dense
+// (8 x 4 x 4 points) that those windows touch; the result is the dense
 // definition's, only without the exact zeros:
 //   M_ij = <phi_i|W_j> = dV sum over tiles of W_j of phi_i W_j
 //   Mbar = (M + M^T)/2, -Mbar = L L^T (Cholesky, one CTA), L^-1
@@ -14,8 +14,8 @@
 
 namespace sea {
 
-#define TX 16
-#define TY 8
+#define TX 8
+#define TY 4
 #define TZ 4
 #define TP (TX * TY * TZ)
 
@@ -143,10 +143,12 @@ __device__ __forceinline__ long long tile_point(const TileGeom& G, int T, int r)
 }
 
 // partial[(tptr[T] + s) * m + a] = sum_{r in T} A[a][r] W[list[s]][r].
-// CTA per (tile, chunk of 128 rows of A); 256 threads = 128 rows x 2 halves
-// of a 16-wide group of W rows; points staged 32 at a time in shared memory.
-#define GA 128
-#define GJ 16
+// CTA per (tile, chunk of 64 rows of A); thread = (row a, quarter q) and
+// accumulates the W rows q, q+4, q+8, ... of the tile's list (no padding:
+// the quarter is uniform across a warp); W rows in blocks of 32, points
+// staged 32 at a time in shared memory.
+#define GA 64
+#define GJ 32
 #define GP 32
 __global__ void __launch_bounds__(256)
     k_gram_partial(const double* __restrict__ A, int m, const double* __restrict__ W,
@@ -157,14 +159,18 @@ __global__ void __launch_bounds__(256)
   const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
   if (nJ == 0) return;
   __shared__ double As[GA][GP + 1];
-  __shared__ double Ws[GJ][GP];
+  __shared__ double Ws[GJ][GP + 1];
   __shared__ long long addr[TP];
+  __shared__ int wrow[GJ];
   for (int r = threadIdx.x; r < TP; r += blockDim.x) addr[r] = tile_point(G, T, r);
-  const int al = threadIdx.x % GA, jh = threadIdx.x / GA;
-  for (int jg = 0; jg < nJ; jg += GJ) {
-    double acc[GJ / 2];
+  const int al = threadIdx.x % GA, qq = threadIdx.x / GA;
+  for (int jb = 0; jb < nJ; jb += GJ) {
+    const int nj = min(GJ, nJ - jb);
+    double acc[GJ / 4];
 #pragma unroll
-    for (int u = 0; u < GJ / 2; ++u) acc[u] = 0.0;
+    for (int u = 0; u < GJ / 4; ++u) acc[u] = 0.0;
+    __syncthreads();
+    if (threadIdx.x < nj) wrow[threadIdx.x] = tlist[j0 + jb + threadIdx.x];
     for (int pc = 0; pc < TP; pc += GP) {
       __syncthreads();
       for (int idx = threadIdx.x; idx < GA * GP; idx += blockDim.x) {
@@ -172,24 +178,25 @@ __global__ void __launch_bounds__(256)
         const long long g = addr[pc + pt];
         As[a][pt] = (a0 + a < m && g >= 0) ? A[(size_t)(a0 + a) * ng + g] : 0.0;
       }
-      for (int idx = threadIdx.x; idx < GJ * GP; idx += blockDim.x) {
+      for (int idx = threadIdx.x; idx < nj * GP; idx += blockDim.x) {
         const int jl = idx / GP, pt = idx % GP;
         const long long g = addr[pc + pt];
-        Ws[jl][pt] = (jg + jl < nJ && g >= 0) ? W[(size_t)tlist[j0 + jg + jl] * ng + g] : 0.0;
+        Ws[jl][pt] = g >= 0 ? W[(size_t)wrow[jl] * ng + g] : 0.0;
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int pt = 0; pt < GP; ++pt) {
         const double av = As[al][pt];
 #pragma unroll
-        for (int u = 0; u < GJ / 2; ++u) acc[u] = fma(av, Ws[jh * (GJ / 2) + u][pt], acc[u]);
+        for (int u = 0; u < GJ / 4; ++u)
+          if (qq + 4 * u < nj) acc[u] = fma(av, Ws[qq + 4 * u][pt], acc[u]);
       }
     }
     if (a0 + al < m) {
 #pragma unroll
-      for (int u = 0; u < GJ / 2; ++u) {
-        const int jl = jg + jh * (GJ / 2) + u;
-        if (jl < nJ) partial[(size_t)(j0 + jl) * m + a0 + al] = acc[u];
+      for (int u = 0; u < GJ / 4; ++u) {
+        const int jl = qq + 4 * u;
+        if (jl < nj) partial[(size_t)(j0 + jb + jl) * m + a0 + al] = acc[u];
       }
     }
   }
@@ -208,43 +215,107 @@ __global__ void k_gram_reduce(const double* __restrict__ partial, int m, int n_o
   out[(size_t)a * sa + (size_t)o * so] = scale * s;
 }
 
-// -Mbar = L L^T, right-looking, one CTA; L overwrites A's lower triangle,
-// the upper triangle is zeroed.  A non-positive pivot sets SEA_FLAG_NOT_PD
-// and stops.
-__global__ void k_cholesky(const double* __restrict__ M, int n, double* __restrict__ A,
-                           unsigned* __restrict__ status) {
-  for (size_t q = threadIdx.x; q < (size_t)n * n; q += blockDim.x) {
-    const int i = (int)(q / n), j = (int)(q % n);
-    A[q] = -0.5 * (M[(size_t)i * n + j] + M[(size_t)j * n + i]);
-  }
+// -Mbar = L L^T by a blocked right-looking Cholesky over several kernels
+// (block 32): k_chol_init forms A = -(M + M^T)/2; per block column,
+// k_chol_panel factors the 32 x 32 diagonal block in shared memory and
+// solves the rows below it; k_chol_update subtracts the panel's
+// contribution from the trailing lower triangle, one CTA per 32 x 32 block.
+// A non-positive pivot sets SEA_FLAG_NOT_PD and the later kernels return.
+#define CB 32
+__global__ void k_chol_init(const double* __restrict__ M, int n, double* __restrict__ A) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)n * n) return;
+  const int i = (int)(q / n), j = (int)(q % n);
+  A[q] = (j <= i) ? -0.5 * (M[(size_t)i * n + j] + M[(size_t)j * n + i]) : 0.0;
+}
+
+__global__ void __launch_bounds__(256)
+    k_chol_panel(double* __restrict__ A, int n, int kb, unsigned* __restrict__ status) {
+  if (*status & SEA_FLAG_NOT_PD) return;
+  __shared__ double D[CB][CB + 1];
   __shared__ int bad;
+  const int nb = min(CB, n - kb);
   if (threadIdx.x == 0) bad = 0;
+  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
+    const int i = q / CB, j = q % CB;
+    D[i][j] = (i < nb && j < nb) ? A[(size_t)(kb + i) * n + kb + j] : 0.0;
+  }
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = A[(size_t)k * n + k];
+  if (threadIdx.x < 32) {  // one warp factors the diagonal block
+    const int lane = threadIdx.x;
+    for (int k = 0; k < nb; ++k) {
+      double d = D[k][k];
       if (!(d > 0.0)) {
-        bad = 1;
-        atomicOr(status, SEA_FLAG_NOT_PD);
-      } else {
-        A[(size_t)k * n + k] = sqrt(d);
+        if (lane == 0) bad = 1;
+        break;
+      }
+      d = sqrt(d);
+      __syncwarp();
+      if (lane == 0) D[k][k] = d;
+      if (lane > k && lane < nb) D[lane][k] /= d;
+      __syncwarp();
+      for (int j = k + 1; j < nb; ++j)
+        if (lane >= j && lane < nb) D[lane][j] = fma(-D[lane][k], D[j][k], D[lane][j]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicOr(status, SEA_FLAG_NOT_PD);
+    return;
+  }
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int i = q / nb, j = q % nb;
+    if (j <= i) A[(size_t)(kb + i) * n + kb + j] = D[i][j];
+  }
+  // rows below: x L_kk^T = a  (forward substitution per row)
+  for (int i = kb + nb + threadIdx.x; i < n; i += blockDim.x) {
+    double x[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) x[j] = j < nb ? A[(size_t)i * n + kb + j] : 0.0;
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      if (j < nb) {
+        double v = x[j];
+        for (int l = 0; l < j; ++l) v = fma(-x[l], D[j][l], v);
+        x[j] = v / D[j][j];
       }
     }
-    __syncthreads();
-    if (bad) return;
-    const double dk = A[(size_t)k * n + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + k] /= dk;
-    __syncthreads();
-    const int mm = n - k - 1;
-    for (long long idx = threadIdx.x; idx < (long long)mm * mm; idx += blockDim.x) {
-      const int i = k + 1 + (int)(idx / mm), j = k + 1 + (int)(idx % mm);
-      if (j <= i) A[(size_t)i * n + j] = fma(-A[(size_t)i * n + k], A[(size_t)j * n + k], A[(size_t)i * n + j]);
-    }
-    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < CB; ++j)
+      if (j < nb) A[(size_t)i * n + kb + j] = x[j];
   }
-  for (size_t q = threadIdx.x; q < (size_t)n * n; q += blockDim.x) {
-    const int i = (int)(q / n), j = (int)(q % n);
-    if (j > i) A[q] = 0.0;
+}
+
+__global__ void __launch_bounds__(256)
+    k_chol_update(double* __restrict__ A, int n, int kb, const unsigned* __restrict__ status) {
+  if (*status & SEA_FLAG_NOT_PD) return;
+  // lower-triangular block (bi, bj), bj <= bi, of the trailing matrix
+  const int t0 = kb + CB;
+  const int nbt = (n - t0 + CB - 1) / CB;
+  int bi = 0, rem = blockIdx.x;
+  while (rem > bi) {
+    rem -= bi + 1;
+    ++bi;
+  }
+  const int bj = rem;
+  if (bi >= nbt) return;
+  __shared__ double Li[CB][CB + 1], Lj[CB][CB + 1];
+  const int i0 = t0 + bi * CB, j0 = t0 + bj * CB;
+  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
+    const int r = q / CB, k = q % CB;
+    Li[r][k] = (i0 + r < n) ? A[(size_t)(i0 + r) * n + kb + k] : 0.0;
+    Lj[r][k] = (j0 + r < n) ? A[(size_t)(j0 + r) * n + kb + k] : 0.0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
+    const int r = q / CB, cidx = q % CB;
+    const int i = i0 + r, j = j0 + cidx;
+    if (i >= n || j >= n || j > i) continue;
+    double s = A[(size_t)i * n + j];
+#pragma unroll 8
+    for (int k = 0; k < CB; ++k) s = fma(-Li[r][k], Lj[cidx][k], s);
+    A[(size_t)i * n + j] = s;
   }
 }
 
@@ -286,8 +357,9 @@ __global__ void k_small_gemm(const double* __restrict__ A, int transA, const dou
 }
 
 // out[v][r] = sign * sum_{j in tile list} W[j][r] H(j, v), H(j, v) =
-// H[j * hj + v * hv], for every point r of the tile and v in a chunk of 16.
-#define EV 16
+// H[j * hj + v * hv], for every point r of the tile and v in a chunk of 32:
+// thread = (point, half of the chunk), 16 accumulators.
+#define EV 32
 __global__ void __launch_bounds__(256)
     k_tile_expand(const double* __restrict__ W, TileGeom G, size_t ng,
                   const int* __restrict__ tptr, const int* __restrict__ tlist,
@@ -302,31 +374,22 @@ __global__ void __launch_bounds__(256)
     Hs[idx] = (v0 + vl < m) ? H[(long long)tlist[j0 + jl] * hj + (long long)(v0 + vl) * hv] : 0.0;
   }
   __syncthreads();
-  const long long g0 = tile_point(G, T, threadIdx.x);
-  const long long g1 = tile_point(G, T, threadIdx.x + 256);
-  double acc0[EV], acc1[EV];
+  const int pt = threadIdx.x % TP, vh = threadIdx.x / TP;
+  const long long g = tile_point(G, T, pt);
+  double acc[EV / 2];
 #pragma unroll
-  for (int u = 0; u < EV; ++u) {
-    acc0[u] = 0.0;
-    acc1[u] = 0.0;
-  }
+  for (int u = 0; u < EV / 2; ++u) acc[u] = 0.0;
   for (int jl = 0; jl < nJ; ++jl) {
-    const double* Wj = W + (size_t)tlist[j0 + jl] * ng;
-    const double w0 = g0 >= 0 ? Wj[g0] : 0.0;
-    const double w1 = g1 >= 0 ? Wj[g1] : 0.0;
+    const double w = g >= 0 ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0;
+    const double* hrow = Hs + jl * EV + vh * (EV / 2);
 #pragma unroll
-    for (int u = 0; u < EV; ++u) {
-      const double hvv = Hs[jl * EV + u];
-      acc0[u] = fma(w0, hvv, acc0[u]);
-      acc1[u] = fma(w1, hvv, acc1[u]);
-    }
+    for (int u = 0; u < EV / 2; ++u) acc[u] = fma(w, hrow[u], acc[u]);
   }
+  if (g < 0) return;
 #pragma unroll
-  for (int u = 0; u < EV; ++u) {
-    if (v0 + u >= m) break;
-    double* o = out + (size_t)(v0 + u) * ng;
-    if (g0 >= 0) o[g0] = sign * acc0[u];
-    if (g1 >= 0) o[g1] = sign * acc1[u];
+  for (int u = 0; u < EV / 2; ++u) {
+    const int v = v0 + vh * (EV / 2) + u;
+    if (v < m) out[(size_t)v * ng + g] = sign * acc[u];
   }
 }
 
@@ -402,11 +465,20 @@ cudaError_t launch_ace_build(sea_ctx* c) {
       (double*)c->partial.p);
   k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p, n, 1);
-  k_cholesky<<<1, 1024, 0, c->stream>>>((const double*)c->Mbuf.p, n, (double*)c->Lbuf.p,
-                                        (unsigned*)c->status.p);
+  k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
+      (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
+  int nchol = 1;
+  for (int kb = 0; kb < n; kb += CB) {
+    k_chol_panel<<<1, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb, (unsigned*)c->status.p);
+    const int nbt = (n - kb - CB + CB - 1) / CB;
+    if (nbt > 0)
+      k_chol_update<<<nbt * (nbt + 1) / 2, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb,
+                                                                 (const unsigned*)c->status.p);
+    nchol += 1 + (nbt > 0);
+  }
   k_trinv<<<n, 256, n * sizeof(double), c->stream>>>((const double*)c->Lbuf.p, n,
                                                      (double*)c->Linv.p);
-  c->launches += 12;
+  c->launches += 11 + nchol;
   return cudaGetLastError();
 }
 

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "sea_internal.cuh"
@@ -40,7 +41,7 @@ cudaError_t launch_plan_pairs(sea_ctx* c);
 // Second-derivative weights of the symmetric 13-point stencil by Fornberg's
 // recursion (B. Fornberg, Math. Comp. 51, 699 (1988)) for nodes
 // 0, 1, -1, ..., 6, -6; returns w[k], k = 0..6 (symmetric).
-static void fornberg_second_derivative(double* w) {
+void sea::fornberg_weights(double* w) {
   const int np = 2 * SEA_FDP + 1, M = 2;
   double x[2 * SEA_FDP + 1];
   x[0] = 0.0;
@@ -151,7 +152,7 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
   if (p) prm = *p;
   if (!(prm.eps >= 0.0 && prm.eps < 1.0) || !(prm.delta >= 0.0) || !(prm.cg_tol > 0.0) ||
       prm.cg_max_iter < 1 || prm.lmax < 0 || prm.lmax > SEA_LMAX || prm.fd_order != 12 ||
-      prm.self_scale != 2.0 || prm.precision != 0 || prm.warm_start != 0 ||
+      prm.self_scale != 2.0 || (prm.precision != 0 && prm.precision != 1) || prm.warm_start != 0 ||
       (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1))
     return SEA_ERR_ARG;
   sea_ctx* c = new (std::nothrow) sea_ctx();
@@ -170,7 +171,7 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
   c->dV = c->h[0] * c->h[1] * c->h[2];
   c->ng = (size_t)grid[0] * grid[1] * grid[2];
   double w[SEA_FDP + 1];
-  fornberg_second_derivative(w);
+  sea::fornberg_weights(w);
   c->w_center = 0.0;
   for (int a = 0; a < 3; ++a) {
     const double ih2 = 1.0 / (c->h[a] * c->h[a]);
@@ -441,6 +442,90 @@ sea_status sea_get_plan(sea_ctx* c, int* box, int* n_pairs, int max_pairs, int* 
   }
   SEA_CK(cudaStreamSynchronize(c->stream), "get_plan");
   return SEA_OK;
+}
+
+sea_status sea_poisson_batch(const double h[3], int n_box, const int* ext, const double* rhs,
+                             double* x, double tol, int tol_mode, int max_iter, int* iters,
+                             void* cuda_stream) {
+  if (!h || n_box < 0 || (n_box > 0 && (!ext || !rhs || !x))) return SEA_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!(h[a] > 0.0)) return SEA_ERR_ARG;
+  if (!(tol > 0.0) || max_iter < 1 || (tol_mode != 0 && tol_mode != 1)) return SEA_ERR_ARG;
+  if (n_box == 0) return SEA_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return SEA_ERR_CUDA;
+  PairInfo* hb = (PairInfo*)malloc((size_t)n_box * sizeof(PairInfo));
+  long long* ho = (long long*)malloc((size_t)n_box * sizeof(long long));
+  int* hord = (int*)malloc((size_t)n_box * sizeof(int));
+  if (!hb || !ho || !hord) {
+    free(hb);
+    free(ho);
+    free(hord);
+    return SEA_ERR_OOM;
+  }
+  long long tot = 0;
+  sea_status rs = SEA_OK;
+  for (int b = 0; b < n_box && rs == SEA_OK; ++b) {
+    PairInfo P;
+    memset(&P, 0, sizeof(P));
+    for (int a = 0; a < 3; ++a) {
+      P.ext[a] = ext[3 * b + a];
+      if (P.ext[a] < 1 || P.ext[a] > 1024) rs = SEA_ERR_ARG;
+    }
+    P.n = P.ext[0] * P.ext[1] * P.ext[2];
+    hb[b] = P;
+    ho[b] = tot;
+    tot += P.n;
+    hord[b] = b;
+  }
+  if (rs != SEA_OK) {
+    free(hb);
+    free(ho);
+    free(hord);
+    return rs;
+  }
+  // longest boxes first
+  std::stable_sort(hord, hord + n_box, [&](int a, int b) { return hb[a].n > hb[b].n; });
+  void* dev = nullptr;
+  const size_t bytes = (size_t)n_box * (sizeof(PairInfo) + sizeof(long long) + 2 * sizeof(int)) +
+                       3 * (size_t)tot * sizeof(double) + 64;
+  if (cudaMalloc(&dev, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free(hb);
+    free(ho);
+    free(hord);
+    return SEA_ERR_OOM;
+  }
+  char* q = (char*)dev;
+  double* r = (double*)q;
+  double* pp = r + tot;
+  double* qq = pp + tot;
+  q = (char*)(qq + tot);
+  long long* dvoff = (long long*)q;
+  PairInfo* dbox = (PairInfo*)(dvoff + n_box);
+  int* dord = (int*)(dbox + n_box);
+  int* dit = dord + n_box;
+  unsigned* dst = (unsigned*)(dit + n_box);
+  int* dq = (int*)(dst + 1);
+  cudaError_t e = cudaMemcpyAsync(dvoff, ho, n_box * sizeof(long long), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbox, hb, n_box * sizeof(PairInfo), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dord, hord, n_box * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dst, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess)
+    e = sea::launch_cg_boxes(st, device, h, n_box, dbox, dvoff, dord, rhs, x, r, pp, qq, dit, dst,
+                             dq, tol, tol_mode, max_iter);
+  unsigned hst = 0;
+  if (e == cudaSuccess && iters)
+    e = cudaMemcpyAsync(iters, dit, n_box * sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, dst, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dev);
+  free(hb);
+  free(ho);
+  free(hord);
+  if (e != cudaSuccess) return SEA_ERR_CUDA;
+  return (hst & SEA_FLAG_CG_CAP) ? SEA_ERR_CG_NOT_CONVERGED : SEA_OK;
 }
 
 sea_status sea_get_stats(const sea_ctx* c, sea_stats* s) {

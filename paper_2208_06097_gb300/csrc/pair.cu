@@ -11,6 +11,8 @@
 //   the 37-point O(h^12) operator written as 37 fused multiply-adds (on this
 //   part the FP64 FMA pipe issues faster than FP64 add); then the pair
 //   integral sum rho v dV of Eq. exxGen_mlwf.
+#include <cstring>
+
 #include "sea_internal.cuh"
 
 namespace sea {
@@ -147,35 +149,61 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
-// q = -Lap_h p at box point t = (x, y, z), zero outside the box.
+// Contribution of one axis to q = -Lap_h p at box point t (coordinate u
+// along that axis, extent e, stride st), zero outside the box.
+__device__ __forceinline__ double lap_axis(const double* __restrict__ pv, int t, int u, int e,
+                                           int st, const double* __restrict__ w) {
+  double a = 0.0;
+#pragma unroll
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    const double L = (u - k >= 0) ? pv[t - k * st] : 0.0;
+    const double R = (u + k < e) ? pv[t + k * st] : 0.0;
+    a = fma(w[k], L, a);
+    a = fma(w[k], R, a);
+  }
+  return a;
+}
+
+// q = -Lap_h p at box point t = (x, y, z): three independent FMA chains
+// (one per axis) to keep the FP64 pipe fed.
 __device__ __forceinline__ double neg_lap(const double* __restrict__ pv, int t, int x, int y,
                                           int z, int ex, int ey, int ez, const StencilW& W) {
-  const int sy = ex, sz = ex * ey;
-  double a0 = W.center * pv[t];
-  double a1 = 0.0;
-#pragma unroll
-  for (int k = 1; k <= SEA_FDP; ++k) {
-    const double L = (x - k >= 0) ? pv[t - k] : 0.0;
-    const double R = (x + k < ex) ? pv[t + k] : 0.0;
-    a0 = fma(W.ax[0][k], L, a0);
-    a1 = fma(W.ax[0][k], R, a1);
-  }
-#pragma unroll
-  for (int k = 1; k <= SEA_FDP; ++k) {
-    const double L = (y - k >= 0) ? pv[t - k * sy] : 0.0;
-    const double R = (y + k < ey) ? pv[t + k * sy] : 0.0;
-    a0 = fma(W.ax[1][k], L, a0);
-    a1 = fma(W.ax[1][k], R, a1);
-  }
-#pragma unroll
-  for (int k = 1; k <= SEA_FDP; ++k) {
-    const double L = (z - k >= 0) ? pv[t - k * sz] : 0.0;
-    const double R = (z + k < ez) ? pv[t + k * sz] : 0.0;
-    a0 = fma(W.ax[2][k], L, a0);
-    a1 = fma(W.ax[2][k], R, a1);
-  }
-  return a0 + a1;
+  const double ax = lap_axis(pv, t, x, ex, 1, W.ax[0]);
+  const double ay = lap_axis(pv, t, y, ey, ex, W.ax[1]);
+  const double az = fma(W.center, pv[t], lap_axis(pv, t, z, ez, ex * ey, W.ax[2]));
+  return (ax + ay) + az;
 }
+
+// Walks the points t = t0, t0 + S, t0 + 2S, ... of an ex x ey x ez box in
+// [z][y][x] order with their coordinates, without divisions in the loop.
+struct BoxWalk {
+  int t, x, y, z, dx, dy, dz, ex, ey;
+  __device__ BoxWalk(int t0, int S, int ex_, int ey_) : ex(ex_), ey(ey_) {
+    t = t0;
+    x = t0 % ex;
+    y = (t0 / ex) % ey;
+    z = t0 / (ex * ey);
+    dx = S % ex;
+    dy = (S / ex) % ey;
+    dz = S / (ex * ey);
+  }
+  __device__ __forceinline__ void next(int S) {
+    t += S;
+    x += dx;
+    int cy = 0;
+    if (x >= ex) {
+      x -= ex;
+      cy = 1;
+    }
+    y += dy + cy;
+    int cz = 0;
+    if (y >= ey) {
+      y -= ey;
+      cz = 1;
+    }
+    z += dz + cz;
+  }
+};
 
 struct CgArgs {
   const double* phi;
@@ -227,14 +255,26 @@ __global__ void __launch_bounds__(256) k_cg(CgArgs A, StencilW W) {
     int it = 0;
     bool done = sqrt(rr) <= target;
     while (!done && it < A.max_iter) {
-      double pq = 0.0;
-      for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
-        const double qt = neg_lap(pv, t, xx, yy, zz, ex, ey, ez, W);
-        q[t] = qt;
-        pq = fma(pv[t], qt, pq);
+      double pq = 0.0, pq2 = 0.0;
+      {
+        const int S = blockDim.x;
+        BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
+        BoxWalk w1(threadIdx.x + S, 2 * S, ex, ey);
+        for (; w1.t < n; w0.next(2 * S), w1.next(2 * S)) {
+          const double q0 = neg_lap(pv, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
+          const double q1 = neg_lap(pv, w1.t, w1.x, w1.y, w1.z, ex, ey, ez, W);
+          q[w0.t] = q0;
+          q[w1.t] = q1;
+          pq = fma(pv[w0.t], q0, pq);
+          pq2 = fma(pv[w1.t], q1, pq2);
+        }
+        if (w0.t < n) {
+          const double q0 = neg_lap(pv, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
+          q[w0.t] = q0;
+          pq = fma(pv[w0.t], q0, pq);
+        }
       }
-      pq = block_sum(pq, red[1]);
+      pq = block_sum(pq + pq2, red[1]);
       const double alpha = rr / pq;
       double rn = 0.0;
       for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -256,11 +296,12 @@ __global__ void __launch_bounds__(256) k_cg(CgArgs A, StencilW W) {
       for (int t = threadIdx.x; t < n; t += blockDim.x) pv[t] = fma(beta, pv[t], r[t]);
       __syncthreads();
     }
-    // pair integral of Eq. exxGen_mlwf over Omega_ij
-    const double* fi = A.phi + (size_t)P.i * ng;
-    const double* fj = A.phi + (size_t)P.j * ng;
+    // pair integral of Eq. exxGen_mlwf over Omega_ij (skipped for a bare
+    // batch of boxes, phi == nullptr)
+    const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
+    const double* fj = A.phi ? A.phi + (size_t)P.j * ng : nullptr;
     double e = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    for (int t = threadIdx.x; fi && t < n; t += blockDim.x) {
       const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
       const size_t g = ((size_t)wrapi(P.lo[2] + zz, A.nz) * A.ny + wrapi(P.lo[1] + yy, A.ny)) * A.nx +
                        wrapi(P.lo[0] + xx, A.nx);
@@ -268,9 +309,213 @@ __global__ void __launch_bounds__(256) k_cg(CgArgs A, StencilW W) {
     }
     e = block_sum(e, red[1]);
     if (threadIdx.x == 0) {
-      A.epair[pidx] = e * A.dV;
+      if (A.epair) A.epair[pidx] = e * A.dV;
       A.iters[pidx] = done ? it : -it;
       if (!done) atomicOr(A.status, SEA_FLAG_CG_CAP);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision form: FP32 stencil sweeps and CG vectors, FP64 where the
+// accuracy is decided.  Per pair, iterative refinement:
+//   x = 0 (FP64), r = b (FP64)
+//   while ||r||_2 > tol ||b||_2 (FP64 norm of the true FP64 residual):
+//     solve A d = r / ||r|| by CG in FP32 to a relative residual of
+//       SEA_MIXED_INNER (dot products: per-thread partial sums in
+//       compensated FP32 -- exact products by FMA, error-free additions --
+//       then summed across the block in FP64)
+//     x += ||r|| d (FP64);  r = b - A x (FP64 stencil)
+// The stopping rule is applied to the true FP64 residual, so the result
+// meets the same bound as the FP64 solver.
+// ---------------------------------------------------------------------------
+#define SEA_MIXED_INNER 1e-4f
+#define SEA_MIXED_MAX_OUTER 30
+
+struct StencilWf {
+  float ax[3][SEA_FDP + 1];
+  float center;
+};
+
+// Compensated FP32 accumulator of a sum of products (value = hi + lo).
+struct DotF {
+  float hi, lo;
+  __device__ DotF() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);  // exact product = p + pe
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float se = (hi - (s - bb)) + (p - bb);  // exact sum = s + se
+    hi = s;
+    lo += se + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ float lap_axis_f(const float* __restrict__ pv, int t, int u, int e,
+                                            int st, const float* __restrict__ w) {
+  float a = 0.f;
+#pragma unroll
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    const float L = (u - k >= 0) ? pv[t - k * st] : 0.f;
+    const float R = (u + k < e) ? pv[t + k * st] : 0.f;
+    a = fmaf(w[k], L, a);
+    a = fmaf(w[k], R, a);
+  }
+  return a;
+}
+
+__device__ __forceinline__ float neg_lap_f(const float* __restrict__ pv, int t, int x, int y,
+                                           int z, int ex, int ey, int ez, const StencilWf& W) {
+  const float ax = lap_axis_f(pv, t, x, ex, 1, W.ax[0]);
+  const float ay = lap_axis_f(pv, t, y, ey, ex, W.ax[1]);
+  const float az = fmaf(W.center, pv[t], lap_axis_f(pv, t, z, ez, ex * ey, W.ax[2]));
+  return (ax + ay) + az;
+}
+
+struct CgMixedArgs {
+  const double* phi;
+  int nx, ny, nz;
+  const PairInfo* pinfo;
+  const long long* voff;
+  const int* order;
+  int P;
+  double dV, tol;
+  int tol_mode, max_iter;
+  double *x, *b, *r;       // FP64: solution, right-hand side, true residual
+  float *d, *rf, *pf, *qf;  // FP32 inner-solve vectors
+  double* epair;
+  int* iters;     // total inner iterations (negative if capped)
+  int* outers;    // refinement steps
+  unsigned* status;
+  int* queue;
+};
+
+__global__ void __launch_bounds__(256) k_cg_mixed(CgMixedArgs A, StencilW W, StencilWf Wf) {
+  __shared__ double red[2][32];
+  __shared__ int s_item;
+  const size_t ng = (size_t)A.nx * A.ny * A.nz;
+  const int S = blockDim.x;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= A.P) break;
+    const int pidx = A.order[item];
+    const PairInfo P = A.pinfo[pidx];
+    const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2], n = P.n;
+    const long long off = A.voff[pidx];
+    double* x = A.x + off;
+    const double* b = A.b + off;
+    double* r = A.r + off;
+    float* d = A.d + off;
+    float* rf = A.rf + off;
+    float* pf = A.pf + off;
+    float* qf = A.qf + off;
+
+    double bb = 0.0;
+    for (int t = threadIdx.x; t < n; t += S) {
+      const double bt = b[t];
+      x[t] = 0.0;
+      r[t] = bt;
+      bb = fma(bt, bt, bb);
+    }
+    bb = block_sum(bb, red[0]);
+    const double bnorm = sqrt(bb);
+    const double target =
+        A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
+    double rnorm = bnorm;
+    int inner_total = 0, outer = 0;
+    bool done = rnorm <= target, capped = false;
+    while (!done) {
+      if (outer >= SEA_MIXED_MAX_OUTER || inner_total >= A.max_iter) {
+        capped = true;
+        break;
+      }
+      // inner FP32 CG on A d = r / ||r||
+      const double inv = 1.0 / rnorm;
+      DotF rr0;
+      for (int t = threadIdx.x; t < n; t += S) {
+        const float v = (float)(r[t] * inv);
+        rf[t] = v;
+        pf[t] = v;
+        d[t] = 0.f;
+        rr0.add(v, v);
+      }
+      double rr = block_sum(rr0.value(), red[1]);
+      const double inner_target = (double)SEA_MIXED_INNER * sqrt(rr);
+      int k = 0;
+      while (sqrt(rr) > inner_target && inner_total < A.max_iter) {
+        DotF pq0, pq1;
+        {
+          BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
+          BoxWalk w1(threadIdx.x + S, 2 * S, ex, ey);
+          for (; w1.t < n; w0.next(2 * S), w1.next(2 * S)) {
+            const float q0 = neg_lap_f(pf, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wf);
+            const float q1 = neg_lap_f(pf, w1.t, w1.x, w1.y, w1.z, ex, ey, ez, Wf);
+            qf[w0.t] = q0;
+            qf[w1.t] = q1;
+            pq0.add(pf[w0.t], q0);
+            pq1.add(pf[w1.t], q1);
+          }
+          if (w0.t < n) {
+            const float q0 = neg_lap_f(pf, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wf);
+            qf[w0.t] = q0;
+            pq0.add(pf[w0.t], q0);
+          }
+        }
+        const double pq = block_sum(pq0.value() + pq1.value(), red[0]);
+        const float alpha = (float)(rr / pq);
+        DotF rn0;
+        for (int t = threadIdx.x; t < n; t += S) {
+          d[t] = fmaf(alpha, pf[t], d[t]);
+          const float rt = fmaf(-alpha, qf[t], rf[t]);
+          rf[t] = rt;
+          rn0.add(rt, rt);
+        }
+        const double rn = block_sum(rn0.value(), red[1]);
+        ++k;
+        ++inner_total;
+        const float beta = (float)(rn / rr);
+        rr = rn;
+        if (sqrt(rn) <= inner_target) break;
+        for (int t = threadIdx.x; t < n; t += S) pf[t] = fmaf(beta, pf[t], rf[t]);
+        __syncthreads();
+      }
+      // FP64 correction and true residual
+      for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+      __syncthreads();
+      double r2 = 0.0;
+      {
+        BoxWalk w0(threadIdx.x, S, ex, ey);
+        for (; w0.t < n; w0.next(S)) {
+          const double rt = b[w0.t] - neg_lap(x, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
+          r[w0.t] = rt;
+          r2 = fma(rt, rt, r2);
+        }
+      }
+      rnorm = sqrt(block_sum(r2, red[0]));
+      ++outer;
+      done = rnorm <= target;
+    }
+    // pair integral of Eq. exxGen_mlwf over Omega_ij
+    const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
+    const double* fj = A.phi ? A.phi + (size_t)P.j * ng : nullptr;
+    double e = 0.0;
+    for (int t = threadIdx.x; fi && t < n; t += S) {
+      const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
+      const size_t g = ((size_t)wrapi(P.lo[2] + zz, A.nz) * A.ny + wrapi(P.lo[1] + yy, A.ny)) * A.nx +
+                       wrapi(P.lo[0] + xx, A.nx);
+      e = fma(fi[g] * fj[g], x[t], e);
+    }
+    e = block_sum(e, red[1]);
+    if (threadIdx.x == 0) {
+      if (A.epair) A.epair[pidx] = e * A.dV;
+      A.iters[pidx] = capped ? -inner_total : inner_total;
+      if (A.outers) A.outers[pidx] = outer;
+      if (capped) atomicOr(A.status, SEA_FLAG_CG_CAP);
     }
     __syncthreads();
   }
@@ -297,14 +542,58 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
   return cudaGetLastError();
 }
 
+static StencilWf make_weights_f(const StencilW& W) {
+  StencilWf F;
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k <= SEA_FDP; ++k) F.ax[a][k] = (float)W.ax[a][k];
+  F.center = (float)W.center;
+  return F;
+}
+
 cudaError_t launch_cg(sea_ctx* c) {
   if (c->P == 0) return cudaSuccess;
   int nsm = 0, occ = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, 256, 0);
+  if (c->prm.precision == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_mixed, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, 256, 0);
   if (occ < 1) occ = 1;
   const int grid = min(c->P, nsm * occ);
   cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream);
+  const StencilW W = make_weights(c);
+  if (c->prm.precision == 1) {
+    CgMixedArgs A;
+    memset(&A, 0, sizeof(A));
+    A.phi = (const double*)c->phi.p;
+    A.nx = c->N[0];
+    A.ny = c->N[1];
+    A.nz = c->N[2];
+    A.pinfo = (const PairInfo*)c->pinfo.p;
+    A.voff = (const long long*)c->voff.p;
+    A.order = (const int*)c->order.p;
+    A.P = c->P;
+    A.dV = c->dV;
+    A.tol = c->prm.cg_tol;
+    A.tol_mode = c->prm.cg_tol_mode;
+    A.max_iter = c->prm.cg_max_iter;
+    A.x = (double*)c->vbuf.p;
+    A.b = (double*)c->bbuf.p;
+    A.r = (double*)c->rbuf.p;
+    // FP32 vectors: two per FP64-sized buffer
+    A.d = (float*)c->pbuf.p;
+    A.rf = A.d + c->U;
+    A.pf = (float*)c->qbuf.p;
+    A.qf = A.pf + c->U;
+    A.epair = (double*)c->epair.p;
+    A.iters = (int*)c->iters.p;
+    A.outers = nullptr;
+    A.status = (unsigned*)c->status.p;
+    A.queue = (int*)c->queue.p;
+    k_cg_mixed<<<grid, 256, 0, c->stream>>>(A, W, make_weights_f(W));
+    c->launches += 1;
+    return cudaGetLastError();
+  }
   CgArgs A;
   A.phi = (const double*)c->phi.p;
   A.nx = c->N[0];
@@ -327,8 +616,60 @@ cudaError_t launch_cg(sea_ctx* c) {
   A.iters = (int*)c->iters.p;
   A.status = (unsigned*)c->status.p;
   A.queue = (int*)c->queue.p;
-  k_cg<<<grid, 256, 0, c->stream>>>(A, make_weights(c));
+  k_cg<<<grid, 256, 0, c->stream>>>(A, W);
   c->launches += 1;
+  return cudaGetLastError();
+}
+
+// Batched solve of -Lap_h x = rhs on independent boxes (no pair energies):
+// boxes[] and voff[] on the device, order[] the processing order; r, p, q
+// scratch of the same total length as x.
+cudaError_t launch_cg_boxes(cudaStream_t stream, int device, const double h[3], int nbox,
+                            const PairInfo* boxes, const long long* voff, const int* order,
+                            const double* rhs, double* x, double* r, double* p, double* q,
+                            int* iters, unsigned* status, int* queue, double tol, int tol_mode,
+                            int max_iter) {
+  if (nbox == 0) return cudaSuccess;
+  double w[SEA_FDP + 1];
+  fornberg_weights(w);
+  StencilW W;
+  W.center = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double ih2 = 1.0 / (h[a] * h[a]);
+    for (int k = 0; k <= SEA_FDP; ++k) {
+      W.ax[a][k] = -w[k] * ih2;
+      W.rhs[a][k] = w[k] * ih2;
+    }
+    W.center += -w[0] * ih2;
+  }
+  int nsm = 0, occ = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, 256, 0);
+  if (occ < 1) occ = 1;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  CgArgs A;
+  memset(&A, 0, sizeof(A));
+  A.phi = nullptr;
+  A.nx = A.ny = A.nz = 1;
+  A.pinfo = boxes;
+  A.voff = voff;
+  A.order = order;
+  A.P = nbox;
+  A.dV = h[0] * h[1] * h[2];
+  A.tol = tol;
+  A.tol_mode = tol_mode;
+  A.max_iter = max_iter;
+  A.x = x;
+  A.b = (double*)rhs;
+  A.r = r;
+  A.p = p;
+  A.q = q;
+  A.epair = nullptr;
+  A.iters = iters;
+  A.status = status;
+  A.queue = queue;
+  k_cg<<<min(nbox, nsm * occ), 256, 0, stream>>>(A, W);
   return cudaGetLastError();
 }
 

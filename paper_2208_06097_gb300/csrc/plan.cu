@@ -1,10 +1,11 @@
 // plan.cu -- domain truncation (Eq. oii) and pair selection (Eq. sij).
 //
 // Both steps end in integer decisions taken on FP64 sums.  Every sum here
-// has a fixed order and no fused multiply-add (__dmul_rn/__dadd_rn), so the
-// decisions do not depend on the launch shape:
+// has a fixed order and a fixed rounding (explicit fma, or __dmul_rn /
+// __dadd_rn where no fusion is wanted), so the decisions do not depend on
+// the launch shape and match the oracle bit for bit:
 //   rows R[z][y] = sum_x phi^2 (x ascending), columns C[z][x] = sum_y phi^2
-//   (y ascending); marginals m_z = (sum_y R) dV, m_y = (sum_z R) dV,
+//   (y ascending), each square added by one fused multiply-add; marginals m_z = (sum_y R) dV, m_y = (sum_z R) dV,
 //   m_x = (sum_z C) dV (ascending); the box of each axis is the shortest
 //   cyclic interval whose outside mass T - inside <= eps/3, inside summed
 //   from the interval start upward, T the ascending total (ties: lowest
@@ -15,27 +16,46 @@
 namespace sea {
 
 // One CTA per (z-plane, orbital): row sums (thread per y) and column sums
-// (thread per x) of phi^2 over the plane.
-__global__ void k_row_col_sums(const double* __restrict__ phi, int nx, int ny, int nz,
-                               double* __restrict__ R, double* __restrict__ C) {
+// (thread per x) of phi^2 over the plane, each square accumulated with one
+// fused multiply-add in ascending order.  The plane is staged through shared
+// memory in chunks of whole rows (coalesced loads); column sums carry over
+// the chunks in registers, so the y order is kept.
+#define SEA_RC_CHUNK 4096
+__global__ void __launch_bounds__(256)
+    k_row_col_sums(const double* __restrict__ phi, int nx, int ny, int nz,
+                   double* __restrict__ R, double* __restrict__ C) {
+  __shared__ double tile[SEA_RC_CHUNK];
   const int z = blockIdx.x, i = blockIdx.y;
   const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
-  for (int y = threadIdx.x; y < ny; y += blockDim.x) {
-    const double* row = plane + (size_t)y * nx;
-    double s = 0.0;
-    for (int x = 0; x < nx; ++x) {
-      double v = row[x];
-      s = __dadd_rn(s, __dmul_rn(v, v));
+  const int rows = max(1, SEA_RC_CHUNK / nx);
+  double col[4] = {0.0, 0.0, 0.0, 0.0};  // nx <= 1024 = 4 x 256 threads
+  for (int y0 = 0; y0 < ny; y0 += rows) {
+    const int nr = min(rows, ny - y0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) tile[q] = plane[(size_t)y0 * nx + q];
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      double sr = 0.0;
+      for (int x = 0; x < nx; ++x) {
+        const double v = tile[r * nx + x];
+        sr = fma(v, v, sr);
+      }
+      R[((size_t)i * nz + z) * ny + y0 + r] = sr;
     }
-    R[((size_t)i * nz + z) * ny + y] = s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int x = threadIdx.x + u * blockDim.x;
+      if (x < nx)
+        for (int r = 0; r < nr; ++r) {
+          const double v = tile[r * nx + x];
+          col[u] = fma(v, v, col[u]);
+        }
+    }
   }
-  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-    double s = 0.0;
-    for (int y = 0; y < ny; ++y) {
-      double v = plane[(size_t)y * nx + x];
-      s = __dadd_rn(s, __dmul_rn(v, v));
-    }
-    C[((size_t)i * nz + z) * nx + x] = s;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int x = threadIdx.x + u * blockDim.x;
+    if (x < nx) C[((size_t)i * nz + z) * nx + x] = col[u];
   }
 }
 
@@ -326,7 +346,7 @@ __global__ void k_lpt_order(const int* __restrict__ sz, const int* __restrict__ 
 cudaError_t launch_plan_boxes(sea_ctx* c) {
   const int n = c->n_orb, nx = c->N[0], ny = c->N[1], nz = c->N[2];
   const int Nmax = max(nx, max(ny, nz));
-  k_row_col_sums<<<dim3(nz, n), 128, 0, c->stream>>>((const double*)c->phi.p, nx, ny, nz,
+  k_row_col_sums<<<dim3(nz, n), 256, 0, c->stream>>>((const double*)c->phi.p, nx, ny, nz,
                                                      (double*)c->rowsum.p, (double*)c->colsum.p);
   const int tot = n * 3 * Nmax;
   k_marginals<<<(tot + 255) / 256, 256, 0, c->stream>>>(

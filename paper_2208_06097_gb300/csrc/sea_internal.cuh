@@ -207,5 +207,11 @@ cudaError_t launch_ace_build(sea_ctx* c);
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int n_vec, double* out);
 cudaError_t launch_ace_vectors(sea_ctx* c, double* xi);
 cudaError_t upload_harmonics_pair();
+void fornberg_weights(double* w);
+cudaError_t launch_cg_boxes(cudaStream_t stream, int device, const double h[3], int nbox,
+                            const PairInfo* boxes, const long long* voff, const int* order,
+                            const double* rhs, double* x, double* r, double* p, double* q,
+                            int* iters, unsigned* status, int* queue, double tol, int tol_mode,
+                            int max_iter);
 cudaError_t upload_harmonics_accum();
 }  // namespace sea
