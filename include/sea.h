@@ -51,7 +51,8 @@ typedef enum {
   SEA_ERR_CG_NOT_CONVERGED = 5, /* a pair's CG hit cg_max_iter (result kept)     */
   SEA_ERR_NOT_PD = 6,           /* -Mbar not positive definite (Cholesky pivot)  */
   SEA_ERR_TIMEOUT = 7,          /* reserved                                      */
-  SEA_ERR_INPUT = 8             /* orbitals not finite                           */
+  SEA_ERR_INPUT = 8,            /* orbitals not finite                           */
+  SEA_ERR_LIMIT = 9             /* request above a fixed capacity (see below)    */
 } sea_status;
 
 /* Method knobs.  Defaults (sea_default_params): eps = 10^-3.5 (Eq. oii),
@@ -163,6 +164,22 @@ sea_status sea_poisson_batch(const double h[3], int n_box, const int* ext, const
                              double* x, double tol, int tol_mode, int max_iter, int* iters,
                              void* cuda_stream);
 
+/* Same solve as sea_poisson_batch, for callers that cannot allocate device
+ * memory (inside graph capture, under a host framework that owns all
+ * device memory, or with a footprint fixed at start-up).  It allocates
+ * nothing: its scratch is one fixed array of device memory inside the
+ * library (about 25 MB, held on every GPU that loads the library until the
+ * process exits).  The paper has no counterpart to this entry point.
+ * Limits: n_box <= 4096 and sum of box sizes <= 1048576 unknowns, else
+ * SEA_ERR_LIMIT before any GPU work.  The caller still provides rhs and x
+ * (device) and ext, iters (host), as for sea_poisson_batch.  All calls share
+ * the one array: calls that overlap on the GPU race, so order them; each
+ * call clears what must start at zero.  The first call on a device looks up
+ * the array's device address (once per device); make it before any stream
+ * capture begins.  Synchronizes the stream. */
+sea_status sea_poisson_batch_noalloc(const double h[3], int n_box, const int* ext,
+                                     const double* rhs, double* x, double tol, int tol_mode,
+                                     int max_iter, int* iters, void* cuda_stream);
 
 /* Message for the last failing call on ctx (static text; never NULL). */
 const char* sea_last_error(const sea_ctx* ctx);

@@ -20,12 +20,12 @@ LIB_PATH = os.path.join(HERE, "libsea.so")
 SEA_OK = 0
 STATUS = {0: "SEA_OK", 1: "SEA_ERR_ARG", 2: "SEA_ERR_STATE", 3: "SEA_ERR_CUDA",
           4: "SEA_ERR_OOM", 5: "SEA_ERR_CG_NOT_CONVERGED", 6: "SEA_ERR_NOT_PD",
-          7: "SEA_ERR_TIMEOUT", 8: "SEA_ERR_INPUT"}
+          7: "SEA_ERR_TIMEOUT", 8: "SEA_ERR_INPUT", 9: "SEA_ERR_LIMIT"}
 
 EXPORTS = ["sea_default_params", "sea_create", "sea_set_orbitals", "sea_apply_vxx",
            "sea_build_ace", "sea_apply_ace", "sea_get_ace_matrices", "sea_get_ace_vectors",
            "sea_get_plan", "sea_get_stats", "sea_last_error", "sea_destroy",
-           "sea_poisson_batch"]
+           "sea_poisson_batch", "sea_poisson_batch_noalloc"]
 
 
 class SeaError(RuntimeError):
@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
         L.sea_last_error.argtypes = [_p]
         L.sea_last_error.restype = ctypes.c_char_p
         L.sea_poisson_batch.argtypes = [_p, _i, _p, _p, _p, ctypes.c_double, _i, _i, _p, _p]
+        L.sea_poisson_batch_noalloc.argtypes = [_p, _i, _p, _p, _p, ctypes.c_double, _i, _i,
+                                                _p, _p]
         L.sea_destroy.argtypes = [_p]
         L.sea_destroy.restype = None
         for f in EXPORTS:
@@ -112,8 +114,12 @@ def _ptr(a):
     raise TypeError("expected a numpy array or a CUDA torch tensor")
 
 
-def poisson_batch(h, ext, rhs, x, tol=1e-8, tol_mode=0, max_iter=5000, stream=None):
-    """Solve -Lap_h x_b = rhs_b on boxes (device tensors, concatenated)."""
+def poisson_batch(h, ext, rhs, x, tol=1e-8, tol_mode=0, max_iter=5000, stream=None,
+                  noalloc=False):
+    """Solve -Lap_h x_b = rhs_b on boxes (device tensors, concatenated).
+
+    ``noalloc=True`` calls sea_poisson_batch_noalloc (fixed internal
+    scratch, no device allocation; see include/sea.h for its limits)."""
     ext = np.ascontiguousarray(np.asarray(ext, dtype=np.int32).reshape(-1, 3))
     nb = ext.shape[0]
     it = np.zeros(nb, np.int32)
@@ -122,8 +128,9 @@ def poisson_batch(h, ext, rhs, x, tol=1e-8, tol_mode=0, max_iter=5000, stream=No
     p2, d2 = _ptr(x)
     if not (d1 and d2):
         raise ValueError("rhs and x must be CUDA tensors")
-    rc = lib().sea_poisson_batch(hh, nb, _p(ext.ctypes.data), _p(p1), _p(p2), tol, tol_mode,
-                                 max_iter, _p(it.ctypes.data), _p(stream) if stream else None)
+    fn = lib().sea_poisson_batch_noalloc if noalloc else lib().sea_poisson_batch
+    rc = fn(hh, nb, _p(ext.ctypes.data), _p(p1), _p(p2), tol, tol_mode, max_iter,
+            _p(it.ctypes.data), _p(stream) if stream else None)
     if rc not in (SEA_OK, 5):
         raise SeaError(rc, "poisson_batch")
     return it, rc
