@@ -1,6 +1,8 @@
 """Benchmark: (H2O)64-like exact-exchange applications per second on GB300.
 
-One step = one pass of the whole path on one synthetic configuration:
+One step = one pass of the whole path on one synthetic configuration
+(the headline is the chosen form, mixed precision; plain FP64 is timed in
+the same run and reported beside it):
 sea_apply_vxx (domain boxes, pair selection, per-pair Poisson CG with
 multipole boundaries, far field, accumulation of V_xx phi and E_xx),
 sea_build_ace (M, Cholesky, L^-1) and sea_apply_ace on 256 trial vectors.
@@ -36,6 +38,12 @@ METRIC = "(H2O)64 V_xx applications/s, plain FP64 vs chosen form, same |dExx| bo
 UNIT = "applications/s"
 CONFIG = "h2o64_96"
 N_TRIAL = 256
+WORKLOAD = ("(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, eps=10^-3.5, "
+            "delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; ACE build + apply to "
+            "256 trial vectors")
+FORMS = {"plain": "plain FP64",
+         "mixed": "mixed: FP32 CG sweeps/vectors inside FP64 iterative refinement; FP64 "
+                  "residuals, dots across blocks, E_xx, multipoles and ACE"}
 
 # Algorithmic FP64 flops per CG unknown and iteration: the symmetric 37-point
 # stencil as 18 pair sums, 18 multiply-adds and the centre product (55), plus
@@ -95,6 +103,54 @@ def _peaks():
         return {}
 
 
+def _time_form(args, sea, s, psi, vxx, y, stream, precision, barrier, torch, rank, local,
+               sample_clocks):
+    """W warm-up + K timed steps of one form; per-stage and per-kernel times."""
+    ctx = sea.Context(s.cell, s.grid, stream=stream.cuda_stream, precision=precision)
+    phi = torch.from_numpy(s.phi).to(vxx.device)
+    ctx.set_orbitals(phi)
+    del phi
+    for _ in range(args.warmup):
+        ctx.apply_vxx(vxx)
+        ctx.build_ace()
+        ctx.apply_ace(psi, y)
+    stream.synchronize()
+    clk_path = os.path.join(tempfile.gettempdir(), f"sea_clocks_{os.getpid()}_{precision}.csv")
+    sampler = _clock_sampler(clk_path) if (rank == 0 and sample_clocks) else None
+    time.sleep(0.5 if sampler else 0)
+    st0 = ctx.stats()
+    keys = ["ms_plan", "ms_setup", "ms_cg", "ms_accumulate", "ms_ace_build", "ms_gram_build",
+            "ms_ace_apply", "ms_gram_apply", "ms_expand_apply"]
+    acc = {k: 0.0 for k in keys}
+    cg_work = 0
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.apply_vxx(vxx)
+        ctx.build_ace()
+        ctx.apply_ace(psi, y)
+        stream.synchronize()
+        st = ctx.stats()
+        for k in keys:
+            acc[k] += st[k]
+        cg_work += st["cg_unknown_iters"]
+    e1.record(stream)
+    barrier()
+    t_ms = e0.elapsed_time(e1)
+    st1 = ctx.stats()
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clock_summary(clk_path, local) if sampler else None
+    K = args.steps
+    out = {"ctx": ctx, "t_ms": t_ms, "clocks": clocks, "launches": st1["n_launches"] - st0["n_launches"],
+           "stage_ms": {k[3:]: v / K for k, v in acc.items()}, "cg_unknown_iters": cg_work / K,
+           "stats": st1}
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -110,24 +166,10 @@ def run_ours(args, ws, rank, local):
     s = synth.make_config(args.config)
     psi_h = synth.random_trial_vectors(N_TRIAL, s.grid, 2024)
     stream = torch.cuda.Stream(device=dev)
-    ctx = sea.Context(s.cell, s.grid, stream=stream.cuda_stream,
-                      precision=1 if args.form == "mixed" else 0)
-
-    phi = torch.from_numpy(s.phi).to(dev)
     psi = torch.from_numpy(psi_h).to(dev)
-    vxx = torch.empty_like(phi)
+    vxx = torch.empty(s.phi.shape, dtype=torch.float64, device=dev)
     y = torch.empty_like(psi)
     torch.cuda.synchronize()
-    ctx.set_orbitals(phi)
-
-    def step():
-        ctx.apply_vxx(vxx)
-        ctx.build_ace()
-        ctx.apply_ace(psi, y)
-
-    for _ in range(args.warmup):
-        step()
-    stream.synchronize()
 
     def barrier():
         if ws > 1:
@@ -135,41 +177,17 @@ def run_ours(args, ws, rank, local):
             dist.barrier()
         torch.cuda.synchronize()
 
-    clk_path = os.path.join(tempfile.gettempdir(), f"sea_clocks_{os.getpid()}.csv")
-    sampler = _clock_sampler(clk_path) if rank == 0 else None
-    time.sleep(0.5 if sampler else 0)
-    st0 = ctx.stats()
-    ms = {"plan": 0.0, "setup": 0.0, "cg": 0.0, "acc": 0.0, "ace_b": 0.0, "ace_a": 0.0}
-    cg_work = 0
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    ea = torch.cuda.Event(enable_timing=True)
-    eb = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        ctx.apply_vxx(vxx)
-        ctx.build_ace()
-        ea.record(stream)
-        ctx.apply_ace(psi, y)
-        eb.record(stream)
-        st = ctx.stats()
-        eb.synchronize()
-        ms["plan"] += st["ms_plan"]
-        ms["setup"] += st["ms_setup"]
-        ms["cg"] += st["ms_cg"]
-        ms["acc"] += st["ms_accumulate"]
-        ms["ace_b"] += st["ms_ace_build"]
-        ms["ace_a"] += ea.elapsed_time(eb)
-        cg_work += st["cg_unknown_iters"]
-    e1.record(stream)
-    barrier()
-    t_ms = e0.elapsed_time(e1)
-    st1 = ctx.stats()
-    if sampler:
-        sampler.terminate()
-        sampler.wait()
-    clocks = _clock_summary(clk_path, local) if rank == 0 else None
+    forms = ["plain", "mixed"] if args.form == "both" else [args.form]
+    chosen = "mixed" if "mixed" in forms else forms[0]
+    res = {}
+    for f in forms:
+        res[f] = _time_form(args, sea, s, psi, vxx, y, stream, 1 if f == "mixed" else 0, barrier,
+                            torch, rank, local, sample_clocks=(f == chosen))
+        if f != chosen:
+            res[f]["ctx"].close()
+    R = res[chosen]
+    ctx = R["ctx"]
+    nnz_w = int((vxx != 0).sum().item())  # exact support of W (outside the timed region)
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     phi_pin = torch.from_numpy(s.phi).pin_memory().numpy()
@@ -193,22 +211,35 @@ def run_ours(args, ws, rank, local):
     barrier()
     t_e2e = time.perf_counter() - t0
 
-    ts = torch.tensor([t_ms, t_e2e], dtype=torch.float64, device=dev)
+    ts = torch.tensor([R["t_ms"], t_e2e] + [res[f]["t_ms"] for f in forms], dtype=torch.float64,
+                      device=dev)
     if ws > 1:
         import torch.distributed as dist
         dist.all_reduce(ts, op=dist.ReduceOp.MAX)
     t_ms, t_e2e = float(ts[0]), float(ts[1])
+    form_ms = {f: float(ts[2 + k]) for k, f in enumerate(forms)}
     if rank != 0:
         ctx.close()
         return None
 
-    value = ws * args.steps / (t_ms / 1e3)
-    e2e_value = ws * e2e_steps / t_e2e if e2e_steps else None
     K = args.steps
-    cg_ms = ms["cg"] / K
-    cg_flops = CG_FLOPS_PER_UNKNOWN_ITER * (cg_work / K)
-    achieved = cg_flops / (cg_ms / 1e3) / 1e12
-    stats = ctx.stats()
+    value = ws * K / (t_ms / 1e3)
+    e2e_value = ws * e2e_steps / t_e2e if e2e_steps else None
+    st = R["stats"]
+    sm = R["stage_ms"]
+    n = s.n_orb
+    # candidate kernels: (name, ms per launch, launches per step, flops per launch, peak, bound)
+    cand = []
+    if chosen == "plain":
+        cand.append(("k_cg (persistent FP64 CG)", sm["cg"], 1,
+                     CG_FLOPS_PER_UNKNOWN_ITER * R["cg_unknown_iters"], FP64_PEAK_TFLOPS, "alu"))
+    cand.append(("k_gram_partial (FP64 M = Phi^T W and W^T psi over W's tiles)",
+                 (sm["gram_build"] + sm["gram_apply"]) / 2, 2,
+                 2.0 * n * nnz_w, FP64_PEAK_TFLOPS, "alu"))
+    cand.append(("k_tile_expand (FP64 W H over W's tiles)", sm["expand_apply"], 1,
+                 2.0 * N_TRIAL * nnz_w, FP64_PEAK_TFLOPS, "alu"))
+    name, kms, nl, flops, peak, bound = max(cand, key=lambda c: c[1] * c[2])
+    achieved = flops / (kms / 1e3) / 1e12 if kms > 0 else 0.0
     cpu = cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline) else None
     line = {
         "metric": METRIC,
@@ -221,22 +252,22 @@ def run_ours(args, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if chosen == "plain" else "f64+f32",
         "data": "synthetic (seeded water-like localized orbitals, see synth.py)",
         "config": {
-            "workload": "(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, "
-                        "eps=10^-3.5, delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; "
-                        "ACE build + apply to 256 trial vectors",
-            "form": "plain FP64" if args.form == "plain" else
-                    "mixed: FP32 CG sweeps/vectors inside FP64 refinement",
+            "workload": WORKLOAD,
+            "form": FORMS[chosen],
+            "forms_applications_per_s": {f: ws * K / (form_ms[f] / 1e3) for f in forms},
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
             "l2": "inputs larger than L2 (Phi and psi 1.81 GB each)",
-            "n_pairs": stats["n_pairs"],
-            "cg_unknowns": stats["n_unknowns"],
-            "cg_iters_mean": stats["cg_iters_mean"],
-            "cg_unknown_iters": stats["cg_unknown_iters"],
-            "ace_support_points": stats["ace_support_points"],
-            "stage_ms": {k: v / K for k, v in ms.items()},
+            "n_pairs": st["n_pairs"],
+            "cg_unknowns": st["n_unknowns"],
+            "cg_iters_mean": st["cg_iters_mean"],
+            "cg_unknown_iters": R["cg_unknown_iters"],
+            "w_nonzeros": nnz_w,
+            "ace_tile_points": st["ace_support_points"],
+            "stage_ms": sm,
+            "stage_ms_plain": res["plain"]["stage_ms"] if "plain" in res else None,
         },
         "e2e": {
             "value": e2e_value,
@@ -244,19 +275,19 @@ def run_ours(args, ws, rank, local):
             "h2d_bytes_per_step": int(s.phi.nbytes + psi_h.nbytes),
             "d2h_bytes_per_step": int(s.phi.nbytes + psi_h.nbytes + 8),
         },
-        "gpu_launches": int(st1["n_launches"] - st0["n_launches"]),
+        "gpu_launches": int(R["launches"]),
         "roofline": {
-            "kernel": "k_cg (persistent FP64 CG, all pairs)",
-            "bound": "alu",
+            "kernel": name,
+            "bound": bound,
             "achieved": achieved,
-            "peak": FP64_PEAK_TFLOPS,
+            "peak": peak,
             "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
+            "frac": achieved / peak,
             "traffic": None,
-            "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal); "
-                         "65 algorithmic flops per unknown per CG iteration",
+            "peak_note": "FP64 ALU from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; "
+                         "algorithmic flops: CG 65/unknown/iteration, ACE 2 x rows x nonzeros of W",
         },
-        "clocks": clocks,
+        "clocks": R["clocks"],
     }
     if cpu:
         line["cpu_baseline"] = cpu
@@ -310,9 +341,7 @@ def run_reference(args, ws, rank):
         "warmup": min(args.warmup, 1), "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded water-like localized orbitals, see synth.py)",
-        "config": {"workload": "(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, "
-                               "eps=10^-3.5, delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; "
-                               "ACE build + apply to 256 trial vectors",
+        "config": {"workload": WORKLOAD,
                    "form": "CPU oracle (plain FP64 reference of the method)"},
         "impl": "reference",
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
@@ -333,8 +362,8 @@ def main():
     ap.add_argument("--config", default=CONFIG, help="workload name in synth.CONFIGS "
                     "(default: the (H2O)64 96^3 benchmark workload; smaller ones for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
-    ap.add_argument("--form", choices=["plain", "mixed"], default="plain",
-                    help="plain FP64, or FP32 CG sweeps inside FP64 refinement")
+    ap.add_argument("--form", choices=["plain", "mixed", "both"], default="both",
+                    help="plain FP64, the mixed form, or both (headline: mixed)")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

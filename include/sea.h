@@ -80,7 +80,8 @@ typedef struct {
 } sea_params;
 
 /* Per-call statistics of the last sea_apply_vxx / sea_build_ace /
- * sea_apply_ace on a context. */
+ * sea_apply_ace on a context (device times from CUDA events on the context
+ * stream; the sea_apply_ace times are filled once its work has finished). */
 typedef struct {
   int n_orb;
   int n_pairs;        /* selected pairs <ij>, i <= j                       */
@@ -95,6 +96,8 @@ typedef struct {
   double ms_ace_build, ms_ace_apply;
   long long ace_support_points; /* sum over orbitals of tile-rounded support */
   long long n_launches;  /* kernels this context has launched since creation */
+  double ms_gram_build;  /* M = Phi^T W dV contraction, last sea_build_ace       */
+  double ms_gram_apply, ms_expand_apply; /* W^T psi and W H, last sea_apply_ace */
 } sea_stats;
 
 typedef struct sea_ctx sea_ctx;

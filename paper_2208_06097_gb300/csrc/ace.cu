@@ -29,9 +29,25 @@ __device__ __forceinline__ bool cyc_meets(int s, int L, int a, int b, int n) {
   return (wrapi(s - a, n) < b - a) || (wrapi(a - s, n) < L);
 }
 
-// inc[o][T] = 1 if any entry window of orbital o touches tile T.
+// Covered range [lo, hi) of the tile interval [a, b) by the cyclic window
+// [s, s+L) on a ring of n points (lo >= hi: none).
+__device__ __forceinline__ void cyc_cover(int s, int L, int a, int b, int n, int* lo, int* hi) {
+  *lo = b;
+  *hi = a;
+  for (int x = a; x < b; ++x)
+    if (L >= n || wrapi(x - s, n) < L) {
+      *lo = min(*lo, x);
+      *hi = max(*hi, x + 1);
+    }
+}
+
+// inc[o][T] = 1 if any entry window of orbital o touches tile T, and
+// sub[o][T] = the bounding box, in tile coordinates, of the union of those
+// windows inside the tile, packed x0 | x1 << 4 | y0 << 8 | y1 << 12 |
+// z0 << 16 | z1 << 20 (W_o is exactly zero in the tile outside it).
 __global__ void k_tile_incidence(const Entry* __restrict__ ent, const int* __restrict__ eptr,
-                                 int n_orb, TileGeom G, int n_tiles, int* __restrict__ inc) {
+                                 int n_orb, TileGeom G, int n_tiles, int* __restrict__ inc,
+                                 int* __restrict__ sub) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_orb * n_tiles) return;
   const int o = (int)(t / n_tiles), T = (int)(t % n_tiles);
@@ -39,21 +55,34 @@ __global__ void k_tile_incidence(const Entry* __restrict__ ent, const int* __res
   const int ax = txi * TX, bx = min(G.nx, ax + TX);
   const int ay = tyi * TY, by = min(G.ny, ay + TY);
   const int az = tzi * TZ, bz = min(G.nz, az + TZ);
-  int hit = 0;
-  for (int k = eptr[o]; k < eptr[o + 1] && !hit; ++k) {
+  int x0 = TX, x1 = 0, y0 = TY, y1 = 0, z0 = TZ, z1 = 0;
+  for (int k = eptr[o]; k < eptr[o + 1]; ++k) {
     const Entry e = ent[k];
-    hit = cyc_meets(wrapi(e.ws[0], G.nx), e.wl[0], ax, bx, G.nx) &&
-          cyc_meets(wrapi(e.ws[1], G.ny), e.wl[1], ay, by, G.ny) &&
-          cyc_meets(wrapi(e.ws[2], G.nz), e.wl[2], az, bz, G.nz);
+    int lx, hx, ly, hy, lz, hz;
+    cyc_cover(wrapi(e.ws[0], G.nx), e.wl[0], ax, bx, G.nx, &lx, &hx);
+    if (lx >= hx) continue;
+    cyc_cover(wrapi(e.ws[1], G.ny), e.wl[1], ay, by, G.ny, &ly, &hy);
+    if (ly >= hy) continue;
+    cyc_cover(wrapi(e.ws[2], G.nz), e.wl[2], az, bz, G.nz, &lz, &hz);
+    if (lz >= hz) continue;
+    x0 = min(x0, lx - ax);
+    x1 = max(x1, hx - ax);
+    y0 = min(y0, ly - ay);
+    y1 = max(y1, hy - ay);
+    z0 = min(z0, lz - az);
+    z1 = max(z1, hz - az);
   }
+  const int hit = x1 > x0;
   inc[t] = hit;
+  sub[t] = hit ? (x0 | (x1 << 4) | (y0 << 8) | (y1 << 12) | (z0 << 16) | (z1 << 20)) : 0;
 }
 
 // Tile-major lists: thread per tile, orbitals ascending.  mode 0 counts,
 // mode 1 writes the list and the incidence index gidx[o][T].
-__global__ void k_tile_lists(const int* __restrict__ inc, int n_orb, int n_tiles, int mode,
-                             int* __restrict__ cnt, const int* __restrict__ ptr,
-                             int* __restrict__ list, int* __restrict__ gidx) {
+__global__ void k_tile_lists(const int* __restrict__ inc, const int* __restrict__ sub, int n_orb,
+                             int n_tiles, int mode, int* __restrict__ cnt,
+                             const int* __restrict__ ptr, int* __restrict__ list,
+                             int* __restrict__ lsub, int* __restrict__ gidx) {
   const int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= n_tiles) return;
   int c = 0;
@@ -67,6 +96,7 @@ __global__ void k_tile_lists(const int* __restrict__ inc, int n_orb, int n_tiles
     ++c;
     if (mode) {
       list[pos] = o;
+      lsub[pos] = sub[q];
       gidx[q] = pos;
       ++pos;
     }
@@ -74,26 +104,29 @@ __global__ void k_tile_lists(const int* __restrict__ inc, int n_orb, int n_tiles
   if (!mode) cnt[T] = c;
 }
 
-// Orbital-major lists: thread per orbital, tiles ascending, with the
-// incidence index of each (orbital, tile).
+// Orbital-major lists: one warp per orbital, tiles ascending (ballot
+// compaction keeps the order), with the incidence index of each
+// (orbital, tile).  mode 0 counts, mode 1 writes.
 __global__ void k_orb_lists(const int* __restrict__ gidx, int n_orb, int n_tiles, int mode,
                             int* __restrict__ cnt, const int* __restrict__ ptr,
                             int* __restrict__ list, int* __restrict__ slot) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (o >= n_orb) return;
   int c = 0;
-  int pos = mode ? ptr[o] : 0;
-  for (int T = 0; T < n_tiles; ++T) {
-    const int g = gidx[(size_t)o * n_tiles + T];
-    if (g < 0) continue;
-    ++c;
-    if (mode) {
+  const int base = mode ? ptr[o] : 0;
+  for (int T0 = 0; T0 < n_tiles; T0 += 32) {
+    const int T = T0 + lane;
+    const int g = T < n_tiles ? gidx[(size_t)o * n_tiles + T] : -1;
+    const unsigned bal = __ballot_sync(0xffffffffu, g >= 0);
+    if (mode && g >= 0) {
+      const int pos = base + c + __popc(bal & ((1u << lane) - 1u));
       list[pos] = T;
       slot[pos] = g;
-      ++pos;
     }
+    c += __popc(bal);
   }
-  if (!mode) cnt[o] = c;
+  if (!mode && lane == 0) cnt[o] = c;
 }
 
 __global__ void k_scan_small(const int* __restrict__ in, int n, int* __restrict__ out,
@@ -143,62 +176,209 @@ __device__ __forceinline__ long long tile_point(const TileGeom& G, int T, int r)
 }
 
 // partial[(tptr[T] + s) * m + a] = sum_{r in T} A[a][r] W[list[s]][r].
-// CTA per (tile, chunk of 64 rows of A); thread = (row a, quarter q) and
-// accumulates the W rows q, q+4, q+8, ... of the tile's list (no padding:
-// the quarter is uniform across a warp); W rows in blocks of 32, points
-// staged 32 at a time in shared memory.
+// CTA per (tile, chunk of 64 rows of A).  The tile's 128 points of the 64
+// A rows and of up to 32 W rows sit in shared memory; a work unit is
+// (W row, half of the A rows), units are dealt to warps in a warp-uniform
+// loop (no predicated FMAs: on this part a predicated-off FP64 FMA still
+// costs FP64 pipe time), each lane one A row; the dot product runs over the
+// W row's sub-box of the tile only (W is exactly zero outside it), with
+// four independent FMA chains along x.
 #define GA 64
-#define GJ 32
-#define GP 32
-__global__ void __launch_bounds__(256)
+#define GJB 32
+#define GROW (TP + 1)
+#define GRAM_SMEM ((size_t)(GA + GJB) * GROW * sizeof(double))
+__global__ void __launch_bounds__(256, 2)
     k_gram_partial(const double* __restrict__ A, int m, const double* __restrict__ W,
                    TileGeom G, size_t ng, const int* __restrict__ tptr,
-                   const int* __restrict__ tlist, double* __restrict__ partial) {
+                   const int* __restrict__ tlist, const int* __restrict__ tsub,
+                   double* __restrict__ partial) {
   const int T = blockIdx.x;
   const int a0 = blockIdx.y * GA;
   const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
   if (nJ == 0) return;
-  __shared__ double As[GA][GP + 1];
-  __shared__ double Ws[GJ][GP + 1];
+  extern __shared__ double gsm[];
+  double* As = gsm;               // [GA][GROW]
+  double* Ws = gsm + GA * GROW;   // [GJB][GROW]
   __shared__ long long addr[TP];
-  __shared__ int wrow[GJ];
+  __shared__ int wrow[GJB];
   for (int r = threadIdx.x; r < TP; r += blockDim.x) addr[r] = tile_point(G, T, r);
-  const int al = threadIdx.x % GA, qq = threadIdx.x / GA;
-  for (int jb = 0; jb < nJ; jb += GJ) {
-    const int nj = min(GJ, nJ - jb);
-    double acc[GJ / 4];
-#pragma unroll
-    for (int u = 0; u < GJ / 4; ++u) acc[u] = 0.0;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < GA * TP; idx += blockDim.x) {
+    const int a = idx / TP, pt = idx % TP;
+    const long long g = addr[pt];
+    As[a * GROW + pt] = (a0 + a < m && g >= 0) ? A[(size_t)(a0 + a) * ng + g] : 0.0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int jb = 0; jb < nJ; jb += GJB) {
+    const int nj = min(GJB, nJ - jb);
     __syncthreads();
     if (threadIdx.x < nj) wrow[threadIdx.x] = tlist[j0 + jb + threadIdx.x];
-    for (int pc = 0; pc < TP; pc += GP) {
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < GA * GP; idx += blockDim.x) {
-        const int a = idx / GP, pt = idx % GP;
-        const long long g = addr[pc + pt];
-        As[a][pt] = (a0 + a < m && g >= 0) ? A[(size_t)(a0 + a) * ng + g] : 0.0;
-      }
-      for (int idx = threadIdx.x; idx < nj * GP; idx += blockDim.x) {
-        const int jl = idx / GP, pt = idx % GP;
-        const long long g = addr[pc + pt];
-        Ws[jl][pt] = g >= 0 ? W[(size_t)wrow[jl] * ng + g] : 0.0;
-      }
-      __syncthreads();
-#pragma unroll 4
-      for (int pt = 0; pt < GP; ++pt) {
-        const double av = As[al][pt];
-#pragma unroll
-        for (int u = 0; u < GJ / 4; ++u)
-          if (qq + 4 * u < nj) acc[u] = fma(av, Ws[qq + 4 * u][pt], acc[u]);
-      }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nj * TP; idx += blockDim.x) {
+      const int jl = idx / TP, pt = idx % TP;
+      const long long g = addr[pt];
+      Ws[jl * GROW + pt] = g >= 0 ? W[(size_t)wrow[jl] * ng + g] : 0.0;
     }
-    if (a0 + al < m) {
-#pragma unroll
-      for (int u = 0; u < GJ / 4; ++u) {
-        const int jl = qq + 4 * u;
-        if (jl < nj) partial[(size_t)(j0 + jb + jl) * m + a0 + al] = acc[u];
-      }
+    __syncthreads();
+    for (int u = warp; u < 2 * nj; u += nwarp) {
+      const int jl = u >> 1, ah = u & 1;
+      const double* ar = As + (ah * 32 + lane) * GROW;
+      const double* wr = Ws + jl * GROW;
+      const int sb = tsub[j0 + jb + jl];
+      const int x0 = sb & 15, x1 = (sb >> 4) & 15, y0 = (sb >> 8) & 15, y1 = (sb >> 12) & 15,
+                z0 = (sb >> 16) & 15, z1 = (sb >> 20) & 15;
+      double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+      for (int z = z0; z < z1; ++z)
+        for (int y = y0; y < y1; ++y) {
+          const int base = (z * TY + y) * TX;
+          int x = x0;
+          for (; x + 4 <= x1; x += 4) {
+            c0 = fma(ar[base + x], wr[base + x], c0);
+            c1 = fma(ar[base + x + 1], wr[base + x + 1], c1);
+            c2 = fma(ar[base + x + 2], wr[base + x + 2], c2);
+            c3 = fma(ar[base + x + 3], wr[base + x + 3], c3);
+          }
+          for (; x < x1; ++x) c0 = fma(ar[base + x], wr[base + x], c0);
+        }
+      const int a = a0 + ah * 32 + lane;
+      if (a < m) partial[(size_t)(j0 + jb + jl) * m + a] = (c0 + c1) + (c2 + c3);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed form of the same contraction: FP64 operands split into FP32 pairs
+// (v = hi + lo, hi = fl32(v), lo = fl32(v - hi)), each product formed as
+// hi*hi exactly (FMA residual) plus the two cross terms, and summed with an
+// error-free addition into a (sum, compensation) pair of FP32 values.  The
+// result carries about 44 significant bits (relative error ~1e-13 per
+// tile partial; partials are combined in FP64), at the FP32 issue rate,
+// which on this part is 64x the FP64 rate.
+// ---------------------------------------------------------------------------
+struct CompF {
+  float s, c;
+  __device__ CompF() : s(0.f), c(0.f) {}
+  // add (ah + al)(bh + bl), dropping al*bl
+  __device__ __forceinline__ void add_prod(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);
+    const float x = fmaf(ah, bl, al * bh);
+    const float t = s + p;
+    const float z = t - s;
+    const float err = (s - (t - z)) + (p - z);
+    s = t;
+    c += (err + e) + x;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ float2 split64(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+#define GROWX (TP + 1)
+#define GRAMX_SMEM ((size_t)(GA + GJB) * GROWX * sizeof(float2))
+__global__ void __launch_bounds__(256, 2)
+    k_gram_partial_x(const double* __restrict__ A, int m, const double* __restrict__ W,
+                     TileGeom G, size_t ng, const int* __restrict__ tptr,
+                     const int* __restrict__ tlist, const int* __restrict__ tsub,
+                     double* __restrict__ partial) {
+  const int T = blockIdx.x;
+  const int a0 = blockIdx.y * GA;
+  const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
+  if (nJ == 0) return;
+  extern __shared__ float2 gsx[];
+  float2* As = gsx;               // [GA][GROWX]
+  float2* Ws = gsx + GA * GROWX;  // [GJB][GROWX]
+  __shared__ long long addr[TP];
+  __shared__ int wrow[GJB];
+  for (int r = threadIdx.x; r < TP; r += blockDim.x) addr[r] = tile_point(G, T, r);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < GA * TP; idx += blockDim.x) {
+    const int a = idx / TP, pt = idx % TP;
+    const long long g = addr[pt];
+    As[a * GROWX + pt] = split64((a0 + a < m && g >= 0) ? A[(size_t)(a0 + a) * ng + g] : 0.0);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int jb = 0; jb < nJ; jb += GJB) {
+    const int nj = min(GJB, nJ - jb);
+    __syncthreads();
+    if (threadIdx.x < nj) wrow[threadIdx.x] = tlist[j0 + jb + threadIdx.x];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nj * TP; idx += blockDim.x) {
+      const int jl = idx / TP, pt = idx % TP;
+      const long long g = addr[pt];
+      Ws[jl * GROWX + pt] = split64(g >= 0 ? W[(size_t)wrow[jl] * ng + g] : 0.0);
+    }
+    __syncthreads();
+    for (int u = warp; u < 2 * nj; u += nwarp) {
+      const int jl = u >> 1, ah = u & 1;
+      const float2* ar = As + (ah * 32 + lane) * GROWX;
+      const float2* wr = Ws + jl * GROWX;
+      const int sb = tsub[j0 + jb + jl];
+      const int x0 = sb & 15, x1 = (sb >> 4) & 15, y0 = (sb >> 8) & 15, y1 = (sb >> 12) & 15,
+                z0 = (sb >> 16) & 15, z1 = (sb >> 20) & 15;
+      CompF c0, c1;
+      for (int z = z0; z < z1; ++z)
+        for (int y = y0; y < y1; ++y) {
+          const int base = (z * TY + y) * TX;
+          int x = x0;
+          for (; x + 2 <= x1; x += 2) {
+            const float2 a0v = ar[base + x], w0v = wr[base + x];
+            const float2 a1v = ar[base + x + 1], w1v = wr[base + x + 1];
+            c0.add_prod(a0v.x, a0v.y, w0v.x, w0v.y);
+            c1.add_prod(a1v.x, a1v.y, w1v.x, w1v.y);
+          }
+          if (x < x1) {
+            const float2 av = ar[base + x], wv = wr[base + x];
+            c0.add_prod(av.x, av.y, wv.x, wv.y);
+          }
+        }
+      const int a = a0 + ah * 32 + lane;
+      if (a < m) partial[(size_t)(j0 + jb + jl) * m + a] = c0.value() + c1.value();
+    }
+  }
+}
+
+// Mixed form of k_tile_expand (same splitting and compensated sums).
+__global__ void __launch_bounds__(256)
+    k_tile_expand_x(const double* __restrict__ W, TileGeom G, size_t ng,
+                    const int* __restrict__ tptr, const int* __restrict__ tlist,
+                    const int* __restrict__ tsub, const double* __restrict__ H, long long hj,
+                    long long hv, int m, double sign, double* __restrict__ out) {
+  const int T = blockIdx.x;
+  const int v0 = blockIdx.y * 32;
+  const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
+  extern __shared__ float2 Hx[];  // [nJ][32]
+  for (int idx = threadIdx.x; idx < nJ * 32; idx += blockDim.x) {
+    const int jl = idx / 32, vl = idx % 32;
+    Hx[idx] = split64((v0 + vl < m) ? H[(long long)tlist[j0 + jl] * hj + (long long)(v0 + vl) * hv]
+                                    : 0.0);
+  }
+  __syncthreads();
+  const int pt = threadIdx.x % TP, vh = threadIdx.x / TP;
+  const long long g = tile_point(G, T, pt);
+  CompF acc[16];
+  const int pz = pt / (TX * TY), py = (pt / TX) % TY, px = pt % TX;  // pz: one per warp
+  for (int jl = 0; jl < nJ; ++jl) {
+    const int sb = tsub[j0 + jl];
+    if (pz < ((sb >> 16) & 15) || pz >= ((sb >> 20) & 15)) continue;  // warp-uniform
+    const bool in = px >= (sb & 15) && px < ((sb >> 4) & 15) && py >= ((sb >> 8) & 15) &&
+                    py < ((sb >> 12) & 15);
+    const float2 w = split64((g >= 0 && in) ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0);
+    const float2* hrow = Hx + jl * 32 + vh * 16;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const float2 hh = hrow[u];
+      acc[u].add_prod(w.x, w.y, hh.x, hh.y);
+    }
+  }
+  if (g < 0) return;
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int v = v0 + vh * 16 + u;
+    if (v < m) out[(size_t)v * ng + g] = sign * acc[u].value();
   }
 }
 
@@ -230,7 +410,8 @@ __global__ void k_chol_init(const double* __restrict__ M, int n, double* __restr
 }
 
 __global__ void __launch_bounds__(256)
-    k_chol_panel(double* __restrict__ A, int n, int kb, unsigned* __restrict__ status) {
+    k_chol_panel(double* __restrict__ A, int n, int kb, unsigned* __restrict__ status,
+                 double* __restrict__ Tbuf) {
   if (*status & SEA_FLAG_NOT_PD) return;
   __shared__ double D[CB][CB + 1];
   __shared__ int bad;
@@ -268,22 +449,33 @@ __global__ void __launch_bounds__(256)
     const int i = q / nb, j = q % nb;
     if (j <= i) A[(size_t)(kb + i) * n + kb + j] = D[i][j];
   }
-  // rows below: x L_kk^T = a  (forward substitution per row)
-  for (int i = kb + nb + threadIdx.x; i < n; i += blockDim.x) {
-    double x[CB];
-#pragma unroll
-    for (int j = 0; j < CB; ++j) x[j] = j < nb ? A[(size_t)i * n + kb + j] : 0.0;
-#pragma unroll
-    for (int j = 0; j < CB; ++j) {
-      if (j < nb) {
-        double v = x[j];
-        for (int l = 0; l < j; ++l) v = fma(-x[l], D[j][l], v);
-        x[j] = v / D[j][j];
-      }
+  // rows below solve x L_kk^T = a: with Y = L_kk^-1 (one column per thread,
+  // forward substitution), x_j = sum_l a_l Y_jl -- independent dot products.
+  __shared__ double Y[CB][CB + 1];
+  if (threadIdx.x < CB) {
+    const int k = threadIdx.x;
+    for (int i = 0; i < CB; ++i) {
+      double v = (i == k) ? 1.0 : 0.0;
+      if (i < nb)
+        for (int l = k; l < i; ++l) v = fma(-D[i][l], Y[l][k], v);
+      Y[i][k] = (i < nb && i >= k) ? v / D[i][i] : 0.0;
     }
-#pragma unroll
-    for (int j = 0; j < CB; ++j)
-      if (j < nb) A[(size_t)i * n + kb + j] = x[j];
+  }
+  __syncthreads();
+  const int rows = n - kb - nb;
+  for (int q = threadIdx.x; q < rows * CB; q += blockDim.x) {
+    const int i = kb + nb + q / CB, j = q % CB;
+    double x = 0.0;
+    if (j < nb) {
+      const double* ai = A + (size_t)i * n + kb;
+      for (int l = 0; l <= j; ++l) x = fma(ai[l], Y[j][l], x);
+    }
+    Tbuf[q] = x;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < rows * CB; q += blockDim.x) {
+    const int i = kb + nb + q / CB, j = q % CB;
+    if (j < nb) A[(size_t)i * n + kb + j] = Tbuf[q];
   }
 }
 
@@ -363,8 +555,8 @@ __global__ void k_small_gemm(const double* __restrict__ A, int transA, const dou
 __global__ void __launch_bounds__(256)
     k_tile_expand(const double* __restrict__ W, TileGeom G, size_t ng,
                   const int* __restrict__ tptr, const int* __restrict__ tlist,
-                  const double* __restrict__ H, long long hj, long long hv, int m, double sign,
-                  double* __restrict__ out) {
+                  const int* __restrict__ tsub, const double* __restrict__ H, long long hj,
+                  long long hv, int m, double sign, double* __restrict__ out) {
   const int T = blockIdx.x;
   const int v0 = blockIdx.y * EV;
   const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
@@ -379,8 +571,13 @@ __global__ void __launch_bounds__(256)
   double acc[EV / 2];
 #pragma unroll
   for (int u = 0; u < EV / 2; ++u) acc[u] = 0.0;
+  const int pz = pt / (TX * TY), py = (pt / TX) % TY, px = pt % TX;  // pz: one per warp
   for (int jl = 0; jl < nJ; ++jl) {
-    const double w = g >= 0 ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0;
+    const int sb = tsub[j0 + jl];
+    if (pz < ((sb >> 16) & 15) || pz >= ((sb >> 20) & 15)) continue;  // warp-uniform
+    const bool in = px >= (sb & 15) && px < ((sb >> 4) & 15) && py >= ((sb >> 8) & 15) &&
+                    py < ((sb >> 12) & 15);
+    const double w = (g >= 0 && in) ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0;
     const double* hrow = Hs + jl * EV + vh * (EV / 2);
 #pragma unroll
     for (int u = 0; u < EV / 2; ++u) acc[u] = fma(w, hrow[u], acc[u]);
@@ -404,6 +601,35 @@ static TileGeom tile_geom(const sea_ctx* c) {
   return G;
 }
 
+// The contractions with W: FP64 kernels for the plain form, the FP32
+// error-free-transformation kernels for the mixed form.
+static void launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G, const int* tptr,
+                        const int* tlist, const int* tsub) {
+  const dim3 grid(c->n_tiles, (m + GA - 1) / GA);
+  if (c->prm.precision == 1)
+    k_gram_partial_x<<<grid, 256, GRAMX_SMEM, c->stream>>>(A, m, (const double*)c->vxx_dev.p, G,
+                                                           c->ng, tptr, tlist, tsub,
+                                                           (double*)c->partial.p);
+  else
+    k_gram_partial<<<grid, 256, GRAM_SMEM, c->stream>>>(A, m, (const double*)c->vxx_dev.p, G,
+                                                        c->ng, tptr, tlist, tsub,
+                                                        (double*)c->partial.p);
+}
+
+static void launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr, const int* tlist,
+                          const int* tsub, const double* H, long long hj, long long hv, int m,
+                          double sign, double* out) {
+  if (c->prm.precision == 1) {
+    const size_t smem = (size_t)c->max_tile_list * 32 * sizeof(float2);
+    k_tile_expand_x<<<dim3(c->n_tiles, (m + 31) / 32), 256, smem, c->stream>>>(
+        (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, tsub, H, hj, hv, m, sign, out);
+  } else {
+    const size_t smem = (size_t)c->max_tile_list * EV * sizeof(double);
+    k_tile_expand<<<dim3(c->n_tiles, (m + EV - 1) / EV), 256, smem, c->stream>>>(
+        (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, tsub, H, hj, hv, m, sign, out);
+  }
+}
+
 // Tile lists of W's support, M, Cholesky and L^-1.  Needs the incidence
 // count on the host to size the partial sums: one stream sync.
 cudaError_t launch_ace_build(sea_ctx* c) {
@@ -412,24 +638,26 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   const int nt = G.ntx * G.nty * G.ntz;
   c->n_tiles = nt;
   const long long ninc = (long long)n * nt;
-  if (!sea_ensure(c, c->tmask, ninc * sizeof(int) * 2) ||
+  if (!sea_ensure(c, c->tmask, ninc * sizeof(int) * 3) ||
       !sea_ensure(c, c->tptr_t, (size_t)(nt + 1) * sizeof(int) * 2) ||
       !sea_ensure(c, c->tptr_o, (size_t)(n + 1) * sizeof(int) * 2) ||
       !sea_ensure(c, c->Mbuf, (size_t)n * n * sizeof(double)) ||
       !sea_ensure(c, c->Lbuf, (size_t)n * n * sizeof(double)) ||
-      !sea_ensure(c, c->Linv, (size_t)n * n * sizeof(double)))
+      !sea_ensure(c, c->Linv, (size_t)n * n * sizeof(double)) ||
+      !sea_ensure(c, c->Abuf, (size_t)n * CB * sizeof(double)))
     return cudaErrorMemoryAllocation;
   int* inc = (int*)c->tmask.p;
   int* gidx = inc + ninc;
+  int* sub = inc + 2 * ninc;
   int* tcnt = (int*)c->tptr_t.p;
   int* tptr = tcnt + (nt + 1);
   int* ocnt = (int*)c->tptr_o.p;
   int* optr = ocnt + (n + 1);
   int* counts = (int*)c->counts.p;
   k_tile_incidence<<<(unsigned)((ninc + 255) / 256), 256, 0, c->stream>>>(
-      (const Entry*)c->ewin.p, (const int*)c->eptr.p, n, G, nt, inc);
-  k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, n, nt, 0, tcnt, nullptr, nullptr,
-                                                        nullptr);
+      (const Entry*)c->ewin.p, (const int*)c->eptr.p, n, G, nt, inc, sub);
+  k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, sub, n, nt, 0, tcnt, nullptr,
+                                                        nullptr, nullptr, nullptr);
   k_scan_small<<<1, 1024, 0, c->stream>>>(tcnt, nt, tptr, counts + 10);
   k_max_int<<<1, 1024, 0, c->stream>>>(tcnt, nt, counts + 12);
   int hc[3] = {0, 0, 0};
@@ -444,32 +672,46 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     if (smem > 48 * 1024) {
       err = cudaFuncSetAttribute(k_tile_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
+      if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_tile_expand_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
       if (err != cudaSuccess) return err;
     }
   }
-  if (!sea_ensure(c, c->tlist_t, (size_t)max(hinc, 1) * sizeof(int)) ||
+  // tlist_t holds the tile-major orbital list and, after it, the sub-boxes
+  if (!sea_ensure(c, c->tlist_t, (size_t)max(hinc, 1) * sizeof(int) * 2) ||
       !sea_ensure(c, c->tlist_o, (size_t)max(hinc, 1) * sizeof(int) * 2) ||
       !sea_ensure(c, c->partial, (size_t)max(hinc, 1) * n * sizeof(double)))
     return cudaErrorMemoryAllocation;
   int* tlist = (int*)c->tlist_t.p;
+  int* tsub = tlist + max(hinc, 1);
   int* olist = (int*)c->tlist_o.p;
   int* oslot = olist + max(hinc, 1);
-  k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, n, nt, 1, nullptr, tptr, tlist, gidx);
-  k_orb_lists<<<(n + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 0, ocnt, nullptr, nullptr,
-                                                      nullptr);
+  k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, sub, n, nt, 1, nullptr, tptr, tlist,
+                                                        tsub, gidx);
+  k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 0, ocnt, nullptr,
+                                                           nullptr, nullptr);
   k_scan_small<<<1, 1024, 0, c->stream>>>(ocnt, n, optr, counts + 11);
-  k_orb_lists<<<(n + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 1, nullptr, optr, olist, oslot);
+  k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 1, nullptr, optr, olist,
+                                                           oslot);
   // M = Phi^T W dV
-  k_gram_partial<<<dim3(nt, (n + GA - 1) / GA), 256, 0, c->stream>>>(
-      (const double*)c->phi.p, n, (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist,
-      (double*)c->partial.p);
+  err = cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GRAM_SMEM);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_gram_partial_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)GRAMX_SMEM);
+  if (err != cudaSuccess) return err;
+  cudaEventRecord(c->ev[10], c->stream);
+  launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
+  cudaEventRecord(c->ev[11], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p, n, 1);
   k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
   int nchol = 1;
   for (int kb = 0; kb < n; kb += CB) {
-    k_chol_panel<<<1, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb, (unsigned*)c->status.p);
+    k_chol_panel<<<1, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb, (unsigned*)c->status.p,
+                                           (double*)c->Abuf.p);
     const int nbt = (n - kb - CB + CB - 1) / CB;
     if (nbt > 0)
       k_chol_update<<<nbt * (nbt + 1) / 2, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb,
@@ -494,12 +736,14 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
     return cudaErrorMemoryAllocation;
   const int* tptr = (const int*)c->tptr_t.p + (nt + 1);
   const int* tlist = (const int*)c->tlist_t.p;
+  const int* tsub = tlist + max(hinc, 1);
   const int* optr = (const int*)c->tptr_o.p + (n + 1);
   const int* olist = (const int*)c->tlist_o.p;
   const int* oslot = olist + max(hinc, 1);
   // G[o][v] = <W_o|psi_v> dV
-  k_gram_partial<<<dim3(nt, (nv + GA - 1) / GA), 256, 0, c->stream>>>(
-      psi, nv, (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, (double*)c->partial.p);
+  cudaEventRecord(c->ev[12], c->stream);
+  launch_gram(c, psi, nv, G, tptr, tlist, tsub);
+  cudaEventRecord(c->ev[13], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * nv + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p, 1, nv);
   // H = L^-T (L^-1 G)
@@ -509,10 +753,9 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
   k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Hbuf2.p, n,
                                          nv, (double*)c->Hbuf.p);
   // out[v] = -sum_j W_j H[j][v]
-  const size_t smem = (size_t)c->max_tile_list * EV * sizeof(double);
-  k_tile_expand<<<dim3(nt, (nv + EV - 1) / EV), 256, smem, c->stream>>>(
-      (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, (const double*)c->Hbuf.p, nv, 1, nv,
-      -1.0, out);
+  cudaEventRecord(c->ev[14], c->stream);
+  launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Hbuf.p, nv, 1, nv, -1.0, out);
+  cudaEventRecord(c->ev[15], c->stream);
   c->launches += 5;
   return cudaGetLastError();
 }
@@ -523,11 +766,9 @@ cudaError_t launch_ace_vectors(sea_ctx* c, double* xi) {
   const int nt = c->n_tiles;
   const int* tptr = (const int*)c->tptr_t.p + (nt + 1);
   const int* tlist = (const int*)c->tlist_t.p;
-  const size_t smem = (size_t)c->max_tile_list * EV * sizeof(double);
+  const int* tsub = tlist + max(c->tile_inc, 1);
   // Xi[k][r] = sum_j W[j][r] (L^-1)[k][j]:  H(j, k) = Linv[k * n + j]
-  k_tile_expand<<<dim3(nt, (n + EV - 1) / EV), 256, smem, c->stream>>>(
-      (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, (const double*)c->Linv.p, 1, n, n, 1.0,
-      xi);
+  launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Linv.p, 1, n, n, 1.0, xi);
   c->launches += 1;
   return cudaGetLastError();
 }

@@ -11,18 +11,41 @@
 
 namespace sea {
 
-// Real solid-harmonic recurrence coefficients (Racah normalization).
+// Coefficients of the rescaled solid-harmonic recurrences (see
+// sea_internal.cuh).  From the Racah-normalized recurrences
+//   C_{l+1,+-(l+1)} = t_l (x C_ll -+ y C_l,-l ...),  t_l = sqrt(2^[l=0] (2l+1)/(2l+2))
+//   C_{l+1,m} = b_lm z C_lm - c_lm r^2 C_{l-1,m},
+//   b_lm = (2l+1)/sqrt((l+m+1)(l-m+1)),  c_lm = sqrt((l+m)(l-m)/((l+m+1)(l-m+1))),
+// the scaling kappa_lm = tau_|m| sigma_lm with tau_0 = 1, tau_{k+1} = t_k tau_k,
+// sigma_{|m|,m} = 1, sigma_{l+1,m} = b_lm sigma_lm removes t and b; then
+// gam_lm = c_lm sigma_{l-1,m} / sigma_{l+1,m}.
 HarmCoef make_harmonic_coefficients() {
   HarmCoef h;
   memset(&h, 0, sizeof(h));
-  for (int l = 0; l < SEA_LMAX; ++l) {
-    h.top[l] = std::sqrt((l == 0 ? 2.0 : 1.0) * (2.0 * l + 1.0) / (2.0 * l + 2.0));
+  double tau[SEA_LMAX + 1];
+  tau[0] = 1.0;
+  for (int k = 0; k < SEA_LMAX; ++k)
+    tau[k + 1] = std::sqrt((k == 0 ? 2.0 : 1.0) * (2.0 * k + 1.0) / (2.0 * k + 2.0)) * tau[k];
+  double sig[SEA_LMAX + 1][2 * SEA_LMAX + 1];
+  for (int l = 0; l <= SEA_LMAX; ++l)
     for (int m = -l; m <= l; ++m) {
-      const double d = std::sqrt((double)(l + m + 1) * (double)(l - m + 1));
-      h.mid_b[l][m + SEA_LMAX] = (2.0 * l + 1.0) / d;
-      h.mid_c[l][m + SEA_LMAX] = std::sqrt((double)(l + m) * (double)(l - m)) / d;
+      const int am = m < 0 ? -m : m;
+      if (l == am) {
+        sig[l][m + SEA_LMAX] = 1.0;
+      } else {
+        const int lp = l - 1;  // sigma_{lp+1,m} = b_{lp,m} sigma_{lp,m}
+        const double b = (2.0 * lp + 1.0) / std::sqrt((double)(lp + m + 1) * (double)(lp - m + 1));
+        sig[l][m + SEA_LMAX] = b * sig[lp][m + SEA_LMAX];
+      }
+      const double kap = tau[am] * sig[l][m + SEA_LMAX];
+      h.kap2[l * l + l + m] = kap * kap;
     }
-  }
+  for (int l = 1; l < SEA_LMAX; ++l)
+    for (int m = -(l - 1); m <= l - 1; ++m) {
+      const double c = std::sqrt((double)(l + m) * (double)(l - m) /
+                                 ((double)(l + m + 1) * (double)(l - m + 1)));
+      h.gam[l][m + SEA_LMAX] = c * sig[l - 1][m + SEA_LMAX] / sig[l + 1][m + SEA_LMAX];
+    }
   return h;
 }
 
@@ -182,7 +205,7 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
     delete c;
     return SEA_ERR_CUDA;
   }
-  for (int k = 0; k < 10; ++k)
+  for (int k = 0; k < 16; ++k)
     if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
       delete c;
       return SEA_ERR_CUDA;
@@ -335,7 +358,9 @@ sea_status sea_build_ace(sea_ctx* c) {
   float t = 0;
   cudaEventElapsedTime(&t, c->ev[5], c->ev[6]);
   c->stats.ms_ace_build = t;
-  c->stats.ace_support_points = (long long)c->tile_inc * 512;
+  cudaEventElapsedTime(&t, c->ev[10], c->ev[11]);
+  c->stats.ms_gram_build = t;
+  c->stats.ace_support_points = (long long)c->tile_inc * 128;
   if (st & SEA_FLAG_NOT_PD) return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is not positive definite");
   c->have_ace = true;
   return SEA_OK;
@@ -364,10 +389,8 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   if (!on_device) {
     SEA_CK(cudaMemcpyAsync(out, c->out_dev.p, bytes, cudaMemcpyDeviceToHost, c->stream), "copy out");
     SEA_CK(cudaStreamSynchronize(c->stream), "apply_ace");
-    float t = 0;
-    cudaEventElapsedTime(&t, c->ev[7], c->ev[8]);
-    c->stats.ms_ace_apply = t;
   }
+  c->apply_timed = true;
   return SEA_OK;
 }
 
@@ -532,6 +555,14 @@ sea_status sea_get_stats(const sea_ctx* c, sea_stats* s) {
   if (!c || !s) return SEA_ERR_ARG;
   *s = c->stats;
   s->n_launches = c->launches;
+  // timings of the last sea_apply_ace, if its work has finished (no wait)
+  if (c->apply_timed && cudaEventQuery(c->ev[8]) == cudaSuccess) {
+    float t = 0;
+    if (cudaEventElapsedTime(&t, c->ev[7], c->ev[8]) == cudaSuccess) s->ms_ace_apply = t;
+    if (cudaEventElapsedTime(&t, c->ev[12], c->ev[13]) == cudaSuccess) s->ms_gram_apply = t;
+    if (cudaEventElapsedTime(&t, c->ev[14], c->ev[15]) == cudaSuccess) s->ms_expand_apply = t;
+  }
+  cudaGetLastError();
   return SEA_OK;
 }
 
@@ -552,7 +583,7 @@ void sea_destroy(sea_ctx* c) {
                    &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf,
                    &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2};
   for (SeaBuf* b : all) release(*b);
-  for (int k = 0; k < 10; ++k)
+  for (int k = 0; k < 16; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   delete c;
 }

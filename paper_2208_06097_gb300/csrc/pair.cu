@@ -1,10 +1,10 @@
 // pair.cu -- per-pair Poisson problems (Sec. II B: Eqs. pe, me, mepole).
 //
-// k_pair_setup (one CTA per pair): rho_ij = phi_i phi_j on Omega_ij, its
-//   multipole moments about the box centre, the multipole potential at every
+// k_pair_moments (one CTA per pair): rho_ij = phi_i phi_j on Omega_ij and
+//   its multipole moments about the box centre; b = 4 pi rho.
+// k_pair_boundary (one CTA per pair): the multipole potential at every
 //   point outside the box that the 37-point stencil reaches (one coordinate
-//   outside, by 1..6), and the right-hand side b = 4 pi rho + (stencil
-//   weights x those boundary values).
+//   outside, by 1..6), added to b with the stencil weights.
 // k_cg (persistent, longest pairs first): conjugate gradients for
 //   -Lap_h v = b on the box with zero values outside, FP64, two block
 //   reductions per iteration (warp shuffles, then warps in fixed order),
@@ -23,53 +23,25 @@ struct StencilW {
   double rhs[3][SEA_FDP + 1]; // +c_k / h_a^2 (boundary values moved to b)
 };
 
-// Moments: acc[lm] += rho * C_lm(x, y, z), computed level by level.
-__device__ __forceinline__ void moment_accumulate(double rho, double x, double y, double z,
-                                                  double* acc) {
-  const double r2 = x * x + y * y + z * z;
-  double C[SEA_NQ];
-  C[0] = 1.0;
-  acc[0] += rho;
-#pragma unroll
-  for (int l = 0; l < SEA_LMAX; ++l) {
-    const double t = c_harm.top[l];
-    if (l == 0) {
-      C[lmi(1, 1)] = t * x;
-      C[lmi(1, -1)] = t * y;
-    } else {
-      C[lmi(l + 1, l + 1)] = t * (x * C[lmi(l, l)] - y * C[lmi(l, -l)]);
-      C[lmi(l + 1, -(l + 1))] = t * (y * C[lmi(l, l)] + x * C[lmi(l, -l)]);
-    }
-#pragma unroll
-    for (int m = -l; m <= l; ++m) {
-      double v = c_harm.mid_b[l][m + SEA_LMAX] * z * C[lmi(l, m)];
-      if (l >= 1 && m >= -(l - 1) && m <= l - 1)
-        v -= c_harm.mid_c[l][m + SEA_LMAX] * r2 * C[lmi(l - 1, m)];
-      C[lmi(l + 1, m)] = v;
-    }
-#pragma unroll
-    for (int m = -(l + 1); m <= l + 1; ++m) acc[lmi(l + 1, m)] = fma(rho, C[lmi(l + 1, m)], acc[lmi(l + 1, m)]);
-  }
-}
-
+// Pair density and moments, one CTA per pair: b = 4 pi rho on the box,
+// Qs = rescaled multipole moments of rho about the box centre (Eq. mepole).
 __global__ void __launch_bounds__(256, 1)
-    k_pair_setup(const double* __restrict__ phi, int nx, int ny, int nz,
-                 const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
-                 double hx, double hy, double hz, double dV, int lmax, StencilW W,
-                 double* __restrict__ bbuf, double* __restrict__ Qout) {
+    k_pair_moments(const double* __restrict__ phi, int nx, int ny, int nz,
+                   const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
+                   double hx, double hy, double hz, double dV, int lmax,
+                   double* __restrict__ bbuf, double* __restrict__ Qout) {
   const int p = blockIdx.x;
   const PairInfo P = pinfo[p];
-  const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
+  const int ex = P.ext[0], ey = P.ext[1];
   const int n = P.n;
   const size_t ng = (size_t)nx * ny * nz;
   const double* fi = phi + (size_t)P.i * ng;
   const double* fj = phi + (size_t)P.j * ng;
   double* b = bbuf + voff[p];
-  const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (ez - 1);
+  const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (P.ext[2] - 1);
+  const double fourpi = 4.0 * 3.14159265358979323846;
 
   __shared__ double red[8][SEA_NQ];
-  __shared__ double Qs[SEA_NQ];
-
   double acc[SEA_NQ];
 #pragma unroll
   for (int q = 0; q < SEA_NQ; ++q) acc[q] = 0.0;
@@ -78,8 +50,8 @@ __global__ void __launch_bounds__(256, 1)
     const size_t g = ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx +
                      wrapi(P.lo[0] + x, nx);
     const double rho = fi[g] * fj[g];
-    b[t] = rho;
-    moment_accumulate(rho, (x - cx) * hx, (y - cy) * hy, (z - cz) * hz, acc);
+    b[t] = fourpi * rho;
+    harm_accumulate(rho, (x - cx) * hx, (y - cy) * hy, (z - cz) * hz, acc);
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -96,43 +68,57 @@ __global__ void __launch_bounds__(256, 1)
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][q];
     int l = 0;
     while ((l + 1) * (l + 1) <= q) ++l;
-    const double Q = (l <= lmax) ? s * dV : 0.0;
-    Qs[q] = Q;
-    Qout[(size_t)p * SEA_NQ + q] = Q;
+    Qout[(size_t)p * SEA_NQ + q] = (l <= lmax) ? c_harm.kap2[q] * s * dV : 0.0;
   }
-  const double fourpi = 4.0 * 3.14159265358979323846;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) b[t] *= fourpi;
-  __syncthreads();
+}
 
-  // Boundary values along each axis, one thread per line of the box.
-  const int e3[3] = {ex, ey, ez};
-  const double h3[3] = {hx, hy, hz};
-  const double c3[3] = {cx, cy, cz};
+// Boundary values (Eq. me) at every point outside the box that the
+// 37-point stencil reaches, moved into b with the stencil weights; one CTA
+// per pair, one thread per line of the box along each axis in turn (the
+// axes one after the other, so every b entry is updated in a fixed order).
+__global__ void __launch_bounds__(256, 1)
+    k_pair_boundary(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
+                    double hx, double hy, double hz, StencilW W, const double* __restrict__ Qg,
+                    double* __restrict__ bbuf) {
+  const int p = blockIdx.x;
+  const PairInfo P = pinfo[p];
+  const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
+  double* b = bbuf + voff[p];
+  __shared__ double Qs[SEA_NQ];
+  if (threadIdx.x < SEA_NQ) Qs[threadIdx.x] = Qg[(size_t)p * SEA_NQ + threadIdx.x];
+  __syncthreads();
+  const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (ez - 1);
   for (int a = 0; a < 3; ++a) {
-    const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
-    const int nl = e3[b1] * e3[b2];
-    const int ea = e3[a];
+    // line coordinates (u1, u2) across axis a; along-axis extent ea, stride sa
+    const int e1 = a == 0 ? ey : ex, e2 = a == 2 ? ey : ez;
+    const int ea = a == 0 ? ex : (a == 1 ? ey : ez);
+    const int sa = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
+    const double ha = a == 0 ? hx : (a == 1 ? hy : hz);
+    const double ca = a == 0 ? cx : (a == 1 ? cy : cz);
+    const int nl = e1 * e2;
     for (int line = threadIdx.x; line < nl; line += blockDim.x) {
-      int u[3];
-      u[b1] = line % e3[b1];
-      u[b2] = line / e3[b1];
+      const int u1 = line % e1, u2 = line / e1;
+      // the two fixed coordinates in (x, y, z) order and the base index
+      int bx = 0, by = 0, bz = 0;
+      double px = 0, py = 0, pz = 0;
+      if (a == 0) { by = u1; bz = u2; py = (by - cy) * hy; pz = (bz - cz) * hz; }
+      else if (a == 1) { bx = u1; bz = u2; px = (bx - cx) * hx; pz = (bz - cz) * hz; }
+      else { bx = u1; by = u2; px = (bx - cx) * hx; py = (by - cy) * hy; }
+      const int base = (bz * ey + by) * ex + bx;
       double Glo[SEA_FDP + 1], Ghi[SEA_FDP + 1];
 #pragma unroll
       for (int d = 1; d <= SEA_FDP; ++d) {
-        double r[3];
-        r[b1] = (u[b1] - c3[b1]) * h3[b1];
-        r[b2] = (u[b2] - c3[b2]) * h3[b2];
-        r[a] = (-d - c3[a]) * h3[a];
-        Glo[d] = me_potential(Qs, r[0], r[1], r[2]);
-        r[a] = (ea - 1 + d - c3[a]) * h3[a];
-        Ghi[d] = me_potential(Qs, r[0], r[1], r[2]);
-      }
-      const int sa = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
-      int base = 0;
-      {
-        int uu[3] = {u[0], u[1], u[2]};
-        uu[a] = 0;
-        base = (uu[2] * ey + uu[1]) * ex + uu[0];
+        const double lo = (-d - ca) * ha, hi = (ea - 1 + d - ca) * ha;
+        if (a == 0) {
+          Glo[d] = me_potential(Qs, lo, py, pz);
+          Ghi[d] = me_potential(Qs, hi, py, pz);
+        } else if (a == 1) {
+          Glo[d] = me_potential(Qs, px, lo, pz);
+          Ghi[d] = me_potential(Qs, px, hi, pz);
+        } else {
+          Glo[d] = me_potential(Qs, px, py, lo);
+          Ghi[d] = me_potential(Qs, px, py, hi);
+        }
       }
       for (int ta = 0; ta < ea; ++ta) {
         if (ta >= SEA_FDP && ta < ea - SEA_FDP) continue;
@@ -534,11 +520,14 @@ static StencilW make_weights(const sea_ctx* c) {
 
 cudaError_t launch_pair_setup(sea_ctx* c) {
   if (c->P == 0) return cudaSuccess;
-  k_pair_setup<<<c->P, 256, 0, c->stream>>>(
+  k_pair_moments<<<c->P, 256, 0, c->stream>>>(
       (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const PairInfo*)c->pinfo.p,
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
-      make_weights(c), (double*)c->bbuf.p, (double*)c->Q.p);
-  c->launches += 1;
+      (double*)c->bbuf.p, (double*)c->Q.p);
+  k_pair_boundary<<<c->P, 256, 0, c->stream>>>(
+      (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2],
+      make_weights(c), (const double*)c->Q.p, (double*)c->bbuf.p);
+  c->launches += 2;
   return cudaGetLastError();
 }
 

@@ -30,18 +30,24 @@ __host__ __device__ inline int wrapi(int x, int n) {
 
 __host__ __device__ inline int lmi(int l, int m) { return l * l + l + m; }
 
-// Coefficients of the real solid-harmonic recurrences in Racah
-// normalization (C_l0 = r^l P_l(cos theta)), filled by the host:
-//   C_{l+1,+-(l+1)} = top[l] (x C_{l,l} -+ y C_{l,-l}),  (x C_00 / y C_00 at l = 0)
-//   C_{l+1,m} = mid_b[l][m] z C_{l,m} - mid_c[l][m] r^2 C_{l-1,m},  |m| <= l.
-// With Q_lm = sum rho C_lm dV, the multipole potential of Eq. me is
+// Real solid harmonics in a rescaled basis D_lm = C_lm / kappa_lm, where
+// C_lm are the Racah-normalized real regular solid harmonics
+// (C_l0 = r^l P_l(cos theta)).  The scaling is chosen so that the
+// recurrences carry no per-term normalization:
+//   D_00 = 1, D_11 = x, D_1-1 = y,
+//   D_{l+1,l+1} = x D_ll - y D_l,-l,   D_{l+1,-(l+1)} = y D_ll + x D_l,-l,
+//   D_{l+1,m} = z D_lm - gam_lm r^2 D_{l-1,m}   (|m| <= l; no second term
+//                                                 when |m| = l).
+// With Q_lm = sum rho C_lm dV the multipole potential of Eq. me is
 //   v(r) = sum_lm Q_lm C_lm(r) / r^(2l+1)
-// (the orthonormal form 4 pi Q Y /((2l+1) r^(l+1)) with the (2l+1)/(4 pi)
-// normalization folded into C).
+// (the orthonormal form 4 pi Q Y / ((2l+1) r^(l+1)), the (2l+1)/(4 pi)
+// normalization folded into C).  Kelvin inversion, u = r / r^2, gives
+// C_lm(r) / r^(2l+1) = C_lm(u) / r, so
+//   v(r) = (1/r) sum_lm Qs_lm D_lm(u),   Qs_lm = kappa_lm^2 sum rho D_lm dV,
+// the D_lm(u) from the same recurrence with r^2 replaced by |u|^2 = 1/r^2.
 struct HarmCoef {
-  double top[SEA_LMAX];
-  double mid_b[SEA_LMAX][2 * SEA_LMAX + 1];
-  double mid_c[SEA_LMAX][2 * SEA_LMAX + 1];
+  double gam[SEA_LMAX][2 * SEA_LMAX + 1];
+  double kap2[SEA_NQ];
 };
 // Each translation unit that evaluates harmonics holds its own copy (the
 // library is built without relocatable device code) and uploads it through
@@ -54,61 +60,66 @@ static inline cudaError_t upload_harmonics_here() {
   return cudaMemcpyToSymbol(c_harm, &h, sizeof(h));
 }
 
-// All regular solid harmonics C_lm(x, y, z), l <= SEA_LMAX.
-__device__ __forceinline__ void solid_regular(double x, double y, double z, double* C) {
+// acc[lm] += w * D_lm(x, y, z) (regular, rescaled basis), level by level.
+__device__ __forceinline__ void harm_accumulate(double w, double x, double y, double z,
+                                                double* acc) {
   const double r2 = x * x + y * y + z * z;
-  C[0] = 1.0;
+  double D[SEA_NQ];
+  D[0] = 1.0;
+  D[lmi(1, 1)] = x;
+  D[lmi(1, -1)] = y;
+  D[lmi(1, 0)] = z;
+  acc[0] += w;
+  acc[lmi(1, -1)] = fma(w, y, acc[lmi(1, -1)]);
+  acc[lmi(1, 0)] = fma(w, z, acc[lmi(1, 0)]);
+  acc[lmi(1, 1)] = fma(w, x, acc[lmi(1, 1)]);
 #pragma unroll
-  for (int l = 0; l < SEA_LMAX; ++l) {
-    const double t = c_harm.top[l];
-    if (l == 0) {
-      C[lmi(1, 1)] = t * x;
-      C[lmi(1, -1)] = t * y;
-    } else {
-      C[lmi(l + 1, l + 1)] = t * (x * C[lmi(l, l)] - y * C[lmi(l, -l)]);
-      C[lmi(l + 1, -(l + 1))] = t * (y * C[lmi(l, l)] + x * C[lmi(l, -l)]);
-    }
+  for (int l = 1; l < SEA_LMAX; ++l) {
+    D[lmi(l + 1, l + 1)] = fma(x, D[lmi(l, l)], -y * D[lmi(l, -l)]);
+    D[lmi(l + 1, -(l + 1))] = fma(y, D[lmi(l, l)], x * D[lmi(l, -l)]);
 #pragma unroll
     for (int m = -l; m <= l; ++m) {
-      double v = c_harm.mid_b[l][m + SEA_LMAX] * z * C[lmi(l, m)];
-      if (l >= 1 && m >= -(l - 1) && m <= l - 1)
-        v -= c_harm.mid_c[l][m + SEA_LMAX] * r2 * C[lmi(l - 1, m)];
-      C[lmi(l + 1, m)] = v;
+      if (m >= -(l - 1) && m <= l - 1)
+        D[lmi(l + 1, m)] = fma(z, D[lmi(l, m)], -(c_harm.gam[l][m + SEA_LMAX] * r2) * D[lmi(l - 1, m)]);
+      else
+        D[lmi(l + 1, m)] = z * D[lmi(l, m)];
     }
+#pragma unroll
+    for (int m = -(l + 1); m <= l + 1; ++m) acc[lmi(l + 1, m)] = fma(w, D[lmi(l + 1, m)], acc[lmi(l + 1, m)]);
   }
 }
 
-// Multipole potential sum_lm Q_lm C_lm(r)/r^(2l+1) at r = (x, y, z) != 0,
-// through the irregular harmonics I_lm = C_lm / r^(2l+1), which obey the
-// same recurrence scaled by 1/r^2 per level (I_00 = 1/r).  Q in shared or
-// global memory, zero beyond the requested l_max.
+// Multipole potential at r = (x, y, z) != 0 (relative to the expansion
+// centre) from the rescaled moments Qs (shared or global memory, zero beyond
+// the requested l_max): v = (1/r) sum Qs_lm D_lm(r / r^2).
 __device__ __forceinline__ double me_potential(const double* __restrict__ Q, double x,
                                                double y, double z) {
-  const double r2 = x * x + y * y + z * z;
-  const double ir2 = 1.0 / r2;
-  double I[SEA_NQ];
-  I[0] = sqrt(ir2);
-  double v = Q[0] * I[0];
+  const double ir2 = 1.0 / (x * x + y * y + z * z);
+  const double ux = x * ir2, uy = y * ir2, uz = z * ir2;
+  double D[SEA_NQ];
+  D[0] = 1.0;
+  D[lmi(1, 1)] = ux;
+  D[lmi(1, -1)] = uy;
+  D[lmi(1, 0)] = uz;
+  double v = Q[0];
+  v = fma(Q[lmi(1, -1)], uy, v);
+  v = fma(Q[lmi(1, 0)], uz, v);
+  v = fma(Q[lmi(1, 1)], ux, v);
 #pragma unroll
-  for (int l = 0; l < SEA_LMAX; ++l) {
-    const double t = c_harm.top[l] * ir2;
-    if (l == 0) {
-      I[lmi(1, 1)] = t * x * I[0];
-      I[lmi(1, -1)] = t * y * I[0];
-    } else {
-      I[lmi(l + 1, l + 1)] = t * (x * I[lmi(l, l)] - y * I[lmi(l, -l)]);
-      I[lmi(l + 1, -(l + 1))] = t * (y * I[lmi(l, l)] + x * I[lmi(l, -l)]);
-    }
+  for (int l = 1; l < SEA_LMAX; ++l) {
+    D[lmi(l + 1, l + 1)] = fma(ux, D[lmi(l, l)], -uy * D[lmi(l, -l)]);
+    D[lmi(l + 1, -(l + 1))] = fma(uy, D[lmi(l, l)], ux * D[lmi(l, -l)]);
 #pragma unroll
     for (int m = -l; m <= l; ++m) {
-      double u = c_harm.mid_b[l][m + SEA_LMAX] * z * I[lmi(l, m)];
-      if (l >= 1 && m >= -(l - 1) && m <= l - 1) u -= c_harm.mid_c[l][m + SEA_LMAX] * I[lmi(l - 1, m)];
-      I[lmi(l + 1, m)] = u * ir2;
+      if (m >= -(l - 1) && m <= l - 1)
+        D[lmi(l + 1, m)] = fma(uz, D[lmi(l, m)], -(c_harm.gam[l][m + SEA_LMAX] * ir2) * D[lmi(l - 1, m)]);
+      else
+        D[lmi(l + 1, m)] = uz * D[lmi(l, m)];
     }
 #pragma unroll
-    for (int m = -(l + 1); m <= l + 1; ++m) v = fma(Q[lmi(l + 1, m)], I[lmi(l + 1, m)], v);
+    for (int m = -(l + 1); m <= l + 1; ++m) v = fma(Q[lmi(l + 1, m)], D[lmi(l + 1, m)], v);
   }
-  return v;
+  return v * sqrt(ir2);
 }
 
 // Sum over the block of one double; every thread gets the same total, added
@@ -152,7 +163,7 @@ struct sea_ctx {
   char err[256] = {0};
 
   int n_orb = 0;
-  bool have_phi = false, have_vxx = false, have_ace = false;
+  bool have_phi = false, have_vxx = false, have_ace = false, apply_timed = false;
 
   // plan sizes (host copies)
   int P = 0, Pproto = 0, E = 0;
@@ -174,7 +185,7 @@ struct sea_ctx {
   int n_tiles = 0, tile_inc = 0, max_tile_list = 0;
 
   long long launches = 0;
-  cudaEvent_t ev[10] = {};
+  cudaEvent_t ev[16] = {};
 };
 
 // Host-side helpers implemented in api.cu.

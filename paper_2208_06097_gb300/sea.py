@@ -52,7 +52,9 @@ class Stats(ctypes.Structure):
                 ("ms_plan", ctypes.c_double), ("ms_setup", ctypes.c_double),
                 ("ms_cg", ctypes.c_double), ("ms_accumulate", ctypes.c_double),
                 ("ms_ace_build", ctypes.c_double), ("ms_ace_apply", ctypes.c_double),
-                ("ace_support_points", ctypes.c_longlong), ("n_launches", ctypes.c_longlong)]
+                ("ace_support_points", ctypes.c_longlong), ("n_launches", ctypes.c_longlong),
+                ("ms_gram_build", ctypes.c_double), ("ms_gram_apply", ctypes.c_double),
+                ("ms_expand_apply", ctypes.c_double)]
 
 
 _LIB = None

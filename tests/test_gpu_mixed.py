@@ -52,3 +52,30 @@ def test_mixed_precision_workload_per_density(name):
     n_mol = s.n_orb // 4
     assert abs(exx - ref["exx"]) / n_mol <= 1e-6
     assert np.abs(v - ref["vxx"]).max() <= 5e-8 * np.abs(ref["vxx"]).max()
+
+
+def test_mixed_ace_matches_fp64_oracle(h2o8):
+    # the mixed form's ACE contractions use FP32 error-free transformations;
+    # their results must stay within FP64-class error of the dense oracle
+    from oracle import ace as OA
+    from paper_2208_06097_gb300 import sea
+    ref = O.apply_vxx(h2o8.phi, h2o8.cell, O.Params(cg_tol=1e-12))
+    F = h2o8.phi.reshape(h2o8.n_orb, -1)
+    a = OA.build_ace(F, ref["vxx"].reshape(h2o8.n_orb, -1), h2o8.dV)
+    with sea.Context(h2o8.cell, h2o8.grid, precision=1, cg_tol=1e-12) as ctx:
+        phi = torch.from_numpy(h2o8.phi).cuda()
+        out = torch.empty_like(phi)
+        ctx.set_orbitals(phi)
+        ctx.apply_vxx(out)
+        ctx.build_ace()
+        M, L = ctx.ace_matrices()
+        psi = synth.random_trial_vectors(4, h2o8.grid, 12)
+        y = np.empty_like(psi)
+        ctx.apply_ace(psi, y)
+        xi = torch.empty_like(phi)
+        ctx.ace_vectors(xi)
+    assert np.abs(M - a["M"]).max() <= 1e-9
+    assert np.abs(L - a["L"]).max() <= 1e-9
+    yr = OA.apply_ace(a["Xi"], psi.reshape(4, -1), h2o8.dV)
+    assert np.abs(y.reshape(4, -1) - yr).max() <= 1e-9 * np.abs(yr).max()
+    assert np.abs(xi.cpu().numpy().reshape(h2o8.n_orb, -1) - a["Xi"]).max() <= 1e-8 * np.abs(a["Xi"]).max()
