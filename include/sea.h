@@ -61,7 +61,11 @@ typedef enum {
  * residual density in bohr^-3 as App. C states it), cg_max_iter = 5000,
  * lmax = 6 (App. C), fd_order = 12 (App. C, O(h^12) Laplacian; the only
  * supported value), self_scale = 2 (Omega^D_ii = scale_2x Omega_ii, the only
- * supported value), precision = 0 (FP64 everywhere; 1: the mixed form --
+ * supported value), ace_decomp = 0 (Cholesky of -Mbar, with the eigen
+ * decomposition of App. A -- -Mbar = Q Lambda Q^T, operator
+ * -W Q |Lambda|^-1 Q^T W^T (the complex zeta of App. A under a Hermitian
+ * inner product), eigenvalues within 1e-13 max|lambda| of zero dropped --
+ * when a Cholesky pivot is not positive), precision = 0 (FP64 everywhere; 1: the mixed form --
  * FP32 stencil sweeps and CG vectors inside an FP64 iterative refinement of
  * each pair's solve: true residual, its norm, the stopping rule, dot
  * products across the block, E_xx and the ACE stay FP64), warm_start = 0. */
@@ -77,6 +81,8 @@ typedef struct {
   int precision;  /* 0: FP64, 1: mixed (FP32 CG inside FP64 refinement) */
   int warm_start; /* 0: none */
   double timeout_ms; /* reserved, 0 */
+  int ace_decomp; /* 0: Cholesky, eigen form of App. A if a pivot fails;
+                     1: Cholesky only (SEA_ERR_NOT_PD on failure); 2: eigen form */
 } sea_params;
 
 /* Per-call statistics of the last sea_apply_vxx / sea_build_ace /
@@ -98,6 +104,10 @@ typedef struct {
   long long n_launches;  /* kernels this context has launched since creation */
   double ms_gram_build;  /* M = Phi^T W dV contraction, last sea_build_ace       */
   double ms_gram_apply, ms_expand_apply; /* W^T psi and W H, last sea_apply_ace */
+  int ace_eigen;                /* 1 if the last build used the eigen form      */
+  int ace_eigen_sweeps;         /* Jacobi sweeps of that build                  */
+  int ace_negative_eigenvalues; /* eigenvalues of -Mbar below zero              */
+  int ace_dropped_eigenvalues;  /* eigenvalues treated as zero                  */
 } sea_stats;
 
 typedef struct sea_ctx sea_ctx;
@@ -126,8 +136,15 @@ sea_status sea_apply_vxx(sea_ctx* ctx, double* vxx_phi, int on_device, double* e
 
 /* Build the ACE operator from the orbitals and the last sea_apply_vxx
  * result.  Returns SEA_ERR_STATE if no sea_apply_vxx result is current and
- * SEA_ERR_NOT_PD when -Mbar has a non-positive Cholesky pivot. */
+ * SEA_ERR_NOT_PD when -Mbar has a non-positive Cholesky pivot and
+ * ace_decomp = 1 (with ace_decomp = 0 the eigen form takes over). */
 sea_status sea_build_ace(sea_ctx* ctx);
+
+/* Same, from a caller-supplied W = V_xx Phi ([n_orb][nz][ny][nx], host or
+ * device; the decomposition step of Fig. 2(c) on its own).  W is treated
+ * as dense (its support is not known), and it replaces any earlier
+ * sea_apply_vxx result in the context. */
+sea_status sea_build_ace_from(sea_ctx* ctx, const double* W, int on_device);
 
 /* out[n_vec][nz][ny][nx] = V^ACE psi for psi[n_vec][nz][ny][nx] (host or
  * device, same flag for both).  Requires a successful sea_build_ace. */
@@ -136,10 +153,12 @@ sea_status sea_apply_ace(sea_ctx* ctx, const double* psi, int n_vec, double* out
 
 /* Optional exports of the last results (host or device destination).
  *   sea_get_ace_matrices: M[n][n] (M_ij = <phi_i|W_j>), L[n][n] (lower,
- *     zero above the diagonal); either pointer may be NULL.
+ *     zero above the diagonal; in the eigen form, the diagonalized -Mbar:
+ *     eigenvalues on the diagonal); either pointer may be NULL.
  *   sea_get_ace_vectors: xi[n][nz][ny][nx], the ACE vectors Xi = W L^-T
  *     (materialized on demand; the operator itself is applied in the
- *     factored form W L^-T L^-1 W^T).
+ *     factored form W L^-T L^-1 W^T).  SEA_ERR_STATE in the eigen form,
+ *     whose vectors may be complex.
  *   sea_get_plan: box[n][6] (start x,y,z then extent x,y,z of Omega_ii),
  *     pairs[P][2], lo[P][3], ext[P][3] (Omega_ij in i's unwrapped frame),
  *     S[P] (Eq. sij), iters[P] (CG iterations, negative if capped),

@@ -60,3 +60,29 @@ def exx_ace(F: np.ndarray, Xi: np.ndarray, dV: float) -> float:
     """E_xx = -sum_ik <phi_i|xi_k>^2 (Eq. exx_ace)."""
     P = (F @ Xi.T) * dV
     return float(-np.sum(P * P))
+
+
+def build_ace_eigen(F: np.ndarray, W: np.ndarray, dV: float, cut: float = 1e-13) -> dict:
+    """App. A: -Mbar = Q Lambda Q^T (library eigensolver) and
+    zeta_k = sum_i W_i (Q Lambda^-1/2)_ik, complex where lambda_k < 0
+    (the paper's zeta = -D Z^-T with D = -W).  Eigenvalues within
+    cut * max|lambda| of zero are dropped."""
+    F = np.asarray(F, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    M = (F @ W.T) * dV
+    Mbar = 0.5 * (M + M.T)
+    lam, Q = np.linalg.eigh(-Mbar)
+    keep = np.abs(lam) > cut * np.abs(lam).max()
+    s = np.zeros(len(lam), dtype=np.complex128)
+    s[keep] = 1.0 / np.sqrt(lam[keep].astype(np.complex128))
+    zeta = (Q * s[None, :]).T @ W  # rows: zeta_k
+    return dict(M=M, Mbar=Mbar, lam=lam, Q=Q, keep=keep, zeta=zeta[keep])
+
+
+def apply_ace_eigen(zeta: np.ndarray, psi: np.ndarray, dV: float) -> np.ndarray:
+    """V^ACE psi = -sum_k |zeta_k> <zeta_k|psi> dV (Eq. Vace_alter) with the
+    Hermitian inner product <zeta_k|psi> = sum conj(zeta_k) psi (reading:
+    the plane-wave code's products are Hermitian)."""
+    C = (np.conj(zeta) @ psi.T) * dV
+    Y = -(C.T @ zeta)
+    return np.real(Y)

@@ -46,8 +46,8 @@ __device__ __forceinline__ void cyc_cover(int s, int L, int a, int b, int n, int
 // windows inside the tile, packed x0 | x1 << 4 | y0 << 8 | y1 << 12 |
 // z0 << 16 | z1 << 20 (W_o is exactly zero in the tile outside it).
 __global__ void k_tile_incidence(const Entry* __restrict__ ent, const int* __restrict__ eptr,
-                                 int n_orb, TileGeom G, int n_tiles, int* __restrict__ inc,
-                                 int* __restrict__ sub) {
+                                 int n_orb, TileGeom G, int n_tiles, int dense,
+                                 int* __restrict__ inc, int* __restrict__ sub) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n_orb * n_tiles) return;
   const int o = (int)(t / n_tiles), T = (int)(t % n_tiles);
@@ -55,6 +55,11 @@ __global__ void k_tile_incidence(const Entry* __restrict__ ent, const int* __res
   const int ax = txi * TX, bx = min(G.nx, ax + TX);
   const int ay = tyi * TY, by = min(G.ny, ay + TY);
   const int az = tzi * TZ, bz = min(G.nz, az + TZ);
+  if (dense) {  // W given by the caller: no known support, the whole tile
+    inc[t] = 1;
+    sub[t] = 0 | ((bx - ax) << 4) | (0 << 8) | ((by - ay) << 12) | (0 << 16) | ((bz - az) << 20);
+    return;
+  }
   int x0 = TX, x1 = 0, y0 = TY, y1 = 0, z0 = TZ, z1 = 0;
   for (int k = eptr[o]; k < eptr[o + 1]; ++k) {
     const Entry e = ent[k];
@@ -272,9 +277,23 @@ struct CompF {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// v = hi + lo with integer operations only (no FP64 instruction): hi keeps
+// the sign, the exponent and the top 23 mantissa bits (truncation), lo the
+// remaining 29 bits, rounded to an FP32 value of the same sign.  |v| below
+// the FP32 normal range (2^-126) is flushed to (0, 0).  Relative error of
+// hi + lo: <= 2^-47.
 __device__ __forceinline__ float2 split64(double v) {
-  const float hi = (float)v;
-  return make_float2(hi, (float)(v - (double)hi));
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e - 1023 + 127 <= 0) return make_float2(0.f, 0.f);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+  // lo = (m mod 2^29) 2^(e - 1075) = ((m mod 2^29) 2^-64) 2^(e - 1011); e > 896 keeps
+  // the second factor a normal FP32 power of two
+  const float l = ((float)(unsigned)(m & 0x1FFFFFFFULL) * 5.421010862427522e-20f) *
+                  __uint_as_float((unsigned)(e - 884) << 23);
+  return make_float2(hi, __uint_as_float(__float_as_uint(l) | sign));
 }
 
 #define GROWX (TP + 1)
@@ -511,6 +530,130 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Eigen-decomposition form of the ACE build (App. A): -Mbar = Q Lambda Q^T
+// by the cyclic Jacobi method with round-robin ordering (each round rotates
+// ne/2 disjoint index pairs at once; ne = n rounded up to even).  Per round,
+// k_jac_rows computes each pair's rotation from the current matrix and
+// rotates its two rows; k_jac_cols rotates the two columns of S and of Q.
+// App. A's zeta_k = -D Q Lambda^-1/2 is complex where lambda_k < 0; with the
+// Hermitian inner product <zeta_k| of the plane-wave code the phase cancels
+// and V^ACE = -sum_k |zeta_k><zeta_k| = -W Q |Lambda|^-1 Q^T W^T (reading;
+// the same as the Cholesky form when -Mbar is positive definite).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void jac_pair(int k, int r, int ne, int* p, int* q) {
+  // positions k and ne-1-k of the circle: position 0 holds index 0, position
+  // i >= 1 holds 1 + (i - 1 + r) mod (ne - 1)
+  auto idx = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + r) % (ne - 1); };
+  *p = idx(k);
+  *q = idx(ne - 1 - k);
+}
+
+__global__ void k_jac_init(const double* __restrict__ M, int n, double* __restrict__ S,
+                           double* __restrict__ Q) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * n) return;
+  const int i = (int)(t / n), j = (int)(t % n);
+  S[t] = -0.5 * (M[(size_t)i * n + j] + M[(size_t)j * n + i]);
+  Q[t] = (i == j) ? 1.0 : 0.0;
+}
+
+__global__ void k_jac_rows(double* __restrict__ S, int n, int ne, int r, double* __restrict__ cs) {
+  int p, q;
+  jac_pair(blockIdx.x, r, ne, &p, &q);
+  __shared__ double sc[2];
+  if (threadIdx.x == 0) {
+    double c = 1.0, s = 0.0;
+    if (p < n && q < n) {
+      const double apq = S[(size_t)p * n + q];
+      if (apq != 0.0) {
+        const double th = (S[(size_t)q * n + q] - S[(size_t)p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        c = 1.0 / sqrt(t * t + 1.0);
+        s = t * c;
+      }
+    }
+    sc[0] = c;
+    sc[1] = s;
+    cs[2 * blockIdx.x] = c;
+    cs[2 * blockIdx.x + 1] = s;
+  }
+  __syncthreads();
+  if (p >= n || q >= n) return;
+  const double c = sc[0], s = sc[1];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double a = S[(size_t)p * n + j], b = S[(size_t)q * n + j];
+    S[(size_t)p * n + j] = c * a - s * b;
+    S[(size_t)q * n + j] = s * a + c * b;
+  }
+}
+
+__global__ void k_jac_cols(double* __restrict__ S, double* __restrict__ Q, int n, int ne, int r,
+                           const double* __restrict__ cs) {
+  int p, q;
+  jac_pair(blockIdx.x, r, ne, &p, &q);
+  if (p >= n || q >= n) return;
+  const double c = cs[2 * blockIdx.x], s = cs[2 * blockIdx.x + 1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = S[(size_t)i * n + p], b = S[(size_t)i * n + q];
+    S[(size_t)i * n + p] = c * a - s * b;
+    S[(size_t)i * n + q] = s * a + c * b;
+    a = Q[(size_t)i * n + p];
+    b = Q[(size_t)i * n + q];
+    Q[(size_t)i * n + p] = c * a - s * b;
+    Q[(size_t)i * n + q] = s * a + c * b;
+  }
+}
+
+// out[0] = sum of squared off-diagonal entries, out[1] = sum of squared
+// diagonal entries (fixed-order block reduction).
+__global__ void k_jac_norms(const double* __restrict__ S, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double off = 0.0, dia = 0.0;
+  for (size_t t = threadIdx.x; t < (size_t)n * n; t += blockDim.x) {
+    const double v = S[t];
+    if ((int)(t / n) == (int)(t % n))
+      dia = fma(v, v, dia);
+    else
+      off = fma(v, v, off);
+  }
+  off = block_sum(off, red);
+  __syncthreads();
+  dia = block_sum(dia, red);
+  if (threadIdx.x == 0) {
+    out[0] = off;
+    out[1] = dia;
+  }
+}
+
+// inv[i] = 1/|lambda_i| for |lambda_i| > cut, else 0 (eigenvalues within
+// 1e-13 max|lambda| of zero are dropped); counts negative and dropped
+// eigenvalues.
+__global__ void k_jac_invdiag(const double* __restrict__ S, int n, double* __restrict__ inv,
+                              int* __restrict__ counts) {
+  __shared__ double mx;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m = fmax(m, fabs(S[(size_t)i * n + i]));
+    mx = m;
+  }
+  __syncthreads();
+  const double cut = 1e-13 * mx;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double l = S[(size_t)i * n + i];
+    inv[i] = fabs(l) > cut ? 1.0 / fabs(l) : 0.0;
+    if (l < -cut) atomicAdd(&counts[0], 1);
+    if (!(fabs(l) > cut)) atomicAdd(&counts[1], 1);
+  }
+}
+
+// B[i][v] *= d[i]
+__global__ void k_scale_rows(double* __restrict__ B, const double* __restrict__ d, int n, int m) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * m) return;
+  B[t] *= d[t / m];
+}
+
 // Column k of L^-1 by forward substitution, CTA per column.
 __global__ void k_trinv(const double* __restrict__ L, int n, double* __restrict__ Linv) {
   extern __shared__ double xs[];
@@ -655,7 +798,7 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   int* optr = ocnt + (n + 1);
   int* counts = (int*)c->counts.p;
   k_tile_incidence<<<(unsigned)((ninc + 255) / 256), 256, 0, c->stream>>>(
-      (const Entry*)c->ewin.p, (const int*)c->eptr.p, n, G, nt, inc, sub);
+      (const Entry*)c->ewin.p, (const int*)c->eptr.p, n, G, nt, c->w_dense ? 1 : 0, inc, sub);
   k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, sub, n, nt, 0, tcnt, nullptr,
                                                         nullptr, nullptr, nullptr);
   k_scan_small<<<1, 1024, 0, c->stream>>>(tcnt, nt, tptr, counts + 10);
@@ -724,6 +867,52 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   return cudaGetLastError();
 }
 
+// Eigen form (App. A) after M is known: Q into Linv, S (eigenvalues on the
+// diagonal) into Lbuf, 1/lambda into Abuf.  Host loop over sweeps; stops when
+// the off-diagonal mass is below 1e-30 of the diagonal mass (or 60 sweeps).
+cudaError_t launch_ace_eigen(sea_ctx* c) {
+  const int n = c->n_orb;
+  const int ne = n + (n & 1);
+  if (!sea_ensure(c, c->Gbuf, (size_t)max(ne, 2) * sizeof(double) * 2 + 64) ||
+      !sea_ensure(c, c->Abuf, (size_t)n * CB * sizeof(double) + (size_t)n * sizeof(double)))
+    return cudaErrorMemoryAllocation;
+  double* S = (double*)c->Lbuf.p;
+  double* Q = (double*)c->Linv.p;
+  double* cs = (double*)c->Gbuf.p;
+  double* norms = cs + 2 * max(ne, 2);
+  int* counts = (int*)c->counts.p + 14;
+  k_jac_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
+      (const double*)c->Mbuf.p, n, S, Q);
+  c->launches += 1;
+  int sweeps = 0;
+  for (; sweeps < 60 && ne >= 2; ++sweeps) {
+    double hn[2] = {0.0, 0.0};
+    k_jac_norms<<<1, 1024, 0, c->stream>>>(S, n, norms);
+    cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+    if (!(hn[0] > 1e-30 * hn[1])) break;
+    for (int r = 0; r < ne - 1; ++r) {
+      k_jac_rows<<<ne / 2, 128, 0, c->stream>>>(S, n, ne, r, cs);
+      k_jac_cols<<<ne / 2, 128, 0, c->stream>>>(S, Q, n, ne, r, cs);
+    }
+    c->launches += 2 * (ne - 1);
+  }
+  cudaMemsetAsync(counts, 0, 2 * sizeof(int), c->stream);
+  k_jac_invdiag<<<1, 256, 0, c->stream>>>(S, n, (double*)c->Abuf.p, counts);
+  c->launches += 1;
+  int hc[2] = {0, 0};
+  cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  c->stats.ace_eigen_sweeps = sweeps;
+  c->stats.ace_negative_eigenvalues = hc[0];
+  c->stats.ace_dropped_eigenvalues = hc[1];
+  c->ace_eigen = true;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out) {
   const int n = c->n_orb;
   const TileGeom G = tile_geom(c);
@@ -746,12 +935,22 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
   cudaEventRecord(c->ev[13], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * nv + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p, 1, nv);
-  // H = L^-T (L^-1 G)
+  // H = (-Mbar)^-1 G = L^-T (L^-1 G), or Q |Lambda|^-1 Q^T G in the eigen form
   dim3 gb((nv + 15) / 16, (n + 15) / 16), tb(16, 16);
-  k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Gbuf.p, n,
-                                         nv, (double*)c->Hbuf2.p);
-  k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Hbuf2.p, n,
-                                         nv, (double*)c->Hbuf.p);
+  if (c->ace_eigen) {
+    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Gbuf.p,
+                                           n, nv, (double*)c->Hbuf2.p);
+    k_scale_rows<<<(unsigned)(((size_t)n * nv + 255) / 256), 256, 0, c->stream>>>(
+        (double*)c->Hbuf2.p, (const double*)c->Abuf.p, n, nv);
+    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Hbuf2.p,
+                                           n, nv, (double*)c->Hbuf.p);
+    c->launches += 1;
+  } else {
+    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Gbuf.p,
+                                           n, nv, (double*)c->Hbuf2.p);
+    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Hbuf2.p,
+                                           n, nv, (double*)c->Hbuf.p);
+  }
   // out[v] = -sum_j W_j H[j][v]
   cudaEventRecord(c->ev[14], c->stream);
   launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Hbuf.p, nv, 1, nv, -1.0, out);

@@ -160,6 +160,7 @@ void sea_default_params(sea_params* p) {
   p->precision = 0;
   p->warm_start = 0;
   p->timeout_ms = 0.0;
+  p->ace_decomp = 0;
 }
 
 sea_status sea_create(const double cell[3], const int grid[3], const sea_params* p,
@@ -176,7 +177,7 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
   if (!(prm.eps >= 0.0 && prm.eps < 1.0) || !(prm.delta >= 0.0) || !(prm.cg_tol > 0.0) ||
       prm.cg_max_iter < 1 || prm.lmax < 0 || prm.lmax > SEA_LMAX || prm.fd_order != 12 ||
       prm.self_scale != 2.0 || (prm.precision != 0 && prm.precision != 1) || prm.warm_start != 0 ||
-      (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1))
+      (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1) || prm.ace_decomp < 0 || prm.ace_decomp > 2)
     return SEA_ERR_ARG;
   sea_ctx* c = new (std::nothrow) sea_ctx();
   if (!c) return SEA_ERR_OOM;
@@ -340,20 +341,32 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   return SEA_OK;
 }
 
-sea_status sea_build_ace(sea_ctx* c) {
-  if (!c) return SEA_ERR_ARG;
-  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
-  if (!c->have_vxx) return sea_fail(c, SEA_ERR_STATE, "sea_apply_vxx first");
+static sea_status build_ace_common(sea_ctx* c) {
   c->have_ace = false;
+  c->ace_eigen = false;
+  c->stats.ace_eigen = 0;
+  c->stats.ace_eigen_sweeps = 0;
+  c->stats.ace_negative_eigenvalues = 0;
+  c->stats.ace_dropped_eigenvalues = 0;
   SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
   SEA_CK(cudaEventRecord(c->ev[5], c->stream), "event");
   cudaError_t e = sea::launch_ace_build(c);
   if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE workspace");
   SEA_CK(e, "ace build");
-  SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
   unsigned st = 0;
   SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
          "status");
+  SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
+  const bool not_pd = (st & SEA_FLAG_NOT_PD) != 0;
+  if ((not_pd && c->prm.ace_decomp == 0) || c->prm.ace_decomp == 2) {
+    e = sea::launch_ace_eigen(c);
+    if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE eigen workspace");
+    SEA_CK(e, "ace eigen form");
+    c->stats.ace_eigen = 1;
+  } else if (not_pd) {
+    return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is not positive definite");
+  }
+  SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
   SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
   float t = 0;
   cudaEventElapsedTime(&t, c->ev[5], c->ev[6]);
@@ -361,9 +374,32 @@ sea_status sea_build_ace(sea_ctx* c) {
   cudaEventElapsedTime(&t, c->ev[10], c->ev[11]);
   c->stats.ms_gram_build = t;
   c->stats.ace_support_points = (long long)c->tile_inc * 128;
-  if (st & SEA_FLAG_NOT_PD) return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is not positive definite");
+  if (c->ace_eigen && c->stats.ace_dropped_eigenvalues == c->n_orb)
+    return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is zero");
   c->have_ace = true;
   return SEA_OK;
+}
+
+sea_status sea_build_ace(sea_ctx* c) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
+  if (!c->have_vxx) return sea_fail(c, SEA_ERR_STATE, "sea_apply_vxx first");
+  c->w_dense = false;
+  return build_ace_common(c);
+}
+
+sea_status sea_build_ace_from(sea_ctx* c, const double* W, int on_device) {
+  if (!c) return SEA_ERR_ARG;
+  if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
+  if (!c->have_phi) return sea_fail(c, SEA_ERR_STATE, "sea_set_orbitals first");
+  if (!W) return sea_fail(c, SEA_ERR_ARG, "W is NULL");
+  const size_t bytes = (size_t)c->n_orb * c->ng * sizeof(double);
+  SEA_CK(cudaMemcpyAsync(c->vxx_dev.p, W, bytes,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+         "copy W");
+  c->have_vxx = false;  // the context's W is no longer an apply_vxx result
+  c->w_dense = true;
+  return build_ace_common(c);
 }
 
 sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, int on_device) {
@@ -410,6 +446,7 @@ sea_status sea_get_ace_vectors(sea_ctx* c, double* xi, int on_device) {
   if (!c) return SEA_ERR_ARG;
   if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned");
   if (!c->have_ace) return sea_fail(c, SEA_ERR_STATE, "sea_build_ace first");
+  if (c->ace_eigen) return sea_fail(c, SEA_ERR_STATE, "the eigen form's ACE vectors may be complex");
   if (!xi) return sea_fail(c, SEA_ERR_ARG, "xi is NULL");
   const size_t bytes = (size_t)c->n_orb * c->ng * sizeof(double);
   double* dst = xi;

@@ -164,6 +164,7 @@ struct sea_ctx {
 
   int n_orb = 0;
   bool have_phi = false, have_vxx = false, have_ace = false, apply_timed = false;
+  bool ace_eigen = false, w_dense = false;
 
   // plan sizes (host copies)
   int P = 0, Pproto = 0, E = 0;
@@ -215,6 +216,7 @@ cudaError_t launch_cg(sea_ctx* c);
 cudaError_t launch_entries(sea_ctx* c);
 cudaError_t launch_accumulate(sea_ctx* c, double* out);
 cudaError_t launch_ace_build(sea_ctx* c);
+cudaError_t launch_ace_eigen(sea_ctx* c);
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int n_vec, double* out);
 cudaError_t launch_ace_vectors(sea_ctx* c, double* xi);
 cudaError_t upload_harmonics_pair();

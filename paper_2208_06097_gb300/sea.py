@@ -23,7 +23,7 @@ STATUS = {0: "SEA_OK", 1: "SEA_ERR_ARG", 2: "SEA_ERR_STATE", 3: "SEA_ERR_CUDA",
           7: "SEA_ERR_TIMEOUT", 8: "SEA_ERR_INPUT", 9: "SEA_ERR_LIMIT"}
 
 EXPORTS = ["sea_default_params", "sea_create", "sea_set_orbitals", "sea_apply_vxx",
-           "sea_build_ace", "sea_apply_ace", "sea_get_ace_matrices", "sea_get_ace_vectors",
+           "sea_build_ace", "sea_build_ace_from", "sea_apply_ace", "sea_get_ace_matrices", "sea_get_ace_vectors",
            "sea_get_plan", "sea_get_stats", "sea_last_error", "sea_destroy",
            "sea_poisson_batch", "sea_poisson_batch_noalloc"]
 
@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("cg_max_iter", ctypes.c_int), ("lmax", ctypes.c_int),
                 ("fd_order", ctypes.c_int), ("self_scale", ctypes.c_double),
                 ("precision", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("timeout_ms", ctypes.c_double)]
+                ("timeout_ms", ctypes.c_double), ("ace_decomp", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -54,7 +54,9 @@ class Stats(ctypes.Structure):
                 ("ms_ace_build", ctypes.c_double), ("ms_ace_apply", ctypes.c_double),
                 ("ace_support_points", ctypes.c_longlong), ("n_launches", ctypes.c_longlong),
                 ("ms_gram_build", ctypes.c_double), ("ms_gram_apply", ctypes.c_double),
-                ("ms_expand_apply", ctypes.c_double)]
+                ("ms_expand_apply", ctypes.c_double), ("ace_eigen", ctypes.c_int),
+                ("ace_eigen_sweeps", ctypes.c_int), ("ace_negative_eigenvalues", ctypes.c_int),
+                ("ace_dropped_eigenvalues", ctypes.c_int)]
 
 
 _LIB = None
@@ -75,6 +77,7 @@ def lib() -> ctypes.CDLL:
         L.sea_set_orbitals.argtypes = [_p, _p, _i, _i]
         L.sea_apply_vxx.argtypes = [_p, _p, _i, _p]
         L.sea_build_ace.argtypes = [_p]
+        L.sea_build_ace_from.argtypes = [_p, _p, _i]
         L.sea_apply_ace.argtypes = [_p, _p, _i, _p, _i]
         L.sea_get_ace_matrices.argtypes = [_p, _p, _p, _i]
         L.sea_get_ace_vectors.argtypes = [_p, _p, _i]
@@ -178,6 +181,11 @@ class Context:
 
     def build_ace(self):
         self._check(lib().sea_build_ace(self._h), "build_ace")
+
+    def build_ace_from(self, W):
+        """ACE from a caller-supplied W = V_xx Phi (treated as dense)."""
+        ptr, dev = _ptr(W)
+        self._check(lib().sea_build_ace_from(self._h, _p(ptr), dev), "build_ace_from")
 
     def apply_ace(self, psi, out):
         p1, d1 = _ptr(psi)

@@ -76,10 +76,11 @@ def test_cg_cap_reported_results_written(small):
 
 
 def test_zero_orbital_makes_mbar_singular(small):
+    # Cholesky only (ace_decomp = 1): the zero pivot is reported
     from paper_2208_06097_gb300 import sea
     phi = np.ascontiguousarray(small.phi.copy())
     phi[0] = 0.0
-    with _ctx(small) as ctx:
+    with _ctx(small, ace_decomp=1) as ctx:
         ctx.set_orbitals(phi)
         out = np.empty_like(phi)
         ctx.apply_vxx(out)

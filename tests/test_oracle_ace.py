@@ -62,3 +62,37 @@ def test_operator_is_symmetric_negative_semidefinite(ace_c1, h2o8, rng):
     Q, _ = np.linalg.qr(a["Xi"].T)
     z = psi[0] - Q @ (Q.T @ psi[0])
     assert np.abs(ace.apply_ace(a["Xi"], z[None], h2o8.dV)).max() < 1e-10 * np.abs(Y).max()
+
+
+def test_eigen_form_equals_cholesky_form_when_pd(ace_c1, h2o8, rng):
+    F, W, a = ace_c1
+    e = ace.build_ace_eigen(F, W, h2o8.dV)
+    assert np.all(e["lam"] > 0) and e["zeta"].shape[0] == F.shape[0]
+    psi = rng.normal(size=(3, F.shape[1]))
+    np.testing.assert_allclose(ace.apply_ace_eigen(e["zeta"], psi, h2o8.dV),
+                               ace.apply_ace(a["Xi"], psi, h2o8.dV), rtol=0,
+                               atol=1e-9 * np.abs(ace.apply_ace(a["Xi"], psi, h2o8.dV)).max())
+
+
+def test_eigen_form_indefinite(h2o8, rng):
+    # W = -Phi G with G symmetric indefinite: -Mbar = G.  The Cholesky form
+    # fails; the eigen form gives a negative semidefinite operator whose action
+    # on the occupied orbitals is W Q sign(Lambda) Q^T.
+    F = h2o8.phi.reshape(h2o8.n_orb, -1)
+    n = F.shape[0]
+    B = rng.normal(size=(n, n))
+    G = 0.5 * (B + B.T)
+    W = -(G @ F)
+    with pytest.raises(ace.NotPositiveDefinite):
+        ace.build_ace(F, W, h2o8.dV)
+    e = ace.build_ace_eigen(F, W, h2o8.dV)
+    assert np.any(e["lam"] < 0)
+    np.testing.assert_allclose(np.sort(e["lam"]), np.sort(np.linalg.eigvalsh(G)), atol=1e-10)
+    Y = ace.apply_ace_eigen(e["zeta"], F, h2o8.dV)
+    Q, lam = e["Q"], e["lam"]
+    pred = (Q @ np.diag(np.sign(lam)) @ Q.T).T @ W  # rows: sum_i (Q sign Q^T)_{ij} W_i
+    np.testing.assert_allclose(Y, pred, rtol=0, atol=1e-9 * np.abs(W).max())
+    psi = rng.normal(size=(4, F.shape[1]))
+    Yp = ace.apply_ace_eigen(e["zeta"], psi, h2o8.dV)
+    Gm = psi @ Yp.T * h2o8.dV
+    assert np.all(np.linalg.eigvalsh(0.5 * (Gm + Gm.T)) <= 1e-10 * np.abs(Gm).max())
