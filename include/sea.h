@@ -108,6 +108,8 @@ typedef struct {
   int ace_eigen_sweeps;         /* Jacobi sweeps of that build                  */
   int ace_negative_eigenvalues; /* eigenvalues of -Mbar below zero              */
   int ace_dropped_eigenvalues;  /* eigenvalues treated as zero                  */
+  int batch_graph;  /* last sea_apply_vxx_batch led by this context: 0 direct
+                       launches, 1 graph captured, 2 graph replayed            */
 } sea_stats;
 
 typedef struct sea_ctx sea_ctx;
@@ -133,6 +135,19 @@ sea_status sea_set_orbitals(sea_ctx* ctx, const double* phi, int n_orb, int on_d
  * Returns SEA_ERR_CG_NOT_CONVERGED (results still written) if any pair's CG
  * reached cg_max_iter. */
 sea_status sea_apply_vxx(sea_ctx* ctx, double* vxx_phi, int on_device, double* exx);
+
+/* Batched form: apply V_xx for n independent configurations (each its own
+ * context, orbitals already set) in one pass -- all their pairs' Poisson
+ * problems in one persistent launch.  All contexts must use the same device
+ * and the same stream; vxx_phi[k] (host or device per on_device) receives
+ * configuration k's V_xx phi, exx[k] (may be NULL) its E_xx.  The phase
+ * after the plan (pair setup, CG, far field, accumulation) is captured in a
+ * CUDA graph on the first call and replayed while the plan's sizes and the
+ * buffers stay the same (not on the legacy NULL stream, which cannot be
+ * captured).  Per-context results and statistics as for sea_apply_vxx;
+ * returns SEA_ERR_CG_NOT_CONVERGED if any configuration hit the cap. */
+sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* const* vxx_phi,
+                               int on_device, double* exx);
 
 /* Build the ACE operator from the orbitals and the last sea_apply_vxx
  * result.  Returns SEA_ERR_STATE if no sea_apply_vxx result is current and

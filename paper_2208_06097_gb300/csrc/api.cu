@@ -610,7 +610,8 @@ const char* sea_last_error(const sea_ctx* c) {
 
 void sea_destroy(sea_ctx* c) {
   if (!c) return;
-  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
+  sea_batch_cache_free(c);
   SeaBuf* all[] = {&c->phi, &c->vxx_dev, &c->psi_dev, &c->out_dev, &c->rowsum, &c->colsum,
                    &c->marg, &c->box, &c->cand_flag, &c->cand_geom, &c->list_a, &c->list_b,
                    &c->cand_S, &c->counts, &c->pinfo, &c->pS, &c->psize, &c->voff, &c->order,
@@ -618,7 +619,7 @@ void sea_destroy(sea_ctx* c) {
                    &c->qbuf, &c->eptr, &c->eent, &c->ewin, &c->coff, &c->cbuf, &c->status,
                    &c->exx_dev, &c->queue, &c->tmask, &c->tptr_o, &c->tlist_o, &c->tslot_o,
                    &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf,
-                   &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2};
+                   &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2, &c->bdesc, &c->bitems};
   for (SeaBuf* b : all) release(*b);
   for (int k = 0; k < 16; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -207,98 +207,106 @@ struct CgArgs {
   int* queue;
 };
 
-__global__ void __launch_bounds__(256) k_cg(CgArgs A, StencilW W) {
+// One pair's FP64 CG (the whole CTA), results into A's per-pair arrays.
+__device__ __forceinline__ void cg_pair_fp64(const CgArgs& A, const StencilW& W, int pidx,
+                                             double (*red)[32]) {
+  const size_t ng = (size_t)A.nx * A.ny * A.nz;
+  const PairInfo P = A.pinfo[pidx];
+  const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2], n = P.n;
+  const long long off = A.voff[pidx];
+  double* x = A.x + off;
+  const double* b = A.b + off;
+  double* r = A.r + off;
+  double* pv = A.p + off;
+  double* q = A.q + off;
+
+  double rr = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const double bt = b[t];
+    x[t] = 0.0;
+    r[t] = bt;
+    pv[t] = bt;
+    rr = fma(bt, bt, rr);
+  }
+  rr = block_sum(rr, red[0]);
+  const double bnorm = sqrt(rr);
+  const double target =
+      A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
+  int it = 0;
+  bool done = sqrt(rr) <= target;
+  while (!done && it < A.max_iter) {
+    double pq = 0.0, pq2 = 0.0;
+    {
+      const int S = blockDim.x;
+      BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
+      BoxWalk w1(threadIdx.x + S, 2 * S, ex, ey);
+      for (; w1.t < n; w0.next(2 * S), w1.next(2 * S)) {
+        const double q0 = neg_lap(pv, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
+        const double q1 = neg_lap(pv, w1.t, w1.x, w1.y, w1.z, ex, ey, ez, W);
+        q[w0.t] = q0;
+        q[w1.t] = q1;
+        pq = fma(pv[w0.t], q0, pq);
+        pq2 = fma(pv[w1.t], q1, pq2);
+      }
+      if (w0.t < n) {
+        const double q0 = neg_lap(pv, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
+        q[w0.t] = q0;
+        pq = fma(pv[w0.t], q0, pq);
+      }
+    }
+    pq = block_sum(pq + pq2, red[1]);
+    const double alpha = rr / pq;
+    double rn = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const double pt = pv[t];
+      x[t] = fma(alpha, pt, x[t]);
+      const double rt = fma(-alpha, q[t], r[t]);
+      r[t] = rt;
+      rn = fma(rt, rt, rn);
+    }
+    rn = block_sum(rn, red[0]);
+    ++it;
+    if (sqrt(rn) <= target) {
+      rr = rn;
+      done = true;
+      break;
+    }
+    const double beta = rn / rr;
+    rr = rn;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) pv[t] = fma(beta, pv[t], r[t]);
+    __syncthreads();
+  }
+  // pair integral of Eq. exxGen_mlwf over Omega_ij (skipped for a bare
+  // batch of boxes, phi == nullptr)
+  const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
+  const double* fj = A.phi ? A.phi + (size_t)P.j * ng : nullptr;
+  double e = 0.0;
+  for (int t = threadIdx.x; fi && t < n; t += blockDim.x) {
+    const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
+    const size_t g = ((size_t)wrapi(P.lo[2] + zz, A.nz) * A.ny + wrapi(P.lo[1] + yy, A.ny)) * A.nx +
+                     wrapi(P.lo[0] + xx, A.nx);
+    e = fma(fi[g] * fj[g], x[t], e);
+  }
+  e = block_sum(e, red[1]);
+  if (threadIdx.x == 0) {
+    if (A.epair) A.epair[pidx] = e * A.dV;
+    A.iters[pidx] = done ? it : -it;
+    if (!done) atomicOr(A.status, SEA_FLAG_CG_CAP);
+  }
+}
+
+// 3 CTAs per SM: fewer pairs start at once and the longest-first queue
+// balances the tail (measured faster than the 4 CTAs/SM the compiler picks).
+__global__ void __launch_bounds__(256, 3) k_cg(CgArgs A, StencilW W) {
   __shared__ double red[2][32];
   __shared__ int s_item;
-  const size_t ng = (size_t)A.nx * A.ny * A.nz;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= A.P) break;
     const int pidx = A.order[item];
-    const PairInfo P = A.pinfo[pidx];
-    const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2], n = P.n;
-    const long long off = A.voff[pidx];
-    double* x = A.x + off;
-    const double* b = A.b + off;
-    double* r = A.r + off;
-    double* pv = A.p + off;
-    double* q = A.q + off;
-
-    double rr = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const double bt = b[t];
-      x[t] = 0.0;
-      r[t] = bt;
-      pv[t] = bt;
-      rr = fma(bt, bt, rr);
-    }
-    rr = block_sum(rr, red[0]);
-    const double bnorm = sqrt(rr);
-    const double target =
-        A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
-    int it = 0;
-    bool done = sqrt(rr) <= target;
-    while (!done && it < A.max_iter) {
-      double pq = 0.0, pq2 = 0.0;
-      {
-        const int S = blockDim.x;
-        BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
-        BoxWalk w1(threadIdx.x + S, 2 * S, ex, ey);
-        for (; w1.t < n; w0.next(2 * S), w1.next(2 * S)) {
-          const double q0 = neg_lap(pv, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
-          const double q1 = neg_lap(pv, w1.t, w1.x, w1.y, w1.z, ex, ey, ez, W);
-          q[w0.t] = q0;
-          q[w1.t] = q1;
-          pq = fma(pv[w0.t], q0, pq);
-          pq2 = fma(pv[w1.t], q1, pq2);
-        }
-        if (w0.t < n) {
-          const double q0 = neg_lap(pv, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
-          q[w0.t] = q0;
-          pq = fma(pv[w0.t], q0, pq);
-        }
-      }
-      pq = block_sum(pq + pq2, red[1]);
-      const double alpha = rr / pq;
-      double rn = 0.0;
-      for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const double pt = pv[t];
-        x[t] = fma(alpha, pt, x[t]);
-        const double rt = fma(-alpha, q[t], r[t]);
-        r[t] = rt;
-        rn = fma(rt, rt, rn);
-      }
-      rn = block_sum(rn, red[0]);
-      ++it;
-      if (sqrt(rn) <= target) {
-        rr = rn;
-        done = true;
-        break;
-      }
-      const double beta = rn / rr;
-      rr = rn;
-      for (int t = threadIdx.x; t < n; t += blockDim.x) pv[t] = fma(beta, pv[t], r[t]);
-      __syncthreads();
-    }
-    // pair integral of Eq. exxGen_mlwf over Omega_ij (skipped for a bare
-    // batch of boxes, phi == nullptr)
-    const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
-    const double* fj = A.phi ? A.phi + (size_t)P.j * ng : nullptr;
-    double e = 0.0;
-    for (int t = threadIdx.x; fi && t < n; t += blockDim.x) {
-      const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
-      const size_t g = ((size_t)wrapi(P.lo[2] + zz, A.nz) * A.ny + wrapi(P.lo[1] + yy, A.ny)) * A.nx +
-                       wrapi(P.lo[0] + xx, A.nx);
-      e = fma(fi[g] * fj[g], x[t], e);
-    }
-    e = block_sum(e, red[1]);
-    if (threadIdx.x == 0) {
-      if (A.epair) A.epair[pidx] = e * A.dV;
-      A.iters[pidx] = done ? it : -it;
-      if (!done) atomicOr(A.status, SEA_FLAG_CG_CAP);
-    }
+    cg_pair_fp64(A, W, pidx, red);
     __syncthreads();
   }
 }
@@ -379,130 +387,179 @@ struct CgMixedArgs {
   int* queue;
 };
 
+// One pair's mixed-precision solve (the whole CTA).
+__device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const StencilW& W,
+                                              const StencilWf& Wf, int pidx, double (*red)[32]) {
+  const size_t ng = (size_t)A.nx * A.ny * A.nz;
+  const int S = blockDim.x;
+  const PairInfo P = A.pinfo[pidx];
+  const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2], n = P.n;
+  const long long off = A.voff[pidx];
+  double* x = A.x + off;
+  const double* b = A.b + off;
+  double* r = A.r + off;
+  float* d = A.d + off;
+  float* rf = A.rf + off;
+  float* pf = A.pf + off;
+  float* qf = A.qf + off;
+
+  double bb = 0.0;
+  for (int t = threadIdx.x; t < n; t += S) {
+    const double bt = b[t];
+    x[t] = 0.0;
+    r[t] = bt;
+    bb = fma(bt, bt, bb);
+  }
+  bb = block_sum(bb, red[0]);
+  const double bnorm = sqrt(bb);
+  const double target =
+      A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
+  double rnorm = bnorm;
+  int inner_total = 0, outer = 0;
+  bool done = rnorm <= target, capped = false;
+  while (!done) {
+    if (outer >= SEA_MIXED_MAX_OUTER || inner_total >= A.max_iter) {
+      capped = true;
+      break;
+    }
+    // inner FP32 CG on A d = r / ||r||
+    const double inv = 1.0 / rnorm;
+    DotF rr0;
+    for (int t = threadIdx.x; t < n; t += S) {
+      const float v = (float)(r[t] * inv);
+      rf[t] = v;
+      pf[t] = v;
+      d[t] = 0.f;
+      rr0.add(v, v);
+    }
+    double rr = block_sum(rr0.value(), red[1]);
+    const double inner_target = (double)SEA_MIXED_INNER * sqrt(rr);
+    int k = 0;
+    while (sqrt(rr) > inner_target && inner_total < A.max_iter) {
+      DotF pq0, pq1;
+      {
+        BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
+        BoxWalk w1(threadIdx.x + S, 2 * S, ex, ey);
+        for (; w1.t < n; w0.next(2 * S), w1.next(2 * S)) {
+          const float q0 = neg_lap_f(pf, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wf);
+          const float q1 = neg_lap_f(pf, w1.t, w1.x, w1.y, w1.z, ex, ey, ez, Wf);
+          qf[w0.t] = q0;
+          qf[w1.t] = q1;
+          pq0.add(pf[w0.t], q0);
+          pq1.add(pf[w1.t], q1);
+        }
+        if (w0.t < n) {
+          const float q0 = neg_lap_f(pf, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wf);
+          qf[w0.t] = q0;
+          pq0.add(pf[w0.t], q0);
+        }
+      }
+      const double pq = block_sum(pq0.value() + pq1.value(), red[0]);
+      const float alpha = (float)(rr / pq);
+      DotF rn0;
+      for (int t = threadIdx.x; t < n; t += S) {
+        d[t] = fmaf(alpha, pf[t], d[t]);
+        const float rt = fmaf(-alpha, qf[t], rf[t]);
+        rf[t] = rt;
+        rn0.add(rt, rt);
+      }
+      const double rn = block_sum(rn0.value(), red[1]);
+      ++k;
+      ++inner_total;
+      const float beta = (float)(rn / rr);
+      rr = rn;
+      if (sqrt(rn) <= inner_target) break;
+      for (int t = threadIdx.x; t < n; t += S) pf[t] = fmaf(beta, pf[t], rf[t]);
+      __syncthreads();
+    }
+    // FP64 correction and true residual
+    for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+    __syncthreads();
+    double r2 = 0.0;
+    {
+      BoxWalk w0(threadIdx.x, S, ex, ey);
+      for (; w0.t < n; w0.next(S)) {
+        const double rt = b[w0.t] - neg_lap(x, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
+        r[w0.t] = rt;
+        r2 = fma(rt, rt, r2);
+      }
+    }
+    rnorm = sqrt(block_sum(r2, red[0]));
+    ++outer;
+    done = rnorm <= target;
+  }
+  // pair integral of Eq. exxGen_mlwf over Omega_ij
+  const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
+  const double* fj = A.phi ? A.phi + (size_t)P.j * ng : nullptr;
+  double e = 0.0;
+  for (int t = threadIdx.x; fi && t < n; t += S) {
+    const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
+    const size_t g = ((size_t)wrapi(P.lo[2] + zz, A.nz) * A.ny + wrapi(P.lo[1] + yy, A.ny)) * A.nx +
+                     wrapi(P.lo[0] + xx, A.nx);
+    e = fma(fi[g] * fj[g], x[t], e);
+  }
+  e = block_sum(e, red[1]);
+  if (threadIdx.x == 0) {
+    if (A.epair) A.epair[pidx] = e * A.dV;
+    A.iters[pidx] = capped ? -inner_total : inner_total;
+    if (A.outers) A.outers[pidx] = outer;
+    if (capped) atomicOr(A.status, SEA_FLAG_CG_CAP);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_cg_mixed(CgMixedArgs A, StencilW W, StencilWf Wf) {
   __shared__ double red[2][32];
   __shared__ int s_item;
-  const size_t ng = (size_t)A.nx * A.ny * A.nz;
-  const int S = blockDim.x;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= A.P) break;
     const int pidx = A.order[item];
-    const PairInfo P = A.pinfo[pidx];
-    const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2], n = P.n;
-    const long long off = A.voff[pidx];
-    double* x = A.x + off;
-    const double* b = A.b + off;
-    double* r = A.r + off;
-    float* d = A.d + off;
-    float* rf = A.rf + off;
-    float* pf = A.pf + off;
-    float* qf = A.qf + off;
+    cg_pair_mixed(A, W, Wf, pidx, red);
+    __syncthreads();
+  }
+}
 
-    double bb = 0.0;
-    for (int t = threadIdx.x; t < n; t += S) {
-      const double bt = b[t];
-      x[t] = 0.0;
-      r[t] = bt;
-      bb = fma(bt, bt, bb);
+// ---------------------------------------------------------------------------
+// Batched form: the pairs of several independent configurations in one
+// persistent launch.  items[k] = (configuration, rank): the pair of that
+// rank in the configuration's longest-first order; the item list deals the
+// ranks round-robin over the configurations, so the longest pairs of every
+// configuration start first.  Each configuration brings its own grid,
+// stencil weights and buffers.
+// ---------------------------------------------------------------------------
+struct BatchCg {
+  CgArgs a;
+  CgMixedArgs m;
+  StencilW W;
+  StencilWf Wf;
+  int mixed;
+};
+
+__global__ void __launch_bounds__(256) k_cg_batch(const BatchCg* __restrict__ descs,
+                                                  const int2* __restrict__ items, int total,
+                                                  int* __restrict__ queue) {
+  __shared__ double red[2][32];
+  __shared__ int s_item;
+  __shared__ BatchCg d;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    const int2 it = items[item];
+    {
+      const int* src = (const int*)(descs + it.x);
+      int* dst = (int*)&d;
+      for (int w = threadIdx.x; w < (int)(sizeof(BatchCg) / sizeof(int)); w += blockDim.x)
+        dst[w] = src[w];
     }
-    bb = block_sum(bb, red[0]);
-    const double bnorm = sqrt(bb);
-    const double target =
-        A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
-    double rnorm = bnorm;
-    int inner_total = 0, outer = 0;
-    bool done = rnorm <= target, capped = false;
-    while (!done) {
-      if (outer >= SEA_MIXED_MAX_OUTER || inner_total >= A.max_iter) {
-        capped = true;
-        break;
-      }
-      // inner FP32 CG on A d = r / ||r||
-      const double inv = 1.0 / rnorm;
-      DotF rr0;
-      for (int t = threadIdx.x; t < n; t += S) {
-        const float v = (float)(r[t] * inv);
-        rf[t] = v;
-        pf[t] = v;
-        d[t] = 0.f;
-        rr0.add(v, v);
-      }
-      double rr = block_sum(rr0.value(), red[1]);
-      const double inner_target = (double)SEA_MIXED_INNER * sqrt(rr);
-      int k = 0;
-      while (sqrt(rr) > inner_target && inner_total < A.max_iter) {
-        DotF pq0, pq1;
-        {
-          BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
-          BoxWalk w1(threadIdx.x + S, 2 * S, ex, ey);
-          for (; w1.t < n; w0.next(2 * S), w1.next(2 * S)) {
-            const float q0 = neg_lap_f(pf, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wf);
-            const float q1 = neg_lap_f(pf, w1.t, w1.x, w1.y, w1.z, ex, ey, ez, Wf);
-            qf[w0.t] = q0;
-            qf[w1.t] = q1;
-            pq0.add(pf[w0.t], q0);
-            pq1.add(pf[w1.t], q1);
-          }
-          if (w0.t < n) {
-            const float q0 = neg_lap_f(pf, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wf);
-            qf[w0.t] = q0;
-            pq0.add(pf[w0.t], q0);
-          }
-        }
-        const double pq = block_sum(pq0.value() + pq1.value(), red[0]);
-        const float alpha = (float)(rr / pq);
-        DotF rn0;
-        for (int t = threadIdx.x; t < n; t += S) {
-          d[t] = fmaf(alpha, pf[t], d[t]);
-          const float rt = fmaf(-alpha, qf[t], rf[t]);
-          rf[t] = rt;
-          rn0.add(rt, rt);
-        }
-        const double rn = block_sum(rn0.value(), red[1]);
-        ++k;
-        ++inner_total;
-        const float beta = (float)(rn / rr);
-        rr = rn;
-        if (sqrt(rn) <= inner_target) break;
-        for (int t = threadIdx.x; t < n; t += S) pf[t] = fmaf(beta, pf[t], rf[t]);
-        __syncthreads();
-      }
-      // FP64 correction and true residual
-      for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
-      __syncthreads();
-      double r2 = 0.0;
-      {
-        BoxWalk w0(threadIdx.x, S, ex, ey);
-        for (; w0.t < n; w0.next(S)) {
-          const double rt = b[w0.t] - neg_lap(x, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
-          r[w0.t] = rt;
-          r2 = fma(rt, rt, r2);
-        }
-      }
-      rnorm = sqrt(block_sum(r2, red[0]));
-      ++outer;
-      done = rnorm <= target;
-    }
-    // pair integral of Eq. exxGen_mlwf over Omega_ij
-    const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
-    const double* fj = A.phi ? A.phi + (size_t)P.j * ng : nullptr;
-    double e = 0.0;
-    for (int t = threadIdx.x; fi && t < n; t += S) {
-      const int xx = t % ex, yy = (t / ex) % ey, zz = t / (ex * ey);
-      const size_t g = ((size_t)wrapi(P.lo[2] + zz, A.nz) * A.ny + wrapi(P.lo[1] + yy, A.ny)) * A.nx +
-                       wrapi(P.lo[0] + xx, A.nx);
-      e = fma(fi[g] * fj[g], x[t], e);
-    }
-    e = block_sum(e, red[1]);
-    if (threadIdx.x == 0) {
-      if (A.epair) A.epair[pidx] = e * A.dV;
-      A.iters[pidx] = capped ? -inner_total : inner_total;
-      if (A.outers) A.outers[pidx] = outer;
-      if (capped) atomicOr(A.status, SEA_FLAG_CG_CAP);
-    }
+    __syncthreads();
+    if (d.mixed)
+      cg_pair_mixed(d.m, d.W, d.Wf, d.m.order[it.y], red);
+    else
+      cg_pair_fp64(d.a, d.W, d.a.order[it.y], red);
     __syncthreads();
   }
 }
@@ -539,51 +596,40 @@ static StencilWf make_weights_f(const StencilW& W) {
   return F;
 }
 
-cudaError_t launch_cg(sea_ctx* c) {
-  if (c->P == 0) return cudaSuccess;
-  int nsm = 0, occ = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  if (c->prm.precision == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_mixed, 256, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, 256, 0);
-  if (occ < 1) occ = 1;
-  const int grid = min(c->P, nsm * occ);
-  cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream);
-  const StencilW W = make_weights(c);
-  if (c->prm.precision == 1) {
-    CgMixedArgs A;
-    memset(&A, 0, sizeof(A));
-    A.phi = (const double*)c->phi.p;
-    A.nx = c->N[0];
-    A.ny = c->N[1];
-    A.nz = c->N[2];
-    A.pinfo = (const PairInfo*)c->pinfo.p;
-    A.voff = (const long long*)c->voff.p;
-    A.order = (const int*)c->order.p;
-    A.P = c->P;
-    A.dV = c->dV;
-    A.tol = c->prm.cg_tol;
-    A.tol_mode = c->prm.cg_tol_mode;
-    A.max_iter = c->prm.cg_max_iter;
-    A.x = (double*)c->vbuf.p;
-    A.b = (double*)c->bbuf.p;
-    A.r = (double*)c->rbuf.p;
-    // FP32 vectors: two per FP64-sized buffer
-    A.d = (float*)c->pbuf.p;
-    A.rf = A.d + c->U;
-    A.pf = (float*)c->qbuf.p;
-    A.qf = A.pf + c->U;
-    A.epair = (double*)c->epair.p;
-    A.iters = (int*)c->iters.p;
-    A.outers = nullptr;
-    A.status = (unsigned*)c->status.p;
-    A.queue = (int*)c->queue.p;
-    k_cg_mixed<<<grid, 256, 0, c->stream>>>(A, W, make_weights_f(W));
-    c->launches += 1;
-    return cudaGetLastError();
-  }
+static CgMixedArgs mixed_args(sea_ctx* c) {
+  CgMixedArgs A;
+  memset(&A, 0, sizeof(A));
+  A.phi = (const double*)c->phi.p;
+  A.nx = c->N[0];
+  A.ny = c->N[1];
+  A.nz = c->N[2];
+  A.pinfo = (const PairInfo*)c->pinfo.p;
+  A.voff = (const long long*)c->voff.p;
+  A.order = (const int*)c->order.p;
+  A.P = c->P;
+  A.dV = c->dV;
+  A.tol = c->prm.cg_tol;
+  A.tol_mode = c->prm.cg_tol_mode;
+  A.max_iter = c->prm.cg_max_iter;
+  A.x = (double*)c->vbuf.p;
+  A.b = (double*)c->bbuf.p;
+  A.r = (double*)c->rbuf.p;
+  // FP32 vectors: two per FP64-sized buffer
+  A.d = (float*)c->pbuf.p;
+  A.rf = A.d + c->U;
+  A.pf = (float*)c->qbuf.p;
+  A.qf = A.pf + c->U;
+  A.epair = (double*)c->epair.p;
+  A.iters = (int*)c->iters.p;
+  A.outers = nullptr;
+  A.status = (unsigned*)c->status.p;
+  A.queue = (int*)c->queue.p;
+  return A;
+}
+
+static CgArgs fp64_args(sea_ctx* c) {
   CgArgs A;
+  memset(&A, 0, sizeof(A));
   A.phi = (const double*)c->phi.p;
   A.nx = c->N[0];
   A.ny = c->N[1];
@@ -605,8 +651,53 @@ cudaError_t launch_cg(sea_ctx* c) {
   A.iters = (int*)c->iters.p;
   A.status = (unsigned*)c->status.p;
   A.queue = (int*)c->queue.p;
-  k_cg<<<grid, 256, 0, c->stream>>>(A, W);
+  return A;
+}
+
+cudaError_t launch_cg(sea_ctx* c) {
+  if (c->P == 0) return cudaSuccess;
+  int nsm = 0, occ = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (c->prm.precision == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_mixed, 256, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, 256, 0);
+  if (occ < 1) occ = 1;
+  const int grid = min(c->P, nsm * occ);
+  cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream);
+  const StencilW W = make_weights(c);
+  if (c->prm.precision == 1)
+    k_cg_mixed<<<grid, 256, 0, c->stream>>>(mixed_args(c), W, make_weights_f(W));
+  else
+    k_cg<<<grid, 256, 0, c->stream>>>(fp64_args(c), W);
   c->launches += 1;
+  return cudaGetLastError();
+}
+
+// Descriptor of one configuration for k_cg_batch (host side).
+void make_batch_desc(sea_ctx* c, void* out) {
+  BatchCg d;
+  memset(&d, 0, sizeof(d));
+  d.a = fp64_args(c);
+  d.m = mixed_args(c);
+  d.W = make_weights(c);
+  d.Wf = make_weights_f(d.W);
+  d.mixed = c->prm.precision == 1;
+  memcpy(out, &d, sizeof(d));
+}
+
+size_t batch_desc_bytes() { return sizeof(BatchCg); }
+
+cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, const int2* items,
+                            int total, int* queue) {
+  if (total == 0) return cudaSuccess;
+  int nsm = 0, occ = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, 256, 0);
+  if (occ < 1) occ = 1;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_cg_batch<<<min(total, nsm * occ), 256, 0, st>>>((const BatchCg*)descs, items, total, queue);
   return cudaGetLastError();
 }
 

@@ -165,6 +165,8 @@ struct sea_ctx {
   int n_orb = 0;
   bool have_phi = false, have_vxx = false, have_ace = false, apply_timed = false;
   bool ace_eigen = false, w_dense = false;
+  void* batch_cache = nullptr;  // CUDA graph of sea_apply_vxx_batch (batch.cu)
+  SeaBuf bdesc, bitems;
 
   // plan sizes (host copies)
   int P = 0, Pproto = 0, E = 0;
@@ -191,6 +193,7 @@ struct sea_ctx {
 
 // Host-side helpers implemented in api.cu.
 sea_status sea_fail(sea_ctx* c, sea_status s, const char* msg);
+void sea_batch_cache_free(sea_ctx* c);
 bool sea_ensure(sea_ctx* c, SeaBuf& b, size_t bytes);
 
 // Pair record (device), one per selected pair, in (i, j) order.
@@ -213,6 +216,10 @@ cudaError_t launch_plan_boxes(sea_ctx* c);
 cudaError_t launch_plan_pairs(sea_ctx* c);
 cudaError_t launch_pair_setup(sea_ctx* c);
 cudaError_t launch_cg(sea_ctx* c);
+void make_batch_desc(sea_ctx* c, void* out);
+size_t batch_desc_bytes();
+cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, const int2* items,
+                            int total, int* queue);
 cudaError_t launch_entries(sea_ctx* c);
 cudaError_t launch_accumulate(sea_ctx* c, double* out);
 cudaError_t launch_ace_build(sea_ctx* c);

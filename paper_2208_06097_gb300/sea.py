@@ -25,7 +25,7 @@ STATUS = {0: "SEA_OK", 1: "SEA_ERR_ARG", 2: "SEA_ERR_STATE", 3: "SEA_ERR_CUDA",
 EXPORTS = ["sea_default_params", "sea_create", "sea_set_orbitals", "sea_apply_vxx",
            "sea_build_ace", "sea_build_ace_from", "sea_apply_ace", "sea_get_ace_matrices", "sea_get_ace_vectors",
            "sea_get_plan", "sea_get_stats", "sea_last_error", "sea_destroy",
-           "sea_poisson_batch", "sea_poisson_batch_noalloc"]
+           "sea_poisson_batch", "sea_poisson_batch_noalloc", "sea_apply_vxx_batch"]
 
 
 class SeaError(RuntimeError):
@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
                 ("ms_gram_build", ctypes.c_double), ("ms_gram_apply", ctypes.c_double),
                 ("ms_expand_apply", ctypes.c_double), ("ace_eigen", ctypes.c_int),
                 ("ace_eigen_sweeps", ctypes.c_int), ("ace_negative_eigenvalues", ctypes.c_int),
-                ("ace_dropped_eigenvalues", ctypes.c_int)]
+                ("ace_dropped_eigenvalues", ctypes.c_int), ("batch_graph", ctypes.c_int)]
 
 
 _LIB = None
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
         L.sea_poisson_batch.argtypes = [_p, _i, _p, _p, _p, ctypes.c_double, _i, _i, _p, _p]
         L.sea_poisson_batch_noalloc.argtypes = [_p, _i, _p, _p, _p, ctypes.c_double, _i, _i,
                                                 _p, _p]
+        L.sea_apply_vxx_batch.argtypes = [_p, _i, _p, _i, _p]
         L.sea_destroy.argtypes = [_p]
         L.sea_destroy.restype = None
         for f in EXPORTS:
@@ -139,6 +140,24 @@ def poisson_batch(h, ext, rhs, x, tol=1e-8, tol_mode=0, max_iter=5000, stream=No
     if rc not in (SEA_OK, 5):
         raise SeaError(rc, "poisson_batch")
     return it, rc
+
+
+def apply_vxx_batch(ctxs, outs):
+    """Batched V_xx application over several contexts (same device and
+    stream); outs: matching torch CUDA tensors or numpy arrays.  Returns the
+    list of E_xx values."""
+    n = len(ctxs)
+    hs = (_p * n)(*[c.handle for c in ctxs])
+    ptrs = [_ptr(o) for o in outs]
+    if len({d for _, d in ptrs}) != 1:
+        raise ValueError("outputs must be all host or all device")
+    op = (_p * n)(*[p for p, _ in ptrs])
+    ex = (ctypes.c_double * n)()
+    rc = lib().sea_apply_vxx_batch(hs, n, op, ptrs[0][1], ex)
+    if rc != SEA_OK:
+        msgs = "; ".join(lib().sea_last_error(c.handle).decode() for c in ctxs)
+        raise SeaError(rc, f"apply_vxx_batch: {msgs}")
+    return list(ex)
 
 
 class Context:
