@@ -52,6 +52,13 @@ CG_FLOPS_PER_UNKNOWN_ITER = 65
 # FP64 peak from the part's unit counts and clock: 152 SMs x 2 FP64 FMA/clk x
 # 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 figure).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 issue peak: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per
+# lane and clock (an FMA counts as one operation here).
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# FP32 operations per FP64-accurate product in the mixed-form contractions
+# (split operands, exact hi*hi by an FMA residual, two cross terms, two-sum
+# into a compensated accumulator): 2 multiplies, 2 FMAs, 9 adds.
+EFT_OPS_PER_PRODUCT = 13
 
 
 def _dist():
@@ -215,14 +222,25 @@ def run_ours(args, ws, rank, local):
     y_pin = torch.empty(psi_h.shape, dtype=torch.float64).pin_memory().numpy()
     e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
 
+    e2e_calls = {"set_orbitals": 0.0, "apply_vxx": 0.0, "build_ace": 0.0, "apply_ace": 0.0}
+
     def step_host():
+        t = [time.perf_counter()]
         ctx.set_orbitals(phi_pin)
+        t.append(time.perf_counter())
         ctx.apply_vxx(out_pin)
+        t.append(time.perf_counter())
         ctx.build_ace()
+        t.append(time.perf_counter())
         ctx.apply_ace(psi_pin, y_pin)
+        t.append(time.perf_counter())
+        for k, key in enumerate(e2e_calls):
+            e2e_calls[key] += (t[k + 1] - t[k]) * 1e3
 
     if e2e_steps:
         step_host()
+        for key in e2e_calls:
+            e2e_calls[key] = 0.0
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -243,17 +261,29 @@ def run_ours(args, ws, rank, local):
     st = R["stats"]
     sm = R["stage_ms"]
     n = s.n_orb
-    # candidate kernels: (name, ms per launch, launches per step, flops per launch, peak, bound)
+    # candidate kernels: (name, ms per launch, launches per step, work per
+    # launch, peak, bound, note); work in the peak's unit (flop or FP32 op)
     cand = []
+    gram_ms = (sm["gram_build"] + sm["gram_apply"]) / 2
     if chosen == "plain":
+        note = ("FP64 ALU from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; "
+                "algorithmic flops: CG 65/unknown/iteration, ACE 2 x rows x nonzeros of W")
         cand.append(("k_cg (persistent FP64 CG)", sm["cg"], 1,
-                     CG_FLOPS_PER_UNKNOWN_ITER * R["cg_unknown_iters"], FP64_PEAK_TFLOPS, "alu"))
-    cand.append(("k_gram_partial (FP64 M = Phi^T W and W^T psi over W's tiles)",
-                 (sm["gram_build"] + sm["gram_apply"]) / 2, 2,
-                 2.0 * n * nnz_w, FP64_PEAK_TFLOPS, "alu"))
-    cand.append(("k_tile_expand (FP64 W H over W's tiles)", sm["expand_apply"], 1,
-                 2.0 * N_TRIAL * nnz_w, FP64_PEAK_TFLOPS, "alu"))
-    name, kms, nl, flops, peak, bound = max(cand, key=lambda c: c[1] * c[2])
+                     CG_FLOPS_PER_UNKNOWN_ITER * R["cg_unknown_iters"], FP64_PEAK_TFLOPS, "alu",
+                     note))
+        cand.append(("k_gram_partial (FP64 M = Phi^T W and W^T psi over W's tiles)", gram_ms, 2,
+                     2.0 * n * nnz_w, FP64_PEAK_TFLOPS, "alu", note))
+        cand.append(("k_tile_expand (FP64 W H over W's tiles)", sm["expand_apply"], 1,
+                     2.0 * N_TRIAL * nnz_w, FP64_PEAK_TFLOPS, "alu", note))
+    else:
+        note = ("FP32 issue from unit counts: 152 SMs x 128 lanes x 2.07 GHz = 40.3 T op/s; "
+                "work = rows x nonzeros of W products x 13 FP32 operations per FP64-accurate "
+                "product (error-free transformation)")
+        cand.append(("k_gram_pipe_x (mixed M = Phi^T W and W^T psi, FP32 error-free products)",
+                     gram_ms, 2, EFT_OPS_PER_PRODUCT * n * nnz_w, FP32_PEAK_TOPS, "alu", note))
+        cand.append(("k_tile_expand_x (mixed W H, FP32 error-free products)", sm["expand_apply"],
+                     1, EFT_OPS_PER_PRODUCT * N_TRIAL * nnz_w, FP32_PEAK_TOPS, "alu", note))
+    name, kms, nl, flops, peak, bound, peak_note = max(cand, key=lambda c: c[1] * c[2])
     achieved = flops / (kms / 1e3) / 1e12 if kms > 0 else 0.0
     cpu = cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline) else None
     batched = run_batched(args, sea, torch, dev) if (ws == 1 and not args.no_batched) else None
@@ -291,6 +321,7 @@ def run_ours(args, ws, rank, local):
             "unit": UNIT,
             "h2d_bytes_per_step": int(s.phi.nbytes + psi_h.nbytes),
             "d2h_bytes_per_step": int(s.phi.nbytes + psi_h.nbytes + 8),
+            "call_ms": {k: v / e2e_steps for k, v in e2e_calls.items()} if e2e_steps else None,
         },
         "gpu_launches": int(R["launches"]),
         "roofline": {
@@ -301,8 +332,7 @@ def run_ours(args, ws, rank, local):
             "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": None,
-            "peak_note": "FP64 ALU from unit counts: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; "
-                         "algorithmic flops: CG 65/unknown/iteration, ACE 2 x rows x nonzeros of W",
+            "peak_note": peak_note,
         },
         "clocks": R["clocks"],
     }

@@ -126,12 +126,16 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
 
 /* Copy n_orb orbitals ([n_orb][nz][ny][nx], host or device) into the
  * context.  Any earlier exchange/ACE result is invalidated.  Returns
- * SEA_ERR_INPUT if a value is not finite. */
+ * SEA_ERR_INPUT if a value is not finite.  Host orbitals are copied in
+ * orbital ranges, each range checked while the next one is in flight. */
 sea_status sea_set_orbitals(sea_ctx* ctx, const double* phi, int n_orb, int on_device);
 
 /* Apply V_xx to every orbital: vxx_phi[n_orb][nz][ny][nx] (host or device,
  * caller-owned) receives V_xx phi_i = -D^i; *exx (may be NULL) receives E_xx.
- * Synchronizes the context stream once to read E_xx and the status word.
+ * Synchronizes the context stream after the plan (sizes) and at the end (E_xx
+ * and the status word).  With a host vxx_phi (page-locked for full speed)
+ * the last stage runs by orbital ranges and each range's copy out overlaps
+ * the kernels of the next.
  * Returns SEA_ERR_CG_NOT_CONVERGED (results still written) if any pair's CG
  * reached cg_max_iter. */
 sea_status sea_apply_vxx(sea_ctx* ctx, double* vxx_phi, int on_device, double* exx);
@@ -162,7 +166,13 @@ sea_status sea_build_ace(sea_ctx* ctx);
 sea_status sea_build_ace_from(sea_ctx* ctx, const double* W, int on_device);
 
 /* out[n_vec][nz][ny][nx] = V^ACE psi for psi[n_vec][nz][ny][nx] (host or
- * device, same flag for both).  Requires a successful sea_build_ace. */
+ * device, same flag for both).  Requires a successful sea_build_ace.
+ * With host buffers (page-locked for full speed) the call works through
+ * chunks of at least 32 vectors, overlapping the copy in of one chunk, the
+ * kernels of the previous one and the copy out of the one before on
+ * separate streams; it returns when out is written.  Stats of such a call:
+ * ms_ace_apply spans the whole pipeline (copies included), ms_gram_apply
+ * and ms_expand_apply the last chunk's kernels. */
 sea_status sea_apply_ace(sea_ctx* ctx, const double* psi, int n_vec, double* out,
                          int on_device);
 

@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(256)
 // CTA per (orbital, slab of SLAB z-planes).
 #define SEA_SLAB 4
 __global__ void __launch_bounds__(256)
-    k_accumulate(int nx, int ny, int nz, const int* __restrict__ eptr,
+    k_accumulate(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
                  const Entry* __restrict__ ent, const long long* __restrict__ coff,
                  const double* __restrict__ cbuf, double* __restrict__ out) {
-  const int o = blockIdx.x;
+  const int o = o_begin + blockIdx.x;
   const int z0 = blockIdx.y * SEA_SLAB, z1 = min(nz, z0 + SEA_SLAB);
   const size_t plane = (size_t)nx * ny;
   double* Do = out + (size_t)o * plane * nz;
@@ -273,26 +273,43 @@ cudaError_t launch_entries(sea_ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate(sea_ctx* c, double* out) {
-  if (c->E > 0) {
+// Window contributions and their accumulation for orbitals [o_begin, o_end),
+// whose entries are [e_begin, e_end) (entries are grouped by orbital).
+cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
+                                    int e_end) {
+  if (e_end > e_begin) {
     const int chunks = (int)((c->max_window + SEA_CHUNK - 1) / SEA_CHUNK);
-    for (int e0 = 0; e0 < c->E; e0 += 65535) {
-      const int ne = std::min(65535, c->E - e0);
+    for (int e0 = e_begin; e0 < e_end; e0 += 65535) {
+      const int ne = std::min(65535, e_end - e0);
       k_contrib<<<dim3(chunks, ne), 256, 0, c->stream>>>(
           (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const Entry*)c->ewin.p + e0,
           (const long long*)c->coff.p + e0, (const PairInfo*)c->pinfo.p,
           (const long long*)c->voff.p, (const double*)c->vbuf.p, (const double*)c->Q.p, c->h[0],
           c->h[1], c->h[2], (double*)c->cbuf.p);
+      c->launches += 1;
     }
   }
-  k_accumulate<<<dim3(c->n_orb, (c->N[2] + SEA_SLAB - 1) / SEA_SLAB), 256, 0, c->stream>>>(
-      c->N[0], c->N[1], c->N[2], (const int*)c->eptr.p, (const Entry*)c->ewin.p,
-      (const long long*)c->coff.p, (const double*)c->cbuf.p, out);
+  if (o_end > o_begin) {
+    k_accumulate<<<dim3(o_end - o_begin, (c->N[2] + SEA_SLAB - 1) / SEA_SLAB), 256, 0, c->stream>>>(
+        c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p, (const Entry*)c->ewin.p,
+        (const long long*)c->coff.p, (const double*)c->cbuf.p, out);
+    c->launches += 1;
+  }
+  return cudaGetLastError();
+}
+
+// E_xx and the CG statistics (after every pair energy is final).
+cudaError_t launch_exx(sea_ctx* c) {
   k_exx<<<1, 32, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const int*)c->counts.p + 1,
                                  (const double*)c->epair.p, (const int*)c->iters.p,
                                  (double*)c->exx_dev.p);
-  c->launches += 2 + (c->E > 0 ? (c->E + 65534) / 65535 : 0);
+  c->launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(sea_ctx* c, double* out) {
+  cudaError_t e = launch_accumulate_range(c, out, 0, c->n_orb, 0, c->E);
+  return e != cudaSuccess ? e : launch_exx(c);
 }
 
 cudaError_t upload_harmonics_accum() { return upload_harmonics_here(); }

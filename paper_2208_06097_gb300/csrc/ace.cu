@@ -360,6 +360,196 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined mixed-form contractions (used when nx is even, so every tile row
+// of 8 doubles starts on a 16-byte boundary).  Persistent CTAs, one per SM,
+// take tiles from a queue; the FP64 data of the next chunk are copied into
+// shared memory with cp.async while the current chunk is computed from its
+// FP32 hi/lo copy.  Every cp.async source is in bounds: out-of-range rows and
+// points copy 0 bytes from a valid address and are zero-filled.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+#define PGA 64           // rows of A per chunk
+#define PGJ 32           // W rows per tile held in shared memory
+#define PROW (TP + 1)    // padded float2 row (odd in 8-byte units: conflict-free)
+struct PipeSmem {
+  double A64[PGA * TP];   // staged FP64 chunk of A (16-byte chunks)
+  double W64[PGJ * TP];   // staged FP64 W rows of the tile
+  float2 Asp[PGA * PROW];
+  float2 Wsp[PGJ * PROW];
+};
+#define PIPE_SMEM (sizeof(PipeSmem))
+
+// Issue the cp.async copies of rows [a0, a0+PGA) of A at the tile's points.
+__device__ __forceinline__ void stage_rows(double* dst, const double* __restrict__ A, int a0, int m,
+                                           const long long* addr, size_t ng, int nrows) {
+  // 16-byte pieces: row r, points 2q and 2q+1 (same x-row of the tile)
+  for (int idx = threadIdx.x; idx < nrows * (TP / 2); idx += blockDim.x) {
+    const int r = idx / (TP / 2), q = idx % (TP / 2);
+    const long long g = addr[2 * q];
+    const bool ok = (a0 + r < m) && g >= 0;
+    const double* src = ok ? A + (size_t)(a0 + r) * ng + g : A;
+    cp_async16(dst + r * TP + 2 * q, src, ok);
+  }
+}
+
+#define PIPE_THREADS 512
+__device__ __forceinline__ void stage_wrows(double* dst, const double* __restrict__ W,
+                                            const int* wrow, const long long* addr, size_t ng,
+                                            int nrows) {
+  for (int idx = threadIdx.x; idx < nrows * (TP / 2); idx += blockDim.x) {
+    const int r = idx / (TP / 2), q = idx % (TP / 2);
+    const long long g = addr[2 * q];
+    cp_async16(dst + r * TP + 2 * q, g >= 0 ? W + (size_t)wrow[r] * ng + g : W, g >= 0);
+  }
+}
+
+// Split W rows [jb, jb + nj) of tile T's list straight from global memory
+// (used only for tiles whose list is longer than PGJ).
+__device__ __forceinline__ void load_wrows_direct(float2* dst, const double* __restrict__ W,
+                                                  const TileGeom& G, int T, size_t ng,
+                                                  const int* __restrict__ tlist, int j, int nj) {
+  for (int idx = threadIdx.x; idx < nj * TP; idx += blockDim.x) {
+    const int r = idx / TP, pt = idx % TP;
+    const long long g = tile_point(G, T, pt);
+    dst[r * PROW + pt] = split64(g >= 0 ? W[(size_t)tlist[j + r] * ng + g] : 0.0);
+  }
+}
+
+// One warp-uniform pass over units (W row jl < nj, half of the A rows) of
+// the current chunk; lane = A row.
+__device__ __forceinline__ void gram_units(const float2* __restrict__ Asp,
+                                           const float2* __restrict__ Wsp,
+                                           const int* __restrict__ tsub, int jbase, int nj,
+                                           int a0, int m, double* __restrict__ partial) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int u = warp; u < 2 * nj; u += nwarp) {
+    const int jl = u >> 1, ah = u & 1;
+    const float2* ar = Asp + (ah * 32 + lane) * PROW;
+    const float2* wr = Wsp + jl * PROW;
+    const int sb = tsub[jbase + jl];
+    const int x0 = sb & 15, x1 = (sb >> 4) & 15, y0 = (sb >> 8) & 15, y1 = (sb >> 12) & 15,
+              z0 = (sb >> 16) & 15, z1 = (sb >> 20) & 15;
+    CompF s0, s1;
+    for (int z = z0; z < z1; ++z)
+      for (int y = y0; y < y1; ++y) {
+        const int base = (z * TY + y) * TX;
+        int x = x0;
+        for (; x + 2 <= x1; x += 2) {
+          const float2 a0v = ar[base + x], w0v = wr[base + x];
+          const float2 a1v = ar[base + x + 1], w1v = wr[base + x + 1];
+          s0.add_prod(a0v.x, a0v.y, w0v.x, w0v.y);
+          s1.add_prod(a1v.x, a1v.y, w1v.x, w1v.y);
+        }
+        if (x < x1) {
+          const float2 av = ar[base + x], wv = wr[base + x];
+          s0.add_prod(av.x, av.y, wv.x, wv.y);
+        }
+      }
+    const int a = a0 + ah * 32 + lane;
+    if (a < m) partial[(size_t)(jbase + jl) * m + a] = s0.value() + s1.value();
+  }
+}
+
+// Same result as k_gram_partial_x.  Work item = (tile, chunk of PGA rows of
+// A), taken in order from a queue (tile-major, so consecutive chunks of a
+// tile reuse its W rows); *queue must be 0 at launch.
+__global__ void __launch_bounds__(PIPE_THREADS, 1)
+    k_gram_pipe_x(const double* __restrict__ A, int m, const double* __restrict__ W, TileGeom G,
+                  size_t ng, int n_tiles, const int* __restrict__ tptr,
+                  const int* __restrict__ tlist, const int* __restrict__ tsub,
+                  double* __restrict__ partial, int* __restrict__ queue) {
+  extern __shared__ __align__(16) unsigned char pipe_raw[];
+  PipeSmem& S = *reinterpret_cast<PipeSmem*>(pipe_raw);
+  __shared__ long long addr[TP];
+  __shared__ int wrow[PGJ];
+  __shared__ int s_tile;
+  const int nch = (m + PGA - 1) / PGA;
+
+  // next tile with a non-empty list (>= n_tiles: none left)
+  auto claim = [&]() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t;
+      do {
+        t = atomicAdd(queue, 1);
+      } while (t < n_tiles && tptr[t + 1] == tptr[t]);
+      s_tile = t;
+    }
+    __syncthreads();
+    return s_tile;
+  };
+  // addresses and first W block of tile T, then its chunk 0 (one group)
+  auto start_tile = [&](int T) {
+    const int j0 = tptr[T], nj = min(tptr[T + 1] - j0, PGJ);
+    for (int r = threadIdx.x; r < TP; r += blockDim.x) addr[r] = tile_point(G, T, r);
+    if (threadIdx.x < nj) wrow[threadIdx.x] = tlist[j0 + threadIdx.x];
+    __syncthreads();
+    stage_wrows(S.W64, W, wrow, addr, ng, nj);
+    stage_rows(S.A64, A, 0, m, addr, ng, PGA);
+    cp_async_commit();
+  };
+
+  int T = claim();
+  if (T >= n_tiles) return;
+  start_tile(T);
+  int c = 0;
+  for (;;) {
+    const int j0 = tptr[T], nJ = tptr[T + 1] - j0, njb = min(nJ, PGJ);
+    cp_async_wait_all();
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < PGA * TP; idx += blockDim.x)
+      S.Asp[(idx / TP) * PROW + idx % TP] = split64(S.A64[idx]);
+    if (c == 0)
+      for (int idx = threadIdx.x; idx < njb * TP; idx += blockDim.x)
+        S.Wsp[(idx / TP) * PROW + idx % TP] = split64(S.W64[idx]);
+    __syncthreads();
+    // issue the next item's copies; they land while this chunk computes
+    const int cT = T, cc = c;
+    bool more = true;
+    if (c + 1 < nch) {
+      c += 1;
+      stage_rows(S.A64, A, c * PGA, m, addr, ng, PGA);
+      cp_async_commit();
+    } else {
+      T = claim();
+      c = 0;
+      if (T < n_tiles)
+        start_tile(T);
+      else
+        more = false;
+    }
+    const int a0 = cc * PGA;
+    gram_units(S.Asp, S.Wsp, tsub, j0, njb, a0, m, partial);
+    if (nJ > PGJ) {  // long list: the remaining W blocks, synchronously
+      for (int jb = PGJ; jb < nJ; jb += PGJ) {
+        const int nj = min(PGJ, nJ - jb);
+        __syncthreads();
+        load_wrows_direct(S.Wsp, W, G, cT, ng, tlist, j0 + jb, nj);
+        __syncthreads();
+        gram_units(S.Asp, S.Wsp, tsub, j0 + jb, nj, a0, m, partial);
+      }
+      if (more && c > 0) {  // next chunk is of the same tile: first block back
+        __syncthreads();
+        load_wrows_direct(S.Wsp, W, G, cT, ng, tlist, j0, njb);
+      }
+    }
+    if (!more) break;
+    __syncthreads();
+  }
+  cp_async_wait_all();
+}
+
 // Mixed form of k_tile_expand (same splitting and compensated sums).
 __global__ void __launch_bounds__(256)
     k_tile_expand_x(const double* __restrict__ W, TileGeom G, size_t ng,
@@ -380,12 +570,21 @@ __global__ void __launch_bounds__(256)
   const long long g = tile_point(G, T, pt);
   CompF acc[16];
   const int pz = pt / (TX * TY), py = (pt / TX) % TY, px = pt % TX;  // pz: one per warp
+  // W value of list entry jl at this point (0 outside its sub-box); the
+  // next entry's value is loaded while the current one is used
+  auto fetch = [&](int jl) {
+    const int sb = tsub[j0 + jl];
+    const bool in = px >= (sb & 15) && px < ((sb >> 4) & 15) && py >= ((sb >> 8) & 15) &&
+                    py < ((sb >> 12) & 15) && pz >= ((sb >> 16) & 15) && pz < ((sb >> 20) & 15);
+    return (g >= 0 && in) ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0;
+  };
+  double wnext = nJ > 0 ? fetch(0) : 0.0;
   for (int jl = 0; jl < nJ; ++jl) {
+    const double wv = wnext;
+    if (jl + 1 < nJ) wnext = fetch(jl + 1);
     const int sb = tsub[j0 + jl];
     if (pz < ((sb >> 16) & 15) || pz >= ((sb >> 20) & 15)) continue;  // warp-uniform
-    const bool in = px >= (sb & 15) && px < ((sb >> 4) & 15) && py >= ((sb >> 8) & 15) &&
-                    py < ((sb >> 12) & 15);
-    const float2 w = split64((g >= 0 && in) ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0);
+    const float2 w = split64(wv);
     const float2* hrow = Hx + jl * 32 + vh * 16;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
@@ -749,9 +948,17 @@ static TileGeom tile_geom(const sea_ctx* c) {
 static void launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G, const int* tptr,
                         const int* tlist, const int* tsub) {
   const dim3 grid(c->n_tiles, (m + GA - 1) / GA);
-  if (c->prm.precision == 1)
-    k_gram_partial_x<<<grid, 256, GRAMX_SMEM, c->stream>>>(A, m, (const double*)c->vxx_dev.p, G,
-                                                           c->ng, tptr, tlist, tsub,
+  const double* W = (const double*)c->vxx_dev.p;
+  const bool pipe = (G.nx % 2 == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)W % 16 == 0);
+  if (c->prm.precision == 1 && pipe) {
+    int* queue = (int*)c->counts.p + 20;
+    cudaMemsetAsync(queue, 0, sizeof(int), c->stream);
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    k_gram_pipe_x<<<min(nsm, c->n_tiles), PIPE_THREADS, PIPE_SMEM, c->stream>>>(
+        A, m, W, G, c->ng, c->n_tiles, tptr, tlist, tsub, (double*)c->partial.p, queue);
+  } else if (c->prm.precision == 1)
+    k_gram_partial_x<<<grid, 256, GRAMX_SMEM, c->stream>>>(A, m, W, G, c->ng, tptr, tlist, tsub,
                                                            (double*)c->partial.p);
   else
     k_gram_partial<<<grid, 256, GRAM_SMEM, c->stream>>>(A, m, (const double*)c->vxx_dev.p, G,
@@ -843,6 +1050,9 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   if (err == cudaSuccess)
     err = cudaFuncSetAttribute(k_gram_partial_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)GRAMX_SMEM);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(k_gram_pipe_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PIPE_SMEM);
   if (err != cudaSuccess) return err;
   cudaEventRecord(c->ev[10], c->stream);
   launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);

@@ -208,7 +208,17 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
   }
   for (int k = 0; k < 16; ++k)
     if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
-      delete c;
+      sea_destroy(c);
+      return SEA_ERR_CUDA;
+    }
+  for (int k = 0; k < 2; ++k)
+    if (cudaStreamCreateWithFlags(&c->xfer[k], cudaStreamNonBlocking) != cudaSuccess) {
+      sea_destroy(c);
+      return SEA_ERR_CUDA;
+    }
+  for (int k = 0; k < 2 * SEA_XCHUNKS_MAX + 2; ++k)
+    if (cudaEventCreateWithFlags(&c->xev[k], cudaEventDisableTiming) != cudaSuccess) {
+      sea_destroy(c);
       return SEA_ERR_CUDA;
     }
   if (!sea_ensure(c, c->status, 64) || !sea_ensure(c, c->counts, 128) ||
@@ -249,12 +259,34 @@ sea_status sea_set_orbitals(sea_ctx* c, const double* phi, int n_orb, int on_dev
   SEA_ALLOC(eptr, (size_t)(n_orb + 1) * sizeof(int));
   SEA_ALLOC(ewin, (size_t)2 * ncand * sizeof(Entry));
   SEA_ALLOC(coff, (size_t)2 * ncand * sizeof(long long));
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  SEA_CK(cudaMemcpyAsync(c->phi.p, phi, bytes, kind, c->stream), "copy orbitals");
   SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
-  sea::k_check_finite<<<1024, 256, 0, c->stream>>>((const double*)c->phi.p, n_orb * c->ng,
-                                                   (unsigned*)c->status.p);
-  c->launches += 1;
+  double* pd = (double*)c->phi.p;
+  if (on_device) {
+    SEA_CK(cudaMemcpyAsync(pd, phi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy orbitals");
+    sea::k_check_finite<<<1024, 256, 0, c->stream>>>(pd, n_orb * c->ng, (unsigned*)c->status.p);
+    c->launches += 1;
+  } else {
+    // orbital ranges copied in on the copy stream, each checked on the
+    // context stream once it has arrived
+    const int nch = std::min(8, n_orb);
+    cudaEvent_t ev_start = c->xev[2 * SEA_XCHUNKS_MAX];
+    SEA_CK(cudaEventRecord(ev_start, c->stream), "event");
+    SEA_CK(cudaStreamWaitEvent(c->xfer[0], ev_start, 0), "wait");
+    for (int k = 0; k < nch; ++k) {
+      const size_t o0 = (size_t)n_orb * k / nch, o1 = (size_t)n_orb * (k + 1) / nch;
+      SEA_CK(cudaMemcpyAsync(pd + o0 * c->ng, phi + o0 * c->ng, (o1 - o0) * c->ng * sizeof(double),
+                             cudaMemcpyHostToDevice, c->xfer[0]),
+             "copy orbitals");
+      SEA_CK(cudaEventRecord(c->xev[k], c->xfer[0]), "event");
+    }
+    for (int k = 0; k < nch; ++k) {
+      const size_t o0 = (size_t)n_orb * k / nch, o1 = (size_t)n_orb * (k + 1) / nch;
+      SEA_CK(cudaStreamWaitEvent(c->stream, c->xev[k], 0), "wait");
+      sea::k_check_finite<<<1024, 256, 0, c->stream>>>(pd + o0 * c->ng, (o1 - o0) * c->ng,
+                                                       (unsigned*)c->status.p);
+      c->launches += 1;
+    }
+  }
   SEA_CK(cudaGetLastError(), "finite check");
   unsigned st = 0;
   SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
@@ -279,6 +311,12 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_CK(sea::launch_entries(c), "accumulation entries");
   int hc[16];
   SEA_CK(cudaMemcpyAsync(hc, c->counts.p, sizeof(hc), cudaMemcpyDeviceToHost, c->stream), "counts");
+  if (!on_device) {  // entry offsets: the output is produced and copied out by orbital ranges
+    c->h_eptr.resize((size_t)c->n_orb + 1);
+    SEA_CK(cudaMemcpyAsync(c->h_eptr.data(), c->eptr.p, ((size_t)c->n_orb + 1) * sizeof(int),
+                           cudaMemcpyDeviceToHost, c->stream),
+           "entry offsets");
+  }
   SEA_CK(cudaStreamSynchronize(c->stream), "plan");
   c->Pproto = hc[0];
   c->P = hc[1];
@@ -301,12 +339,38 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
   SEA_CK(sea::launch_cg(c), "cg");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
-  SEA_CK(sea::launch_accumulate(c, (double*)c->vxx_dev.p), "accumulate");
-  SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
   const size_t bytes = (size_t)c->n_orb * c->ng * sizeof(double);
-  SEA_CK(cudaMemcpyAsync(vxx_phi, c->vxx_dev.p, bytes,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
-         "copy V_xx phi");
+  double* vd = (double*)c->vxx_dev.p;
+  if (on_device) {
+    SEA_CK(sea::launch_accumulate(c, vd), "accumulate");
+    SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
+    SEA_CK(cudaMemcpyAsync(vxx_phi, vd, bytes, cudaMemcpyDeviceToDevice, c->stream),
+           "copy V_xx phi");
+  } else {
+    // Host output: orbital ranges are finished and copied out one after
+    // another, the copy of one range overlapping the kernels of the next.
+    const int nch = std::min(8, c->n_orb);
+    cudaEvent_t ev_start = c->xev[2 * SEA_XCHUNKS_MAX];
+    cudaEvent_t ev_out = c->xev[2 * SEA_XCHUNKS_MAX + 1];
+    SEA_CK(cudaEventRecord(ev_start, c->stream), "event");
+    SEA_CK(cudaStreamWaitEvent(c->xfer[1], ev_start, 0), "wait");
+    for (int k = 0; k < nch; ++k) {
+      const int o0 = (int)((long long)c->n_orb * k / nch);
+      const int o1 = (int)((long long)c->n_orb * (k + 1) / nch);
+      SEA_CK(sea::launch_accumulate_range(c, vd, o0, o1, c->h_eptr[o0], c->h_eptr[o1]),
+             "accumulate");
+      SEA_CK(cudaEventRecord(c->xev[SEA_XCHUNKS_MAX + k], c->stream), "event");
+      SEA_CK(cudaStreamWaitEvent(c->xfer[1], c->xev[SEA_XCHUNKS_MAX + k], 0), "wait");
+      SEA_CK(cudaMemcpyAsync(vxx_phi + (size_t)o0 * c->ng, vd + (size_t)o0 * c->ng,
+                             (size_t)(o1 - o0) * c->ng * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->xfer[1]),
+             "copy V_xx phi");
+    }
+    SEA_CK(sea::launch_exx(c), "exx");
+    SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
+    SEA_CK(cudaEventRecord(ev_out, c->xfer[1]), "event");
+    SEA_CK(cudaStreamWaitEvent(c->stream, ev_out, 0), "wait");
+  }
   struct {
     double res[5];
     unsigned st;
@@ -408,24 +472,56 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   if (!c->have_ace) return sea_fail(c, SEA_ERR_STATE, "sea_build_ace first");
   if (!psi || !out || n_vec < 1) return sea_fail(c, SEA_ERR_ARG, "bad psi/out");
   const size_t bytes = (size_t)n_vec * c->ng * sizeof(double);
-  const double* src = psi;
-  double* dst = out;
-  if (!on_device) {
-    SEA_ALLOC(psi_dev, bytes);
-    SEA_ALLOC(out_dev, bytes);
-    SEA_CK(cudaMemcpyAsync(c->psi_dev.p, psi, bytes, cudaMemcpyHostToDevice, c->stream), "copy psi");
-    src = (const double*)c->psi_dev.p;
-    dst = (double*)c->out_dev.p;
+  if (on_device) {
+    SEA_CK(cudaEventRecord(c->ev[7], c->stream), "event");
+    cudaError_t e = sea::launch_ace_apply(c, psi, n_vec, out);
+    if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE apply workspace");
+    SEA_CK(e, "ace apply");
+    SEA_CK(cudaEventRecord(c->ev[8], c->stream), "event");
+    c->apply_timed = true;
+    return SEA_OK;
+  }
+  // Host buffers: the vectors are independent, so the call runs in chunks
+  // of vectors: chunk k is copied in on one copy stream, applied on the
+  // context stream and copied out on the other copy stream, so the two
+  // transfer directions and the kernels overlap.
+  SEA_ALLOC(psi_dev, bytes);
+  SEA_ALLOC(out_dev, bytes);
+  const int per = std::max(32, (n_vec + SEA_XCHUNKS_MAX - 1) / SEA_XCHUNKS_MAX);
+  const int nch = (n_vec + per - 1) / per;
+  double* pd = (double*)c->psi_dev.p;
+  double* od = (double*)c->out_dev.p;
+  cudaEvent_t* evH = c->xev;             // chunk k copied in
+  cudaEvent_t* evC = c->xev + SEA_XCHUNKS_MAX;  // chunk k applied
+  cudaEvent_t ev_start = c->xev[2 * SEA_XCHUNKS_MAX];
+  cudaEvent_t ev_out = c->xev[2 * SEA_XCHUNKS_MAX + 1];
+  SEA_CK(cudaEventRecord(ev_start, c->stream), "event");
+  SEA_CK(cudaStreamWaitEvent(c->xfer[0], ev_start, 0), "wait");
+  SEA_CK(cudaStreamWaitEvent(c->xfer[1], ev_start, 0), "wait");
+  for (int k = 0; k < nch; ++k) {
+    const size_t v0 = (size_t)k * per, nv = std::min<size_t>(per, n_vec - v0);
+    SEA_CK(cudaMemcpyAsync(pd + v0 * c->ng, psi + v0 * c->ng, nv * c->ng * sizeof(double),
+                           cudaMemcpyHostToDevice, c->xfer[0]),
+           "copy psi");
+    SEA_CK(cudaEventRecord(evH[k], c->xfer[0]), "event");
   }
   SEA_CK(cudaEventRecord(c->ev[7], c->stream), "event");
-  cudaError_t e = sea::launch_ace_apply(c, src, n_vec, dst);
-  if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE apply workspace");
-  SEA_CK(e, "ace apply");
-  SEA_CK(cudaEventRecord(c->ev[8], c->stream), "event");
-  if (!on_device) {
-    SEA_CK(cudaMemcpyAsync(out, c->out_dev.p, bytes, cudaMemcpyDeviceToHost, c->stream), "copy out");
-    SEA_CK(cudaStreamSynchronize(c->stream), "apply_ace");
+  for (int k = 0; k < nch; ++k) {
+    const size_t v0 = (size_t)k * per, nv = std::min<size_t>(per, n_vec - v0);
+    SEA_CK(cudaStreamWaitEvent(c->stream, evH[k], 0), "wait");
+    cudaError_t e = sea::launch_ace_apply(c, pd + v0 * c->ng, (int)nv, od + v0 * c->ng);
+    if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE apply workspace");
+    SEA_CK(e, "ace apply");
+    SEA_CK(cudaEventRecord(evC[k], c->stream), "event");
+    SEA_CK(cudaStreamWaitEvent(c->xfer[1], evC[k], 0), "wait");
+    SEA_CK(cudaMemcpyAsync(out + v0 * c->ng, od + v0 * c->ng, nv * c->ng * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->xfer[1]),
+           "copy out");
   }
+  SEA_CK(cudaEventRecord(c->ev[8], c->stream), "event");
+  SEA_CK(cudaEventRecord(ev_out, c->xfer[1]), "event");
+  SEA_CK(cudaStreamWaitEvent(c->stream, ev_out, 0), "wait");
+  SEA_CK(cudaStreamSynchronize(c->stream), "apply_ace");
   c->apply_timed = true;
   return SEA_OK;
 }
@@ -611,6 +707,13 @@ const char* sea_last_error(const sea_ctx* c) {
 void sea_destroy(sea_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  for (int k = 0; k < 2; ++k)
+    if (c->xfer[k]) {
+      cudaStreamSynchronize(c->xfer[k]);
+      cudaStreamDestroy(c->xfer[k]);
+    }
+  for (cudaEvent_t e : c->xev)
+    if (e) cudaEventDestroy(e);
   sea_batch_cache_free(c);
   SeaBuf* all[] = {&c->phi, &c->vxx_dev, &c->psi_dev, &c->out_dev, &c->rowsum, &c->colsum,
                    &c->marg, &c->box, &c->cand_flag, &c->cand_geom, &c->list_a, &c->list_b,

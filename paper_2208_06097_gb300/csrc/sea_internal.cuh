@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <vector>
 
 #include "../../include/sea.h"
 
@@ -20,6 +21,9 @@
 #define SEA_FLAG_NOT_PD 2u
 #define SEA_FLAG_BOUNDS 4u
 #define SEA_FLAG_NONFINITE 8u
+
+// At most this many chunks per pipelined host-buffer call.
+#define SEA_XCHUNKS_MAX 64
 
 namespace sea {
 
@@ -189,6 +193,11 @@ struct sea_ctx {
 
   long long launches = 0;
   cudaEvent_t ev[16] = {};
+  // host-buffer transfers: copy streams (host to device, device to host) and
+  // per-chunk events, created with the context
+  cudaStream_t xfer[2] = {};
+  std::vector<int> h_eptr;  // entry offsets per orbital, host copy (last plan)
+  cudaEvent_t xev[2 * SEA_XCHUNKS_MAX + 2] = {};
 };
 
 // Host-side helpers implemented in api.cu.
@@ -222,6 +231,9 @@ cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, cons
                             int total, int* queue);
 cudaError_t launch_entries(sea_ctx* c);
 cudaError_t launch_accumulate(sea_ctx* c, double* out);
+cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
+                                    int e_end);
+cudaError_t launch_exx(sea_ctx* c);
 cudaError_t launch_ace_build(sea_ctx* c);
 cudaError_t launch_ace_eigen(sea_ctx* c);
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int n_vec, double* out);
