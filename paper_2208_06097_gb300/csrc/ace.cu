@@ -613,11 +613,20 @@ __global__ void k_gram_reduce(const double* __restrict__ partial, int m, int n_o
   out[(size_t)a * sa + (size_t)o * so] = scale * s;
 }
 
-// -Mbar = L L^T by a blocked right-looking Cholesky over several kernels
-// (block 32): k_chol_init forms A = -(M + M^T)/2; per block column,
-// k_chol_panel factors the 32 x 32 diagonal block in shared memory and
-// solves the rows below it; k_chol_update subtracts the panel's
-// contribution from the trailing lower triangle, one CTA per 32 x 32 block.
+// -Mbar = L L^T by a blocked right-looking Cholesky (block CB = 32), and
+// L^-1.  On this part a warp's FP64 instruction holds an SM sub-partition's
+// FP64 unit for about 64 cycles whatever its active lanes, so the kernels
+// keep the sequential pivot chain short and spread the products over many
+// CTAs:
+//   k_chol_init   A = -(M + M^T)/2 (lower triangle; zeros above)
+//   per block column kb:
+//     k_chol_diag   one CTA: L_kk = chol(A_kk) and Y_kk = L_kk^-1
+//     k_chol_trsm   rows below: L_ik = A_ik L_kk^-T = A_ik Y_kk^T
+//     k_chol_syrk   trailing lower triangle: A_ij -= L_ik L_jk^T
+//   k_linv_init   diagonal blocks of L^-1 from the Y_kk
+//   k_inv_pairs   L^-1 by doubling: for s = 32, 64, ..., each diagonal pair
+//                 [[P, 0], [B, Q]] with known P^-1, Q^-1 has the off-diagonal
+//                 block -Q^-1 B P^-1 (two batched products per level).
 // A non-positive pivot sets SEA_FLAG_NOT_PD and the later kernels return.
 #define CB 32
 __global__ void k_chol_init(const double* __restrict__ M, int n, double* __restrict__ A) {
@@ -627,106 +636,159 @@ __global__ void k_chol_init(const double* __restrict__ M, int n, double* __restr
   A[q] = (j <= i) ? -0.5 * (M[(size_t)i * n + j] + M[(size_t)j * n + i]) : 0.0;
 }
 
-__global__ void __launch_bounds__(256)
-    k_chol_panel(double* __restrict__ A, int n, int kb, unsigned* __restrict__ status,
-                 double* __restrict__ Tbuf) {
+// Warp w holds column w of the block (lane = row).  Step k: every column
+// w > k subtracts L(:, k) L(w, k); column k + 1 is then complete and its
+// warp takes the pivot at once, while the other warps still update.
+__global__ void __launch_bounds__(1024)
+    k_chol_diag(double* __restrict__ A, int n, int kb, unsigned* __restrict__ status,
+                double* __restrict__ Y) {
   if (*status & SEA_FLAG_NOT_PD) return;
-  __shared__ double D[CB][CB + 1];
+  __shared__ double Lc[CB][CB + 1];  // Lc[k][i] = L(i, k), column k final
+  __shared__ double Sc[CB][CB + 1];  // Sc[k][i] = L(i, k) / L(k, k) for i > k, else 0
+  __shared__ double rinv[CB];        // 1 / L(k, k)
   __shared__ int bad;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nb = min(CB, n - kb);
+  double a = 0.0;
+  if (w < nb) {
+    if (lane < nb && lane >= w) a = A[(size_t)(kb + lane) * n + kb + w];
+  } else if (lane == w) {
+    a = 1.0;  // identity beyond the matrix edge
+  }
   if (threadIdx.x == 0) bad = 0;
-  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
-    const int i = q / CB, j = q % CB;
-    D[i][j] = (i < nb && j < nb) ? A[(size_t)(kb + i) * n + kb + j] : 0.0;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {  // one warp factors the diagonal block
-    const int lane = threadIdx.x;
-    for (int k = 0; k < nb; ++k) {
-      double d = D[k][k];
-      if (!(d > 0.0)) {
-        if (lane == 0) bad = 1;
-        break;
-      }
-      d = sqrt(d);
-      __syncwarp();
-      if (lane == 0) D[k][k] = d;
-      if (lane > k && lane < nb) D[lane][k] /= d;
-      __syncwarp();
-      for (int j = k + 1; j < nb; ++j)
-        if (lane >= j && lane < nb) D[lane][j] = fma(-D[lane][k], D[j][k], D[lane][j]);
-      __syncwarp();
+  auto pivot = [&]() {
+    const double d = __shfl_sync(0xffffffffu, a, w);
+    const bool ok = d > 0.0;
+    const double r = ok ? rsqrt(d) : 0.0;
+    const double l = (lane == w) ? d * r : (lane > w ? a * r : 0.0);
+    Lc[w][lane] = l;
+    Sc[w][lane] = (lane > w) ? l * r : 0.0;
+    if (lane == 0) {
+      rinv[w] = r;
+      if (!ok) bad = 1;
     }
-  }
+  };
+  if (w == 0) pivot();
   __syncthreads();
+  for (int k = 0; k < CB - 1; ++k) {
+    if (bad) break;
+    if (w > k) {
+      a = fma(-Lc[k][lane], Lc[k][w], a);
+      if (w == k + 1) pivot();
+    }
+    __syncthreads();
+  }
   if (bad) {
     if (threadIdx.x == 0) atomicOr(status, SEA_FLAG_NOT_PD);
     return;
   }
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int i = q / nb, j = q % nb;
-    if (j <= i) A[(size_t)(kb + i) * n + kb + j] = D[i][j];
-  }
-  // rows below solve x L_kk^T = a: with Y = L_kk^-1 (one column per thread,
-  // forward substitution), x_j = sum_l a_l Y_jl -- independent dot products.
-  __shared__ double Y[CB][CB + 1];
-  if (threadIdx.x < CB) {
-    const int k = threadIdx.x;
-    for (int i = 0; i < CB; ++i) {
-      double v = (i == k) ? 1.0 : 0.0;
-      if (i < nb)
-        for (int l = k; l < i; ++l) v = fma(-D[i][l], Y[l][k], v);
-      Y[i][k] = (i < nb && i >= k) ? v / D[i][i] : 0.0;
-    }
-  }
-  __syncthreads();
-  const int rows = n - kb - nb;
-  for (int q = threadIdx.x; q < rows * CB; q += blockDim.x) {
-    const int i = kb + nb + q / CB, j = q % CB;
-    double x = 0.0;
-    if (j < nb) {
-      const double* ai = A + (size_t)i * n + kb;
-      for (int l = 0; l <= j; ++l) x = fma(ai[l], Y[j][l], x);
-    }
-    Tbuf[q] = x;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < rows * CB; q += blockDim.x) {
-    const int i = kb + nb + q / CB, j = q % CB;
-    if (j < nb) A[(size_t)i * n + kb + j] = Tbuf[q];
-  }
+  if (w < nb && lane < nb && lane >= w) A[(size_t)(kb + lane) * n + kb + w] = Lc[w][lane];
+  // column w of Y: forward substitution, t_i -= (L(i, j) / L(j, j)) t_j
+  double t = (lane == w) ? 1.0 : 0.0;
+  for (int j = w; j < CB - 1; ++j) t = fma(-Sc[j][lane], __shfl_sync(0xffffffffu, t, j), t);
+  Y[lane * CB + w] = t * rinv[lane];
 }
 
-__global__ void __launch_bounds__(256)
-    k_chol_update(double* __restrict__ A, int n, int kb, const unsigned* __restrict__ status) {
+// Rows [kb + CB, n) of the panel, 16 per CTA (thread = row, column):
+// L(i, j) = sum_{l <= j} A(i, l) Y(j, l), written in place.
+__global__ void __launch_bounds__(512)
+    k_chol_trsm(double* __restrict__ A, int n, int kb, const unsigned* __restrict__ status,
+                const double* __restrict__ Y) {
   if (*status & SEA_FLAG_NOT_PD) return;
-  // lower-triangular block (bi, bj), bj <= bi, of the trailing matrix
-  const int t0 = kb + CB;
-  const int nbt = (n - t0 + CB - 1) / CB;
-  int bi = 0, rem = blockIdx.x;
-  while (rem > bi) {
-    rem -= bi + 1;
-    ++bi;
+  __shared__ double As[16][CB + 1], Ys[CB][CB + 1];
+  const int r = threadIdx.x / CB, j = threadIdx.x % CB;
+  const int i = kb + CB + blockIdx.x * 16 + r;
+  Ys[r][j] = Y[r * CB + j];
+  Ys[r + 16][j] = Y[(r + 16) * CB + j];
+  As[r][j] = (i < n && kb + j < n) ? A[(size_t)i * n + kb + j] : 0.0;
+  __syncthreads();
+  double x = 0.0;
+  for (int l = 0; l <= j; ++l) x = fma(As[r][l], Ys[j][l], x);
+  if (i < n && kb + j < n) A[(size_t)i * n + kb + j] = x;
+}
+
+// Trailing lower triangle after block column kb, one 16 x 16 tile per CTA
+// (tiles (ti, tj), tj <= ti, numbered row by row).
+__global__ void __launch_bounds__(256)
+    k_chol_syrk(double* __restrict__ A, int n, int kb, const unsigned* __restrict__ status) {
+  if (*status & SEA_FLAG_NOT_PD) return;
+  int ti = 0, rem = blockIdx.x;
+  while (rem > ti) {
+    rem -= ti + 1;
+    ++ti;
   }
-  const int bj = rem;
-  if (bi >= nbt) return;
-  __shared__ double Li[CB][CB + 1], Lj[CB][CB + 1];
-  const int i0 = t0 + bi * CB, j0 = t0 + bj * CB;
-  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
+  const int tj = rem;
+  const int t0 = kb + CB;
+  __shared__ double Li[16][CB + 1], Lj[16][CB + 1];
+  const int i0 = t0 + ti * 16, j0 = t0 + tj * 16;
+  for (int q = threadIdx.x; q < 16 * CB; q += blockDim.x) {
     const int r = q / CB, k = q % CB;
-    Li[r][k] = (i0 + r < n) ? A[(size_t)(i0 + r) * n + kb + k] : 0.0;
-    Lj[r][k] = (j0 + r < n) ? A[(size_t)(j0 + r) * n + kb + k] : 0.0;
+    const bool kin = kb + k < n;
+    Li[r][k] = (i0 + r < n && kin) ? A[(size_t)(i0 + r) * n + kb + k] : 0.0;
+    Lj[r][k] = (j0 + r < n && kin) ? A[(size_t)(j0 + r) * n + kb + k] : 0.0;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < CB * CB; q += blockDim.x) {
-    const int r = q / CB, cidx = q % CB;
-    const int i = i0 + r, j = j0 + cidx;
-    if (i >= n || j >= n || j > i) continue;
-    double s = A[(size_t)i * n + j];
+  const int r = threadIdx.x / 16, cidx = threadIdx.x % 16;
+  const int i = i0 + r, j = j0 + cidx;
+  if (i >= n || j > i) return;
+  double s = A[(size_t)i * n + j];
 #pragma unroll 8
-    for (int k = 0; k < CB; ++k) s = fma(-Li[r][k], Lj[cidx][k], s);
-    A[(size_t)i * n + j] = s;
+  for (int k = 0; k < CB; ++k) s = fma(-Li[r][k], Lj[cidx][k], s);
+  A[(size_t)i * n + j] = s;
+}
+
+// Linv = block diagonal of the Y_kk (zeros elsewhere).
+__global__ void k_linv_init(const double* __restrict__ Y, int n, double* __restrict__ Linv) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)n * n) return;
+  const int i = (int)(q / n), j = (int)(q % n);
+  const int b = i / CB;
+  Linv[q] = (j / CB == b && j <= i) ? Y[(size_t)b * CB * CB + (i % CB) * CB + (j % CB)] : 0.0;
+}
+
+// One level of the doubling.  Pair p covers rows/columns [o, o + s + s2),
+// o = 2 s p, s2 = min(s, n - o - s): P = Linv[o.., o..] (s x s), B = L[o+s..,
+// o..] (s2 x s), Q = Linv[o+s.., o+s..] (s2 x s2), all known.  phase 0:
+// T_p = B P (P lower: k >= j);  phase 1: Linv[o+s+i][o+j] = -(Q T_p)[i][j]
+// (Q lower: k <= i).  16 x 16 output tile per CTA, grid (s/16, s/16, pairs).
+__global__ void __launch_bounds__(256)
+    k_inv_pairs(int n, int s, int phase, const double* __restrict__ L, double* __restrict__ Linv,
+                double* __restrict__ T) {
+  const int p = blockIdx.z, o = 2 * s * p;
+  const int s2 = min(s, n - o - s);
+  if (s2 <= 0) return;
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  if (i0 >= s2) return;
+  const int i = i0 + ty, j = j0 + tx;
+  double* Tp = T + (size_t)p * s * s;  // [s2][s]
+  __shared__ double As[16][17], Bs[16][17];
+  double acc = 0.0;
+  // phase 0: k in [j0, s); phase 1: k in [0, min(i0 + 16, s2))
+  const int kbeg = phase == 0 ? j0 : 0;
+  const int kend = phase == 0 ? s : min(i0 + 16, s2);
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    const int ka = k0 + tx, kr = k0 + ty;
+    double av = 0.0, bv = 0.0;
+    if (phase == 0) {
+      if (i < s2 && ka < s) av = L[(size_t)(o + s + i) * n + o + ka];
+      if (kr < s && j < s) bv = Linv[(size_t)(o + kr) * n + o + j];
+    } else {
+      if (i < s2 && ka < s2) av = Linv[(size_t)(o + s + i) * n + o + s + ka];
+      if (kr < s2 && j < s) bv = Tp[(size_t)kr * s + j];
+    }
+    As[ty][tx] = av;
+    Bs[ty][tx] = bv;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+    __syncthreads();
   }
+  if (i >= s2 || j >= s) return;
+  if (phase == 0)
+    Tp[(size_t)i * s + j] = acc;
+  else
+    Linv[(size_t)(o + s + i) * n + o + j] = -acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -853,22 +915,6 @@ __global__ void k_scale_rows(double* __restrict__ B, const double* __restrict__ 
   B[t] *= d[t / m];
 }
 
-// Column k of L^-1 by forward substitution, CTA per column.
-__global__ void k_trinv(const double* __restrict__ L, int n, double* __restrict__ Linv) {
-  extern __shared__ double xs[];
-  const int k = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = (i == k) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int l = k; l < n; ++l) {
-    if (threadIdx.x == 0) xs[l] /= L[(size_t)l * n + l];
-    __syncthreads();
-    const double xl = xs[l];
-    for (int i = l + 1 + threadIdx.x; i < n; i += blockDim.x) xs[i] = fma(-L[(size_t)i * n + l], xl, xs[i]);
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) Linv[(size_t)i * n + k] = (i >= k) ? xs[i] : 0.0;
-}
-
 // C[n1][n2] = op(A) B, op(A)(i, k) = A[k][i] if transA else A[i][k]; A is
 // n1 x n1 (square), B is [n1][n2].  16 x 16 shared-memory tiles.
 __global__ void k_small_gemm(const double* __restrict__ A, int transA, const double* __restrict__ B,
@@ -980,6 +1026,16 @@ static void launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr, const 
   }
 }
 
+// Scratch (doubles) of the L^-1 doubling: the largest level's pairs x s x s.
+static size_t inv_scratch_doubles(int n) {
+  size_t m = 1;
+  for (int s = CB; s < n; s *= 2) {
+    const size_t pairs = (size_t)((n - s + 2 * s - 1) / (2 * s));
+    m = std::max(m, pairs * s * s);
+  }
+  return m;
+}
+
 // Tile lists of W's support, M, Cholesky and L^-1.  Needs the incidence
 // count on the host to size the partial sums: one stream sync.
 cudaError_t launch_ace_build(sea_ctx* c) {
@@ -994,7 +1050,8 @@ cudaError_t launch_ace_build(sea_ctx* c) {
       !sea_ensure(c, c->Mbuf, (size_t)n * n * sizeof(double)) ||
       !sea_ensure(c, c->Lbuf, (size_t)n * n * sizeof(double)) ||
       !sea_ensure(c, c->Linv, (size_t)n * n * sizeof(double)) ||
-      !sea_ensure(c, c->Abuf, (size_t)n * CB * sizeof(double)))
+      !sea_ensure(c, c->Abuf, (size_t)((n + CB - 1) / CB) * CB * CB * sizeof(double)) ||
+      !sea_ensure(c, c->Hbuf2, inv_scratch_doubles(n) * sizeof(double)))
     return cudaErrorMemoryAllocation;
   int* inc = (int*)c->tmask.p;
   int* gidx = inc + ninc;
@@ -1061,19 +1118,32 @@ cudaError_t launch_ace_build(sea_ctx* c) {
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p, n, 1);
   k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
+  double* L = (double*)c->Lbuf.p;
+  double* Y = (double*)c->Abuf.p;  // Y_kk blocks, CB x CB each
+  unsigned* status = (unsigned*)c->status.p;
   int nchol = 1;
-  for (int kb = 0; kb < n; kb += CB) {
-    k_chol_panel<<<1, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb, (unsigned*)c->status.p,
-                                           (double*)c->Abuf.p);
-    const int nbt = (n - kb - CB + CB - 1) / CB;
-    if (nbt > 0)
-      k_chol_update<<<nbt * (nbt + 1) / 2, 256, 0, c->stream>>>((double*)c->Lbuf.p, n, kb,
-                                                                 (const unsigned*)c->status.p);
-    nchol += 1 + (nbt > 0);
+  for (int kb = 0, b = 0; kb < n; kb += CB, ++b) {
+    k_chol_diag<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
+    const int rows = n - kb - CB;
+    if (rows > 0) {
+      const int nt = (rows + 15) / 16;
+      k_chol_trsm<<<nt, 512, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
+      k_chol_syrk<<<nt * (nt + 1) / 2, 256, 0, c->stream>>>(L, n, kb, status);
+      nchol += 2;
+    }
+    nchol += 1;
   }
-  k_trinv<<<n, 256, n * sizeof(double), c->stream>>>((const double*)c->Lbuf.p, n,
-                                                     (double*)c->Linv.p);
-  c->launches += 11 + nchol;
+  double* Linv = (double*)c->Linv.p;
+  k_linv_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(Y, n, Linv);
+  for (int s = CB; s < n; s *= 2) {
+    const int pairs = (n - s + 2 * s - 1) / (2 * s);
+    const dim3 g((s + 15) / 16, (s + 15) / 16, pairs);
+    double* T = (double*)c->Hbuf2.p;
+    k_inv_pairs<<<g, 256, 0, c->stream>>>(n, s, 0, L, Linv, T);
+    k_inv_pairs<<<g, 256, 0, c->stream>>>(n, s, 1, L, Linv, T);
+    nchol += 2;
+  }
+  c->launches += 10 + nchol;
   return cudaGetLastError();
 }
 
