@@ -14,14 +14,6 @@
 
 namespace sea {
 
-#define TX 8
-#define TY 4
-#define TZ 4
-#define TP (TX * TY * TZ)
-
-struct TileGeom {
-  int nx, ny, nz, ntx, nty, ntz;
-};
 
 __device__ __forceinline__ bool cyc_meets(int s, int L, int a, int b, int n) {
   // cyclic [s, s+L) (s wrapped) meets [a, b) (0 <= a < b <= n)
@@ -173,12 +165,6 @@ __global__ void k_max_int(const int* __restrict__ in, int n, int* __restrict__ o
   }
 }
 
-__device__ __forceinline__ long long tile_point(const TileGeom& G, int T, int r) {
-  const int txi = T % G.ntx, tyi = (T / G.ntx) % G.nty, tzi = T / (G.ntx * G.nty);
-  const int x = txi * TX + (r % TX), y = tyi * TY + (r / TX) % TY, z = tzi * TZ + r / (TX * TY);
-  if (x >= G.nx || y >= G.ny || z >= G.nz) return -1;
-  return ((long long)z * G.ny + y) * G.nx + x;
-}
 
 // partial[(tptr[T] + s) * m + a] = sum_{r in T} A[a][r] W[list[s]][r].
 // CTA per (tile, chunk of 64 rows of A).  The tile's 128 points of the 64
@@ -252,13 +238,13 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // ---------------------------------------------------------------------------
-// Mixed form of the same contraction: FP64 operands split into FP32 pairs
-// (v = hi + lo, hi = fl32(v), lo = fl32(v - hi)), each product formed as
-// hi*hi exactly (FMA residual) plus the two cross terms, and summed with an
-// error-free addition into a (sum, compensation) pair of FP32 values.  The
-// result carries about 44 significant bits (relative error ~1e-13 per
-// tile partial; partials are combined in FP64), at the FP32 issue rate,
-// which on this part is 64x the FP64 rate.
+// Mixed form of the expansion W H (k_tile_expand_x): FP64 operands split into
+// FP32 pairs (v = hi + lo, hi = fl32(v), lo = fl32(v - hi)), each product
+// formed as hi*hi exactly (FMA residual) plus the two cross terms, and
+// summed with an error-free addition into a (sum, compensation) pair of
+// FP32 values: about 44 significant bits, at the FP32 issue rate, which on
+// this part is 64x the FP64 rate.  (The mixed form's contraction with W,
+// M = Phi^T W and W^T psi, runs on the tensor cores: gram_tc.cu.)
 // ---------------------------------------------------------------------------
 struct CompF {
   float s, c;
@@ -294,260 +280,6 @@ __device__ __forceinline__ float2 split64(double v) {
   const float l = ((float)(unsigned)(m & 0x1FFFFFFFULL) * 5.421010862427522e-20f) *
                   __uint_as_float((unsigned)(e - 884) << 23);
   return make_float2(hi, __uint_as_float(__float_as_uint(l) | sign));
-}
-
-#define GROWX (TP + 1)
-#define GRAMX_SMEM ((size_t)(GA + GJB) * GROWX * sizeof(float2))
-__global__ void __launch_bounds__(256, 2)
-    k_gram_partial_x(const double* __restrict__ A, int m, const double* __restrict__ W,
-                     TileGeom G, size_t ng, const int* __restrict__ tptr,
-                     const int* __restrict__ tlist, const int* __restrict__ tsub,
-                     double* __restrict__ partial) {
-  const int T = blockIdx.x;
-  const int a0 = blockIdx.y * GA;
-  const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
-  if (nJ == 0) return;
-  extern __shared__ float2 gsx[];
-  float2* As = gsx;               // [GA][GROWX]
-  float2* Ws = gsx + GA * GROWX;  // [GJB][GROWX]
-  __shared__ long long addr[TP];
-  __shared__ int wrow[GJB];
-  for (int r = threadIdx.x; r < TP; r += blockDim.x) addr[r] = tile_point(G, T, r);
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < GA * TP; idx += blockDim.x) {
-    const int a = idx / TP, pt = idx % TP;
-    const long long g = addr[pt];
-    As[a * GROWX + pt] = split64((a0 + a < m && g >= 0) ? A[(size_t)(a0 + a) * ng + g] : 0.0);
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int jb = 0; jb < nJ; jb += GJB) {
-    const int nj = min(GJB, nJ - jb);
-    __syncthreads();
-    if (threadIdx.x < nj) wrow[threadIdx.x] = tlist[j0 + jb + threadIdx.x];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nj * TP; idx += blockDim.x) {
-      const int jl = idx / TP, pt = idx % TP;
-      const long long g = addr[pt];
-      Ws[jl * GROWX + pt] = split64(g >= 0 ? W[(size_t)wrow[jl] * ng + g] : 0.0);
-    }
-    __syncthreads();
-    for (int u = warp; u < 2 * nj; u += nwarp) {
-      const int jl = u >> 1, ah = u & 1;
-      const float2* ar = As + (ah * 32 + lane) * GROWX;
-      const float2* wr = Ws + jl * GROWX;
-      const int sb = tsub[j0 + jb + jl];
-      const int x0 = sb & 15, x1 = (sb >> 4) & 15, y0 = (sb >> 8) & 15, y1 = (sb >> 12) & 15,
-                z0 = (sb >> 16) & 15, z1 = (sb >> 20) & 15;
-      CompF c0, c1;
-      for (int z = z0; z < z1; ++z)
-        for (int y = y0; y < y1; ++y) {
-          const int base = (z * TY + y) * TX;
-          int x = x0;
-          for (; x + 2 <= x1; x += 2) {
-            const float2 a0v = ar[base + x], w0v = wr[base + x];
-            const float2 a1v = ar[base + x + 1], w1v = wr[base + x + 1];
-            c0.add_prod(a0v.x, a0v.y, w0v.x, w0v.y);
-            c1.add_prod(a1v.x, a1v.y, w1v.x, w1v.y);
-          }
-          if (x < x1) {
-            const float2 av = ar[base + x], wv = wr[base + x];
-            c0.add_prod(av.x, av.y, wv.x, wv.y);
-          }
-        }
-      const int a = a0 + ah * 32 + lane;
-      if (a < m) partial[(size_t)(j0 + jb + jl) * m + a] = c0.value() + c1.value();
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Pipelined mixed-form contractions (used when nx is even, so every tile row
-// of 8 doubles starts on a 16-byte boundary).  Persistent CTAs, one per SM,
-// take tiles from a queue; the FP64 data of the next chunk are copied into
-// shared memory with cp.async while the current chunk is computed from its
-// FP32 hi/lo copy.  Every cp.async source is in bounds: out-of-range rows and
-// points copy 0 bytes from a valid address and are zero-filled.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(valid ? 16 : 0));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-#define PGA 64           // rows of A per chunk
-#define PGJ 32           // W rows per tile held in shared memory
-#define PROW (TP + 1)    // padded float2 row (odd in 8-byte units: conflict-free)
-struct PipeSmem {
-  double A64[PGA * TP];   // staged FP64 chunk of A (16-byte chunks)
-  double W64[PGJ * TP];   // staged FP64 W rows of the tile
-  float2 Asp[PGA * PROW];
-  float2 Wsp[PGJ * PROW];
-};
-#define PIPE_SMEM (sizeof(PipeSmem))
-
-// Issue the cp.async copies of rows [a0, a0+PGA) of A at the tile's points.
-__device__ __forceinline__ void stage_rows(double* dst, const double* __restrict__ A, int a0, int m,
-                                           const long long* addr, size_t ng, int nrows) {
-  // 16-byte pieces: row r, points 2q and 2q+1 (same x-row of the tile)
-  for (int idx = threadIdx.x; idx < nrows * (TP / 2); idx += blockDim.x) {
-    const int r = idx / (TP / 2), q = idx % (TP / 2);
-    const long long g = addr[2 * q];
-    const bool ok = (a0 + r < m) && g >= 0;
-    const double* src = ok ? A + (size_t)(a0 + r) * ng + g : A;
-    cp_async16(dst + r * TP + 2 * q, src, ok);
-  }
-}
-
-#define PIPE_THREADS 512
-__device__ __forceinline__ void stage_wrows(double* dst, const double* __restrict__ W,
-                                            const int* wrow, const long long* addr, size_t ng,
-                                            int nrows) {
-  for (int idx = threadIdx.x; idx < nrows * (TP / 2); idx += blockDim.x) {
-    const int r = idx / (TP / 2), q = idx % (TP / 2);
-    const long long g = addr[2 * q];
-    cp_async16(dst + r * TP + 2 * q, g >= 0 ? W + (size_t)wrow[r] * ng + g : W, g >= 0);
-  }
-}
-
-// Split W rows [jb, jb + nj) of tile T's list straight from global memory
-// (used only for tiles whose list is longer than PGJ).
-__device__ __forceinline__ void load_wrows_direct(float2* dst, const double* __restrict__ W,
-                                                  const TileGeom& G, int T, size_t ng,
-                                                  const int* __restrict__ tlist, int j, int nj) {
-  for (int idx = threadIdx.x; idx < nj * TP; idx += blockDim.x) {
-    const int r = idx / TP, pt = idx % TP;
-    const long long g = tile_point(G, T, pt);
-    dst[r * PROW + pt] = split64(g >= 0 ? W[(size_t)tlist[j + r] * ng + g] : 0.0);
-  }
-}
-
-// One warp-uniform pass over units (W row jl < nj, half of the A rows) of
-// the current chunk; lane = A row.
-__device__ __forceinline__ void gram_units(const float2* __restrict__ Asp,
-                                           const float2* __restrict__ Wsp,
-                                           const int* __restrict__ tsub, int jbase, int nj,
-                                           int a0, int m, double* __restrict__ partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int u = warp; u < 2 * nj; u += nwarp) {
-    const int jl = u >> 1, ah = u & 1;
-    const float2* ar = Asp + (ah * 32 + lane) * PROW;
-    const float2* wr = Wsp + jl * PROW;
-    const int sb = tsub[jbase + jl];
-    const int x0 = sb & 15, x1 = (sb >> 4) & 15, y0 = (sb >> 8) & 15, y1 = (sb >> 12) & 15,
-              z0 = (sb >> 16) & 15, z1 = (sb >> 20) & 15;
-    CompF s0, s1;
-    for (int z = z0; z < z1; ++z)
-      for (int y = y0; y < y1; ++y) {
-        const int base = (z * TY + y) * TX;
-        int x = x0;
-        for (; x + 2 <= x1; x += 2) {
-          const float2 a0v = ar[base + x], w0v = wr[base + x];
-          const float2 a1v = ar[base + x + 1], w1v = wr[base + x + 1];
-          s0.add_prod(a0v.x, a0v.y, w0v.x, w0v.y);
-          s1.add_prod(a1v.x, a1v.y, w1v.x, w1v.y);
-        }
-        if (x < x1) {
-          const float2 av = ar[base + x], wv = wr[base + x];
-          s0.add_prod(av.x, av.y, wv.x, wv.y);
-        }
-      }
-    const int a = a0 + ah * 32 + lane;
-    if (a < m) partial[(size_t)(jbase + jl) * m + a] = s0.value() + s1.value();
-  }
-}
-
-// Same result as k_gram_partial_x.  Work item = (tile, chunk of PGA rows of
-// A), taken in order from a queue (tile-major, so consecutive chunks of a
-// tile reuse its W rows); *queue must be 0 at launch.
-__global__ void __launch_bounds__(PIPE_THREADS, 1)
-    k_gram_pipe_x(const double* __restrict__ A, int m, const double* __restrict__ W, TileGeom G,
-                  size_t ng, int n_tiles, const int* __restrict__ tptr,
-                  const int* __restrict__ tlist, const int* __restrict__ tsub,
-                  double* __restrict__ partial, int* __restrict__ queue) {
-  extern __shared__ __align__(16) unsigned char pipe_raw[];
-  PipeSmem& S = *reinterpret_cast<PipeSmem*>(pipe_raw);
-  __shared__ long long addr[TP];
-  __shared__ int wrow[PGJ];
-  __shared__ int s_tile;
-  const int nch = (m + PGA - 1) / PGA;
-
-  // next tile with a non-empty list (>= n_tiles: none left)
-  auto claim = [&]() {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int t;
-      do {
-        t = atomicAdd(queue, 1);
-      } while (t < n_tiles && tptr[t + 1] == tptr[t]);
-      s_tile = t;
-    }
-    __syncthreads();
-    return s_tile;
-  };
-  // addresses and first W block of tile T, then its chunk 0 (one group)
-  auto start_tile = [&](int T) {
-    const int j0 = tptr[T], nj = min(tptr[T + 1] - j0, PGJ);
-    for (int r = threadIdx.x; r < TP; r += blockDim.x) addr[r] = tile_point(G, T, r);
-    if (threadIdx.x < nj) wrow[threadIdx.x] = tlist[j0 + threadIdx.x];
-    __syncthreads();
-    stage_wrows(S.W64, W, wrow, addr, ng, nj);
-    stage_rows(S.A64, A, 0, m, addr, ng, PGA);
-    cp_async_commit();
-  };
-
-  int T = claim();
-  if (T >= n_tiles) return;
-  start_tile(T);
-  int c = 0;
-  for (;;) {
-    const int j0 = tptr[T], nJ = tptr[T + 1] - j0, njb = min(nJ, PGJ);
-    cp_async_wait_all();
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < PGA * TP; idx += blockDim.x)
-      S.Asp[(idx / TP) * PROW + idx % TP] = split64(S.A64[idx]);
-    if (c == 0)
-      for (int idx = threadIdx.x; idx < njb * TP; idx += blockDim.x)
-        S.Wsp[(idx / TP) * PROW + idx % TP] = split64(S.W64[idx]);
-    __syncthreads();
-    // issue the next item's copies; they land while this chunk computes
-    const int cT = T, cc = c;
-    bool more = true;
-    if (c + 1 < nch) {
-      c += 1;
-      stage_rows(S.A64, A, c * PGA, m, addr, ng, PGA);
-      cp_async_commit();
-    } else {
-      T = claim();
-      c = 0;
-      if (T < n_tiles)
-        start_tile(T);
-      else
-        more = false;
-    }
-    const int a0 = cc * PGA;
-    gram_units(S.Asp, S.Wsp, tsub, j0, njb, a0, m, partial);
-    if (nJ > PGJ) {  // long list: the remaining W blocks, synchronously
-      for (int jb = PGJ; jb < nJ; jb += PGJ) {
-        const int nj = min(PGJ, nJ - jb);
-        __syncthreads();
-        load_wrows_direct(S.Wsp, W, G, cT, ng, tlist, j0 + jb, nj);
-        __syncthreads();
-        gram_units(S.Asp, S.Wsp, tsub, j0 + jb, nj, a0, m, partial);
-      }
-      if (more && c > 0) {  // next chunk is of the same tile: first block back
-        __syncthreads();
-        load_wrows_direct(S.Wsp, W, G, cT, ng, tlist, j0, njb);
-      }
-    }
-    if (!more) break;
-    __syncthreads();
-  }
-  cp_async_wait_all();
 }
 
 // Mixed form of k_tile_expand (same splitting and compensated sums).
@@ -978,38 +710,18 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-static TileGeom tile_geom(const sea_ctx* c) {
-  TileGeom G;
-  G.nx = c->N[0];
-  G.ny = c->N[1];
-  G.nz = c->N[2];
-  G.ntx = (G.nx + TX - 1) / TX;
-  G.nty = (G.ny + TY - 1) / TY;
-  G.ntz = (G.nz + TZ - 1) / TZ;
-  return G;
-}
 
-// The contractions with W: FP64 kernels for the plain form, the FP32
-// error-free-transformation kernels for the mixed form.
+// The contractions with W: FP64 kernels for the plain form, the
+// tensor-core kernel (exact BF16 digit splitting) for the mixed form.
 static void launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G, const int* tptr,
                         const int* tlist, const int* tsub) {
-  const dim3 grid(c->n_tiles, (m + GA - 1) / GA);
   const double* W = (const double*)c->vxx_dev.p;
-  const bool pipe = (G.nx % 2 == 0) && ((uintptr_t)A % 16 == 0) && ((uintptr_t)W % 16 == 0);
-  if (c->prm.precision == 1 && pipe) {
-    int* queue = (int*)c->counts.p + 20;
-    cudaMemsetAsync(queue, 0, sizeof(int), c->stream);
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    k_gram_pipe_x<<<min(nsm, c->n_tiles), PIPE_THREADS, PIPE_SMEM, c->stream>>>(
-        A, m, W, G, c->ng, c->n_tiles, tptr, tlist, tsub, (double*)c->partial.p, queue);
-  } else if (c->prm.precision == 1)
-    k_gram_partial_x<<<grid, 256, GRAMX_SMEM, c->stream>>>(A, m, W, G, c->ng, tptr, tlist, tsub,
-                                                           (double*)c->partial.p);
+  if (c->prm.precision == 1)
+    launch_gram_tc(c->stream, c->device, A, m, W, G, c->ng, c->n_tiles, tptr, tlist,
+                   (double*)c->partial.p, (int*)c->counts.p + 20, (unsigned*)c->status.p);
   else
-    k_gram_partial<<<grid, 256, GRAM_SMEM, c->stream>>>(A, m, (const double*)c->vxx_dev.p, G,
-                                                        c->ng, tptr, tlist, tsub,
-                                                        (double*)c->partial.p);
+    k_gram_partial<<<dim3(c->n_tiles, (m + GA - 1) / GA), 256, GRAM_SMEM, c->stream>>>(
+        A, m, W, G, c->ng, tptr, tlist, tsub, (double*)c->partial.p);
 }
 
 static void launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr, const int* tlist,
@@ -1040,7 +752,7 @@ static size_t inv_scratch_doubles(int n) {
 // count on the host to size the partial sums: one stream sync.
 cudaError_t launch_ace_build(sea_ctx* c) {
   const int n = c->n_orb;
-  const TileGeom G = tile_geom(c);
+  const TileGeom G = make_tile_geom(c->N);
   const int nt = G.ntx * G.nty * G.ntz;
   c->n_tiles = nt;
   const long long ninc = (long long)n * nt;
@@ -1104,18 +816,13 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   // M = Phi^T W dV
   err = cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)GRAM_SMEM);
-  if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_gram_partial_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)GRAMX_SMEM);
-  if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(k_gram_pipe_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)PIPE_SMEM);
   if (err != cudaSuccess) return err;
   cudaEventRecord(c->ev[10], c->stream);
   launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
   cudaEventRecord(c->ev[11], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, c->stream>>>(
-      (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p, n, 1);
+      (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
+      n, 1);
   k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
   double* L = (double*)c->Lbuf.p;
@@ -1195,10 +902,11 @@ cudaError_t launch_ace_eigen(sea_ctx* c) {
 
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out) {
   const int n = c->n_orb;
-  const TileGeom G = tile_geom(c);
+  const TileGeom G = make_tile_geom(c->N);
   const int nt = c->n_tiles;
   const int hinc = c->tile_inc;
-  if (!sea_ensure(c, c->partial, (size_t)max(hinc, 1) * max(n, nv) * sizeof(double)) ||
+  if (!sea_ensure(c, c->partial,
+                  (size_t)max(hinc, 1) * max(n, nv) * sizeof(double)) ||
       !sea_ensure(c, c->Gbuf, (size_t)n * nv * sizeof(double)) ||
       !sea_ensure(c, c->Hbuf, (size_t)n * nv * sizeof(double)) ||
       !sea_ensure(c, c->Hbuf2, (size_t)n * nv * sizeof(double)))
@@ -1214,7 +922,8 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
   launch_gram(c, psi, nv, G, tptr, tlist, tsub);
   cudaEventRecord(c->ev[13], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * nv + 255) / 256), 256, 0, c->stream>>>(
-      (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p, 1, nv);
+      (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p,
+      1, nv);
   // H = (-Mbar)^-1 G = L^-T (L^-1 G), or Q |Lambda|^-1 Q^T G in the eigen form
   dim3 gb((nv + 15) / 16, (n + 15) / 16), tb(16, 16);
   if (c->ace_eigen) {
@@ -1241,7 +950,7 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
 
 cudaError_t launch_ace_vectors(sea_ctx* c, double* xi) {
   const int n = c->n_orb;
-  const TileGeom G = tile_geom(c);
+  const TileGeom G = make_tile_geom(c->N);
   const int nt = c->n_tiles;
   const int* tptr = (const int*)c->tptr_t.p + (nt + 1);
   const int* tlist = (const int*)c->tlist_t.p;

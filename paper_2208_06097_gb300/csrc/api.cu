@@ -421,6 +421,8 @@ static sea_status build_ace_common(sea_ctx* c) {
   SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
          "status");
   SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
+  if (st & SEA_FLAG_WAIT)
+    return sea_fail(c, SEA_ERR_CUDA, "a tensor-core completion wait timed out (M build)");
   const bool not_pd = (st & SEA_FLAG_NOT_PD) != 0;
   if ((not_pd && c->prm.ace_decomp == 0) || c->prm.ace_decomp == 2) {
     e = sea::launch_ace_eigen(c);
@@ -521,8 +523,13 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   SEA_CK(cudaEventRecord(c->ev[8], c->stream), "event");
   SEA_CK(cudaEventRecord(ev_out, c->xfer[1]), "event");
   SEA_CK(cudaStreamWaitEvent(c->stream, ev_out, 0), "wait");
+  unsigned st = 0;
+  SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+         "status");
   SEA_CK(cudaStreamSynchronize(c->stream), "apply_ace");
   c->apply_timed = true;
+  if (st & SEA_FLAG_WAIT)
+    return sea_fail(c, SEA_ERR_CUDA, "a tensor-core completion wait timed out (ACE apply)");
   return SEA_OK;
 }
 

@@ -1,0 +1,490 @@
+// gram_tc.cu -- the mixed form's contraction with W on the tensor cores.
+//
+//   partial[s m + a] = sum over the points r of tile T of A[a][r] W[list(T)[s]][r]
+//
+// (s a slot of tile T's W list); the per-orbital sums of M = Phi^T W and of
+// W^T psi add these partials afterwards in FP64.
+//
+// Precision: FP64 operands, FP64-accurate result from BF16 tensor-core
+// products by exact splitting (the Ozaki scheme).  Each row segment x (the
+// 64 points of one half tile, 8 x 4 x 2, of an A row or a W row) shares one
+// exponent E (|x| < 2^E); x 2^-E is truncated to an integer X on a 2^-47
+// grid and written in S = 6 balanced base-256 digits, x 2^-E ~ sum_k d_k
+// 2^(-7-8k) with |d_k| <= 128, each exactly a BF16 value.  For a pair of
+// segments,
+//   sum_r x_r w_r ~ 2^(Ex+Ew) sum_{d=0}^{S-1} 2^(-14-8d) D_d,
+//   D_d = sum_{k+l=d} sum_r dx_k(r) dw_l(r),
+// where every D_d is a sum of at most 6 x 64 products of magnitude <= 2^14,
+// hence an integer below 2^24: the tensor core's FP32 accumulation of it is
+// exact.  The epilogue combines the D_d exactly in 64-bit integers, rounds
+// each half tile once to FP64 and adds the two halves.  Error: the
+// truncation of X (2^-47 of the segment maximum) and the dropped diagonals
+// d >= S (below 2^-45.7 of max|x| max|w| times the segment length).
+//
+// Kernel shape: persistent CTAs (one per SM, 512 threads) take tiles from
+// a queue and walk units (W block of up to 32 slots, A block of 128 rows,
+// half tile).  Per unit the A digits go to shared memory in the tensor
+// core's K-major layout without swizzle (8 x 16-byte core matrices; row
+// groups 128 B apart, x-runs of 8 points one row-group stack apart), one
+// thread issues the tcgen05.mma instructions (M = 128, N = 16 or 32, K = 16)
+// into 6 FP32 accumulators in tensor memory per half (32 columns each), and
+// after the second half all warps read them back with tcgen05.ld for the
+// epilogue.  While a unit's MMAs run, the warps load the next unit's A rows
+// and form their digits in registers (and a new W block's digits in the
+// second W buffer).  Every wait on the MMA completion barrier is bounded:
+// on expiry the kernel sets SEA_FLAG_WAIT, waits once more (bounded) for
+// its MMAs, frees its tensor memory and ends.
+#include "sea_internal.cuh"
+
+namespace sea {
+namespace {
+
+constexpr int DIG = 6;                          // digits per operand
+constexpr int KH = 64;                          // points per half tile
+constexpr int NBLK = 32;                        // W rows per block
+constexpr int MBLK = 128;                       // A rows per block
+constexpr int GT_THREADS = 512;
+constexpr uint32_t A_PLANE = MBLK * KH * 2;     // bytes per digit plane of A
+constexpr uint32_t W_PLANE = NBLK * KH * 2;     // bytes per digit plane of W
+constexpr uint32_t A_LBO = (MBLK / 8) * 128;    // K-adjacent core matrices of A
+constexpr uint32_t W_LBO = (NBLK / 8) * 128;    // K-adjacent core matrices of W
+constexpr uint32_t CORE_SBO = 128;              // row-group-adjacent core matrices
+constexpr uint32_t SMEM_A = DIG * A_PLANE;      // 96 KB
+constexpr uint32_t SMEM_W = 2 * DIG * W_PLANE;  // 48 KB (both halves)
+constexpr size_t GT_SMEM = SMEM_A + 2 * SMEM_W + 128;  // A digits, two W buffers
+constexpr uint32_t TMEM_COLS = 512;             // 12 accumulators x 32 columns used
+constexpr long long WAIT_CYCLES = 2000000000LL; // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MBLK >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for completion `parity` of the barrier.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 4 consecutive FP32 columns of the warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// x 2^-E on the 2^-47 grid (truncated toward zero), E = emax - 1022 for
+// the segment's largest biased exponent emax: a signed integer below 2^47.
+// Integer operations only.
+__device__ __forceinline__ long long fixed47(double v, int emax) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int sh = emax - e + 6;
+  if (e == 0 || sh > 60) return 0;
+  const long long X = (long long)(((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52)) >> sh);
+  return (b >> 63) ? -X : X;
+}
+
+// Balanced base-256 digits of X: with Y = X + 128 (256^0 + ... + 256^4),
+// digit 5 - i = byte i of Y minus 128 (i < 5) and digit 0 = Y >> 40, so
+// X = sum_k d_k 256^(5-k), d_1..d_5 in [-128, 127], |d_0| <= 128.  Each
+// digit as an FP32 value (exact), from the bit pattern 0x4B4000bb = 2^23 +
+// 2^22 + b.
+__device__ __forceinline__ void digit_floats(long long X, float* f) {
+  const long long Y = X + 0x8080808080LL;
+  const unsigned lo = (unsigned)Y, hi = (unsigned)(Y >> 32);
+  const float m = 12582912.0f + 128.0f;
+  f[5] = __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7650)) - m;
+  f[4] = __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7651)) - m;
+  f[3] = __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7652)) - m;
+  f[2] = __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7653)) - m;
+  f[1] = __uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7650)) - m;
+  f[0] = __int_as_float(0x4B400000 + (int)(Y >> 40)) - 12582912.0f;
+}
+
+// BF16 bit patterns of two small integer-valued floats, packed low/high.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// Digits of one row group (8 rows) of a block, half h of tile T, held in
+// registers: the warp's lane l takes row l % 8 and the x-runs u = l / 8 and
+// l / 8 + 4 (run u: y = u % 4, z = 2h + u / 4, 8 points along x).  Row
+// pointer rp (nullptr: zero row).
+struct GroupDigits {
+  uint32_t w[2][DIG][4];  // [run][digit plane][pair of points]
+  int emax;               // the row's largest biased exponent
+};
+
+__device__ __forceinline__ void make_digits(const double* __restrict__ rp, const TileGeom& G,
+                                            int T, int h, GroupDigits& o) {
+  const int lane = threadIdx.x & 31;
+  const int txi = T % G.ntx, tyi = (T / G.ntx) % G.nty, tzi = T / (G.ntx * G.nty);
+  const int gx0 = txi * TX;
+  double v[2][8];
+  int em = 0;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int u = (lane >> 3) + 4 * q;
+    const int gy = tyi * TY + (u & 3), gz = tzi * TZ + 2 * h + (u >> 2);
+    const bool in = rp && gy < G.ny && gz < G.nz;
+    const double* src = in ? rp + ((size_t)gz * G.ny + gy) * G.nx + gx0 : rp;
+    if (in && gx0 + 8 <= G.nx && (((uintptr_t)src) & 15) == 0) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const double2 t = __ldg(reinterpret_cast<const double2*>(src) + p);
+        v[q][2 * p] = t.x;
+        v[q][2 * p + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int x = 0; x < 8; ++x) v[q][x] = (in && gx0 + x < G.nx) ? src[x] : 0.0;
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x)
+      em = max(em, (int)((__double_as_longlong(v[q][x]) >> 52) & 0x7FF));
+  }
+  em = max(em, __shfl_xor_sync(0xffffffffu, em, 8));
+  em = max(em, __shfl_xor_sync(0xffffffffu, em, 16));
+  o.emax = em;
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      float f0[DIG], f1[DIG];
+      digit_floats(fixed47(v[q][2 * p], em), f0);
+      digit_floats(fixed47(v[q][2 * p + 1], em), f1);
+#pragma unroll
+      for (int k = 0; k < DIG; ++k) o.w[q][k][p] = pack_bf16(f0[k], f1[k]);
+    }
+}
+
+// Digit planes of the group to shared memory (core matrices: row group g
+// 128 B apart, run u one lbo apart, row l % 8 at 16 B), and the exponent
+// (lanes 0..7) to emax_row[l % 8].
+__device__ __forceinline__ void store_digits(const GroupDigits& o, unsigned char* plane0,
+                                             uint32_t plane_bytes, uint32_t lbo, int g,
+                                             int* emax_row) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    unsigned char* dst = plane0 + g * CORE_SBO + ((lane >> 3) + 4 * q) * lbo + (lane & 7) * 16;
+#pragma unroll
+    for (int k = 0; k < DIG; ++k)
+      *reinterpret_cast<uint4*>(dst + k * plane_bytes) =
+          make_uint4(o.w[q][k][0], o.w[q][k][1], o.w[q][k][2], o.w[q][k][3]);
+  }
+  if (lane < 8) emax_row[lane] = o.emax;
+}
+
+// Exact value of an integer-valued float below 2^24 in magnitude.
+__device__ __forceinline__ int float_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int e = (int)((u >> 23) & 255);
+  if (e < 127) return 0;
+  const int mag = (int)(((u & 0x7FFFFFu) | 0x800000u) >> (150 - e));
+  return (u >> 31) ? -mag : mag;
+}
+
+// v 2^e2 rounded to the nearest FP64 value (ties to even); 0 if below the
+// normal range.  Integer operations only.
+__device__ __forceinline__ double scaled_i64(long long v, int e2) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ULL;
+  unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned long long mnt = a >> 11;
+  const unsigned rem = (unsigned)(a & 0x7FF);
+  if (rem > 0x400u || (rem == 0x400u && (mnt & 1ULL))) ++mnt;
+  int ex = 63 - lz + e2 + 1023;
+  if (mnt >> 53) {
+    mnt >>= 1;
+    ++ex;
+  }
+  if (ex <= 0) return 0.0;
+  return __longlong_as_double(
+      (long long)(sgn | ((unsigned long long)ex << 52) | (mnt & 0xFFFFFFFFFFFFFULL)));
+}
+
+// A unit of work: half h of A block mb against W block jb of tile T, whose
+// W digits are in buffer wb.
+struct Unit {
+  int T, j0, nJ, jb, mb, h, wb;
+};
+
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    k_gram_tc(const double* __restrict__ A, int m, const double* __restrict__ W, TileGeom G,
+              size_t ng, int n_tiles, const int* __restrict__ tptr, const int* __restrict__ tlist,
+              double* __restrict__ partial, int* __restrict__ queue,
+              unsigned* __restrict__ status) {
+  extern __shared__ unsigned char gt_raw[];
+  unsigned char* sA = gt_raw + ((128 - (smem_addr(gt_raw) & 127)) & 127);
+  unsigned char* sW = sA + SMEM_A;  // two buffers of SMEM_W
+  __shared__ int Aexp[2][MBLK], Wexp[2][2][NBLK];  // [half][row], [buffer][half][row]
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_tile, s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar = smem_addr(&mbar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t a_base = smem_addr(sA), w_base = smem_addr(sW);
+  const int nmb = (m + MBLK - 1) / MBLK;
+
+  // first unit of the next tile with a non-empty list; uniform, contains
+  // __syncthreads (false: no tile left)
+  auto claim = [&](Unit& u) -> bool {
+    __syncthreads();
+    if (tid == 0) {
+      int t;
+      do {
+        t = atomicAdd(queue, 1);
+      } while (t < n_tiles && tptr[t + 1] == tptr[t]);
+      s_tile = t;
+    }
+    __syncthreads();
+    const int T = s_tile;
+    if (T >= n_tiles) return false;
+    u.T = T;
+    u.j0 = tptr[T];
+    u.nJ = tptr[T + 1] - u.j0;
+    u.jb = 0;
+    u.mb = 0;
+    u.h = 0;
+    u.wb ^= 1;
+    return true;
+  };
+  // the unit after u; *new_block: it starts another W block
+  auto advance = [&](Unit& u, bool* new_block) -> bool {
+    *new_block = false;
+    if (u.h == 0) {
+      u.h = 1;
+      return true;
+    }
+    u.h = 0;
+    if (++u.mb < nmb) return true;
+    u.mb = 0;
+    *new_block = true;
+    u.jb += NBLK;
+    if (u.jb < u.nJ) {
+      u.wb ^= 1;
+      return true;
+    }
+    return claim(u);
+  };
+  auto a_row = [&](const Unit& u) -> const double* {
+    const int a = u.mb * MBLK + 8 * warp + (lane & 7);
+    return a < m ? A + (size_t)a * ng : nullptr;
+  };
+  // W digits of u's block (both halves) into buffer u.wb: warps 0..7
+  auto split_w = [&](const Unit& u) {
+    if (warp < 8) {
+      const int g = warp & 3, h = warp >> 2;
+      const int s = 8 * g + (lane & 7);
+      const int nj = min(NBLK, u.nJ - u.jb);
+      const double* rp = s < nj ? W + (size_t)tlist[u.j0 + u.jb + s] * ng : nullptr;
+      GroupDigits d;
+      make_digits(rp, G, u.T, h, d);
+      store_digits(d, sW + (u.wb * 2 + h) * DIG * W_PLANE, W_PLANE, W_LBO, g,
+                   &Wexp[u.wb][h][8 * g]);
+    }
+  };
+  // partials of u's A block (both halves done): warp = (lane quarter,
+  // column group of 8 W slots)
+  auto epilogue = [&](const Unit& u) {
+    const int nj = min(NBLK, u.nJ - u.jb);
+    const int quarter = warp & 3, cg = warp >> 2;
+    if (cg * 8 >= nj) return;
+    const int a = u.mb * MBLK + 32 * quarter + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+#pragma unroll 1
+    for (int c0 = cg * 8; c0 < cg * 8 + 8 && c0 < nj; c0 += 4) {
+      double sum[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        long long acc[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIG; ++d) {
+          float f[4];
+          tmem_ld4(lane_addr + (uint32_t)((h * DIG + d) * 32 + c0), f);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[c] += (long long)float_int(f[c]) << (8 * (DIG - 1 - d));
+        }
+        const int ea = Aexp[h][32 * quarter + lane] - 1022;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c0 + c < nj) sum[c] += scaled_i64(acc[c], ea + (Wexp[u.wb][h][c0 + c] - 1022) - 54);
+      }
+      if (a < m) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c0 + c < nj) partial[(size_t)(u.j0 + u.jb + c0 + c) * m + a] = sum[c];
+      }
+    }
+  };
+
+  Unit cur;
+  cur.wb = 1;
+  if (claim(cur)) {
+    split_w(cur);
+    GroupDigits dg;
+    make_digits(a_row(cur), G, cur.T, cur.h, dg);
+    Unit prev = cur;
+    bool have_prev = false;
+    uint32_t phase = 0;
+    for (;;) {
+      if (have_prev) {
+        // prev's MMAs done: the A digits and the accumulators are free
+        const bool ok = mbar_wait(bar, phase);
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        phase ^= 1;
+        tc_fence_after();
+        if (prev.h == 1) {
+          epilogue(prev);
+          __syncthreads();  // the exponents are read before they are replaced
+        }
+      }
+      store_digits(dg, sA, A_PLANE, A_LBO, warp, &Aexp[cur.h][8 * warp]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        // descriptors differ only in the start address (low 14 bits, no
+        // carry: shared addresses are below 2^18)
+        const int nj = min(NBLK, cur.nJ - cur.jb);
+        const uint32_t id = idesc_bf16(nj <= 16 ? 16 : 32);
+        const uint64_t a0 = sdesc(a_base, A_LBO, CORE_SBO);
+        const uint64_t w0 =
+            sdesc(w_base + cur.wb * SMEM_W + cur.h * DIG * W_PLANE, W_LBO, CORE_SBO);
+        // consecutive MMAs go to different accumulators (diagonals d), so
+        // they do not wait on one another
+#pragma unroll
+        for (int q = 0; q < KH / 16; ++q)
+#pragma unroll
+          for (int k = 0; k < DIG; ++k)
+#pragma unroll
+            for (int d = k; d < DIG; ++d)
+              mma_bf16(tmem + (uint32_t)((cur.h * DIG + d) * 32),
+                       a0 + ((k * A_PLANE + q * 2 * A_LBO) >> 4),
+                       w0 + (((d - k) * W_PLANE + q * 2 * W_LBO) >> 4), id,
+                       (k > 0 || q > 0) ? 1u : 0u);
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+            : "memory");
+      }
+      prev = cur;
+      have_prev = true;
+      // while the MMAs run: the next unit's W digits (a new block goes to
+      // the other buffer, whose MMAs are done) and A digits
+      bool new_block;
+      if (!advance(cur, &new_block)) break;
+      if (new_block) split_w(cur);
+      make_digits(a_row(cur), G, cur.T, cur.h, dg);
+    }
+    // the last unit: its MMAs (bounded wait) and epilogue
+    if (!s_fail) {
+      const bool ok = mbar_wait(bar, phase);
+      if (!ok) s_fail = 1;
+      __syncthreads();
+      if (!s_fail) {
+        tc_fence_after();
+        if (prev.h == 1) epilogue(prev);
+      }
+    }
+    if (s_fail) mbar_wait(bar, phase);  // once more, bounded, before freeing
+  }
+  if (s_fail && tid == 0) atomicOr(status, SEA_FLAG_WAIT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
+}  // namespace
+
+
+cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const double* W,
+                           const TileGeom& G, size_t ng, int n_tiles, const int* tptr,
+                           const int* tlist, double* partial, int* queue, unsigned* status) {
+  static bool attr_set[64] = {};
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[device]) {
+    const cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)GT_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[device] = true;
+  }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_gram_tc<<<std::min(nsm, std::max(n_tiles, 1)), GT_THREADS, GT_SMEM, st>>>(
+      A, m, W, G, ng, n_tiles, tptr, tlist, partial, queue, status);
+  return cudaGetLastError();
+}
+
+}  // namespace sea

@@ -21,6 +21,7 @@
 #define SEA_FLAG_NOT_PD 2u
 #define SEA_FLAG_BOUNDS 4u
 #define SEA_FLAG_NONFINITE 8u
+#define SEA_FLAG_WAIT 16u  // a bounded wait on a tensor-core completion expired
 
 // At most this many chunks per pipelined host-buffer call.
 #define SEA_XCHUNKS_MAX 64
@@ -151,6 +152,40 @@ struct SeaBuf {
   size_t bytes = 0;
 };
 
+namespace sea {
+
+// Grid tiles of the ACE contractions: 8 x 4 x 4 points, point r of a tile
+// at x = r % 8, y = (r / 8) % 4, z = r / 32 inside it.
+#define TX 8
+#define TY 4
+#define TZ 4
+#define TP (TX * TY * TZ)
+
+struct TileGeom {
+  int nx, ny, nz, ntx, nty, ntz;
+};
+
+// Flat grid index of point r of tile T (-1 outside the grid).
+__device__ __forceinline__ long long tile_point(const TileGeom& G, int T, int r) {
+  const int txi = T % G.ntx, tyi = (T / G.ntx) % G.nty, tzi = T / (G.ntx * G.nty);
+  const int x = txi * TX + (r % TX), y = tyi * TY + (r / TX) % TY, z = tzi * TZ + r / (TX * TY);
+  if (x >= G.nx || y >= G.ny || z >= G.nz) return -1;
+  return ((long long)z * G.ny + y) * G.nx + x;
+}
+
+inline TileGeom make_tile_geom(const int N[3]) {
+  TileGeom G;
+  G.nx = N[0];
+  G.ny = N[1];
+  G.nz = N[2];
+  G.ntx = (G.nx + TX - 1) / TX;
+  G.nty = (G.ny + TY - 1) / TY;
+  G.ntz = (G.nz + TZ - 1) / TZ;
+  return G;
+}
+
+}  // namespace sea
+
 struct sea_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -234,6 +269,11 @@ cudaError_t launch_accumulate(sea_ctx* c, double* out);
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
                                     int e_end);
 cudaError_t launch_exx(sea_ctx* c);
+// Tensor-core contraction of A rows with W over W's tiles (mixed form):
+// partial[slot m + a]; *queue is reset on the stream.
+cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const double* W,
+                           const TileGeom& G, size_t ng, int n_tiles, const int* tptr,
+                           const int* tlist, double* partial, int* queue, unsigned* status);
 cudaError_t launch_ace_build(sea_ctx* c);
 cudaError_t launch_ace_eigen(sea_ctx* c);
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int n_vec, double* out);
