@@ -717,8 +717,9 @@ static void launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G, c
                         const int* tlist, const int* tsub) {
   const double* W = (const double*)c->vxx_dev.p;
   if (c->prm.precision == 1)
-    launch_gram_tc(c->stream, c->device, A, m, W, G, c->ng, c->n_tiles, tptr, tlist,
-                   (double*)c->partial.p, (int*)c->counts.p + 20, (unsigned*)c->status.p);
+    launch_gram_tc(c->stream, c->device, A, m, G, c->ng, c->n_tiles, tptr, c->tile_inc,
+                   c->wdig.p, (double*)c->partial.p, (int*)c->counts.p + 20,
+                   (unsigned*)c->status.p);
   else
     k_gram_partial<<<dim3(c->n_tiles, (m + GA - 1) / GA), 256, GRAM_SMEM, c->stream>>>(
         A, m, W, G, c->ng, tptr, tlist, tsub, (double*)c->partial.p);
@@ -817,6 +818,13 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   err = cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)GRAM_SMEM);
   if (err != cudaSuccess) return err;
+  if (c->prm.precision == 1) {  // W's digits for the tensor-core contractions
+    if (!sea_ensure(c, c->wdig, w_digits_bytes(hinc))) return cudaErrorMemoryAllocation;
+    err = launch_w_digits(c->stream, (const double*)c->vxx_dev.p, G, c->ng, nt, c->max_tile_list,
+                          tptr, tlist, hinc, c->wdig.p);
+    if (err != cudaSuccess) return err;
+    c->launches += 1;
+  }
   cudaEventRecord(c->ev[10], c->stream);
   launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
   cudaEventRecord(c->ev[11], c->stream);

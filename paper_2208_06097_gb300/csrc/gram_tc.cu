@@ -25,11 +25,14 @@
 // a queue and walk units (W block of up to 32 slots, A block of 128 rows,
 // half tile).  Per unit the A digits go to shared memory in the tensor
 // core's K-major layout without swizzle (8 x 16-byte core matrices; row
-// groups 128 B apart, x-runs of 8 points one row-group stack apart), one
-// thread issues the tcgen05.mma instructions (M = 128, N = 16 or 32, K = 16)
-// into 6 FP32 accumulators in tensor memory per half (32 columns each), and
-// after the second half all warps read them back with tcgen05.ld for the
-// epilogue.  While a unit's MMAs run, the warps load the next unit's A rows
+// groups 128 B apart, x-runs of 8 points one row-group stack apart).  W's
+// digit planes of the block are stacked along N (plane l at rows l P, P =
+// 16 or 32 the padded block width) and the accumulator of diagonal d sits
+// at tensor-memory columns d P, so one MMA of A plane k against the stacked
+// W planes 0..5-k (N = (6 - k) P) adds every product of plane k to the
+// diagonals k..5 at once: 24 tcgen05.mma instructions (M = 128, K = 16) per
+// unit, issued by one thread.  After the second half all warps read the
+// accumulators back with tcgen05.ld for the epilogue.  While a unit's MMAs run, the warps load the next unit's A rows
 // and form their digits in registers (and a new W block's digits in the
 // second W buffer).  Every wait on the MMA completion barrier is bounded:
 // on expiry the kernel sets SEA_FLAG_WAIT, waits once more (bounded) for
@@ -45,14 +48,14 @@ constexpr int NBLK = 32;                        // W rows per block
 constexpr int MBLK = 128;                       // A rows per block
 constexpr int GT_THREADS = 512;
 constexpr uint32_t A_PLANE = MBLK * KH * 2;     // bytes per digit plane of A
-constexpr uint32_t W_PLANE = NBLK * KH * 2;     // bytes per digit plane of W
+constexpr uint32_t W_HALF = DIG * NBLK * KH * 2;  // bytes of W digits per half tile
 constexpr uint32_t A_LBO = (MBLK / 8) * 128;    // K-adjacent core matrices of A
-constexpr uint32_t W_LBO = (NBLK / 8) * 128;    // K-adjacent core matrices of W
 constexpr uint32_t CORE_SBO = 128;              // row-group-adjacent core matrices
 constexpr uint32_t SMEM_A = DIG * A_PLANE;      // 96 KB
-constexpr uint32_t SMEM_W = 2 * DIG * W_PLANE;  // 48 KB (both halves)
+constexpr uint32_t SMEM_W = 2 * W_HALF;         // 48 KB (both halves)
 constexpr size_t GT_SMEM = SMEM_A + 2 * SMEM_W + 128;  // A digits, two W buffers
-constexpr uint32_t TMEM_COLS = 512;             // 12 accumulators x 32 columns used
+constexpr uint32_t TMEM_HALF = DIG * NBLK;      // accumulator columns per half tile
+constexpr uint32_t TMEM_COLS = 512;             // 2 x 192 columns used
 constexpr long long WAIT_CYCLES = 2000000000LL; // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -105,15 +108,22 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// 4 consecutive FP32 columns of the warp's 32 tensor-memory lanes.
-__device__ __forceinline__ void tmem_ld4(uint32_t addr, float* v) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
+// One FP32 column of the warp's 32 tensor-memory lanes (no wait).
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t addr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(addr));
+  return r;
+}
+__device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // x 2^-E on the 2^-47 grid (truncated toward zero), E = emax - 1022 for
@@ -250,16 +260,47 @@ __device__ __forceinline__ double scaled_i64(long long v, int e2) {
       (long long)(sgn | ((unsigned long long)ex << 52) | (mnt & 0xFFFFFFFFFFFFFULL)));
 }
 
+// W digits, once per W: for every slot s of every tile list and half h,
+// wdig[((s * 2 + h) * DIG + k) * 8 + u] = the 8 BF16 digits (16 bytes) of
+// plane k, x-run u of W row list[s] on that half tile, and wexp[2 s + h]
+// the row segment's largest biased exponent.  Warp per (tile, half, group
+// of 8 slots).
+__global__ void __launch_bounds__(256)
+    k_w_digits(const double* __restrict__ W, TileGeom G, size_t ng, int n_tiles, int ngroups,
+               const int* __restrict__ tptr, const int* __restrict__ tlist, uint4* __restrict__ wdig,
+               int* __restrict__ wexp) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (long long)n_tiles * 2 * ngroups) return;  // warp-uniform
+  const int g = (int)(gw % ngroups), h = (int)((gw / ngroups) % 2), T = (int)(gw / (2 * ngroups));
+  const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
+  if (8 * g >= nJ) return;  // warp-uniform
+  const int lane = threadIdx.x & 31, r = lane & 7, s = 8 * g + r;
+  const double* rp = s < nJ ? W + (size_t)tlist[j0 + s] * ng : nullptr;
+  GroupDigits d;
+  make_digits(rp, G, T, h, d);
+  if (s < nJ) {
+    uint4* dst = wdig + ((size_t)(j0 + s) * 2 + h) * DIG * 8;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int u = (lane >> 3) + 4 * q;
+#pragma unroll
+      for (int k = 0; k < DIG; ++k) dst[k * 8 + u] = make_uint4(d.w[q][k][0], d.w[q][k][1], d.w[q][k][2], d.w[q][k][3]);
+    }
+    if (lane < 8) wexp[(size_t)(j0 + s) * 2 + h] = d.emax;
+  }
+}
+
 // A unit of work: half h of A block mb against W block jb of tile T, whose
 // W digits are in buffer wb.
 struct Unit {
   int T, j0, nJ, jb, mb, h, wb;
 };
 
+
 __global__ void __launch_bounds__(GT_THREADS, 1)
-    k_gram_tc(const double* __restrict__ A, int m, const double* __restrict__ W, TileGeom G,
-              size_t ng, int n_tiles, const int* __restrict__ tptr, const int* __restrict__ tlist,
-              double* __restrict__ partial, int* __restrict__ queue,
+    k_gram_tc(const double* __restrict__ A, int m, TileGeom G, size_t ng, int n_tiles,
+              const int* __restrict__ tptr, const uint4* __restrict__ wdig,
+              const int* __restrict__ wexp, double* __restrict__ partial, int* __restrict__ queue,
               unsigned* __restrict__ status) {
   extern __shared__ unsigned char gt_raw[];
   unsigned char* sA = gt_raw + ((128 - (smem_addr(gt_raw) & 127)) & 127);
@@ -334,57 +375,79 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     const int a = u.mb * MBLK + 8 * warp + (lane & 7);
     return a < m ? A + (size_t)a * ng : nullptr;
   };
-  // W digits of u's block (both halves) into buffer u.wb: warps 0..7
-  auto split_w = [&](const Unit& u) {
-    if (warp < 8) {
-      const int g = warp & 3, h = warp >> 2;
-      const int s = 8 * g + (lane & 7);
-      const int nj = min(NBLK, u.nJ - u.jb);
-      const double* rp = s < nj ? W + (size_t)tlist[u.j0 + u.jb + s] * ng : nullptr;
-      GroupDigits d;
-      make_digits(rp, G, u.T, h, d);
-      store_digits(d, sW + (u.wb * 2 + h) * DIG * W_PLANE, W_PLANE, W_LBO, g,
-                   &Wexp[u.wb][h][8 * g]);
+  // W digits of u's block (both halves) into buffer u.wb, planes stacked
+  // along N with row stride P (16 or 32): row l P + slot of half h at core
+  // matrix (row / 8, run), K-adjacent ones 6 P 16 bytes apart.  16-byte
+  // asynchronous copies, zeros beyond the list (completed before the next
+  // __syncthreads that precedes the MMAs reading them).
+  auto load_w = [&](const Unit& u) {
+    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+    const uint32_t lbo = DIG * P * 16;
+    const uint32_t dst0 = w_base + u.wb * SMEM_W;
+    for (int p = tid; p < P * 2 * DIG * 8; p += GT_THREADS) {
+      const int run = p & 7, k = (p >> 3) % DIG, h = (p / (8 * DIG)) & 1, sl = p / (16 * DIG);
+      const bool ok = sl < nj;
+      const uint4* src = ok ? wdig + ((size_t)(u.j0 + u.jb + sl) * 2 + h) * DIG * 8 + k * 8 + run : wdig;
+      const int row = k * P + sl;
+      cp_async16(dst0 + h * W_HALF + (row >> 3) * CORE_SBO + run * lbo + (row & 7) * 16, src, ok);
+    }
+    if (tid < 2 * NBLK) {
+      const int h = tid / NBLK, sl = tid % NBLK;
+      Wexp[u.wb][h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
     }
   };
-  // partials of u's A block (both halves done): warp = (lane quarter,
-  // column group of 8 W slots)
+  // partials of u's A block (both halves done): warp = (lane quarter q,
+  // column class g), columns g, g + 4, ... of the block
   auto epilogue = [&](const Unit& u) {
-    const int nj = min(NBLK, u.nJ - u.jb);
-    const int quarter = warp & 3, cg = warp >> 2;
-    if (cg * 8 >= nj) return;
+    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+    const int quarter = warp & 3, g = warp >> 2;
     const int a = u.mb * MBLK + 32 * quarter + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+    const int ea0 = Aexp[0][32 * quarter + lane] - 1022, ea1 = Aexp[1][32 * quarter + lane] - 1022;
 #pragma unroll 1
-    for (int c0 = cg * 8; c0 < cg * 8 + 8 && c0 < nj; c0 += 4) {
-      double sum[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = g; c < nj; c += 4) {
+      uint32_t f[2 * DIG];
+#pragma unroll
+      for (int q = 0; q < 2 * DIG; ++q)
+        f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
+      tmem_wait_ld();
+      double sum = 0.0;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        long long acc[4] = {0, 0, 0, 0};
+        long long acc = 0;
 #pragma unroll
-        for (int d = 0; d < DIG; ++d) {
-          float f[4];
-          tmem_ld4(lane_addr + (uint32_t)((h * DIG + d) * 32 + c0), f);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[c] += (long long)float_int(f[c]) << (8 * (DIG - 1 - d));
-        }
-        const int ea = Aexp[h][32 * quarter + lane] - 1022;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c0 + c < nj) sum[c] += scaled_i64(acc[c], ea + (Wexp[u.wb][h][c0 + c] - 1022) - 54);
+        for (int d = 0; d < DIG; ++d)
+          acc += (long long)float_int(__uint_as_float(f[h * DIG + d])) << (8 * (DIG - 1 - d));
+        sum += scaled_i64(acc, (h ? ea1 : ea0) + (Wexp[u.wb][h][c] - 1022) - 54);
       }
-      if (a < m) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c0 + c < nj) partial[(size_t)(u.j0 + u.jb + c0 + c) * m + a] = sum[c];
-      }
+      if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = sum;
     }
+  };
+  // the MMAs of unit u (half u.h), then the commit: for K step q and A
+  // plane k, one MMA against W planes 0..5-k into diagonals k..5
+  auto issue = [&](const Unit& u) {
+    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+    const uint32_t lbo = DIG * P * 16;
+    // descriptors differ only in the start address (low 14 bits, no
+    // carry: shared addresses are below 2^18)
+    const uint64_t a0 = sdesc(a_base, A_LBO, CORE_SBO);
+    const uint64_t w0 = sdesc(w_base + u.wb * SMEM_W + u.h * W_HALF, lbo, CORE_SBO);
+    const uint32_t dcol = tmem + (uint32_t)(u.h * TMEM_HALF);
+#pragma unroll
+    for (int q = 0; q < KH / 16; ++q)
+#pragma unroll
+      for (int k = 0; k < DIG; ++k)
+        mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A_PLANE + q * 2 * A_LBO) >> 4),
+                 w0 + ((q * 2 * lbo) >> 4), idesc_bf16((DIG - k) * P), (k > 0 || q > 0) ? 1u : 0u);
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
   };
 
   Unit cur;
   cur.wb = 1;
   if (claim(cur)) {
-    split_w(cur);
+    load_w(cur);
     GroupDigits dg;
     make_digits(a_row(cur), G, cur.T, cur.h, dg);
     Unit prev = cur;
@@ -405,41 +468,19 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
         }
       }
       store_digits(dg, sA, A_PLANE, A_LBO, warp, &Aexp[cur.h][8 * warp]);
+      cp_async_wait_all();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
-      if (tid == 0) {
-        // descriptors differ only in the start address (low 14 bits, no
-        // carry: shared addresses are below 2^18)
-        const int nj = min(NBLK, cur.nJ - cur.jb);
-        const uint32_t id = idesc_bf16(nj <= 16 ? 16 : 32);
-        const uint64_t a0 = sdesc(a_base, A_LBO, CORE_SBO);
-        const uint64_t w0 =
-            sdesc(w_base + cur.wb * SMEM_W + cur.h * DIG * W_PLANE, W_LBO, CORE_SBO);
-        // consecutive MMAs go to different accumulators (diagonals d), so
-        // they do not wait on one another
-#pragma unroll
-        for (int q = 0; q < KH / 16; ++q)
-#pragma unroll
-          for (int k = 0; k < DIG; ++k)
-#pragma unroll
-            for (int d = k; d < DIG; ++d)
-              mma_bf16(tmem + (uint32_t)((cur.h * DIG + d) * 32),
-                       a0 + ((k * A_PLANE + q * 2 * A_LBO) >> 4),
-                       w0 + (((d - k) * W_PLANE + q * 2 * W_LBO) >> 4), id,
-                       (k > 0 || q > 0) ? 1u : 0u);
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-            : "memory");
-      }
+      if (tid == 0) issue(cur);
       prev = cur;
       have_prev = true;
       // while the MMAs run: the next unit's W digits (a new block goes to
       // the other buffer, whose MMAs are done) and A digits
       bool new_block;
       if (!advance(cur, &new_block)) break;
-      if (new_block) split_w(cur);
+      if (new_block) load_w(cur);
       make_digits(a_row(cur), G, cur.T, cur.h, dg);
     }
     // the last unit: its MMAs (bounded wait) and epilogue
@@ -454,6 +495,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     }
     if (s_fail) mbar_wait(bar, phase);  // once more, bounded, before freeing
   }
+  cp_async_wait_all();
   if (s_fail && tid == 0) atomicOr(status, SEA_FLAG_WAIT);
   tc_fence_before();
   __syncthreads();
@@ -467,9 +509,27 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 }  // namespace
 
 
-cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const double* W,
-                           const TileGeom& G, size_t ng, int n_tiles, const int* tptr,
-                           const int* tlist, double* partial, int* queue, unsigned* status) {
+size_t w_digits_bytes(long long slots) {
+  return (size_t)std::max(slots, 1LL) * 2 * DIG * 8 * sizeof(uint4) +
+         (size_t)std::max(slots, 1LL) * 2 * sizeof(int);
+}
+
+cudaError_t launch_w_digits(cudaStream_t st, const double* W, const TileGeom& G, size_t ng,
+                            int n_tiles, int max_list, const int* tptr, const int* tlist,
+                            long long slots, void* wbuf) {
+  if (n_tiles <= 0 || max_list <= 0) return cudaSuccess;
+  uint4* wdig = (uint4*)wbuf;
+  int* wexp = (int*)(wdig + (size_t)std::max(slots, 1LL) * 2 * DIG * 8);
+  const int ngroups = (max_list + 7) / 8;
+  const long long warps = (long long)n_tiles * 2 * ngroups;
+  k_w_digits<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(W, G, ng, n_tiles, ngroups, tptr, tlist,
+                                                          wdig, wexp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const TileGeom& G,
+                           size_t ng, int n_tiles, const int* tptr, long long slots,
+                           const void* wbuf, double* partial, int* queue, unsigned* status) {
   static bool attr_set[64] = {};
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[device]) {
@@ -478,12 +538,14 @@ cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, 
     if (e != cudaSuccess) return e;
     attr_set[device] = true;
   }
+  const uint4* wdig = (const uint4*)wbuf;
+  const int* wexp = (const int*)(wdig + (size_t)std::max(slots, 1LL) * 2 * DIG * 8);
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   k_gram_tc<<<std::min(nsm, std::max(n_tiles, 1)), GT_THREADS, GT_SMEM, st>>>(
-      A, m, W, G, ng, n_tiles, tptr, tlist, partial, queue, status);
+      A, m, G, ng, n_tiles, tptr, wdig, wexp, partial, queue, status);
   return cudaGetLastError();
 }
 

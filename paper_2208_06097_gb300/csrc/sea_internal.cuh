@@ -222,6 +222,7 @@ struct sea_ctx {
   SeaBuf eptr, eent, ewin, coff, cbuf;
   SeaBuf status, exx_dev, queue;
   // ACE
+  SeaBuf wdig;  // the mixed form's W digits (tensor-core contraction)
   SeaBuf tmask, tptr_o, tlist_o, tslot_o, tptr_t, tlist_t, partial, Mbuf, Abuf, Lbuf, Linv,
       Gbuf, Hbuf, Hbuf2;
   int n_tiles = 0, tile_inc = 0, max_tile_list = 0;
@@ -269,11 +270,17 @@ cudaError_t launch_accumulate(sea_ctx* c, double* out);
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
                                     int e_end);
 cudaError_t launch_exx(sea_ctx* c);
-// Tensor-core contraction of A rows with W over W's tiles (mixed form):
-// partial[slot m + a]; *queue is reset on the stream.
-cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const double* W,
-                           const TileGeom& G, size_t ng, int n_tiles, const int* tptr,
-                           const int* tlist, double* partial, int* queue, unsigned* status);
+// Mixed form's contraction with W on the tensor cores.  launch_w_digits
+// splits W's rows on every tile of every list once into wbuf
+// (w_digits_bytes(slots), slots = total list length); launch_gram_tc then
+// forms partial[slot m + a] for A's m rows.  *queue is reset on the stream.
+size_t w_digits_bytes(long long slots);
+cudaError_t launch_w_digits(cudaStream_t st, const double* W, const TileGeom& G, size_t ng,
+                            int n_tiles, int max_list, const int* tptr, const int* tlist,
+                            long long slots, void* wbuf);
+cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const TileGeom& G,
+                           size_t ng, int n_tiles, const int* tptr, long long slots,
+                           const void* wbuf, double* partial, int* queue, unsigned* status);
 cudaError_t launch_ace_build(sea_ctx* c);
 cudaError_t launch_ace_eigen(sea_ctx* c);
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int n_vec, double* out);
