@@ -122,6 +122,18 @@ def job_value(steps, ws, t_ms_max):
     return ws * steps / (t_ms_max / 1e3)
 
 
+def _tiles_with_support(w, torch):
+    """Number of 8 x 4 x 4 grid tiles on which some row of W is nonzero (the
+    tiles the contraction with W reads A on)."""
+    n, nz, ny, nx = w.shape
+    pz, py, px = (-nz) % 4, (-ny) % 4, (-nx) % 8
+    nzmask = (w != 0).any(dim=0).to(torch.float32)
+    if pz or py or px:
+        nzmask = torch.nn.functional.pad(nzmask, (0, px, 0, py, 0, pz))
+    t = nzmask.reshape((nz + pz) // 4, 4, (ny + py) // 4, 4, (nx + px) // 8, 8)
+    return int((t.sum(dim=(1, 3, 5)) > 0).sum().item())
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -214,6 +226,7 @@ def run_ours(args, ws, rank, local):
     R = res[chosen]
     ctx = R["ctx"]
     nnz_w = int((vxx != 0).sum().item())  # exact support of W (outside the timed region)
+    tiles_w = _tiles_with_support(vxx, torch)
 
     # e2e: host buffers through the C ABI, copies inside the timed region
     phi_pin = torch.from_numpy(s.phi).pin_memory().numpy()
@@ -276,15 +289,34 @@ def run_ours(args, ws, rank, local):
         cand.append(("k_tile_expand (FP64 W H over W's tiles)", sm["expand_apply"], 1,
                      2.0 * N_TRIAL * nnz_w, FP64_PEAK_TFLOPS, "alu", note))
     else:
+        hbm = float(_peaks().get("hbm_gbs", 6800.0))  # GB/s, measured copy
+        note_cg = ("HBM of measured (copy, MEASURED_PEAKS.json); effective model bytes: 11 vector "
+                   "passes x 4 B per unknown and FP32 inner iteration (the pair vectors stay "
+                   "on chip, so DRAM traffic is lower)")
+        cand.append(("k_cg_mixed (FP32 CG sweeps inside FP64 refinement)", sm["cg"], 1,
+                     44.0 * R["cg_unknown_iters"], hbm, "hbm", note_cg))
+        note_gt = ("HBM of measured (copy); algorithmic bytes: the A rows on the tiles where W is "
+                   "nonzero (8 B per point), W's BF16 digit planes (1536 B per tile slot and "
+                   "128-row block), the FP64 partials written")
+        slots = st["ace_support_points"] / 128  # total W list length over the tiles
+        gram_bytes = (n * 128 * 8.0 * tiles_w + 1536.0 * slots * ((n + 127) // 128) +
+                      8.0 * slots * n)
+        cand.append(("k_gram_tc (tensor-core M = Phi^T W and W^T psi, exact BF16 digits)",
+                     gram_ms, 2, gram_bytes, hbm, "hbm", note_gt))
         note = ("FP32 issue from unit counts: 152 SMs x 128 lanes x 2.07 GHz = 40.3 T op/s; "
                 "work = rows x nonzeros of W products x 13 FP32 operations per FP64-accurate "
                 "product (error-free transformation)")
-        cand.append(("k_gram_pipe_x (mixed M = Phi^T W and W^T psi, FP32 error-free products)",
-                     gram_ms, 2, EFT_OPS_PER_PRODUCT * n * nnz_w, FP32_PEAK_TOPS, "alu", note))
         cand.append(("k_tile_expand_x (mixed W H, FP32 error-free products)", sm["expand_apply"],
                      1, EFT_OPS_PER_PRODUCT * N_TRIAL * nnz_w, FP32_PEAK_TOPS, "alu", note))
-    name, kms, nl, flops, peak, bound, peak_note = max(cand, key=lambda c: c[1] * c[2])
-    achieved = flops / (kms / 1e3) / 1e12 if kms > 0 else 0.0
+    def _rate(c):  # work per launch / time: flop -> TFLOP/s, bytes -> GB/s
+        return c[3] / (c[1] / 1e3) / (1e9 if c[5] == "hbm" else 1e12) if c[1] > 0 else 0.0
+
+    top = max(cand, key=lambda c: c[1] * c[2])
+    name, kms, nl, flops, peak, bound, peak_note = top
+    achieved = _rate(top)
+    others = [{"kernel": c[0], "bound": c[5], "ms_per_step": c[1] * c[2], "achieved": _rate(c),
+               "peak": c[4], "unit": "GB/s" if c[5] == "hbm" else "TFLOP/s",
+               "frac": _rate(c) / c[4]} for c in cand if c is not top]
     cpu = cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline) else None
     batched = run_batched(args, sea, torch, dev) if (ws == 1 and not args.no_batched) else None
     line = {
@@ -329,10 +361,11 @@ def run_ours(args, ws, rank, local):
             "bound": bound,
             "achieved": achieved,
             "peak": peak,
-            "unit": "TFLOP/s",
+            "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
             "frac": achieved / peak,
             "traffic": None,
             "peak_note": peak_note,
+            "other_kernels": others,
         },
         "clocks": R["clocks"],
     }

@@ -68,7 +68,9 @@ typedef enum {
  * when a Cholesky pivot is not positive), precision = 0 (FP64 everywhere; 1: the mixed form --
  * FP32 stencil sweeps and CG vectors inside an FP64 iterative refinement of
  * each pair's solve: true residual, its norm, the stopping rule, dot
- * products across the block, E_xx and the ACE stay FP64), warm_start = 0. */
+ * products across the block, E_xx and the ACE stay FP64), warm_start = 0
+ * (1: every pair's CG starts from the attached learned model's guess and
+ * runs to the same tolerance; the batched form always starts from zero). */
 typedef struct {
   double eps;
   double delta;
@@ -79,7 +81,7 @@ typedef struct {
   int fd_order;   /* 12 */
   double self_scale;
   int precision;  /* 0: FP64, 1: mixed (FP32 CG inside FP64 refinement) */
-  int warm_start; /* 0: none */
+  int warm_start; /* 0: none; 1: the attached sea_unet's guesses (sea_unet_attach) */
   double timeout_ms; /* reserved, 0 */
   int ace_decomp; /* 0: Cholesky, eigen form of App. A if a pivot fails;
                      1: Cholesky only (SEA_ERR_NOT_PD on failure); 2: eigen form */
@@ -227,6 +229,53 @@ sea_status sea_poisson_batch(const double h[3], int n_box, const int* ext, const
 sea_status sea_poisson_batch_noalloc(const double h[3], int n_box, const int* ext,
                                      const double* rhs, double* x, double tol, int tol_mode,
                                      int max_iter, int* iters, void* cuda_stream);
+
+/* Learned warm start for the pair solves (the paper has no counterpart:
+ * its CG starts from zero; this changes only the starting point).  A 3-level
+ * 3D U-Net (width c: 16/32/64 channels for c = 16) maps a pair's
+ * right-hand side b of -Lap_h v = b (Eq. pe with the ghost-shell boundary
+ * terms of Eqs. me, mepole moved into b), divided by s = max|b| on the box,
+ * together with the box mask -- both embedded at the centre of a 32^3
+ * patch, layout [2][32][32][32] floats -- to v / s on the patch.  Pairs
+ * whose box exceeds 32 points on an axis start from zero.  BF16 weights,
+ * FP32 activations and accumulation, fixed-order reductions.
+ *   sea_unet_create       seeded He-normal weights, zero biases; NULL stream
+ *                         = legacy stream.  width 1..64.
+ *   sea_unet_num_weights  length of the flat FP32 weight array: per layer
+ *                         (conv3 2->c, c->c, c->2c, 2c->2c, 2c->4c, 4c->4c,
+ *                         6c->2c, 2c->2c, 3c->c, c->c, conv1 c->1) W[cout][cin][k]
+ *                         (k = 27 as z, y, x of the 3x3x3 stencil, or 1), then
+ *                         b[cout].
+ *   sea_unet_weights      host copy out (set = 0) or in (set = 1); the kernels
+ *                         use the weights rounded to BF16, the biases as FP32.
+ *   sea_unet_forward      out[B][32^3] for in[B][2][32^3] (host or device).
+ *   sea_unet_loss_grad    masked mean squared error of forward(in) against
+ *                         target[B][32^3] (mask = input channel 1) and its
+ *                         gradient w.r.t. the flat weights (host, may be NULL);
+ *                         B <= 32.
+ *   sea_unet_collect      appends the context's last sea_apply_vxx pairs as
+ *                         training samples (b / s and mask -> v / s).
+ *   sea_unet_train        Adam (beta 0.9, 0.999) for `steps` batches drawn with
+ *                         replacement (seeded); *last_loss = the last batch's.
+ *   sea_unet_attach       the model warm-starts ctx's CG when
+ *                         params.warm_start = 1 (NULL detaches; the context
+ *                         does not own the model, keep it alive while attached).
+ * All calls synchronize the model's stream (the warm start itself runs on the
+ * context's stream inside sea_apply_vxx). */
+typedef struct sea_unet sea_unet;
+sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** out);
+long long sea_unet_num_weights(const sea_unet* net);
+sea_status sea_unet_weights(sea_unet* net, float* w, int set);
+sea_status sea_unet_forward(sea_unet* net, const float* in, int B, float* out, int on_device);
+sea_status sea_unet_loss_grad(sea_unet* net, const float* in, const float* target, int B,
+                              double* loss, float* grad, int on_device);
+sea_status sea_unet_collect(sea_unet* net, sea_ctx* ctx);
+long long sea_unet_num_samples(const sea_unet* net);
+sea_status sea_unet_train(sea_unet* net, int steps, int batch, double lr, int seed,
+                          double* last_loss);
+sea_status sea_unet_attach(sea_ctx* ctx, sea_unet* net);
+const char* sea_unet_last_error(const sea_unet* net);
+void sea_unet_destroy(sea_unet* net);
 
 /* Message for the last failing call on ctx (static text; never NULL). */
 const char* sea_last_error(const sea_ctx* ctx);

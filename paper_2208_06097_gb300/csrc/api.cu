@@ -176,7 +176,7 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
   if (p) prm = *p;
   if (!(prm.eps >= 0.0 && prm.eps < 1.0) || !(prm.delta >= 0.0) || !(prm.cg_tol > 0.0) ||
       prm.cg_max_iter < 1 || prm.lmax < 0 || prm.lmax > SEA_LMAX || prm.fd_order != 12 ||
-      prm.self_scale != 2.0 || (prm.precision != 0 && prm.precision != 1) || prm.warm_start != 0 ||
+      prm.self_scale != 2.0 || (prm.precision != 0 && prm.precision != 1) || (prm.warm_start != 0 && prm.warm_start != 1) ||
       (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1) || prm.ace_decomp < 0 || prm.ace_decomp > 2)
     return SEA_ERR_ARG;
   sea_ctx* c = new (std::nothrow) sea_ctx();
@@ -336,6 +336,14 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_ALLOC(epair, (size_t)std::max(c->P, 1) * sizeof(double));
   SEA_ALLOC(iters, (size_t)std::max(c->P, 1) * sizeof(int));
   SEA_CK(sea::launch_pair_setup(c), "pair setup");
+  c->cg_warm = false;
+  if (c->prm.warm_start == 1) {  // learned initial guesses (the model's time counts as setup)
+    if (!c->unet) return sea_fail(c, SEA_ERR_STATE, "warm_start = 1 needs sea_unet_attach");
+    const cudaError_t e = sea::launch_warm_start(c);
+    if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "warm-start workspace");
+    SEA_CK(e, "warm start");
+    c->cg_warm = true;
+  }
   SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
   SEA_CK(sea::launch_cg(c), "cg");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");

@@ -111,7 +111,10 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
   // descriptors and items (longest-first ranks dealt round-robin)
   const size_t db = sea::batch_desc_bytes();
   std::vector<unsigned char> hdesc((size_t)n * db);
-  for (int k = 0; k < n; ++k) sea::make_batch_desc(ctxs[k], &hdesc[(size_t)k * db]);
+  for (int k = 0; k < n; ++k) {
+    ctxs[k]->cg_warm = false;  // the batched form solves from zero
+    sea::make_batch_desc(ctxs[k], &hdesc[(size_t)k * db]);
+  }
   std::vector<int2> hitems;
   hitems.reserve((size_t)total);
   for (int r = 0; r < maxP; ++r)

@@ -205,6 +205,7 @@ struct CgArgs {
   int* iters;
   unsigned* status;
   int* queue;
+  int warm;  // x holds an initial guess (else the solve starts from 0)
 };
 
 // One pair's FP64 CG (the whole CTA), results into A's per-pair arrays.
@@ -220,16 +221,23 @@ __device__ __forceinline__ void cg_pair_fp64(const CgArgs& A, const StencilW& W,
   double* pv = A.p + off;
   double* q = A.q + off;
 
-  double rr = 0.0;
+  double rr = 0.0, bb = 0.0;
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const double bt = b[t];
-    x[t] = 0.0;
-    r[t] = bt;
-    pv[t] = bt;
-    rr = fma(bt, bt, rr);
+    double rt = bt;
+    if (A.warm)  // r = b - A x0
+      rt = bt - neg_lap(x, t, t % ex, (t / ex) % ey, t / (ex * ey), ex, ey, ez, W);
+    r[t] = rt;
+    pv[t] = rt;
+    rr = fma(rt, rt, rr);
+    bb = fma(bt, bt, bb);
   }
+  if (!A.warm)
+    for (int t = threadIdx.x; t < n; t += blockDim.x) x[t] = 0.0;
   rr = block_sum(rr, red[0]);
-  const double bnorm = sqrt(rr);
+  bb = block_sum(bb, red[1]);
+  __syncthreads();  // both slot arrays are read before their next use
+  const double bnorm = sqrt(bb);
   const double target =
       A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
   int it = 0;
@@ -385,6 +393,7 @@ struct CgMixedArgs {
   int* outers;    // refinement steps
   unsigned* status;
   int* queue;
+  int warm;       // x holds an initial guess (else the solve starts from 0)
 };
 
 // One pair's mixed-precision solve (the whole CTA).
@@ -403,18 +412,25 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
   float* pf = A.pf + off;
   float* qf = A.qf + off;
 
-  double bb = 0.0;
+  double bb = 0.0, rr0 = 0.0;
   for (int t = threadIdx.x; t < n; t += S) {
     const double bt = b[t];
-    x[t] = 0.0;
-    r[t] = bt;
+    double rt = bt;
+    if (A.warm)  // r = b - A x0
+      rt = bt - neg_lap(x, t, t % ex, (t / ex) % ey, t / (ex * ey), ex, ey, ez, W);
+    r[t] = rt;
     bb = fma(bt, bt, bb);
+    rr0 = fma(rt, rt, rr0);
   }
+  if (!A.warm)
+    for (int t = threadIdx.x; t < n; t += S) x[t] = 0.0;
   bb = block_sum(bb, red[0]);
+  rr0 = block_sum(rr0, red[1]);
+  __syncthreads();  // both slot arrays are read before their next use
   const double bnorm = sqrt(bb);
   const double target =
       A.tol_mode == 0 ? A.tol * bnorm : A.tol * 4.0 * 3.14159265358979323846 * sqrt((double)n);
-  double rnorm = bnorm;
+  double rnorm = sqrt(rr0);
   int inner_total = 0, outer = 0;
   bool done = rnorm <= target, capped = false;
   while (!done) {
@@ -624,6 +640,7 @@ static CgMixedArgs mixed_args(sea_ctx* c) {
   A.outers = nullptr;
   A.status = (unsigned*)c->status.p;
   A.queue = (int*)c->queue.p;
+  A.warm = c->cg_warm ? 1 : 0;
   return A;
 }
 
@@ -651,6 +668,7 @@ static CgArgs fp64_args(sea_ctx* c) {
   A.iters = (int*)c->iters.p;
   A.status = (unsigned*)c->status.p;
   A.queue = (int*)c->queue.p;
+  A.warm = c->cg_warm ? 1 : 0;
   return A;
 }
 

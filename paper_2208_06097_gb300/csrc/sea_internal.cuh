@@ -233,6 +233,8 @@ struct sea_ctx {
   // per-chunk events, created with the context
   cudaStream_t xfer[2] = {};
   std::vector<int> h_eptr;  // entry offsets per orbital, host copy (last plan)
+  struct sea_unet* unet = nullptr;  // learned warm start (attached model, not owned)
+  bool cg_warm = false;             // the next CG starts from the guess in vbuf
   cudaEvent_t xev[2 * SEA_XCHUNKS_MAX + 2] = {};
 };
 
@@ -270,6 +272,8 @@ cudaError_t launch_accumulate(sea_ctx* c, double* out);
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
                                     int e_end);
 cudaError_t launch_exx(sea_ctx* c);
+// Learned warm start (unet.cu): x0 of every pair's CG from the attached model.
+cudaError_t launch_warm_start(sea_ctx* c);
 // Mixed form's contraction with W on the tensor cores.  launch_w_digits
 // splits W's rows on every tile of every list once into wbuf
 // (w_digits_bytes(slots), slots = total list length); launch_gram_tc then

@@ -25,7 +25,10 @@ STATUS = {0: "SEA_OK", 1: "SEA_ERR_ARG", 2: "SEA_ERR_STATE", 3: "SEA_ERR_CUDA",
 EXPORTS = ["sea_default_params", "sea_create", "sea_set_orbitals", "sea_apply_vxx",
            "sea_build_ace", "sea_build_ace_from", "sea_apply_ace", "sea_get_ace_matrices", "sea_get_ace_vectors",
            "sea_get_plan", "sea_get_stats", "sea_last_error", "sea_destroy",
-           "sea_poisson_batch", "sea_poisson_batch_noalloc", "sea_apply_vxx_batch"]
+           "sea_poisson_batch", "sea_poisson_batch_noalloc", "sea_apply_vxx_batch",
+           "sea_unet_create", "sea_unet_num_weights", "sea_unet_weights", "sea_unet_forward",
+           "sea_unet_loss_grad", "sea_unet_collect", "sea_unet_num_samples", "sea_unet_train",
+           "sea_unet_attach", "sea_unet_last_error", "sea_unet_destroy"]
 
 
 class SeaError(RuntimeError):
@@ -91,8 +94,25 @@ def lib() -> ctypes.CDLL:
         L.sea_apply_vxx_batch.argtypes = [_p, _i, _p, _i, _p]
         L.sea_destroy.argtypes = [_p]
         L.sea_destroy.restype = None
+        L.sea_unet_create.argtypes = [_i, _i, _p, ctypes.POINTER(_p)]
+        L.sea_unet_num_weights.argtypes = [_p]
+        L.sea_unet_num_weights.restype = ctypes.c_longlong
+        L.sea_unet_weights.argtypes = [_p, _p, _i]
+        L.sea_unet_forward.argtypes = [_p, _p, _i, _p, _i]
+        L.sea_unet_loss_grad.argtypes = [_p, _p, _p, _i, _p, _p, _i]
+        L.sea_unet_collect.argtypes = [_p, _p]
+        L.sea_unet_num_samples.argtypes = [_p]
+        L.sea_unet_num_samples.restype = ctypes.c_longlong
+        L.sea_unet_train.argtypes = [_p, _i, _i, ctypes.c_double, _i, _p]
+        L.sea_unet_attach.argtypes = [_p, _p]
+        L.sea_unet_last_error.argtypes = [_p]
+        L.sea_unet_last_error.restype = ctypes.c_char_p
+        L.sea_unet_destroy.argtypes = [_p]
+        L.sea_unet_destroy.restype = None
+        special = ("sea_default_params", "sea_last_error", "sea_destroy", "sea_unet_num_weights",
+                   "sea_unet_num_samples", "sea_unet_last_error", "sea_unet_destroy")
         for f in EXPORTS:
-            if f not in ("sea_default_params", "sea_last_error", "sea_destroy"):
+            if f not in special:
                 getattr(L, f).restype = _i
         _LIB = L
     return _LIB
@@ -265,3 +285,106 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+PATCH = 32  # edge of the warm-start patches
+
+
+def _fptr(a, shape=None):
+    """(pointer, on_device) of a float32 numpy array or CUDA tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float32")
+        return a.ctypes.data, 0
+    if getattr(a, "is_cuda", False):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous float32")
+        return a.data_ptr(), 1
+    raise TypeError("expected a numpy array or a CUDA torch tensor")
+
+
+class WarmStartNet:
+    """The learned warm start (sea_unet_*): a 3-level 3D U-Net on 32^3
+    patches (see include/sea.h)."""
+
+    def __init__(self, width=16, seed=0, stream=None):
+        self._h = _p()
+        self.width = width
+        rc = lib().sea_unet_create(width, seed, _p(stream) if stream else None,
+                                   ctypes.byref(self._h))
+        if rc != SEA_OK:
+            raise SeaError(rc, "unet_create")
+
+    def _check(self, rc, what):
+        if rc != SEA_OK:
+            raise SeaError(rc, f"{what}: {lib().sea_unet_last_error(self._h).decode()}")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def num_weights(self) -> int:
+        return int(lib().sea_unet_num_weights(self._h))
+
+    def get_weights(self) -> np.ndarray:
+        w = np.zeros(self.num_weights(), np.float32)
+        self._check(lib().sea_unet_weights(self._h, _p(w.ctypes.data), 0), "unet_weights")
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.size != self.num_weights():
+            raise ValueError("weight count mismatch")
+        self._check(lib().sea_unet_weights(self._h, _p(w.ctypes.data), 1), "unet_weights")
+
+    def forward(self, x, out):
+        p1, d1 = _fptr(x)
+        p2, d2 = _fptr(out)
+        if d1 != d2:
+            raise ValueError("in and out must both be host or both device")
+        self._check(lib().sea_unet_forward(self._h, _p(p1), int(x.shape[0]), _p(p2), d1),
+                    "unet_forward")
+
+    def loss_grad(self, x, target, want_grad=True):
+        p1, d1 = _fptr(x)
+        p2, d2 = _fptr(target)
+        if d1 != d2:
+            raise ValueError("in and target must both be host or both device")
+        loss = ctypes.c_double(0.0)
+        g = np.zeros(self.num_weights(), np.float32) if want_grad else None
+        self._check(lib().sea_unet_loss_grad(self._h, _p(p1), _p(p2), int(x.shape[0]),
+                                             ctypes.byref(loss),
+                                             _p(g.ctypes.data) if want_grad else None, d1),
+                    "unet_loss_grad")
+        return loss.value, g
+
+    def collect(self, ctx):
+        self._check(lib().sea_unet_collect(self._h, ctx.handle), "unet_collect")
+        return int(lib().sea_unet_num_samples(self._h))
+
+    def train(self, steps, batch=8, lr=1e-3, seed=0) -> float:
+        loss = ctypes.c_double(0.0)
+        self._check(lib().sea_unet_train(self._h, steps, batch, lr, seed, ctypes.byref(loss)),
+                    "unet_train")
+        return loss.value
+
+    def attach(self, ctx):
+        rc = lib().sea_unet_attach(ctx.handle, self._h)
+        if rc != SEA_OK:
+            raise SeaError(rc, "unet_attach")
+
+    @staticmethod
+    def detach(ctx):
+        lib().sea_unet_attach(ctx.handle, None)
+
+    def close(self):
+        if self._h:
+            lib().sea_unet_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
