@@ -319,6 +319,7 @@ def run_ours(args, ws, rank, local):
                "frac": _rate(c) / c[4]} for c in cand if c is not top]
     cpu = cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline) else None
     batched = run_batched(args, sea, torch, dev) if (ws == 1 and not args.no_batched) else None
+    warm = run_warm_start(args, sea, synth, torch, dev, s) if (ws == 1 and not args.no_warm_start) else None
     line = {
         "metric": METRIC,
         "value": value,
@@ -347,6 +348,7 @@ def run_ours(args, ws, rank, local):
             "stage_ms": sm,
             "stage_ms_plain": res["plain"]["stage_ms"] if "plain" in res else None,
             "batched_form": batched,
+            "warm_start": warm,
         },
         "e2e": {
             "value": e2e_value,
@@ -389,6 +391,63 @@ def batched_workload(n_cfg=16, seed=3000):
         grid = max(16, int(round(L * synth.ANGSTROM / 0.2457)))
         out.append(synth.make_waters(n_mol, L, grid, seed=seed + 1 + k))
     return out
+
+
+def run_warm_start(args, sea, synth, torch, dev, s, width=16, train_seeds=(2001, 2002), steps=400,
+                   batch=8):
+    """The learned warm start: a width-16 U-Net trained on the pair solves of
+    two other seeded (H2O)64-like systems (plain CG), then CG iterations and
+    apply_vxx time with and without it on the benchmark system (outside the
+    timed region)."""
+    t0 = time.perf_counter()
+    net = sea.WarmStartNet(width=width, seed=11)
+    for seed in train_seeds:
+        sys_t = synth.make_waters(64, s.cell[0] / synth.ANGSTROM, s.grid[0], seed)
+        ctx = sea.Context(sys_t.cell, sys_t.grid)
+        phi = torch.from_numpy(sys_t.phi).to(dev)
+        ctx.set_orbitals(phi)
+        ctx.apply_vxx(torch.empty_like(phi))
+        net.collect(ctx)
+        ctx.close()
+        del phi
+    n_samples = int(sea.lib().sea_unet_num_samples(net.handle))
+    loss0 = net.train(1, batch=batch, lr=1e-3, seed=1)
+    loss1 = net.train(steps, batch=batch, lr=1e-3, seed=2)
+    t_train = time.perf_counter() - t0
+    phi = torch.from_numpy(s.phi).to(dev)
+    out = torch.empty_like(phi)
+    res = {"width": width, "train_systems": [f"(H2O)64-like seed {k}" for k in train_seeds],
+           "train_samples": n_samples, "train_steps": steps + 1, "batch": batch,
+           "loss_first": loss0, "loss_last": loss1, "train_s": t_train,
+           "eval": "the benchmark system (not in the training set), cg_tol 1e-8"}
+    for name, prec in (("plain", 0), ("mixed", 1)):
+        row = {}
+        for mode in (0, 1):
+            ctx = sea.Context(s.cell, s.grid, precision=prec, warm_start=mode)
+            if mode:
+                net.attach(ctx)
+            ctx.set_orbitals(phi)
+            ctx.apply_vxx(out)  # warm-up
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            e = ctx.apply_vxx(out)
+            ev1.record()
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            key = "warm" if mode else "cold"
+            row[key] = {"cg_iters_mean": st["cg_iters_mean"], "cg_unknown_iters": st["cg_unknown_iters"],
+                        "ms_apply_vxx": ev0.elapsed_time(ev1), "ms_setup": st["ms_setup"],
+                        "ms_cg": st["ms_cg"], "exx": e}
+            if mode:
+                sea.WarmStartNet.detach(ctx)
+            ctx.close()
+        row["cg_work_saved_frac"] = 1.0 - row["warm"]["cg_unknown_iters"] / max(row["cold"]["cg_unknown_iters"], 1.0)
+        row["ms_network"] = row["warm"]["ms_setup"] - row["cold"]["ms_setup"]
+        row["exx_rel_diff"] = abs(row["warm"]["exx"] - row["cold"]["exx"]) / abs(row["cold"]["exx"])
+        res[name] = row
+    net.close()
+    return res
 
 
 def run_batched(args, sea, torch, dev):
@@ -498,6 +557,8 @@ def main():
                     "(default: the (H2O)64 96^3 benchmark workload; smaller ones for profiling)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer pass")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form section")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned warm-start section")
     ap.add_argument("--form", choices=["plain", "mixed", "both"], default="both",
                     help="plain FP64, the mixed form, or both (headline: mixed)")
     args = ap.parse_args()

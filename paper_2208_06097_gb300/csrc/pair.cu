@@ -692,6 +692,37 @@ cudaError_t launch_cg(sea_ctx* c) {
   return cudaGetLastError();
 }
 
+// Damped Jacobi sweeps on every pair's starting vector x (CTA per pair):
+// x += omega (b - A x) / diag(A).  Removes the high-frequency part of a
+// guess's error, which A would otherwise amplify in the CG's first residual.
+__global__ void __launch_bounds__(256)
+    k_smooth(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff, int P,
+             const double* __restrict__ b, double* __restrict__ x, double* __restrict__ r,
+             StencilW W, int sweeps, double omega) {
+  const int p = blockIdx.x;
+  if (p >= P) return;
+  const PairInfo Pi = pinfo[p];
+  const int ex = Pi.ext[0], ey = Pi.ext[1], ez = Pi.ext[2], n = Pi.n;
+  const long long off = voff[p];
+  const double s = omega / W.center;
+  for (int k = 0; k < sweeps; ++k) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+      r[off + t] = b[off + t] - neg_lap(x + off, t, t % ex, (t / ex) % ey, t / (ex * ey), ex, ey, ez, W);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) x[off + t] = fma(s, r[off + t], x[off + t]);
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_smooth(sea_ctx* c, int sweeps, double omega) {
+  if (c->P == 0 || sweeps <= 0) return cudaSuccess;
+  k_smooth<<<c->P, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const long long*)c->voff.p,
+                                        c->P, (const double*)c->bbuf.p, (double*)c->vbuf.p,
+                                        (double*)c->rbuf.p, make_weights(c), sweeps, omega);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 // Descriptor of one configuration for k_cg_batch (host side).
 void make_batch_desc(sea_ctx* c, void* out) {
   BatchCg d;

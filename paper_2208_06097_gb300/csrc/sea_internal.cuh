@@ -274,6 +274,8 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
 cudaError_t launch_exx(sea_ctx* c);
 // Learned warm start (unet.cu): x0 of every pair's CG from the attached model.
 cudaError_t launch_warm_start(sea_ctx* c);
+// Damped Jacobi sweeps on every pair's starting vector (pair.cu).
+cudaError_t launch_smooth(sea_ctx* c, int sweeps, double omega);
 // Mixed form's contraction with W on the tensor cores.  launch_w_digits
 // splits W's rows on every tile of every list once into wbuf
 // (w_digits_bytes(slots), slots = total list length); launch_gram_tc then

@@ -811,7 +811,8 @@ sea_status sea_unet_attach(sea_ctx* c, sea_unet* u) {
 namespace sea {
 
 // Warm start of the context's CG: x0 = s * U-Net(b / s, mask) on every pair
-// whose box fits the patch (0 elsewhere), written into the solution buffer.
+// whose box fits the patch (0 elsewhere), written into the solution buffer,
+// then 4 damped Jacobi sweeps (omega = 2/3) on it.
 cudaError_t launch_warm_start(sea_ctx* c) {
   sea_unet* u = c->unet;
   if (!u || c->P == 0) return cudaSuccess;
@@ -840,7 +841,10 @@ cudaError_t launch_warm_start(sea_ctx* c) {
     c->launches += 2 + 15;
   }
   u->stream = saved;
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // smooth the guesses' high-frequency error before the CG
+  return launch_smooth(c, 4, 2.0 / 3.0);
 }
 
 }  // namespace sea
