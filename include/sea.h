@@ -132,6 +132,23 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
  * orbital ranges, each range checked while the next one is in flight. */
 sea_status sea_set_orbitals(sea_ctx* ctx, const double* phi, int n_orb, int on_device);
 
+/* SCDM localization (Sec. II A): from n_orb orthonormal orbitals phi
+ * (canonical or any other basis of the occupied space; [n_orb][nz][ny][nx],
+ * host or device, orthonormal with the grid weight) the context's orbitals
+ * become Phi~ = Phi U with
+ *   Phi^T Pi = Q R (column-pivoted QR, Eq. phi_qr), C = first n_orb pivots,
+ *   B = (Phi^T)_{:,C}, P_CC = B^T B, U = B P_CC^{-1/2} (Eqs. nonortho_scdm,
+ *   ortho_scdm, unitary_scdm).
+ * U[n_orb][n_orb] (row-major, host, may be NULL) receives U and cols[n_orb]
+ * (host, may be NULL) the selected grid points (flat index z ny nx + y nx
+ * + x) in pivot order.  Pivots: at each step the grid point whose column
+ * of Phi^T has the longest component orthogonal to those already chosen
+ * (ties: smallest index).  Any earlier exchange/ACE result is invalidated.
+ * SEA_ERR_INPUT if a value is not finite or the orbitals are rank
+ * deficient.  Synchronizes the context stream. */
+sea_status sea_scdm(sea_ctx* ctx, const double* phi, int n_orb, int on_device, double* U,
+                    int* cols);
+
 /* Apply V_xx to every orbital: vxx_phi[n_orb][nz][ny][nx] (host or device,
  * caller-owned) receives V_xx phi_i = -D^i; *exx (may be NULL) receives E_xx.
  * Synchronizes the context stream after the plan (sizes) and at the end (E_xx

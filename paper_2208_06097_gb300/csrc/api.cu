@@ -298,6 +298,33 @@ sea_status sea_set_orbitals(sea_ctx* c, const double* phi, int n_orb, int on_dev
   return SEA_OK;
 }
 
+sea_status sea_scdm(sea_ctx* c, const double* phi, int n_orb, int on_device, double* U, int* cols) {
+  if (!c) return SEA_ERR_ARG;
+  const sea_status st0 = sea_set_orbitals(c, phi, n_orb, on_device);
+  if (st0 != SEA_OK) return st0;
+  c->have_phi = false;
+  const size_t nn = (size_t)n_orb * n_orb;
+  SEA_ALLOC(scdm_u, nn * sizeof(double));
+  SEA_ALLOC(scdm_c, (size_t)n_orb * sizeof(long long));
+  SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
+  const cudaError_t e = sea::launch_scdm(c, (double*)c->scdm_u.p, (long long*)c->scdm_c.p);
+  if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "SCDM workspace");
+  SEA_CK(e, "scdm");
+  std::vector<long long> hc(n_orb);
+  unsigned st = 0;
+  if (U) SEA_CK(cudaMemcpyAsync(U, c->scdm_u.p, nn * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy U");
+  SEA_CK(cudaMemcpyAsync(hc.data(), c->scdm_c.p, (size_t)n_orb * sizeof(long long), cudaMemcpyDeviceToHost,
+                         c->stream),
+         "copy pivots");
+  SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "status");
+  SEA_CK(cudaStreamSynchronize(c->stream), "scdm");
+  if (st & SEA_FLAG_NOT_PD) return sea_fail(c, SEA_ERR_INPUT, "orbitals are rank deficient (SCDM pivot of zero norm)");
+  if (cols)
+    for (int k = 0; k < n_orb; ++k) cols[k] = (int)hc[k];
+  c->have_phi = true;
+  return SEA_OK;
+}
+
 sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx) {
   if (!c) return SEA_ERR_ARG;
   if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
@@ -737,6 +764,7 @@ void sea_destroy(sea_ctx* c) {
                    &c->qbuf, &c->eptr, &c->eent, &c->ewin, &c->coff, &c->cbuf, &c->status,
                    &c->exx_dev, &c->queue, &c->tmask, &c->tptr_o, &c->tlist_o, &c->tslot_o,
                    &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf, &c->wdig,
+                   &c->scdm_u, &c->scdm_c,
                    &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2, &c->bdesc, &c->bitems};
   for (SeaBuf* b : all) release(*b);
   for (int k = 0; k < 16; ++k)

@@ -223,6 +223,7 @@ struct sea_ctx {
   SeaBuf status, exx_dev, queue;
   // ACE
   SeaBuf wdig;  // the mixed form's W digits (tensor-core contraction)
+  SeaBuf scdm_u, scdm_c;  // SCDM rotation and pivots
   SeaBuf tmask, tptr_o, tlist_o, tslot_o, tptr_t, tlist_t, partial, Mbuf, Abuf, Lbuf, Linv,
       Gbuf, Hbuf, Hbuf2;
   int n_tiles = 0, tile_inc = 0, max_tile_list = 0;
@@ -274,6 +275,9 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
 cudaError_t launch_exx(sea_ctx* c);
 // Learned warm start (unet.cu): x0 of every pair's CG from the attached model.
 cudaError_t launch_warm_start(sea_ctx* c);
+// SCDM localization of the orbitals in the context (scdm.cu): U and the
+// pivots on the device; the localized orbitals replace c->phi.
+cudaError_t launch_scdm(sea_ctx* c, double* U_dev, long long* C_dev);
 // Damped Jacobi sweeps on every pair's starting vector (pair.cu).
 cudaError_t launch_smooth(sea_ctx* c, int sweeps, double omega);
 // Mixed form's contraction with W on the tensor cores.  launch_w_digits

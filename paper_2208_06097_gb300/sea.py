@@ -28,7 +28,7 @@ EXPORTS = ["sea_default_params", "sea_create", "sea_set_orbitals", "sea_apply_vx
            "sea_poisson_batch", "sea_poisson_batch_noalloc", "sea_apply_vxx_batch",
            "sea_unet_create", "sea_unet_num_weights", "sea_unet_weights", "sea_unet_forward",
            "sea_unet_loss_grad", "sea_unet_collect", "sea_unet_num_samples", "sea_unet_train",
-           "sea_unet_attach", "sea_unet_last_error", "sea_unet_destroy"]
+           "sea_unet_attach", "sea_unet_last_error", "sea_unet_destroy", "sea_scdm"]
 
 
 class SeaError(RuntimeError):
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         L.sea_apply_vxx_batch.argtypes = [_p, _i, _p, _i, _p]
         L.sea_destroy.argtypes = [_p]
         L.sea_destroy.restype = None
+        L.sea_scdm.argtypes = [_p, _p, _i, _i, _p, _p]
         L.sea_unet_create.argtypes = [_i, _i, _p, ctypes.POINTER(_p)]
         L.sea_unet_num_weights.argtypes = [_p]
         L.sea_unet_num_weights.restype = ctypes.c_longlong
@@ -208,6 +209,18 @@ class Context:
         n = int(phi.shape[0])
         self._check(lib().sea_set_orbitals(self._h, _p(ptr), n, dev), "set_orbitals")
         self.n_orb = n
+
+    def scdm(self, phi):
+        """Localize the orbitals phi (SCDM, Sec. II A) into the context;
+        returns (U, selected grid points)."""
+        ptr, dev = _ptr(phi)
+        n = int(phi.shape[0])
+        U = np.zeros((n, n))
+        cols = np.zeros(n, np.int32)
+        self._check(lib().sea_scdm(self._h, _p(ptr), n, dev, _p(U.ctypes.data),
+                                   _p(cols.ctypes.data)), "scdm")
+        self.n_orb = n
+        return U, cols
 
     def apply_vxx(self, out, allow_cap: bool = False):
         """out <- V_xx phi (same kind as out: torch CUDA tensor or numpy)."""

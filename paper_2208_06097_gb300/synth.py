@@ -217,6 +217,22 @@ def loewdin_orthonormalize(phi: np.ndarray, dV: float) -> np.ndarray:
     return (Sm.T @ F).reshape(phi.shape)
 
 
+def separated_gaussians(n: int, grid: int, L: float, alpha: float = 3.0):
+    """n Gaussians exp(-alpha r^2) on a simple cubic lattice of centres in a
+    cubic cell of edge L (bohr) on grid^3 points, Loewdin-orthonormalized:
+    a localized basis whose rotations test orbital localization.  Returns
+    (phi [n][grid][grid][grid], dV)."""
+    ax = np.arange(grid) * (L / grid)
+    Z, Y, X = np.meshgrid(ax, ax, ax, indexing="ij")
+    side = int(np.ceil(n ** (1 / 3)))
+    phi = np.zeros((n, grid, grid, grid))
+    for k in range(n):
+        c = (np.array([k % side, (k // side) % side, k // (side * side)]) + 0.5) * (L / side)
+        phi[k] = np.exp(-alpha * ((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2))
+    dV = (L / grid) ** 3
+    return loewdin_orthonormalize(phi, dV), dV
+
+
 # Workload shapes (cubic cells).  Densities follow from 18.015 g/mol waters.
 CONFIGS = {
     # 8 waters, 6.21 A, 48^3: the small case the oracle finishes in seconds.
