@@ -122,6 +122,16 @@ def job_value(steps, ws, t_ms_max):
     return ws * steps / (t_ms_max / 1e3)
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
+# ncu capture of the benchmark workload with the current kernels; see
+# profiles/dram_traffic_h2o64_96.md).  None: not captured.
+DRAM_BYTES_PER_LAUNCH = {
+    "k_cg_mixed": 26.1e6,
+    "k_gram_tc": 2.024e9,
+    "k_tile_expand_x": 2.260e9,
+}
+
+
 def _tiles_with_support(w, torch):
     """Number of 8 x 4 x 4 grid tiles on which some row of W is nonzero (the
     tiles the contraction with W reads A on)."""
@@ -365,7 +375,8 @@ def run_ours(args, ws, rank, local):
             "peak": peak,
             "unit": "GB/s" if bound == "hbm" else "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": None,
+            "traffic": DRAM_BYTES_PER_LAUNCH.get(name.split(" ")[0]) if args.config == "h2o64_96" else None,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
             "peak_note": peak_note,
             "other_kernels": others,
         },

@@ -327,7 +327,10 @@ __global__ void __launch_bounds__(256, 3) k_cg(CgArgs A, StencilW W) {
 //     solve A d = r / ||r|| by CG in FP32 to a relative residual of
 //       SEA_MIXED_INNER (dot products: per-thread partial sums in
 //       compensated FP32 -- exact products by FMA, error-free additions --
-//       then summed across the block in FP64)
+//       combined across the block by error-free FP32 additions; alpha,
+//       beta and the inner stopping test in FP32: on this part one FP64
+//       instruction of a warp costs the time of 64 FP32 ones, and the
+//       inner solve needs only SEA_MIXED_INNER)
 //     x += ||r|| d (FP64);  r = b - A x (FP64 stencil)
 // The stopping rule is applied to the true FP64 residual, so the result
 // meets the same bound as the FP64 solver.
@@ -355,6 +358,34 @@ struct DotF {
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+
+// (hi, lo) += (bh, bl) with an error-free addition of the leading parts.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float v = s - hi;
+  const float e = (hi - (s - v)) + (bh - v);
+  hi = s;
+  lo = (lo + bl) + e;
+}
+
+// Block sum of compensated (hi, lo) partials in FP32 only: warp butterfly,
+// then every thread adds the warps' results in warp order.  `slots` holds
+// 32 float2 of shared memory, reused only after the next __syncthreads.
+// Returns hi + lo rounded to FP32 (the same value in every thread).
+__device__ __forceinline__ float block_sum_f(float hi, float lo, float2* slots) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    two_sum_add(hi, lo, bh, bl);
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) slots[w] = make_float2(hi, lo);
+  __syncthreads();
+  float2 t = slots[0];
+  for (int k = 1; k < nw; ++k) two_sum_add(t.x, t.y, slots[k].x, slots[k].y);
+  return t.x + t.y;
+}
 
 __device__ __forceinline__ float lap_axis_f(const float* __restrict__ pv, int t, int u, int e,
                                             int st, const float* __restrict__ w) {
@@ -438,7 +469,10 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
       capped = true;
       break;
     }
-    // inner FP32 CG on A d = r / ||r||
+    // inner FP32 CG on A d = r / ||r||: vectors, scalars and the block
+    // reductions (compensated partials) all in FP32
+    float2* fs0 = reinterpret_cast<float2*>(red[0]);
+    float2* fs1 = reinterpret_cast<float2*>(red[1]);
     const double inv = 1.0 / rnorm;
     DotF rr0;
     for (int t = threadIdx.x; t < n; t += S) {
@@ -448,10 +482,9 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
       d[t] = 0.f;
       rr0.add(v, v);
     }
-    double rr = block_sum(rr0.value(), red[1]);
-    const double inner_target = (double)SEA_MIXED_INNER * sqrt(rr);
-    int k = 0;
-    while (sqrt(rr) > inner_target && inner_total < A.max_iter) {
+    float rr = block_sum_f(rr0.hi, rr0.lo, fs1);
+    const float stop = (float)SEA_MIXED_INNER * (float)SEA_MIXED_INNER * rr;  // on ||r||^2
+    while (rr > stop && inner_total < A.max_iter) {
       DotF pq0, pq1;
       {
         BoxWalk w0(threadIdx.x, 2 * S, ex, ey);
@@ -470,8 +503,9 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
           pq0.add(pf[w0.t], q0);
         }
       }
-      const double pq = block_sum(pq0.value() + pq1.value(), red[0]);
-      const float alpha = (float)(rr / pq);
+      two_sum_add(pq0.hi, pq0.lo, pq1.hi, pq1.lo);
+      const float pq = block_sum_f(pq0.hi, pq0.lo, fs0);
+      const float alpha = rr / pq;
       DotF rn0;
       for (int t = threadIdx.x; t < n; t += S) {
         d[t] = fmaf(alpha, pf[t], d[t]);
@@ -479,12 +513,11 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
         rf[t] = rt;
         rn0.add(rt, rt);
       }
-      const double rn = block_sum(rn0.value(), red[1]);
-      ++k;
+      const float rn = block_sum_f(rn0.hi, rn0.lo, fs1);
       ++inner_total;
-      const float beta = (float)(rn / rr);
+      const float beta = rn / rr;
       rr = rn;
-      if (sqrt(rn) <= inner_target) break;
+      if (rn <= stop) break;
       for (int t = threadIdx.x; t < n; t += S) pf[t] = fmaf(beta, pf[t], rf[t]);
       __syncthreads();
     }

@@ -243,6 +243,10 @@ CONFIGS = {
     "h2o64_d04_128": dict(n_mol=64, L=16.86, grid=128, seed=1002),
     "h2o64_d10_96": dict(n_mol=64, L=12.42, grid=96, seed=1002),
     "h2o64_d17_80": dict(n_mol=64, L=10.41, grid=80, seed=1002),
+    # the 256-orbital system on a coarse 48^3 grid (h = 0.49 bohr): a
+    # profiling case with the benchmark's orbital count, small enough for
+    # multi-pass kernel captures, its orbital array still larger than L2.
+    "h2o64_48": dict(n_mol=64, L=12.42, grid=48, seed=1001),
 }
 
 
