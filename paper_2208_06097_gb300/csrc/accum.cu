@@ -164,7 +164,9 @@ __global__ void k_entry_offsets(const Entry* __restrict__ ent, const int* __rest
 
 #define SEA_CHUNK 1024
 
-__global__ void __launch_bounds__(256)
+// DFM: the multipole potential in double-float arithmetic (mixed form).
+template <bool DFM>
+__global__ void __launch_bounds__(256, DFM ? 2 : 1)
     k_contrib(const double* __restrict__ phi, int nx, int ny, int nz, const Entry* __restrict__ ent,
               const long long* __restrict__ coff, const PairInfo* __restrict__ pinfo,
               const long long* __restrict__ voff, const double* __restrict__ vbuf,
@@ -176,8 +178,16 @@ __global__ void __launch_bounds__(256)
   if (t0 >= nw) return;
   const PairInfo P = pinfo[e.pair];
   __shared__ double Qs[SEA_NQ];
-  if (threadIdx.x < SEA_NQ) Qs[threadIdx.x] = Qg[(size_t)e.pair * SEA_NQ + threadIdx.x];
+  __shared__ DF Qd[SEA_NQ];
+  if (threadIdx.x < SEA_NQ) {
+    const double q = Qg[(size_t)e.pair * SEA_NQ + threadIdx.x];
+    if (DFM)
+      Qd[threadIdx.x] = df_from_double(q);
+    else
+      Qs[threadIdx.x] = q;
+  }
   __syncthreads();
+  const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
   const double* v = vbuf + voff[e.pair];
   const size_t ng = (size_t)nx * ny * nz;
   const double* fp = phi + (size_t)e.partner * ng;
@@ -191,6 +201,10 @@ __global__ void __launch_bounds__(256)
     double val;
     if (lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2])
       val = v[(lz * P.ext[1] + ly) * P.ext[0] + lx];
+    else if (DFM)  // lx - cx etc. are half-integers, exact in FP32
+      val = df_to_double(me_potential_df(Qd, df_mul_f((float)(lx - cx), Hx),
+                                         df_mul_f((float)(ly - cy), Hy),
+                                         df_mul_f((float)(lz - cz), Hz)));
     else
       val = me_potential(Qs, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
     const size_t g = ((size_t)wrapi(uz, nz) * ny + wrapi(uy, ny)) * nx + wrapi(ux, nx);
@@ -281,7 +295,8 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
     const int chunks = (int)((c->max_window + SEA_CHUNK - 1) / SEA_CHUNK);
     for (int e0 = e_begin; e0 < e_end; e0 += 65535) {
       const int ne = std::min(65535, e_end - e0);
-      k_contrib<<<dim3(chunks, ne), 256, 0, c->stream>>>(
+      auto kern = c->prm.precision == 1 ? k_contrib<true> : k_contrib<false>;
+      kern<<<dim3(chunks, ne), 256, 0, c->stream>>>(
           (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const Entry*)c->ewin.p + e0,
           (const long long*)c->coff.p + e0, (const PairInfo*)c->pinfo.p,
           (const long long*)c->voff.p, (const double*)c->vbuf.p, (const double*)c->Q.p, c->h[0],

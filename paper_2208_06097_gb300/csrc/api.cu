@@ -46,6 +46,12 @@ HarmCoef make_harmonic_coefficients() {
                                  ((double)(l + m + 1) * (double)(l - m + 1)));
       h.gam[l][m + SEA_LMAX] = c * sig[l - 1][m + SEA_LMAX] / sig[l + 1][m + SEA_LMAX];
     }
+  for (int l = 0; l < SEA_LMAX; ++l)
+    for (int k = 0; k < 2 * SEA_LMAX + 1; ++k) {
+      const float hi = (float)h.gam[l][k];
+      h.gam_hi[l][k] = hi;
+      h.gam_lo[l][k] = (float)(h.gam[l][k] - (double)hi);
+    }
   return h;
 }
 

@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(256, 1)
 // 37-point stencil reaches, moved into b with the stencil weights; one CTA
 // per pair, one thread per line of the box along each axis in turn (the
 // axes one after the other, so every b entry is updated in a fixed order).
-__global__ void __launch_bounds__(256, 1)
+// DFM: the potentials in double-float arithmetic (mixed form).
+template <bool DFM>
+__global__ void __launch_bounds__(256, DFM ? 2 : 1)
     k_pair_boundary(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
                     double hx, double hy, double hz, StencilW W, const double* __restrict__ Qg,
                     double* __restrict__ bbuf) {
@@ -85,40 +87,51 @@ __global__ void __launch_bounds__(256, 1)
   const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
   double* b = bbuf + voff[p];
   __shared__ double Qs[SEA_NQ];
-  if (threadIdx.x < SEA_NQ) Qs[threadIdx.x] = Qg[(size_t)p * SEA_NQ + threadIdx.x];
+  __shared__ DF Qd[SEA_NQ];
+  if (threadIdx.x < SEA_NQ) {
+    const double q = Qg[(size_t)p * SEA_NQ + threadIdx.x];
+    if (DFM)
+      Qd[threadIdx.x] = df_from_double(q);
+    else
+      Qs[threadIdx.x] = q;
+  }
   __syncthreads();
+  // me_potential at grid offsets (ox, oy, oz) from the box centre, in units
+  // of h (half-integers)
+  const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
+  auto pot = [&](double ox, double oy, double oz) -> double {
+    if (DFM)
+      return df_to_double(me_potential_df(Qd, df_mul_f((float)ox, Hx), df_mul_f((float)oy, Hy),
+                                          df_mul_f((float)oz, Hz)));
+    return me_potential(Qs, ox * hx, oy * hy, oz * hz);
+  };
   const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (ez - 1);
   for (int a = 0; a < 3; ++a) {
     // line coordinates (u1, u2) across axis a; along-axis extent ea, stride sa
     const int e1 = a == 0 ? ey : ex, e2 = a == 2 ? ey : ez;
     const int ea = a == 0 ? ex : (a == 1 ? ey : ez);
     const int sa = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
-    const double ha = a == 0 ? hx : (a == 1 ? hy : hz);
     const double ca = a == 0 ? cx : (a == 1 ? cy : cz);
     const int nl = e1 * e2;
     for (int line = threadIdx.x; line < nl; line += blockDim.x) {
       const int u1 = line % e1, u2 = line / e1;
       // the two fixed coordinates in (x, y, z) order and the base index
       int bx = 0, by = 0, bz = 0;
-      double px = 0, py = 0, pz = 0;
-      if (a == 0) { by = u1; bz = u2; py = (by - cy) * hy; pz = (bz - cz) * hz; }
-      else if (a == 1) { bx = u1; bz = u2; px = (bx - cx) * hx; pz = (bz - cz) * hz; }
-      else { bx = u1; by = u2; px = (bx - cx) * hx; py = (by - cy) * hy; }
+      double px = 0, py = 0, pz = 0;  // offsets from the centre in units of h
+      if (a == 0) { by = u1; bz = u2; py = by - cy; pz = bz - cz; }
+      else if (a == 1) { bx = u1; bz = u2; px = bx - cx; pz = bz - cz; }
+      else { bx = u1; by = u2; px = bx - cx; py = by - cy; }
       const int base = (bz * ey + by) * ex + bx;
       double Glo[SEA_FDP + 1], Ghi[SEA_FDP + 1];
-#pragma unroll
-      for (int d = 1; d <= SEA_FDP; ++d) {
-        const double lo = (-d - ca) * ha, hi = (ea - 1 + d - ca) * ha;
-        if (a == 0) {
-          Glo[d] = me_potential(Qs, lo, py, pz);
-          Ghi[d] = me_potential(Qs, hi, py, pz);
-        } else if (a == 1) {
-          Glo[d] = me_potential(Qs, px, lo, pz);
-          Ghi[d] = me_potential(Qs, px, hi, pz);
-        } else {
-          Glo[d] = me_potential(Qs, px, py, lo);
-          Ghi[d] = me_potential(Qs, px, py, hi);
-        }
+#pragma unroll 1
+      for (int k = 0; k < 2 * SEA_FDP; ++k) {  // one call site: d = 1..FDP below, then above
+        const int d = k % SEA_FDP + 1;
+        const double t = k < SEA_FDP ? -d - ca : ea - 1 + d - ca;
+        const double g = pot(a == 0 ? t : px, a == 1 ? t : py, a == 2 ? t : pz);
+        if (k < SEA_FDP)
+          Glo[d] = g;
+        else
+          Ghi[d] = g;
       }
       for (int ta = 0; ta < ea; ++ta) {
         if (ta >= SEA_FDP && ta < ea - SEA_FDP) continue;
@@ -630,7 +643,8 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
       (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const PairInfo*)c->pinfo.p,
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
       (double*)c->bbuf.p, (double*)c->Q.p);
-  k_pair_boundary<<<c->P, 256, 0, c->stream>>>(
+  auto boundary = c->prm.precision == 1 ? k_pair_boundary<true> : k_pair_boundary<false>;
+  boundary<<<c->P, 256, 0, c->stream>>>(
       (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2],
       make_weights(c), (const double*)c->Q.p, (double*)c->bbuf.p);
   c->launches += 2;

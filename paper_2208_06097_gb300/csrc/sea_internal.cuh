@@ -53,6 +53,8 @@ __host__ __device__ inline int lmi(int l, int m) { return l * l + l + m; }
 struct HarmCoef {
   double gam[SEA_LMAX][2 * SEA_LMAX + 1];
   double kap2[SEA_NQ];
+  float gam_hi[SEA_LMAX][2 * SEA_LMAX + 1];  // gam = gam_hi + gam_lo (double-float)
+  float gam_lo[SEA_LMAX][2 * SEA_LMAX + 1];
 };
 // Each translation unit that evaluates harmonics holds its own copy (the
 // library is built without relocatable device code) and uploads it through
@@ -125,6 +127,100 @@ __device__ __forceinline__ double me_potential(const double* __restrict__ Q, dou
     for (int m = -(l + 1); m <= l + 1; ++m) v = fma(Q[lmi(l + 1, m)], D[lmi(l + 1, m)], v);
   }
   return v * sqrt(ir2);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): Knuth's
+// two-sum and the fused-multiply-add two-product (Dekker's method), about 48
+// significant bits from FP32 operations only.  The mixed form evaluates the
+// multipole potential with it: on this part an FP64 instruction of a warp
+// costs the issue time of 64 FP32 ones.
+// ---------------------------------------------------------------------------
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  const float e = (a.hi - (s - v)) + (b.hi - v);
+  return df_fast_two_sum(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  return df_fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ DF df_mul_f(float a, DF b) {  // a exact in FP32
+  const float p = a * b.hi;
+  const float e = fmaf(a, b.hi, -p);
+  return df_fast_two_sum(p, fmaf(a, b.lo, e));
+}
+// 1 / a: FP32 reciprocal, one Newton step in double-float
+__device__ __forceinline__ DF df_rcp(DF a) {
+  const float y = 1.0f / a.hi;
+  const DF t = df_mul_f(y, a);  // a y = 1 - e
+  const float e = (1.0f - t.hi) - t.lo;
+  return df_fast_two_sum(y, y * e);
+}
+// sqrt(a): FP32 square root, one Newton step in double-float
+__device__ __forceinline__ DF df_sqrt(DF a) {
+  const float s = sqrtf(a.hi);
+  const float p = s * s;
+  const float pe = fmaf(s, s, -p);
+  const float d = ((a.hi - p) - pe) + a.lo;  // a - s^2
+  return df_fast_two_sum(s, d * (0.5f / s));
+}
+__device__ __forceinline__ DF df_from_double(double x) {
+  const float hi = (float)x;
+  return DF{hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// me_potential in double-float: the same recurrences and summation order,
+// Q as double-float coefficients.
+__device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF y, DF z) {
+  const DF r2 = df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z));
+  const DF ir2 = df_rcp(r2);
+  const DF ux = df_mul(x, ir2), uy = df_mul(y, ir2), uz = df_mul(z, ir2);
+  DF Dm[2 * SEA_LMAX + 1], Dc[2 * SEA_LMAX + 1], Dn[2 * SEA_LMAX + 1];  // l-1, l, l+1
+#pragma unroll
+  for (int k = 0; k < 2 * SEA_LMAX + 1; ++k) Dm[k] = Dc[k] = Dn[k] = DF{0.f, 0.f};
+  Dm[SEA_LMAX] = DF{1.f, 0.f};  // l = 0
+  Dc[SEA_LMAX + 1] = ux;        // l = 1: m = 1, -1, 0
+  Dc[SEA_LMAX - 1] = uy;
+  Dc[SEA_LMAX] = uz;
+  DF v = Q[0];
+  v = df_add(v, df_mul(Q[lmi(1, -1)], uy));
+  v = df_add(v, df_mul(Q[lmi(1, 0)], uz));
+  v = df_add(v, df_mul(Q[lmi(1, 1)], ux));
+#pragma unroll
+  for (int l = 1; l < SEA_LMAX; ++l) {
+    Dn[SEA_LMAX + l + 1] = df_add(df_mul(ux, Dc[SEA_LMAX + l]), df_neg(df_mul(uy, Dc[SEA_LMAX - l])));
+    Dn[SEA_LMAX - l - 1] = df_add(df_mul(uy, Dc[SEA_LMAX + l]), df_mul(ux, Dc[SEA_LMAX - l]));
+#pragma unroll
+    for (int m = -l; m <= l; ++m) {
+      if (m >= -(l - 1) && m <= l - 1) {
+        const DF g = df_mul(DF{c_harm.gam_hi[l][m + SEA_LMAX], c_harm.gam_lo[l][m + SEA_LMAX]}, ir2);
+        Dn[SEA_LMAX + m] = df_add(df_mul(uz, Dc[SEA_LMAX + m]), df_neg(df_mul(g, Dm[SEA_LMAX + m])));
+      } else {
+        Dn[SEA_LMAX + m] = df_mul(uz, Dc[SEA_LMAX + m]);
+      }
+    }
+#pragma unroll
+    for (int m = -(l + 1); m <= l + 1; ++m) v = df_add(v, df_mul(Q[lmi(l + 1, m)], Dn[SEA_LMAX + m]));
+#pragma unroll
+    for (int k = 0; k < 2 * SEA_LMAX + 1; ++k) {
+      Dm[k] = Dc[k];
+      Dc[k] = Dn[k];
+    }
+  }
+  return df_mul(v, df_sqrt(ir2));
 }
 
 // Sum over the block of one double; every thread gets the same total, added
