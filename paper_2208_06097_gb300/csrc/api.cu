@@ -357,6 +357,7 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   memcpy(&c->U, hc + 4, sizeof(long long));
   memcpy(&c->WC, hc + 6, sizeof(long long));
   memcpy(&c->max_window, hc + 8, sizeof(long long));
+  c->cg_pad_max = hc[10];
   SEA_CK(cudaEventRecord(c->ev[1], c->stream), "event");
   const size_t U = (size_t)std::max<long long>(c->U, 1);
   SEA_ALLOC(vbuf, U * sizeof(double));

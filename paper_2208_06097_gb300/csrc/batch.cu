@@ -96,6 +96,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
     memcpy(&c->U, h + 4, sizeof(long long));
     memcpy(&c->WC, h + 6, sizeof(long long));
     memcpy(&c->max_window, h + 8, sizeof(long long));
+    c->cg_pad_max = h[10];
     const size_t U = (size_t)(c->U > 1 ? c->U : 1);
     const size_t P = (size_t)(c->P > 1 ? c->P : 1);
     if (!sea_ensure(c, c->vbuf, U * sizeof(double)) || !sea_ensure(c, c->bbuf, U * sizeof(double)) ||
@@ -111,15 +112,23 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
   // descriptors and items (longest-first ranks dealt round-robin)
   const size_t db = sea::batch_desc_bytes();
   std::vector<unsigned char> hdesc((size_t)n * db);
+  int pad_cap = 0;
   for (int k = 0; k < n; ++k) {
+    pad_cap = std::max(pad_cap, sea::cg_pad_cap(ctxs[k]));
     ctxs[k]->cg_warm = false;  // the batched form solves from zero
     sea::make_batch_desc(ctxs[k], &hdesc[(size_t)k * db]);
   }
+  // mixed-form items first, then FP64 ones: one launch each (their CTA sizes differ)
   std::vector<int2> hitems;
   hitems.reserve((size_t)total);
-  for (int r = 0; r < maxP; ++r)
-    for (int k = 0; k < n; ++k)
-      if (r < ctxs[k]->P) hitems.push_back(make_int2(k, r));
+  for (int mixed = 1; mixed >= 0; --mixed)
+    for (int r = 0; r < maxP; ++r)
+      for (int k = 0; k < n; ++k)
+        if (r < ctxs[k]->P && (ctxs[k]->prm.precision == 1) == (mixed == 1))
+          hitems.push_back(make_int2(k, r));
+  long long total_mixed = 0;
+  for (int k = 0; k < n; ++k)
+    if (ctxs[k]->prm.precision == 1) total_mixed += ctxs[k]->P;
   if (!sea_ensure(c0, c0->bdesc, (size_t)n * db) ||
       !sea_ensure(c0, c0->bitems, (size_t)(total > 1 ? total : 1) * sizeof(int2)))
     return sea_fail(c0, SEA_ERR_OOM, "device allocation failed: batch descriptors");
@@ -145,6 +154,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
     sig.push_back(c->U);
     sig.push_back(c->WC);
     sig.push_back(c->max_window);
+    sig.push_back(c->cg_pad_max);
     sig.push_back(c->prm.precision);
     sig.push_back((long long)(uintptr_t)outs[k]);
     const SeaBuf* bufs[] = {&c->phi, &c->vxx_dev, &c->pinfo, &c->voff, &c->order, &c->Q,
@@ -163,9 +173,13 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
       if (e != cudaSuccess) return e;
     }
     cudaError_t e = sea::launch_cg_batch(st, c0->device, c0->bdesc.p, (const int2*)c0->bitems.p,
-                                         (int)total, (int*)c0->queue.p);
+                                         (int)total_mixed, (int*)c0->queue.p, pad_cap, true);
     if (e != cudaSuccess) return e;
-    c0->launches += 1;
+    e = sea::launch_cg_batch(st, c0->device, c0->bdesc.p,
+                             (const int2*)c0->bitems.p + total_mixed, (int)(total - total_mixed),
+                             (int*)c0->queue.p, 0, false);
+    if (e != cudaSuccess) return e;
+    c0->launches += (total_mixed > 0) + (total > total_mixed);
     for (int k = 0; k < n; ++k) {
       e = sea::launch_accumulate(ctxs[k], (double*)ctxs[k]->vxx_dev.p);
       if (e != cudaSuccess) return e;

@@ -349,6 +349,8 @@ __global__ void __launch_bounds__(256, 3) k_cg(CgArgs A, StencilW W) {
 // meets the same bound as the FP64 solver.
 // ---------------------------------------------------------------------------
 #define SEA_MIXED_INNER 1e-4f
+// CTA size of the mixed CG (one pair per CTA at a time)
+#define SEA_CG_THREADS 512
 #define SEA_MIXED_MAX_OUTER 30
 
 struct StencilWf {
@@ -382,9 +384,11 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float bh, floa
 }
 
 // Block sum of compensated (hi, lo) partials in FP32 only: warp butterfly,
-// then every thread adds the warps' results in warp order.  `slots` holds
-// 32 float2 of shared memory, reused only after the next __syncthreads.
-// Returns hi + lo rounded to FP32 (the same value in every thread).
+// then every warp combines the warps' results by a second butterfly (the
+// error-free addition is symmetric in its operands, so every lane ends with
+// the same bits).  `slots` holds 32 float2 of shared memory, reused only
+// after the next __syncthreads.  Returns hi + lo rounded to FP32 (the same
+// value in every thread).
 __device__ __forceinline__ float block_sum_f(float hi, float lo, float2* slots) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -392,12 +396,19 @@ __device__ __forceinline__ float block_sum_f(float hi, float lo, float2* slots) 
     const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
     two_sum_add(hi, lo, bh, bl);
   }
-  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if ((threadIdx.x & 31) == 0) slots[w] = make_float2(hi, lo);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) slots[w] = make_float2(hi, lo);
   __syncthreads();
-  float2 t = slots[0];
-  for (int k = 1; k < nw; ++k) two_sum_add(t.x, t.y, slots[k].x, slots[k].y);
-  return t.x + t.y;
+  const float2 t = lane < nw ? slots[lane] : make_float2(0.f, 0.f);
+  hi = t.x;
+  lo = t.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+    two_sum_add(hi, lo, bh, bl);
+  }
+  return hi + lo;
 }
 
 __device__ __forceinline__ float lap_axis_f(const float* __restrict__ pv, int t, int u, int e,
@@ -421,6 +432,141 @@ __device__ __forceinline__ float neg_lap_f(const float* __restrict__ pv, int t, 
   return (ax + ay) + az;
 }
 
+// Shared-memory layout of the mixed CG's search direction: the pair box
+// with rows of PX = ex + F and planes of PY = ey + F rows (F = SEA_FDP zeros
+// after each row and F zero rows after each plane, which serve as the halo
+// on both sides of the next row or plane) and F zero planes before and after
+// the box.  Every stencil neighbour outside the box then reads a zero.
+__host__ __device__ __forceinline__ int cg_pad_volume(int ex, int ey, int ez) {
+  return (ex + SEA_FDP) * (ey + SEA_FDP) * (ez + 2 * SEA_FDP);
+}
+
+// -Lap_h p at padded index tp: the same products and order as neg_lap_f,
+// with no bounds tests.
+__device__ __forceinline__ float neg_lap_pad(const float* __restrict__ pv, int tp, int PX, int PXY,
+                                             const StencilWf& W) {
+  float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    ax = fmaf(W.ax[0][k], pv[tp - k], ax);
+    ax = fmaf(W.ax[0][k], pv[tp + k], ax);
+  }
+#pragma unroll
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    ay = fmaf(W.ax[1][k], pv[tp - k * PX], ay);
+    ay = fmaf(W.ax[1][k], pv[tp + k * PX], ay);
+  }
+#pragma unroll
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    az = fmaf(W.ax[2][k], pv[tp - k * PXY], az);
+    az = fmaf(W.ax[2][k], pv[tp + k * PXY], az);
+  }
+  az = fmaf(W.center, pv[tp], az);
+  return (ax + ay) + az;
+}
+
+// Block sum of two FP32 values at once (one barrier): warp butterfly, then
+// every warp combines the warps' results by a second butterfly, so every
+// thread gets the same bits.  `slots` holds 32 float2 of shared memory,
+// reused only after the next __syncthreads.
+__device__ __forceinline__ float2 block_sum2_f(float a, float b, float2* slots) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) slots[w] = make_float2(a, b);
+  __syncthreads();
+  float2 t = lane < nw ? slots[lane] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+    t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+  }
+  return t;
+}
+
+// Inner solve in the single-reduction arrangement of CG (Chronopoulos and
+// Gear, 1989): per iteration one stencil product w = A r and one block
+// reduction of (r, r) and (w, r), then
+//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old)
+//   p = r + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s
+// (beta = 0, alpha = gamma / delta at the first step), which is CG in exact
+// arithmetic with two barriers per iteration instead of four.  The residual r
+// lives in shared memory in the padded layout above (the stencil needs no
+// bounds tests); p, s, w and d in global memory (L1-resident).  Stops when
+// (r, r) <= SEA_MIXED_INNER^2 (r0, r0).  For pairs whose padded box fits the
+// shared buffer.  Ends with x += rnorm d (FP64).  Returns the new total of
+// inner iterations (stencil products followed by an update).
+__device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, double rnorm,
+                                             double* __restrict__ x, float* __restrict__ d,
+                                             float* __restrict__ pf, float* __restrict__ sf,
+                                             float* __restrict__ wf, float* __restrict__ rS,
+                                             int n, int ex, int ey, int ez, const StencilWf& Wf,
+                                             float2* fs0, float2* fs1, int inner_total,
+                                             int max_iter) {
+  const int S = blockDim.x;
+  const int PX = ex + SEA_FDP, PXY = PX * (ey + SEA_FDP);
+  const int Vp = PXY * (ez + 2 * SEA_FDP);
+  const int org = SEA_FDP * PXY;  // padded index of box point (0, 0, 0)
+  for (int t = threadIdx.x; t < Vp; t += S) rS[t] = 0.f;
+  __syncthreads();
+  const double inv = 1.0 / rnorm;
+  {
+    BoxWalk w(threadIdx.x, S, ex, ey);
+    for (; w.t < n; w.next(S)) {
+      rS[org + w.z * PXY + w.y * PX + w.x] = (float)(r[w.t] * inv);
+      pf[w.t] = 0.f;
+      sf[w.t] = 0.f;
+      d[w.t] = 0.f;
+    }
+  }
+  __syncthreads();
+  float stop = 0.f, gamma_old = 1.f, alpha_old = 1.f;
+  float2* slots[2] = {fs0, fs1};
+  for (int it = 0;; ++it) {
+    float g = 0.f, dl = 0.f;
+    {
+      BoxWalk w(threadIdx.x, S, ex, ey);
+      for (; w.t < n; w.next(S)) {
+        const int tp = org + w.z * PXY + w.y * PX + w.x;
+        const float wv = neg_lap_pad(rS, tp, PX, PXY, Wf);
+        const float rv = rS[tp];
+        wf[w.t] = wv;
+        g = fmaf(rv, rv, g);
+        dl = fmaf(wv, rv, dl);
+      }
+    }
+    const float2 gd = block_sum2_f(g, dl, slots[it & 1]);
+    const float gamma = gd.x, delta = gd.y;
+    if (it == 0) stop = (float)SEA_MIXED_INNER * (float)SEA_MIXED_INNER * gamma;
+    if (gamma <= stop || inner_total >= max_iter) break;
+    const float beta = it == 0 ? 0.f : gamma / gamma_old;
+    const float alpha = it == 0 ? gamma / delta : gamma / (delta - beta * gamma / alpha_old);
+    {
+      BoxWalk w(threadIdx.x, S, ex, ey);
+      for (; w.t < n; w.next(S)) {
+        const int tp = org + w.z * PXY + w.y * PX + w.x;
+        const float rv = rS[tp];
+        const float pv = fmaf(beta, pf[w.t], rv);
+        const float sv = fmaf(beta, sf[w.t], wf[w.t]);
+        pf[w.t] = pv;
+        sf[w.t] = sv;
+        d[w.t] = fmaf(alpha, pv, d[w.t]);
+        rS[tp] = fmaf(-alpha, sv, rv);
+      }
+    }
+    gamma_old = gamma;
+    alpha_old = alpha;
+    ++inner_total;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+  __syncthreads();  // rS is free for the next pair
+  return inner_total;
+}
+
 struct CgMixedArgs {
   const double* phi;
   int nx, ny, nz;
@@ -438,11 +584,32 @@ struct CgMixedArgs {
   unsigned* status;
   int* queue;
   int warm;       // x holds an initial guess (else the solve starts from 0)
+  int pad_cap;    // floats of shared memory for the padded search direction
 };
+
+// block_sum with the serial combine done by one warp (the same order, so the
+// same bits) and the total broadcast through *bc: an FP64 instruction costs
+// a warp the same time however many of its lanes are active, so the warps of
+// a large CTA should not all repeat the combine.
+__device__ __forceinline__ double block_sum_1w(double v, double* slots, double* bc) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) slots[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += slots[k];
+    if (threadIdx.x == 0) *bc = s;
+  }
+  __syncthreads();
+  return *bc;
+}
 
 // One pair's mixed-precision solve (the whole CTA).
 __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const StencilW& W,
-                                              const StencilWf& Wf, int pidx, double (*red)[32]) {
+                                              const StencilWf& Wf, int pidx, double (*red)[32],
+                                              double* bc, float* pS) {
   const size_t ng = (size_t)A.nx * A.ny * A.nz;
   const int S = blockDim.x;
   const PairInfo P = A.pinfo[pidx];
@@ -468,8 +635,8 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
   }
   if (!A.warm)
     for (int t = threadIdx.x; t < n; t += S) x[t] = 0.0;
-  bb = block_sum(bb, red[0]);
-  rr0 = block_sum(rr0, red[1]);
+  bb = block_sum_1w(bb, red[0], bc);
+  rr0 = block_sum_1w(rr0, red[1], bc);
   __syncthreads();  // both slot arrays are read before their next use
   const double bnorm = sqrt(bb);
   const double target =
@@ -486,6 +653,10 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
     // reductions (compensated partials) all in FP32
     float2* fs0 = reinterpret_cast<float2*>(red[0]);
     float2* fs1 = reinterpret_cast<float2*>(red[1]);
+    if (cg_pad_volume(ex, ey, ez) <= A.pad_cap) {
+      inner_total = inner_cg_smem(r, rnorm, x, d, pf, rf, qf, pS, n, ex, ey, ez, Wf, fs0, fs1,
+                                  inner_total, A.max_iter);
+    } else {
     const double inv = 1.0 / rnorm;
     DotF rr0;
     for (int t = threadIdx.x; t < n; t += S) {
@@ -534,9 +705,11 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
       for (int t = threadIdx.x; t < n; t += S) pf[t] = fmaf(beta, pf[t], rf[t]);
       __syncthreads();
     }
-    // FP64 correction and true residual
+    // FP64 correction
     for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+    }
     __syncthreads();
+    // true residual
     double r2 = 0.0;
     {
       BoxWalk w0(threadIdx.x, S, ex, ey);
@@ -546,7 +719,7 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
         r2 = fma(rt, rt, r2);
       }
     }
-    rnorm = sqrt(block_sum(r2, red[0]));
+    rnorm = sqrt(block_sum_1w(r2, red[0], bc));
     ++outer;
     done = rnorm <= target;
   }
@@ -560,7 +733,7 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
                      wrapi(P.lo[0] + xx, A.nx);
     e = fma(fi[g] * fj[g], x[t], e);
   }
-  e = block_sum(e, red[1]);
+  e = block_sum_1w(e, red[1], bc);
   if (threadIdx.x == 0) {
     if (A.epair) A.epair[pidx] = e * A.dV;
     A.iters[pidx] = capped ? -inner_total : inner_total;
@@ -569,16 +742,18 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
   }
 }
 
-__global__ void __launch_bounds__(256) k_cg_mixed(CgMixedArgs A, StencilW W, StencilWf Wf) {
+__global__ void __launch_bounds__(SEA_CG_THREADS, 1024 / SEA_CG_THREADS) k_cg_mixed(CgMixedArgs A, StencilW W, StencilWf Wf) {
   __shared__ double red[2][32];
   __shared__ int s_item;
+  __shared__ double bc;
+  extern __shared__ float pS[];  // A.pad_cap floats
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= A.P) break;
     const int pidx = A.order[item];
-    cg_pair_mixed(A, W, Wf, pidx, red);
+    cg_pair_mixed(A, W, Wf, pidx, red, &bc, pS);
     __syncthreads();
   }
 }
@@ -599,12 +774,18 @@ struct BatchCg {
   int mixed;
 };
 
-__global__ void __launch_bounds__(256) k_cg_batch(const BatchCg* __restrict__ descs,
-                                                  const int2* __restrict__ items, int total,
-                                                  int* __restrict__ queue) {
+// MIXED: the items are all mixed-form (CTA of SEA_CG_THREADS, as k_cg_mixed)
+// or all FP64 (CTA of 256, as k_cg), so every pair is solved with the same
+// CTA size, hence the same bits, as in its own configuration's launch.
+template <bool MIXED>
+__global__ void __launch_bounds__(MIXED ? SEA_CG_THREADS : 256, MIXED ? 1024 / SEA_CG_THREADS : 2)
+    k_cg_batch(const BatchCg* __restrict__ descs, const int2* __restrict__ items, int total,
+               int* __restrict__ queue) {
   __shared__ double red[2][32];
   __shared__ int s_item;
   __shared__ BatchCg d;
+  __shared__ double bc;
+  extern __shared__ float pS[];  // the largest pad_cap of the descriptors
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
     __syncthreads();
@@ -618,8 +799,8 @@ __global__ void __launch_bounds__(256) k_cg_batch(const BatchCg* __restrict__ de
         dst[w] = src[w];
     }
     __syncthreads();
-    if (d.mixed)
-      cg_pair_mixed(d.m, d.W, d.Wf, d.m.order[it.y], red);
+    if (MIXED)
+      cg_pair_mixed(d.m, d.W, d.Wf, d.m.order[it.y], red, &bc, pS);
     else
       cg_pair_fp64(d.a, d.W, d.a.order[it.y], red);
     __syncthreads();
@@ -687,6 +868,7 @@ static CgMixedArgs mixed_args(sea_ctx* c) {
   A.outers = nullptr;
   A.status = (unsigned*)c->status.p;
   A.queue = (int*)c->queue.p;
+  A.pad_cap = cg_pad_cap(c);
   A.warm = c->cg_warm ? 1 : 0;
   return A;
 }
@@ -719,20 +901,34 @@ static CgArgs fp64_args(sea_ctx* c) {
   return A;
 }
 
+// Shared memory of the mixed CG's padded search direction: the largest
+// padded pair box, at most SEA_CG_PAD_LIMIT floats (four CTAs per SM);
+// pairs above the limit solve on global vectors.
+#define SEA_CG_PAD_LIMIT 13824
+int cg_pad_cap(const sea_ctx* c) {
+  return c->prm.precision == 1 ? std::min(c->cg_pad_max, SEA_CG_PAD_LIMIT) : 0;
+}
+
 cudaError_t launch_cg(sea_ctx* c) {
   if (c->P == 0) return cudaSuccess;
   int nsm = 0, occ = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-  if (c->prm.precision == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_mixed, 256, 0);
-  else
+  const int pad_cap = cg_pad_cap(c);
+  const size_t smem = (size_t)pad_cap * sizeof(float);
+  if (c->prm.precision == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_cg_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(SEA_CG_PAD_LIMIT * sizeof(float)));
+    if (e != cudaSuccess) return e;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_mixed, SEA_CG_THREADS, smem);
+  } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg, 256, 0);
+  }
   if (occ < 1) occ = 1;
   const int grid = min(c->P, nsm * occ);
   cudaMemsetAsync(c->queue.p, 0, sizeof(int), c->stream);
   const StencilW W = make_weights(c);
   if (c->prm.precision == 1)
-    k_cg_mixed<<<grid, 256, 0, c->stream>>>(mixed_args(c), W, make_weights_f(W));
+    k_cg_mixed<<<grid, SEA_CG_THREADS, smem, c->stream>>>(mixed_args(c), W, make_weights_f(W));
   else
     k_cg<<<grid, 256, 0, c->stream>>>(fp64_args(c), W);
   c->launches += 1;
@@ -785,15 +981,21 @@ void make_batch_desc(sea_ctx* c, void* out) {
 size_t batch_desc_bytes() { return sizeof(BatchCg); }
 
 cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, const int2* items,
-                            int total, int* queue) {
+                            int total, int* queue, int pad_cap, bool mixed) {
   if (total == 0) return cudaSuccess;
   int nsm = 0, occ = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_batch, 256, 0);
-  if (occ < 1) occ = 1;
-  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  const size_t smem = (size_t)pad_cap * sizeof(float);
+  const int threads = mixed ? SEA_CG_THREADS : 256;
+  auto kern = mixed ? k_cg_batch<true> : k_cg_batch<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(SEA_CG_PAD_LIMIT * sizeof(float)));
   if (e != cudaSuccess) return e;
-  k_cg_batch<<<min(total, nsm * occ), 256, 0, st>>>((const BatchCg*)descs, items, total, queue);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+  if (occ < 1) occ = 1;
+  e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  kern<<<min(total, nsm * occ), threads, smem, st>>>((const BatchCg*)descs, items, total, queue);
   return cudaGetLastError();
 }
 

@@ -298,26 +298,39 @@ __global__ void k_fill_pairs(const int* __restrict__ kept, const int* __restrict
   pn[p] = P.n;
 }
 
-// Single-CTA exclusive scan of P sizes into 64-bit offsets; total in *tot.
+// Single-CTA exclusive scan of P sizes into 64-bit offsets; total in *tot,
+// and the largest pair box in the mixed CG's padded shared-memory layout
+// ((ex + F)(ey + F)(ez + 2F) floats, F = SEA_FDP) in *maxpad.
 __global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__ count,
-                             long long* __restrict__ off, long long* __restrict__ tot) {
+                             const PairInfo* __restrict__ pinfo, long long* __restrict__ off,
+                             long long* __restrict__ tot, int* __restrict__ maxpad) {
   __shared__ long long part[1024];
+  __shared__ int pmax[1024];
   const int n = *count;
   const int T = blockDim.x;
   const int chunk = (n + T - 1) / T;
   const int b = chunk * threadIdx.x, e = min(n, b + chunk);
   long long s = 0;
-  for (int x = b; x < e; ++x) s += sz[x];
+  int pm = 0;
+  for (int x = b; x < e; ++x) {
+    s += sz[x];
+    const PairInfo P = pinfo[x];
+    pm = max(pm, (P.ext[0] + SEA_FDP) * (P.ext[1] + SEA_FDP) * (P.ext[2] + 2 * SEA_FDP));
+  }
   part[threadIdx.x] = s;
+  pmax[threadIdx.x] = pm;
   __syncthreads();
   if (threadIdx.x == 0) {
     long long acc = 0;
+    int m = 0;
     for (int t = 0; t < T; ++t) {
       long long v = part[t];
       part[t] = acc;
       acc += v;
+      m = max(m, pmax[t]);
     }
     *tot = acc;
+    *maxpad = m;
   }
   __syncthreads();
   long long pos = part[threadIdx.x];
@@ -363,7 +376,7 @@ cudaError_t launch_plan_boxes(sea_ctx* c) {
 // Candidates, proto-pair compaction, screening, kept compaction, pair
 // records, unknown offsets and the CG order, all with device-side counts:
 // counts[0] = proto pairs, counts[1] = pairs, *(long long*)(counts + 4) =
-// total unknowns.  Grids are sized for the worst case (every candidate).
+// total unknowns, counts[10] = largest padded pair box.  Grids are sized for the worst case (every candidate).
 cudaError_t launch_plan_pairs(sea_ctx* c) {
   const int n = c->n_orb;
   const long long ncand = (long long)n * (n + 1) / 2;
@@ -384,7 +397,8 @@ cudaError_t launch_plan_pairs(sea_ctx* c) {
                                           (const double*)c->cand_S.p, n, (PairInfo*)c->pinfo.p,
                                           (double*)c->pS.p, (int*)c->psize.p);
   k_scan_sizes<<<1, 1024, 0, c->stream>>>((const int*)c->psize.p, counts + 1,
-                                          (long long*)c->voff.p, (long long*)(counts + 4));
+                                          (const PairInfo*)c->pinfo.p, (long long*)c->voff.p,
+                                          (long long*)(counts + 4), counts + 10);
   k_lpt_order<<<gc, 256, 0, c->stream>>>((const int*)c->psize.p, counts + 1, (int*)c->order.p);
   c->launches += 7;
   return cudaGetLastError();

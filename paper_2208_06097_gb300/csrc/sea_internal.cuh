@@ -306,6 +306,7 @@ struct sea_ctx {
   // plan sizes (host copies)
   int P = 0, Pproto = 0, E = 0;
   long long U = 0, WC = 0, max_window = 0;
+  int cg_pad_max = 0;  // largest zero-padded pair box (floats), for the mixed CG
 
   sea_stats stats{};
 
@@ -363,7 +364,8 @@ cudaError_t launch_cg(sea_ctx* c);
 void make_batch_desc(sea_ctx* c, void* out);
 size_t batch_desc_bytes();
 cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, const int2* items,
-                            int total, int* queue);
+                            int total, int* queue, int pad_cap, bool mixed);
+int cg_pad_cap(const sea_ctx* c);
 cudaError_t launch_entries(sea_ctx* c);
 cudaError_t launch_accumulate(sea_ctx* c, double* out);
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
