@@ -260,7 +260,27 @@ struct CompF {
     s = t;
     c += (err + e) + x;
   }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  // sgn * (s + c) as FP64, with integer operations only: both terms as
+  // fixed-point integers on the larger one's exponent (truncating the
+  // smaller one's bits below 2^-38 of it), then one rounding to nearest.
+  // FP32 subnormals count as zero.
+  __device__ __forceinline__ double value(bool negate) const {
+    const unsigned bs = __float_as_uint(s), bc = __float_as_uint(c);
+    const int es = (int)((bs >> 23) & 0xFF), ec = (int)((bc >> 23) & 0xFF);
+    const int E = max(es, ec);
+    if (E == 0) return 0.0;
+    auto fixed = [&](unsigned b, int e) -> long long {
+      if (e == 0) return 0;
+      const int sh = E - e;
+      if (sh > 62) return 0;
+      const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u) << 38;
+      const long long v = m >> sh;
+      return (b >> 31) ? -v : v;
+    };
+    long long X = fixed(bs, es) + fixed(bc, ec);
+    if (negate) X = -X;
+    return scaled_i64(X, E - 150 - 38);
+  }
 };
 
 // v = hi + lo with integer operations only (no FP64 instruction): hi keeps
@@ -325,10 +345,11 @@ __global__ void __launch_bounds__(256)
     }
   }
   if (g < 0) return;
+  const bool negate = sign < 0.0;
 #pragma unroll
   for (int u = 0; u < 16; ++u) {
     const int v = v0 + vh * 16 + u;
-    if (v < m) out[(size_t)v * ng + g] = sign * acc[u].value();
+    if (v < m) out[(size_t)v * ng + g] = acc[u].value(negate);
   }
 }
 

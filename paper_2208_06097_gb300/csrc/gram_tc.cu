@@ -239,26 +239,6 @@ __device__ __forceinline__ int float_int(float f) {
   return (u >> 31) ? -mag : mag;
 }
 
-// v 2^e2 rounded to the nearest FP64 value (ties to even); 0 if below the
-// normal range.  Integer operations only.
-__device__ __forceinline__ double scaled_i64(long long v, int e2) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = (unsigned long long)v & 0x8000000000000000ULL;
-  unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  a <<= lz;
-  unsigned long long mnt = a >> 11;
-  const unsigned rem = (unsigned)(a & 0x7FF);
-  if (rem > 0x400u || (rem == 0x400u && (mnt & 1ULL))) ++mnt;
-  int ex = 63 - lz + e2 + 1023;
-  if (mnt >> 53) {
-    mnt >>= 1;
-    ++ex;
-  }
-  if (ex <= 0) return 0.0;
-  return __longlong_as_double(
-      (long long)(sgn | ((unsigned long long)ex << 52) | (mnt & 0xFFFFFFFFFFFFFULL)));
-}
 
 // W digits, once per W: for every slot s of every tile list and half h,
 // wdig[((s * 2 + h) * DIG + k) * 8 + u] = the 8 BF16 digits (16 bytes) of

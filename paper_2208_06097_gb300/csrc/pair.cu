@@ -432,29 +432,32 @@ __device__ __forceinline__ float neg_lap_f(const float* __restrict__ pv, int t, 
   return (ax + ay) + az;
 }
 
-// Shared-memory layout of the mixed CG's search direction: the pair box
-// with rows of PX = ex + F and planes of PY = ey + F rows (F = SEA_FDP zeros
-// after each row and F zero rows after each plane, which serve as the halo
-// on both sides of the next row or plane) and F zero planes before and after
-// the box.  Every stencil neighbour outside the box then reads a zero.
+// Shared-memory layout of the mixed CG's residual: the pair box's planes of
+// ex x ey points stored row after row (so consecutive points of a warp sit
+// in consecutive banks), each plane followed by F = SEA_FDP zero rows, which
+// serve as the y halo on both sides, and F zero planes before and after the
+// box for the z halo.  Box point t = (z ey + y) ex + x sits at
+// org + t + z F ex.  Neighbours along y and z outside the box read zeros;
+// along x they are masked.
 __host__ __device__ __forceinline__ int cg_pad_volume(int ex, int ey, int ez) {
-  return (ex + SEA_FDP) * (ey + SEA_FDP) * (ez + 2 * SEA_FDP);
+  return ex * (ey + SEA_FDP) * (ez + 2 * SEA_FDP);
 }
 
-// -Lap_h p at padded index tp: the same products and order as neg_lap_f,
-// with no bounds tests.
-__device__ __forceinline__ float neg_lap_pad(const float* __restrict__ pv, int tp, int PX, int PXY,
-                                             const StencilWf& W) {
+// -Lap_h r at padded index tp (box x coordinate x, row length ex, plane
+// size PXY): the same products and order as neg_lap_f.
+__device__ __forceinline__ float neg_lap_pad(const float* __restrict__ pv, int tp, int x, int ex,
+                                             int PXY, const StencilWf& W) {
   float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
   for (int k = 1; k <= SEA_FDP; ++k) {
-    ax = fmaf(W.ax[0][k], pv[tp - k], ax);
-    ax = fmaf(W.ax[0][k], pv[tp + k], ax);
+    const float L = pv[tp - k], R = pv[tp + k];
+    ax = fmaf(W.ax[0][k], x - k >= 0 ? L : 0.f, ax);
+    ax = fmaf(W.ax[0][k], x + k < ex ? R : 0.f, ax);
   }
 #pragma unroll
   for (int k = 1; k <= SEA_FDP; ++k) {
-    ay = fmaf(W.ax[1][k], pv[tp - k * PX], ay);
-    ay = fmaf(W.ax[1][k], pv[tp + k * PX], ay);
+    ay = fmaf(W.ax[1][k], pv[tp - k * ex], ay);
+    ay = fmaf(W.ax[1][k], pv[tp + k * ex], ay);
   }
 #pragma unroll
   for (int k = 1; k <= SEA_FDP; ++k) {
@@ -494,8 +497,9 @@ __device__ __forceinline__ float2 block_sum2_f(float a, float b, float2* slots) 
 //   p = r + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s
 // (beta = 0, alpha = gamma / delta at the first step), which is CG in exact
 // arithmetic with two barriers per iteration instead of four.  The residual r
-// lives in shared memory in the padded layout above (the stencil needs no
-// bounds tests); p, s, w and d in global memory (L1-resident).  Stops when
+// lives in shared memory in the padded layout above (no bounds tests along
+// y and z, consecutive points in consecutive banks); p, s, w and d in global
+// memory (L1-resident).  Stops when
 // (r, r) <= SEA_MIXED_INNER^2 (r0, r0).  For pairs whose padded box fits the
 // shared buffer.  Ends with x += rnorm d (FP64).  Returns the new total of
 // inner iterations (stencil products followed by an update).
@@ -507,7 +511,7 @@ __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, doubl
                                              float2* fs0, float2* fs1, int inner_total,
                                              int max_iter) {
   const int S = blockDim.x;
-  const int PX = ex + SEA_FDP, PXY = PX * (ey + SEA_FDP);
+  const int PXY = ex * (ey + SEA_FDP), gap = SEA_FDP * ex;
   const int Vp = PXY * (ez + 2 * SEA_FDP);
   const int org = SEA_FDP * PXY;  // padded index of box point (0, 0, 0)
   for (int t = threadIdx.x; t < Vp; t += S) rS[t] = 0.f;
@@ -516,7 +520,7 @@ __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, doubl
   {
     BoxWalk w(threadIdx.x, S, ex, ey);
     for (; w.t < n; w.next(S)) {
-      rS[org + w.z * PXY + w.y * PX + w.x] = (float)(r[w.t] * inv);
+      rS[org + w.t + w.z * gap] = (float)(r[w.t] * inv);
       pf[w.t] = 0.f;
       sf[w.t] = 0.f;
       d[w.t] = 0.f;
@@ -530,8 +534,8 @@ __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, doubl
     {
       BoxWalk w(threadIdx.x, S, ex, ey);
       for (; w.t < n; w.next(S)) {
-        const int tp = org + w.z * PXY + w.y * PX + w.x;
-        const float wv = neg_lap_pad(rS, tp, PX, PXY, Wf);
+        const int tp = org + w.t + w.z * gap;
+        const float wv = neg_lap_pad(rS, tp, w.x, ex, PXY, Wf);
         const float rv = rS[tp];
         wf[w.t] = wv;
         g = fmaf(rv, rv, g);
@@ -547,7 +551,7 @@ __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, doubl
     {
       BoxWalk w(threadIdx.x, S, ex, ey);
       for (; w.t < n; w.next(S)) {
-        const int tp = org + w.z * PXY + w.y * PX + w.x;
+        const int tp = org + w.t + w.z * gap;
         const float rv = rS[tp];
         const float pv = fmaf(beta, pf[w.t], rv);
         const float sv = fmaf(beta, sf[w.t], wf[w.t]);

@@ -15,48 +15,67 @@
 
 namespace sea {
 
-// One CTA per (z-plane, orbital): row sums (thread per y) and column sums
-// (thread per x) of phi^2 over the plane, each square accumulated with one
-// fused multiply-add in ascending order.  The plane is staged through shared
-// memory in chunks of whole rows (coalesced loads); column sums carry over
-// the chunks in registers, so the y order is kept.
-#define SEA_RC_CHUNK 4096
-__global__ void __launch_bounds__(256)
+// One CTA of four warps per (z-plane, orbital): row sums (lane per y) and
+// column sums (lane per x) of phi^2 over the plane, each square accumulated
+// with one fused multiply-add in ascending order.  The plane is staged
+// through shared memory in chunks of RC_ROWS whole rows (coalesced loads;
+// row pitch nx + 1 so that the lanes of a row-sum warp, one row each, hit
+// distinct banks).  In chunk k warp k % 4 forms the chunk's row sums and
+// the other three warps continue the column sums, which carry over the
+// chunks in shared memory, so the y order is kept.  On this part an FP64
+// instruction costs a warp the same time whatever its active lanes, so the
+// row sums take whole warps (32 rows) and the roles rotate to spread them
+// over the sub-partitions.
+#define RC_ROWS 32
+#define RC_SMEM_DOUBLES 6144
+__host__ __device__ __forceinline__ int rc_rows(int nx) {
+  return min(RC_ROWS, max(1, (RC_SMEM_DOUBLES - nx) / (nx + 1)));
+}
+
+__global__ void __launch_bounds__(128)
     k_row_col_sums(const double* __restrict__ phi, int nx, int ny, int nz,
                    double* __restrict__ R, double* __restrict__ C) {
-  __shared__ double tile[SEA_RC_CHUNK];
+  extern __shared__ double rc_sm[];  // [rows][nx + 1] tile, then [nx] column sums
+  const int pitch = nx + 1;
+  const int rows = rc_rows(nx);
+  double* tile = rc_sm;
+  double* col = rc_sm + rows * pitch;
   const int z = blockIdx.x, i = blockIdx.y;
   const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
-  const int rows = max(1, SEA_RC_CHUNK / nx);
-  double col[4] = {0.0, 0.0, 0.0, 0.0};  // nx <= 1024 = 4 x 256 threads
-  for (int y0 = 0; y0 < ny; y0 += rows) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) col[x] = 0.0;
+  for (int y0 = 0, k = 0; y0 < ny; y0 += rows, ++k) {
     const int nr = min(rows, ny - y0);
     __syncthreads();
-    for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) tile[q] = plane[(size_t)y0 * nx + q];
+    for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
+      const int r = q / nx, x = q - r * nx;
+      tile[r * pitch + x] = plane[(size_t)y0 * nx + q];
+    }
     __syncthreads();
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
-      double sr = 0.0;
-      for (int x = 0; x < nx; ++x) {
-        const double v = tile[r * nx + x];
-        sr = fma(v, v, sr);
-      }
-      R[((size_t)i * nz + z) * ny + y0 + r] = sr;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int x = threadIdx.x + u * blockDim.x;
-      if (x < nx)
-        for (int r = 0; r < nr; ++r) {
-          const double v = tile[r * nx + x];
-          col[u] = fma(v, v, col[u]);
+    const int rw = k & 3;  // this chunk's row-sum warp
+    if (w == rw) {
+      for (int r = lane; r < nr; r += 32) {
+        double sr = 0.0;
+        for (int x = 0; x < nx; ++x) {
+          const double v = tile[r * pitch + x];
+          sr = fma(v, v, sr);
         }
+        R[((size_t)i * nz + z) * ny + y0 + r] = sr;
+      }
+    } else {
+      const int cw = (w - rw + 3) & 3;  // 0, 1, 2 among the column warps
+      for (int x = cw * 32 + lane; x < nx; x += 96) {
+        double sc = col[x];
+        for (int r = 0; r < nr; ++r) {
+          const double v = tile[r * pitch + x];
+          sc = fma(v, v, sc);
+        }
+        col[x] = sc;
+      }
     }
   }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int x = threadIdx.x + u * blockDim.x;
-    if (x < nx) C[((size_t)i * nz + z) * nx + x] = col[u];
-  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) C[((size_t)i * nz + z) * nx + x] = col[x];
 }
 
 // Thread per (orbital, axis, coordinate): the three marginals of |phi|^2 dV.
@@ -300,7 +319,7 @@ __global__ void k_fill_pairs(const int* __restrict__ kept, const int* __restrict
 
 // Single-CTA exclusive scan of P sizes into 64-bit offsets; total in *tot,
 // and the largest pair box in the mixed CG's padded shared-memory layout
-// ((ex + F)(ey + F)(ez + 2F) floats, F = SEA_FDP) in *maxpad.
+// (ex (ey + F)(ez + 2F) floats, F = SEA_FDP) in *maxpad.
 __global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__ count,
                              const PairInfo* __restrict__ pinfo, long long* __restrict__ off,
                              long long* __restrict__ tot, int* __restrict__ maxpad) {
@@ -315,7 +334,7 @@ __global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__
   for (int x = b; x < e; ++x) {
     s += sz[x];
     const PairInfo P = pinfo[x];
-    pm = max(pm, (P.ext[0] + SEA_FDP) * (P.ext[1] + SEA_FDP) * (P.ext[2] + 2 * SEA_FDP));
+    pm = max(pm, P.ext[0] * (P.ext[1] + SEA_FDP) * (P.ext[2] + 2 * SEA_FDP));
   }
   part[threadIdx.x] = s;
   pmax[threadIdx.x] = pm;
@@ -359,8 +378,9 @@ __global__ void k_lpt_order(const int* __restrict__ sz, const int* __restrict__ 
 cudaError_t launch_plan_boxes(sea_ctx* c) {
   const int n = c->n_orb, nx = c->N[0], ny = c->N[1], nz = c->N[2];
   const int Nmax = max(nx, max(ny, nz));
-  k_row_col_sums<<<dim3(nz, n), 256, 0, c->stream>>>((const double*)c->phi.p, nx, ny, nz,
-                                                     (double*)c->rowsum.p, (double*)c->colsum.p);
+  const size_t rc_smem = ((size_t)rc_rows(nx) * (nx + 1) + nx) * sizeof(double);
+  k_row_col_sums<<<dim3(nz, n), 128, rc_smem, c->stream>>>(
+      (const double*)c->phi.p, nx, ny, nz, (double*)c->rowsum.p, (double*)c->colsum.p);
   const int tot = n * 3 * Nmax;
   k_marginals<<<(tot + 255) / 256, 256, 0, c->stream>>>(
       (const double*)c->rowsum.p, (const double*)c->colsum.p, n, nx, ny, nz, Nmax, c->dV,
