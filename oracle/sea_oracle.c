@@ -262,52 +262,54 @@ int ora_cg(const double* b, double* x, int ex, int ey, int ez, const double h[3]
 /* Domain truncation, Eq. oii: one tight periodic AABB per orbital.     */
 /* ------------------------------------------------------------------ */
 
-/* Per-axis marginals of |phi|^2 dV, each summed in a fixed order:
- *   R[z][y] = sum_x phi^2 (x ascending)   C[z][x] = sum_y phi^2 (y ascending)
- *   mz[z] = (sum_y R[z][y]) dV           my[y] = (sum_z R[z][y]) dV
- *   mx[x] = (sum_z C[z][x]) dV            (outer sums ascending).
- * Each square is accumulated with one fused multiply-add, s = fma(v, v, s)
- * (one rounding per term; the paper fixes no rounding for Eq. oii). */
+/* Per-axis marginals of |phi|^2 dV, with exact sums.  Each square is
+ * taken on the fixed-point grid 2^-64:
+ *   F(v) = min(floor(v^2 2^64), 2^96)      (v^2 >= 2^32 saturates),
+ * computed exactly from v's integer significand; the marginal sums of F
+ * are exact integers (so their order is immaterial) and
+ *   m_a(x) = fl(fl(2^-64 sum F) dV)
+ * with one rounding to nearest for the sum and one for the product.  The
+ * paper fixes no rounding for the marginals of Eq. oii; this reading makes
+ * them independent of any summation order.  Squares below 2^-64 (|v| below
+ * about 2.3e-10) count as zero, which moves a marginal by at most
+ * (points in a plane) 2^-64 dV. */
+typedef unsigned __int128 u128;
+
+static u128 sq_fixed(double v) {
+  if (v == 0.0 || !isfinite(v)) return 0;
+  int e;
+  double fr = frexp(fabs(v), &e); /* |v| = fr 2^e, fr in [0.5, 1) */
+  if (e > 16) return (u128)1 << 96; /* |v| >= 2^16: v^2 >= 2^32 */
+  /* |v| = m 2^(e - 53) with the integer m = fr 2^53 < 2^53 */
+  unsigned long long m = (unsigned long long)ldexp(fr, 53);
+  u128 mm = (u128)m * m; /* v^2 = mm 2^(2e - 106) */
+  int sh = 2 * e - 106 + 64; /* F = floor(mm 2^sh) */
+  if (sh >= 0) return mm << sh; /* sh <= -10 for e <= 16; kept for clarity */
+  if (-sh >= 128) return 0;
+  return mm >> (-sh);
+}
+
 void ora_marginals(const double* f, const int N[3], double dV, double* mx,
                    double* my, double* mz) {
   int nx = N[0], ny = N[1], nz = N[2];
-  double* R = (double*)malloc((size_t)nz * ny * sizeof(double));
-  double* C = (double*)malloc((size_t)nz * nx * sizeof(double));
+  u128* sx = (u128*)calloc((size_t)nx, sizeof(u128));
+  u128* sy = (u128*)calloc((size_t)ny, sizeof(u128));
+  u128* sz = (u128*)calloc((size_t)nz, sizeof(u128));
   for (int z = 0; z < nz; ++z)
-    for (int y = 0; y < ny; ++y) {
-      double s = 0.0;
+    for (int y = 0; y < ny; ++y)
       for (int x = 0; x < nx; ++x) {
-        double v = f[((size_t)z * ny + y) * nx + x];
-        s = fma(v, v, s);
+        u128 F = sq_fixed(f[((size_t)z * ny + y) * nx + x]);
+        sx[x] += F;
+        sy[y] += F;
+        sz[z] += F;
       }
-      R[(size_t)z * ny + y] = s;
-    }
-  for (int z = 0; z < nz; ++z)
-    for (int x = 0; x < nx; ++x) {
-      double s = 0.0;
-      for (int y = 0; y < ny; ++y) {
-        double v = f[((size_t)z * ny + y) * nx + x];
-        s = fma(v, v, s);
-      }
-      C[(size_t)z * nx + x] = s;
-    }
-  for (int z = 0; z < nz; ++z) {
-    double s = 0.0;
-    for (int y = 0; y < ny; ++y) s = s + R[(size_t)z * ny + y];
-    mz[z] = s * dV;
-  }
-  for (int y = 0; y < ny; ++y) {
-    double s = 0.0;
-    for (int z = 0; z < nz; ++z) s = s + R[(size_t)z * ny + y];
-    my[y] = s * dV;
-  }
-  for (int x = 0; x < nx; ++x) {
-    double s = 0.0;
-    for (int z = 0; z < nz; ++z) s = s + C[(size_t)z * nx + x];
-    mx[x] = s * dV;
-  }
-  free(R);
-  free(C);
+  /* (double) of an unsigned 128-bit integer rounds to nearest, ties even */
+  for (int x = 0; x < nx; ++x) mx[x] = ldexp((double)sx[x], -64) * dV;
+  for (int y = 0; y < ny; ++y) my[y] = ldexp((double)sy[y], -64) * dV;
+  for (int z = 0; z < nz; ++z) mz[z] = ldexp((double)sz[z], -64) * dV;
+  free(sx);
+  free(sy);
+  free(sz);
 }
 
 /* Shortest cyclic interval [s, s+len) whose complement holds at most tail

@@ -38,8 +38,49 @@ def test_marginals_sum_to_total(h2o8):
     mx, my, mz = O.marginals(f, h2o8.dV)
     tot = (f * f).sum() * h2o8.dV
     for m, ax in ((mx, (0, 1)), (my, (0, 2)), (mz, (1, 2))):
-        np.testing.assert_allclose(m, (f * f).sum(axis=ax) * h2o8.dV, rtol=1e-12)
+        # squares below the 2^-64 grid count as zero: at most one grid unit
+        # per point of the plane
+        plane = f.size // m.size
+        np.testing.assert_allclose(m, (f * f).sum(axis=ax) * h2o8.dV, rtol=1e-12,
+                                   atol=plane * 2.0 ** -64 * h2o8.dV)
         assert m.sum() == pytest.approx(tot, rel=1e-13)
+
+
+def _exact_marginals(f, dV):
+    """Eq. oii marginals under the exact reading, with Python integers: each
+    square on the grid 2^-64 (floor, saturated at 2^96), exact sums, one
+    rounding to nearest of the sum (fractions.Fraction -> float) and one of
+    the product with dV."""
+    from fractions import Fraction
+    def F(v):
+        p, q = float(v).as_integer_ratio()  # |v| = p/q, q a power of two
+        val = (p * p << 64) // (q * q)
+        return min(val, 1 << 96)
+    nz, ny, nx = f.shape
+    Fs = [[[F(f[z, y, x]) for x in range(nx)] for y in range(ny)] for z in range(nz)]
+    mx = [sum(Fs[z][y][x] for z in range(nz) for y in range(ny)) for x in range(nx)]
+    my = [sum(Fs[z][y][x] for z in range(nz) for x in range(nx)) for y in range(ny)]
+    mz = [sum(Fs[z][y][x] for y in range(ny) for x in range(nx)) for z in range(nz)]
+    conv = lambda S: float(Fraction(S, 1 << 64)) * dV
+    return [np.array([conv(S) for S in m]) for m in (mx, my, mz)]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_marginals_are_exact_fixed_point_sums(seed):
+    r = np.random.default_rng(seed)
+    shape = (3, 4, 5)
+    # magnitudes from far below the 2^-64 grid of the squares up to the
+    # saturation point, both signs, a few exact zeros
+    f = r.standard_normal(shape) * 10.0 ** r.uniform(-14, 5, size=shape)
+    f[0, 0, 0] = 0.0
+    f[1, 2, 3] = 2.0 ** 16  # square exactly 2^32: saturates to 2^96
+    f[2, 3, 4] = -(2.0 ** 16) * (1 - 2.0 ** -52)  # just below saturation
+    f[0, 1, 2] = 2.0 ** -32  # square exactly one grid unit
+    f[0, 1, 3] = 2.0 ** -32 * (1 - 2.0 ** -53)  # square just below one unit
+    dV = 0.0146
+    got = O.marginals(f, dV)
+    for g, e in zip(got, _exact_marginals(f, dV)):
+        np.testing.assert_array_equal(g, e)
 
 
 def test_boxes_cover_mass_and_are_tight(h2o8):
