@@ -247,8 +247,8 @@ sea_status sea_set_orbitals(sea_ctx* c, const double* phi, int n_orb, int on_dev
   c->n_orb = n_orb;
   const long long ncand = (long long)n_orb * (n_orb + 1) / 2;
   const int Nmax = std::max(c->N[0], std::max(c->N[1], c->N[2]));
-  SEA_ALLOC(rowsum, (size_t)n_orb * c->N[2] * std::max(c->N[0], c->N[1]) * sizeof(double));
-  SEA_ALLOC(colsum, (size_t)n_orb * c->N[2] * c->N[0] * sizeof(double));
+  SEA_ALLOC(rowsum, (size_t)n_orb * c->N[2] * c->N[1] * sizeof(ulonglong2));
+  SEA_ALLOC(colsum, (size_t)n_orb * c->N[2] * c->N[0] * sizeof(ulonglong2));
   SEA_ALLOC(marg, (size_t)n_orb * 3 * Nmax * sizeof(double));
   SEA_ALLOC(box, (size_t)n_orb * 6 * sizeof(int));
   SEA_ALLOC(cand_flag, ncand * sizeof(int));

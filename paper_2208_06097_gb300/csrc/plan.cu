@@ -1,105 +1,212 @@
 // plan.cu -- domain truncation (Eq. oii) and pair selection (Eq. sij).
 //
 // Both steps end in integer decisions taken on FP64 sums.  Every sum here
-// has a fixed order and a fixed rounding (explicit fma, or __dmul_rn /
-// __dadd_rn where no fusion is wanted), so the decisions do not depend on
-// the launch shape and match the oracle bit for bit:
-//   rows R[z][y] = sum_x phi^2 (x ascending), columns C[z][x] = sum_y phi^2
-//   (y ascending), each square added by one fused multiply-add; marginals m_z = (sum_y R) dV, m_y = (sum_z R) dV,
-//   m_x = (sum_z C) dV (ascending); the box of each axis is the shortest
-//   cyclic interval whose outside mass T - inside <= eps/3, inside summed
-//   from the interval start upward, T the ascending total (ties: lowest
-//   start); S_|ij| sums |phi_i phi_j| over each (z, y) row of Omega_ij in x
-//   order, then the rows in (z, y) order, then multiplies by dV.
+// is either exact or has a fixed order and a fixed rounding (explicit fma,
+// or __dmul_rn / __dadd_rn where no fusion is wanted), so the decisions do
+// not depend on the launch shape and match the oracle bit for bit:
+//   marginals m_a(x) = fl(fl(2^-64 sum F(phi)) dV) with the exact integer
+//   sums of F(v) = min(floor(v^2 2^64), 2^96) over each plane normal to
+//   axis a; the box of each axis is the shortest cyclic interval whose
+//   outside mass T - inside <= eps/3, inside summed from the interval
+//   start upward, T the ascending total (ties: lowest start); S_|ij| sums
+//   |phi_i phi_j| over each (z, y) row of Omega_ij in x order, then the
+//   rows in (z, y) order, then multiplies by dV.
 #include "sea_internal.cuh"
 
 namespace sea {
 
-// One CTA of four warps per (z-plane, orbital): row sums (lane per y) and
-// column sums (lane per x) of phi^2 over the plane, each square accumulated
-// with one fused multiply-add in ascending order.  The plane is staged
-// through shared memory in chunks of RC_ROWS whole rows (coalesced loads;
-// row pitch nx + 1 so that the lanes of a row-sum warp, one row each, hit
-// distinct banks).  In chunk k warp k % 4 forms the chunk's row sums and
-// the other three warps continue the column sums, which carry over the
-// chunks in shared memory, so the y order is kept.  On this part an FP64
-// instruction costs a warp the same time whatever its active lanes, so the
-// row sums take whole warps (32 rows) and the roles rotate to spread them
-// over the sub-partitions.
+// F(v) = min(floor(v^2 2^64), 2^96), exactly, as two 48-bit limbs
+// (F = lo + hi 2^48).  |v| = m 2^(eb - 1075) with the 53-bit significand m
+// and biased exponent eb, so F = floor(m^2 2^(2 eb - 2086)); subnormals and
+// zeros give 0, |v| >= 2^16 (eb >= 1039) saturates.  Integer operations only.
+__device__ __forceinline__ void sq_fixed(double v, unsigned long long& lo, unsigned long long& hi) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int eb = (int)((b >> 52) & 0x7FF);
+  const int r = 2086 - 2 * eb;  // right shift of m^2
+  if (eb == 0 || r >= 106) {
+    lo = hi = 0;
+    return;
+  }
+  if (eb >= 1039) {
+    lo = 0;
+    hi = 1ULL << 48;
+    return;
+  }
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+  const unsigned long long ml = m & 0xFFFFFFFFULL, mh = m >> 32;  // mh < 2^21
+  // m^2 = P1 2^64 + P0 (128-bit)
+  const unsigned long long a0 = ml * ml, a1 = mh * ml, a2 = mh * mh;
+  unsigned long long P0 = a0 + (a1 << 33);
+  unsigned long long P1 = a2 + (a1 >> 31) + (P0 < a0 ? 1ULL : 0ULL);
+  // F = (P1 2^64 + P0) >> r, r in [10, 106)
+  unsigned long long F0, F1;
+  if (r < 64) {
+    F0 = (P0 >> r) | (P1 << (64 - r));
+    F1 = P1 >> r;
+  } else {
+    F0 = P1 >> (r - 64);
+    F1 = 0;
+  }
+  lo = F0 & 0xFFFFFFFFFFFFULL;
+  hi = (F0 >> 48) | (F1 << 16);
+}
+
+// One CTA of four warps per (z-plane, orbital): row sums and column sums of
+// F(phi) over the plane, as 48-bit limb sums (exact: a row or column has at
+// most 1024 points).  The plane is staged through shared memory as F values
+// in chunks of whole rows (coalesced loads, RC_BATCH in flight per thread;
+// row pitch nx + 1 so that lanes reading different rows hit distinct
+// banks).  Warp w sums quarter w of every row of the chunk (lane per row),
+// the quarters are then added; thread per column carries the column sums
+// over the chunks in shared memory.  All sums are exact, so the split is
+// free.
 #define RC_ROWS 32
-#define RC_SMEM_DOUBLES 6144
+#define RC_SMEM_ELEMS 3200
+#define RC_BATCH 8
 __host__ __device__ __forceinline__ int rc_rows(int nx) {
-  return min(RC_ROWS, max(1, (RC_SMEM_DOUBLES - nx) / (nx + 1)));
+  return min(RC_ROWS, max(1, (RC_SMEM_ELEMS - nx) / (nx + 1)));
+}
+__host__ __forceinline__ size_t rc_smem_bytes(int nx) {
+  return ((size_t)rc_rows(nx) * (nx + 1) + nx) * sizeof(ulonglong2);
 }
 
 __global__ void __launch_bounds__(128)
     k_row_col_sums(const double* __restrict__ phi, int nx, int ny, int nz,
-                   double* __restrict__ R, double* __restrict__ C) {
-  extern __shared__ double rc_sm[];  // [rows][nx + 1] tile, then [nx] column sums
+                   ulonglong2* __restrict__ R, ulonglong2* __restrict__ C) {
+  extern __shared__ ulonglong2 rc_sm[];  // [rows][nx + 1] F tile, then [nx] column sums
+  __shared__ ulonglong2 rpart[4 * RC_ROWS];  // row partial sums, one per warp
   const int pitch = nx + 1;
   const int rows = rc_rows(nx);
-  double* tile = rc_sm;
-  double* col = rc_sm + rows * pitch;
+  ulonglong2* tile = rc_sm;
+  ulonglong2* col = rc_sm + rows * pitch;
   const int z = blockIdx.x, i = blockIdx.y;
   const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int x = threadIdx.x; x < nx; x += blockDim.x) col[x] = 0.0;
-  for (int y0 = 0, k = 0; y0 < ny; y0 += rows, ++k) {
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) col[x] = make_ulonglong2(0, 0);
+  for (int y0 = 0; y0 < ny; y0 += rows) {
     const int nr = min(rows, ny - y0);
     __syncthreads();
-    for (int q = threadIdx.x; q < nr * nx; q += blockDim.x) {
-      const int r = q / nx, x = q - r * nx;
-      tile[r * pitch + x] = plane[(size_t)y0 * nx + q];
+    // RC_BATCH loads in flight per thread before the conversions
+    const int nq = nr * nx;
+    const double* src = plane + (size_t)y0 * nx;
+    for (int q0 = threadIdx.x; q0 < nq; q0 += RC_BATCH * blockDim.x) {
+      double v[RC_BATCH];
+#pragma unroll
+      for (int u = 0; u < RC_BATCH; ++u) {
+        const int q = q0 + u * blockDim.x;
+        v[u] = q < nq ? src[q] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < RC_BATCH; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < nq) {
+          const int r = q / nx, x = q - r * nx;
+          unsigned long long lo, hi;
+          sq_fixed(v[u], lo, hi);
+          tile[r * pitch + x] = make_ulonglong2(lo, hi);
+        }
+      }
     }
     __syncthreads();
-    const int rw = k & 3;  // this chunk's row-sum warp
-    if (w == rw) {
-      for (int r = lane; r < nr; r += 32) {
-        double sr = 0.0;
-        for (int x = 0; x < nx; ++x) {
-          const double v = tile[r * pitch + x];
-          sr = fma(v, v, sr);
-        }
-        R[((size_t)i * nz + z) * ny + y0 + r] = sr;
+    // row sums: warp w adds quarter w of every row (lane = row); the four
+    // partial sums are exact, so their combination below is too
+    const int qx = (nx + 3) / 4, xa = w * qx, xb = min(nx, xa + qx);
+    if (lane < nr) {
+      unsigned long long slo = 0, shi = 0;
+      for (int x = xa; x < xb; ++x) {
+        const ulonglong2 f = tile[lane * pitch + x];
+        slo += f.x;
+        shi += f.y;
       }
-    } else {
-      const int cw = (w - rw + 3) & 3;  // 0, 1, 2 among the column warps
-      for (int x = cw * 32 + lane; x < nx; x += 96) {
-        double sc = col[x];
-        for (int r = 0; r < nr; ++r) {
-          const double v = tile[r * pitch + x];
-          sc = fma(v, v, sc);
-        }
-        col[x] = sc;
+      rpart[w * 32 + lane] = make_ulonglong2(slo, shi);
+    }
+    // column sums: thread per column, carried over the chunks
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      ulonglong2 c = col[x];
+      for (int r = 0; r < nr; ++r) {
+        const ulonglong2 f = tile[r * pitch + x];
+        c.x += f.x;
+        c.y += f.y;
       }
+      col[x] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+      ulonglong2 t = rpart[threadIdx.x];
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        t.x += rpart[u * 32 + threadIdx.x].x;
+        t.y += rpart[u * 32 + threadIdx.x].y;
+      }
+      R[((size_t)i * nz + z) * ny + y0 + threadIdx.x] = t;
     }
   }
   __syncthreads();
   for (int x = threadIdx.x; x < nx; x += blockDim.x) C[((size_t)i * nz + z) * nx + x] = col[x];
 }
 
-// Thread per (orbital, axis, coordinate): the three marginals of |phi|^2 dV.
+// 128-bit unsigned (hi, lo) += limb pair (a + b 2^48).
+__device__ __forceinline__ void add_limbs(unsigned long long& hi, unsigned long long& lo,
+                                          ulonglong2 v) {
+  const unsigned long long b_lo = v.y << 48, b_hi = v.y >> 16;
+  unsigned long long t = lo + v.x;
+  hi += (t < lo ? 1ULL : 0ULL);
+  const unsigned long long t2 = t + b_lo;
+  hi += (t2 < t ? 1ULL : 0ULL) + b_hi;
+  lo = t2;
+}
+
+// (hi 2^64 + lo) 2^e2 rounded to the nearest FP64 value (ties to even);
+// integer operations only.  0 for a zero input.
+__device__ __forceinline__ double scaled_u128(unsigned long long hi, unsigned long long lo, int e2) {
+  if (hi == 0 && lo == 0) return 0.0;
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  unsigned long long H, L;
+  if (lz >= 64) {
+    H = lo << (lz - 64);
+    L = 0;
+  } else if (lz > 0) {
+    H = (hi << lz) | (lo >> (64 - lz));
+    L = lo << lz;
+  } else {
+    H = hi;
+    L = lo;
+  }
+  unsigned long long mnt = H >> 11;
+  const unsigned rem = (unsigned)(H & 0x7FF);
+  if (rem > 0x400u || (rem == 0x400u && (L != 0 || (mnt & 1ULL)))) ++mnt;
+  int ex = 127 - lz + e2 + 1023;
+  if (mnt >> 53) {
+    mnt >>= 1;
+    ++ex;
+  }
+  if (ex <= 0) return 0.0;
+  return __longlong_as_double((long long)(((unsigned long long)ex << 52) | (mnt & 0xFFFFFFFFFFFFFULL)));
+}
+
+// Thread per (orbital, axis, coordinate): the three marginals of |phi|^2 dV,
+// m = fl(fl(2^-64 S) dV) with S the exact sum of the plane's F values.
 // marg layout: [n][3][Nmax].
-__global__ void k_marginals(const double* __restrict__ R, const double* __restrict__ C,
+__global__ void k_marginals(const ulonglong2* __restrict__ R, const ulonglong2* __restrict__ C,
                             int n, int nx, int ny, int nz, int Nmax, double dV,
                             double* __restrict__ marg) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int total = n * 3 * Nmax;
   if (t >= total) return;
   const int coord = t % Nmax, axis = (t / Nmax) % 3, i = t / (3 * Nmax);
-  double s = 0.0;
+  unsigned long long hi = 0, lo = 0;
   if (axis == 2) {
     if (coord >= nz) return;
-    const double* r = R + ((size_t)i * nz + coord) * ny;
-    for (int y = 0; y < ny; ++y) s = __dadd_rn(s, r[y]);
+    const ulonglong2* r = R + ((size_t)i * nz + coord) * ny;
+    for (int y = 0; y < ny; ++y) add_limbs(hi, lo, r[y]);
   } else if (axis == 1) {
     if (coord >= ny) return;
-    for (int z = 0; z < nz; ++z) s = __dadd_rn(s, R[((size_t)i * nz + z) * ny + coord]);
+    for (int z = 0; z < nz; ++z) add_limbs(hi, lo, R[((size_t)i * nz + z) * ny + coord]);
   } else {
     if (coord >= nx) return;
-    for (int z = 0; z < nz; ++z) s = __dadd_rn(s, C[((size_t)i * nz + z) * nx + coord]);
+    for (int z = 0; z < nz; ++z) add_limbs(hi, lo, C[((size_t)i * nz + z) * nx + coord]);
   }
-  marg[t] = __dmul_rn(s, dV);
+  marg[t] = __dmul_rn(scaled_u128(hi, lo, -64), dV);
 }
 
 // One CTA per (orbital, axis): shortest cyclic interval with outside mass
@@ -378,12 +485,15 @@ __global__ void k_lpt_order(const int* __restrict__ sz, const int* __restrict__ 
 cudaError_t launch_plan_boxes(sea_ctx* c) {
   const int n = c->n_orb, nx = c->N[0], ny = c->N[1], nz = c->N[2];
   const int Nmax = max(nx, max(ny, nz));
-  const size_t rc_smem = ((size_t)rc_rows(nx) * (nx + 1) + nx) * sizeof(double);
+  const size_t rc_smem = rc_smem_bytes(nx);
+  cudaError_t e = cudaFuncSetAttribute(k_row_col_sums, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)rc_smem);
+  if (e != cudaSuccess) return e;
   k_row_col_sums<<<dim3(nz, n), 128, rc_smem, c->stream>>>(
-      (const double*)c->phi.p, nx, ny, nz, (double*)c->rowsum.p, (double*)c->colsum.p);
+      (const double*)c->phi.p, nx, ny, nz, (ulonglong2*)c->rowsum.p, (ulonglong2*)c->colsum.p);
   const int tot = n * 3 * Nmax;
   k_marginals<<<(tot + 255) / 256, 256, 0, c->stream>>>(
-      (const double*)c->rowsum.p, (const double*)c->colsum.p, n, nx, ny, nz, Nmax, c->dV,
+      (const ulonglong2*)c->rowsum.p, (const ulonglong2*)c->colsum.p, n, nx, ny, nz, Nmax, c->dV,
       (double*)c->marg.p);
   k_box_fit<<<n * 3, 128, Nmax * sizeof(double), c->stream>>>(
       (const double*)c->marg.p, nx, ny, nz, Nmax, c->prm.eps / 3.0, (int*)c->box.p);
@@ -391,8 +501,6 @@ cudaError_t launch_plan_boxes(sea_ctx* c) {
   return cudaGetLastError();
 }
 
-// Candidates, proto-pair compaction, screening and kept compaction.  Leaves
-// the kept count in counts[1] and the proto count in counts[0] (device).
 // Candidates, proto-pair compaction, screening, kept compaction, pair
 // records, unknown offsets and the CG order, all with device-side counts:
 // counts[0] = proto pairs, counts[1] = pairs, *(long long*)(counts + 4) =
