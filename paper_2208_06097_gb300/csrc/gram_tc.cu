@@ -37,6 +37,8 @@
 // second W buffer).  Every wait on the MMA completion barrier is bounded:
 // on expiry the kernel sets SEA_FLAG_WAIT, waits once more (bounded) for
 // its MMAs, frees its tensor memory and ends.
+#include <cuda.h>
+
 #include "sea_internal.cuh"
 
 namespace sea {
@@ -278,7 +280,7 @@ struct Unit {
 
 
 __global__ void __launch_bounds__(GT_THREADS, 1)
-    k_gram_tc(const double* __restrict__ A, int m, TileGeom G, size_t ng, int n_tiles,
+    k_gram_tc_ldg(const double* __restrict__ A, int m, TileGeom G, size_t ng, int n_tiles,
               const int* __restrict__ tptr, const uint4* __restrict__ wdig,
               const int* __restrict__ wexp, double* __restrict__ partial, int* __restrict__ queue,
               unsigned* __restrict__ status) {
@@ -486,6 +488,298 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same contraction with A's rows brought in by the tensor memory
+// accelerator.  Per unit one 4D box (x 8, y 4, z 2, rows 64) per half of
+// the A block, i.e. two 32 KB loads into two raw buffers, each tracked by
+// its own mbarrier; while the warps turn raw buffer 0 into digits, buffer
+// 1 is still landing, and the next unit's buffer-0 load starts as soon as
+// its rows are converted.  Points outside the grid and rows beyond m read
+// the box's zero fill.  One W buffer (a W block is loaded after the MMAs
+// of the previous block completed).  Digits go to shared memory by 4-byte
+// stores, lane = two points of one row, with the K-adjacent core matrices
+// 2064 bytes apart (2048 + 16) so that the 32 lanes hit 32 banks.
+// ---------------------------------------------------------------------------
+constexpr uint32_t A2_LBO = (MBLK / 8) * 128 + 16;    // 2064
+constexpr uint32_t A2_PLANE = 8 * A2_LBO;             // 8 runs of 8 points
+constexpr uint32_t SMEM_A2 = DIG * A2_PLANE;          // 99,072
+constexpr uint32_t RAW_HALF = (MBLK / 2) * KH * 8;    // 32 KB: 64 rows x 64 points
+constexpr size_t GT2_SMEM = SMEM_A2 + SMEM_W + 2 * RAW_HALF + 256;
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap tmA, int m, TileGeom G, int n_tiles,
+              const int* __restrict__ tptr, const uint4* __restrict__ wdig,
+              const int* __restrict__ wexp, double* __restrict__ partial, int* __restrict__ queue,
+              unsigned* __restrict__ status) {
+  extern __shared__ unsigned char gt_raw[];
+  unsigned char* sA = gt_raw + ((128 - (smem_addr(gt_raw) & 127)) & 127);
+  unsigned char* sW = sA + SMEM_A2;
+  unsigned char* sR = sW + SMEM_W;  // two raw halves of RAW_HALF
+  __shared__ int Aexp[2][MBLK], Wexp[2][NBLK];  // [half][row]
+  __shared__ __align__(8) unsigned long long mbar, tbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_tile, s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar = smem_addr(&mbar);
+  const uint32_t tb[2] = {smem_addr(&tbar[0]), smem_addr(&tbar[1])};
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tb[0]));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tb[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t a_base = smem_addr(sA), w_base = smem_addr(sW), r_base = smem_addr(sR);
+  const int nmb = (m + MBLK - 1) / MBLK;
+  bool tma_pending[2] = {false, false};  // meaningful in thread 0
+
+  auto claim = [&](Unit& u) -> bool {
+    __syncthreads();
+    if (tid == 0) {
+      int t;
+      do {
+        t = atomicAdd(queue, 1);
+      } while (t < n_tiles && tptr[t + 1] == tptr[t]);
+      s_tile = t;
+    }
+    __syncthreads();
+    const int T = s_tile;
+    if (T >= n_tiles) return false;
+    u.T = T;
+    u.j0 = tptr[T];
+    u.nJ = tptr[T + 1] - u.j0;
+    u.jb = 0;
+    u.mb = 0;
+    u.h = 0;
+    u.wb = 0;
+    return true;
+  };
+  auto advance = [&](Unit& u, bool* new_block) -> bool {
+    *new_block = false;
+    if (u.h == 0) {
+      u.h = 1;
+      return true;
+    }
+    u.h = 0;
+    if (++u.mb < nmb) return true;
+    u.mb = 0;
+    *new_block = true;
+    u.jb += NBLK;
+    if (u.jb < u.nJ) return true;
+    return claim(u);
+  };
+  // raw half q (rows 64 q .. 64 q + 63 of the A block) of unit u (thread 0)
+  auto tma_issue = [&](const Unit& u, int q) {
+    const int txi = u.T % G.ntx, tyi = (u.T / G.ntx) % G.nty, tzi = u.T / (G.ntx * G.nty);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(tb[q], RAW_HALF);
+    tma_load_4d(r_base + q * RAW_HALF, &tmA, txi * TX, tyi * TY, tzi * TZ + 2 * u.h,
+                u.mb * MBLK + 64 * q, tb[q]);
+    tma_pending[q] = true;
+  };
+  auto load_w = [&](const Unit& u) {
+    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+    const uint32_t lbo = DIG * P * 16;
+    for (int p = tid; p < P * 2 * DIG * 8; p += GT_THREADS) {
+      const int run = p & 7, k = (p >> 3) % DIG, h = (p / (8 * DIG)) & 1, sl = p / (16 * DIG);
+      const bool ok = sl < nj;
+      const uint4* src = ok ? wdig + ((size_t)(u.j0 + u.jb + sl) * 2 + h) * DIG * 8 + k * 8 + run : wdig;
+      const int row = k * P + sl;
+      cp_async16(w_base + h * W_HALF + (row >> 3) * CORE_SBO + run * lbo + (row & 7) * 16, src, ok);
+    }
+    if (tid < 2 * NBLK) {
+      const int h = tid / NBLK, sl = tid % NBLK;
+      Wexp[h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
+    }
+  };
+  // rows 64 q .. 64 q + 63 of raw half q to digits: warp w, rows 4 w .. 4 w + 3
+  // of the half (lane = points 2 lane, 2 lane + 1: run lane / 4)
+  auto convert = [&](const Unit& u, int q) {
+    const double2* raw = reinterpret_cast<const double2*>(sR + q * RAW_HALF);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rh = 4 * warp + i, row = 64 * q + rh;
+      const double2 v = raw[rh * 32 + lane];
+      int em = max((int)((__double_as_longlong(v.x) >> 52) & 0x7FF),
+                   (int)((__double_as_longlong(v.y) >> 52) & 0x7FF));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+      float f0[DIG], f1[DIG];
+      digit_floats(fixed47(v.x, em), f0);
+      digit_floats(fixed47(v.y, em), f1);
+      unsigned char* dst = sA + (row >> 3) * CORE_SBO + (lane >> 2) * A2_LBO + (row & 7) * 16 +
+                           (lane & 3) * 4;
+#pragma unroll
+      for (int k = 0; k < DIG; ++k)
+        *reinterpret_cast<uint32_t*>(dst + k * A2_PLANE) = pack_bf16(f0[k], f1[k]);
+      if (lane == 0) Aexp[u.h][row] = em;
+    }
+  };
+  // bounded wait on raw half q (all threads); false on expiry
+  uint32_t tphase[2] = {0, 0};
+  auto wait_raw = [&](int q) -> bool {
+    const bool ok = mbar_wait(tb[q], tphase[q]);
+    tphase[q] ^= 1;
+    if (tid == 0) tma_pending[q] = false;
+    return ok;
+  };
+  auto epilogue = [&](const Unit& u) {
+    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+    const int quarter = warp & 3, g = warp >> 2;
+    const int a = u.mb * MBLK + 32 * quarter + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+    const int ea0 = Aexp[0][32 * quarter + lane] - 1022, ea1 = Aexp[1][32 * quarter + lane] - 1022;
+#pragma unroll 1
+    for (int c = g; c < nj; c += 4) {
+      uint32_t f[2 * DIG];
+#pragma unroll
+      for (int q = 0; q < 2 * DIG; ++q)
+        f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
+      tmem_wait_ld();
+      double sum = 0.0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        long long acc = 0;
+#pragma unroll
+        for (int d = 0; d < DIG; ++d)
+          acc += (long long)float_int(__uint_as_float(f[h * DIG + d])) << (8 * (DIG - 1 - d));
+        sum += scaled_i64(acc, (h ? ea1 : ea0) + (Wexp[h][c] - 1022) - 54);
+      }
+      if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = sum;
+    }
+  };
+  auto issue = [&](const Unit& u) {
+    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+    const uint32_t lbo = DIG * P * 16;
+    const uint64_t a0 = sdesc(a_base, A2_LBO, CORE_SBO);
+    const uint64_t w0 = sdesc(w_base + u.h * W_HALF, lbo, CORE_SBO);
+    const uint32_t dcol = tmem + (uint32_t)(u.h * TMEM_HALF);
+#pragma unroll
+    for (int q = 0; q < KH / 16; ++q)
+#pragma unroll
+      for (int k = 0; k < DIG; ++k)
+        mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A2_PLANE + q * 2 * A2_LBO) >> 4),
+                 w0 + ((q * 2 * lbo) >> 4), idesc_bf16((DIG - k) * P), (k > 0 || q > 0) ? 1u : 0u);
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+  };
+
+  Unit cur;
+  cur.wb = 0;
+  uint32_t phase = 0;
+  bool have_prev = false, mma_pending = false;
+  Unit prev = cur;
+  if (claim(cur)) {
+    load_w(cur);
+    if (tid == 0) {
+      tma_issue(cur, 0);
+      tma_issue(cur, 1);
+    }
+    bool need_w = false;
+    for (;;) {
+      if (have_prev) {
+        // prev's MMAs done: digits, accumulators and W buffer are free
+        const bool ok = mbar_wait(bar, phase);
+        if (!ok) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        phase ^= 1;
+        mma_pending = false;
+        tc_fence_after();
+        if (prev.h == 1) {
+          epilogue(prev);
+          __syncthreads();  // exponents and W read before they are replaced
+        }
+      }
+      if (need_w) load_w(cur);
+      // the two raw halves of cur, converted as they land; half 0's buffer
+      // is refilled for the next unit right after its conversion
+      if (!wait_raw(0)) s_fail = 1;
+      __syncthreads();
+      if (s_fail) break;
+      convert(cur, 0);
+      __syncthreads();  // raw half 0 consumed
+      Unit next = cur;
+      bool new_block = false;
+      const bool has_next = advance(next, &new_block);  // may claim (uniform, syncs)
+      if (tid == 0 && has_next) tma_issue(next, 0);
+      if (!wait_raw(1)) s_fail = 1;
+      __syncthreads();
+      if (s_fail) break;
+      convert(cur, 1);
+      cp_async_wait_all();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();  // digits, W and raw half 1 consumed
+      tc_fence_after();
+      if (tid == 0) {
+        if (has_next) tma_issue(next, 1);
+        issue(cur);
+      }
+      mma_pending = true;
+      prev = cur;
+      have_prev = true;
+      if (!has_next) break;
+      need_w = new_block;
+      cur = next;
+    }
+    // the last unit's MMAs (bounded wait) and epilogue
+    if (!s_fail && mma_pending) {
+      const bool ok = mbar_wait(bar, phase);
+      if (!ok) s_fail = 1;
+      __syncthreads();
+      if (!s_fail) {
+        mma_pending = false;
+        tc_fence_after();
+        if (prev.h == 1) epilogue(prev);
+      }
+    }
+    if (s_fail) {
+      if (mma_pending) mbar_wait(bar, phase);  // once more, bounded, before freeing
+      // loads still in flight land before the CTA's shared memory is released
+      if (tid == 0)
+        for (int q = 0; q < 2; ++q)
+          if (tma_pending[q]) mbar_wait(tb[q], tphase[q]);
+    }
+  }
+  cp_async_wait_all();
+  if (s_fail && tid == 0) atomicOr(status, SEA_FLAG_WAIT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
 }  // namespace
 
 
@@ -507,14 +801,54 @@ cudaError_t launch_w_digits(cudaStream_t st, const double* W, const TileGeom& G,
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the
+// runtime (no link-time dependence on the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// The 4D view (x, y, z, row) of A for the tensor-memory-accelerator path;
+// false where it does not apply (odd nx: rows not 16-byte strided; A not
+// 16-byte aligned; no driver entry point).
+static bool make_a_map(const double* A, int m, const TileGeom& G, CUtensorMap* map) {
+  if ((G.nx & 1) || (((uintptr_t)A) & 15)) return false;
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dim[4] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz, (cuuint64_t)m};
+  const cuuint64_t stride[3] = {(cuuint64_t)G.nx * 8, (cuuint64_t)G.nx * G.ny * 8,
+                                (cuuint64_t)G.nx * G.ny * G.nz * 8};
+  const cuuint32_t box[4] = {TX, TY, 2, MBLK / 2};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)A, dim, stride, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const TileGeom& G,
                            size_t ng, int n_tiles, const int* tptr, long long slots,
                            const void* wbuf, double* partial, int* queue, unsigned* status) {
   static bool attr_set[64] = {};
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[device]) {
-    const cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)GT_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc_ldg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GT_SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GT2_SMEM);
     if (e != cudaSuccess) return e;
     attr_set[device] = true;
   }
@@ -524,8 +858,14 @@ cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_gram_tc<<<std::min(nsm, std::max(n_tiles, 1)), GT_THREADS, GT_SMEM, st>>>(
-      A, m, G, ng, n_tiles, tptr, wdig, wexp, partial, queue, status);
+  const int grid = std::min(nsm, std::max(n_tiles, 1));
+  alignas(64) CUtensorMap map;
+  if (make_a_map(A, m, G, &map))
+    k_gram_tc<<<grid, GT_THREADS, GT2_SMEM, st>>>(map, m, G, n_tiles, tptr, wdig, wexp, partial,
+                                                  queue, status);
+  else
+    k_gram_tc_ldg<<<grid, GT_THREADS, GT_SMEM, st>>>(A, m, G, ng, n_tiles, tptr, wdig, wexp,
+                                                     partial, queue, status);
   return cudaGetLastError();
 }
 
