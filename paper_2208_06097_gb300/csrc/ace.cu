@@ -307,10 +307,11 @@ __global__ void __launch_bounds__(256)
     k_tile_expand_x(const double* __restrict__ W, TileGeom G, size_t ng,
                     const int* __restrict__ tptr, const int* __restrict__ tlist,
                     const int* __restrict__ tsub, const double* __restrict__ H, long long hj,
-                    long long hv, int m, double sign, double* __restrict__ out) {
+                    long long hv, int m, double sign, int skip_upto, double* __restrict__ out) {
   const int T = blockIdx.x;
   const int v0 = blockIdx.y * 32;
   const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
+  if (nJ <= skip_upto) return;  // done by the tensor-core expansion
   extern __shared__ float2 Hx[];  // [nJ][32]
   for (int idx = threadIdx.x; idx < nJ * 32; idx += blockDim.x) {
     const int jl = idx / 32, vl = idx % 32;
@@ -746,18 +747,29 @@ static void launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G, c
         A, m, W, G, c->ng, tptr, tlist, tsub, (double*)c->partial.p);
 }
 
-static void launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr, const int* tlist,
-                          const int* tsub, const double* H, long long hj, long long hv, int m,
-                          double sign, double* out) {
+static cudaError_t launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr,
+                                 const int* tlist, const int* tsub, const double* H, long long hj,
+                                 long long hv, int m, double sign, double* out) {
   if (c->prm.precision == 1) {
-    const size_t smem = (size_t)c->max_tile_list * 32 * sizeof(float2);
-    k_tile_expand_x<<<dim3(c->n_tiles, (m + 31) / 32), 256, smem, c->stream>>>(
-        (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, tsub, H, hj, hv, m, sign, out);
+    // tiles with at most expand_tc_max_list() W rows on the tensor cores,
+    // longer lists (if any) by the FP32 kernel
+    const cudaError_t e = launch_expand_tc(c->stream, c->device, c->wx.p, G, c->ng, c->n_tiles,
+                                           tptr, tlist, H, hj, hv, m, sign < 0.0,
+                                           out, (int*)c->counts.p + 24, (unsigned*)c->status.p);
+    if (e != cudaSuccess) return e;
+    if (c->max_tile_list > expand_tc_max_list()) {
+      const size_t smem = (size_t)c->max_tile_list * 32 * sizeof(float2);
+      k_tile_expand_x<<<dim3(c->n_tiles, (m + 31) / 32), 256, smem, c->stream>>>(
+          (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, tsub, H, hj, hv, m, sign,
+          expand_tc_max_list(), out);
+      c->launches += 1;
+    }
   } else {
     const size_t smem = (size_t)c->max_tile_list * EV * sizeof(double);
     k_tile_expand<<<dim3(c->n_tiles, (m + EV - 1) / EV), 256, smem, c->stream>>>(
         (const double*)c->vxx_dev.p, G, c->ng, tptr, tlist, tsub, H, hj, hv, m, sign, out);
   }
+  return cudaGetLastError();
 }
 
 // Scratch (doubles) of the L^-1 doubling: the largest level's pairs x s x s.
@@ -844,7 +856,11 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     err = launch_w_digits(c->stream, (const double*)c->vxx_dev.p, G, c->ng, nt, c->max_tile_list,
                           tptr, tlist, hinc, c->wdig.p);
     if (err != cudaSuccess) return err;
-    c->launches += 1;
+    if (!sea_ensure(c, c->wx, wx_digits_bytes(nt, hinc))) return cudaErrorMemoryAllocation;
+    err = launch_wx_digits(c->stream, (const double*)c->vxx_dev.p, G, c->ng, nt, tptr, tlist, tsub,
+                           c->wx.p);
+    if (err != cudaSuccess) return err;
+    c->launches += 2;
   }
   cudaEventRecord(c->ev[10], c->stream);
   launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
@@ -971,7 +987,9 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
   }
   // out[v] = -sum_j W_j H[j][v]
   cudaEventRecord(c->ev[14], c->stream);
-  launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Hbuf.p, nv, 1, nv, -1.0, out);
+  cudaError_t ex = launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Hbuf.p, nv, 1, nv,
+                                 -1.0, out);
+  if (ex != cudaSuccess) return ex;
   cudaEventRecord(c->ev[15], c->stream);
   c->launches += 5;
   return cudaGetLastError();
@@ -985,7 +1003,8 @@ cudaError_t launch_ace_vectors(sea_ctx* c, double* xi) {
   const int* tlist = (const int*)c->tlist_t.p;
   const int* tsub = tlist + max(c->tile_inc, 1);
   // Xi[k][r] = sum_j W[j][r] (L^-1)[k][j]:  H(j, k) = Linv[k * n + j]
-  launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Linv.p, 1, n, n, 1.0, xi);
+  cudaError_t ex = launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Linv.p, 1, n, n, 1.0, xi);
+  if (ex != cudaSuccess) return ex;
   c->launches += 1;
   return cudaGetLastError();
 }

@@ -780,6 +780,346 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// The mixed form's expansion y[v][r] = sign sum_j W[list(j)][r] H(j, v) on
+// the tensor cores, per tile (M = the tile's 128 points, N = vectors, K =
+// the tile's W list, at most XJ = 32 entries; longer lists go to the FP32
+// kernel).  Scales: W's digits are taken per (tile, list entry j) with the
+// exponent E_j of that W row on the tile; H(j, v) is scaled exactly by 2^E_j
+// and split per (tile, vector v) with one exponent E_v over the list, so
+//   y = 2^(E_v) sum_d 2^(-14-8d) D_d,  D_d = sum_j sum_{k+l=d} a_k(j) b_l(j),
+// E_j cancels and every D_d (at most 32 x 6 products of magnitude <= 2^14)
+// is an integer below 2^24, exact in the FP32 accumulator.  W's digits are
+// formed once per W into a per-tile image in the K-major layout (two K steps
+// of 16 list entries, six planes, 4 KB each); H's digits per tile, for 256
+// vectors at a time, into shared memory with the six planes of each chunk
+// of 32 vectors stacked along N, so one MMA of A plane k against planes
+// 0..5-k adds plane k's products to diagonals k..5 (TMEM columns 32 d).
+// Two accumulator buffers of 192 columns: the MMAs of chunk c + 1 run while
+// chunk c's epilogue reads its buffer back.
+// ---------------------------------------------------------------------------
+constexpr int XJ = 32, XKS = 16, XN = 32, XVB = 256;
+constexpr uint32_t XA_BLOCK = MBLK * XKS * 2;          // 4 KB: one plane, one K step
+constexpr uint32_t XA_LBO = (MBLK / 8) * 128;          // 2048
+constexpr uint32_t XA_STEP = DIG * XA_BLOCK;           // 24 KB
+constexpr uint32_t XA_TILE = 2 * XA_STEP;              // 48 KB
+constexpr uint32_t XB_LBO = (DIG * XN / 8) * 128;      // 3072
+constexpr uint32_t XB_CHUNK = 2 * XB_LBO;              // 6 KB: 192 rows x 16 K
+constexpr uint32_t XB_STEP = (XVB / XN) * XB_CHUNK;    // 48 KB
+constexpr uint32_t XT_COLS = DIG * XN;                 // 192
+constexpr size_t XE_SMEM = 2 * XA_TILE + 2 * XB_STEP + 256;
+
+// W's digit image: CTA per tile (thread = point p), for tiles whose list has
+// 1..XJ entries.  wx[T][(q 6 + k) 4096 + (p / 8) 128 + (jq / 8) 2048 +
+// (p % 8) 16 + (jq % 8) 2] = digit k of W[list(16 q + jq)] at point p (zero
+// outside the entry's sub-box and beyond the list), wxexp[slot] = E_j + 1022.
+__global__ void __launch_bounds__(MBLK)
+    k_wx_digits(const double* __restrict__ W, TileGeom G, size_t ng, int n_tiles,
+                const int* __restrict__ tptr, const int* __restrict__ tlist,
+                const int* __restrict__ tsub, uint4* __restrict__ wx, int* __restrict__ wxexp) {
+  const int T = blockIdx.x;
+  const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
+  if (nJ == 0 || nJ > XJ) return;  // uniform
+  __shared__ int emx[XJ];
+  const int p = threadIdx.x;
+  if (p < XJ) emx[p] = 0;
+  const long long g = tile_point(G, T, p);
+  const int pz = p / (TX * TY), py = (p / TX) % TY, px = p % TX;
+  auto wval = [&](int jl) -> double {
+    if (jl >= nJ || g < 0) return 0.0;
+    const int sb = tsub[j0 + jl];
+    const bool in = px >= (sb & 15) && px < ((sb >> 4) & 15) && py >= ((sb >> 8) & 15) &&
+                    py < ((sb >> 12) & 15) && pz >= ((sb >> 16) & 15) && pz < ((sb >> 20) & 15);
+    return in ? W[(size_t)tlist[j0 + jl] * ng + g] : 0.0;
+  };
+  __syncthreads();
+  for (int jl = 0; jl < nJ; ++jl)
+    atomicMax(&emx[jl], (int)((__double_as_longlong(wval(jl)) >> 52) & 0x7FF));
+  __syncthreads();
+  if (p < nJ) wxexp[j0 + p] = emx[p];
+  const int nq = (nJ + XKS - 1) / XKS;
+  unsigned char* base = reinterpret_cast<unsigned char*>(wx) + (size_t)T * XA_TILE;
+  for (int grp = 0; grp < 2 * nq; ++grp) {  // 8 list entries at a time
+    uint32_t pk[DIG][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      const int jl = 8 * grp + e;
+      float f0[DIG], f1[DIG];
+      digit_floats(jl < nJ ? fixed47(wval(jl), emx[jl]) : 0, f0);
+      digit_floats(jl + 1 < nJ ? fixed47(wval(jl + 1), emx[jl + 1]) : 0, f1);
+#pragma unroll
+      for (int k = 0; k < DIG; ++k) pk[k][e / 2] = pack_bf16(f0[k], f1[k]);
+    }
+    const int q = grp >> 1, jj = grp & 1;
+#pragma unroll
+    for (int k = 0; k < DIG; ++k)
+      *reinterpret_cast<uint4*>(base + (q * DIG + k) * XA_BLOCK + (p >> 3) * 128 + jj * XA_LBO +
+                                (p & 7) * 16) = make_uint4(pk[k][0], pk[k][1], pk[k][2], pk[k][3]);
+  }
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(addr));
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Integer value of an integer-valued FP32 number below 2^22 in magnitude:
+// adding 1.5 2^23 puts it in the low mantissa bits.
+__device__ __forceinline__ int small_float_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
+}
+
+constexpr int XE_WARPS = 16;                       // digit and epilogue warps
+constexpr int XE_THREADS = 32 * (XE_WARPS + 1);    // and one MMA-issuing warp
+
+// Persistent CTAs (one per SM) over the tiles whose list has at most XJ
+// entries.  Warps 0..15 form H's digits and read the accumulators back
+// (warp w: tensor-memory lanes 32 (w % 4), vectors 8 (w / 4) .. + 7 of a
+// chunk); warp 16 issues the MMAs.  Per accumulator buffer two mbarriers:
+// MMAs done (tcgen05.commit) and buffer read back (one arrival per
+// epilogue warp, right after its tensor-memory loads), so chunk c + 2's
+// MMAs start while chunk c's outputs are still being converted and
+// stored.  H(j, v) = H[j hj + v hv]; out[v ng + r].
+__global__ void __launch_bounds__(XE_THREADS, 1)
+    k_expand_tc(const uint4* __restrict__ wx, const int* __restrict__ wxexp, TileGeom G, size_t ng,
+                int n_tiles, const int* __restrict__ tptr, const int* __restrict__ tlist,
+                const double* __restrict__ H, long long hj, long long hv, int m, int negate,
+                double* __restrict__ out, int* __restrict__ queue, unsigned* __restrict__ status) {
+  extern __shared__ unsigned char xe_raw[];
+  unsigned char* sA = xe_raw + ((128 - (smem_addr(xe_raw) & 127)) & 127);  // two tile images
+  unsigned char* sB = sA + 2 * XA_TILE;                                     // two K steps
+  __shared__ int lj[XJ], shj[XJ], emv2[2][XVB], evx[XVB];
+  __shared__ __align__(8) unsigned long long abar[2], mdone[2], bfree[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_next, s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool issuer = warp == XE_WARPS;
+  const uint32_t ab[2] = {smem_addr(&abar[0]), smem_addr(&abar[1])};
+  const uint32_t md[2] = {smem_addr(&mdone[0]), smem_addr(&mdone[1])};
+  const uint32_t bf[2] = {smem_addr(&bfree[0]), smem_addr(&bfree[1])};
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ab[q]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(md[q]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bf[q]), "r"(XE_WARPS));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
+  uint32_t aphase[2] = {0, 0};
+  bool a_pending[2] = {false, false};  // thread 0's bookkeeping
+  long long cg = 0;                    // chunks with MMAs so far (uniform)
+  auto list_len = [&](int T) { return tptr[T + 1] - tptr[T]; };
+  auto claim = [&]() -> int {
+    __syncthreads();
+    if (tid == 0) {
+      int t;
+      do {
+        t = atomicAdd(queue, 1);
+      } while (t < n_tiles && list_len(t) > XJ);
+      s_next = t;
+    }
+    __syncthreads();
+    return s_next;
+  };
+  auto prefetch = [&](int T, int b) {  // thread 0: W digit image of tile T into buffer b
+    const int nJ = list_len(T);
+    if (nJ == 0) return;
+    const uint32_t bytes = (uint32_t)((nJ + XKS - 1) / XKS) * XA_STEP;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(ab[b], bytes);
+    bulk_load(a_base + b * XA_TILE, reinterpret_cast<const unsigned char*>(wx) + (size_t)T * XA_TILE,
+              bytes, ab[b]);
+    a_pending[b] = true;
+  };
+  int T = claim(), buf = 0;
+  if (tid == 0 && T < n_tiles) prefetch(T, 0);
+  while (T < n_tiles) {
+    const int Tn = claim();
+    if (s_fail) break;
+    if (tid == 0 && Tn < n_tiles) prefetch(Tn, buf ^ 1);
+    const int j0 = tptr[T], nJ = list_len(T), nq = (nJ + XKS - 1) / XKS;
+    if (tid < XJ && tid < nJ) {
+      lj[tid] = tlist[j0 + tid];
+      shj[tid] = wxexp[j0 + tid] - 1022;
+    }
+    const int p = 32 * (warp & 3) + lane;  // epilogue point (tensor-memory lane)
+    const long long g = issuer ? -1 : tile_point(G, T, p);
+    bool a_ready = nJ == 0;
+    for (int vb = 0; vb < m; vb += XVB) {
+      __syncthreads();  // lj/shj visible; the previous block's MMAs and read-backs are done
+      if (s_fail) break;
+      const int vl = tid & (XVB - 1), q = tid >> 8;  // thread pair per vector: K step q
+      const int v = vb + vl;
+      if (nJ > 0) {
+        // E_v over the list (two partial maxima), then the digits of K step q
+        double hreg[XKS];
+        int em = 0;
+        if (!issuer) {
+#pragma unroll
+          for (int i = 0; i < XKS; ++i) {
+            const int jl = q * XKS + i;
+            hreg[i] = (v < m && jl < nJ) ? H[(long long)lj[jl] * hj + (long long)v * hv] : 0.0;
+          }
+#pragma unroll
+          for (int i = 0; i < XKS; ++i) {
+            const int e = (int)((__double_as_longlong(hreg[i]) >> 52) & 0x7FF);
+            if (e) em = max(em, e + shj[q * XKS + i]);
+          }
+          emv2[q][vl] = em;
+        }
+        __syncthreads();
+        if (!issuer) {
+          em = max(emv2[0][vl], emv2[1][vl]);
+          if (q == 0) evx[vl] = em;  // E_v for the epilogue (read after the next barrier)
+          if (q < nq) {
+            const int c = vl / XN, vv = vl % XN;
+            unsigned char* dstc = sB + q * XB_STEP + c * XB_CHUNK;
+#pragma unroll
+            for (int jp = 0; jp < XKS; jp += 2) {
+              const int jl = q * XKS + jp;
+              float f0[DIG], f1[DIG];
+              digit_floats(jl < nJ ? fixed47(hreg[jp], em - shj[jl]) : 0, f0);
+              digit_floats(jl + 1 < nJ ? fixed47(hreg[jp + 1], em - shj[jl + 1]) : 0, f1);
+#pragma unroll
+              for (int l = 0; l < DIG; ++l) {
+                const int row = l * XN + vv;
+                *reinterpret_cast<uint32_t*>(dstc + (row >> 3) * 128 + (jp >> 3) * XB_LBO +
+                                             (row & 7) * 16 + (jp & 7) * 2) = pack_bf16(f0[l], f1[l]);
+              }
+            }
+          }
+        }
+      }
+      if (!a_ready) {
+        if (!mbar_wait(ab[buf], aphase[buf])) s_fail = 1;
+        aphase[buf] ^= 1;
+        if (tid == 0) a_pending[buf] = false;
+        a_ready = true;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (s_fail) break;
+      const int nchunk = (min(XVB, m - vb) + XN - 1) / XN;
+      if (issuer) {
+        if (lane == 0 && nJ > 0) {
+          for (int c = 0; c < nchunk; ++c) {
+            const long long seq = cg + c;
+            const int tb = (int)(seq & 1);
+            const long long use = seq >> 1;
+            if (use >= 1 && !mbar_wait(bf[tb], (uint32_t)((use - 1) & 1))) {
+              s_fail = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dcol = tmem + (uint32_t)(tb * XT_COLS);
+            for (int qq = 0; qq < nq; ++qq)
+#pragma unroll
+              for (int k = 0; k < DIG; ++k) {
+                const uint64_t a =
+                    sdesc(a_base + buf * XA_TILE + qq * XA_STEP + k * XA_BLOCK, XA_LBO, 128);
+                const uint64_t b = sdesc(b_base + qq * XB_STEP + c * XB_CHUNK, XB_LBO, 128);
+                mma_bf16(dcol + (uint32_t)(k * XN), a, b, idesc_bf16((DIG - k) * XN),
+                         (k > 0 || qq > 0) ? 1u : 0u);
+              }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    md[tb])
+                : "memory");
+          }
+        }
+        __syncwarp();
+      } else {
+        const int vv0 = 8 * (warp >> 2);
+        for (int c = 0; c < nchunk; ++c) {
+          double vals[8];
+          if (nJ > 0) {
+            const long long seq = cg + c;
+            const int tb = (int)(seq & 1);
+            if (!mbar_wait(md[tb], (uint32_t)((seq >> 1) & 1))) {
+              s_fail = 1;
+              break;
+            }
+            tc_fence_after();
+            uint32_t f[DIG][8];
+            const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                       (uint32_t)(tb * XT_COLS + vv0);
+#pragma unroll
+            for (int d = 0; d < DIG; ++d) tmem_ld8(lane_addr + (uint32_t)(d * XN), f[d]);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bf[tb]) : "memory");
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              // sum_d D_d 256^(5 - d), |D_d| < 2^22, in three 32-bit pairs
+              const int t01 = small_float_int(f[0][u]) * 256 + small_float_int(f[1][u]);
+              const int t23 = small_float_int(f[2][u]) * 256 + small_float_int(f[3][u]);
+              const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
+              const long long acc =
+                  ((long long)t01 << 32) + ((long long)t23 << 16) + (long long)t45;
+              vals[u] = scaled_i64(negate ? -acc : acc, evx[c * XN + vv0 + u] - 1022 - 54);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) vals[u] = 0.0;
+          }
+          if (g >= 0) {
+            double* o = out + (size_t)(vb + c * XN + vv0) * ng + g;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (vb + c * XN + vv0 + u < m) o[(size_t)u * ng] = vals[u];
+          }
+        }
+      }
+      if (nJ > 0) cg += nchunk;
+    }
+    T = Tn;
+    buf ^= 1;
+  }
+  __syncthreads();
+  if (s_fail && tid == 0) {
+    // bounded waits for work still in flight before the memory is released
+    for (int b = 0; b < 2; ++b) {
+      mbar_wait(md[b], (uint32_t)(((cg + b) >> 1) & 1));
+      if (a_pending[b]) mbar_wait(ab[b], aphase[b]);
+    }
+    atomicOr(status, SEA_FLAG_WAIT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
 }  // namespace
 
 
@@ -838,6 +1178,46 @@ static bool make_a_map(const double* A, int m, const TileGeom& G, CUtensorMap* m
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+size_t wx_digits_bytes(int n_tiles, long long slots) {
+  return (size_t)std::max(n_tiles, 1) * XA_TILE + (size_t)std::max(slots, 1LL) * sizeof(int);
+}
+
+cudaError_t launch_wx_digits(cudaStream_t st, const double* W, const TileGeom& G, size_t ng,
+                             int n_tiles, const int* tptr, const int* tlist, const int* tsub,
+                             void* wxbuf) {
+  if (n_tiles <= 0) return cudaSuccess;
+  uint4* wx = (uint4*)wxbuf;
+  int* wxexp = (int*)((unsigned char*)wxbuf + (size_t)n_tiles * XA_TILE);
+  k_wx_digits<<<n_tiles, MBLK, 0, st>>>(W, G, ng, n_tiles, tptr, tlist, tsub, wx, wxexp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_tc(cudaStream_t st, int device, const void* wxbuf, const TileGeom& G,
+                             size_t ng, int n_tiles, const int* tptr, const int* tlist,
+                             const double* H, long long hj, long long hv, int m, bool negate,
+                             double* out, int* queue, unsigned* status) {
+  static bool attr_set[64] = {};
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  if (!attr_set[device]) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_expand_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XE_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[device] = true;
+  }
+  if (n_tiles <= 0 || m <= 0) return cudaSuccess;
+  const uint4* wx = (const uint4*)wxbuf;
+  const int* wxexp = (const int*)((const unsigned char*)wxbuf + (size_t)n_tiles * XA_TILE);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_expand_tc<<<std::min(nsm, n_tiles), XE_THREADS, XE_SMEM, st>>>(
+      wx, wxexp, G, ng, n_tiles, tptr, tlist, H, hj, hv, m, negate ? 1 : 0, out, queue, status);
+  return cudaGetLastError();
+}
+
+int expand_tc_max_list() { return XJ; }
 
 cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const TileGeom& G,
                            size_t ng, int n_tiles, const int* tptr, long long slots,
