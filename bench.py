@@ -52,13 +52,6 @@ CG_FLOPS_PER_UNKNOWN_ITER = 65
 # FP64 peak from the part's unit counts and clock: 152 SMs x 2 FP64 FMA/clk x
 # 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 figure).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP32 issue peak: 152 SMs x 128 FP32 lanes x 2.07 GHz, one operation per
-# lane and clock (an FMA counts as one operation here).
-FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-# FP32 operations per FP64-accurate product in the mixed-form contractions
-# (split operands, exact hi*hi by an FMA residual, two cross terms, two-sum
-# into a compensated accumulator): 2 multiplies, 2 FMAs, 9 adds.
-EFT_OPS_PER_PRODUCT = 13
 
 
 def _dist():
@@ -126,9 +119,9 @@ def job_value(steps, ws, t_ms_max):
 # ncu capture of the benchmark workload with the current kernels; see
 # profiles/dram_traffic_h2o64_96.md).  None: not captured.
 DRAM_BYTES_PER_LAUNCH = {
-    "k_cg_mixed": 27.0e6,
-    "k_gram_tc": 2.024e9,
-    "k_tile_expand_x": 2.260e9,
+    "k_cg_mixed": 26.9e6,
+    "k_gram_tc": 2.025e9,
+    "k_expand_tc": 1.986e9,
 }
 
 
@@ -313,11 +306,13 @@ def run_ours(args, ws, rank, local):
                       8.0 * slots * n)
         cand.append(("k_gram_tc (tensor-core M = Phi^T W and W^T psi, exact BF16 digits)",
                      gram_ms, 2, gram_bytes, hbm, "hbm", note_gt))
-        note = ("FP32 issue from unit counts: 152 SMs x 128 lanes x 2.07 GHz = 40.3 T op/s; "
-                "work = rows x nonzeros of W products x 13 FP32 operations per FP64-accurate "
-                "product (error-free transformation)")
-        cand.append(("k_tile_expand_x (mixed W H, FP32 error-free products)", sm["expand_apply"],
-                     1, EFT_OPS_PER_PRODUCT * N_TRIAL * nnz_w, FP32_PEAK_TOPS, "alu", note))
+        note_x = ("HBM of measured (copy); algorithmic bytes: the FP64 output (8 B per grid "
+                  "point and vector) and W's per-tile BF16 digit image (24 KB per tile with "
+                  "support and K step of 16 W rows)")
+        ng = float(np.prod(s.grid))
+        expand_bytes = 8.0 * N_TRIAL * ng + 24576.0 * tiles_w
+        cand.append(("k_expand_tc (tensor-core W H, exact BF16 digits)", sm["expand_apply"], 1,
+                     expand_bytes, hbm, "hbm", note_x))
     def _rate(c):  # work per launch / time: flop -> TFLOP/s, bytes -> GB/s
         return c[3] / (c[1] / 1e3) / (1e9 if c[5] == "hbm" else 1e12) if c[1] > 0 else 0.0
 

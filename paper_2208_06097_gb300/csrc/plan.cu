@@ -54,7 +54,7 @@ __device__ __forceinline__ void sq_fixed(double v, unsigned long long& lo, unsig
 // One CTA of four warps per (z-plane, orbital): row sums and column sums of
 // F(phi) over the plane, as 48-bit limb sums (exact: a row or column has at
 // most 1024 points).  The plane is staged through shared memory as F values
-// in chunks of whole rows (coalesced loads, RC_BATCH in flight per thread;
+// in chunks of whole rows (coalesced loads, one chunk ahead in registers;
 // row pitch nx + 1 so that lanes reading different rows hit distinct
 // banks).  Warp w sums quarter w of every row of the chunk (lane per row),
 // the quarters are then added; thread per column carries the column sums
@@ -62,7 +62,7 @@ __device__ __forceinline__ void sq_fixed(double v, unsigned long long& lo, unsig
 // free.
 #define RC_ROWS 32
 #define RC_SMEM_ELEMS 3200
-#define RC_BATCH 8
+#define RC_PER_THREAD (RC_SMEM_ELEMS / 128)  // tile elements per thread (128 threads)
 __host__ __device__ __forceinline__ int rc_rows(int nx) {
   return min(RC_ROWS, max(1, (RC_SMEM_ELEMS - nx) / (nx + 1)));
 }
@@ -83,31 +83,35 @@ __global__ void __launch_bounds__(128)
   const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int x = threadIdx.x; x < nx; x += blockDim.x) col[x] = make_ulonglong2(0, 0);
+  // a chunk's values are loaded into registers one chunk ahead, so the loads
+  // of chunk k + 1 are in flight while chunk k is summed
+  double v[RC_PER_THREAD];
+  auto load_chunk = [&](int y0) {
+    const int nq = min(rows, ny - y0) * nx;
+    const double* src = plane + (size_t)y0 * nx;
+#pragma unroll
+    for (int u = 0; u < RC_PER_THREAD; ++u) {
+      const int q = threadIdx.x + u * 128;
+      v[u] = q < nq ? src[q] : 0.0;
+    }
+  };
+  load_chunk(0);
   for (int y0 = 0; y0 < ny; y0 += rows) {
     const int nr = min(rows, ny - y0);
-    __syncthreads();
-    // RC_BATCH loads in flight per thread before the conversions
+    __syncthreads();  // the previous chunk's tile is no longer read
     const int nq = nr * nx;
-    const double* src = plane + (size_t)y0 * nx;
-    for (int q0 = threadIdx.x; q0 < nq; q0 += RC_BATCH * blockDim.x) {
-      double v[RC_BATCH];
 #pragma unroll
-      for (int u = 0; u < RC_BATCH; ++u) {
-        const int q = q0 + u * blockDim.x;
-        v[u] = q < nq ? src[q] : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < RC_BATCH; ++u) {
-        const int q = q0 + u * blockDim.x;
-        if (q < nq) {
-          const int r = q / nx, x = q - r * nx;
-          unsigned long long lo, hi;
-          sq_fixed(v[u], lo, hi);
-          tile[r * pitch + x] = make_ulonglong2(lo, hi);
-        }
+    for (int u = 0; u < RC_PER_THREAD; ++u) {
+      const int q = threadIdx.x + u * 128;
+      if (q < nq) {
+        const int r = q / nx, x = q - r * nx;
+        unsigned long long lo, hi;
+        sq_fixed(v[u], lo, hi);
+        tile[r * pitch + x] = make_ulonglong2(lo, hi);
       }
     }
     __syncthreads();
+    if (y0 + rows < ny) load_chunk(y0 + rows);
     // row sums: warp w adds quarter w of every row (lane = row); the four
     // partial sums are exact, so their combination below is too
     const int qx = (nx + 3) / 4, xa = w * qx, xb = min(nx, xa + qx);
