@@ -283,24 +283,6 @@ struct CompF {
   }
 };
 
-// v = hi + lo with integer operations only (no FP64 instruction): hi keeps
-// the sign, the exponent and the top 23 mantissa bits (truncation), lo the
-// remaining 29 bits, rounded to an FP32 value of the same sign.  |v| below
-// the FP32 normal range (2^-126) is flushed to (0, 0).  Relative error of
-// hi + lo: <= 2^-47.
-__device__ __forceinline__ float2 split64(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned sign = (unsigned)(b >> 63) << 31;
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e - 1023 + 127 <= 0) return make_float2(0.f, 0.f);
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
-  const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
-  // lo = (m mod 2^29) 2^(e - 1075) = ((m mod 2^29) 2^-64) 2^(e - 1011); e > 896 keeps
-  // the second factor a normal FP32 power of two
-  const float l = ((float)(unsigned)(m & 0x1FFFFFFFULL) * 5.421010862427522e-20f) *
-                  __uint_as_float((unsigned)(e - 884) << 23);
-  return make_float2(hi, __uint_as_float(__float_as_uint(l) | sign));
-}
 
 // Mixed form of k_tile_expand (same splitting and compensated sums).
 __global__ void __launch_bounds__(256)

@@ -25,6 +25,8 @@ struct StencilW {
 
 // Pair density and moments, one CTA per pair: b = 4 pi rho on the box,
 // Qs = rescaled multipole moments of rho about the box centre (Eq. mepole).
+// DFM: the moments in double-float arithmetic (mixed form).
+template <bool DFM>
 __global__ void __launch_bounds__(256, 1)
     k_pair_moments(const double* __restrict__ phi, int nx, int ny, int nz,
                    const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
@@ -40,26 +42,56 @@ __global__ void __launch_bounds__(256, 1)
   double* b = bbuf + voff[p];
   const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (P.ext[2] - 1);
   const double fourpi = 4.0 * 3.14159265358979323846;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 
   __shared__ double red[8][SEA_NQ];
-  double acc[SEA_NQ];
+  if (DFM) {
+    // positions as exact half-integers times h in double-float
+    const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
+    DF acc[SEA_NQ];
 #pragma unroll
-  for (int q = 0; q < SEA_NQ; ++q) acc[q] = 0.0;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
-    const size_t g = ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx +
-                     wrapi(P.lo[0] + x, nx);
-    const double rho = fi[g] * fj[g];
-    b[t] = fourpi * rho;
-    harm_accumulate(rho, (x - cx) * hx, (y - cy) * hy, (z - cz) * hz, acc);
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < SEA_NQ; ++q) acc[q] = DF{0.f, 0.f};
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+      const size_t g = ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx +
+                       wrapi(P.lo[0] + x, nx);
+      const double a = fi[g], c = fj[g];
+      b[t] = fourpi * (a * c);
+      const float2 as = split64(a), cs = split64(c);
+      harm_accumulate_df(df_mul(DF{as.x, as.y}, DF{cs.x, cs.y}),
+                         df_mul_f((float)(x - cx), Hx), df_mul_f((float)(y - cy), Hy),
+                         df_mul_f((float)(z - cz), Hz), acc);
+    }
+    // warp sums in double-float, then the warps' sums in FP64 (fixed order)
 #pragma unroll
-  for (int q = 0; q < SEA_NQ; ++q) {
-    double v = acc[q];
+    for (int q = 0; q < SEA_NQ; ++q) {
+      DF v = acc[q];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[w][q] = v;
+      for (int o = 16; o > 0; o >>= 1) {
+        const DF u = DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, u);
+      }
+      if (lane == 0) red[w][q] = df_to_double(v);
+    }
+  } else {
+    double acc[SEA_NQ];
+#pragma unroll
+    for (int q = 0; q < SEA_NQ; ++q) acc[q] = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
+      const size_t g = ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx +
+                       wrapi(P.lo[0] + x, nx);
+      const double rho = fi[g] * fj[g];
+      b[t] = fourpi * rho;
+      harm_accumulate(rho, (x - cx) * hx, (y - cy) * hy, (z - cz) * hz, acc);
+    }
+#pragma unroll
+    for (int q = 0; q < SEA_NQ; ++q) {
+      double v = acc[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[w][q] = v;
+    }
   }
   __syncthreads();
   if (threadIdx.x < SEA_NQ) {
@@ -824,7 +856,8 @@ static StencilW make_weights(const sea_ctx* c) {
 
 cudaError_t launch_pair_setup(sea_ctx* c) {
   if (c->P == 0) return cudaSuccess;
-  k_pair_moments<<<c->P, 256, 0, c->stream>>>(
+  auto moments = c->prm.precision == 1 ? k_pair_moments<true> : k_pair_moments<false>;
+  moments<<<c->P, 256, 0, c->stream>>>(
       (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const PairInfo*)c->pinfo.p,
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
       (double*)c->bbuf.p, (double*)c->Q.p);

@@ -203,6 +203,25 @@ __device__ __forceinline__ DF df_from_double(double x) {
 }
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
+// v = hi + lo with integer operations only (no FP64 instruction): hi keeps
+// the sign, the exponent and the top 23 mantissa bits (truncation), lo the
+// remaining 29 bits, rounded to an FP32 value of the same sign.  |v| below
+// the FP32 normal range (2^-126) is flushed to (0, 0).  Relative error of
+// hi + lo: <= 2^-47.
+__device__ __forceinline__ float2 split64(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e - 1023 + 127 <= 0) return make_float2(0.f, 0.f);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFULL;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 1023 + 127) << 23) | (unsigned)(m >> 29));
+  // lo = (m mod 2^29) 2^(e - 1075) = ((m mod 2^29) 2^-64) 2^(e - 1011); e > 896 keeps
+  // the second factor a normal FP32 power of two
+  const float l = ((float)(unsigned)(m & 0x1FFFFFFFULL) * 5.421010862427522e-20f) *
+                  __uint_as_float((unsigned)(e - 884) << 23);
+  return make_float2(hi, __uint_as_float(__float_as_uint(l) | sign));
+}
+
 // me_potential in double-float: the same recurrences and summation order,
 // Q as double-float coefficients.
 __device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF y, DF z) {
@@ -242,6 +261,45 @@ __device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF
     }
   }
   return df_mul(v, df_sqrt(ir2));
+}
+
+// harm_accumulate in double-float: acc[q] += w D_q(x, y, z), the same
+// recurrences in the same order.
+__device__ __forceinline__ void harm_accumulate_df(DF w, DF x, DF y, DF z, DF* acc) {
+  const DF r2 = df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z));
+  DF Dm[2 * SEA_LMAX + 1], Dc[2 * SEA_LMAX + 1], Dn[2 * SEA_LMAX + 1];  // l-1, l, l+1
+#pragma unroll
+  for (int k = 0; k < 2 * SEA_LMAX + 1; ++k) Dm[k] = Dc[k] = Dn[k] = DF{0.f, 0.f};
+  Dm[SEA_LMAX] = DF{1.f, 0.f};
+  Dc[SEA_LMAX + 1] = x;
+  Dc[SEA_LMAX - 1] = y;
+  Dc[SEA_LMAX] = z;
+  acc[0] = df_add(acc[0], w);
+  acc[lmi(1, -1)] = df_add(acc[lmi(1, -1)], df_mul(w, y));
+  acc[lmi(1, 0)] = df_add(acc[lmi(1, 0)], df_mul(w, z));
+  acc[lmi(1, 1)] = df_add(acc[lmi(1, 1)], df_mul(w, x));
+#pragma unroll
+  for (int l = 1; l < SEA_LMAX; ++l) {
+    Dn[SEA_LMAX + l + 1] = df_add(df_mul(x, Dc[SEA_LMAX + l]), df_neg(df_mul(y, Dc[SEA_LMAX - l])));
+    Dn[SEA_LMAX - l - 1] = df_add(df_mul(y, Dc[SEA_LMAX + l]), df_mul(x, Dc[SEA_LMAX - l]));
+#pragma unroll
+    for (int m = -l; m <= l; ++m) {
+      if (m >= -(l - 1) && m <= l - 1) {
+        const DF g = df_mul(DF{c_harm.gam_hi[l][m + SEA_LMAX], c_harm.gam_lo[l][m + SEA_LMAX]}, r2);
+        Dn[SEA_LMAX + m] = df_add(df_mul(z, Dc[SEA_LMAX + m]), df_neg(df_mul(g, Dm[SEA_LMAX + m])));
+      } else {
+        Dn[SEA_LMAX + m] = df_mul(z, Dc[SEA_LMAX + m]);
+      }
+    }
+#pragma unroll
+    for (int m = -(l + 1); m <= l + 1; ++m)
+      acc[lmi(l + 1, m)] = df_add(acc[lmi(l + 1, m)], df_mul(w, Dn[SEA_LMAX + m]));
+#pragma unroll
+    for (int k = 0; k < 2 * SEA_LMAX + 1; ++k) {
+      Dm[k] = Dc[k];
+      Dc[k] = Dn[k];
+    }
+  }
 }
 
 // Sum over the block of one double; every thread gets the same total, added
