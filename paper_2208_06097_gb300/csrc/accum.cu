@@ -193,22 +193,32 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   const double* fp = phi + (size_t)e.partner * ng;
   double* out = cbuf + coff[blockIdx.y];
   const double cx = 0.5 * (P.ext[0] - 1), cy = 0.5 * (P.ext[1] - 1), cz = 0.5 * (P.ext[2] - 1);
+  const float cxf = 0.5f * (float)(P.ext[0] - 1), cyf = 0.5f * (float)(P.ext[1] - 1),
+              czf = 0.5f * (float)(P.ext[2] - 1);
   const int t1 = min(nw, t0 + SEA_CHUNK);
   for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
     const int tx = t % e.wl[0], ty = (t / e.wl[0]) % e.wl[1], tz = t / (e.wl[0] * e.wl[1]);
     const int ux = e.ws[0] + tx, uy = e.ws[1] + ty, uz = e.ws[2] + tz;
     const int lx = ux - P.lo[0], ly = uy - P.lo[1], lz = uz - P.lo[2];
-    double val;
-    if (lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2])
-      val = v[(lz * P.ext[1] + ly) * P.ext[0] + lx];
-    else if (DFM)  // lx - cx etc. are half-integers, exact in FP32
-      val = df_to_double(me_potential_df(Qd, df_mul_f((float)(lx - cx), Hx),
-                                         df_mul_f((float)(ly - cy), Hy),
-                                         df_mul_f((float)(lz - cz), Hz)));
-    else
-      val = me_potential(Qs, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
+    const bool inside =
+        lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2];
     const size_t g = ((size_t)wrapi(uz, nz) * ny + wrapi(uy, ny)) * nx + wrapi(ux, nx);
-    out[t] = __dmul_rn(val, fp[g]);
+    if (DFM) {  // c = v phi in double-float, no FP64 instruction
+      DF val;
+      if (inside) {
+        const float2 s = split64(v[(lz * P.ext[1] + ly) * P.ext[0] + lx]);
+        val = DF{s.x, s.y};
+      } else {  // lx - cx etc. are half-integers, exact in FP32
+        val = me_potential_df(Qd, df_mul_f((float)lx - cxf, Hx), df_mul_f((float)ly - cyf, Hy),
+                              df_mul_f((float)lz - czf, Hz));
+      }
+      const float2 f = split64(fp[g]);
+      out[t] = df_to_double(df_mul(val, DF{f.x, f.y}));
+    } else {
+      const double val = inside ? v[(lz * P.ext[1] + ly) * P.ext[0] + lx]
+                                : me_potential(Qs, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
+      out[t] = __dmul_rn(val, fp[g]);
+    }
   }
 }
 

@@ -106,9 +106,12 @@ __global__ void __launch_bounds__(256, 1)
 
 // Boundary values (Eq. me) at every point outside the box that the
 // 37-point stencil reaches, moved into b with the stencil weights; one CTA
-// per pair, one thread per line of the box along each axis in turn (the
-// axes one after the other, so every b entry is updated in a fixed order).
+// per pair, the axes one after the other: the ghost values of up to
+// SEA_BND_LINES lines across the axis (one evaluation per thread) go to
+// shared memory, then one thread per line adds them into b (every b entry
+// is updated in a fixed order).
 // DFM: the potentials in double-float arithmetic (mixed form).
+#define SEA_BND_LINES 128
 template <bool DFM>
 __global__ void __launch_bounds__(256, DFM ? 2 : 1)
     k_pair_boundary(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
@@ -129,54 +132,60 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   }
   __syncthreads();
   // me_potential at grid offsets (ox, oy, oz) from the box centre, in units
-  // of h (half-integers)
+  // of h (half-integers, exact in FP32)
   const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
-  auto pot = [&](double ox, double oy, double oz) -> double {
-    if (DFM)
-      return df_to_double(me_potential_df(Qd, df_mul_f((float)ox, Hx), df_mul_f((float)oy, Hy),
-                                          df_mul_f((float)oz, Hz)));
-    return me_potential(Qs, ox * hx, oy * hy, oz * hz);
-  };
-  const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (ez - 1);
+  const float cx = 0.5f * (float)(ex - 1), cy = 0.5f * (float)(ey - 1), cz = 0.5f * (float)(ez - 1);
+  constexpr int NG = 2 * SEA_FDP;  // ghost values per line: d = 1..FDP below, then above
+  __shared__ double Gs[SEA_BND_LINES * NG];
   for (int a = 0; a < 3; ++a) {
     // line coordinates (u1, u2) across axis a; along-axis extent ea, stride sa
     const int e1 = a == 0 ? ey : ex, e2 = a == 2 ? ey : ez;
     const int ea = a == 0 ? ex : (a == 1 ? ey : ez);
     const int sa = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
-    const double ca = a == 0 ? cx : (a == 1 ? cy : cz);
+    const float ca = a == 0 ? cx : (a == 1 ? cy : cz);
     const int nl = e1 * e2;
-    for (int line = threadIdx.x; line < nl; line += blockDim.x) {
-      const int u1 = line % e1, u2 = line / e1;
-      // the two fixed coordinates in (x, y, z) order and the base index
-      int bx = 0, by = 0, bz = 0;
-      double px = 0, py = 0, pz = 0;  // offsets from the centre in units of h
-      if (a == 0) { by = u1; bz = u2; py = by - cy; pz = bz - cz; }
-      else if (a == 1) { bx = u1; bz = u2; px = bx - cx; pz = bz - cz; }
-      else { bx = u1; by = u2; px = bx - cx; py = by - cy; }
-      const int base = (bz * ey + by) * ex + bx;
-      double Glo[SEA_FDP + 1], Ghi[SEA_FDP + 1];
-#pragma unroll 1
-      for (int k = 0; k < 2 * SEA_FDP; ++k) {  // one call site: d = 1..FDP below, then above
+    for (int l0 = 0; l0 < nl; l0 += SEA_BND_LINES) {
+      const int nb = min(SEA_BND_LINES, nl - l0);
+      // the ghost values of SEA_BND_LINES lines, one evaluation per thread
+      for (int e = threadIdx.x; e < nb * NG; e += blockDim.x) {
+        const int line = l0 + e / NG, k = e % NG;
+        const int u1 = line % e1, u2 = line / e1;
+        const float o1 = (float)u1 - (a == 0 ? cy : cx), o2 = (float)u2 - (a == 2 ? cy : cz);
         const int d = k % SEA_FDP + 1;
-        const double t = k < SEA_FDP ? -d - ca : ea - 1 + d - ca;
-        const double g = pot(a == 0 ? t : px, a == 1 ? t : py, a == 2 ? t : pz);
-        if (k < SEA_FDP)
-          Glo[d] = g;
+        const float t = k < SEA_FDP ? (float)(-d) - ca : (float)(ea - 1 + d) - ca;
+        const float ox = a == 0 ? t : o1, oy = a == 0 ? o1 : (a == 1 ? t : o2);
+        const float oz = a == 2 ? t : o2;
+        if (DFM)
+          Gs[e] = df_to_double(me_potential_df(Qd, df_mul_f(ox, Hx), df_mul_f(oy, Hy),
+                                               df_mul_f(oz, Hz)));
         else
-          Ghi[d] = g;
+          Gs[e] = me_potential(Qs, (double)ox * hx, (double)oy * hy, (double)oz * hz);
       }
-      for (int ta = 0; ta < ea; ++ta) {
-        if (ta >= SEA_FDP && ta < ea - SEA_FDP) continue;
-        double add = 0.0;
+      __syncthreads();
+      // moved into b with the stencil weights, thread per line (fixed order)
+      for (int li = threadIdx.x; li < nb; li += blockDim.x) {
+        const int line = l0 + li;
+        const int u1 = line % e1, u2 = line / e1;
+        int bx = 0, by = 0, bz = 0;
+        if (a == 0) { by = u1; bz = u2; }
+        else if (a == 1) { bx = u1; bz = u2; }
+        else { bx = u1; by = u2; }
+        const int base = (bz * ey + by) * ex + bx;
+        // ghost value d below: entry d - 1; above: entry FDP + d - 1
+        for (int ta = 0; ta < ea; ++ta) {
+          if (ta >= SEA_FDP && ta < ea - SEA_FDP) continue;
+          const double* G = Gs + li * NG;
+          double add = 0.0;
 #pragma unroll
-        for (int k = 1; k <= SEA_FDP; ++k) {
-          if (ta - k < 0) add += W.rhs[a][k] * Glo[k - ta];
-          if (ta + k > ea - 1) add += W.rhs[a][k] * Ghi[ta + k - (ea - 1)];
+          for (int k = 1; k <= SEA_FDP; ++k) {
+            if (ta - k < 0) add += W.rhs[a][k] * G[k - ta - 1];
+            if (ta + k > ea - 1) add += W.rhs[a][k] * G[SEA_FDP + ta + k - (ea - 1) - 1];
+          }
+          b[base + ta * sa] += add;
         }
-        b[base + ta * sa] += add;
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

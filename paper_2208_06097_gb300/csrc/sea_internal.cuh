@@ -201,7 +201,23 @@ __device__ __forceinline__ DF df_from_double(double x) {
   const float hi = (float)x;
   return DF{hi, (float)(x - (double)hi)};
 }
-__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+// hi + lo as FP64 with integer operations only: both terms as fixed-point
+// integers on the larger one's exponent (bits more than 2^-62 below it
+// dropped), one rounding to nearest.  FP32 subnormals count as zero.
+__device__ __forceinline__ double df_to_double(DF a) {
+  const unsigned bh = __float_as_uint(a.hi), bl = __float_as_uint(a.lo);
+  const int eh = (int)((bh >> 23) & 0xFF), el = (int)((bl >> 23) & 0xFF);
+  const int E = max(eh, el);
+  if (E == 0) return 0.0;
+  auto fixed = [&](unsigned b, int e) -> long long {
+    if (e == 0) return 0;
+    const int sh = E - e;
+    if (sh > 62) return 0;
+    const long long v = ((long long)((b & 0x7FFFFFu) | 0x800000u) << 38) >> sh;
+    return (b >> 31) ? -v : v;
+  };
+  return scaled_i64(fixed(bh, eh) + fixed(bl, el), E - 150 - 38);
+}
 
 // v = hi + lo with integer operations only (no FP64 instruction): hi keeps
 // the sign, the exponent and the top 23 mantissa bits (truncation), lo the
