@@ -54,47 +54,53 @@ __device__ __forceinline__ void scale_twice(int s, int L, int n, int* ws, int* w
 
 // Thread per orbital: count (mode 0) or write (mode 1) its entries in pair
 // order.  eptr must hold the exclusive scan of the counts for mode 1.
+// Warp per orbital: the lanes test 32 pairs at a time and the entries of o
+// are numbered in pair order by ballots (deterministic).
 __global__ void k_entries(const PairInfo* __restrict__ pinfo, const int* __restrict__ npairs,
                           const int* __restrict__ box, int n_orb, int nx, int ny, int nz,
                           int mode, int* __restrict__ ecount, const int* __restrict__ eptr,
                           Entry* __restrict__ ent) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n_orb) return;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (o >= n_orb) return;  // warp-uniform
   const int P = *npairs;
   const int N[3] = {nx, ny, nz};
   int cnt = 0;
   int pos = mode ? eptr[o] : 0;
-  for (int p = 0; p < P; ++p) {
-    const PairInfo I = pinfo[p];
-    int role;
-    if (I.i == o)
-      role = 0;
-    else if (I.j == o)
-      role = 1;
-    else
-      continue;
-    ++cnt;
-    if (!mode) continue;
-    Entry e;
-    e.pair = p;
-    e.o = o;
-    e.partner = role == 0 ? I.j : I.i;
-    for (int a = 0; a < 3; ++a) {
-      if (role == 0 && I.i == I.j) {
-        int s0, l0;
-        box_window(box[I.i * 6 + a], box[I.i * 6 + 3 + a], 0, N[a], I.lo[a], I.ext[a], &s0, &l0);
-        scale_twice(s0, l0, N[a], &e.ws[a], &e.wl[a]);
-      } else if (role == 0) {
-        box_window(box[I.j * 6 + a], box[I.j * 6 + 3 + a], I.k[a], N[a], I.lo[a], I.ext[a],
-                   &e.ws[a], &e.wl[a]);
-      } else {
-        box_window(box[I.i * 6 + a], box[I.i * 6 + 3 + a], 0, N[a], I.lo[a], I.ext[a], &e.ws[a],
-                   &e.wl[a]);
-      }
+  for (int p0 = 0; p0 < P; p0 += 32) {
+    const int p = p0 + lane;
+    int role = -1;
+    int pi = -1, pj = -1;
+    if (p < P) {
+      pi = pinfo[p].i;
+      pj = pinfo[p].j;
+      role = pi == o ? 0 : (pj == o ? 1 : -1);
     }
-    ent[pos++] = e;
+    const unsigned mask = __ballot_sync(0xffffffffu, role >= 0);
+    if (mode && role >= 0) {
+      const PairInfo I = pinfo[p];
+      Entry e;
+      e.pair = p;
+      e.o = o;
+      e.partner = role == 0 ? I.j : I.i;
+      for (int a = 0; a < 3; ++a) {
+        if (role == 0 && I.i == I.j) {
+          int s0, l0;
+          box_window(box[I.i * 6 + a], box[I.i * 6 + 3 + a], 0, N[a], I.lo[a], I.ext[a], &s0, &l0);
+          scale_twice(s0, l0, N[a], &e.ws[a], &e.wl[a]);
+        } else if (role == 0) {
+          box_window(box[I.j * 6 + a], box[I.j * 6 + 3 + a], I.k[a], N[a], I.lo[a], I.ext[a],
+                     &e.ws[a], &e.wl[a]);
+        } else {
+          box_window(box[I.i * 6 + a], box[I.i * 6 + 3 + a], 0, N[a], I.lo[a], I.ext[a], &e.ws[a],
+                     &e.wl[a]);
+        }
+      }
+      ent[pos + __popc(mask & ((1u << lane) - 1u))] = e;
+    }
+    pos += __popc(mask);
+    cnt += __popc(mask);
   }
-  if (!mode) ecount[o] = cnt;
+  if (!mode && lane == 0) ecount[o] = cnt;
 }
 
 // Single-CTA exclusive scan of n ints (n small); total into *tot.
@@ -255,41 +261,69 @@ __global__ void __launch_bounds__(256)
 // E_xx = -sum_p (2 - delta_ij) e_p in pair order, plus CG statistics:
 // res[0] = E_xx, res[1] = sum |Omega_ij| x iterations, res[2..4] = min,
 // max, mean iterations.
-__global__ void k_exx(const PairInfo* __restrict__ pinfo, const int* __restrict__ npairs,
-                      const double* __restrict__ epair, const int* __restrict__ iters,
-                      double* __restrict__ res) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) k_exx(const PairInfo* __restrict__ pinfo,
+                                              const int* __restrict__ npairs,
+                                              const double* __restrict__ epair,
+                                              const int* __restrict__ iters,
+                                              double* __restrict__ res) {
+  // thread t sums a contiguous range of pairs in order, then the block sums
+  // the threads' values in a fixed order (deterministic)
+  __shared__ double red[3][32];
+  __shared__ int ired[2][32];
   const int P = *npairs;
+  const int T = blockDim.x, chunk = (P + T - 1) / T;
+  const int p0 = threadIdx.x * chunk, p1 = min(P, p0 + chunk);
   double e = 0.0, ui = 0.0, sum = 0.0;
   int mn = 0x7fffffff, mx = 0;
-  for (int p = 0; p < P; ++p) {
-    e += (pinfo[p].i == pinfo[p].j ? 1.0 : 2.0) * epair[p];
+  for (int p = p0; p < p1; ++p) {
+    const PairInfo I = pinfo[p];
+    e += (I.i == I.j ? 1.0 : 2.0) * epair[p];
     const int it = iters[p] < 0 ? -iters[p] : iters[p];
-    ui += (double)pinfo[p].n * it;
+    ui += (double)I.n * it;
     sum += it;
     mn = min(mn, it);
     mx = max(mx, it);
   }
-  res[0] = -e;
-  res[1] = ui;
-  res[2] = P ? mn : 0;
-  res[3] = mx;
-  res[4] = P ? sum / P : 0.0;
+  e = block_sum(e, red[0]);
+  ui = block_sum(ui, red[1]);
+  sum = block_sum(sum, red[2]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ired[0][threadIdx.x >> 5] = mn;
+    ired[1][threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (T >> 5); ++k) {
+      mn = min(mn, ired[0][k]);
+      mx = max(mx, ired[1][k]);
+    }
+    mn = min(mn, ired[0][0]);
+    mx = max(mx, ired[1][0]);
+    res[0] = -e;
+    res[1] = ui;
+    res[2] = P ? mn : 0;
+    res[3] = mx;
+    res[4] = P ? sum / P : 0.0;
+  }
 }
 
 cudaError_t launch_entries(sea_ctx* c) {
   const int n = c->n_orb;
   int* counts = (int*)c->counts.p;
-  k_entries<<<(n + 127) / 128, 128, 0, c->stream>>>((const PairInfo*)c->pinfo.p, counts + 1,
-                                                    (const int*)c->box.p, n, c->N[0], c->N[1],
-                                                    c->N[2], 0, (int*)c->eent.p, nullptr,
-                                                    nullptr);
+  k_entries<<<(n + 7) / 8, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p, counts + 1,
+                                                (const int*)c->box.p, n, c->N[0], c->N[1],
+                                                c->N[2], 0, (int*)c->eent.p, nullptr, nullptr);
   // counts were written into the start of eent as scratch: scan them into eptr
   k_scan_int<<<1, 1024, 0, c->stream>>>((const int*)c->eent.p, n, (int*)c->eptr.p, counts + 2);
-  k_entries<<<(n + 127) / 128, 128, 0, c->stream>>>((const PairInfo*)c->pinfo.p, counts + 1,
-                                                    (const int*)c->box.p, n, c->N[0], c->N[1],
-                                                    c->N[2], 1, nullptr, (const int*)c->eptr.p,
-                                                    (Entry*)c->ewin.p);
+  k_entries<<<(n + 7) / 8, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p, counts + 1,
+                                                (const int*)c->box.p, n, c->N[0], c->N[1],
+                                                c->N[2], 1, nullptr, (const int*)c->eptr.p,
+                                                (Entry*)c->ewin.p);
   k_entry_offsets<<<1, 1024, 0, c->stream>>>((const Entry*)c->ewin.p, counts + 2,
                                              (long long*)c->coff.p, (long long*)(counts + 6),
                                              (long long*)(counts + 8));
@@ -325,7 +359,7 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
 
 // E_xx and the CG statistics (after every pair energy is final).
 cudaError_t launch_exx(sea_ctx* c) {
-  k_exx<<<1, 32, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const int*)c->counts.p + 1,
+  k_exx<<<1, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const int*)c->counts.p + 1,
                                  (const double*)c->epair.p, (const int*)c->iters.p,
                                  (double*)c->exx_dev.p);
   c->launches += 1;

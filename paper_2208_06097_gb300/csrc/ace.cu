@@ -74,31 +74,36 @@ __global__ void k_tile_incidence(const Entry* __restrict__ ent, const int* __res
   sub[t] = hit ? (x0 | (x1 << 4) | (y0 << 8) | (y1 << 12) | (z0 << 16) | (z1 << 20)) : 0;
 }
 
-// Tile-major lists: thread per tile, orbitals ascending.  mode 0 counts,
-// mode 1 writes the list and the incidence index gidx[o][T].
+// Tile-major lists: one warp per tile, orbitals ascending (ballot
+// compaction keeps the order).  mode 0 counts, mode 1 writes the list and
+// the incidence index gidx[o][T].
 __global__ void k_tile_lists(const int* __restrict__ inc, const int* __restrict__ sub, int n_orb,
                              int n_tiles, int mode, int* __restrict__ cnt,
                              const int* __restrict__ ptr, int* __restrict__ list,
                              int* __restrict__ lsub, int* __restrict__ gidx) {
-  const int T = blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= n_tiles) return;
+  const int T = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (T >= n_tiles) return;  // warp-uniform
   int c = 0;
-  int pos = mode ? ptr[T] : 0;
-  for (int o = 0; o < n_orb; ++o) {
+  const int base = mode ? ptr[T] : 0;
+  for (int o0 = 0; o0 < n_orb; o0 += 32) {
+    const int o = o0 + lane;
     const size_t q = (size_t)o * n_tiles + T;
-    if (!inc[q]) {
-      if (mode) gidx[q] = -1;
-      continue;
+    const bool hit = o < n_orb && inc[q];
+    const unsigned bal = __ballot_sync(0xffffffffu, hit);
+    if (mode && o < n_orb) {
+      if (hit) {
+        const int pos = base + c + __popc(bal & ((1u << lane) - 1u));
+        list[pos] = o;
+        lsub[pos] = sub[q];
+        gidx[q] = pos;
+      } else {
+        gidx[q] = -1;
+      }
     }
-    ++c;
-    if (mode) {
-      list[pos] = o;
-      lsub[pos] = sub[q];
-      gidx[q] = pos;
-      ++pos;
-    }
+    c += __popc(bal);
   }
-  if (!mode) cnt[T] = c;
+  if (!mode && lane == 0) cnt[T] = c;
 }
 
 // Orbital-major lists: one warp per orbital, tiles ascending (ballot
@@ -112,16 +117,23 @@ __global__ void k_orb_lists(const int* __restrict__ gidx, int n_orb, int n_tiles
   if (o >= n_orb) return;
   int c = 0;
   const int base = mode ? ptr[o] : 0;
-  for (int T0 = 0; T0 < n_tiles; T0 += 32) {
-    const int T = T0 + lane;
-    const int g = T < n_tiles ? gidx[(size_t)o * n_tiles + T] : -1;
-    const unsigned bal = __ballot_sync(0xffffffffu, g >= 0);
-    if (mode && g >= 0) {
-      const int pos = base + c + __popc(bal & ((1u << lane) - 1u));
-      list[pos] = T;
-      slot[pos] = g;
+  for (int T0 = 0; T0 < n_tiles; T0 += 128) {  // four chunks of 32 tiles per step
+    int g[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int T = T0 + 32 * u + lane;
+      g[u] = T < n_tiles ? gidx[(size_t)o * n_tiles + T] : -1;
     }
-    c += __popc(bal);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned bal = __ballot_sync(0xffffffffu, g[u] >= 0);
+      if (mode && g[u] >= 0) {
+        const int pos = base + c + __popc(bal & ((1u << lane) - 1u));
+        list[pos] = T0 + 32 * u + lane;
+        slot[pos] = g[u];
+      }
+      c += __popc(bal);
+    }
   }
   if (!mode && lane == 0) cnt[o] = c;
 }
@@ -791,8 +803,8 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   int* counts = (int*)c->counts.p;
   k_tile_incidence<<<(unsigned)((ninc + 255) / 256), 256, 0, c->stream>>>(
       (const Entry*)c->ewin.p, (const int*)c->eptr.p, n, G, nt, c->w_dense ? 1 : 0, inc, sub);
-  k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, sub, n, nt, 0, tcnt, nullptr,
-                                                        nullptr, nullptr, nullptr);
+  k_tile_lists<<<(nt + 7) / 8, 256, 0, c->stream>>>(inc, sub, n, nt, 0, tcnt, nullptr, nullptr,
+                                                    nullptr, nullptr);
   k_scan_small<<<1, 1024, 0, c->stream>>>(tcnt, nt, tptr, counts + 10);
   k_max_int<<<1, 1024, 0, c->stream>>>(tcnt, nt, counts + 12);
   int hc[3] = {0, 0, 0};
@@ -822,8 +834,8 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   int* tsub = tlist + max(hinc, 1);
   int* olist = (int*)c->tlist_o.p;
   int* oslot = olist + max(hinc, 1);
-  k_tile_lists<<<(nt + 127) / 128, 128, 0, c->stream>>>(inc, sub, n, nt, 1, nullptr, tptr, tlist,
-                                                        tsub, gidx);
+  k_tile_lists<<<(nt + 7) / 8, 256, 0, c->stream>>>(inc, sub, n, nt, 1, nullptr, tptr, tlist,
+                                                    tsub, gidx);
   k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 0, ocnt, nullptr,
                                                            nullptr, nullptr);
   k_scan_small<<<1, 1024, 0, c->stream>>>(ocnt, n, optr, counts + 11);
