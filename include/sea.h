@@ -112,6 +112,9 @@ typedef struct {
   int ace_dropped_eigenvalues;  /* eigenvalues treated as zero                  */
   int batch_graph;  /* last sea_apply_vxx_batch led by this context: 0 direct
                        launches, 1 graph captured, 2 graph replayed            */
+  int ace_max_tile_list; /* longest W list of a tile, last sea_build_ace (the
+                            mixed form expands lists up to 32 on the tensor
+                            cores, longer ones in FP32 error-free arithmetic) */
 } sea_stats;
 
 typedef struct sea_ctx sea_ctx;

@@ -482,6 +482,7 @@ static sea_status build_ace_common(sea_ctx* c) {
   cudaEventElapsedTime(&t, c->ev[10], c->ev[11]);
   c->stats.ms_gram_build = t;
   c->stats.ace_support_points = (long long)c->tile_inc * 128;
+  c->stats.ace_max_tile_list = c->max_tile_list;
   if (c->ace_eigen && c->stats.ace_dropped_eigenvalues == c->n_orb)
     return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is zero");
   c->have_ace = true;

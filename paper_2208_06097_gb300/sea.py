@@ -59,7 +59,8 @@ class Stats(ctypes.Structure):
                 ("ms_gram_build", ctypes.c_double), ("ms_gram_apply", ctypes.c_double),
                 ("ms_expand_apply", ctypes.c_double), ("ace_eigen", ctypes.c_int),
                 ("ace_eigen_sweeps", ctypes.c_int), ("ace_negative_eigenvalues", ctypes.c_int),
-                ("ace_dropped_eigenvalues", ctypes.c_int), ("batch_graph", ctypes.c_int)]
+                ("ace_dropped_eigenvalues", ctypes.c_int), ("batch_graph", ctypes.c_int),
+                ("ace_max_tile_list", ctypes.c_int)]
 
 
 _LIB = None

@@ -79,3 +79,44 @@ def test_mixed_ace_matches_fp64_oracle(h2o8):
     yr = OA.apply_ace(a["Xi"], psi.reshape(4, -1), h2o8.dV)
     assert np.abs(y.reshape(4, -1) - yr).max() <= 1e-9 * np.abs(yr).max()
     assert np.abs(xi.cpu().numpy().reshape(h2o8.n_orb, -1) - a["Xi"]).max() <= 1e-8 * np.abs(a["Xi"]).max()
+
+
+def _mixed_ace_vs_oracle(s, n_vec=4):
+    """Mixed-form M, L and V_ace psi against the FP64 oracle; returns the
+    context statistics of the build."""
+    from oracle import ace as OA
+    from paper_2208_06097_gb300 import sea
+    ref = O.apply_vxx(s.phi, s.cell, O.Params(cg_tol=1e-12))
+    F = s.phi.reshape(s.n_orb, -1)
+    a = OA.build_ace(F, ref["vxx"].reshape(s.n_orb, -1), s.dV)
+    with sea.Context(s.cell, s.grid, precision=1, cg_tol=1e-12) as ctx:
+        phi = torch.from_numpy(np.ascontiguousarray(s.phi)).cuda()
+        out = torch.empty_like(phi)
+        ctx.set_orbitals(phi)
+        ctx.apply_vxx(out)
+        ctx.build_ace()
+        M, L = ctx.ace_matrices()
+        psi = synth.random_trial_vectors(n_vec, s.grid, 21)
+        y = np.empty_like(psi)
+        ctx.apply_ace(psi, y)
+        st = ctx.stats()
+    assert np.abs(M - a["M"]).max() <= 1e-9 * max(1.0, np.abs(a["M"]).max())
+    assert np.abs(L - a["L"]).max() <= 1e-9 * max(1.0, np.abs(a["L"]).max())
+    yr = OA.apply_ace(a["Xi"], psi.reshape(n_vec, -1), s.dV)
+    assert np.abs(y.reshape(n_vec, -1) - yr).max() <= 1e-9 * np.abs(yr).max()
+    return st
+
+
+def test_mixed_ace_odd_grid():
+    # odd nx: rows are not 16-byte strided, so the contraction takes the
+    # per-thread-load kernel instead of the TMA one; partial tiles on every axis
+    s = synth.make_waters(4, 7.5, (41, 36, 44), seed=42)
+    _mixed_ace_vs_oracle(s)
+
+
+def test_mixed_ace_long_tile_lists():
+    # a coarse grid puts more than 32 W rows on some tiles: those tiles are
+    # expanded by the FP32 kernel, the others on the tensor cores
+    s = synth.make_waters(64, 12.42, 32, seed=1001)
+    st = _mixed_ace_vs_oracle(s, n_vec=40)
+    assert st["ace_max_tile_list"] > 32, st["ace_max_tile_list"]
