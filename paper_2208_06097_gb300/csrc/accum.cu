@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   const double* fp = phi + (size_t)e.partner * ng;
   double* out = cbuf + coff[blockIdx.y];
   const double cx = 0.5 * (P.ext[0] - 1), cy = 0.5 * (P.ext[1] - 1), cz = 0.5 * (P.ext[2] - 1);
-  const float cxf = 0.5f * (float)(P.ext[0] - 1), cyf = 0.5f * (float)(P.ext[1] - 1),
-              czf = 0.5f * (float)(P.ext[2] - 1);
+  const float cxf = 0.5f * i2f_exact(P.ext[0] - 1), cyf = 0.5f * i2f_exact(P.ext[1] - 1),
+              czf = 0.5f * i2f_exact(P.ext[2] - 1);
   const int t1 = min(nw, t0 + SEA_CHUNK);
   for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
     const int tx = t % e.wl[0], ty = (t / e.wl[0]) % e.wl[1], tz = t / (e.wl[0] * e.wl[1]);
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
         const float2 s = split64(v[(lz * P.ext[1] + ly) * P.ext[0] + lx]);
         val = DF{s.x, s.y};
       } else {  // lx - cx etc. are half-integers, exact in FP32
-        val = me_potential_df(Qd, df_mul_f((float)lx - cxf, Hx), df_mul_f((float)ly - cyf, Hy),
-                              df_mul_f((float)lz - czf, Hz));
+        val = me_potential_df(Qd, df_mul_f(i2f_exact(lx) - cxf, Hx),
+                              df_mul_f(i2f_exact(ly) - cyf, Hy), df_mul_f(i2f_exact(lz) - czf, Hz));
       }
       const float2 f = split64(fp[g]);
       out[t] = df_to_double(df_mul(val, DF{f.x, f.y}));

@@ -58,9 +58,11 @@ __global__ void __launch_bounds__(256, 1)
       const double a = fi[g], c = fj[g];
       b[t] = fourpi * (a * c);
       const float2 as = split64(a), cs = split64(c);
+      // offsets from the centre, (2 x - (ex - 1)) / 2 etc., exact in FP32
       harm_accumulate_df(df_mul(DF{as.x, as.y}, DF{cs.x, cs.y}),
-                         df_mul_f((float)(x - cx), Hx), df_mul_f((float)(y - cy), Hy),
-                         df_mul_f((float)(z - cz), Hz), acc);
+                         df_mul_f(0.5f * i2f_exact(2 * x - (ex - 1)), Hx),
+                         df_mul_f(0.5f * i2f_exact(2 * y - (ey - 1)), Hy),
+                         df_mul_f(0.5f * i2f_exact(2 * z - (P.ext[2] - 1)), Hz), acc);
     }
     // warp sums in double-float, then the warps' sums in FP64 (fixed order)
 #pragma unroll
@@ -110,13 +112,19 @@ __global__ void __launch_bounds__(256, 1)
 // SEA_BND_LINES lines across the axis (one evaluation per thread) go to
 // shared memory, then one thread per line adds them into b (every b entry
 // is updated in a fixed order).
-// DFM: the potentials in double-float arithmetic (mixed form).
+// The stencil's right-hand-side weights as double-float pairs (mixed form).
+struct StencilWd {
+  float hi[3][SEA_FDP + 1], lo[3][SEA_FDP + 1];
+};
+
+// DFM: the potentials and their weighted sums in double-float arithmetic
+// (mixed form).
 #define SEA_BND_LINES 128
 template <bool DFM>
 __global__ void __launch_bounds__(256, DFM ? 2 : 1)
     k_pair_boundary(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
-                    double hx, double hy, double hz, StencilW W, const double* __restrict__ Qg,
-                    double* __restrict__ bbuf) {
+                    double hx, double hy, double hz, StencilW W, StencilWd Wd,
+                    const double* __restrict__ Qg, double* __restrict__ bbuf) {
   const int p = blockIdx.x;
   const PairInfo P = pinfo[p];
   const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
@@ -134,9 +142,11 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   // me_potential at grid offsets (ox, oy, oz) from the box centre, in units
   // of h (half-integers, exact in FP32)
   const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
-  const float cx = 0.5f * (float)(ex - 1), cy = 0.5f * (float)(ey - 1), cz = 0.5f * (float)(ez - 1);
+  const float cx = 0.5f * i2f_exact(ex - 1), cy = 0.5f * i2f_exact(ey - 1),
+              cz = 0.5f * i2f_exact(ez - 1);
   constexpr int NG = 2 * SEA_FDP;  // ghost values per line: d = 1..FDP below, then above
-  __shared__ double Gs[SEA_BND_LINES * NG];
+  __shared__ double Gs[SEA_BND_LINES * NG];  // plain form
+  __shared__ DF Gd[SEA_BND_LINES * NG];      // mixed form
   for (int a = 0; a < 3; ++a) {
     // line coordinates (u1, u2) across axis a; along-axis extent ea, stride sa
     const int e1 = a == 0 ? ey : ex, e2 = a == 2 ? ey : ez;
@@ -150,20 +160,23 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
       for (int e = threadIdx.x; e < nb * NG; e += blockDim.x) {
         const int line = l0 + e / NG, k = e % NG;
         const int u1 = line % e1, u2 = line / e1;
-        const float o1 = (float)u1 - (a == 0 ? cy : cx), o2 = (float)u2 - (a == 2 ? cy : cz);
+        const float o1 = i2f_exact(u1) - (a == 0 ? cy : cx), o2 = i2f_exact(u2) - (a == 2 ? cy : cz);
         const int d = k % SEA_FDP + 1;
-        const float t = k < SEA_FDP ? (float)(-d) - ca : (float)(ea - 1 + d) - ca;
+        const float t = i2f_exact(k < SEA_FDP ? -d : ea - 1 + d) - ca;
         const float ox = a == 0 ? t : o1, oy = a == 0 ? o1 : (a == 1 ? t : o2);
         const float oz = a == 2 ? t : o2;
         if (DFM)
-          Gs[e] = df_to_double(me_potential_df(Qd, df_mul_f(ox, Hx), df_mul_f(oy, Hy),
-                                               df_mul_f(oz, Hz)));
+          Gd[e] = me_potential_df(Qd, df_mul_f(ox, Hx), df_mul_f(oy, Hy), df_mul_f(oz, Hz));
         else
           Gs[e] = me_potential(Qs, (double)ox * hx, (double)oy * hy, (double)oz * hz);
       }
       __syncthreads();
-      // moved into b with the stencil weights, thread per line (fixed order)
-      for (int li = threadIdx.x; li < nb; li += blockDim.x) {
+      // moved into b with the stencil weights: thread per (line, boundary
+      // point); the terms of each point in a fixed order
+      const int nbp = min(ea, NG);  // points of a line within FDP of either end
+      for (int e = threadIdx.x; e < nb * nbp; e += blockDim.x) {
+        const int li = e / nbp, idx = e % nbp;
+        const int ta = ea <= NG ? idx : (idx < SEA_FDP ? idx : ea - NG + idx);
         const int line = l0 + li;
         const int u1 = line % e1, u2 = line / e1;
         int bx = 0, by = 0, bz = 0;
@@ -172,8 +185,17 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
         else { bx = u1; by = u2; }
         const int base = (bz * ey + by) * ex + bx;
         // ghost value d below: entry d - 1; above: entry FDP + d - 1
-        for (int ta = 0; ta < ea; ++ta) {
-          if (ta >= SEA_FDP && ta < ea - SEA_FDP) continue;
+        if (DFM) {
+          const DF* G = Gd + li * NG;
+          DF add{0.f, 0.f};
+#pragma unroll
+          for (int k = 1; k <= SEA_FDP; ++k) {
+            const DF w{Wd.hi[a][k], Wd.lo[a][k]};
+            if (ta - k < 0) add = df_add(add, df_mul(w, G[k - ta - 1]));
+            if (ta + k > ea - 1) add = df_add(add, df_mul(w, G[SEA_FDP + ta + k - (ea - 1) - 1]));
+          }
+          b[base + ta * sa] += df_to_double(add);
+        } else {
           const double* G = Gs + li * NG;
           double add = 0.0;
 #pragma unroll
@@ -871,9 +893,16 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
       (double*)c->bbuf.p, (double*)c->Q.p);
   auto boundary = c->prm.precision == 1 ? k_pair_boundary<true> : k_pair_boundary<false>;
+  const StencilW W = make_weights(c);
+  StencilWd Wd;
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k <= SEA_FDP; ++k) {
+      Wd.hi[a][k] = (float)W.rhs[a][k];
+      Wd.lo[a][k] = (float)(W.rhs[a][k] - (double)Wd.hi[a][k]);
+    }
   boundary<<<c->P, 256, 0, c->stream>>>(
-      (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2],
-      make_weights(c), (const double*)c->Q.p, (double*)c->bbuf.p);
+      (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], W, Wd,
+      (const double*)c->Q.p, (double*)c->bbuf.p);
   c->launches += 2;
   return cudaGetLastError();
 }

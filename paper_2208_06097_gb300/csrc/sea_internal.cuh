@@ -197,6 +197,11 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
   const float d = ((a.hi - p) - pe) + a.lo;  // a - s^2
   return df_fast_two_sum(s, d * (0.5f / s));
 }
+// An int |v| < 2^22 as FP32, exactly, without a conversion instruction:
+// added to the bit pattern of 1.5 2^23 it lands in the low mantissa bits.
+__device__ __forceinline__ float i2f_exact(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
 __device__ __forceinline__ DF df_from_double(double x) {
   const float hi = (float)x;
   return DF{hi, (float)(x - (double)hi)};
