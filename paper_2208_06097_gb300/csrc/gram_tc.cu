@@ -500,6 +500,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 // stores, lane = two points of one row, with the K-adjacent core matrices
 // 2064 bytes apart (2048 + 16) so that the 32 lanes hit 32 banks.
 // ---------------------------------------------------------------------------
+constexpr int GT2_THREADS = 512;                      // 16 warps
+constexpr int GT2_RPW = 64 / (GT2_THREADS / 32);      // rows per warp and raw half
 constexpr uint32_t A2_LBO = (MBLK / 8) * 128 + 16;    // 2064
 constexpr uint32_t A2_PLANE = 8 * A2_LBO;             // 8 runs of 8 points
 constexpr uint32_t SMEM_A2 = DIG * A2_PLANE;          // 99,072
@@ -520,7 +522,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(GT_THREADS, 1)
+__global__ void __launch_bounds__(GT2_THREADS, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap tmA, int m, TileGeom G, int n_tiles,
               const int* __restrict__ tptr, const uint4* __restrict__ wdig,
               const int* __restrict__ wexp, double* __restrict__ partial, int* __restrict__ queue,
@@ -606,7 +608,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   auto load_w = [&](const Unit& u) {
     const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
     const uint32_t lbo = DIG * P * 16;
-    for (int p = tid; p < P * 2 * DIG * 8; p += GT_THREADS) {
+    for (int p = tid; p < P * 2 * DIG * 8; p += GT2_THREADS) {
       const int run = p & 7, k = (p >> 3) % DIG, h = (p / (8 * DIG)) & 1, sl = p / (16 * DIG);
       const bool ok = sl < nj;
       const uint4* src = ok ? wdig + ((size_t)(u.j0 + u.jb + sl) * 2 + h) * DIG * 8 + k * 8 + run : wdig;
@@ -618,13 +620,14 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
       Wexp[h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
     }
   };
-  // rows 64 q .. 64 q + 63 of raw half q to digits: warp w, rows 4 w .. 4 w + 3
-  // of the half (lane = points 2 lane, 2 lane + 1: run lane / 4)
+  // rows 64 q .. 64 q + 63 of raw half q to digits: warp w, rows GT2_RPW w ..
+  // GT2_RPW w + GT2_RPW - 1 of the half (lane = points 2 lane, 2 lane + 1:
+  // run lane / 4)
   auto convert = [&](const Unit& u, int q) {
     const double2* raw = reinterpret_cast<const double2*>(sR + q * RAW_HALF);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int rh = 4 * warp + i, row = 64 * q + rh;
+    for (int i = 0; i < GT2_RPW; ++i) {
+      const int rh = GT2_RPW * warp + i, row = 64 * q + rh;
       const double2 v = raw[rh * 32 + lane];
       int em = max((int)((__double_as_longlong(v.x) >> 52) & 0x7FF),
                    (int)((__double_as_longlong(v.y) >> 52) & 0x7FF));
@@ -651,12 +654,12 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
   };
   auto epilogue = [&](const Unit& u) {
     const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
-    const int quarter = warp & 3, g = warp >> 2;
+    const int quarter = warp & 3, g = warp >> 2, ng4 = GT2_THREADS / 128;
     const int a = u.mb * MBLK + 32 * quarter + lane;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
     const int ea0 = Aexp[0][32 * quarter + lane] - 1022, ea1 = Aexp[1][32 * quarter + lane] - 1022;
 #pragma unroll 1
-    for (int c = g; c < nj; c += 4) {
+    for (int c = g; c < nj; c += ng4) {
       uint32_t f[2 * DIG];
 #pragma unroll
       for (int q = 0; q < 2 * DIG; ++q)
@@ -1241,7 +1244,7 @@ cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, 
   const int grid = std::min(nsm, std::max(n_tiles, 1));
   alignas(64) CUtensorMap map;
   if (make_a_map(A, m, G, &map))
-    k_gram_tc<<<grid, GT_THREADS, GT2_SMEM, st>>>(map, m, G, n_tiles, tptr, wdig, wexp, partial,
+    k_gram_tc<<<grid, GT2_THREADS, GT2_SMEM, st>>>(map, m, G, n_tiles, tptr, wdig, wexp, partial,
                                                   queue, status);
   else
     k_gram_tc_ldg<<<grid, GT_THREADS, GT_SMEM, st>>>(A, m, G, ng, n_tiles, tptr, wdig, wexp,
