@@ -88,3 +88,26 @@ def test_batch_rejects_mixed_streams():
     assert e.value.code == 1
     a.close()
     b.close()
+
+
+def test_batch_with_both_forms():
+    # FP64 and mixed-form contexts in one batch: the two forms' pairs run in
+    # separate launches with their own CTA sizes, each equal bit for bit to
+    # its own configuration's call
+    from paper_2208_06097_gb300 import sea
+    systems = _systems()
+    stream = torch.cuda.Stream()
+    ctxs = [sea.Context(s.cell, s.grid, stream=stream.cuda_stream, precision=k % 2)
+            for k, s in enumerate(systems)]
+    single = []
+    for c, s in zip(ctxs, systems):
+        c.set_orbitals(torch.from_numpy(s.phi).cuda())
+        out = torch.empty(s.phi.shape, dtype=torch.float64, device="cuda")
+        e = c.apply_vxx(out)
+        single.append((e, out.cpu().numpy()))
+    outs = [torch.empty(s.phi.shape, dtype=torch.float64, device="cuda") for s in systems]
+    ex = sea.apply_vxx_batch(ctxs, outs)
+    for (e, v), o, e1 in zip(single, outs, ex):
+        assert np.array_equal(o.cpu().numpy(), v) and e1 == e
+    for c in ctxs:
+        c.close()
