@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(128)
   const int z = blockIdx.x, i = blockIdx.y;
   const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int dqr = 128 / nx, dqx = 128 - dqr * nx;  // the step of 128 elements in rows and columns
   for (int x = threadIdx.x; x < nx; x += blockDim.x) col[x] = make_ulonglong2(0, 0);
   // a chunk's values are loaded into registers one chunk ahead, so the loads
   // of chunk k + 1 are in flight while chunk k is summed
@@ -100,14 +101,20 @@ __global__ void __launch_bounds__(128)
     const int nr = min(rows, ny - y0);
     __syncthreads();  // the previous chunk's tile is no longer read
     const int nq = nr * nx;
+    // (row, column) of element q = tid + 128 u, advanced without divisions
+    int r = threadIdx.x / nx, x = threadIdx.x - r * nx;
 #pragma unroll
     for (int u = 0; u < RC_PER_THREAD; ++u) {
-      const int q = threadIdx.x + u * 128;
-      if (q < nq) {
-        const int r = q / nx, x = q - r * nx;
+      if (threadIdx.x + u * 128 < nq) {
         unsigned long long lo, hi;
         sq_fixed(v[u], lo, hi);
         tile[r * pitch + x] = make_ulonglong2(lo, hi);
+      }
+      x += dqx;
+      r += dqr;
+      if (x >= nx) {
+        x -= nx;
+        ++r;
       }
     }
     __syncthreads();
