@@ -532,8 +532,31 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   // transfer directions and the kernels overlap.
   SEA_ALLOC(psi_dev, bytes);
   SEA_ALLOC(out_dev, bytes);
+  // chunk starts: a half-size first and last chunk (the copy-in before the
+  // first kernels and the copy-out after the last ones are not overlapped)
   const int per = std::max(32, (n_vec + SEA_XCHUNKS_MAX - 1) / SEA_XCHUNKS_MAX);
-  const int nch = (n_vec + per - 1) / per;
+  std::vector<int> cs;
+  {
+    const int h = per / 2;
+    int v = 0;
+    cs.push_back(0);
+    if (n_vec > 2 * per && (n_vec - 2 * h) / per + 3 <= SEA_XCHUNKS_MAX) {
+      v = h;
+      cs.push_back(v);
+      while (n_vec - h - v >= per) {
+        v += per;
+        cs.push_back(v);
+      }
+      if (n_vec - h > v) cs.push_back(n_vec - h);
+    } else {
+      while (v + per < n_vec) {
+        v += per;
+        cs.push_back(v);
+      }
+    }
+    cs.push_back(n_vec);
+  }
+  const int nch = (int)cs.size() - 1;
   double* pd = (double*)c->psi_dev.p;
   double* od = (double*)c->out_dev.p;
   cudaEvent_t* evH = c->xev;             // chunk k copied in
@@ -544,7 +567,7 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   SEA_CK(cudaStreamWaitEvent(c->xfer[0], ev_start, 0), "wait");
   SEA_CK(cudaStreamWaitEvent(c->xfer[1], ev_start, 0), "wait");
   for (int k = 0; k < nch; ++k) {
-    const size_t v0 = (size_t)k * per, nv = std::min<size_t>(per, n_vec - v0);
+    const size_t v0 = (size_t)cs[k], nv = (size_t)(cs[k + 1] - cs[k]);
     SEA_CK(cudaMemcpyAsync(pd + v0 * c->ng, psi + v0 * c->ng, nv * c->ng * sizeof(double),
                            cudaMemcpyHostToDevice, c->xfer[0]),
            "copy psi");
@@ -552,7 +575,7 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   }
   SEA_CK(cudaEventRecord(c->ev[7], c->stream), "event");
   for (int k = 0; k < nch; ++k) {
-    const size_t v0 = (size_t)k * per, nv = std::min<size_t>(per, n_vec - v0);
+    const size_t v0 = (size_t)cs[k], nv = (size_t)(cs[k + 1] - cs[k]);
     SEA_CK(cudaStreamWaitEvent(c->stream, evH[k], 0), "wait");
     cudaError_t e = sea::launch_ace_apply(c, pd + v0 * c->ng, (int)nv, od + v0 * c->ng);
     if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE apply workspace");
