@@ -9,9 +9,12 @@
 // (Eq. me) outside it.
 //   k_contrib   (grid over entries x chunks): c = v * phi_partner on the
 //               entry's window, stored per entry; no accumulation here.
-//   k_accumulate (CTA per orbital x z-slab): the slab of the output is
-//               zeroed, then each entry of the orbital is subtracted in
-//               pair order (a fixed order: no floating-point atomics).
+//   k_accumulate (CTA per orbital x z-plane): the plane is built in
+//               shared memory from zero, each entry of the orbital
+//               subtracted in pair order (a fixed order: no floating-point
+//               atomics), then stored once to the output and, when given,
+//               to a second output (the caller's copy).  Planes too large
+//               for shared memory take the same steps on a global slab.
 #include <algorithm>
 
 #include "sea_internal.cuh"
@@ -228,12 +231,16 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   }
 }
 
-// CTA per (orbital, slab of SLAB z-planes).
+// Global-memory form: CTA per (orbital, slab of SLAB z-planes); out2, when
+// given, receives the finished slab.
 #define SEA_SLAB 4
+// Largest plane (bytes) built in shared memory.
+#define SEA_ACC_SMEM_MAX (200 * 1024)
 __global__ void __launch_bounds__(256)
-    k_accumulate(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
-                 const Entry* __restrict__ ent, const long long* __restrict__ coff,
-                 const double* __restrict__ cbuf, double* __restrict__ out) {
+    k_accumulate_gmem(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
+                      const Entry* __restrict__ ent, const long long* __restrict__ coff,
+                      const double* __restrict__ cbuf, double* __restrict__ out,
+                      double* __restrict__ out2) {
   const int o = o_begin + blockIdx.x;
   const int z0 = blockIdx.y * SEA_SLAB, z1 = min(nz, z0 + SEA_SLAB);
   const size_t plane = (size_t)nx * ny;
@@ -255,6 +262,58 @@ __global__ void __launch_bounds__(256)
         Do[g] = __dsub_rn(Do[g], c[(size_t)tz * rowpts + r]);
       }
     }
+  }
+  if (out2) {
+    __syncthreads();
+    double* D2 = out2 + (size_t)o * plane * nz;
+    for (size_t g = z0 * plane + threadIdx.x; g < (size_t)z1 * plane; g += blockDim.x) D2[g] = Do[g];
+  }
+}
+
+// Shared-memory form: CTA per (orbital, z-plane), the plane (nx*ny
+// doubles) in dynamic shared memory.  A thread walks the window rows of an
+// entry with its (tx, ty) advanced by the CTA stride, without divisions.
+__global__ void __launch_bounds__(256)
+    k_accumulate(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
+                 const Entry* __restrict__ ent, const long long* __restrict__ coff,
+                 const double* __restrict__ cbuf, double* __restrict__ out,
+                 double* __restrict__ out2) {
+  extern __shared__ double sp[];
+  const int o = o_begin + blockIdx.x;
+  const int z = blockIdx.y;
+  const int plane = nx * ny;
+  for (int g = threadIdx.x; g < plane; g += blockDim.x) sp[g] = 0.0;
+  const int e0 = eptr[o], e1 = eptr[o + 1];
+  for (int k = e0; k < e1; ++k) {
+    const Entry e = ent[k];
+    const int tz = wrapi(z - e.ws[2], nz);
+    if (tz >= e.wl[2]) continue;  // uniform over the CTA
+    __syncthreads();
+    const int wx = e.wl[0], wy = e.wl[1];
+    const int rowpts = wx * wy;
+    const double* c = cbuf + coff[k] + (size_t)tz * rowpts;
+    const int x0 = wrapi(e.ws[0], nx), y0 = wrapi(e.ws[1], ny);
+    const int sy = blockDim.x / wx, sx = blockDim.x - sy * wx;  // stride as (rows, columns)
+    int ty = threadIdx.x / wx, tx = threadIdx.x - ty * wx;
+    for (int r = threadIdx.x; r < rowpts; r += blockDim.x) {
+      int gx = x0 + tx, gy = y0 + ty;
+      gx -= gx >= nx ? nx : 0;
+      gy -= gy >= ny ? ny : 0;
+      const int g = gy * nx + gx;
+      sp[g] = __dsub_rn(sp[g], c[r]);
+      tx += sx;
+      ty += sy;
+      if (tx >= wx) {
+        tx -= wx;
+        ++ty;
+      }
+    }
+  }
+  __syncthreads();
+  const size_t base = ((size_t)o * nz + z) * plane;
+  for (int g = threadIdx.x; g < plane; g += blockDim.x) {
+    out[base + g] = sp[g];
+    if (out2) out2[base + g] = sp[g];
   }
 }
 
@@ -334,7 +393,7 @@ cudaError_t launch_entries(sea_ctx* c) {
 // Window contributions and their accumulation for orbitals [o_begin, o_end),
 // whose entries are [e_begin, e_end) (entries are grouped by orbital).
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
-                                    int e_end) {
+                                    int e_end, double* out2) {
   if (e_end > e_begin) {
     const int chunks = (int)((c->max_window + SEA_CHUNK - 1) / SEA_CHUNK);
     for (int e0 = e_begin; e0 < e_end; e0 += 65535) {
@@ -349,9 +408,20 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
     }
   }
   if (o_end > o_begin) {
-    k_accumulate<<<dim3(o_end - o_begin, (c->N[2] + SEA_SLAB - 1) / SEA_SLAB), 256, 0, c->stream>>>(
-        c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p, (const Entry*)c->ewin.p,
-        (const long long*)c->coff.p, (const double*)c->cbuf.p, out);
+    const size_t smem = (size_t)c->N[0] * c->N[1] * sizeof(double);
+    if (smem <= SEA_ACC_SMEM_MAX) {
+      cudaError_t e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+      k_accumulate<<<dim3(o_end - o_begin, c->N[2]), 256, smem, c->stream>>>(
+          c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p, (const Entry*)c->ewin.p,
+          (const long long*)c->coff.p, (const double*)c->cbuf.p, out, out2);
+    } else {
+      k_accumulate_gmem<<<dim3(o_end - o_begin, (c->N[2] + SEA_SLAB - 1) / SEA_SLAB), 256, 0,
+                          c->stream>>>(c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p,
+                                       (const Entry*)c->ewin.p, (const long long*)c->coff.p,
+                                       (const double*)c->cbuf.p, out, out2);
+    }
     c->launches += 1;
   }
   return cudaGetLastError();
@@ -366,8 +436,8 @@ cudaError_t launch_exx(sea_ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate(sea_ctx* c, double* out) {
-  cudaError_t e = launch_accumulate_range(c, out, 0, c->n_orb, 0, c->E);
+cudaError_t launch_accumulate(sea_ctx* c, double* out, double* out2) {
+  cudaError_t e = launch_accumulate_range(c, out, 0, c->n_orb, 0, c->E, out2);
   return e != cudaSuccess ? e : launch_exx(c);
 }
 

@@ -381,13 +381,10 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
   SEA_CK(sea::launch_cg(c), "cg");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
-  const size_t bytes = (size_t)c->n_orb * c->ng * sizeof(double);
   double* vd = (double*)c->vxx_dev.p;
   if (on_device) {
-    SEA_CK(sea::launch_accumulate(c, vd), "accumulate");
+    SEA_CK(sea::launch_accumulate(c, vd, vxx_phi), "accumulate");
     SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
-    SEA_CK(cudaMemcpyAsync(vxx_phi, vd, bytes, cudaMemcpyDeviceToDevice, c->stream),
-           "copy V_xx phi");
   } else {
     // Host output: orbital ranges are finished and copied out one after
     // another, the copy of one range overlapping the kernels of the next.

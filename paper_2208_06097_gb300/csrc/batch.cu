@@ -181,14 +181,9 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
     if (e != cudaSuccess) return e;
     c0->launches += (total_mixed > 0) + (total > total_mixed);
     for (int k = 0; k < n; ++k) {
-      e = sea::launch_accumulate(ctxs[k], (double*)ctxs[k]->vxx_dev.p);
+      e = sea::launch_accumulate(ctxs[k], (double*)ctxs[k]->vxx_dev.p,
+                                 on_device ? outs[k] : nullptr);
       if (e != cudaSuccess) return e;
-      if (on_device) {
-        e = cudaMemcpyAsync(outs[k], ctxs[k]->vxx_dev.p,
-                            (size_t)ctxs[k]->n_orb * ctxs[k]->ng * sizeof(double),
-                            cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return e;
-      }
     }
     long long l1 = 0;
     for (int k = 0; k < n; ++k) l1 += ctxs[k]->launches;

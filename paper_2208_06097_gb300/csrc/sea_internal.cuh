@@ -468,9 +468,11 @@ cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, cons
                             int total, int* queue, int pad_cap, bool mixed);
 int cg_pad_cap(const sea_ctx* c);
 cudaError_t launch_entries(sea_ctx* c);
-cudaError_t launch_accumulate(sea_ctx* c, double* out);
+// V_xx phi into out (the context's W) and, when out2 is not null, also into
+// out2 (the caller's device buffer), both written by the same stores.
+cudaError_t launch_accumulate(sea_ctx* c, double* out, double* out2 = nullptr);
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
-                                    int e_end);
+                                    int e_end, double* out2 = nullptr);
 cudaError_t launch_exx(sea_ctx* c);
 // Learned warm start (unet.cu): x0 of every pair's CG from the attached model.
 cudaError_t launch_warm_start(sea_ctx* c);

@@ -75,6 +75,20 @@ def test_ragged_anisotropic_grid():
     _compare(s, cg_tol=1e-12)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_wide_planes(precision):
+    # x-y planes of 170 x 168 points (223 KB of FP64) do not fit in shared
+    # memory: the accumulation takes its global-memory form.  The device and
+    # host outputs come from different launches and must agree bit for bit.
+    s = synth.make_waters(1, 6.0, (170, 168, 24), seed=77)
+    s.phi = synth.loewdin_orthonormalize(s.phi, s.dV)
+    ctx, ref, v, exx = _compare(s, cg_tol=1e-12, precision=precision)
+    vh = np.empty_like(s.phi)
+    ctx.apply_vxx(vh)
+    np.testing.assert_array_equal(vh, v)
+    ctx.close()
+
+
 def test_single_orbital():
     s = synth.make_waters(1, 5.0, 32, seed=5)
     s.phi = synth.loewdin_orthonormalize(s.phi[:1].copy(), s.dV)
