@@ -788,16 +788,16 @@ __global__ void __launch_bounds__(256)
 
 // The contractions with W: FP64 kernels for the plain form, the
 // tensor-core kernel (exact BF16 digit splitting) for the mixed form.
-static void launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G, const int* tptr,
-                        const int* tlist, const int* tsub) {
+static cudaError_t launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G,
+                               const int* tptr, const int* tlist, const int* tsub) {
   const double* W = (const double*)c->vxx_dev.p;
   if (c->prm.precision == 1)
-    launch_gram_tc(c->stream, c->device, A, m, G, c->ng, c->n_tiles, tptr, c->tile_inc,
-                   c->wdig.p, (double*)c->partial.p, (int*)c->counts.p + 20,
-                   (unsigned*)c->status.p);
-  else
-    k_gram_partial<<<dim3(c->n_tiles, (m + GA - 1) / GA), 256, GRAM_SMEM, c->stream>>>(
-        A, m, W, G, c->ng, tptr, tlist, tsub, (double*)c->partial.p);
+    return launch_gram_tc(c->stream, c->device, A, m, G, c->ng, c->n_tiles, tptr, c->tile_inc,
+                          c->wdig.p, (double*)c->partial.p, (int*)c->counts.p + 20,
+                          (unsigned*)c->status.p);
+  k_gram_partial<<<dim3(c->n_tiles, (m + GA - 1) / GA), 256, GRAM_SMEM, c->stream>>>(
+      A, m, W, G, c->ng, tptr, tlist, tsub, (double*)c->partial.p);
+  return cudaGetLastError();
 }
 
 static cudaError_t launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr,
@@ -916,7 +916,8 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     c->launches += 2;
   }
   cudaEventRecord(c->ev[10], c->stream);
-  launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
+  err = launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
+  if (err != cudaSuccess) return err;
   cudaEventRecord(c->ev[11], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
@@ -1020,7 +1021,10 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
   const int* oslot = olist + max(hinc, 1);
   // G[o][v] = <W_o|psi_v> dV
   cudaEventRecord(c->ev[12], c->stream);
-  launch_gram(c, psi, nv, G, tptr, tlist, tsub);
+  {
+    const cudaError_t e = launch_gram(c, psi, nv, G, tptr, tlist, tsub);
+    if (e != cudaSuccess) return e;
+  }
   cudaEventRecord(c->ev[13], c->stream);
   k_gram_reduce<<<(unsigned)(((long long)n * nv + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p,

@@ -490,23 +490,26 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 
 // ---------------------------------------------------------------------------
 // The same contraction with A's rows brought in by the tensor memory
-// accelerator.  Per unit one 4D box (x 8, y 4, z 2, rows 64) per half of
-// the A block, i.e. two 32 KB loads into two raw buffers, each tracked by
-// its own mbarrier; while the warps turn raw buffer 0 into digits, buffer
-// 1 is still landing, and the next unit's buffer-0 load starts as soon as
-// its rows are converted.  Points outside the grid and rows beyond m read
-// the box's zero fill.  One W buffer (a W block is loaded after the MMAs
-// of the previous block completed).  Digits go to shared memory by 4-byte
-// stores, lane = two points of one row, with the K-adjacent core matrices
-// 2064 bytes apart (2048 + 16) so that the 32 lanes hit 32 banks.
+// accelerator.  Per unit two 4D boxes (x 8, y 4, z 1, rows 128): the two
+// z-planes of the half tile (K halves 0 and 1) for the whole A block, 32 KB
+// each, written with the 64-byte swizzle so that the reads below are free
+// of bank conflicts.  Thread t takes row t / 4 and the x-run y = t % 4 of
+// both planes (16 values; the row's exponent from a 4-lane maximum), forms
+// the digits in registers and stores one 16-byte core-matrix row per digit
+// plane.  The MMAs of K half 0 (committed to barrier 0) run while K half 1
+// is converted; those of K half 1 (barrier 1) run while the next unit's
+// rows are read and converted.  Both raw buffers are refilled for the next
+// unit as soon as their values are in registers.  Points outside the grid
+// and rows beyond m read the box's zero fill.  One W buffer: a new W block
+// is loaded after every MMA of the previous block completed.
 // ---------------------------------------------------------------------------
-constexpr int GT2_THREADS = 512;                      // 16 warps
-constexpr int GT2_RPW = 64 / (GT2_THREADS / 32);      // rows per warp and raw half
-constexpr uint32_t A2_LBO = (MBLK / 8) * 128 + 16;    // 2064
-constexpr uint32_t A2_PLANE = 8 * A2_LBO;             // 8 runs of 8 points
-constexpr uint32_t SMEM_A2 = DIG * A2_PLANE;          // 99,072
-constexpr uint32_t RAW_HALF = (MBLK / 2) * KH * 8;    // 32 KB: 64 rows x 64 points
-constexpr size_t GT2_SMEM = SMEM_A2 + SMEM_W + 2 * RAW_HALF + 256;
+constexpr int GT2_CONV = 512;                        // converting threads: 4 per A row
+constexpr int GT2_THREADS = GT2_CONV + 32;           // and one MMA-issuing warp
+constexpr uint32_t A2_LBO = (MBLK / 8) * 128 + 32;   // 2080: x-runs 8 banks apart
+constexpr uint32_t A2_PLANE = 8 * A2_LBO;            // 8 runs of 8 points
+constexpr uint32_t SMEM_A2 = DIG * A2_PLANE;         // 99,840
+constexpr uint32_t RAW_KHALF = MBLK * (KH / 2) * 8;  // 32 KB: 128 rows x 32 points
+constexpr size_t GT2_SMEM = 1024 + 2 * RAW_KHALF + SMEM_A2 + SMEM_W;
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
                                             int c2, int c3, uint32_t bar) {
@@ -522,22 +525,90 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
+// Balanced digits of |v| 2^-E on the 2^-47 grid (as fixed47 and
+// digit_floats), each multiplied by the sign of v: six exact FP32 values.
+// The sign is applied by one FFMA per digit, s (b - c) = s b + (-s c).
+__device__ __forceinline__ void digits_signed(double v, int emax, float (&f)[DIG]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned hv = (unsigned)(bits >> 32);
+  const int e = (int)((hv >> 20) & 0x7FF);
+  int sh = emax - e + 6;
+  const bool ok = e != 0 && sh <= 60;
+  unsigned mh = ok ? ((hv & 0xFFFFFu) | 0x100000u) : 0u, ml = ok ? (unsigned)bits : 0u;
+  if (sh >= 32) {
+    ml = mh;
+    mh = 0u;
+    sh -= 32;
+  }
+  const unsigned xl = __funnelshift_r(ml, mh, sh), xh = __funnelshift_r(mh, 0u, sh);
+  const unsigned long long Y = (((unsigned long long)xh << 32) | xl) + 0x8080808080ULL;
+  const unsigned lo = (unsigned)Y, hi = (unsigned)(Y >> 32);
+  const unsigned sg = hv & 0x80000000u;
+  const float s = __uint_as_float(0x3F800000u | sg);
+  const float cm = __uint_as_float(__float_as_uint(-(12582912.0f + 128.0f)) ^ sg);
+  const float c0 = __uint_as_float(__float_as_uint(-12582912.0f) ^ sg);
+  f[5] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7650)), cm);
+  f[4] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7651)), cm);
+  f[3] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7652)), cm);
+  f[2] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7653)), cm);
+  f[1] = fmaf(s, __uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7650)), cm);
+  f[0] = fmaf(s, __uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7651)), c0);
+}
+
+// The digit planes of 8 consecutive points: d[k] = their 8 BF16 digits of
+// plane k (points 2i, 2i + 1 in word i).
+__device__ __forceinline__ void digits8(const double (&v)[8], int emax, uint4 (&d)[DIG]) {
+  uint32_t w[DIG][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float f0[DIG], f1[DIG];
+    digits_signed(v[2 * i], emax, f0);
+    digits_signed(v[2 * i + 1], emax, f1);
+#pragma unroll
+    for (int k = 0; k < DIG; ++k) w[k][i] = pack_bf16(f0[k], f1[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < DIG; ++k) d[k] = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
+}
+
+// Converting warps 0..15 (named barrier 1) and the issuing warp 16.  Per
+// unit the converting warps post the unit's block width and half to a
+// two-entry ring and arrive on ready[0] once K half 0's digits are in place,
+// on ready[1] once K half 1's are; the issuing thread waits on each,
+// issues that K half's MMAs and commits them to mma[0] / mma[1].  A unit
+// with width 0 ends the issuing loop.
+__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+// The same barrier returning whether v held in any converting thread (the
+// same value in all of them).
+__device__ __forceinline__ bool conv_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, 512, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
 __global__ void __launch_bounds__(GT2_THREADS, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap tmA, int m, TileGeom G, int n_tiles,
               const int* __restrict__ tptr, const uint4* __restrict__ wdig,
               const int* __restrict__ wexp, double* __restrict__ partial, int* __restrict__ queue,
               unsigned* __restrict__ status) {
   extern __shared__ unsigned char gt_raw[];
-  unsigned char* sA = gt_raw + ((128 - (smem_addr(gt_raw) & 127)) & 127);
+  unsigned char* sR = gt_raw + ((1024 - (smem_addr(gt_raw) & 1023)) & 1023);  // two K halves
+  unsigned char* sA = sR + 2 * RAW_KHALF;
   unsigned char* sW = sA + SMEM_A2;
-  unsigned char* sR = sW + SMEM_W;  // two raw halves of RAW_HALF
   __shared__ int Aexp[2][MBLK], Wexp[2][NBLK];  // [half][row]
-  __shared__ __align__(8) unsigned long long mbar, tbar[2];
+  __shared__ __align__(8) unsigned long long mbar[2], tbar[2], rbar[2];
+  __shared__ int u_ring[2][2];  // per posted unit: W block width (0: end), half
   __shared__ uint32_t tmem_base;
-  __shared__ int s_tile, s_fail;
+  __shared__ int s_tile, s_fail, s_ifail;  // converting / issuing side failed
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t bar = smem_addr(&mbar);
+  const uint32_t mb[2] = {smem_addr(&mbar[0]), smem_addr(&mbar[1])};
   const uint32_t tb[2] = {smem_addr(&tbar[0]), smem_addr(&tbar[1])};
+  const uint32_t rb[2] = {smem_addr(&rbar[0]), smem_addr(&rbar[1])};
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -546,236 +617,303 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tb[0]));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tb[1]));
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb[q]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tb[q]));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(rb[q]));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     s_fail = 0;
+    s_ifail = 0;
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
   const uint32_t a_base = smem_addr(sA), w_base = smem_addr(sW), r_base = smem_addr(sR);
-  const int nmb = (m + MBLK - 1) / MBLK;
-  bool tma_pending[2] = {false, false};  // meaningful in thread 0
 
-  auto claim = [&](Unit& u) -> bool {
-    __syncthreads();
-    if (tid == 0) {
-      int t;
-      do {
-        t = atomicAdd(queue, 1);
-      } while (t < n_tiles && tptr[t + 1] == tptr[t]);
-      s_tile = t;
-    }
-    __syncthreads();
-    const int T = s_tile;
-    if (T >= n_tiles) return false;
-    u.T = T;
-    u.j0 = tptr[T];
-    u.nJ = tptr[T + 1] - u.j0;
-    u.jb = 0;
-    u.mb = 0;
-    u.h = 0;
-    u.wb = 0;
-    return true;
-  };
-  auto advance = [&](Unit& u, bool* new_block) -> bool {
-    *new_block = false;
-    if (u.h == 0) {
-      u.h = 1;
-      return true;
-    }
-    u.h = 0;
-    if (++u.mb < nmb) return true;
-    u.mb = 0;
-    *new_block = true;
-    u.jb += NBLK;
-    if (u.jb < u.nJ) return true;
-    return claim(u);
-  };
-  // raw half q (rows 64 q .. 64 q + 63 of the A block) of unit u (thread 0)
-  auto tma_issue = [&](const Unit& u, int q) {
-    const int txi = u.T % G.ntx, tyi = (u.T / G.ntx) % G.nty, tzi = u.T / (G.ntx * G.nty);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(tb[q], RAW_HALF);
-    tma_load_4d(r_base + q * RAW_HALF, &tmA, txi * TX, tyi * TY, tzi * TZ + 2 * u.h,
-                u.mb * MBLK + 64 * q, tb[q]);
-    tma_pending[q] = true;
-  };
-  auto load_w = [&](const Unit& u) {
-    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
-    const uint32_t lbo = DIG * P * 16;
-    for (int p = tid; p < P * 2 * DIG * 8; p += GT2_THREADS) {
-      const int run = p & 7, k = (p >> 3) % DIG, h = (p / (8 * DIG)) & 1, sl = p / (16 * DIG);
-      const bool ok = sl < nj;
-      const uint4* src = ok ? wdig + ((size_t)(u.j0 + u.jb + sl) * 2 + h) * DIG * 8 + k * 8 + run : wdig;
-      const int row = k * P + sl;
-      cp_async16(w_base + h * W_HALF + (row >> 3) * CORE_SBO + run * lbo + (row & 7) * 16, src, ok);
-    }
-    if (tid < 2 * NBLK) {
-      const int h = tid / NBLK, sl = tid % NBLK;
-      Wexp[h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
-    }
-  };
-  // rows 64 q .. 64 q + 63 of raw half q to digits: warp w, rows GT2_RPW w ..
-  // GT2_RPW w + GT2_RPW - 1 of the half (lane = points 2 lane, 2 lane + 1:
-  // run lane / 4)
-  auto convert = [&](const Unit& u, int q) {
-    const double2* raw = reinterpret_cast<const double2*>(sR + q * RAW_HALF);
-#pragma unroll
-    for (int i = 0; i < GT2_RPW; ++i) {
-      const int rh = GT2_RPW * warp + i, row = 64 * q + rh;
-      const double2 v = raw[rh * 32 + lane];
-      int em = max((int)((__double_as_longlong(v.x) >> 52) & 0x7FF),
-                   (int)((__double_as_longlong(v.y) >> 52) & 0x7FF));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
-      float f0[DIG], f1[DIG];
-      digit_floats(fixed47(v.x, em), f0);
-      digit_floats(fixed47(v.y, em), f1);
-      unsigned char* dst = sA + (row >> 3) * CORE_SBO + (lane >> 2) * A2_LBO + (row & 7) * 16 +
-                           (lane & 3) * 4;
-#pragma unroll
-      for (int k = 0; k < DIG; ++k)
-        *reinterpret_cast<uint32_t*>(dst + k * A2_PLANE) = pack_bf16(f0[k], f1[k]);
-      if (lane == 0) Aexp[u.h][row] = em;
-    }
-  };
-  // bounded wait on raw half q (all threads); false on expiry
-  uint32_t tphase[2] = {0, 0};
-  auto wait_raw = [&](int q) -> bool {
-    const bool ok = mbar_wait(tb[q], tphase[q]);
-    tphase[q] ^= 1;
-    if (tid == 0) tma_pending[q] = false;
-    return ok;
-  };
-  auto epilogue = [&](const Unit& u) {
-    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
-    const int quarter = warp & 3, g = warp >> 2, ng4 = GT2_THREADS / 128;
-    const int a = u.mb * MBLK + 32 * quarter + lane;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
-    const int ea0 = Aexp[0][32 * quarter + lane] - 1022, ea1 = Aexp[1][32 * quarter + lane] - 1022;
-#pragma unroll 1
-    for (int c = g; c < nj; c += ng4) {
-      uint32_t f[2 * DIG];
-#pragma unroll
-      for (int q = 0; q < 2 * DIG; ++q)
-        f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
-      tmem_wait_ld();
-      double sum = 0.0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        long long acc = 0;
-#pragma unroll
-        for (int d = 0; d < DIG; ++d)
-          acc += (long long)float_int(__uint_as_float(f[h * DIG + d])) << (8 * (DIG - 1 - d));
-        sum += scaled_i64(acc, (h ? ea1 : ea0) + (Wexp[h][c] - 1022) - 54);
-      }
-      if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = sum;
-    }
-  };
-  auto issue = [&](const Unit& u) {
-    const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
-    const uint32_t lbo = DIG * P * 16;
-    const uint64_t a0 = sdesc(a_base, A2_LBO, CORE_SBO);
-    const uint64_t w0 = sdesc(w_base + u.h * W_HALF, lbo, CORE_SBO);
-    const uint32_t dcol = tmem + (uint32_t)(u.h * TMEM_HALF);
-#pragma unroll
-    for (int q = 0; q < KH / 16; ++q)
-#pragma unroll
-      for (int k = 0; k < DIG; ++k)
-        mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A2_PLANE + q * 2 * A2_LBO) >> 4),
-                 w0 + ((q * 2 * lbo) >> 4), idesc_bf16((DIG - k) * P), (k > 0 || q > 0) ? 1u : 0u);
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-  };
-
-  Unit cur;
-  cur.wb = 0;
-  uint32_t phase = 0;
-  bool have_prev = false, mma_pending = false;
-  Unit prev = cur;
-  if (claim(cur)) {
-    load_w(cur);
-    if (tid == 0) {
-      tma_issue(cur, 0);
-      tma_issue(cur, 1);
-    }
-    bool need_w = false;
-    for (;;) {
-      if (have_prev) {
-        // prev's MMAs done: digits, accumulators and W buffer are free
-        const bool ok = mbar_wait(bar, phase);
-        if (!ok) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        phase ^= 1;
-        mma_pending = false;
-        tc_fence_after();
-        if (prev.h == 1) {
-          epilogue(prev);
-          __syncthreads();  // exponents and W read before they are replaced
+  if (warp == GT2_CONV / 32) {
+    // ---- the issuing warp ----
+    if (lane == 0) {
+      uint32_t rph[2] = {0, 0};
+      for (int seq = 0;; ++seq) {
+        if (!mbar_wait(rb[0], rph[0])) {
+          s_ifail = 1;
+          break;
         }
+        rph[0] ^= 1;
+        const int nj = u_ring[seq & 1][0], h = u_ring[seq & 1][1];
+        if (nj == 0) break;
+        const int P = nj <= 16 ? 16 : 32;
+        const uint32_t lbo = DIG * P * 16;
+        const uint64_t a0 = sdesc(a_base, A2_LBO, CORE_SBO);
+        const uint64_t w0 = sdesc(w_base + h * W_HALF, lbo, CORE_SBO);
+        const uint32_t dcol = tmem + (uint32_t)(h * TMEM_HALF);
+        for (int kh = 0; kh < 2; ++kh) {
+          if (kh == 1) {
+            if (!mbar_wait(rb[1], rph[1])) {
+              s_ifail = 1;
+              break;
+            }
+            rph[1] ^= 1;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int qq = 0; qq < 2; ++qq) {
+            const int q = 2 * kh + qq;
+#pragma unroll
+            for (int k = 0; k < DIG; ++k)
+              mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A2_PLANE + q * 2 * A2_LBO) >> 4),
+                       w0 + ((q * 2 * lbo) >> 4), idesc_bf16((DIG - k) * P),
+                       (k > 0 || q > 0) ? 1u : 0u);
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  mb[kh])
+              : "memory");
+        }
+        if (s_ifail) break;
       }
-      if (need_w) load_w(cur);
-      // the two raw halves of cur, converted as they land; half 0's buffer
-      // is refilled for the next unit right after its conversion
-      if (!wait_raw(0)) s_fail = 1;
-      __syncthreads();
-      if (s_fail) break;
-      convert(cur, 0);
-      __syncthreads();  // raw half 0 consumed
-      Unit next = cur;
-      bool new_block = false;
-      const bool has_next = advance(next, &new_block);  // may claim (uniform, syncs)
-      if (tid == 0 && has_next) tma_issue(next, 0);
-      if (!wait_raw(1)) s_fail = 1;
-      __syncthreads();
-      if (s_fail) break;
-      convert(cur, 1);
-      cp_async_wait_all();
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_fence_before();
-      __syncthreads();  // digits, W and raw half 1 consumed
-      tc_fence_after();
+    }
+    __syncwarp();
+  } else {
+    // ---- the converting warps ----
+    const int nmb = (m + MBLK - 1) / MBLK;
+    bool tma_pending[2] = {false, false};  // meaningful in thread 0
+    // this thread's row and x-run, and the swizzled offset of its run
+    const int row = tid >> 2, run = tid & 3;
+    const uint32_t r_off = (uint32_t)(row * 256 + run * 64);
+    const uint32_t r_swz = (uint32_t)((((row & 1) << 1) | (run >> 1)) << 4);
+    auto claim = [&](Unit& u) -> bool {
+      conv_sync();
       if (tid == 0) {
-        if (has_next) tma_issue(next, 1);
-        issue(cur);
+        int t;
+        do {
+          t = atomicAdd(queue, 1);
+        } while (t < n_tiles && tptr[t + 1] == tptr[t]);
+        s_tile = t;
       }
-      mma_pending = true;
-      prev = cur;
-      have_prev = true;
-      if (!has_next) break;
-      need_w = new_block;
-      cur = next;
-    }
-    // the last unit's MMAs (bounded wait) and epilogue
-    if (!s_fail && mma_pending) {
-      const bool ok = mbar_wait(bar, phase);
-      if (!ok) s_fail = 1;
-      __syncthreads();
-      if (!s_fail) {
-        mma_pending = false;
+      conv_sync();
+      const int T = s_tile;
+      if (T >= n_tiles) return false;
+      u.T = T;
+      u.j0 = tptr[T];
+      u.nJ = tptr[T + 1] - u.j0;
+      u.jb = 0;
+      u.mb = 0;
+      u.h = 0;
+      u.wb = 0;
+      return true;
+    };
+    auto advance = [&](Unit& u, bool* new_block) -> bool {
+      *new_block = false;
+      if (u.h == 0) {
+        u.h = 1;
+        return true;
+      }
+      u.h = 0;
+      if (++u.mb < nmb) return true;
+      u.mb = 0;
+      *new_block = true;
+      u.jb += NBLK;
+      if (u.jb < u.nJ) return true;
+      return claim(u);
+    };
+    // K half q (z-plane 2 h + q of the half tile) of unit u's A block (thread 0)
+    auto tma_issue = [&](const Unit& u, int q) {
+      const int txi = u.T % G.ntx, tyi = (u.T / G.ntx) % G.nty, tzi = u.T / (G.ntx * G.nty);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(tb[q], RAW_KHALF);
+      tma_load_4d(r_base + q * RAW_KHALF, &tmA, txi * TX, tyi * TY, tzi * TZ + 2 * u.h + q,
+                  u.mb * MBLK, tb[q]);
+      tma_pending[q] = true;
+    };
+    auto load_w = [&](const Unit& u) {
+      const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+      const uint32_t lbo = DIG * P * 16;
+      for (int p = tid; p < P * 2 * DIG * 8; p += GT2_CONV) {
+        const int rn = p & 7, k = (p >> 3) % DIG, h = (p / (8 * DIG)) & 1, sl = p / (16 * DIG);
+        const bool ok = sl < nj;
+        const uint4* src =
+            ok ? wdig + ((size_t)(u.j0 + u.jb + sl) * 2 + h) * DIG * 8 + k * 8 + rn : wdig;
+        const int r = k * P + sl;
+        cp_async16(w_base + h * W_HALF + (r >> 3) * CORE_SBO + rn * lbo + (r & 7) * 16, src, ok);
+      }
+      if (tid < 2 * NBLK) {
+        const int h = tid / NBLK, sl = tid % NBLK;
+        Wexp[h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
+      }
+    };
+    // bounded waits; false on expiry
+    uint32_t tphase[2] = {0, 0}, mphase[2] = {0, 0};
+    bool mma_pend[2] = {false, false};
+    auto wait_raw = [&](int q) -> bool {
+      const bool ok = mbar_wait(tb[q], tphase[q]);
+      tphase[q] ^= 1;
+      if (tid == 0) tma_pending[q] = false;
+      return ok;
+    };
+    auto wait_mma = [&](int q) -> bool {
+      if (!mma_pend[q]) return true;
+      if (!mbar_wait(mb[q], mphase[q])) return false;
+      mphase[q] ^= 1;
+      mma_pend[q] = false;
+      return true;
+    };
+    // digits of K half q (x-run run + 4 q of the half tile) to shared memory
+    auto store_digits = [&](const uint4 (&d)[DIG], int q) {
+      unsigned char* dst = sA + (row >> 3) * CORE_SBO + (run + 4 * q) * A2_LBO + (row & 7) * 16;
+#pragma unroll
+      for (int k = 0; k < DIG; ++k) *reinterpret_cast<uint4*>(dst + k * A2_PLANE) = d[k];
+    };
+    auto epilogue = [&](const Unit& u) {
+      const int nj = min(NBLK, u.nJ - u.jb), P = nj <= 16 ? 16 : 32;
+      const int quarter = warp & 3, g = warp >> 2, ng4 = GT2_CONV / 128;
+      const int a = u.mb * MBLK + 32 * quarter + lane;
+      const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+      const int ea0 = Aexp[0][32 * quarter + lane] - 1022, ea1 = Aexp[1][32 * quarter + lane] - 1022;
+#pragma unroll 1
+      for (int c = g; c < nj; c += ng4) {
+        uint32_t f[2 * DIG];
+#pragma unroll
+        for (int q = 0; q < 2 * DIG; ++q)
+          f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
+        tmem_wait_ld();
+        double sum = 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          long long acc = 0;
+#pragma unroll
+          for (int d = 0; d < DIG; ++d)
+            acc += (long long)float_int(__uint_as_float(f[h * DIG + d])) << (8 * (DIG - 1 - d));
+          sum += scaled_i64(acc, (h ? ea1 : ea0) + (Wexp[h][c] - 1022) - 54);
+        }
+        if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = sum;
+      }
+    };
+    // post unit u (or the end, nj = 0) to the issuing thread: ring entry
+    // seq & 1, then ready[0] (thread 0, after a converting-warp barrier)
+    auto post = [&](int seq, int nj, int h) {
+      if (tid == 0) {
+        u_ring[seq & 1][0] = nj;
+        u_ring[seq & 1][1] = h;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rb[0]) : "memory");
+      }
+    };
+
+    Unit cur;
+    cur.wb = 0;
+    bool have_prev = false, fail = false;  // fail: uniform over the converting threads
+    Unit prev = cur;
+    int seq = 0;
+    if (claim(cur)) {
+      load_w(cur);
+      if (tid == 0) {
+        tma_issue(cur, 0);
+        tma_issue(cur, 1);
+      }
+      bool need_w = false;
+      for (;;) {
+        // both K halves of cur to registers; the row's exponent
+        bool ok = wait_raw(0);
+        ok = wait_raw(1) && ok;
+        if (conv_sync_or(!ok)) {
+          fail = true;
+          break;
+        }
+        double v[2][8];
+        int em = 0;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            const double2 t = *reinterpret_cast<const double2*>(
+                sR + q * RAW_KHALF + r_off + (((uint32_t)p << 4) ^ r_swz));
+            v[q][2 * p] = t.x;
+            v[q][2 * p + 1] = t.y;
+            em = max(em, (int)((__double_as_longlong(t.x) >> 52) & 0x7FF));
+            em = max(em, (int)((__double_as_longlong(t.y) >> 52) & 0x7FF));
+          }
+        em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
+        em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
+        conv_sync();  // both raw buffers consumed
+        Unit next = cur;
+        bool new_block = false;
+        const bool has_next = advance(next, &new_block);  // may claim (uniform, syncs)
+        if (tid == 0 && has_next) {
+          tma_issue(next, 0);
+          tma_issue(next, 1);
+        }
+        // K half 0's digits replace those prev's first MMAs read; the
+        // epilogue and a new W block need all of prev's MMAs
+        ok = wait_mma(0);
+        uint4 d[DIG];
+        digits8(v[0], em, d);
+        store_digits(d, 0);
+        if (have_prev && (prev.h == 1 || need_w)) ok = wait_mma(1) && ok;
+        if (conv_sync_or(!ok)) {
+          fail = true;
+          break;
+        }
         tc_fence_after();
-        if (prev.h == 1) epilogue(prev);
+        if (have_prev && prev.h == 1) {
+          epilogue(prev);
+          conv_sync();  // exponents and W read before they are replaced
+        }
+        if (need_w) load_w(cur);
+        if (run == 0) Aexp[cur.h][row] = em;
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        conv_sync();  // digits of K half 0, W and exponents in place
+        post(seq, min(NBLK, cur.nJ - cur.jb), cur.h);
+        mma_pend[0] = true;
+        digits8(v[1], em, d);
+        ok = wait_mma(1);  // prev's MMAs of K half 1
+        store_digits(d, 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        ++seq;
+        if (conv_sync_or(!ok)) {  // digits of K half 1 in place
+          fail = true;
+          break;
+        }
+        if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rb[1]) : "memory");
+        mma_pend[1] = true;
+        prev = cur;
+        have_prev = true;
+        if (!has_next) break;
+        need_w = new_block;
+        cur = next;
       }
     }
-    if (s_fail) {
-      if (mma_pending) mbar_wait(bar, phase);  // once more, bounded, before freeing
+    // the last unit's MMAs (bounded waits; the issuing thread has then taken
+    // every posted unit), the end of the issuing loop, the last epilogue
+    if (!fail) {
+      bool ok = wait_mma(0);
+      ok = wait_mma(1) && ok;
+      fail = conv_sync_or(!ok);
+    }
+    post(seq, 0, 0);
+    if (!fail) {
+      tc_fence_after();
+      if (have_prev && prev.h == 1) epilogue(prev);
+    } else {
+      // once more, bounded, before the tensor memory is freed
+      for (int q = 0; q < 2; ++q)
+        if (mma_pend[q]) mbar_wait(mb[q], mphase[q]);
       // loads still in flight land before the CTA's shared memory is released
       if (tid == 0)
         for (int q = 0; q < 2; ++q)
           if (tma_pending[q]) mbar_wait(tb[q], tphase[q]);
     }
+    cp_async_wait_all();
+    if (fail && tid == 0) s_fail = 1;
   }
-  cp_async_wait_all();
-  if (s_fail && tid == 0) atomicOr(status, SEA_FLAG_WAIT);
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && (s_fail || s_ifail)) atomicOr(status, SEA_FLAG_WAIT);
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -1175,10 +1313,10 @@ static bool make_a_map(const double* A, int m, const TileGeom& G, CUtensorMap* m
   const cuuint64_t dim[4] = {(cuuint64_t)G.nx, (cuuint64_t)G.ny, (cuuint64_t)G.nz, (cuuint64_t)m};
   const cuuint64_t stride[3] = {(cuuint64_t)G.nx * 8, (cuuint64_t)G.nx * G.ny * 8,
                                 (cuuint64_t)G.nx * G.ny * G.nz * 8};
-  const cuuint32_t box[4] = {TX, TY, 2, MBLK / 2};
+  const cuuint32_t box[4] = {TX, TY, 1, MBLK};
   const cuuint32_t estride[4] = {1, 1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)A, dim, stride, box, estride,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
