@@ -16,10 +16,13 @@
 //   D_d = sum_{k+l=d} sum_r dx_k(r) dw_l(r),
 // where every D_d is a sum of at most 6 x 64 products of magnitude <= 2^14,
 // hence an integer below 2^24: the tensor core's FP32 accumulation of it is
-// exact.  The epilogue combines the D_d exactly in 64-bit integers, rounds
-// each half tile once to FP64 and adds the two halves.  Error: the
-// truncation of X (2^-47 of the segment maximum) and the dropped diagonals
-// d >= S (below 2^-45.7 of max|x| max|w| times the segment length).
+// exact.  The epilogue combines the D_d exactly in 64-bit integers; the
+// per-thread-load kernel rounds each half tile once to FP64 and adds the
+// two halves, the TMA kernel aligns the two halves' integers on the larger
+// scale (the other truncated at its unit, 2^-54 of that segment's scale)
+// and rounds once, with no FP64 instruction.  Error: the truncation of X
+// (2^-47 of the segment maximum) and the dropped diagonals d >= S (below
+// 2^-45.7 of max|x| max|w| times the segment length).
 //
 // Kernel shape: persistent CTAs (one per SM, 512 threads) take tiles from
 // a queue and walk units (W block of up to 32 slots, A block of 128 rows,
@@ -230,6 +233,12 @@ __device__ __forceinline__ void store_digits(const GroupDigits& o, unsigned char
           make_uint4(o.w[q][k][0], o.w[q][k][1], o.w[q][k][2], o.w[q][k][3]);
   }
   if (lane < 8) emax_row[lane] = o.emax;
+}
+
+// Integer value of an integer-valued FP32 number at most 2^22 in magnitude:
+// adding 1.5 2^23 puts it in the low mantissa bits.
+__device__ __forceinline__ int small_float_int(uint32_t f) {
+  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
 }
 
 // Exact value of an integer-valued float below 2^24 in magnitude.
@@ -520,6 +529,11 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// L2 prefetch of bytes (a multiple of 16) at p (16-byte aligned).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
@@ -604,7 +618,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
   __shared__ __align__(8) unsigned long long mbar[2], tbar[2], rbar[2];
   __shared__ int u_ring[2][2];  // per posted unit: W block width (0: end), half
   __shared__ uint32_t tmem_base;
-  __shared__ int s_tile, s_fail, s_ifail;  // converting / issuing side failed
+  __shared__ int s_tile, s_j[2], s_fail, s_ifail;  // claimed tile, its list bounds; failures
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mb[2] = {smem_addr(&mbar[0]), smem_addr(&mbar[1])};
   const uint32_t tb[2] = {smem_addr(&tbar[0]), smem_addr(&tbar[1])};
@@ -685,21 +699,53 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
     const int row = tid >> 2, run = tid & 3;
     const uint32_t r_off = (uint32_t)(row * 256 + run * 64);
     const uint32_t r_swz = (uint32_t)((((row & 1) << 1) | (run >> 1)) << 4);
+    // Thread 0 claims tiles one ahead: the next index is taken from the
+    // queue when the current tile is published, and over the following units
+    // its bounds are read (q_stage 1 -> 2), empty tiles skipped and its first
+    // W block prefetched to L2 (2 -> 3), so a claim seldom waits on memory.
+    int q_t = 0, q_j0 = 0, q_j1 = 0, q_stage = 0;  // 1 index taken, 2 bounds read, 3 resolved
+    auto q_step = [&]() {
+      if (q_stage == 1) {
+        if (q_t < n_tiles) {
+          q_j0 = __ldg(tptr + q_t);
+          q_j1 = __ldg(tptr + q_t + 1);
+          q_stage = 2;
+        } else {
+          q_stage = 3;
+        }
+      } else if (q_stage == 2) {
+        if (q_j1 == q_j0) {
+          q_t = atomicAdd(queue, 1);
+          q_stage = 1;
+        } else {
+          bulk_prefetch_l2(wdig + (size_t)q_j0 * 2 * DIG * 8,
+                           (uint32_t)min(q_j1 - q_j0, NBLK) * 2 * DIG * 8 * 16);
+          q_stage = 3;
+        }
+      }
+    };
     auto claim = [&](Unit& u) -> bool {
       conv_sync();
       if (tid == 0) {
-        int t;
-        do {
-          t = atomicAdd(queue, 1);
-        } while (t < n_tiles && tptr[t + 1] == tptr[t]);
-        s_tile = t;
+        if (q_stage == 0) {
+          q_t = atomicAdd(queue, 1);
+          q_stage = 1;
+        }
+        while (q_stage != 3) q_step();
+        s_tile = q_t;
+        s_j[0] = q_j0;
+        s_j[1] = q_j1;
+        if (q_t < n_tiles) {
+          q_t = atomicAdd(queue, 1);
+          q_stage = 1;
+        }
       }
       conv_sync();
       const int T = s_tile;
       if (T >= n_tiles) return false;
       u.T = T;
-      u.j0 = tptr[T];
-      u.nJ = tptr[T + 1] - u.j0;
+      u.j0 = s_j[0];
+      u.nJ = s_j[1] - u.j0;
       u.jb = 0;
       u.mb = 0;
       u.h = 0;
@@ -780,16 +826,24 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         for (int q = 0; q < 2 * DIG; ++q)
           f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
         tmem_wait_ld();
-        double sum = 0.0;
+        // |D_d| <= (d + 1) 2^20: D_0..D_3 by the 2^22 conversion; the three
+        // 32-bit pairs D_d 256 + D_(d+1) stay below 2^31
+        long long acc[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          long long acc = 0;
-#pragma unroll
-          for (int d = 0; d < DIG; ++d)
-            acc += (long long)float_int(__uint_as_float(f[h * DIG + d])) << (8 * (DIG - 1 - d));
-          sum += scaled_i64(acc, (h ? ea1 : ea0) + (Wexp[h][c] - 1022) - 54);
+          const uint32_t* fh = f + h * DIG;
+          const int t01 = small_float_int(fh[0]) * 256 + small_float_int(fh[1]);
+          const int t23 = small_float_int(fh[2]) * 256 + small_float_int(fh[3]);
+          const int t45 = float_int(__uint_as_float(fh[4])) * 256 + float_int(__uint_as_float(fh[5]));
+          acc[h] = ((long long)t01 << 32) + ((long long)t23 << 16) + (long long)t45;
         }
-        if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = sum;
+        // the two halves on the larger scale (the other truncated at its
+        // unit, 2^-54 of that segment's scale), one rounding
+        const int e0 = ea0 + Wexp[0][c] - 1022 - 54, e1 = ea1 + Wexp[1][c] - 1022 - 54;
+        const bool b0 = e0 >= e1;
+        const int sh = min(b0 ? e0 - e1 : e1 - e0, 63);
+        const long long s2 = (b0 ? acc[0] : acc[1]) + ((b0 ? acc[1] : acc[0]) >> sh);
+        if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64(s2, b0 ? e0 : e1);
       }
     };
     // post unit u (or the end, nj = 0) to the issuing thread: ring entry
@@ -837,6 +891,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
           }
         em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
         em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
+        if (tid == 0) q_step();
         conv_sync();  // both raw buffers consumed
         Unit next = cur;
         bool new_block = false;
@@ -1016,11 +1071,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-// Integer value of an integer-valued FP32 number below 2^22 in magnitude:
-// adding 1.5 2^23 puts it in the low mantissa bits.
-__device__ __forceinline__ int small_float_int(uint32_t f) {
-  return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
-}
 
 constexpr int XE_WARPS = 16;                       // digit and epilogue warps
 constexpr int XE_THREADS = 32 * (XE_WARPS + 1);    // and one MMA-issuing warp
