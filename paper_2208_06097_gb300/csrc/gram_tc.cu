@@ -20,7 +20,7 @@
 // per-thread-load kernel rounds each half tile once to FP64 and adds the
 // two halves, the TMA kernel aligns the two halves' integers on the larger
 // scale (the other truncated at its unit, 2^-54 of that segment's scale)
-// and rounds once, with no FP64 instruction.  Error: the truncation of X
+// and truncates once to FP64, with no FP64 instruction.  Error: the truncation of X
 // (2^-47 of the segment maximum) and the dropped diagonals d >= S (below
 // 2^-45.7 of max|x| max|w| times the segment length).
 //
@@ -838,12 +838,12 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
           acc[h] = ((long long)t01 << 32) + ((long long)t23 << 16) + (long long)t45;
         }
         // the two halves on the larger scale (the other truncated at its
-        // unit, 2^-54 of that segment's scale), one rounding
+        // unit, 2^-54 of that segment's scale), one truncation
         const int e0 = ea0 + Wexp[0][c] - 1022 - 54, e1 = ea1 + Wexp[1][c] - 1022 - 54;
         const bool b0 = e0 >= e1;
         const int sh = min(b0 ? e0 - e1 : e1 - e0, 63);
         const long long s2 = (b0 ? acc[0] : acc[1]) + ((b0 ? acc[1] : acc[0]) >> sh);
-        if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64(s2, b0 ? e0 : e1);
+        if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64_rz(s2, b0 ? e0 : e1);
       }
     };
     // post unit u (or the end, nj = 0) to the issuing thread: ring entry
@@ -1174,6 +1174,8 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
           for (int i = 0; i < XKS; ++i) {
             const int jl = q * XKS + i;
             hreg[i] = (v < m && jl < nJ) ? H[(long long)lj[jl] * hj + (long long)v * hv] : 0.0;
+            if (negate)  // the sign of y folded into H's digits (sign bit, exact)
+              hreg[i] = __longlong_as_double(__double_as_longlong(hreg[i]) ^ (long long)0x8000000000000000ULL);
           }
 #pragma unroll
           for (int i = 0; i < XKS; ++i) {
@@ -1274,7 +1276,7 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
               const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
               const long long acc =
                   ((long long)t01 << 32) + ((long long)t23 << 16) + (long long)t45;
-              vals[u] = scaled_i64(negate ? -acc : acc, evx[c * XN + vv0 + u] - 1022 - 54);
+              vals[u] = scaled_i64_rz(acc, evx[c * XN + vv0 + u] - 1022 - 54);
             }
           } else {
 #pragma unroll

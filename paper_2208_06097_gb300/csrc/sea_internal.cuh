@@ -150,6 +150,30 @@ __device__ __forceinline__ double scaled_i64(long long v, int e2) {
       (long long)(sgn | ((unsigned long long)ex << 52) | (mnt & 0xFFFFFFFFFFFFFULL)));
 }
 
+// v 2^e2 truncated toward zero to FP64 (error below one unit in the last
+// place); 0 if below the normal range.  The normalisation works on the two
+// 32-bit halves of |v|; integer operations only.
+__device__ __forceinline__ double scaled_i64_rz(long long v, int e2) {
+  const unsigned long long u = (unsigned long long)v;
+  const unsigned sg = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned long long a = v < 0 ? 0ULL - u : u;
+  unsigned hi = (unsigned)(a >> 32), lo = (unsigned)a;
+  int top = 63;  // bit index of hi's bit 31 in |v|
+  if (hi == 0u) {
+    hi = lo;
+    lo = 0u;
+    top = 31;
+  }
+  if (hi == 0u) return 0.0;
+  const int lz = __clz(hi);
+  const int ex = top - lz + e2 + 1023;
+  if (ex <= 0) return 0.0;
+  const unsigned nh = __funnelshift_l(lo, hi, lz), nl = lo << lz;  // leading 1 at bit 63
+  const unsigned bh = sg | ((unsigned)ex << 20) | ((nh >> 11) & 0xFFFFFu);
+  const unsigned bl = __funnelshift_r(nl, nh, 11);
+  return __hiloint2double((int)bh, (int)bl);
+}
+
 // ---------------------------------------------------------------------------
 // Double-float arithmetic (a value is hi + lo, |lo| <= ulp(hi) / 2): Knuth's
 // two-sum and the fused-multiply-add two-product (Dekker's method), about 48
