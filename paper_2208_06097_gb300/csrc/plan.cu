@@ -156,6 +156,71 @@ __global__ void __launch_bounds__(128)
   for (int x = threadIdx.x; x < nx; x += blockDim.x) C[((size_t)i * nz + z) * nx + x] = col[x];
 }
 
+// The same sums without a shared-memory tile, for rows of at most 32 KX
+// points: warp w takes the rows y = w, w + 4, ... (two at a time), lane l
+// the points x = l + 32 k; a row's sum is a warp butterfly, a column's
+// partial sums stay in the lane's registers until one exchange between the
+// four warps at the end of the plane.  All sums are exact, so the order is
+// free.
+template <int KX>
+__global__ void __launch_bounds__(128)
+    k_row_col_sums_reg(const double* __restrict__ phi, int nx, int ny, int nz,
+                       ulonglong2* __restrict__ R, ulonglong2* __restrict__ C) {
+  __shared__ ulonglong2 cpart[4][32 * KX];  // per warp: column partial sums
+  const int z = blockIdx.x, i = blockIdx.y;
+  const double* plane = phi + ((size_t)i * nz + z) * (size_t)ny * nx;
+  ulonglong2* Rp = R + ((size_t)i * nz + z) * ny;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long clo[KX], chi[KX];
+#pragma unroll
+  for (int k = 0; k < KX; ++k) clo[k] = chi[k] = 0;
+  for (int y0 = w; y0 < ny; y0 += 8) {
+    double v[2][KX];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int y = y0 + 4 * t;
+      const double* row = plane + (size_t)y * nx;
+#pragma unroll
+      for (int k = 0; k < KX; ++k) {
+        const int x = lane + 32 * k;
+        v[t][k] = (y < ny && x < nx) ? row[x] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      unsigned long long rlo = 0, rhi = 0;
+#pragma unroll
+      for (int k = 0; k < KX; ++k) {
+        unsigned long long lo, hi;
+        sq_fixed(v[t][k], lo, hi);
+        clo[k] += lo;
+        chi[k] += hi;
+        rlo += lo;
+        rhi += hi;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        rlo += __shfl_xor_sync(0xffffffffu, rlo, o);
+        rhi += __shfl_xor_sync(0xffffffffu, rhi, o);
+      }
+      const int y = y0 + 4 * t;
+      if (lane == 0 && y < ny) Rp[y] = make_ulonglong2(rlo, rhi);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < KX; ++k) cpart[w][32 * k + lane] = make_ulonglong2(clo[k], chi[k]);
+  __syncthreads();
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+    ulonglong2 c = cpart[0][x];
+#pragma unroll
+    for (int u = 1; u < 4; ++u) {
+      c.x += cpart[u][x].x;
+      c.y += cpart[u][x].y;
+    }
+    C[((size_t)i * nz + z) * nx + x] = c;
+  }
+}
+
 // 128-bit unsigned (hi, lo) += limb pair (a + b 2^48).
 __device__ __forceinline__ void add_limbs(unsigned long long& hi, unsigned long long& lo,
                                           ulonglong2 v) {
@@ -496,12 +561,27 @@ __global__ void k_lpt_order(const int* __restrict__ sz, const int* __restrict__ 
 cudaError_t launch_plan_boxes(sea_ctx* c) {
   const int n = c->n_orb, nx = c->N[0], ny = c->N[1], nz = c->N[2];
   const int Nmax = max(nx, max(ny, nz));
-  const size_t rc_smem = rc_smem_bytes(nx);
-  cudaError_t e = cudaFuncSetAttribute(k_row_col_sums, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)rc_smem);
-  if (e != cudaSuccess) return e;
-  k_row_col_sums<<<dim3(nz, n), 128, rc_smem, c->stream>>>(
-      (const double*)c->phi.p, nx, ny, nz, (ulonglong2*)c->rowsum.p, (ulonglong2*)c->colsum.p);
+  const dim3 rc_grid(nz, n);
+  const double* phi = (const double*)c->phi.p;
+  ulonglong2* Rs = (ulonglong2*)c->rowsum.p;
+  ulonglong2* Cs = (ulonglong2*)c->colsum.p;
+  if (nx <= 64)
+    k_row_col_sums_reg<2><<<rc_grid, 128, 0, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
+  else if (nx <= 96)
+    k_row_col_sums_reg<3><<<rc_grid, 128, 0, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
+  else if (nx <= 128)
+    k_row_col_sums_reg<4><<<rc_grid, 128, 0, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
+  else if (nx <= 192)
+    k_row_col_sums_reg<6><<<rc_grid, 128, 0, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
+  else if (nx <= 256)
+    k_row_col_sums_reg<8><<<rc_grid, 128, 0, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
+  else {
+    const size_t rc_smem = rc_smem_bytes(nx);
+    cudaError_t e = cudaFuncSetAttribute(k_row_col_sums, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rc_smem);
+    if (e != cudaSuccess) return e;
+    k_row_col_sums<<<rc_grid, 128, rc_smem, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
+  }
   const int tot = n * 3 * Nmax;
   k_marginals<<<(tot + 255) / 256, 256, 0, c->stream>>>(
       (const ulonglong2*)c->rowsum.p, (const ulonglong2*)c->colsum.p, n, nx, ny, nz, Nmax, c->dV,
