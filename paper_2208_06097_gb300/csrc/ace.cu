@@ -23,14 +23,27 @@ __device__ __forceinline__ bool cyc_meets(int s, int L, int a, int b, int n) {
 
 // Covered range [lo, hi) of the tile interval [a, b) by the cyclic window
 // [s, s+L) on a ring of n points (lo >= hi: none).
+// The window is [s, s + L) and, if it passes n, [0, s + L - n) (s in
+// [0, n), L < n); the covered range spans the parts meeting [a, b).
 __device__ __forceinline__ void cyc_cover(int s, int L, int a, int b, int n, int* lo, int* hi) {
-  *lo = b;
-  *hi = a;
-  for (int x = a; x < b; ++x)
-    if (L >= n || wrapi(x - s, n) < L) {
-      *lo = min(*lo, x);
-      *hi = max(*hi, x + 1);
-    }
+  if (L >= n) {
+    *lo = a;
+    *hi = b;
+    return;
+  }
+  int l = b, h = a;
+  const int l1 = max(a, s), h1 = min(b, s + L);
+  if (l1 < h1) {
+    l = l1;
+    h = h1;
+  }
+  const int h2 = min(b, s + L - n);  // the wrapped part starts at 0 <= a
+  if (a < h2) {
+    l = a;
+    h = max(h, h2);
+  }
+  *lo = l;
+  *hi = h;
 }
 
 // inc[o][T] = 1 if any entry window of orbital o touches tile T, and
@@ -356,8 +369,18 @@ __global__ void k_gram_reduce(const double* __restrict__ partial, int m, int n_o
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)m * n_orb) return;
   const int a = (int)(t % m), o = (int)(t / m);
+  // in slot order; the loads of eight slots are issued before their adds
   double s = 0.0;
-  for (int k = optr[o]; k < optr[o + 1]; ++k) s += partial[(size_t)oslot[k] * m + a];
+  int k = optr[o];
+  const int k1 = optr[o + 1];
+  for (; k + 8 <= k1; k += 8) {
+    double p[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[u] = partial[(size_t)oslot[k + u] * m + a];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += p[u];
+  }
+  for (; k < k1; ++k) s += partial[(size_t)oslot[k] * m + a];
   out[(size_t)a * sa + (size_t)o * so] = scale * s;
 }
 
