@@ -226,10 +226,6 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
 __device__ __forceinline__ float i2f_exact(int v) {
   return __int_as_float(0x4B400000 + v) - 12582912.0f;
 }
-__device__ __forceinline__ DF df_from_double(double x) {
-  const float hi = (float)x;
-  return DF{hi, (float)(x - (double)hi)};
-}
 // hi + lo as FP64 with integer operations only: both terms as fixed-point
 // integers on the larger one's exponent (bits more than 2^-62 below it
 // dropped), one rounding to nearest.  FP32 subnormals count as zero.
@@ -265,6 +261,14 @@ __device__ __forceinline__ float2 split64(double v) {
   const float l = ((float)(unsigned)(m & 0x1FFFFFFFULL) * 5.421010862427522e-20f) *
                   __uint_as_float((unsigned)(e - 884) << 23);
   return make_float2(hi, __uint_as_float(__float_as_uint(l) | sign));
+}
+
+// An FP64 value as a double-float pair, by split64 (no FP64 instruction:
+// on this part a warp's FP64 conversion or add holds the FP64 pipe for
+// about 64 cycles).
+__device__ __forceinline__ DF df_from_double(double x) {
+  const float2 s = split64(x);
+  return DF{s.x, s.y};
 }
 
 // me_potential in double-float: the same recurrences and summation order,
