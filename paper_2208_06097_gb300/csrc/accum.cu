@@ -13,8 +13,10 @@
 //               shared memory from zero, each entry of the orbital
 //               subtracted in pair order (a fixed order: no floating-point
 //               atomics), then stored once to the output and, when given,
-//               to a second output (the caller's copy).  Planes too large
-//               for shared memory take the same steps on a global slab.
+//               to a second output (the caller's copy; the context's copy
+//               is then stored only on the tiles the orbital's windows
+//               touch).  Planes too large for shared memory take the same
+//               steps on a global slab, with full stores.
 #include <algorithm>
 
 #include "sea_internal.cuh"
@@ -270,18 +272,32 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Cyclic window [s, s + L) (s in [0, n)) meets [a, b) (0 <= a < b <= n).
+__device__ __forceinline__ bool cyc_hits(int s, int L, int a, int b, int n) {
+  if (L >= n) return true;
+  if (max(a, s) < min(b, s + L)) return true;
+  return a < min(b, s + L - n);  // the wrapped part [0, s + L - n)
+}
+
 // Shared-memory form: CTA per (orbital, z-plane), the plane (nx*ny
 // doubles) in dynamic shared memory.  A thread walks the window rows of an
 // entry with its (tx, ty) advanced by the CTA stride, without divisions.
+// With a second output (the caller's copy, written in full), the context's
+// copy is stored only on the tiles (TX x TY x TZ) that a window of the
+// orbital touches: the tiles of the orbital's W lists, the only places the
+// ACE kernels read it (tile mask after the plane, in shared memory).
+#define SEA_ACC_MAXE 64
 __global__ void __launch_bounds__(256)
     k_accumulate(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
                  const Entry* __restrict__ ent, const long long* __restrict__ coff,
                  const double* __restrict__ cbuf, double* __restrict__ out,
                  double* __restrict__ out2) {
   extern __shared__ double sp[];
+  __shared__ int es[SEA_ACC_MAXE][5];  // x start, x length, y start, y length, meets the z tile
   const int o = o_begin + blockIdx.x;
   const int z = blockIdx.y;
   const int plane = nx * ny;
+  unsigned char* tmask = reinterpret_cast<unsigned char*>(sp + plane);
   for (int g = threadIdx.x; g < plane; g += blockDim.x) sp[g] = 0.0;
   const int e0 = eptr[o], e1 = eptr[o + 1];
   for (int k = e0; k < e1; ++k) {
@@ -309,11 +325,45 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
+  const int ntx = (nx + TX - 1) / TX;
+  const bool all = out2 == nullptr || e1 - e0 > SEA_ACC_MAXE;  // uniform
+  if (!all) {
+    const int t = threadIdx.x;
+    if (t < e1 - e0) {
+      const Entry e = ent[e0 + t];
+      const int zs = (z / TZ) * TZ;
+      es[t][0] = wrapi(e.ws[0], nx);
+      es[t][1] = e.wl[0];
+      es[t][2] = wrapi(e.ws[1], ny);
+      es[t][3] = e.wl[1];
+      es[t][4] = cyc_hits(wrapi(e.ws[2], nz), e.wl[2], zs, min(nz, zs + TZ), nz);
+    }
+    __syncthreads();
+    const int nty = (ny + TY - 1) / TY;
+    for (int q = threadIdx.x; q < ntx * nty; q += blockDim.x) {
+      const int qy = q / ntx, qx = q - qy * ntx;
+      const int ax = qx * TX, bx = min(nx, ax + TX), ay = qy * TY, by = min(ny, ay + TY);
+      bool hit = false;
+      for (int k = 0; k < e1 - e0; ++k)
+        hit = hit || (es[k][4] && cyc_hits(es[k][0], es[k][1], ax, bx, nx) &&
+                      cyc_hits(es[k][2], es[k][3], ay, by, ny));
+      tmask[q] = hit ? 1 : 0;
+    }
+  }
   __syncthreads();
   const size_t base = ((size_t)o * nz + z) * plane;
+  const int dy = blockDim.x / nx, dx = blockDim.x - dy * nx;  // (x, y) of g, without divisions
+  int y = threadIdx.x / nx, x = threadIdx.x - y * nx;
   for (int g = threadIdx.x; g < plane; g += blockDim.x) {
-    out[base + g] = sp[g];
-    if (out2) out2[base + g] = sp[g];
+    const double v = sp[g];
+    if (out2) out2[base + g] = v;
+    if (all || tmask[(y / TY) * ntx + x / TX]) out[base + g] = v;
+    x += dx;
+    y += dy;
+    if (x >= nx) {
+      x -= nx;
+      ++y;
+    }
   }
 }
 
@@ -408,7 +458,9 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
     }
   }
   if (o_end > o_begin) {
-    const size_t smem = (size_t)c->N[0] * c->N[1] * sizeof(double);
+    // the plane, then one tile-mask byte per (x tile, y tile)
+    const size_t smem = (size_t)c->N[0] * c->N[1] * sizeof(double) +
+                        (size_t)((c->N[0] + TX - 1) / TX) * ((c->N[1] + TY - 1) / TY);
     if (smem <= SEA_ACC_SMEM_MAX) {
       cudaError_t e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
