@@ -287,7 +287,8 @@ __device__ __forceinline__ bool cyc_hits(int s, int L, int a, int b, int n) {
 // orbital touches: the tiles of the orbital's W lists, the only places the
 // ACE kernels read it (tile mask after the plane, in shared memory).
 #define SEA_ACC_MAXE 64
-__global__ void __launch_bounds__(256)
+#define SEA_ACC_THREADS 512
+__global__ void __launch_bounds__(SEA_ACC_THREADS)
     k_accumulate(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
                  const Entry* __restrict__ ent, const long long* __restrict__ coff,
                  const double* __restrict__ cbuf, double* __restrict__ out,
@@ -465,7 +466,7 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
       cudaError_t e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
       if (e != cudaSuccess) return e;
-      k_accumulate<<<dim3(o_end - o_begin, c->N[2]), 256, smem, c->stream>>>(
+      k_accumulate<<<dim3(o_end - o_begin, c->N[2]), SEA_ACC_THREADS, smem, c->stream>>>(
           c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p, (const Entry*)c->ewin.p,
           (const long long*)c->coff.p, (const double*)c->cbuf.p, out, out2);
     } else {
