@@ -119,9 +119,9 @@ def job_value(steps, ws, t_ms_max):
 # ncu capture of the benchmark workload with the current kernels; see
 # profiles/dram_traffic_h2o64_96.md).  None: not captured.
 DRAM_BYTES_PER_LAUNCH = {
-    "k_cg_mixed": 26.9e6,
+    "k_cg_mixed": 26.8e6,
     "k_gram_tc": 2.025e9,
-    "k_expand_tc": 1.986e9,
+    "k_expand_tc": 1.984e9,
 }
 
 
