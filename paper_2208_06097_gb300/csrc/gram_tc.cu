@@ -24,22 +24,27 @@
 // (2^-47 of the segment maximum) and the dropped diagonals d >= S (below
 // 2^-45.7 of max|x| max|w| times the segment length).
 //
-// Kernel shape: persistent CTAs (one per SM, 512 threads) take tiles from
-// a queue and walk units (W block of up to 32 slots, A block of 128 rows,
-// half tile).  Per unit the A digits go to shared memory in the tensor
-// core's K-major layout without swizzle (8 x 16-byte core matrices; row
-// groups 128 B apart, x-runs of 8 points one row-group stack apart).  W's
-// digit planes of the block are stacked along N (plane l at rows l P, P =
-// 16 or 32 the padded block width) and the accumulator of diagonal d sits
-// at tensor-memory columns d P, so one MMA of A plane k against the stacked
-// W planes 0..5-k (N = (6 - k) P) adds every product of plane k to the
+// Kernel shape: persistent CTAs (one per SM) take tiles from a queue and
+// walk units (W block of up to 32 slots, A block of 128 rows, half tile).
+// Per unit the A digits go to shared memory in the tensor core's K-major
+// layout without swizzle (8 x 16-byte core matrices; row groups 128 B
+// apart, x-runs of 8 points one row-group stack apart).  W's digit planes
+// of the block are stacked along N (plane l at rows l P, P = 16 or 32 the
+// padded block width) and the accumulator of diagonal d sits at
+// tensor-memory columns d P, so one MMA of A plane k against the stacked W
+// planes 0..5-k (N = (6 - k) P) adds every product of plane k to the
 // diagonals k..5 at once: 24 tcgen05.mma instructions (M = 128, K = 16) per
-// unit, issued by one thread.  After the second half all warps read the
-// accumulators back with tcgen05.ld for the epilogue.  While a unit's MMAs run, the warps load the next unit's A rows
-// and form their digits in registers (and a new W block's digits in the
-// second W buffer).  Every wait on the MMA completion barrier is bounded:
-// on expiry the kernel sets SEA_FLAG_WAIT, waits once more (bounded) for
-// its MMAs, frees its tensor memory and ends.
+// unit.  After the second half tile the converting warps read the
+// accumulators back with tcgen05.ld for the epilogue.  Two versions:
+//   k_gram_tc_ldg  512 threads load the A rows themselves and form their
+//                  digits in registers while the previous unit's MMAs run
+//                  (issued by thread 0); used when the rows are not
+//                  16-byte strided (odd nx) or A is unaligned;
+//   k_gram_tc      A rows by TMA per K half, 16 converting warps and one
+//                  MMA-issuing warp (described above the kernel).
+// Every wait on a completion barrier is bounded: on expiry the kernel sets
+// SEA_FLAG_WAIT, waits once more (bounded) for work in flight, frees its
+// tensor memory and ends.
 #include <cuda.h>
 
 #include "sea_internal.cuh"
