@@ -207,13 +207,36 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   const float cxf = 0.5f * i2f_exact(P.ext[0] - 1), cyf = 0.5f * i2f_exact(P.ext[1] - 1),
               czf = 0.5f * i2f_exact(P.ext[2] - 1);
   const int t1 = min(nw, t0 + SEA_CHUNK);
-  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-    const int tx = t % e.wl[0], ty = (t / e.wl[0]) % e.wl[1], tz = t / (e.wl[0] * e.wl[1]);
+  // window coordinates of t, advanced by the CTA stride without divisions;
+  // grid coordinates from the window start wrapped once
+  const int wx = e.wl[0], wy = e.wl[1], wxy = wx * wy;
+  const int S = blockDim.x;
+  const int dz = S / wxy, dy = (S - dz * wxy) / wx, dx = S - dz * wxy - dy * wx;
+  const int gx0 = wrapi(e.ws[0], nx), gy0 = wrapi(e.ws[1], ny), gz0 = wrapi(e.ws[2], nz);
+  int tz = (t0 + (int)threadIdx.x) / wxy;
+  int ty = (t0 + (int)threadIdx.x - tz * wxy) / wx;
+  int tx = t0 + (int)threadIdx.x - tz * wxy - ty * wx;
+  for (int t = t0 + threadIdx.x; t < t1; t += S) {
     const int ux = e.ws[0] + tx, uy = e.ws[1] + ty, uz = e.ws[2] + tz;
     const int lx = ux - P.lo[0], ly = uy - P.lo[1], lz = uz - P.lo[2];
     const bool inside =
         lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2];
-    const size_t g = ((size_t)wrapi(uz, nz) * ny + wrapi(uy, ny)) * nx + wrapi(ux, nx);
+    int gx = gx0 + tx, gy = gy0 + ty, gz = gz0 + tz;  // window lengths are at most n
+    gx -= gx >= nx ? nx : 0;
+    gy -= gy >= ny ? ny : 0;
+    gz -= gz >= nz ? nz : 0;
+    const size_t g = ((size_t)gz * ny + gy) * nx + gx;
+    tx += dx;
+    ty += dy;
+    tz += dz;
+    if (tx >= wx) {
+      tx -= wx;
+      ++ty;
+    }
+    if (ty >= wy) {
+      ty -= wy;
+      ++tz;
+    }
     if (DFM) {  // c = v phi in double-float, no FP64 instruction
       DF val;
       if (inside) {

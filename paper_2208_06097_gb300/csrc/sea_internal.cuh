@@ -217,6 +217,18 @@ __device__ __forceinline__ DF df_fma(DF a, DF b, DF c) {
   const float e = (p - (s - v)) + (c.hi - v);
   return df_fast_two_sum(s, (fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, pe)) + c.lo) + e);
 }
+// a b + c d with one normalisation: the two products' high parts by an
+// exact two-sum, their errors and cross terms added to its error (19 FP32
+// operations instead of 22).  For a b - c d pass df_neg(c).
+__device__ __forceinline__ DF df_dot2(DF a, DF b, DF c, DF d) {
+  const float p = a.hi * b.hi, q = c.hi * d.hi;
+  const float pe = fmaf(a.hi, b.hi, -p), qe = fmaf(c.hi, d.hi, -q);
+  const float s = p + q;
+  const float v = s - p;
+  const float e = (p - (s - v)) + (q - v);
+  const float lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, pe)) + fmaf(c.hi, d.lo, fmaf(c.lo, d.hi, qe));
+  return df_fast_two_sum(s, lo + e);
+}
 // 1 / a: FP32 reciprocal, one Newton step in double-float
 __device__ __forceinline__ DF df_rcp(DF a) {
   const float y = 1.0f / a.hi;
@@ -285,7 +297,7 @@ __device__ __forceinline__ DF df_from_double(double x) {
 // me_potential in double-float: the same recurrences and summation order,
 // Q as double-float coefficients.
 __device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF y, DF z) {
-  const DF r2 = df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z));
+  const DF r2 = df_fma(z, z, df_dot2(x, x, y, y));
   const DF ir2 = df_rcp(r2);
   const DF ux = df_mul(x, ir2), uy = df_mul(y, ir2), uz = df_mul(z, ir2);
   DF Dm[2 * SEA_LMAX + 1], Dc[2 * SEA_LMAX + 1], Dn[2 * SEA_LMAX + 1];  // l-1, l, l+1
@@ -301,13 +313,13 @@ __device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF
   v = df_fma(Q[lmi(1, 1)], ux, v);
 #pragma unroll
   for (int l = 1; l < SEA_LMAX; ++l) {
-    Dn[SEA_LMAX + l + 1] = df_fma(ux, Dc[SEA_LMAX + l], df_neg(df_mul(uy, Dc[SEA_LMAX - l])));
-    Dn[SEA_LMAX - l - 1] = df_fma(uy, Dc[SEA_LMAX + l], df_mul(ux, Dc[SEA_LMAX - l]));
+    Dn[SEA_LMAX + l + 1] = df_dot2(ux, Dc[SEA_LMAX + l], df_neg(uy), Dc[SEA_LMAX - l]);
+    Dn[SEA_LMAX - l - 1] = df_dot2(uy, Dc[SEA_LMAX + l], ux, Dc[SEA_LMAX - l]);
 #pragma unroll
     for (int m = -l; m <= l; ++m) {
       if (m >= -(l - 1) && m <= l - 1) {
         const DF g = df_mul(DF{c_harm.gam_hi[l][m + SEA_LMAX], c_harm.gam_lo[l][m + SEA_LMAX]}, ir2);
-        Dn[SEA_LMAX + m] = df_fma(uz, Dc[SEA_LMAX + m], df_neg(df_mul(g, Dm[SEA_LMAX + m])));
+        Dn[SEA_LMAX + m] = df_dot2(uz, Dc[SEA_LMAX + m], df_neg(g), Dm[SEA_LMAX + m]);
       } else {
         Dn[SEA_LMAX + m] = df_mul(uz, Dc[SEA_LMAX + m]);
       }
@@ -326,7 +338,7 @@ __device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF
 // harm_accumulate in double-float: acc[q] += w D_q(x, y, z), the same
 // recurrences in the same order.
 __device__ __forceinline__ void harm_accumulate_df(DF w, DF x, DF y, DF z, DF* acc) {
-  const DF r2 = df_add(df_add(df_mul(x, x), df_mul(y, y)), df_mul(z, z));
+  const DF r2 = df_fma(z, z, df_dot2(x, x, y, y));
   DF Dm[2 * SEA_LMAX + 1], Dc[2 * SEA_LMAX + 1], Dn[2 * SEA_LMAX + 1];  // l-1, l, l+1
 #pragma unroll
   for (int k = 0; k < 2 * SEA_LMAX + 1; ++k) Dm[k] = Dc[k] = Dn[k] = DF{0.f, 0.f};
@@ -340,13 +352,13 @@ __device__ __forceinline__ void harm_accumulate_df(DF w, DF x, DF y, DF z, DF* a
   acc[lmi(1, 1)] = df_fma(w, x, acc[lmi(1, 1)]);
 #pragma unroll
   for (int l = 1; l < SEA_LMAX; ++l) {
-    Dn[SEA_LMAX + l + 1] = df_fma(x, Dc[SEA_LMAX + l], df_neg(df_mul(y, Dc[SEA_LMAX - l])));
-    Dn[SEA_LMAX - l - 1] = df_fma(y, Dc[SEA_LMAX + l], df_mul(x, Dc[SEA_LMAX - l]));
+    Dn[SEA_LMAX + l + 1] = df_dot2(x, Dc[SEA_LMAX + l], df_neg(y), Dc[SEA_LMAX - l]);
+    Dn[SEA_LMAX - l - 1] = df_dot2(y, Dc[SEA_LMAX + l], x, Dc[SEA_LMAX - l]);
 #pragma unroll
     for (int m = -l; m <= l; ++m) {
       if (m >= -(l - 1) && m <= l - 1) {
         const DF g = df_mul(DF{c_harm.gam_hi[l][m + SEA_LMAX], c_harm.gam_lo[l][m + SEA_LMAX]}, r2);
-        Dn[SEA_LMAX + m] = df_fma(z, Dc[SEA_LMAX + m], df_neg(df_mul(g, Dm[SEA_LMAX + m])));
+        Dn[SEA_LMAX + m] = df_dot2(z, Dc[SEA_LMAX + m], df_neg(g), Dm[SEA_LMAX + m]);
       } else {
         Dn[SEA_LMAX + m] = df_mul(z, Dc[SEA_LMAX + m]);
       }
