@@ -1,14 +1,14 @@
 // noalloc.cu -- sea_poisson_batch_noalloc: the batched box Poisson solver
 // for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph
-// that is being captured or replayed, plugins whose host framework owns all
-// device memory through its own pool, and processes that must not grow
-// their footprint after start-up.  For them this entry point runs the same
-// CG kernel as sea_poisson_batch, but its scratch (CG vectors r, p, q, the
-// box records, offsets, order, iteration counts, status word and work-queue
-// counter) lives in one file-scope __device__ array of fixed size instead of
-// memory allocated per call.
+// Some callers cannot call cudaMalloc: plugins whose host framework owns
+// all device memory through its own pool (a call to cudaMalloc behind its
+// back breaks its accounting or fails outright), and processes whose device
+// footprint is fixed at start-up and must not grow afterwards.  For them
+// this entry point runs the same CG kernel as sea_poisson_batch, but its
+// scratch (CG vectors r, p, q, the box records, offsets, order, iteration
+// counts, status word and work-queue counter) lives in one file-scope
+// __device__ array of fixed size instead of memory allocated per call.
 //
 // Costs and limits: every GPU that loads this library holds the array
 // (about 25 MB) until the process exits.  At most SEA_NOALLOC_MAX_BOXES
@@ -20,9 +20,15 @@
 // contents, so every value that must start at zero (status word, queue
 // counter) is cleared by each call.
 //
+// The call is synchronous: it copies the box extents in and the iteration
+// counts and status out through pageable host memory and waits for the
+// stream.  It must therefore not be made while its stream is being captured
+// into a CUDA graph; a capturing stream is detected first and the call
+// returns SEA_ERR_ARG before it queues anything, so the caller's capture
+// stays valid.
+//
 // The array's device address is looked up once per device, on the first
-// call made with that device current (cudaGetSymbolAddress); make that
-// first call before any stream capture begins.
+// call made with that device current (cudaGetSymbolAddress).
 #include <mutex>
 
 #include "sea_internal.cuh"
@@ -44,7 +50,7 @@ constexpr size_t kOffOrder = kOffVoff + (size_t)SEA_NOALLOC_MAX_BOXES * sizeof(l
 constexpr size_t kOffIters = kOffOrder + (size_t)SEA_NOALLOC_MAX_BOXES * sizeof(int);
 constexpr size_t kOffExt = kOffIters + (size_t)SEA_NOALLOC_MAX_BOXES * sizeof(int);
 constexpr size_t kOffMisc = kOffExt + (size_t)SEA_NOALLOC_MAX_BOXES * 3 * sizeof(int);
-constexpr size_t kMiscBytes = 256;  // status word, queue counter, total unknowns
+constexpr size_t kMiscBytes = 256;  // status word, queue counter
 constexpr size_t kScratchBytes = kOffMisc + kMiscBytes;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -52,11 +58,10 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_ptr[SEA_NOALLOC_MAX_DEVICES] = {};
 
-// Box records from the extents: sizes, exclusive-scan offsets, total.
-// One CTA; each thread scans a contiguous chunk.
+// Box records from the extents: sizes and exclusive-scan offsets.  One
+// CTA; each thread scans a contiguous chunk.
 __global__ void k_noalloc_records(const int* __restrict__ ext, int nbox,
-                                  PairInfo* __restrict__ boxes, long long* __restrict__ voff,
-                                  long long* __restrict__ total) {
+                                  PairInfo* __restrict__ boxes, long long* __restrict__ voff) {
   __shared__ long long part[1024];
   const int T = blockDim.x, chunk = (nbox + T - 1) / T;
   const int b = chunk * threadIdx.x, e = min(nbox, b + chunk);
@@ -82,7 +87,6 @@ __global__ void k_noalloc_records(const int* __restrict__ ext, int nbox,
       part[t] = acc;
       acc += v;
     }
-    *total = acc;
   }
   __syncthreads();
   long long pos = part[threadIdx.x];
@@ -92,7 +96,11 @@ __global__ void k_noalloc_records(const int* __restrict__ ext, int nbox,
   }
 }
 
-// Longest boxes first: rank by (size desc, index asc).
+// Longest boxes first: rank by (size desc, index asc).  This is the order
+// the std::stable_sort of sea_poisson_batch (api.cu) produces; the two must
+// stay identical, since the persistent CG takes boxes in this order and the
+// solutions and iteration counts of the two entry points are compared bit
+// for bit.
 __global__ void k_noalloc_order(const PairInfo* __restrict__ boxes, int nbox,
                                 int* __restrict__ order) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,6 +155,11 @@ extern "C" sea_status sea_poisson_batch_noalloc(const double h[3], int n_box, co
   if (total > SEA_NOALLOC_MAX_UNKNOWNS) return SEA_ERR_LIMIT;
   if (n_box == 0) return SEA_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // a stream under capture cannot take the synchronous copies and the wait
+  // below: refuse before anything is queued on it
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SEA_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return SEA_ERR_ARG;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return SEA_ERR_CUDA;
   unsigned char* base = nullptr;
@@ -161,13 +174,12 @@ extern "C" sea_status sea_poisson_batch_noalloc(const double h[3], int n_box, co
   int* dext = (int*)(base + kOffExt);
   unsigned* status = (unsigned*)(base + kOffMisc);
   int* queue = (int*)(base + kOffMisc + 16);
-  long long* dtotal = (long long*)(base + kOffMisc + 32);
 
   cudaError_t e = cudaMemcpyAsync(dext, ext, (size_t)n_box * 3 * sizeof(int),
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
   if (e == cudaSuccess) {
-    k_noalloc_records<<<1, 1024, 0, st>>>(dext, n_box, boxes, voff, dtotal);
+    k_noalloc_records<<<1, 1024, 0, st>>>(dext, n_box, boxes, voff);
     k_noalloc_order<<<(n_box + 255) / 256, 256, 0, st>>>(boxes, n_box, order);
     e = cudaGetLastError();
   }

@@ -1,8 +1,12 @@
 """sea_poisson_batch_noalloc: the box Poisson solver for callers that
-cannot allocate device memory (graph capture, host frameworks that own all
-device memory, fixed footprints).  It must give the same solutions as the
-allocating sea_poisson_batch, on two calls in a row (the shared scratch
-keeps the previous call's contents, which must not leak into the next).
+cannot allocate device memory (host frameworks that own all device memory
+through their own pool, processes with a device footprint fixed at
+start-up).  It must give the same solutions as the allocating
+sea_poisson_batch, on two calls in a row (the shared scratch keeps the
+previous call's contents, which must not leak into the next), also with
+the scratch filled to its capacity; and a caller that is capturing a CUDA
+graph gets SEA_ERR_ARG with its capture left intact (the call is
+synchronous, so it cannot be captured).
 
 Collected last on purpose, so that a run stopping at the first failure has
 already run every other test; it also passes alone in a fresh process."""
@@ -48,3 +52,42 @@ def test_rejects_sizes_beyond_capacity():
     with pytest.raises(sea.SeaError) as e:
         sea.poisson_batch(H, [(1, 1, 1)] * 4097, rhs, rhs, noalloc=True)
     assert e.value.code == 9
+
+
+@pytest.mark.parametrize("exts", [[(16, 64, 64)] * 16, [(2, 2, 2)] * 4096],
+                         ids=["max_unknowns", "max_boxes"])
+def test_exactly_at_capacity(exts):
+    # 1,048,576 unknowns in 16 boxes, and exactly 4096 boxes: the vectors
+    # and the box records fill their regions of the fixed layout
+    for seed in (31, 32):
+        xa, ita, rca = _solve(exts, seed, noalloc=False, tol=1e-8)
+        xn, itn, rcn = _solve(exts, seed, noalloc=True, tol=1e-8)
+        assert rca == 0 and rcn == 0
+        assert np.all(np.isfinite(xn))
+        assert np.abs(xn - xa).max() <= 1e-11 * max(1.0, np.abs(xa).max())
+        np.testing.assert_array_equal(itn, ita)
+
+
+def test_refused_under_stream_capture():
+    from paper_2208_06097_gb300 import sea
+    exts = [(5, 6, 7)]
+    _solve(exts, 3, noalloc=True)  # the device's first call: address look-up
+    rhs = torch.ones(5 * 6 * 7, dtype=torch.float64, device="cuda")
+    x = torch.zeros_like(rhs)
+    y = torch.zeros(4, dtype=torch.float64, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=torch.cuda.Stream()):
+        y.add_(1.0)
+        with pytest.raises(sea.SeaError) as e:
+            sea.poisson_batch(H, exts, rhs, x, noalloc=True,
+                              stream=torch.cuda.current_stream().cuda_stream)
+        y.add_(1.0)
+    assert e.value.code == 1
+    g.replay()  # the capture survived: both adds replay, nothing was solved
+    torch.cuda.synchronize()
+    assert torch.all(y == 2.0)
+    assert torch.all(x == 0.0)
+    # and the entry point works again outside the capture
+    xa, _, _ = _solve(exts, 4, noalloc=False)
+    xn, _, rcn = _solve(exts, 4, noalloc=True)
+    assert rcn == 0 and np.abs(xn - xa).max() <= 1e-11 * max(1.0, np.abs(xa).max())
