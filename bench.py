@@ -42,8 +42,9 @@ WORKLOAD = ("(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, eps=10^
             "delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; ACE build + apply to "
             "256 trial vectors")
 FORMS = {"plain": "plain FP64",
-         "mixed": "mixed: FP32 CG sweeps/vectors inside FP64 iterative refinement; FP64 "
-                  "residuals, dots across blocks, E_xx, multipoles and ACE"}
+         "mixed": "mixed: FP32 CG sweeps/vectors inside FP64 iterative refinement (FP64 true "
+                  "residual and stopping rule, FP64 E_xx); double-float multipoles; ACE "
+                  "contractions on the tensor cores from exact digit splits of FP64 values"}
 
 # Algorithmic FP64 flops per CG unknown and iteration: the symmetric 37-point
 # stencil as 18 pair sums, 18 multiply-adds and the centre product (55), plus
@@ -221,9 +222,12 @@ def run_ours(args, ws, rank, local):
     forms = ["plain", "mixed"] if args.form == "both" else [args.form]
     chosen = "mixed" if "mixed" in forms else forms[0]
     res = {}
+    results = {}  # each form's V_xx phi (host copy, outside the timed region) and E_xx
     for f in forms:
         res[f] = _time_form(args, sea, s, psi, vxx, y, stream, 1 if f == "mixed" else 0, barrier,
                             torch, rank, local, sample_clocks=(f == chosen))
+        if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+            results[f] = (vxx.cpu().numpy(), res[f]["stats"]["exx"])
         if f != chosen:
             res[f]["ctx"].close()
     R = res[chosen]
@@ -298,6 +302,16 @@ def run_ours(args, ws, rank, local):
                    "on chip, so DRAM traffic is lower)")
         cand.append(("k_cg_mixed (FP32 CG sweeps inside FP64 refinement)", sm["cg"], 1,
                      44.0 * R["cg_unknown_iters"], hbm, "hbm", note_cg))
+        # the CG's own roof: shared memory (37 four-byte stencil loads per
+        # unknown and inner iteration) against 152 SMs x 128 B/clk at the
+        # sampled SM clock
+        sm_mhz = (R["clocks"] or {}).get("sm_mhz") or 2070.0
+        smem_peak = 152 * 128 * sm_mhz * 1e6 / 1e9  # GB/s
+        cand.append(("k_cg_mixed [shared-memory roof]", sm["cg"], 1,
+                     37 * 4.0 * R["cg_unknown_iters"], smem_peak, "smem",
+                     "shared-memory bandwidth from unit counts: 152 SMs x 128 B/clk x the "
+                     "sampled SM clock; algorithmic bytes: the 37 stencil loads (4 B) per "
+                     "unknown and inner FP32 iteration"))
         note_gt = ("HBM of measured (copy); algorithmic bytes: the A rows on the tiles where W is "
                    "nonzero (8 B per point), W's BF16 digit planes (1536 B per tile slot and "
                    "128-row block), the FP64 partials written")
@@ -314,21 +328,37 @@ def run_ours(args, ws, rank, local):
         cand.append(("k_expand_tc (tensor-core W H, exact BF16 digits)", sm["expand_apply"], 1,
                      expand_bytes, hbm, "hbm", note_x))
     def _rate(c):  # work per launch / time: flop -> TFLOP/s, bytes -> GB/s
-        return c[3] / (c[1] / 1e3) / (1e9 if c[5] == "hbm" else 1e12) if c[1] > 0 else 0.0
+        return c[3] / (c[1] / 1e3) / (1e9 if c[5] in ("hbm", "smem") else 1e12) if c[1] > 0 else 0.0
 
-    top = max(cand, key=lambda c: c[1] * c[2])
+    top = max((c for c in cand if c[5] != "smem"), key=lambda c: c[1] * c[2])
     name, kms, nl, flops, peak, bound, peak_note = top
     achieved = _rate(top)
     others = [{"kernel": c[0], "bound": c[5], "ms_per_step": c[1] * c[2], "achieved": _rate(c),
-               "peak": c[4], "unit": "GB/s" if c[5] == "hbm" else "TFLOP/s",
+               "peak": c[4], "unit": "GB/s" if c[5] in ("hbm", "smem") else "TFLOP/s",
                "frac": _rate(c) / c[4]} for c in cand if c is not top]
-    cpu = cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline) else None
+    cpu, oracle_res = (cpu_baseline(s, psi_h) if (ws == 1 and not args.no_cpu_baseline)
+                       else (None, None))
+    # the metric's bound: each form's error against the oracle on this input
+    n_mol = s.n_orb // 4
+    errors = None
+    if oracle_res is not None and results:
+        vref = oracle_res["vxx"]
+        vmax = float(np.abs(vref).max())
+        errors = {f: {"exx": e, "exx_oracle": float(oracle_res["exx"]),
+                      "exx_err_per_molecule": abs(e - float(oracle_res["exx"])) / n_mol,
+                      "max_abs_dvxx": float(np.abs(v - vref).max()),
+                      "max_abs_dvxx_rel": float(np.abs(v - vref).max()) / vmax,
+                      "bound_exx_per_molecule": 1e-6}
+                  for f, (v, e) in results.items()}
     batched = run_batched(args, sea, torch, dev) if (ws == 1 and not args.no_batched) else None
     warm = run_warm_start(args, sea, synth, torch, dev, s) if (ws == 1 and not args.no_warm_start) else None
     line = {
         "metric": METRIC,
         "value": value,
         "unit": UNIT,
+        "plain_value": ws * K / (form_ms["plain"] / 1e3) if "plain" in form_ms else None,
+        "exx_err_per_molecule": errors[chosen]["exx_err_per_molecule"] if errors else None,
+        "max_abs_dvxx": errors[chosen]["max_abs_dvxx"] if errors else None,
         "n_gpus": ws,
         "steps": K,
         "warmup": args.warmup,
@@ -352,6 +382,7 @@ def run_ours(args, ws, rank, local):
             "ace_tile_points": st["ace_support_points"],
             "stage_ms": sm,
             "stage_ms_plain": res["plain"]["stage_ms"] if "plain" in res else None,
+            "errors_vs_oracle": errors,
             "batched_form": batched,
             "warm_start": warm,
         },
@@ -509,16 +540,17 @@ def oracle_step(s, psi_h):
 
 def cpu_baseline(s, psi_h):
     """The oracle as it stands, timed on the host cores: one full step of the
-    same workload (about 10-30 s on the GPU machine's host)."""
+    same workload (a few seconds on the GPU machine's host).  Returns the timing
+    record and the oracle's result (V_xx phi, E_xx) on this input."""
     from oracle import oracle as O
     O.build()
     t0 = time.perf_counter()
-    oracle_step(s, psi_h)
+    r = oracle_step(s, psi_h)
     dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": "one full step (V_xx + ACE build + ACE apply to 256 vectors) of the "
-                      "same (H2O)64-like 96^3 workload; C oracle with OpenMP over pairs, "
-                      "numpy/BLAS ACE"}
+    return ({"value": 1.0 / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+             "sample": "one full step (V_xx + ACE build + ACE apply to 256 vectors) of the "
+                       "same (H2O)64-like 96^3 workload; C oracle with OpenMP over pairs, "
+                       "numpy/BLAS ACE"}, r)
 
 
 def run_reference(args, ws, rank):

@@ -50,8 +50,8 @@ typedef enum {
   SEA_ERR_OOM = 4,              /* device allocation failed                      */
   SEA_ERR_CG_NOT_CONVERGED = 5, /* a pair's CG hit cg_max_iter (result kept)     */
   SEA_ERR_NOT_PD = 6,           /* -Mbar not positive definite (Cholesky pivot)  */
-  SEA_ERR_TIMEOUT = 7,          /* reserved                                      */
-  SEA_ERR_INPUT = 8,            /* orbitals not finite                           */
+  SEA_ERR_TIMEOUT = 7,          /* the CG's time budget (timeout_ms) was spent   */
+  SEA_ERR_INPUT = 8,            /* orbitals not finite, or not unit norm         */
   SEA_ERR_LIMIT = 9             /* request above a fixed capacity (see below)    */
 } sea_status;
 
@@ -67,8 +67,15 @@ typedef enum {
  * inner product), eigenvalues within 1e-13 max|lambda| of zero dropped --
  * when a Cholesky pivot is not positive), precision = 0 (FP64 everywhere; 1: the mixed form --
  * FP32 stencil sweeps and CG vectors inside an FP64 iterative refinement of
- * each pair's solve: true residual, its norm, the stopping rule, dot
- * products across the block, E_xx and the ACE stay FP64), warm_start = 0
+ * each pair's solve, whose true residual, its norm, the stopping rule and
+ * E_xx stay FP64; the inner FP32 CG uses compensated FP32 dot products and
+ * FP32 step lengths; the multipole moments, boundary values and far-field
+ * products in double-float arithmetic (pairs of FP32 values, about 48
+ * bits); the two contractions with W (M = Phi^T W dV, W^T psi, W H) on the
+ * tensor cores from exact BF16 digit splits of FP64 values, truncated at
+ * 2^-47 of each 64-point segment's largest value; the Cholesky diagonal
+ * blocks in double-float, the rest of the Cholesky and L^-1 in FP64),
+ * warm_start = 0
  * (1: every pair's CG starts from the attached learned model's guess and
  * runs to the same tolerance; the batched form always starts from zero). */
 typedef struct {
@@ -82,9 +89,16 @@ typedef struct {
   double self_scale;
   int precision;  /* 0: FP64, 1: mixed (FP32 CG inside FP64 refinement) */
   int warm_start; /* 0: none; 1: the attached sea_unet's guesses (sea_unet_attach) */
-  double timeout_ms; /* reserved, 0 */
+  double timeout_ms; /* time budget of sea_apply_vxx's persistent CG launch
+                        (0: none).  Once it is spent no CTA takes another
+                        pair; the call then returns SEA_ERR_TIMEOUT and its
+                        results are not valid (the context stays usable). */
   int ace_decomp; /* 0: Cholesky, eigen form of App. A if a pivot fails;
                      1: Cholesky only (SEA_ERR_NOT_PD on failure); 2: eigen form */
+  double orth_tol; /* sea_set_orbitals returns SEA_ERR_INPUT when some
+                      |<phi_i|phi_i> - 1| exceeds it (default 1e-6; 0: no
+                      norm check).  Mutual orthogonality is not checked: that
+                      needs the dense Gram matrix Phi^T Phi dV. */
 } sea_params;
 
 /* Per-call statistics of the last sea_apply_vxx / sea_build_ace /
@@ -115,6 +129,10 @@ typedef struct {
   int ace_max_tile_list; /* longest W list of a tile, last sea_build_ace (the
                             mixed form expands lists up to 32 on the tensor
                             cores, longer ones in FP32 error-free arithmetic) */
+  double exx_ace; /* E_xx^ACE = sum_i <phi_i|V^ACE|phi_i> = -sum_ik <phi_i|xi_k>^2
+                     (Eq. exx_ace), last sea_build_ace: -tr(M K M^T) with
+                     K = (-Mbar)^-1 = L^-T L^-1 (Cholesky form) or
+                     Q |Lambda|^-1 Q^T (eigen form, kept eigenvalues) */
 } sea_stats;
 
 typedef struct sea_ctx sea_ctx;
@@ -131,8 +149,10 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
 
 /* Copy n_orb orbitals ([n_orb][nz][ny][nx], host or device) into the
  * context.  Any earlier exchange/ACE result is invalidated.  Returns
- * SEA_ERR_INPUT if a value is not finite.  Host orbitals are copied in
- * orbital ranges, each range checked while the next one is in flight. */
+ * SEA_ERR_INPUT if a value is not finite or, with orth_tol > 0, if some
+ * orbital's norm <phi_i|phi_i> = dV sum phi_i^2 (FP64) differs from 1 by
+ * more than orth_tol.  Host orbitals are copied in orbital ranges, each
+ * range checked while the next one is in flight. */
 sea_status sea_set_orbitals(sea_ctx* ctx, const double* phi, int n_orb, int on_device);
 
 /* SCDM localization (Sec. II A): from n_orb orthonormal orbitals phi
@@ -176,9 +196,11 @@ sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* const* vxx_p
                                int on_device, double* exx);
 
 /* Build the ACE operator from the orbitals and the last sea_apply_vxx
- * result.  Returns SEA_ERR_STATE if no sea_apply_vxx result is current and
- * SEA_ERR_NOT_PD when -Mbar has a non-positive Cholesky pivot and
- * ace_decomp = 1 (with ace_decomp = 0 the eigen form takes over). */
+ * result, and E_xx^ACE (Eq. exx_ace, the energy the paper's SeA reports;
+ * in sea_stats.exx_ace).  Returns SEA_ERR_STATE if no sea_apply_vxx result
+ * is current and SEA_ERR_NOT_PD when -Mbar has a non-positive Cholesky
+ * pivot and ace_decomp = 1 (with ace_decomp = 0 the eigen form takes
+ * over). */
 sea_status sea_build_ace(sea_ctx* ctx);
 
 /* Same, from a caller-supplied W = V_xx Phi ([n_orb][nz][ny][nx], host or
@@ -234,18 +256,21 @@ sea_status sea_poisson_batch(const double h[3], int n_box, const int* ext, const
                              void* cuda_stream);
 
 /* Same solve as sea_poisson_batch, for callers that cannot allocate device
- * memory (inside graph capture, under a host framework that owns all
- * device memory, or with a footprint fixed at start-up).  It allocates
- * nothing: its scratch is one fixed array of device memory inside the
- * library (about 25 MB, held on every GPU that loads the library until the
- * process exits).  The paper has no counterpart to this entry point.
+ * memory: plugins whose host framework owns all device memory through its
+ * own pool, and processes whose device footprint is fixed at start-up.  It
+ * allocates nothing: its scratch is one fixed array of device memory inside
+ * the library (about 25 MB, held on every GPU that loads the library until
+ * the process exits).  The paper has no counterpart to this entry point.
  * Limits: n_box <= 4096 and sum of box sizes <= 1048576 unknowns, else
  * SEA_ERR_LIMIT before any GPU work.  The caller still provides rhs and x
  * (device) and ext, iters (host), as for sea_poisson_batch.  All calls share
  * the one array: calls that overlap on the GPU race, so order them; each
  * call clears what must start at zero.  The first call on a device looks up
- * the array's device address (once per device); make it before any stream
- * capture begins.  Synchronizes the stream. */
+ * the array's device address (once per device).  The call is synchronous
+ * (pageable host copies and a stream synchronize), so it must not be made
+ * while its stream is being captured into a CUDA graph: on a capturing
+ * stream it returns SEA_ERR_ARG before queueing anything, and the capture
+ * stays valid. */
 sea_status sea_poisson_batch_noalloc(const double h[3], int n_box, const int* ext,
                                      const double* rhs, double* x, double tol, int tol_mode,
                                      int max_iter, int* iters, void* cuda_stream);

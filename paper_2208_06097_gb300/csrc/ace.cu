@@ -809,6 +809,61 @@ __global__ void __launch_bounds__(256)
 }
 
 
+// E_xx^ACE = sum_i <phi_i|V^ACE|phi_i> (Eq. exx_ace).  With G = W^T Phi dV
+// = M^T, V^ACE phi_i = -W K G_i and so E = -tr(M K M^T); K = L^-T L^-1 for the
+// Cholesky form, Q |Lambda|^-1 Q^T for the eigen form.  Written as
+//   E = -sum_k d_k sum_i Y[k][i]^2,  Y[k][i] = sum_j A(k, j) M[i][j],
+// with A = L^-1, d = 1 (then Y[k][i] = <phi_i|xi_k>, the second form of
+// Eq. exx_ace), or A(k, j) = Q[j][k], d_k = 1/|lambda_k| (0 where dropped).
+// Block k forms row k of Y: warp w takes i = w, w + 8, ... (lanes over j,
+// coalesced rows of M), sums Y^2 in i order; warps' sums in warp order.
+__global__ void __launch_bounds__(256)
+    k_exx_ace_rows(const double* __restrict__ M, const double* __restrict__ A, int transA,
+                   const double* __restrict__ d, int n, double* __restrict__ part) {
+  extern __shared__ double a_row[];  // [n]
+  __shared__ double wsum[8];
+  const int k = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    a_row[j] = transA ? A[(size_t)j * n + k] : A[(size_t)k * n + j];
+  __syncthreads();
+  double s = 0.0;
+  for (int i = warp; i < n; i += 8) {
+    const double* mi = M + (size_t)i * n;
+    double y = 0.0;
+    for (int j = lane; j < n; j += 32) y = fma(a_row[j], mi[j], y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    s = fma(y, y, s);
+  }
+  if (lane == 0) wsum[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    part[k] = (d ? d[k] : 1.0) * t;
+  }
+}
+
+// out = -sum_k part[k] (fixed order: thread strides, then the block sum).
+__global__ void k_exx_ace_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) t += part[k];
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) *out = -t;
+}
+
+static cudaError_t launch_exx_ace(sea_ctx* c, int transA, const double* d) {
+  const int n = c->n_orb;
+  if (!sea_ensure(c, c->Gbuf, (size_t)n * sizeof(double))) return cudaErrorMemoryAllocation;
+  double* part = (double*)c->Gbuf.p;
+  k_exx_ace_rows<<<n, 256, (size_t)n * sizeof(double), c->stream>>>(
+      (const double*)c->Mbuf.p, (const double*)c->Linv.p, transA, d, n, part);
+  k_exx_ace_sum<<<1, 256, 0, c->stream>>>(part, n, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
 // The contractions with W: FP64 kernels for the plain form, the
 // tensor-core kernel (exact BF16 digit splitting) for the mixed form.
 static cudaError_t launch_gram(sea_ctx* c, const double* A, int m, const TileGeom& G,
@@ -976,7 +1031,9 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     nchol += 2;
   }
   c->launches += 10 + nchol;
-  return cudaGetLastError();
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_exx_ace(c, 0, nullptr);  // Y = L^-1 M^T
 }
 
 // Eigen form (App. A) after M is known: Q into Linv, S (eigenvalues on the
@@ -1022,7 +1079,9 @@ cudaError_t launch_ace_eigen(sea_ctx* c) {
   c->stats.ace_negative_eigenvalues = hc[0];
   c->stats.ace_dropped_eigenvalues = hc[1];
   c->ace_eigen = true;
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_exx_ace(c, 1, (const double*)c->Abuf.p);  // Y = Q^T M^T, d = 1/|lambda|
 }
 
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out) {

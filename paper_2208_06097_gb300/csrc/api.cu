@@ -55,12 +55,38 @@ HarmCoef make_harmonic_coefficients() {
   return h;
 }
 
-__global__ void k_check_finite(const double* __restrict__ f, size_t n, unsigned* __restrict__ st) {
+// Input check of sea_set_orbitals, one pass over the orbitals: every value
+// finite, and part[o][b] = sum of phi_o^2 over chunk b of orbital o (grid
+// blockIdx.x = chunk, blockIdx.y = orbital of the range).
+#define SEA_NORM_CHUNKS 16
+__global__ void __launch_bounds__(256)
+    k_check_orbitals(const double* __restrict__ f, size_t ng, unsigned* __restrict__ st,
+                     double* __restrict__ part) {
+  __shared__ double red[32];
+  const size_t chunk = (ng + SEA_NORM_CHUNKS - 1) / SEA_NORM_CHUNKS;
+  const size_t b0 = chunk * blockIdx.x, b1 = min(ng, b0 + chunk);
+  const double* fo = f + (size_t)blockIdx.y * ng;
   bool bad = false;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    bad |= !isfinite(f[i]);
+  double s = 0.0;
+  for (size_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const double v = fo[i];
+    bad |= !isfinite(v);
+    s = fma(v, v, s);
+  }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(st, SEA_FLAG_NONFINITE);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * SEA_NORM_CHUNKS + blockIdx.x] = s;
+}
+
+// |dV sum_b part[o][b] - 1| > tol for some orbital o: SEA_FLAG_NORM (the
+// chunks added in index order).
+__global__ void k_check_norms(const double* __restrict__ part, int n, double dV, double tol,
+                              unsigned* __restrict__ st) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < SEA_NORM_CHUNKS; ++b) s += part[(size_t)o * SEA_NORM_CHUNKS + b];
+  if (!(fabs(s * dV - 1.0) <= tol)) atomicOr(st, SEA_FLAG_NORM);
 }
 
 cudaError_t launch_plan_boxes(sea_ctx* c);
@@ -167,6 +193,7 @@ void sea_default_params(sea_params* p) {
   p->warm_start = 0;
   p->timeout_ms = 0.0;
   p->ace_decomp = 0;
+  p->orth_tol = 1e-6;
 }
 
 sea_status sea_create(const double cell[3], const int grid[3], const sea_params* p,
@@ -183,7 +210,8 @@ sea_status sea_create(const double cell[3], const int grid[3], const sea_params*
   if (!(prm.eps >= 0.0 && prm.eps < 1.0) || !(prm.delta >= 0.0) || !(prm.cg_tol > 0.0) ||
       prm.cg_max_iter < 1 || prm.lmax < 0 || prm.lmax > SEA_LMAX || prm.fd_order != 12 ||
       prm.self_scale != 2.0 || (prm.precision != 0 && prm.precision != 1) || (prm.warm_start != 0 && prm.warm_start != 1) ||
-      (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1) || prm.ace_decomp < 0 || prm.ace_decomp > 2)
+      (prm.cg_tol_mode != 0 && prm.cg_tol_mode != 1) || prm.ace_decomp < 0 || prm.ace_decomp > 2 ||
+      !(prm.timeout_ms >= 0.0 && prm.timeout_ms < 1e12) || !(prm.orth_tol >= 0.0))
     return SEA_ERR_ARG;
   sea_ctx* c = new (std::nothrow) sea_ctx();
   if (!c) return SEA_ERR_OOM;
@@ -265,11 +293,14 @@ sea_status sea_set_orbitals(sea_ctx* c, const double* phi, int n_orb, int on_dev
   SEA_ALLOC(eptr, (size_t)(n_orb + 1) * sizeof(int));
   SEA_ALLOC(ewin, (size_t)2 * ncand * sizeof(Entry));
   SEA_ALLOC(coff, (size_t)2 * ncand * sizeof(long long));
+  SEA_ALLOC(onorm, (size_t)n_orb * SEA_NORM_CHUNKS * sizeof(double));
+  double* npart = (double*)c->onorm.p;
   SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
   double* pd = (double*)c->phi.p;
   if (on_device) {
     SEA_CK(cudaMemcpyAsync(pd, phi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy orbitals");
-    sea::k_check_finite<<<1024, 256, 0, c->stream>>>(pd, n_orb * c->ng, (unsigned*)c->status.p);
+    sea::k_check_orbitals<<<dim3(SEA_NORM_CHUNKS, n_orb), 256, 0, c->stream>>>(
+        pd, c->ng, (unsigned*)c->status.p, npart);
     c->launches += 1;
   } else {
     // orbital ranges copied in on the copy stream, each checked on the
@@ -288,17 +319,25 @@ sea_status sea_set_orbitals(sea_ctx* c, const double* phi, int n_orb, int on_dev
     for (int k = 0; k < nch; ++k) {
       const size_t o0 = (size_t)n_orb * k / nch, o1 = (size_t)n_orb * (k + 1) / nch;
       SEA_CK(cudaStreamWaitEvent(c->stream, c->xev[k], 0), "wait");
-      sea::k_check_finite<<<1024, 256, 0, c->stream>>>(pd + o0 * c->ng, (o1 - o0) * c->ng,
-                                                       (unsigned*)c->status.p);
+      sea::k_check_orbitals<<<dim3(SEA_NORM_CHUNKS, (unsigned)(o1 - o0)), 256, 0, c->stream>>>(
+          pd + o0 * c->ng, c->ng, (unsigned*)c->status.p, npart + o0 * SEA_NORM_CHUNKS);
       c->launches += 1;
     }
   }
-  SEA_CK(cudaGetLastError(), "finite check");
+  if (c->prm.orth_tol > 0.0) {
+    sea::k_check_norms<<<(n_orb + 127) / 128, 128, 0, c->stream>>>(npart, n_orb, c->dV,
+                                                                    c->prm.orth_tol,
+                                                                    (unsigned*)c->status.p);
+    c->launches += 1;
+  }
+  SEA_CK(cudaGetLastError(), "input check");
   unsigned st = 0;
   SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
          "status");
   SEA_CK(cudaStreamSynchronize(c->stream), "set_orbitals");
   if (st & SEA_FLAG_NONFINITE) return sea_fail(c, SEA_ERR_INPUT, "orbitals hold non-finite values");
+  if (st & SEA_FLAG_NORM)
+    return sea_fail(c, SEA_ERR_INPUT, "an orbital's norm <phi|phi> differs from 1 by more than orth_tol");
   c->have_phi = true;
   c->stats.n_orb = n_orb;
   return SEA_OK;
@@ -438,6 +477,9 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   c->stats.cg_iters_max = (int)r.res[3];
   c->stats.cg_iters_mean = r.res[4];
   if (exx) *exx = r.res[0];
+  if (r.st & SEA_FLAG_TIMEOUT)
+    return sea_fail(c, SEA_ERR_TIMEOUT,
+                    "the CG time budget (timeout_ms) was spent before every pair was solved");
   c->have_vxx = true;
   if (r.st & SEA_FLAG_CG_CAP)
     return sea_fail(c, SEA_ERR_CG_NOT_CONVERGED, "a pair's CG reached cg_max_iter");
@@ -472,7 +514,12 @@ static sea_status build_ace_common(sea_ctx* c) {
     return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is not positive definite");
   }
   SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
+  double exx_ace = 0.0;
+  SEA_CK(cudaMemcpyAsync(&exx_ace, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT, sizeof(double),
+                         cudaMemcpyDeviceToHost, c->stream),
+         "exx_ace");
   SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
+  c->stats.exx_ace = exx_ace;
   float t = 0;
   cudaEventElapsedTime(&t, c->ev[5], c->ev[6]);
   c->stats.ms_ace_build = t;
@@ -711,7 +758,10 @@ sea_status sea_poisson_batch(const double h[3], int n_box, const int* ext, const
     free(hord);
     return rs;
   }
-  // longest boxes first
+  // longest boxes first (ties by index).  k_noalloc_order (noalloc.cu) ranks
+  // the boxes of sea_poisson_batch_noalloc the same way; the two orders must
+  // stay identical, since the solutions and iteration counts of the two entry
+  // points are compared bit for bit.
   std::stable_sort(hord, hord + n_box, [&](int a, int b) { return hb[a].n > hb[b].n; });
   void* dev = nullptr;
   const size_t bytes = (size_t)n_box * (sizeof(PairInfo) + sizeof(long long) + 2 * sizeof(int)) +
@@ -793,7 +843,8 @@ void sea_destroy(sea_ctx* c) {
                    &c->exx_dev, &c->queue, &c->tmask, &c->tptr_o, &c->tlist_o, &c->tslot_o,
                    &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf, &c->wdig, &c->wx,
                    &c->scdm_u, &c->scdm_c,
-                   &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2, &c->bdesc, &c->bitems};
+                   &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2, &c->bdesc, &c->bitems,
+                   &c->onorm};
   for (SeaBuf* b : all) release(*b);
   for (int k = 0; k < 16; ++k)
     if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -84,6 +84,11 @@ __device__ __forceinline__ uint32_t idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MBLK >> 4) << 24);
 }
 
+// The same with FP16 A and B (the contraction's digits).
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MBLK >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -170,6 +175,14 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
+// FP16 bit patterns of two small integer-valued floats (|v| <= 2048, exact),
+// packed low/high.
+__device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // Digits of one row group (8 rows) of a block, half h of tile T, held in
 // registers: the warp's lane l takes row l % 8 and the x-runs u = l / 8 and
 // l / 8 + 4 (run u: y = u % 4, z = 2h + u / 4, 8 points along x).  Row
@@ -218,7 +231,7 @@ __device__ __forceinline__ void make_digits(const double* __restrict__ rp, const
       digit_floats(fixed47(v[q][2 * p], em), f0);
       digit_floats(fixed47(v[q][2 * p + 1], em), f1);
 #pragma unroll
-      for (int k = 0; k < DIG; ++k) o.w[q][k][p] = pack_bf16(f0[k], f1[k]);
+      for (int k = 0; k < DIG; ++k) o.w[q][k][p] = pack_f16(f0[k], f1[k]);
     }
 }
 
@@ -434,7 +447,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
 #pragma unroll
       for (int k = 0; k < DIG; ++k)
         mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A_PLANE + q * 2 * A_LBO) >> 4),
-                 w0 + ((q * 2 * lbo) >> 4), idesc_bf16((DIG - k) * P), (k > 0 || q > 0) ? 1u : 0u);
+                 w0 + ((q * 2 * lbo) >> 4), idesc_f16((DIG - k) * P), (k > 0 || q > 0) ? 1u : 0u);
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
         : "memory");
@@ -544,47 +557,70 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
-// Balanced digits of |v| 2^-E on the 2^-47 grid (as fixed47 and
-// digit_floats), each multiplied by the sign of v: six exact FP32 values.
-// The sign is applied by one FFMA per digit, s (b - c) = s b + (-s c).
-__device__ __forceinline__ void digits_signed(double v, int emax, float (&f)[DIG]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const unsigned hv = (unsigned)(bits >> 32);
-  const int e = (int)((hv >> 20) & 0x7FF);
-  int sh = emax - e + 6;
-  const bool ok = e != 0 && sh <= 60;
-  unsigned mh = ok ? ((hv & 0xFFFFFu) | 0x100000u) : 0u, ml = ok ? (unsigned)bits : 0u;
-  if (sh >= 32) {
-    ml = mh;
-    mh = 0u;
-    sh -= 32;
-  }
-  const unsigned xl = __funnelshift_r(ml, mh, sh), xh = __funnelshift_r(mh, 0u, sh);
-  const unsigned long long Y = (((unsigned long long)xh << 32) | xl) + 0x8080808080ULL;
-  const unsigned lo = (unsigned)Y, hi = (unsigned)(Y >> 32);
-  const unsigned sg = hv & 0x80000000u;
-  const float s = __uint_as_float(0x3F800000u | sg);
-  const float cm = __uint_as_float(__float_as_uint(-(12582912.0f + 128.0f)) ^ sg);
-  const float c0 = __uint_as_float(__float_as_uint(-12582912.0f) ^ sg);
-  f[5] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7650)), cm);
-  f[4] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7651)), cm);
-  f[3] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7652)), cm);
-  f[2] = fmaf(s, __uint_as_float(__byte_perm(lo, 0x4B400000u, 0x7653)), cm);
-  f[1] = fmaf(s, __uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7650)), cm);
-  f[0] = fmaf(s, __uint_as_float(__byte_perm(hi, 0x4B400000u, 0x7651)), c0);
+// A's digits in the TMA kernel: unsigned bytes of |x| on the segment's
+// 2^-48 grid, each carrying the sign of x.  With E = emax - 1022 (|x| <
+// 2^E), X = floor(|x| 2^(48 - E)) = m >> (emax - e + 5) for the 53-bit
+// significand m and biased exponent e of x, so X < 2^48 and
+//   x ~ s 2^(E - 48) sum_k b_k 256^(5 - k),  b_k = byte 5 - k of X,
+// with an error below 2^(E - 48).  b_k in [0, 255] is exact in FP16; the
+// FP16 pattern 0x6400 | b is 1024 + b, so one packed FMA (1024 + b) s -
+// 1024 s gives the signed digit s b for two points at once.  Against W's
+// balanced digits (|d| <= 128) every product is below 2^15 and a diagonal
+// sum of at most 6 x 64 of them stays below 2^24, exact in the FP32
+// accumulator.  em_sh = (emax + 5) << 20; segments whose largest value is
+// below 2^-959 (emax < 64) are taken as zero (em_sh = 0xF0000000 makes
+// every shift reach 64).  Integer work per value: the exponent field, the
+// shift count, the significand word, one 64-bit shift; per pair of values
+// nine byte permutations and the sign word.
+
+// 64-bit right shift, the count clamped at 64 (shr.b64 semantics).
+__device__ __forceinline__ unsigned long long shr64(unsigned long long a, uint32_t n) {
+  unsigned long long r;
+  asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(a), "r"(n));
+  return r;
 }
 
-// The digit planes of 8 consecutive points: d[k] = their 8 BF16 digits of
-// plane k (points 2i, 2i + 1 in word i).
-__device__ __forceinline__ void digits8(const double (&v)[8], int emax, uint4 (&d)[DIG]) {
+__device__ __forceinline__ uint32_t hfma2_u(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
+// X of one value: the significand of v (bits h, l) shifted onto the grid.
+__device__ __forceinline__ unsigned long long fixed48(uint32_t h, uint32_t l, uint32_t em_sh) {
+  const uint32_t sh = (em_sh - (h & 0x7FF00000u)) >> 20;
+  const unsigned long long m = ((unsigned long long)((h & 0xFFFFFu) | 0x100000u) << 32) | l;
+  return shr64(m, sh);
+}
+
+// The six FP16 digit planes of 8 consecutive points: d[k] = their 8 signed
+// digits of plane k (points 2i, 2i + 1 in word i, low half first).
+__device__ __forceinline__ void digits8_u(const double (&v)[8], uint32_t em_sh, uint4 (&d)[DIG]) {
+  constexpr uint32_t K64 = 0x64646464u;
   uint32_t w[DIG][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float f0[DIG], f1[DIG];
-    digits_signed(v[2 * i], emax, f0);
-    digits_signed(v[2 * i + 1], emax, f1);
-#pragma unroll
-    for (int k = 0; k < DIG; ++k) w[k][i] = pack_bf16(f0[k], f1[k]);
+    const unsigned long long b0 = (unsigned long long)__double_as_longlong(v[2 * i]);
+    const unsigned long long b1 = (unsigned long long)__double_as_longlong(v[2 * i + 1]);
+    const uint32_t h0 = (uint32_t)(b0 >> 32), h1 = (uint32_t)(b1 >> 32);
+    const unsigned long long X0 = fixed48(h0, (uint32_t)b0, em_sh);
+    const unsigned long long X1 = fixed48(h1, (uint32_t)b1, em_sh);
+    const uint32_t x0h = (uint32_t)(X0 >> 32), x0l = (uint32_t)X0;
+    const uint32_t x1h = (uint32_t)(X1 >> 32), x1l = (uint32_t)X1;
+    // bytes of the two points interleaved: [p0 b, p1 b, p0 b', p1 b']
+    const uint32_t tH = __byte_perm(x0h, x1h, 0x5140);  // bytes 4, 5 of X
+    const uint32_t tB = __byte_perm(x0l, x1l, 0x7362);  // bytes 2, 3
+    const uint32_t tA = __byte_perm(x0l, x1l, 0x5140);  // bytes 0, 1
+    // sign word: FP16 pair (s0, s1) = +-1, and -1024 (s0, s1)
+    const uint32_t S = (__byte_perm(h0, h1, 0x7030) & 0x80008000u) | 0x3C003C00u;
+    const uint32_t C = S ^ 0xD800D800u;
+    // plane k = byte 5 - k: FP16 1024 + b from the pattern 0x64bb
+    w[0][i] = hfma2_u(__byte_perm(tH, K64, 0x4342), S, C);
+    w[1][i] = hfma2_u(__byte_perm(tH, K64, 0x4140), S, C);
+    w[2][i] = hfma2_u(__byte_perm(tB, K64, 0x4342), S, C);
+    w[3][i] = hfma2_u(__byte_perm(tB, K64, 0x4140), S, C);
+    w[4][i] = hfma2_u(__byte_perm(tA, K64, 0x4342), S, C);
+    w[5][i] = hfma2_u(__byte_perm(tA, K64, 0x4140), S, C);
   }
 #pragma unroll
   for (int k = 0; k < DIG; ++k) d[k] = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
@@ -684,7 +720,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < DIG; ++k)
               mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A2_PLANE + q * 2 * A2_LBO) >> 4),
-                       w0 + ((q * 2 * lbo) >> 4), idesc_bf16((DIG - k) * P),
+                       w0 + ((q * 2 * lbo) >> 4), idesc_f16((DIG - k) * P),
                        (k > 0 || q > 0) ? 1u : 0u);
           }
           asm volatile(
@@ -831,20 +867,23 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         for (int q = 0; q < 2 * DIG; ++q)
           f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
         tmem_wait_ld();
-        // |D_d| <= (d + 1) 2^20: D_0..D_3 by the 2^22 conversion; the three
-        // 32-bit pairs D_d 256 + D_(d+1) stay below 2^31
+        // |D_d| < (d + 1) 2^21 (A digits up to 255, W digits up to 128 in
+        // magnitude, 64 points): D_0, D_1 (< 2^22) by the 2^22 conversion,
+        // the others exactly; D_0 256 + D_1 and D_2 256 + D_3 stay below 2^31
         long long acc[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const uint32_t* fh = f + h * DIG;
           const int t01 = small_float_int(fh[0]) * 256 + small_float_int(fh[1]);
-          const int t23 = small_float_int(fh[2]) * 256 + small_float_int(fh[3]);
-          const int t45 = float_int(__uint_as_float(fh[4])) * 256 + float_int(__uint_as_float(fh[5]));
-          acc[h] = ((long long)t01 << 32) + ((long long)t23 << 16) + (long long)t45;
+          const int t23 = float_int(__uint_as_float(fh[2])) * 256 + float_int(__uint_as_float(fh[3]));
+          acc[h] = ((long long)t01 << 32) + ((long long)t23 << 16) +
+                   ((long long)float_int(__uint_as_float(fh[4])) << 8) +
+                   (long long)float_int(__uint_as_float(fh[5]));
         }
-        // the two halves on the larger scale (the other truncated at its
-        // unit, 2^-54 of that segment's scale), one truncation
-        const int e0 = ea0 + Wexp[0][c] - 1022 - 54, e1 = ea1 + Wexp[1][c] - 1022 - 54;
+        // sum_r x w = 2^(E_x + E_w - 55) acc; the two halves on the larger
+        // scale (the other truncated at its unit, 2^-55 of that segment's
+        // scale), one truncation
+        const int e0 = ea0 + Wexp[0][c] - 1022 - 55, e1 = ea1 + Wexp[1][c] - 1022 - 55;
         const bool b0 = e0 >= e1;
         const int sh = min(b0 ? e0 - e1 : e1 - e0, 63);
         const long long s2 = (b0 ? acc[0] : acc[1]) + ((b0 ? acc[1] : acc[0]) >> sh);
@@ -882,7 +921,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
           break;
         }
         double v[2][8];
-        int em = 0;
+        uint32_t emf = 0;  // largest exponent field (high-word bits 20..30) of the row segment
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -891,11 +930,13 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
                 sR + q * RAW_KHALF + r_off + (((uint32_t)p << 4) ^ r_swz));
             v[q][2 * p] = t.x;
             v[q][2 * p + 1] = t.y;
-            em = max(em, (int)((__double_as_longlong(t.x) >> 52) & 0x7FF));
-            em = max(em, (int)((__double_as_longlong(t.y) >> 52) & 0x7FF));
+            emf = max(emf, (uint32_t)__double2hiint(t.x) & 0x7FF00000u);
+            emf = max(emf, (uint32_t)__double2hiint(t.y) & 0x7FF00000u);
           }
-        em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
-        em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
+        emf = max(emf, __shfl_xor_sync(0xffffffffu, emf, 1));
+        emf = max(emf, __shfl_xor_sync(0xffffffffu, emf, 2));
+        const int em = (int)(emf >> 20);
+        const uint32_t em_sh = em < 64 ? 0xF0000000u : emf + (5u << 20);
         if (tid == 0) q_step();
         conv_sync();  // both raw buffers consumed
         Unit next = cur;
@@ -909,7 +950,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         // epilogue and a new W block need all of prev's MMAs
         ok = wait_mma(0);
         uint4 d[DIG];
-        digits8(v[0], em, d);
+        digits8_u(v[0], em_sh, d);
         store_digits(d, 0);
         if (have_prev && (prev.h == 1 || need_w)) ok = wait_mma(1) && ok;
         if (conv_sync_or(!ok)) {
@@ -929,7 +970,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         conv_sync();  // digits of K half 0, W and exponents in place
         post(seq, min(NBLK, cur.nJ - cur.jb), cur.h);
         mma_pend[0] = true;
-        digits8(v[1], em, d);
+        digits8_u(v[1], em_sh, d);
         ok = wait_mma(1);  // prev's MMAs of K half 1
         store_digits(d, 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

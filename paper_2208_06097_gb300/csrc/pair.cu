@@ -282,6 +282,7 @@ struct CgArgs {
   unsigned* status;
   int* queue;
   int warm;  // x holds an initial guess (else the solve starts from 0)
+  unsigned long long budget_ns;  // time budget of the launch (0: none)
 };
 
 // One pair's FP64 CG (the whole CTA), results into A's per-pair arrays.
@@ -379,13 +380,34 @@ __device__ __forceinline__ void cg_pair_fp64(const CgArgs& A, const StencilW& W,
   }
 }
 
+// The device's nanosecond clock (the same on every SM).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Next queue item for the CTA (thread 0).  With a time budget, once more
+// than budget_ns have passed since the CTA started (t0) no further pair is
+// taken: the status gets SEA_FLAG_TIMEOUT and the returned item ends the
+// CTA's loop (the pairs not taken keep no solution).
+__device__ __forceinline__ int claim_item(int* queue, int P, unsigned long long budget_ns,
+                                          unsigned long long t0, unsigned* status) {
+  if (budget_ns && global_ns() - t0 > budget_ns) {
+    atomicOr(status, SEA_FLAG_TIMEOUT);
+    return P;
+  }
+  return atomicAdd(queue, 1);
+}
+
 // 3 CTAs per SM: fewer pairs start at once and the longest-first queue
 // balances the tail (measured faster than the 4 CTAs/SM the compiler picks).
 __global__ void __launch_bounds__(256, 3) k_cg(CgArgs A, StencilW W) {
   __shared__ double red[2][32];
   __shared__ int s_item;
+  const unsigned long long t0 = A.budget_ns ? global_ns() : 0ull;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+    if (threadIdx.x == 0) s_item = claim_item(A.queue, A.P, A.budget_ns, t0, A.status);
     __syncthreads();
     const int item = s_item;
     if (item >= A.P) break;
@@ -652,6 +674,7 @@ struct CgMixedArgs {
   int* queue;
   int warm;       // x holds an initial guess (else the solve starts from 0)
   int pad_cap;    // floats of shared memory for the padded search direction
+  unsigned long long budget_ns;  // time budget of the launch (0: none)
 };
 
 // block_sum with the serial combine done by one warp (the same order, so the
@@ -814,8 +837,9 @@ __global__ void __launch_bounds__(SEA_CG_THREADS, 1024 / SEA_CG_THREADS) k_cg_mi
   __shared__ int s_item;
   __shared__ double bc;
   extern __shared__ float pS[];  // A.pad_cap floats
+  const unsigned long long t0 = A.budget_ns ? global_ns() : 0ull;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(A.queue, 1);
+    if (threadIdx.x == 0) s_item = claim_item(A.queue, A.P, A.budget_ns, t0, A.status);
     __syncthreads();
     const int item = s_item;
     if (item >= A.P) break;
@@ -945,6 +969,7 @@ static CgMixedArgs mixed_args(sea_ctx* c) {
   A.queue = (int*)c->queue.p;
   A.pad_cap = cg_pad_cap(c);
   A.warm = c->cg_warm ? 1 : 0;
+  A.budget_ns = (unsigned long long)(c->prm.timeout_ms * 1e6);
   return A;
 }
 
@@ -973,6 +998,7 @@ static CgArgs fp64_args(sea_ctx* c) {
   A.status = (unsigned*)c->status.p;
   A.queue = (int*)c->queue.p;
   A.warm = c->cg_warm ? 1 : 0;
+  A.budget_ns = (unsigned long long)(c->prm.timeout_ms * 1e6);
   return A;
 }
 
@@ -1047,6 +1073,7 @@ void make_batch_desc(sea_ctx* c, void* out) {
   memset(&d, 0, sizeof(d));
   d.a = fp64_args(c);
   d.m = mixed_args(c);
+  d.a.budget_ns = d.m.budget_ns = 0;  // the batched launch has no time budget
   d.W = make_weights(c);
   d.Wf = make_weights_f(d.W);
   d.mixed = c->prm.precision == 1;

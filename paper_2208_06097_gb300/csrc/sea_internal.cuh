@@ -22,6 +22,12 @@
 #define SEA_FLAG_BOUNDS 4u
 #define SEA_FLAG_NONFINITE 8u
 #define SEA_FLAG_WAIT 16u  // a bounded wait on a tensor-core completion expired
+#define SEA_FLAG_TIMEOUT 32u  // the CG's time budget (sea_params.timeout_ms) was spent
+#define SEA_FLAG_NORM 64u     // an orbital's norm is off 1 by more than orth_tol
+
+// Slot (in doubles) of E_xx^ACE in the context's exx_dev buffer (the first
+// five hold sea_apply_vxx's E_xx and CG statistics).
+#define SEA_EXX_ACE_SLOT 6
 
 // At most this many chunks per pipelined host-buffer call.
 #define SEA_XCHUNKS_MAX 64
@@ -469,6 +475,7 @@ struct sea_ctx {
   SeaBuf vbuf, bbuf, rbuf, pbuf, qbuf;
   SeaBuf eptr, eent, ewin, coff, cbuf;
   SeaBuf status, exx_dev, queue;
+  SeaBuf onorm;  // per-orbital partial sums of phi^2 (input check of sea_set_orbitals)
   // ACE
   SeaBuf wdig;  // the mixed form's W digits (tensor-core contraction)
   SeaBuf wx;    // the mixed form's per-tile W digit images (tensor-core expansion)

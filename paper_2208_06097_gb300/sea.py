@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
                 ("cg_max_iter", ctypes.c_int), ("lmax", ctypes.c_int),
                 ("fd_order", ctypes.c_int), ("self_scale", ctypes.c_double),
                 ("precision", ctypes.c_int), ("warm_start", ctypes.c_int),
-                ("timeout_ms", ctypes.c_double), ("ace_decomp", ctypes.c_int)]
+                ("timeout_ms", ctypes.c_double), ("ace_decomp", ctypes.c_int),
+                ("orth_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -60,7 +61,7 @@ class Stats(ctypes.Structure):
                 ("ms_expand_apply", ctypes.c_double), ("ace_eigen", ctypes.c_int),
                 ("ace_eigen_sweeps", ctypes.c_int), ("ace_negative_eigenvalues", ctypes.c_int),
                 ("ace_dropped_eigenvalues", ctypes.c_int), ("batch_graph", ctypes.c_int),
-                ("ace_max_tile_list", ctypes.c_int)]
+                ("ace_max_tile_list", ctypes.c_int), ("exx_ace", ctypes.c_double)]
 
 
 _LIB = None

@@ -64,3 +64,39 @@ def test_apply_on_occupied_reproduces_vxx_up_to_skew(c1_gpu, h2o8):
     ctx.apply_ace(np.ascontiguousarray(h2o8.phi), y)
     W = OA.apply_ace(a["Xi"], F, h2o8.dV)
     assert np.abs(y.reshape(h2o8.n_orb, -1) - W).max() <= 1e-9 * np.abs(W).max()
+
+
+def test_exx_ace(c1_gpu, h2o8):
+    # Eq. exx_ace: E = -sum_ik <phi_i|xi_k>^2 against the oracle's dense form
+    ctx, a, F = c1_gpu
+    e = ctx.stats()["exx_ace"]
+    e_ref = OA.exx_ace(F, a["Xi"], h2o8.dV)
+    assert abs(e - e_ref) <= 1e-10 * abs(e_ref)
+    # close to the pair-sum E_xx of Eq. exxGen_mlwf (they differ by the
+    # domain truncation of the pair form)
+    ex = ctx.stats()["exx"]
+    assert e < 0 and abs(e - ex) <= 1e-2 * abs(ex), (e, ex)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_exx_ace_closed_form(h2o8, precision):
+    # W = -G Phi with G symmetric positive definite: for orthonormal Phi,
+    # M = Phi^T W dV = -G exactly, -Mbar = G, and E_xx^ACE = -tr(M G^-1 M^T)
+    # = -tr(G) (a closed form independent of the Cholesky factor)
+    from paper_2208_06097_gb300 import sea
+    rng = np.random.default_rng(8)
+    n = h2o8.n_orb
+    B = rng.normal(size=(n, n))
+    G = B @ B.T / n + np.eye(n)
+    W = np.ascontiguousarray(-(G @ F_of(h2o8))).reshape(h2o8.phi.shape)
+    with sea.Context(h2o8.cell, h2o8.grid, precision=precision) as ctx:
+        ctx.set_orbitals(np.ascontiguousarray(h2o8.phi))
+        ctx.build_ace_from(W)
+        e = ctx.stats()["exx_ace"]
+        M, _ = ctx.ace_matrices()
+    assert np.abs(M + G).max() <= 1e-10 * np.abs(G).max()
+    assert abs(e + np.trace(G)) <= 1e-10 * np.trace(G)
+
+
+def F_of(s):
+    return s.phi.reshape(s.n_orb, -1)

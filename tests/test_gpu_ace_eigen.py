@@ -41,6 +41,10 @@ def test_indefinite_w_uses_eigen_form(h2o8, precision):
         y = np.empty_like(psi)
         ctx.apply_ace(psi, y)
         assert np.abs(y.reshape(3, -1) - yr).max() <= 1e-9 * np.abs(yr).max()
+        # Eq. exx_ace, first form: sum_i <phi_i|V^ACE|phi_i> with the oracle's operator
+        yF = OA.apply_ace_eigen(e["zeta"], F, h2o8.dV)
+        e_ref = float(np.sum(F * yF) * h2o8.dV)
+        assert abs(st["exx_ace"] - e_ref) <= 1e-10 * abs(e_ref)
 
 
 def test_forced_eigen_form_equals_cholesky_form(h2o8):
@@ -57,7 +61,11 @@ def test_forced_eigen_form_equals_cholesky_form(h2o8):
         assert ctx.stats()["ace_eigen"] == 1
         y = np.empty_like(psi)
         ctx.apply_ace(psi, y)
+        e_ace = ctx.stats()["exx_ace"]
     assert np.abs(y.reshape(3, -1) - yr).max() <= 1e-9 * np.abs(yr).max()
+    # the eigen form's E_xx^ACE equals the Cholesky form's (Eq. exx_ace)
+    e_ref = OA.exx_ace(F, a["Xi"], h2o8.dV)
+    assert abs(e_ace - e_ref) <= 1e-10 * abs(e_ref)
 
 
 def test_singular_mbar_drops_the_zero_mode(h2o8):
@@ -66,7 +74,7 @@ def test_singular_mbar_drops_the_zero_mode(h2o8):
     phi[0] = 0.0
     s.phi = phi
     from paper_2208_06097_gb300 import sea
-    with _ctx(s) as ctx:
+    with _ctx(s, orth_tol=0.0) as ctx:  # a zero orbital has norm 0
         out = np.empty_like(phi)
         ctx.apply_vxx(out)
         ctx.build_ace()

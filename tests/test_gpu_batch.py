@@ -3,7 +3,8 @@ configurations in one persistent CG launch, the post-plan phase captured in
 a CUDA graph.  Every pair is solved by the same per-pair code as in
 sea_apply_vxx, so the batched results equal the per-configuration results
 bit for bit; a replayed graph reproduces them, and a changed plan is
-re-captured."""
+re-captured.  Each configuration of a batch is also compared with the FP64
+oracle."""
 import numpy as np
 import pytest
 
@@ -56,6 +57,36 @@ def test_batch_equals_single_and_graph_replays(precision):
     ref = torch.empty_like(outs2[1])
     e_ref = ctxs[1].apply_vxx(ref)
     assert np.array_equal(outs2[1].cpu().numpy(), ref.cpu().numpy())
+    for c in ctxs:
+        c.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_tight():
+    from oracle import oracle as O
+    return [O.apply_vxx(s.phi, s.cell, O.Params(cg_tol=1e-12)) for s in _systems()]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_oracle(precision, oracle_tight):
+    # every configuration of the batch against the FP64 oracle, both sides at
+    # cg_tol = 1e-12 (the spec bar: max|dV_xx phi| <= 1e-9 Ha,
+    # rel|dE_xx| <= 1e-10), the post-plan phase captured and replayed
+    from paper_2208_06097_gb300 import sea
+    systems = _systems()
+    stream = torch.cuda.Stream()
+    ctxs = [sea.Context(s.cell, s.grid, stream=stream.cuda_stream, precision=precision,
+                        cg_tol=1e-12) for s in systems]
+    for c, s in zip(ctxs, systems):
+        c.set_orbitals(torch.from_numpy(s.phi).cuda())
+    outs = [torch.empty(s.phi.shape, dtype=torch.float64, device="cuda") for s in systems]
+    for rep in range(2):
+        ex = sea.apply_vxx_batch(ctxs, outs)
+        assert ctxs[0].stats()["batch_graph"] == rep + 1
+        for c, o, e, ref in zip(ctxs, outs, ex, oracle_tight):
+            np.testing.assert_array_equal(c.plan()["pair"], ref["pair"])
+            assert np.abs(o.cpu().numpy() - ref["vxx"]).max() <= 1e-9
+            assert abs(e - ref["exx"]) <= 1e-10 * abs(ref["exx"])
     for c in ctxs:
         c.close()
 

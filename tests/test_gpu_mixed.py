@@ -74,6 +74,8 @@ def test_mixed_ace_matches_fp64_oracle(h2o8):
         ctx.apply_ace(psi, y)
         xi = torch.empty_like(phi)
         ctx.ace_vectors(xi)
+        e_ace = ctx.stats()["exx_ace"]
+    assert abs(e_ace - OA.exx_ace(F, a["Xi"], h2o8.dV)) <= 1e-10 * abs(e_ace)
     assert np.abs(M - a["M"]).max() <= 1e-9
     assert np.abs(L - a["L"]).max() <= 1e-9
     yr = OA.apply_ace(a["Xi"], psi.reshape(4, -1), h2o8.dV)
