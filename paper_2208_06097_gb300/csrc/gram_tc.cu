@@ -868,17 +868,19 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
           f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
         tmem_wait_ld();
         // |D_d| < (d + 1) 2^21 (A digits up to 255, W digits up to 128 in
-        // magnitude, 64 points): D_0, D_1 (< 2^22) by the 2^22 conversion,
-        // the others exactly; D_0 256 + D_1 and D_2 256 + D_3 stay below 2^31
+        // magnitude, 64 points): D_0, D_1 (< 2^22) by the 2^22 conversion on
+        // the FP32 pipe, the others by the conversion unit (exact: integer
+        // values below 2^24); D_0 256 + D_1 and D_2 256 + D_3 stay below 2^31
         long long acc[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const uint32_t* fh = f + h * DIG;
           const int t01 = small_float_int(fh[0]) * 256 + small_float_int(fh[1]);
-          const int t23 = float_int(__uint_as_float(fh[2])) * 256 + float_int(__uint_as_float(fh[3]));
+          const int t23 = __float2int_rz(__uint_as_float(fh[2])) * 256 +
+                          __float2int_rz(__uint_as_float(fh[3]));
           acc[h] = ((long long)t01 << 32) + ((long long)t23 << 16) +
-                   ((long long)float_int(__uint_as_float(fh[4])) << 8) +
-                   (long long)float_int(__uint_as_float(fh[5]));
+                   ((long long)__float2int_rz(__uint_as_float(fh[4])) << 8) +
+                   (long long)__float2int_rz(__uint_as_float(fh[5]));
         }
         // sum_r x w = 2^(E_x + E_w - 55) acc; the two halves on the larger
         // scale (the other truncated at its unit, 2^-55 of that segment's
