@@ -477,6 +477,8 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   c->stats.cg_iters_max = (int)r.res[3];
   c->stats.cg_iters_mean = r.res[4];
   if (exx) *exx = r.res[0];
+  if (r.st & SEA_FLAG_WAIT)
+    return sea_fail(c, SEA_ERR_CUDA, "a tensor-core completion wait timed out (warm start)");
   if (r.st & SEA_FLAG_TIMEOUT)
     return sea_fail(c, SEA_ERR_TIMEOUT,
                     "the CG time budget (timeout_ms) was spent before every pair was solved");

@@ -48,6 +48,7 @@
 #include <cuda.h>
 
 #include "sea_internal.cuh"
+#include "tcgen05.cuh"
 
 namespace sea {
 namespace {
@@ -66,73 +67,6 @@ constexpr uint32_t SMEM_W = 2 * W_HALF;         // 48 KB (both halves)
 constexpr size_t GT_SMEM = SMEM_A + 2 * SMEM_W + 128;  // A digits, two W buffers
 constexpr uint32_t TMEM_HALF = DIG * NBLK;      // accumulator columns per half tile
 constexpr uint32_t TMEM_COLS = 512;             // 2 x 192 columns used
-constexpr long long WAIT_CYCLES = 2000000000LL; // ~1 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: K-major, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, M = 128, N = n.
-__device__ __forceinline__ uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MBLK >> 4) << 24);
-}
-
-// The same with FP16 A and B (the contraction's digits).
-__device__ __forceinline__ uint32_t idesc_f16(int n) {
-  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MBLK >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait for completion `parity` of the barrier.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  return true;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// One FP32 column of the warp's 32 tensor-memory lanes (no wait).
-__device__ __forceinline__ uint32_t tmem_ld1(uint32_t addr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(addr));
-  return r;
-}
-__device__ __forceinline__ void tmem_wait_ld() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
                "r"(valid ? 16 : 0));
@@ -446,8 +380,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1)
     for (int q = 0; q < KH / 16; ++q)
 #pragma unroll
       for (int k = 0; k < DIG; ++k)
-        mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A_PLANE + q * 2 * A_LBO) >> 4),
-                 w0 + ((q * 2 * lbo) >> 4), idesc_f16((DIG - k) * P), (k > 0 || q > 0) ? 1u : 0u);
+        mma_kf16(dcol + (uint32_t)(k * P), a0 + ((k * A_PLANE + q * 2 * A_LBO) >> 4),
+                 w0 + ((q * 2 * lbo) >> 4), idesc_kf16((DIG - k) * P, MBLK, false), (k > 0 || q > 0) ? 1u : 0u);
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
         : "memory");
@@ -719,8 +653,8 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
             const int q = 2 * kh + qq;
 #pragma unroll
             for (int k = 0; k < DIG; ++k)
-              mma_bf16(dcol + (uint32_t)(k * P), a0 + ((k * A2_PLANE + q * 2 * A2_LBO) >> 4),
-                       w0 + ((q * 2 * lbo) >> 4), idesc_f16((DIG - k) * P),
+              mma_kf16(dcol + (uint32_t)(k * P), a0 + ((k * A2_PLANE + q * 2 * A2_LBO) >> 4),
+                       w0 + ((q * 2 * lbo) >> 4), idesc_kf16((DIG - k) * P, MBLK, false),
                        (k > 0 || q > 0) ? 1u : 0u);
           }
           asm volatile(
@@ -1102,14 +1036,6 @@ __global__ void __launch_bounds__(MBLK)
   }
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(addr));
-}
-
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
                                           uint32_t bar) {
   asm volatile(
@@ -1285,7 +1211,7 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
                 const uint64_t a =
                     sdesc(a_base + buf * XA_TILE + qq * XA_STEP + k * XA_BLOCK, XA_LBO, 128);
                 const uint64_t b = sdesc(b_base + qq * XB_STEP + c * XB_CHUNK, XB_LBO, 128);
-                mma_bf16(dcol + (uint32_t)(k * XN), a, b, idesc_bf16((DIG - k) * XN),
+                mma_kf16(dcol + (uint32_t)(k * XN), a, b, idesc_kf16((DIG - k) * XN, MBLK, true),
                          (k > 0 || qq > 0) ? 1u : 0u);
               }
             asm volatile(

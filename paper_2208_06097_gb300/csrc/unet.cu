@@ -14,9 +14,13 @@
 // concat skip 2, conv3(6c -> 2c) relu, conv3(2c -> 2c) relu, nearest up 2,
 // concat skip 1, conv3(3c -> c) relu, conv3(c -> c) relu, conv1(c -> 1).
 // conv3 = 3x3x3 with zero padding.  Weights are BF16 (an FP32 master copy
-// for the optimizer), activations and accumulation FP32.  Training: masked
-// mean squared error against the CG solution, Adam.  All reductions run in
-// a fixed order (no floating-point atomics), so training is deterministic.
+// for the optimizer), activations FP32.  The 3x3x3 convolutions of the
+// forward pass and their data gradients run on the tensor cores (tcgen05,
+// kind::f16, BF16 operands, FP32 accumulation in tensor memory) as an
+// implicit GEMM; each FP32 activation enters as the exact sum of three BF16
+// terms, so the products are those of the FP32 values.  Training: masked
+// mean squared error against the CG solution, Adam.  All reductions run in a
+// fixed order (no floating-point atomics), so training is deterministic.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -26,6 +30,7 @@
 #include <vector>
 
 #include "sea_internal.cuh"
+#include "tcgen05.cuh"
 
 #define UN_P 32                         // patch edge
 #define UN_V (UN_P * UN_P * UN_P)       // patch points
@@ -35,68 +40,228 @@ namespace {
 
 __device__ __forceinline__ int vox(int z, int y, int x, int D) { return (z * D + y) * D + x; }
 
-// y[b][yc0 + co][p] = act(bias[co] + sum_ci sum_k w[co][ci][k] x[b][xc0 + ci][p + off(k)])
-// over a D^3 volume.  CTA: 4 x 8 x 8 output voxels (one per thread) x 8
-// output channels; per input channel the 6 x 10 x 10 input halo and the
-// 8 x 27 weights sit in shared memory.
-#define CV_CO 8
-__global__ void __launch_bounds__(256)
-    k_conv3(const float* __restrict__ x, int xC, int xc0, int Cin,
-            const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
-            float* __restrict__ y, int yC, int yc0, int Cout, int D, int relu) {
-  __shared__ float sx[6][10][10];
-  __shared__ float sw[CV_CO][27];
-  const int tiles_x = (D + 7) / 8, tiles_y = (D + 7) / 8;
-  const int tile = blockIdx.x;
-  const int tx0 = (tile % tiles_x) * 8, ty0 = ((tile / tiles_x) % tiles_y) * 8,
-            tz0 = (tile / (tiles_x * tiles_y)) * 4;
-  const int co0 = blockIdx.y * CV_CO, b = blockIdx.z;
-  const int lx = threadIdx.x % 8, ly = (threadIdx.x / 8) % 8, lz = threadIdx.x / 64;
-  const int ox = tx0 + lx, oy = ty0 + ly, oz = tz0 + lz;
-  float acc[CV_CO];
-#pragma unroll
-  for (int c = 0; c < CV_CO; ++c) acc[c] = (bias && co0 + c < Cout) ? bias[co0 + c] : 0.f;
-  const size_t V = (size_t)D * D * D;
-  for (int ci = 0; ci < Cin; ++ci) {
-    __syncthreads();
-    const float* xs = x + ((size_t)b * xC + xc0 + ci) * V;
-    for (int q = threadIdx.x; q < 600; q += blockDim.x) {
-      const int hx = q % 10, hy = (q / 10) % 10, hz = q / 100;
-      const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-      sx[hz][hy][hx] = (gx >= 0 && gx < D && gy >= 0 && gy < D && gz >= 0 && gz < D)
-                           ? xs[vox(gz, gy, gx, D)]
-                           : 0.f;
-    }
-    for (int q = threadIdx.x; q < CV_CO * 27; q += blockDim.x) {
-      const int c = q / 27, k = q % 27;
-      sw[c][k] = co0 + c < Cout ? __bfloat162float(w[((size_t)(co0 + c) * Cin + ci) * 27 + k]) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 27; ++k) {
-      const float xv = sx[lz + k / 9][ly + (k / 3) % 3][lx + k % 3];
-#pragma unroll
-      for (int c = 0; c < CV_CO; ++c) acc[c] = fmaf(sw[c][k], xv, acc[c]);
-    }
-  }
-  if (ox >= D || oy >= D || oz >= D) return;
-#pragma unroll
-  for (int c = 0; c < CV_CO; ++c) {
-    if (co0 + c >= Cout) break;
-    float v = acc[c];
-    if (relu) v = fmaxf(v, 0.f);
-    y[((size_t)b * yC + yc0 + co0 + c) * V + vox(oz, oy, ox, D)] = v;
-  }
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution on the tensor cores (implicit GEMM).
+//
+//   y[b][yc0 + co][p] = act(bias[co] + sum_ci sum_k W[co][ci][k] x[b][xc0 + ci][p + off(k)])
+//
+// CTA = one tile of 8 (x) x 16 (y) x 1 (z) output points of one batch
+// element (M = 128 rows: row m = y 8 + x) and up to 128 output channels
+// (N).  The input is staged per chunk of 16 channels as the haloed box
+// 10 x 18 x 3 around the tile, point after point (row r = (hz 18 + hy) 10 +
+// hx, 16 bytes = 8 channels per row, one plane per channel octet), so that
+// the A operand of offset k = (kz, ky, kx) is the same layout shifted by
+// (kz 180 + ky 10 + kx) rows: core matrices of 8 x-consecutive points
+// (rows 16 B apart), the next y at 160 B, the next octet one plane further.
+// No im2col copy is made; each chunk costs 27 offsets x 3 terms MMAs (M =
+// 128, K = 16, N = the padded channel count) into one FP32 accumulator in
+// tensor memory.  Each FP32 value v enters as h + m + l, three BF16 terms
+// (h = bf16(v), m = bf16(v - h), l = bf16(v - h - m): exact, every
+// difference is representable), so every product is exact and only the FP32
+// accumulation rounds.  Weights come prepared per chunk (k_conv_wprep) in
+// the B layout [k][octet][8-row group of channels][8 x 8].  Points outside
+// the volume read zeros; rows beyond D (the 8^3 level uses half a tile) are
+// not stored.  The wait for the MMAs is bounded (SEA_FLAG_WAIT).
+// ---------------------------------------------------------------------------
+#define CT_THREADS 256
+#define CT_HX 10
+#define CT_HY 18
+#define CT_ROWS (CT_HX * CT_HY * 3)             // 540 haloed points
+#define CT_PLANE (CT_ROWS * 16)                 // one channel octet of the box, bytes
+#define CT_XBYTES (3 * 2 * CT_PLANE)            // three terms x two octets
+#define CT_NBLK 128                             // output channels per CTA at most
+
+struct ConvTc {
+  const float* x;
+  int xC, xc0, Cin;
+  const __nv_bfloat16* wp;  // prepared weights of the layer (k_conv_wprep)
+  int npad;                 // output channels padded to 16 (the prepared layout's N)
+  const float* bias;        // or null
+  float* y;
+  int yC, yc0, Cout;
+  int D, relu;
+  unsigned* status;
+};
+
+// Prepared weights: wp[chunk][k][o][g][r][c] = W'[co = 8 g + r][ci = 16 chunk
+// + 8 o + c][k] (zero beyond Cout', Cin'), with W' = W (forward) or, for
+// the data gradient (transpose = 1), W'[co'][ci'][k] = W[ci'][co'][26 - k]
+// (Cout' = cin, Cin' = cout of the layer).  w: [cout][cin][27] BF16.
+__global__ void k_conv_wprep(const __nv_bfloat16* __restrict__ w, int cout, int cin, int transpose,
+                             int npad, __nv_bfloat16* __restrict__ wp) {
+  const int Co = transpose ? cin : cout, Ci = transpose ? cout : cin;
+  const int ng = npad / 8, nch = (Ci + 15) / 16;
+  const long long total = (long long)nch * 27 * 2 * ng * 64;
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int c = (int)(q & 7), r = (int)((q >> 3) & 7);
+  long long t = q >> 6;
+  const int g = (int)(t % ng);
+  t /= ng;
+  const int o = (int)(t & 1);
+  t >>= 1;
+  const int k = (int)(t % 27), ch = (int)(t / 27);
+  const int co = 8 * g + r, ci = 16 * ch + 8 * o + c;
+  __nv_bfloat16 v = __float2bfloat16(0.f);
+  if (co < Co && ci < Ci)
+    v = transpose ? w[((size_t)ci * cin + co) * 27 + (26 - k)] : w[((size_t)co * cin + ci) * 27 + k];
+  wp[q] = v;
 }
 
-// wT[ci][co][k] = w[co][ci][26 - k]: the weights of the transposed
-// (data-gradient) convolution.
-__global__ void k_conv3_wT(const __nv_bfloat16* __restrict__ w, int Cout, int Cin,
-                           __nv_bfloat16* __restrict__ wT) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= Cout * Cin * 27) return;
-  const int k = q % 27, ci = (q / 27) % Cin, co = q / (27 * Cin);
-  wT[((size_t)ci * Cout + co) * 27 + (26 - k)] = w[q];
+__device__ __forceinline__ void split3_bf16(float v0, float v1, uint32_t& h, uint32_t& m,
+                                            uint32_t& l) {
+  const __nv_bfloat162 H = __floats2bfloat162_rn(v0, v1);
+  const float r0 = v0 - __low2float(H), r1 = v1 - __high2float(H);
+  const __nv_bfloat162 Mm = __floats2bfloat162_rn(r0, r1);
+  const __nv_bfloat162 L = __floats2bfloat162_rn(r0 - __low2float(Mm), r1 - __high2float(Mm));
+  h = *reinterpret_cast<const uint32_t*>(&H);
+  m = *reinterpret_cast<const uint32_t*>(&Mm);
+  l = *reinterpret_cast<const uint32_t*>(&L);
+}
+
+__global__ void __launch_bounds__(CT_THREADS) k_conv3_tc(ConvTc P) {
+  extern __shared__ unsigned char ct_raw[];
+  unsigned char* sX = ct_raw + ((128 - (smem_addr(ct_raw) & 127)) & 127);
+  unsigned char* sW = sX + CT_XBYTES;
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ uint32_t tbase;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = P.D, ntx = D / 8, nty = (D + 15) / 16;
+  int t = blockIdx.x;
+  const int x0 = (t % ntx) * 8;
+  t /= ntx;
+  const int y0 = (t % nty) * 16, z0 = t / nty;
+  const int b = blockIdx.y, n0 = blockIdx.z * CT_NBLK;
+  const int nb = min(CT_NBLK, P.npad - n0);  // this CTA's N (a multiple of 16)
+  const int ngb = nb / 8, ng = P.npad / 8;
+  const uint32_t ncols = nb <= 32 ? 32u : (nb <= 64 ? 64u : 128u);
+  const uint32_t mb = smem_addr(&bar);
+  if (warp == 0) tmem_alloc(&tbase, ncols);
+  if (tid == 0) {
+    mbar_init(mb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  const size_t V = (size_t)D * D * D;
+  const int nch = (P.Cin + 15) / 16;
+  const uint32_t idesc = idesc_kf16(nb, 128, true);
+  const uint32_t ax = smem_addr(sX), aw = smem_addr(sW);
+  // Thread 0 issues the MMAs and alone waits for their completion (phase:
+  // parity of the next completion); the block learns the outcome through
+  // s_fail after a barrier.
+  uint32_t phase = 0;
+  bool pending = false;  // MMAs committed and not yet waited for (uniform)
+  for (int ch = 0; ch < nch; ++ch) {
+    if (pending) {  // the previous chunk's MMAs read the buffers about to be replaced
+      if (tid == 0) {
+        if (mbar_wait(mb, phase))
+          phase ^= 1;
+        else
+          s_fail = 1;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      pending = false;
+    }
+    // the haloed input of channels 16 ch .. 16 ch + 15, three BF16 terms
+    for (int it = tid; it < 2 * CT_ROWS; it += CT_THREADS) {
+      const int o = it / CT_ROWS, row = it - o * CT_ROWS;
+      const int hx = row % CT_HX, hy = (row / CT_HX) % CT_HY, hz = row / (CT_HX * CT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+      const bool in = gx >= 0 && gx < D && gy >= 0 && gy < D && gz >= 0 && gz < D;
+      const size_t pofs = in ? ((size_t)gz * D + gy) * D + gx : 0;
+      uint32_t w[3][4];
+#pragma unroll
+      for (int c2 = 0; c2 < 4; ++c2) {
+        const int ci = 16 * ch + 8 * o + 2 * c2;
+        const float v0 = (in && ci < P.Cin) ? P.x[((size_t)b * P.xC + P.xc0 + ci) * V + pofs] : 0.f;
+        const float v1 =
+            (in && ci + 1 < P.Cin) ? P.x[((size_t)b * P.xC + P.xc0 + ci + 1) * V + pofs] : 0.f;
+        split3_bf16(v0, v1, w[0][c2], w[1][c2], w[2][c2]);
+      }
+#pragma unroll
+      for (int t3 = 0; t3 < 3; ++t3)
+        *reinterpret_cast<uint4*>(sX + (t3 * 2 + o) * CT_PLANE + row * 16) =
+            make_uint4(w[t3][0], w[t3][1], w[t3][2], w[t3][3]);
+    }
+    // this chunk's weights for output channels n0 .. n0 + nb: per (k, octet)
+    // a run of ngb 128-byte core matrices
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(P.wp) + (size_t)ch * 27 * 2 * ng * 8;
+      uint4* dst = reinterpret_cast<uint4*>(sW);
+      const int per = ngb * 8;  // uint4 per (k, octet)
+      for (int q = tid; q < 27 * 2 * per; q += CT_THREADS) {
+        const int ko = q / per, e = q - ko * per;
+        dst[q] = src[(size_t)ko * ng * 8 + (n0 / 8) * 8 + e];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+#pragma unroll 1
+      for (int k = 0; k < 27; ++k) {
+        const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+        const uint32_t aoff = (uint32_t)((kz * CT_HX * CT_HY + ky * CT_HX + kx) * 16);
+        const uint64_t bd = sdesc(aw + (uint32_t)(k * 2 * ngb * 128), (uint32_t)(ngb * 128), 128);
+#pragma unroll
+        for (int t3 = 0; t3 < 3; ++t3) {
+          const uint64_t ad = sdesc(ax + (uint32_t)(t3 * 2 * CT_PLANE) + aoff, CT_PLANE, CT_HX * 16);
+          mma_kf16(tmem, ad, bd, idesc, (ch > 0 || k > 0 || t3 > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(mb);
+    }
+    pending = true;
+  }
+  if (pending && !s_fail && tid == 0) {
+    if (mbar_wait(mb, phase))
+      pending = false;
+    else
+      s_fail = 1;
+  }
+  __syncthreads();
+  const bool ok = !s_fail;
+  if (!ok) {
+    if (tid == 0) {
+      if (pending) mbar_wait(mb, phase);  // once more, bounded, before freeing
+      atomicOr(P.status, SEA_FLAG_WAIT);
+    }
+  } else {
+    tc_fence_after();
+    // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (row m = lane point),
+    // 8-column groups split between warps w < 4 and w >= 4
+    const int m = 32 * (warp & 3) + lane;
+    const int oy = y0 + (m >> 3), ox = x0 + (m & 7);
+    const bool valid = oy < D;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int c8 = warp >> 2; c8 < ngb; c8 += 2) {
+      uint32_t r[8];
+      tmem_ld8(lane_base + (uint32_t)(c8 * 8), r);
+      tmem_wait_ld();
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int co = n0 + c8 * 8 + e;
+        if (valid && co < P.Cout) {
+          float v = __uint_as_float(r[e]) + (P.bias ? P.bias[co] : 0.f);
+          if (P.relu) v = fmaxf(v, 0.f);
+          P.y[((size_t)b * P.yC + P.yc0 + co) * V + ((size_t)z0 * D + oy) * D + ox] = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, ncols);
+  }
 }
 
 // dw[co][ci][k] = sum_b sum_p dy[b][co][p] x[b][xc0 + ci][p + off(k)], and
@@ -381,6 +546,11 @@ __global__ void k_unpatch(const PairInfo* __restrict__ pinfo, const long long* _
 struct UnLayer {
   int cin, cout, k;           // k = 3 (3x3x3) or 1
   long long w_off, b_off;     // offsets in the parameter array
+  // tensor-core layouts of a 3x3x3 layer's BF16 weights (k_conv_wprep):
+  // forward (N = cout padded to 16) and transposed for the data gradient
+  // (N = cin padded to 16); offsets in sea_unet::wp
+  int npad_f = 0, npad_t = 0;
+  long long wpf_off = 0, wpt_off = 0;
 };
 
 struct sea_unet {
@@ -389,7 +559,10 @@ struct sea_unet {
   std::vector<UnLayer> L;
   long long nparam = 0;
   float *master = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
-  __nv_bfloat16 *wb = nullptr, *wT = nullptr;
+  __nv_bfloat16 *wb = nullptr, *wp = nullptr;  // BF16 weights; their tensor-core layouts
+  long long nwp = 0;
+  unsigned* status = nullptr;   // device status word of the model's own calls
+  unsigned* st_use = nullptr;   // the word the kernels report to (the model's or a context's)
   int adam_t = 0;
   // activations and gradients for a batch of up to bmax patches
   float *e1a = nullptr, *cat1 = nullptr, *p1 = nullptr, *e2a = nullptr, *cat2 = nullptr,
@@ -419,23 +592,75 @@ sea_status un_fail(sea_unet* u, sea_status st, const char* msg) {
 
 unsigned grid1(size_t n, unsigned t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Synchronize the model's stream and check its status word (a bounded
+// tensor-core wait that expired): the word is cleared for the next call.
+sea_status un_sync(sea_unet* u) {
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, u->status, sizeof(unsigned), cudaMemcpyDeviceToHost, u->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(u->stream);
+  if (e != cudaSuccess) return un_fail(u, SEA_ERR_CUDA, cudaGetErrorString(e));
+  if (st & SEA_FLAG_WAIT) {
+    cudaMemsetAsync(u->status, 0, sizeof(unsigned), u->stream);
+    return un_fail(u, SEA_ERR_CUDA, "a tensor-core completion wait timed out");
+  }
+  return SEA_OK;
+}
+
+int pad16(int n) { return (n + 15) / 16 * 16; }
+
+size_t conv_smem(int npad) {
+  return 128 + CT_XBYTES + (size_t)27 * 2 * (std::min(npad, CT_NBLK) / 8) * 128;
+}
+
+// Tensor-core layouts of every 3x3x3 layer's BF16 weights (after any change
+// of u->wb).
+void prep_weights(sea_unet* u) {
+  for (const UnLayer& a : u->L) {
+    if (a.k != 3) continue;
+    const long long nf = (long long)pad16(a.cin) * a.npad_f * 27;
+    sea::k_conv_wprep<<<grid1(nf), 256, 0, u->stream>>>(u->wb + a.w_off, a.cout, a.cin, 0, a.npad_f,
+                                                        u->wp + a.wpf_off);
+    const long long nt = (long long)pad16(a.cout) * a.npad_t * 27;
+    sea::k_conv_wprep<<<grid1(nt), 256, 0, u->stream>>>(u->wb + a.w_off, a.cout, a.cin, 1, a.npad_t,
+                                                        u->wp + a.wpt_off);
+  }
+}
+
+// y (slice yc0 of yC channels) = act(conv3 of x's slice) for layer l, or for
+// transpose = true the data gradient: the transposed convolution of the
+// layer (cin and cout exchanged, flipped taps), no bias, no activation.
+void conv3_tc(sea_unet* u, int l, bool transpose, const float* x, int xC, int xc0, float* y,
+              int yC, int yc0, int D, int B, int relu) {
+  const UnLayer& a = u->L[l];
+  sea::ConvTc P;
+  P.x = x;
+  P.xC = xC;
+  P.xc0 = xc0;
+  P.Cin = transpose ? a.cout : a.cin;
+  P.wp = u->wp + (transpose ? a.wpt_off : a.wpf_off);
+  P.npad = transpose ? a.npad_t : a.npad_f;
+  P.bias = transpose ? nullptr : u->master + a.b_off;
+  P.y = y;
+  P.yC = yC;
+  P.yc0 = yc0;
+  P.Cout = transpose ? a.cin : a.cout;
+  P.D = D;
+  P.relu = relu;
+  P.status = u->st_use;
+  const int tiles = (D / 8) * ((D + 15) / 16) * D;
+  const int nzb = (P.npad + CT_NBLK - 1) / CT_NBLK;
+  sea::k_conv3_tc<<<dim3(tiles, B, nzb), CT_THREADS, conv_smem(P.npad), u->stream>>>(P);
+}
+
 void conv3(sea_unet* u, const float* x, int xC, int xc0, int l, float* y, int yC, int yc0, int D,
            int B, int relu) {
-  const UnLayer& a = u->L[l];
-  const int tiles = ((D + 7) / 8) * ((D + 7) / 8) * ((D + 3) / 4);
-  sea::k_conv3<<<dim3(tiles, (a.cout + CV_CO - 1) / CV_CO, B), 256, 0, u->stream>>>(
-      x, xC, xc0, a.cin, u->wb + a.w_off, u->master + a.b_off, y, yC, yc0, a.cout, D, relu);
+  conv3_tc(u, l, false, x, xC, xc0, y, yC, yc0, D, B, relu);
 }
 
 // dx (slice of a tensor with xC channels) = transposed convolution of dy
 void conv3_dx(sea_unet* u, int l, const float* dy, int dyC, float* dx, int xC, int xc0, int D,
               int B) {
-  const UnLayer& a = u->L[l];
-  sea::k_conv3_wT<<<grid1((size_t)a.cout * a.cin * 27), 256, 0, u->stream>>>(u->wb + a.w_off, a.cout,
-                                                                             a.cin, u->wT);
-  const int tiles = ((D + 7) / 8) * ((D + 7) / 8) * ((D + 3) / 4);
-  sea::k_conv3<<<dim3(tiles, (a.cin + CV_CO - 1) / CV_CO, B), 256, 0, u->stream>>>(
-      dy, dyC, 0, a.cout, u->wT, nullptr, dx, xC, xc0, a.cin, D, 0);
+  conv3_tc(u, l, true, dy, dyC, 0, dx, xC, xc0, D, B, 0);
 }
 
 void conv3_dw(sea_unet* u, int l, const float* x, int xC, int xc0, const float* dy, int dyC, int D,
@@ -524,11 +749,7 @@ void backward(sea_unet* u, const float* in, const float* tgt, int B) {
     sea::k_conv3_dw<<<a.cout * a.cin, 256, 0, u->stream>>>(u->e2a, 2 * c, 0, a.cin, u->gcat2, 6 * c,
                                                             4 * c, a.cout, 16, B, u->grad + a.w_off,
                                                             u->grad + a.b_off);
-    sea::k_conv3_wT<<<grid1((size_t)a.cout * a.cin * 27), 256, 0, u->stream>>>(u->wb + a.w_off,
-                                                                               a.cout, a.cin, u->wT);
-    const int tiles = 2 * 2 * 4;
-    sea::k_conv3<<<dim3(tiles, (a.cin + CV_CO - 1) / CV_CO, B), 256, 0, u->stream>>>(
-        u->gcat2, 6 * c, 4 * c, a.cout, u->wT, nullptr, u->g16a, 2 * c, 0, a.cin, 16, 0);
+    conv3_tc(u, 3, true, u->gcat2, 6 * c, 4 * c, u->g16a, 2 * c, 0, 16, B, 0);
   }
   // e2a = relu(conv2(p1))
   relu_bwd(u, u->g16a, 2 * c, 0, u->e2a, 2 * c, 0, 2 * c, 16, B);
@@ -544,11 +765,7 @@ void backward(sea_unet* u, const float* in, const float* tgt, int B) {
     sea::k_conv3_dw<<<a.cout * a.cin, 256, 0, u->stream>>>(u->e1a, c, 0, a.cin, u->gcat1, 3 * c,
                                                             2 * c, a.cout, 32, B, u->grad + a.w_off,
                                                             u->grad + a.b_off);
-    sea::k_conv3_wT<<<grid1((size_t)a.cout * a.cin * 27), 256, 0, u->stream>>>(u->wb + a.w_off,
-                                                                               a.cout, a.cin, u->wT);
-    const int tiles = 4 * 4 * 8;
-    sea::k_conv3<<<dim3(tiles, (a.cin + CV_CO - 1) / CV_CO, B), 256, 0, u->stream>>>(
-        u->gcat1, 3 * c, 2 * c, a.cout, u->wT, nullptr, u->g32a, c, 0, a.cin, 32, 0);
+    conv3_tc(u, 1, true, u->gcat1, 3 * c, 2 * c, u->g32a, c, 0, 32, B, 0);
   }
   // e1a = relu(conv0(in))
   relu_bwd(u, u->g32a, c, 0, u->e1a, c, 0, c, 32, B);
@@ -576,7 +793,8 @@ void sea_unet_destroy(sea_unet* u) {
   for (float* p : fs)
     if (p) cudaFree(p);
   if (u->wb) cudaFree(u->wb);
-  if (u->wT) cudaFree(u->wT);
+  if (u->wp) cudaFree(u->wp);
+  if (u->status) cudaFree(u->status);
   if (u->dloss) cudaFree(u->dloss);
   if (u->pscale) cudaFree(u->pscale);
   delete u;
@@ -597,7 +815,7 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
   const int dims[11][3] = {{2, c, 3},         {c, c, 3},         {c, 2 * c, 3},     {2 * c, 2 * c, 3},
                            {2 * c, 4 * c, 3}, {4 * c, 4 * c, 3}, {6 * c, 2 * c, 3}, {2 * c, 2 * c, 3},
                            {3 * c, c, 3},     {c, c, 3},         {c, 1, 1}};
-  long long off = 0, maxw = 0;
+  long long off = 0;
   for (auto& d : dims) {
     UnLayer l;
     l.cin = d[0];
@@ -608,7 +826,14 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
     off += nw;
     l.b_off = off;
     off += l.cout;
-    maxw = std::max(maxw, nw);
+    if (l.k == 3) {
+      l.npad_f = pad16(l.cout);
+      l.npad_t = pad16(l.cin);
+      l.wpf_off = u->nwp;
+      u->nwp += (long long)pad16(l.cin) * l.npad_f * 27;
+      l.wpt_off = u->nwp;
+      u->nwp += (long long)pad16(l.cout) * l.npad_t * 27;
+    }
     u->L.push_back(l);
   }
   u->nparam = off;
@@ -624,7 +849,8 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
   const size_t B = u->bmax, V32 = UN_V, V16 = V32 / 8, V8 = V16 / 8;
   bool ok = alloc((void**)&u->master, off * 4) && alloc((void**)&u->grad, off * 4) &&
             alloc((void**)&u->am, off * 4) && alloc((void**)&u->av, off * 4) &&
-            alloc((void**)&u->wb, off * 2) && alloc((void**)&u->wT, maxw * 2) &&
+            alloc((void**)&u->wb, off * 2) && alloc((void**)&u->wp, u->nwp * 2) &&
+            alloc((void**)&u->status, 16) &&
             alloc((void**)&u->e1a, B * c * V32 * 4) && alloc((void**)&u->cat1, B * 3 * c * V32 * 4) &&
             alloc((void**)&u->p1, B * c * V16 * 4) && alloc((void**)&u->e2a, B * 2 * c * V16 * 4) &&
             alloc((void**)&u->cat2, B * 6 * c * V16 * 4) && alloc((void**)&u->p2, B * 2 * c * V8 * 4) &&
@@ -648,7 +874,12 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
     return SEA_ERR_CUDA;
   }
   sea::k_to_bf16<<<grid1(off), 256, 0, u->stream>>>(u->master, off, u->wb);
-  if (cudaStreamSynchronize(u->stream) != cudaSuccess) {
+  prep_weights(u);
+  u->st_use = u->status;
+  if (cudaMemsetAsync(u->status, 0, 16, u->stream) != cudaSuccess ||
+      cudaFuncSetAttribute(sea::k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)conv_smem(CT_NBLK)) != cudaSuccess ||
+      cudaStreamSynchronize(u->stream) != cudaSuccess) {
     sea_unet_destroy(u);
     return SEA_ERR_CUDA;
   }
@@ -664,6 +895,7 @@ sea_status sea_unet_weights(sea_unet* u, float* w, int set) {
     e = cudaMemcpyAsync(u->master, w, bytes, cudaMemcpyHostToDevice, u->stream);
     if (e == cudaSuccess) {
       sea::k_to_bf16<<<grid1(u->nparam), 256, 0, u->stream>>>(u->master, u->nparam, u->wb);
+      prep_weights(u);
       e = cudaGetLastError();
     }
   } else {
@@ -690,8 +922,7 @@ sea_status sea_unet_forward(sea_unet* u, const float* in, int B, float* out, int
                         u->stream) != cudaSuccess)
       return un_fail(u, SEA_ERR_CUDA, "copy output");
   }
-  const cudaError_t e = cudaStreamSynchronize(u->stream);
-  return e == cudaSuccess ? SEA_OK : un_fail(u, SEA_ERR_CUDA, cudaGetErrorString(e));
+  return un_sync(u);
 }
 
 sea_status sea_unet_loss_grad(sea_unet* u, const float* in, const float* target, int B,
@@ -720,8 +951,8 @@ sea_status sea_unet_loss_grad(sea_unet* u, const float* in, const float* target,
   double l = 0.0;
   cudaMemcpyAsync(&l, u->dloss, 8, cudaMemcpyDeviceToHost, u->stream);
   if (grad) cudaMemcpyAsync(grad, u->grad, (size_t)u->nparam * 4, cudaMemcpyDeviceToHost, u->stream);
-  const cudaError_t e = cudaStreamSynchronize(u->stream);
-  if (e != cudaSuccess) return un_fail(u, SEA_ERR_CUDA, cudaGetErrorString(e));
+  const sea_status st = un_sync(u);
+  if (st != SEA_OK) return st;
   if (loss) *loss = l;
   return SEA_OK;
 }
@@ -792,10 +1023,11 @@ sea_status sea_unet_train(sea_unet* u, int steps, int batch, double lr, int seed
     const float c1 = 1.f - std::pow(b1, (float)u->adam_t), c2 = 1.f - std::pow(b2, (float)u->adam_t);
     sea::k_adam<<<grid1(u->nparam), 256, 0, u->stream>>>(u->master, u->grad, u->am, u->av, u->nparam,
                                                         (float)lr, b1, b2, 1e-8f, c1, c2, u->wb);
+    prep_weights(u);
   }
   if (steps > 0) cudaMemcpyAsync(&l, u->dloss, 8, cudaMemcpyDeviceToHost, u->stream);
-  const cudaError_t e = cudaStreamSynchronize(u->stream);
-  if (e != cudaSuccess) return un_fail(u, SEA_ERR_CUDA, cudaGetErrorString(e));
+  const sea_status st = un_sync(u);
+  if (st != SEA_OK) return st;
   if (last_loss) *last_loss = l;
   return SEA_OK;
 }
@@ -826,9 +1058,10 @@ cudaError_t launch_warm_start(sea_ctx* c) {
   }
   if (!u->pin && !alloc((void**)&u->pin, (size_t)u->bmax * 3 * UN_V * 4))
     return cudaErrorMemoryAllocation;
-  // The model runs on the context's stream here.
+  // The model runs on the context's stream here and reports to its status word.
   cudaStream_t saved = u->stream;
   u->stream = c->stream;
+  u->st_use = (unsigned*)c->status.p;
   for (int p0 = 0; p0 < c->P; p0 += B) {
     const int np = std::min(B, c->P - p0);
     k_patch<<<np, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p + p0,
@@ -841,6 +1074,7 @@ cudaError_t launch_warm_start(sea_ctx* c) {
     c->launches += 2 + 15;
   }
   u->stream = saved;
+  u->st_use = u->status;
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // smooth the guesses' high-frequency error before the CG
