@@ -415,19 +415,101 @@ def run_ours(args, ws, rank, local):
     return line
 
 
-def batched_workload(n_cfg=16, seed=3000):
-    """Independent configurations for the batched form: (H2O)n, n ~ U{8..32},
-    density ~ U[0.4, 1.7] g/cm^3, grid spacing ~0.13 A (0.2457 bohr)."""
+def batched_workload(n_cfg=64, seed=3000):
+    """The batched form's workload: n_cfg independent configurations (H2O)n,
+    n ~ U{32..128}, density ~ U[0.4, 1.7] g/cm^3, grid spacing ~0.13 A
+    (0.2457 bohr).  Returns (n_mol, L in angstrom, grid points per axis,
+    seed) per configuration."""
     from paper_2208_06097_gb300 import synth
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n_cfg):
-        n_mol = int(rng.integers(8, 33))
+        n_mol = int(rng.integers(32, 129))
         dens = float(rng.uniform(0.4, 1.7))
         L = (n_mol * 18.015 / 0.60221408 / dens) ** (1.0 / 3.0)  # angstrom
         grid = max(16, int(round(L * synth.ANGSTROM / 0.2457)))
-        out.append(synth.make_waters(n_mol, L, grid, seed=seed + 1 + k))
+        out.append((n_mol, L, grid, seed + 1 + k))
     return out
+
+
+def _groups(work, budget_bytes):
+    """Consecutive groups of configurations whose device arrays (the
+    context's orbitals and W, the output: 3 x n_orb x grid^3 doubles) fit the
+    budget."""
+    groups, cur, used = [], [], 0
+    for w in work:
+        b = 3 * 4 * w[0] * w[2] ** 3 * 8
+        if cur and used + b > budget_bytes:
+            groups.append(cur)
+            cur, used = [], 0
+        cur.append(w)
+        used += b
+    if cur:
+        groups.append(cur)
+    return groups
+
+
+def run_batched(args, sea, torch, dev, budget_gb=140.0):
+    """Batched form vs one call per configuration, V_xx application only, on
+    the 64-configuration workload; orbitals generated on the device.  The
+    configurations go through sea_apply_vxx_batch in groups that fit the
+    device (each group one batched call: autotuned, graph-captured, then
+    replayed); the times of the groups add up."""
+    from paper_2208_06097_gb300 import synth
+    work = batched_workload()
+    groups = _groups(work, budget_gb * 1e9)
+    stream = torch.cuda.Stream(device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    t_batch = t_seq = t_gen = 0.0
+    pairs = orbitals = 0
+    tuned = []
+    for grp in groups:
+        tg = time.perf_counter()
+        ctxs, outs = [], []
+        for n_mol, L, g, seed in grp:
+            phi, cell, grid = synth.make_waters_device(n_mol, L, g, seed, dev)
+            c = sea.Context(cell, grid, stream=stream.cuda_stream, precision=1)
+            c.set_orbitals(phi)
+            del phi
+            torch.cuda.empty_cache()  # the generator's blocks back to the driver
+            ctxs.append(c)
+            outs.append(torch.empty((4 * n_mol, g, g, g), dtype=torch.float64, device=dev))
+        torch.cuda.synchronize()
+        t_gen += time.perf_counter() - tg
+        t_batch += timed(lambda: sea.apply_vxx_batch(ctxs, outs))
+        st0 = ctxs[0].stats()
+        tuned.append({"configurations": len(grp), "order": st0["batch_order"],
+                      "ctas_per_sm": st0["batch_ctas_per_sm"]})
+        t_seq += timed(lambda: [c.apply_vxx(o) for c, o in zip(ctxs, outs)])
+        pairs += sum(c.stats()["n_pairs"] for c in ctxs)
+        orbitals += sum(c.n_orb for c in ctxs)
+        for c in ctxs:
+            c.close()
+        del ctxs, outs
+        torch.cuda.empty_cache()
+    n = len(work)
+    return {"configurations": n, "orbitals_total": orbitals, "pairs_total": pairs,
+            "groups": len(groups), "tuned": tuned,
+            "ms_batched": t_batch, "ms_one_by_one": t_seq,
+            "configs_per_s_batched": n / (t_batch / 1e3),
+            "configs_per_s_one_by_one": n / (t_seq / 1e3),
+            "generation_s": t_gen,
+            "workload": "64 configurations (H2O)32-128, 0.4-1.7 g/cm^3, h = 0.13 A (BASELINE "
+                        "config 4), mixed form, V_xx application only; in groups of at most "
+                        f"{budget_gb:.0f} GB of device arrays, one batched call per group"}
 
 
 def run_warm_start(args, sea, synth, torch, dev, s, width=16, train_seeds=(2001, 2002), steps=400,
@@ -485,46 +567,6 @@ def run_warm_start(args, sea, synth, torch, dev, s, width=16, train_seeds=(2001,
         res[name] = row
     net.close()
     return res
-
-
-def run_batched(args, sea, torch, dev):
-    """Batched form vs one call per configuration, V_xx application only."""
-    systems = batched_workload()
-    stream = torch.cuda.Stream(device=dev)
-    ctxs = [sea.Context(s.cell, s.grid, stream=stream.cuda_stream, precision=1) for s in systems]
-    outs = []
-    for c, s in zip(ctxs, systems):
-        c.set_orbitals(torch.from_numpy(s.phi).to(dev))
-        outs.append(torch.empty(s.phi.shape, dtype=torch.float64, device=dev))
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        stream.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        return e0.elapsed_time(e1) / args.steps
-
-    t_batch = timed(lambda: sea.apply_vxx_batch(ctxs, outs))
-    graph = ctxs[0].stats()["batch_graph"]
-    t_seq = timed(lambda: [c.apply_vxx(o) for c, o in zip(ctxs, outs)])
-    n_pairs = sum(c.stats()["n_pairs"] for c in ctxs)
-    for c in ctxs:
-        c.close()
-    return {"configurations": len(systems),
-            "orbitals": [s.n_orb for s in systems],
-            "pairs_total": n_pairs,
-            "ms_batched": t_batch, "ms_one_by_one": t_seq,
-            "configs_per_s_batched": len(systems) / (t_batch / 1e3),
-            "configs_per_s_one_by_one": len(systems) / (t_seq / 1e3),
-            "graph": {0: "direct", 1: "captured", 2: "replayed"}.get(graph, graph),
-            "workload": "16 configurations (H2O)8-32, 0.4-1.7 g/cm^3, h = 0.13 A, mixed form, "
-                        "V_xx application only"}
 
 
 def oracle_step(s, psi_h):

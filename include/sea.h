@@ -129,6 +129,14 @@ typedef struct {
   int ace_max_tile_list; /* longest W list of a tile, last sea_build_ace (the
                             mixed form expands lists up to 32 on the tensor
                             cores, longer ones in FP32 error-free arithmetic) */
+  int batch_order;       /* last sea_apply_vxx_batch led by this context: the
+                            autotuned order of the CG's work items (0 ranks
+                            round-robin over configurations, 1 all pairs
+                            longest first, 2 configuration-major)          */
+  int batch_ctas_per_sm, batch_ctas_per_sm_fp64; /* its autotuned persistent
+                            grids (CTAs per SM) of the mixed-form and FP64 CG */
+  double batch_tune_ms;  /* device time spent tuning in that call (0: the
+                            workload's choice was already known)           */
   double exx_ace; /* E_xx^ACE = sum_i <phi_i|V^ACE|phi_i> = -sum_ik <phi_i|xi_k>^2
                      (Eq. exx_ace), last sea_build_ace: -tr(M K M^T) with
                      K = (-Mbar)^-1 = L^-T L^-1 (Cholesky form) or
@@ -184,7 +192,11 @@ sea_status sea_apply_vxx(sea_ctx* ctx, double* vxx_phi, int on_device, double* e
 
 /* Batched form: apply V_xx for n independent configurations (each its own
  * context, orbitals already set) in one pass -- all their pairs' Poisson
- * problems in one persistent launch.  All contexts must use the same device
+ * problems in one persistent launch.  The launch's pair order and grid are
+ * autotuned per workload (pair counts, unknowns, grids and forms of the
+ * configurations): the first call for a workload times each candidate on
+ * the batch and keeps the fastest for the process (sea_stats.batch_*);
+ * every candidate gives the same results bit for bit.  All contexts must use the same device
  * and the same stream; vxx_phi[k] (host or device per on_device) receives
  * configuration k's V_xx phi, exx[k] (may be NULL) its E_xx.  The phase
  * after the plan (pair setup, CG, far field, accumulation) is captured in a

@@ -9,8 +9,21 @@
 // configurations, far field and accumulation of every configuration -- is
 // captured once into a CUDA graph and replayed on later calls whose plan
 // sizes and buffers are unchanged (a changed plan re-captures).
+//
+// Autotuner: the persistent CG launch has two free choices that leave every
+// pair's arithmetic unchanged (so the results stay bit-identical to one call
+// per configuration): the order in which the pairs of all configurations
+// are dealt to the CTAs, and the persistent grid (CTAs per SM, up to the
+// occupancy limit).  The first call for a workload (the configurations'
+// pair counts, unknowns, grids and forms) times every order with every grid
+// size on the batch itself, one CG launch each after a warm-up launch, and
+// keeps the fastest in a process-wide table; later calls for the same
+// workload -- and the graph captured for it -- use that choice.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "sea_internal.cuh"
@@ -33,6 +46,43 @@ GraphCache* cache_of(sea_ctx* c0) {
 void push_buf(std::vector<long long>& v, const SeaBuf& b) {
   v.push_back((long long)(uintptr_t)b.p);
   v.push_back((long long)b.bytes);
+}
+
+// Orders of the batched CG's work items (configuration, rank), rank r being
+// a configuration's r-th longest pair: 0 ranks dealt round-robin over the
+// configurations; 1 all pairs by box size, longest first (ties: rank, then
+// configuration); 2 configuration after configuration.
+constexpr int N_ORDERS = 3;
+
+struct Tuned {
+  int order = 0, per_sm_mixed = 0, per_sm_fp64 = 0;
+  double ms = 0.0;  // the chosen candidate's CG time
+};
+std::mutex g_tune_mutex;
+std::map<std::vector<long long>, Tuned> g_tuned;
+
+// Work items in `order`, the mixed-form items first, then the FP64 ones.
+// size[k][r]: box size of configuration k's rank-r pair (order 1 only).
+void build_items(int order, sea_ctx* const* ctxs, int n, int maxP,
+                 const std::vector<std::vector<int>>& size, std::vector<int2>& items) {
+  items.clear();
+  for (int mixed = 1; mixed >= 0; --mixed) {
+    auto form = [&](int k) { return (ctxs[k]->prm.precision == 1) == (mixed == 1); };
+    const size_t first = items.size();
+    if (order == 2) {
+      for (int k = 0; k < n; ++k)
+        if (form(k))
+          for (int r = 0; r < ctxs[k]->P; ++r) items.push_back(make_int2(k, r));
+    } else {
+      for (int r = 0; r < maxP; ++r)
+        for (int k = 0; k < n; ++k)
+          if (r < ctxs[k]->P && form(k)) items.push_back(make_int2(k, r));
+      if (order == 1)
+        std::stable_sort(items.begin() + first, items.end(), [&](const int2& a, const int2& b) {
+          return size[a.x][a.y] > size[b.x][b.y];
+        });
+    }
+  }
 }
 
 }  // namespace
@@ -118,14 +168,54 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
     ctxs[k]->cg_warm = false;  // the batched form solves from zero
     sea::make_batch_desc(ctxs[k], &hdesc[(size_t)k * db]);
   }
-  // mixed-form items first, then FP64 ones: one launch each (their CTA sizes differ)
+  // the workload's tuned choice (absent: tune below, before the capture)
+  std::vector<long long> wsig;
+  wsig.push_back(n);
+  for (int k = 0; k < n; ++k) {
+    const sea_ctx* c = ctxs[k];
+    wsig.push_back(c->P);
+    wsig.push_back(c->U);
+    wsig.push_back(c->cg_pad_max);
+    wsig.push_back(c->prm.precision);
+    for (int a = 0; a < 3; ++a) wsig.push_back(c->N[a]);
+  }
+  Tuned tuned;
+  bool have_tuned = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(wsig);
+    if (it != g_tuned.end()) {
+      tuned = it->second;
+      have_tuned = true;
+    }
+  }
+  // box sizes per rank (the pairs' ranks are longest first in each
+  // configuration): needed by order 1 and by the tuning
+  std::vector<std::vector<int>> rsize((size_t)n);
+  if (!have_tuned || tuned.order == 1) {
+    std::vector<std::vector<int>> ord((size_t)n), psz((size_t)n);
+    for (int k = 0; k < n; ++k) {
+      sea_ctx* c = ctxs[k];
+      ord[k].resize((size_t)c->P);
+      psz[k].resize((size_t)c->P);
+      if (c->P) {
+        SEA_BCK(cudaMemcpyAsync(ord[k].data(), c->order.p, (size_t)c->P * sizeof(int),
+                                cudaMemcpyDeviceToHost, st),
+                "pair order");
+        SEA_BCK(cudaMemcpyAsync(psz[k].data(), c->psize.p, (size_t)c->P * sizeof(int),
+                                cudaMemcpyDeviceToHost, st),
+                "pair sizes");
+      }
+    }
+    SEA_BCK(cudaStreamSynchronize(st), "pair sizes");
+    for (int k = 0; k < n; ++k) {
+      rsize[k].resize(ord[k].size());
+      for (size_t r = 0; r < ord[k].size(); ++r) rsize[k][r] = psz[k][(size_t)ord[k][r]];
+    }
+  }
   std::vector<int2> hitems;
   hitems.reserve((size_t)total);
-  for (int mixed = 1; mixed >= 0; --mixed)
-    for (int r = 0; r < maxP; ++r)
-      for (int k = 0; k < n; ++k)
-        if (r < ctxs[k]->P && (ctxs[k]->prm.precision == 1) == (mixed == 1))
-          hitems.push_back(make_int2(k, r));
+  build_items(have_tuned ? tuned.order : 0, ctxs, n, maxP, rsize, hitems);
   long long total_mixed = 0;
   for (int k = 0; k < n; ++k)
     if (ctxs[k]->prm.precision == 1) total_mixed += ctxs[k]->P;
@@ -173,11 +263,12 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
       if (e != cudaSuccess) return e;
     }
     cudaError_t e = sea::launch_cg_batch(st, c0->device, c0->bdesc.p, (const int2*)c0->bitems.p,
-                                         (int)total_mixed, (int*)c0->queue.p, pad_cap, true);
+                                         (int)total_mixed, (int*)c0->queue.p, pad_cap, true,
+                                         tuned.per_sm_mixed);
     if (e != cudaSuccess) return e;
     e = sea::launch_cg_batch(st, c0->device, c0->bdesc.p,
                              (const int2*)c0->bitems.p + total_mixed, (int)(total - total_mixed),
-                             (int*)c0->queue.p, 0, false);
+                             (int*)c0->queue.p, 0, false, tuned.per_sm_fp64);
     if (e != cudaSuccess) return e;
     c0->launches += (total_mixed > 0) + (total > total_mixed);
     for (int k = 0; k < n; ++k) {
@@ -190,6 +281,73 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
     gc->launches = l1 - l0;
     return cudaSuccess;
   };
+  c0->stats.batch_tune_ms = 0.0;
+  if (!have_tuned && total > 0) {
+    // every order x every grid size, one timed CG launch each (after one
+    // warm-up launch), on the batch's own pairs; the pair setup runs once
+    float t_tune = 0.f;
+    cudaEvent_t ev[3];
+    for (int q = 0; q < 3; ++q) SEA_BCK(cudaEventCreate(&ev[q]), "event");
+    SEA_BCK(cudaEventRecord(ev[2], st), "event");
+    for (int k = 0; k < n; ++k) SEA_BCK(sea::launch_pair_setup(ctxs[k]), "pair setup (tuning)");
+    const int occ_m = sea::cg_batch_max_ctas_per_sm(c0->device, pad_cap, true);
+    const int occ_f = sea::cg_batch_max_ctas_per_sm(c0->device, 0, false);
+    double best = 1e300;
+    std::vector<int2> items;
+    for (int o = 0; o < N_ORDERS; ++o) {
+      build_items(o, ctxs, n, maxP, rsize, items);
+      SEA_BCK(cudaMemcpyAsync(c0->bitems.p, items.data(), items.size() * sizeof(int2),
+                              cudaMemcpyHostToDevice, st),
+              "items");
+      double best_m = 1e300, best_f = 1e300;
+      int pm = 1, pf = 1;
+      for (int form = 0; form < 2; ++form) {
+        const bool mixed = form == 0;
+        const long long cnt = mixed ? total_mixed : total - total_mixed;
+        if (cnt == 0) continue;
+        const int2* it0 = (const int2*)c0->bitems.p + (mixed ? 0 : total_mixed);
+        const int occ = mixed ? occ_m : occ_f;
+        for (int j = (o == 0 ? 0 : 1); j <= occ; ++j) {  // j = 0: the warm-up launch
+          SEA_BCK(cudaEventRecord(ev[0], st), "event");
+          SEA_BCK(sea::launch_cg_batch(st, c0->device, c0->bdesc.p, it0, (int)cnt,
+                                       (int*)c0->queue.p, mixed ? pad_cap : 0, mixed, j < 1 ? 1 : j),
+                  "batched CG (tuning)");
+          SEA_BCK(cudaEventRecord(ev[1], st), "event");
+          SEA_BCK(cudaEventSynchronize(ev[1]), "tuning");
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, ev[0], ev[1]);
+          if (j == 0) continue;
+          if (mixed && ms < best_m) best_m = ms, pm = j;
+          if (!mixed && ms < best_f) best_f = ms, pf = j;
+        }
+      }
+      const double tot = (best_m < 1e300 ? best_m : 0.0) + (best_f < 1e300 ? best_f : 0.0);
+      if (tot < best) {
+        best = tot;
+        tuned.order = o;
+        tuned.per_sm_mixed = pm;
+        tuned.per_sm_fp64 = pf;
+        tuned.ms = tot;
+      }
+    }
+    SEA_BCK(cudaEventRecord(ev[1], st), "event");
+    SEA_BCK(cudaEventSynchronize(ev[1]), "tuning");
+    cudaEventElapsedTime(&t_tune, ev[2], ev[1]);
+    for (int q = 0; q < 3; ++q) cudaEventDestroy(ev[q]);
+    c0->stats.batch_tune_ms = t_tune;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tuned[wsig] = tuned;
+    }
+    // the chosen order's items for the launches below
+    build_items(tuned.order, ctxs, n, maxP, rsize, hitems);
+    SEA_BCK(cudaMemcpyAsync(c0->bitems.p, hitems.data(), hitems.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice, st),
+            "items");
+  }
+  c0->stats.batch_order = tuned.order;
+  c0->stats.batch_ctas_per_sm = tuned.per_sm_mixed;
+  c0->stats.batch_ctas_per_sm_fp64 = tuned.per_sm_fp64;
   if (!can_graph) {
     SEA_BCK(post_plan(), "batched post-plan phase");
     c0->stats.batch_graph = 0;

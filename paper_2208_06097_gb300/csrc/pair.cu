@@ -1082,22 +1082,32 @@ void make_batch_desc(sea_ctx* c, void* out) {
 
 size_t batch_desc_bytes() { return sizeof(BatchCg); }
 
+int cg_batch_max_ctas_per_sm(int device, int pad_cap, bool mixed) {
+  const size_t smem = (size_t)pad_cap * sizeof(float);
+  const int threads = mixed ? SEA_CG_THREADS : 256;
+  auto kern = mixed ? k_cg_batch<true> : k_cg_batch<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(SEA_CG_PAD_LIMIT * sizeof(float))) != cudaSuccess)
+    return 1;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+  (void)device;
+  return occ < 1 ? 1 : occ;
+}
+
 cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, const int2* items,
-                            int total, int* queue, int pad_cap, bool mixed) {
+                            int total, int* queue, int pad_cap, bool mixed, int ctas_per_sm) {
   if (total == 0) return cudaSuccess;
-  int nsm = 0, occ = 0;
+  int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   const size_t smem = (size_t)pad_cap * sizeof(float);
   const int threads = mixed ? SEA_CG_THREADS : 256;
   auto kern = mixed ? k_cg_batch<true> : k_cg_batch<false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(SEA_CG_PAD_LIMIT * sizeof(float)));
+  const int occ = cg_batch_max_ctas_per_sm(device, pad_cap, mixed);
+  const int per_sm = ctas_per_sm >= 1 ? min(ctas_per_sm, occ) : occ;
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
-  if (occ < 1) occ = 1;
-  e = cudaMemsetAsync(queue, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  kern<<<min(total, nsm * occ), threads, smem, st>>>((const BatchCg*)descs, items, total, queue);
+  kern<<<min(total, nsm * per_sm), threads, smem, st>>>((const BatchCg*)descs, items, total, queue);
   return cudaGetLastError();
 }
 

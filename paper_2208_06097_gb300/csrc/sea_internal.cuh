@@ -522,8 +522,11 @@ cudaError_t launch_pair_setup(sea_ctx* c);
 cudaError_t launch_cg(sea_ctx* c);
 void make_batch_desc(sea_ctx* c, void* out);
 size_t batch_desc_bytes();
+// The persistent batched CG: ctas_per_sm CTAs per SM (0 or above the
+// occupancy limit: the limit).
 cudaError_t launch_cg_batch(cudaStream_t st, int device, const void* descs, const int2* items,
-                            int total, int* queue, int pad_cap, bool mixed);
+                            int total, int* queue, int pad_cap, bool mixed, int ctas_per_sm);
+int cg_batch_max_ctas_per_sm(int device, int pad_cap, bool mixed);
 int cg_pad_cap(const sea_ctx* c);
 cudaError_t launch_entries(sea_ctx* c);
 // V_xx phi into out (the context's W) and, when out2 is not null, also into

@@ -61,7 +61,9 @@ class Stats(ctypes.Structure):
                 ("ms_expand_apply", ctypes.c_double), ("ace_eigen", ctypes.c_int),
                 ("ace_eigen_sweeps", ctypes.c_int), ("ace_negative_eigenvalues", ctypes.c_int),
                 ("ace_dropped_eigenvalues", ctypes.c_int), ("batch_graph", ctypes.c_int),
-                ("ace_max_tile_list", ctypes.c_int), ("exx_ace", ctypes.c_double)]
+                ("ace_max_tile_list", ctypes.c_int), ("batch_order", ctypes.c_int),
+                ("batch_ctas_per_sm", ctypes.c_int), ("batch_ctas_per_sm_fp64", ctypes.c_int),
+                ("batch_tune_ms", ctypes.c_double), ("exx_ace", ctypes.c_double)]
 
 
 _LIB = None

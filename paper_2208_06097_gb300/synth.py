@@ -168,17 +168,11 @@ def _orbital(xs, ys, zs, cell, c, alpha, A):
     return f
 
 
-def make_waters(n_mol: int, L_angstrom: float, grid, seed: int,
-                loewdin: bool = True, alpha_range=(1.5, 3.0),
-                centre_first: bool = False) -> System:
-    """Build one seeded (H2O)n-like orbital set in a cubic cell of edge L.
-
-    ``alpha_range`` sets the Gaussian exponent interval (bohr^-2);
-    ``centre_first`` moves the first oxygen to the cell centre (used for
-    isolated-molecule cases that must not touch the cell boundary)."""
+def _draw(n_mol, L_angstrom, grid, seed, alpha_range=(1.5, 3.0), centre_first=False):
+    """The seeded parameters of one configuration: cell, grid, orbital
+    centres, exponents, quadratic-factor matrices, oxygen positions."""
     if isinstance(grid, int):
         grid = (grid, grid, grid)
-    nx, ny, nz = grid
     L = L_angstrom * ANGSTROM
     cell = (L, L, L)
     rng = np.random.default_rng(seed)
@@ -194,6 +188,21 @@ def make_waters(n_mol: int, L_angstrom: float, grid, seed: int,
     alphas = rng.uniform(alpha_range[0], alpha_range[1], size=n_orb)
     As = rng.uniform(-1.0, 1.0, size=(n_orb, 3, 3))
     As = 0.5 * (As + np.transpose(As, (0, 2, 1)))
+    return cell, tuple(grid), centres, alphas, As, oxy
+
+
+def make_waters(n_mol: int, L_angstrom: float, grid, seed: int,
+                loewdin: bool = True, alpha_range=(1.5, 3.0),
+                centre_first: bool = False) -> System:
+    """Build one seeded (H2O)n-like orbital set in a cubic cell of edge L.
+
+    ``alpha_range`` sets the Gaussian exponent interval (bohr^-2);
+    ``centre_first`` moves the first oxygen to the cell centre (used for
+    isolated-molecule cases that must not touch the cell boundary)."""
+    cell, grid, centres, alphas, As, oxy = _draw(n_mol, L_angstrom, grid, seed, alpha_range,
+                                                 centre_first)
+    nx, ny, nz = grid
+    n_orb = len(centres)
     xs = np.arange(nx) * (cell[0] / nx)
     ys = np.arange(ny) * (cell[1] / ny)
     zs = np.arange(nz) * (cell[2] / nz)
@@ -261,3 +270,59 @@ def random_trial_vectors(n_vec: int, grid, seed: int) -> np.ndarray:
     nx, ny, nz = grid if not isinstance(grid, int) else (grid, grid, grid)
     rng = np.random.default_rng(seed)
     return rng.standard_normal((n_vec, nz, ny, nx))
+
+
+def make_waters_device(n_mol: int, L_angstrom: float, grid, seed: int, device):
+    """The orbitals of ``make_waters`` (same seeded parameters) evaluated and
+    Loewdin-orthonormalized with torch float64 on ``device`` -- for the large
+    workloads (hundreds of orbitals on 10^6-10^7 points), whose host
+    generation would take minutes.  The values agree with ``make_waters`` up
+    to floating-point summation order.  Returns (phi [n][nz][ny][nx] tensor on
+    the device, cell, grid)."""
+    import torch
+    cell, grid, centres, alphas, As, _ = _draw(n_mol, L_angstrom, grid, seed)
+    nx, ny, nz = grid
+    n = len(centres)
+    dt = torch.float64
+    c = torch.as_tensor(centres, dtype=dt, device=device)
+    al = torch.as_tensor(alphas, dtype=dt, device=device)
+    A = torch.as_tensor(As, dtype=dt, device=device)
+
+    def moments(npts, axis):
+        coords = torch.arange(npts, dtype=dt, device=device) * (cell[axis] / npts)
+        d0 = coords[None, :] - c[:, axis:axis + 1]
+        g0 = torch.zeros((n, npts), dtype=dt, device=device)
+        g1 = torch.zeros_like(g0)
+        g2 = torch.zeros_like(g0)
+        for img in (-1, 0, 1):
+            d = d0 - img * cell[axis]
+            g = torch.exp(-al[:, None] * d * d)
+            g0 += g
+            g1 += g * d
+            g2 += g * d * d
+        return g0, g1, g2
+
+    X0, X1, X2 = moments(nx, 0)
+    Y0, Y1, Y2 = moments(ny, 1)
+    Z0, Z1, Z2 = moments(nz, 2)
+    phi = torch.empty((n, nz, ny, nx), dtype=dt, device=device)
+    terms = [(None, Z0, Y0, X0), ((0, 0), Z0, Y0, X2), ((1, 1), Z0, Y2, X0), ((2, 2), Z2, Y0, X0),
+             ((0, 1), Z0, Y1, X1), ((0, 2), Z1, Y0, X1), ((1, 2), Z1, Y1, X0)]
+    for i0 in range(0, n, 32):
+        i1 = min(n, i0 + 32)
+        acc = None
+        for idx, Z, Y, X in terms:
+            t = Z[i0:i1, :, None, None] * Y[i0:i1, None, :, None] * X[i0:i1, None, None, :]
+            if idx is not None:
+                w = A[i0:i1, idx[0], idx[1]] * (0.1 if idx[0] == idx[1] else 0.2)
+                t = t * w[:, None, None, None]
+            acc = t if acc is None else acc + t
+        phi[i0:i1] = acc
+    dV = (cell[0] * cell[1] * cell[2]) / (nx * ny * nz)
+    F = phi.reshape(n, -1)
+    S = (F @ F.T) * dV
+    w, U = torch.linalg.eigh(S)
+    Sm = (U / torch.sqrt(w)[None, :]) @ U.T
+    out = (Sm.T @ F).reshape(n, nz, ny, nx)
+    del phi, F
+    return out, cell, grid
