@@ -18,7 +18,8 @@
 // forward pass and their data gradients run on the tensor cores (tcgen05,
 // kind::f16, BF16 operands, FP32 accumulation in tensor memory) as an
 // implicit GEMM; each FP32 activation enters as the exact sum of three BF16
-// terms, so the products are those of the FP32 values.  Training: masked
+// terms, so the products are those of the FP32 values.  The weight
+// gradients run on the tensor cores too (two BF16 terms per value).  Training: masked
 // mean squared error against the CG solution, Adam.  All reductions run in a
 // fixed order (no floating-point atomics), so training is deterministic.
 #include <cuda_bf16.h>
@@ -264,44 +265,254 @@ __global__ void __launch_bounds__(CT_THREADS) k_conv3_tc(ConvTc P) {
   }
 }
 
-// dw[co][ci][k] = sum_b sum_p dy[b][co][p] x[b][xc0 + ci][p + off(k)], and
-// (ci == 0) db[co] = sum dy.  CTA per (co, ci); fixed-order reduction.
-__global__ void __launch_bounds__(256)
-    k_conv3_dw(const float* __restrict__ x, int xC, int xc0, int Cin,
-               const float* __restrict__ dy, int dyC, int dyc0, int Cout, int D, int B,
-               float* __restrict__ dw, float* __restrict__ db) {
-  const int co = blockIdx.x / Cin, ci = blockIdx.x % Cin;
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3x3x3 layer on the tensor cores:
+//
+//   dw[co][ci][k] = sum_b sum_p dy[b][co][p] x[b][ci][p + off(k)]
+//
+// as 27 GEMMs D_k[co][ci] = sum_p A[co][p] B_k[ci][p] whose K dimension is
+// the 128 points of a tile.  Both operands are MN-major (8 channels
+// contiguous per point): A = the tile's dy, staged point after point
+// (rows 16 B apart, one plane per 8 output channels, M = 128 with the
+// channels beyond Cout zero); B_k = the haloed input of a 16-channel chunk
+// in the forward kernel's layout, shifted by the tap's row offset -- so
+// again no im2col copy.  A K step of 16 points is two y-rows of the tile.
+// FP32 values enter as two BF16 terms (h + m, 16 significant bits); the
+// products h h, h m and m h are accumulated (relative error below 2^-16).
+// CTA (g, chunk) of a G x chunks grid takes the tiles g, g + G, ... of the
+// whole batch (a fixed assignment) and keeps the 27 accumulators (27 x 16
+// columns) in tensor memory over all of them; two staging buffers let the
+// next tile be staged while the MMAs of the current one run.  Each CTA
+// writes its partial sums; k_conv_dw_reduce adds the G partials in index
+// order, so the gradient is deterministic.
+// ---------------------------------------------------------------------------
+#define DW_THREADS 256
+#define DW_APLANE (128 * 16)                            // one 8-channel plane of dy
+#define DW_ABYTES (2 * 16 * DW_APLANE)                  // two terms x 16 planes
+#define DW_XBYTES (2 * 2 * CT_PLANE)                    // two terms x two octets
+#define DW_BUF (DW_ABYTES + DW_XBYTES)
+
+struct ConvDw {
+  const float* x;
+  int xC, xc0, Cin;
+  const float* dy;
+  int dyC, dyc0, Cout;
+  int D, B, G;
+  float* part;  // [chunk][G][27][Cout][16]
+  unsigned* status;
+};
+
+__device__ __forceinline__ void split2_bf16(float v0, float v1, uint32_t& h, uint32_t& m) {
+  const __nv_bfloat162 H = __floats2bfloat162_rn(v0, v1);
+  const __nv_bfloat162 Mm = __floats2bfloat162_rn(v0 - __low2float(H), v1 - __high2float(H));
+  h = *reinterpret_cast<const uint32_t*>(&H);
+  m = *reinterpret_cast<const uint32_t*>(&Mm);
+}
+
+__global__ void __launch_bounds__(DW_THREADS, 1) k_conv3_dw_tc(ConvDw P) {
+  extern __shared__ unsigned char dw_raw[];
+  unsigned char* sb = dw_raw + ((128 - (smem_addr(dw_raw) & 127)) & 127);
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ uint32_t tbase;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = P.D, ntx = D / 8, nty = (D + 15) / 16, ntile = ntx * nty * D;
+  const int total = ntile * P.B, g = blockIdx.x, ch = blockIdx.y;
   const size_t V = (size_t)D * D * D;
-  float s[28];
+  const uint32_t mb[2] = {smem_addr(&bars[0]), smem_addr(&bars[1])};
+  if (warp == 0) tmem_alloc(&tbase, 512);
+  if (tid == 0) {
+    mbar_init(mb[0], 1);
+    mbar_init(mb[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  // the dy planes of channels beyond Cout stay zero in both buffers
+  for (int q = tid; q < 2 * DW_ABYTES / 16; q += DW_THREADS) {
+    const int bi = q / (DW_ABYTES / 16), r = q % (DW_ABYTES / 16);
+    const int plane = (r * 16 / DW_APLANE) % 16;
+    if (8 * plane >= P.Cout)
+      *reinterpret_cast<uint4*>(sb + bi * DW_BUF + r * 16) = make_uint4(0, 0, 0, 0);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  // tcgen05 kind::f16 descriptor: BF16 A and B, both MN-major, M = 128, N = 16
+  const uint32_t idesc = idesc_kf16(16, 128, true) | (1u << 15) | (1u << 16);
+  const int nplanes = (P.Cout + 7) / 8;
+  uint32_t phase[2] = {0, 0};  // thread 0's parities
+  int committed[2] = {0, 0};   // commits not yet waited for, per buffer (uniform)
+  int i = 0;
+  for (int t = g; t < total; t += P.G, ++i) {
+    const int buf = i & 1;
+    unsigned char* sA = sb + buf * DW_BUF;
+    unsigned char* sX = sA + DW_ABYTES;
+    if (committed[buf]) {  // the MMAs of two tiles ago read this buffer
+      if (tid == 0) {
+        if (mbar_wait(mb[buf], phase[buf]))
+          phase[buf] ^= 1;
+        else
+          s_fail = 1;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      committed[buf] = 0;
+    }
+    const int b = t / ntile;
+    int r = t % ntile;
+    const int x0 = (r % ntx) * 8;
+    r /= ntx;
+    const int y0 = (r % nty) * 16, z0 = r / nty;
+    // dy of the tile: item = (plane, point m), 8 channels
+    for (int it = tid; it < nplanes * 128; it += DW_THREADS) {
+      const int pl = it / 128, m = it % 128;
+      const int oy = y0 + (m >> 3), ox = x0 + (m & 7);
+      const bool in = oy < D;
+      const size_t pofs = ((size_t)z0 * D + (in ? oy : 0)) * D + ox;
+      uint32_t w[2][4];
 #pragma unroll
-  for (int k = 0; k < 28; ++k) s[k] = 0.f;
-  for (size_t e = threadIdx.x; e < (size_t)B * V; e += blockDim.x) {
-    const int b = (int)(e / V), p = (int)(e % V);
-    const int px = p % D, py = (p / D) % D, pz = p / (D * D);
-    const float g = dy[((size_t)b * dyC + dyc0 + co) * V + p];
-    const float* xs = x + ((size_t)b * xC + xc0 + ci) * V;
-    s[27] += g;
+      for (int c2 = 0; c2 < 4; ++c2) {
+        const int co = 8 * pl + 2 * c2;
+        const float v0 = (in && co < P.Cout) ? P.dy[((size_t)b * P.dyC + P.dyc0 + co) * V + pofs] : 0.f;
+        const float v1 =
+            (in && co + 1 < P.Cout) ? P.dy[((size_t)b * P.dyC + P.dyc0 + co + 1) * V + pofs] : 0.f;
+        split2_bf16(v0, v1, w[0][c2], w[1][c2]);
+      }
 #pragma unroll
-    for (int k = 0; k < 27; ++k) {
-      const int gx = px + k % 3 - 1, gy = py + (k / 3) % 3 - 1, gz = pz + k / 9 - 1;
-      const float xv = (gx >= 0 && gx < D && gy >= 0 && gy < D && gz >= 0 && gz < D)
-                           ? xs[vox(gz, gy, gx, D)]
-                           : 0.f;
-      s[k] = fmaf(g, xv, s[k]);
+      for (int t2 = 0; t2 < 2; ++t2)
+        *reinterpret_cast<uint4*>(sA + (t2 * 16 + pl) * DW_APLANE + m * 16) =
+            make_uint4(w[t2][0], w[t2][1], w[t2][2], w[t2][3]);
+    }
+    // the haloed input of channels 16 ch .. + 15
+    for (int it = tid; it < 2 * CT_ROWS; it += DW_THREADS) {
+      const int o = it / CT_ROWS, row = it - o * CT_ROWS;
+      const int hx = row % CT_HX, hy = (row / CT_HX) % CT_HY, hz = row / (CT_HX * CT_HY);
+      const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+      const bool in = gx >= 0 && gx < D && gy >= 0 && gy < D && gz >= 0 && gz < D;
+      const size_t pofs = in ? ((size_t)gz * D + gy) * D + gx : 0;
+      uint32_t w[2][4];
+#pragma unroll
+      for (int c2 = 0; c2 < 4; ++c2) {
+        const int ci = 16 * ch + 8 * o + 2 * c2;
+        const float v0 = (in && ci < P.Cin) ? P.x[((size_t)b * P.xC + P.xc0 + ci) * V + pofs] : 0.f;
+        const float v1 =
+            (in && ci + 1 < P.Cin) ? P.x[((size_t)b * P.xC + P.xc0 + ci + 1) * V + pofs] : 0.f;
+        split2_bf16(v0, v1, w[0][c2], w[1][c2]);
+      }
+#pragma unroll
+      for (int t2 = 0; t2 < 2; ++t2)
+        *reinterpret_cast<uint4*>(sX + (t2 * 2 + o) * CT_PLANE + row * 16) =
+            make_uint4(w[t2][0], w[t2][1], w[t2][2], w[t2][3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      const uint32_t aa = smem_addr(sA), ax = smem_addr(sX);
+#pragma unroll 1
+      for (int k = 0; k < 27; ++k) {
+        const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+        const uint32_t aoff = (uint32_t)((kz * CT_HX * CT_HY + ky * CT_HX + kx) * 16);
+#pragma unroll 1
+        for (int st = 0; st < 8; ++st) {  // K step: points 16 st .. 16 st + 15 (y rows 2 st, 2 st + 1)
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {  // term pairs h h, h m, m h
+            const int ta = pr == 2 ? 1 : 0, tb = pr == 1 ? 1 : 0;
+            // MN-major operands: lbo = byte distance of K-adjacent core
+            // matrices (the next 8 points), sbo = of M/N-adjacent ones (the
+            // next 8 channels)
+            const uint64_t ad = sdesc(aa + (uint32_t)(ta * 16 * DW_APLANE + st * 256), 128, DW_APLANE);
+            const uint64_t bd =
+                sdesc(ax + (uint32_t)(tb * 2 * CT_PLANE) + aoff + (uint32_t)(st * 2 * CT_HX * 16),
+                      CT_HX * 16, CT_PLANE);
+            mma_kf16(tmem + (uint32_t)(k * 16), ad, bd, idesc, (i > 0 || st > 0 || pr > 0) ? 1u : 0u);
+          }
+        }
+      }
+      mma_commit(mb[buf]);
+    }
+    committed[buf] = 1;
+  }
+  // the last tiles' MMAs
+  for (int q = 0; q < 2; ++q) {
+    const int bq = (i + q) & 1;  // oldest first
+    if (committed[bq] && !s_fail) {
+      if (tid == 0) {
+        if (mbar_wait(mb[bq], phase[bq])) {
+          phase[bq] ^= 1;
+        } else {
+          s_fail = 1;
+        }
+      }
+      __syncthreads();
+      if (!s_fail) committed[bq] = 0;
     }
   }
-  __shared__ float red[28][256];
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) {
+      for (int q = 0; q < 2; ++q)
+        if (committed[q]) mbar_wait(mb[q], phase[q]);  // once more, bounded
+      atomicOr(P.status, SEA_FLAG_WAIT);
+    }
+  } else if (warp < 4) {
+    tc_fence_after();
+    const int co = 32 * warp + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    float* dst = P.part + (((size_t)ch * P.G + g) * 27) * P.Cout * 16;
+    for (int k = 0; k < 27; ++k) {
+      uint32_t v[16];
+      tmem_ld8(lane_base + (uint32_t)(k * 16), v);
+      tmem_ld8(lane_base + (uint32_t)(k * 16 + 8), v + 8);
+      tmem_wait_ld();
+      if (co < P.Cout)
 #pragma unroll
-  for (int k = 0; k < 28; ++k) red[k][threadIdx.x] = s[k];
+        for (int c = 0; c < 16; ++c)
+          dst[((size_t)k * P.Cout + co) * 16 + c] = i > 0 ? __uint_as_float(v[c]) : 0.f;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// dw[co][ci][k] = sum over g (in index order) of the CTAs' partial sums.
+__global__ void k_conv_dw_reduce(const float* __restrict__ part, int Cout, int Cin, int G,
+                                 float* __restrict__ dw) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Cout * Cin * 27) return;
+  const int k = q % 27, ci = (q / 27) % Cin, co = q / (27 * Cin);
+  const int ch = ci / 16, c = ci % 16;
+  const float* p = part + ((size_t)ch * G * 27 + k) * Cout * 16 + (size_t)co * 16 + c;
+  const size_t stride = (size_t)27 * Cout * 16;
+  float s = 0.f;
+  for (int gg = 0; gg < G; ++gg) s += p[gg * stride];
+  dw[q] = s;
+}
+
+// db[co] = sum_b sum_p dy[b][dyc0 + co][p]: CTA per co, fixed-order reduction.
+__global__ void __launch_bounds__(256)
+    k_bias_grad(const float* __restrict__ dy, int dyC, int dyc0, size_t V, int B,
+                float* __restrict__ db) {
+  const int co = blockIdx.x;
+  float s = 0.f;
+  for (size_t e = threadIdx.x; e < (size_t)B * V; e += blockDim.x) {
+    const int b = (int)(e / V);
+    s += dy[((size_t)b * dyC + dyc0 + co) * V + e % V];
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = s;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h)
-#pragma unroll
-      for (int k = 0; k < 28; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + h];
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x < 27) dw[((size_t)co * Cin + ci) * 27 + threadIdx.x] = red[threadIdx.x][0];
-  if (threadIdx.x == 27 && ci == 0 && db) db[co] = red[27][0];
+  if (threadIdx.x == 0) db[co] = red[0];
 }
 
 // g[b][c][p] *= (y[b][c][p] > 0) over a channel slice (the ReLU's gradient).
@@ -561,6 +772,8 @@ struct sea_unet {
   float *master = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
   __nv_bfloat16 *wb = nullptr, *wp = nullptr;  // BF16 weights; their tensor-core layouts
   long long nwp = 0;
+  float* dwpart = nullptr;      // the weight-gradient kernel's per-CTA partial sums
+  int nsm = 0;
   unsigned* status = nullptr;   // device status word of the model's own calls
   unsigned* st_use = nullptr;   // the word the kernels report to (the model's or a context's)
   int adam_t = 0;
@@ -663,11 +876,43 @@ void conv3_dx(sea_unet* u, int l, const float* dy, int dyC, float* dx, int xC, i
   conv3_tc(u, l, true, dy, dyC, 0, dx, xC, xc0, D, B, 0);
 }
 
-void conv3_dw(sea_unet* u, int l, const float* x, int xC, int xc0, const float* dy, int dyC, int D,
-              int B) {
+// Grid of the weight-gradient kernel: G CTAs per 16-channel chunk, about one
+// CTA per SM in all (each holds the SM's 512 tensor-memory columns).
+int dw_grid(const sea_unet* u, int cin, int D, int B) {
+  const int nch = (cin + 15) / 16;
+  const int tiles = (D / 8) * ((D + 15) / 16) * D * B;
+  return std::max(1, std::min(tiles, (u->nsm + nch - 1) / nch));
+}
+
+size_t dw_part_floats(const sea_unet* u, const UnLayer& a, int D, int B) {
+  return (size_t)((a.cin + 15) / 16) * dw_grid(u, a.cin, D, B) * 27 * a.cout * 16;
+}
+
+// u->grad of layer l's weights and bias from the layer input x (slice xc0 of
+// xC channels) and the output gradient dy (slice dyc0 of dyC channels).
+void conv3_dw(sea_unet* u, int l, const float* x, int xC, int xc0, const float* dy, int dyC,
+              int dyc0, int D, int B) {
   const UnLayer& a = u->L[l];
-  sea::k_conv3_dw<<<a.cout * a.cin, 256, 0, u->stream>>>(x, xC, xc0, a.cin, dy, dyC, 0, a.cout, D,
-                                                          B, u->grad + a.w_off, u->grad + a.b_off);
+  sea::ConvDw P;
+  P.x = x;
+  P.xC = xC;
+  P.xc0 = xc0;
+  P.Cin = a.cin;
+  P.dy = dy;
+  P.dyC = dyC;
+  P.dyc0 = dyc0;
+  P.Cout = a.cout;
+  P.D = D;
+  P.B = B;
+  P.G = dw_grid(u, a.cin, D, B);
+  P.part = u->dwpart;
+  P.status = u->st_use;
+  const int nch = (a.cin + 15) / 16;
+  sea::k_conv3_dw_tc<<<dim3(P.G, nch), DW_THREADS, 128 + 2 * DW_BUF, u->stream>>>(P);
+  sea::k_conv_dw_reduce<<<grid1((size_t)a.cout * a.cin * 27), 256, 0, u->stream>>>(
+      u->dwpart, a.cout, a.cin, P.G, u->grad + a.w_off);
+  sea::k_bias_grad<<<a.cout, 256, 0, u->stream>>>(dy, dyC, dyc0, (size_t)D * D * D, B,
+                                                   u->grad + a.b_off);
 }
 
 void relu_bwd(sea_unet* u, float* g, int gC, int gc0, const float* y, int yC, int yc0, int C, int D,
@@ -712,64 +957,54 @@ void backward(sea_unet* u, const float* in, const float* tgt, int B) {
                                                                      u->g32a, V32, B);
   // d1b = relu(conv9(d1a))
   relu_bwd(u, u->g32a, c, 0, u->d1b, c, 0, c, 32, B);
-  conv3_dw(u, 9, u->d1a, c, 0, u->g32a, c, 32, B);
+  conv3_dw(u, 9, u->d1a, c, 0, u->g32a, c, 0, 32, B);
   conv3_dx(u, 9, u->g32a, c, u->g32b, c, 0, 32, B);
   // d1a = relu(conv8(cat1))
   relu_bwd(u, u->g32b, c, 0, u->d1a, c, 0, c, 32, B);
-  conv3_dw(u, 8, u->cat1, 3 * c, 0, u->g32b, c, 32, B);
+  conv3_dw(u, 8, u->cat1, 3 * c, 0, u->g32b, c, 0, 32, B);
   conv3_dx(u, 8, u->g32b, c, u->gcat1, 3 * c, 0, 32, B);
   // cat1[0..2c) = up(d2b)
   sea::k_up_bwd<<<grid1((size_t)B * 2 * c * V16), 256, 0, u->stream>>>(u->gcat1, 3 * c, 0, u->g16a,
                                                                        2 * c, 16, B);
   // d2b = relu(conv7(d2a))
   relu_bwd(u, u->g16a, 2 * c, 0, u->d2b, 2 * c, 0, 2 * c, 16, B);
-  conv3_dw(u, 7, u->d2a, 2 * c, 0, u->g16a, 2 * c, 16, B);
+  conv3_dw(u, 7, u->d2a, 2 * c, 0, u->g16a, 2 * c, 0, 16, B);
   conv3_dx(u, 7, u->g16a, 2 * c, u->g16b, 2 * c, 0, 16, B);
   // d2a = relu(conv6(cat2))
   relu_bwd(u, u->g16b, 2 * c, 0, u->d2a, 2 * c, 0, 2 * c, 16, B);
-  conv3_dw(u, 6, u->cat2, 6 * c, 0, u->g16b, 2 * c, 16, B);
+  conv3_dw(u, 6, u->cat2, 6 * c, 0, u->g16b, 2 * c, 0, 16, B);
   conv3_dx(u, 6, u->g16b, 2 * c, u->gcat2, 6 * c, 0, 16, B);
   // cat2[0..4c) = up(b5)
   sea::k_up_bwd<<<grid1((size_t)B * 4 * c * V8), 256, 0, u->stream>>>(u->gcat2, 6 * c, 0, u->g8a,
                                                                       4 * c, 8, B);
   // b5 = relu(conv5(b4)), b4 = relu(conv4(p2))
   relu_bwd(u, u->g8a, 4 * c, 0, u->b5, 4 * c, 0, 4 * c, 8, B);
-  conv3_dw(u, 5, u->b4, 4 * c, 0, u->g8a, 4 * c, 8, B);
+  conv3_dw(u, 5, u->b4, 4 * c, 0, u->g8a, 4 * c, 0, 8, B);
   conv3_dx(u, 5, u->g8a, 4 * c, u->g8b, 4 * c, 0, 8, B);
   relu_bwd(u, u->g8b, 4 * c, 0, u->b4, 4 * c, 0, 4 * c, 8, B);
-  conv3_dw(u, 4, u->p2, 2 * c, 0, u->g8b, 4 * c, 8, B);
+  conv3_dw(u, 4, u->p2, 2 * c, 0, u->g8b, 4 * c, 0, 8, B);
   conv3_dx(u, 4, u->g8b, 4 * c, u->g8a, 2 * c, 0, 8, B);  // d p2
   // p2 = pool(cat2[4c..6c)): add into the skip-2 gradient slice of gcat2
   sea::k_pool_bwd<<<grid1((size_t)B * 2 * c * V16), 256, 0, u->stream>>>(u->g8a, u->gcat2, 6 * c,
                                                                         4 * c, 2 * c, 16, B, 1);
   // skip 2 = relu(conv3(e2a))
   relu_bwd(u, u->gcat2, 6 * c, 4 * c, u->cat2, 6 * c, 4 * c, 2 * c, 16, B);
-  {
-    const UnLayer& a = u->L[3];
-    sea::k_conv3_dw<<<a.cout * a.cin, 256, 0, u->stream>>>(u->e2a, 2 * c, 0, a.cin, u->gcat2, 6 * c,
-                                                            4 * c, a.cout, 16, B, u->grad + a.w_off,
-                                                            u->grad + a.b_off);
-    conv3_tc(u, 3, true, u->gcat2, 6 * c, 4 * c, u->g16a, 2 * c, 0, 16, B, 0);
-  }
+  conv3_dw(u, 3, u->e2a, 2 * c, 0, u->gcat2, 6 * c, 4 * c, 16, B);
+  conv3_tc(u, 3, true, u->gcat2, 6 * c, 4 * c, u->g16a, 2 * c, 0, 16, B, 0);
   // e2a = relu(conv2(p1))
   relu_bwd(u, u->g16a, 2 * c, 0, u->e2a, 2 * c, 0, 2 * c, 16, B);
-  conv3_dw(u, 2, u->p1, c, 0, u->g16a, 2 * c, 16, B);
+  conv3_dw(u, 2, u->p1, c, 0, u->g16a, 2 * c, 0, 16, B);
   conv3_dx(u, 2, u->g16a, 2 * c, u->g16b, c, 0, 16, B);  // d p1
   // p1 = pool(cat1[2c..3c)): add into the skip-1 gradient slice of gcat1
   sea::k_pool_bwd<<<grid1((size_t)B * c * V32), 256, 0, u->stream>>>(u->g16b, u->gcat1, 3 * c, 2 * c,
                                                                      c, 32, B, 1);
   // skip 1 = relu(conv1(e1a))
   relu_bwd(u, u->gcat1, 3 * c, 2 * c, u->cat1, 3 * c, 2 * c, c, 32, B);
-  {
-    const UnLayer& a = u->L[1];
-    sea::k_conv3_dw<<<a.cout * a.cin, 256, 0, u->stream>>>(u->e1a, c, 0, a.cin, u->gcat1, 3 * c,
-                                                            2 * c, a.cout, 32, B, u->grad + a.w_off,
-                                                            u->grad + a.b_off);
-    conv3_tc(u, 1, true, u->gcat1, 3 * c, 2 * c, u->g32a, c, 0, 32, B, 0);
-  }
+  conv3_dw(u, 1, u->e1a, c, 0, u->gcat1, 3 * c, 2 * c, 32, B);
+  conv3_tc(u, 1, true, u->gcat1, 3 * c, 2 * c, u->g32a, c, 0, 32, B, 0);
   // e1a = relu(conv0(in))
   relu_bwd(u, u->g32a, c, 0, u->e1a, c, 0, c, 32, B);
-  conv3_dw(u, 0, in, 2, 0, u->g32a, c, 32, B);
+  conv3_dw(u, 0, in, 2, 0, u->g32a, c, 0, 32, B);
 }
 
 }  // namespace
@@ -794,6 +1029,7 @@ void sea_unet_destroy(sea_unet* u) {
     if (p) cudaFree(p);
   if (u->wb) cudaFree(u->wb);
   if (u->wp) cudaFree(u->wp);
+  if (u->dwpart) cudaFree(u->dwpart);
   if (u->status) cudaFree(u->status);
   if (u->dloss) cudaFree(u->dloss);
   if (u->pscale) cudaFree(u->pscale);
@@ -837,6 +1073,13 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
     u->L.push_back(l);
   }
   u->nparam = off;
+  cudaDeviceGetAttribute(&u->nsm, cudaDevAttrMultiProcessorCount, u->device);
+  if (u->nsm < 1) u->nsm = 1;
+  size_t dw_max = 1;
+  {
+    const int Ds[10] = {32, 32, 16, 16, 8, 8, 16, 16, 32, 32};
+    for (int l = 0; l < 10; ++l) dw_max = std::max(dw_max, dw_part_floats(u, u->L[l], Ds[l], u->bmax));
+  }
   // He-normal weights, zero biases (seeded)
   std::vector<float> h(off, 0.f);
   std::mt19937_64 gen((unsigned long long)seed * 0x9E3779B97F4A7C15ULL + 12345ULL);
@@ -850,7 +1093,7 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
   bool ok = alloc((void**)&u->master, off * 4) && alloc((void**)&u->grad, off * 4) &&
             alloc((void**)&u->am, off * 4) && alloc((void**)&u->av, off * 4) &&
             alloc((void**)&u->wb, off * 2) && alloc((void**)&u->wp, u->nwp * 2) &&
-            alloc((void**)&u->status, 16) &&
+            alloc((void**)&u->status, 16) && alloc((void**)&u->dwpart, dw_max * 4) &&
             alloc((void**)&u->e1a, B * c * V32 * 4) && alloc((void**)&u->cat1, B * 3 * c * V32 * 4) &&
             alloc((void**)&u->p1, B * c * V16 * 4) && alloc((void**)&u->e2a, B * 2 * c * V16 * 4) &&
             alloc((void**)&u->cat2, B * 6 * c * V16 * 4) && alloc((void**)&u->p2, B * 2 * c * V8 * 4) &&
@@ -879,6 +1122,8 @@ sea_status sea_unet_create(int width, int seed, void* cuda_stream, sea_unet** ou
   if (cudaMemsetAsync(u->status, 0, 16, u->stream) != cudaSuccess ||
       cudaFuncSetAttribute(sea::k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)conv_smem(CT_NBLK)) != cudaSuccess ||
+      cudaFuncSetAttribute(sea::k_conv3_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           128 + 2 * DW_BUF) != cudaSuccess ||
       cudaStreamSynchronize(u->stream) != cudaSuccess) {
     sea_unet_destroy(u);
     return SEA_ERR_CUDA;
