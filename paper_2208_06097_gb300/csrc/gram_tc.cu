@@ -1065,7 +1065,8 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
   extern __shared__ unsigned char xe_raw[];
   unsigned char* sA = xe_raw + ((128 - (smem_addr(xe_raw) & 127)) & 127);  // two tile images
   unsigned char* sB = sA + 2 * XA_TILE;                                     // two K steps
-  __shared__ int lj[XJ], shj[XJ], emv2[2][XVB], evx[XVB];
+  __shared__ int lj[XJ], shj[XJ], emv2[2][XVB];
+  __shared__ __align__(16) int evx[XVB];
   __shared__ __align__(8) unsigned long long abar[2], mdone[2], bfree[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_next, s_fail;
@@ -1224,7 +1225,9 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
       } else {
         const int vv0 = 8 * (warp >> 2);
         for (int c = 0; c < nchunk; ++c) {
-          double vals[8];
+          const int vbase = vb + c * XN + vv0;  // this warp's first vector of the chunk
+          double* o = out + (size_t)vbase * ng + (g >= 0 ? g : 0);
+          const bool full = vbase + 8 <= m;
           if (nJ > 0) {
             const long long seq = cg + c;
             const int tb = (int)(seq & 1);
@@ -1233,34 +1236,39 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
               break;
             }
             tc_fence_after();
-            uint32_t f[DIG][8];
             const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
                                        (uint32_t)(tb * XT_COLS + vv0);
+            const int4 e4[2] = {*reinterpret_cast<const int4*>(evx + c * XN + vv0),
+                                *reinterpret_cast<const int4*>(evx + c * XN + vv0 + 4)};
+            const int ev[8] = {e4[0].x, e4[0].y, e4[0].z, e4[0].w, e4[1].x, e4[1].y, e4[1].z, e4[1].w};
+            // four vectors at a time: six diagonal sums each
 #pragma unroll
-            for (int d = 0; d < DIG; ++d) tmem_ld8(lane_addr + (uint32_t)(d * XN), f[d]);
-            tmem_wait_ld();
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bf[tb]) : "memory");
+            for (int hh = 0; hh < 2; ++hh) {
+              uint32_t f[DIG][4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              // sum_d D_d 256^(5 - d), |D_d| < 2^22, in three 32-bit pairs
-              const int t01 = small_float_int(f[0][u]) * 256 + small_float_int(f[1][u]);
-              const int t23 = small_float_int(f[2][u]) * 256 + small_float_int(f[3][u]);
-              const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
-              const long long acc =
-                  ((long long)t01 << 32) + ((long long)t23 << 16) + (long long)t45;
-              vals[u] = scaled_i64_rz(acc, evx[c * XN + vv0 + u] - 1022 - 54);
+              for (int d = 0; d < DIG; ++d) tmem_ld4(lane_addr + (uint32_t)(d * XN + 4 * hh), f[d]);
+              tmem_wait_ld();
+              if (hh == 1) {  // the buffer is read: the next MMAs may overwrite it
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bf[tb]) : "memory");
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                // sum_d D_d 256^(5 - d), |D_d| < 2^22, in three 32-bit pairs
+                const int t01 = small_float_int(f[0][u]) * 256 + small_float_int(f[1][u]);
+                const int t23 = small_float_int(f[2][u]) * 256 + small_float_int(f[3][u]);
+                const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
+                const long long base = ((long long)t01 << 32) + (long long)t45;
+                const long long acc = base + (long long)t23 * 65536LL;
+                const double v = scaled_i64_rz(acc, ev[4 * hh + u] - 1022 - 54);
+                if (g >= 0 && (full || vbase + 4 * hh + u < m)) o[(size_t)(4 * hh + u) * ng] = v;
+              }
             }
-          } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) vals[u] = 0.0;
-          }
-          if (g >= 0) {
-            double* o = out + (size_t)(vb + c * XN + vv0) * ng + g;
+          } else if (g >= 0) {
 #pragma unroll
             for (int u = 0; u < 8; ++u)
-              if (vb + c * XN + vv0 + u < m) o[(size_t)u * ng] = vals[u];
+              if (full || vbase + u < m) o[(size_t)u * ng] = 0.0;
           }
         }
       }
