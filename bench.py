@@ -512,12 +512,48 @@ def run_batched(args, sea, torch, dev, budget_gb=140.0):
                         f"{budget_gb:.0f} GB of device arrays, one batched call per group"}
 
 
+def _eval_warm(net, sea, torch, phi, cell, grid, out):
+    """CG work and apply_vxx time with and without the learned warm start,
+    both forms, on the orbitals phi (device tensor): one warm-up call and one
+    timed call per case."""
+    res = {}
+    for name, prec in (("plain", 0), ("mixed", 1)):
+        row = {}
+        for mode in (0, 1):
+            ctx = sea.Context(cell, grid, precision=prec, warm_start=mode)
+            if mode:
+                net.attach(ctx)
+            ctx.set_orbitals(phi)
+            ctx.apply_vxx(out)  # warm-up
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            e = ctx.apply_vxx(out)
+            ev1.record()
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            key = "warm" if mode else "cold"
+            row[key] = {"cg_iters_mean": st["cg_iters_mean"], "cg_unknown_iters": st["cg_unknown_iters"],
+                        "ms_apply_vxx": ev0.elapsed_time(ev1), "ms_setup": st["ms_setup"],
+                        "ms_cg": st["ms_cg"], "exx": e, "n_pairs": st["n_pairs"]}
+            if mode:
+                sea.WarmStartNet.detach(ctx)
+            ctx.close()
+        row["cg_work_saved_frac"] = 1.0 - row["warm"]["cg_unknown_iters"] / max(row["cold"]["cg_unknown_iters"], 1.0)
+        row["ms_cg_saved"] = row["cold"]["ms_cg"] - row["warm"]["ms_cg"]
+        row["ms_network"] = row["warm"]["ms_setup"] - row["cold"]["ms_setup"]
+        row["exx_rel_diff"] = abs(row["warm"]["exx"] - row["cold"]["exx"]) / abs(row["cold"]["exx"])
+        res[name] = row
+    return res
+
+
 def run_warm_start(args, sea, synth, torch, dev, s, width=16, train_seeds=(2001, 2002), steps=400,
-                   batch=8):
+                   batch=8, large=True):
     """The learned warm start: a width-16 U-Net trained on the pair solves of
     two other seeded (H2O)64-like systems (plain CG), then CG iterations and
-    apply_vxx time with and without it on the benchmark system (outside the
-    timed region)."""
+    apply_vxx time with and without it on the benchmark system and on the
+    (H2O)256-like system (1024 orbitals, L = 24.84 A, 192^3, seed 1005,
+    generated on the device) (outside the timed region)."""
     t0 = time.perf_counter()
     net = sea.WarmStartNet(width=width, seed=11)
     for seed in train_seeds:
@@ -539,32 +575,26 @@ def run_warm_start(args, sea, synth, torch, dev, s, width=16, train_seeds=(2001,
            "train_samples": n_samples, "train_steps": steps + 1, "batch": batch,
            "loss_first": loss0, "loss_last": loss1, "train_s": t_train,
            "eval": "the benchmark system (not in the training set), cg_tol 1e-8"}
-    for name, prec in (("plain", 0), ("mixed", 1)):
-        row = {}
-        for mode in (0, 1):
-            ctx = sea.Context(s.cell, s.grid, precision=prec, warm_start=mode)
-            if mode:
-                net.attach(ctx)
-            ctx.set_orbitals(phi)
-            ctx.apply_vxx(out)  # warm-up
+    res.update(_eval_warm(net, sea, torch, phi, s.cell, s.grid, out))
+    del phi, out
+    if large:
+        phi = out = None
+        try:
+            t1 = time.perf_counter()
+            phi, cell, grid = synth.make_waters_device(256, 24.84, 192, 1005, dev)
             torch.cuda.synchronize()
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record()
-            e = ctx.apply_vxx(out)
-            ev1.record()
-            torch.cuda.synchronize()
-            st = ctx.stats()
-            key = "warm" if mode else "cold"
-            row[key] = {"cg_iters_mean": st["cg_iters_mean"], "cg_unknown_iters": st["cg_unknown_iters"],
-                        "ms_apply_vxx": ev0.elapsed_time(ev1), "ms_setup": st["ms_setup"],
-                        "ms_cg": st["ms_cg"], "exx": e}
-            if mode:
-                sea.WarmStartNet.detach(ctx)
-            ctx.close()
-        row["cg_work_saved_frac"] = 1.0 - row["warm"]["cg_unknown_iters"] / max(row["cold"]["cg_unknown_iters"], 1.0)
-        row["ms_network"] = row["warm"]["ms_setup"] - row["cold"]["ms_setup"]
-        row["exx_rel_diff"] = abs(row["warm"]["exx"] - row["cold"]["exx"]) / abs(row["cold"]["exx"])
-        res[name] = row
+            t_gen = time.perf_counter() - t1
+            torch.cuda.empty_cache()
+            out = torch.empty_like(phi)
+            big = _eval_warm(net, sea, torch, phi, cell, grid, out)
+            big["generation_s"] = t_gen
+        except (RuntimeError, sea.SeaError) as exc:  # device memory: reported, not fatal
+            big = {"error": str(exc)[:300]}
+        big["system"] = ("(H2O)256-like, 1024 orbitals, L = 24.84 A, 192^3 grid, seed 1005 "
+                         "(generated on the device), cg_tol 1e-8")
+        res["h2o256_192"] = big
+        del phi, out
+        torch.cuda.empty_cache()
     net.close()
     return res
 

@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(256)
 // W digits are in buffer wb.
 struct Unit {
   int T, j0, nJ, jb, mb, h, wb;
+  int ab;  // parity of the A block in processing order (TMA kernel: its exponent buffer)
 };
 
 
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
   unsigned char* sR = gt_raw + ((1024 - (smem_addr(gt_raw) & 1023)) & 1023);  // two K halves
   unsigned char* sA = sR + 2 * RAW_KHALF;
   unsigned char* sW = sA + SMEM_A2;
-  __shared__ int Aexp[2][MBLK], Wexp[2][NBLK];  // [half][row]
+  __shared__ int Aexp[2][2][MBLK], Wexp[2][NBLK];  // [A block parity][half][row], [half][slot]
   __shared__ __align__(8) unsigned long long mbar[2], tbar[2], rbar[2];
   __shared__ int u_ring[2][2];  // per posted unit: W block width (0: end), half
   __shared__ uint32_t tmem_base;
@@ -734,6 +735,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         return true;
       }
       u.h = 0;
+      u.ab ^= 1;
       if (++u.mb < nmb) return true;
       u.mb = 0;
       *new_block = true;
@@ -793,7 +795,8 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
       const int quarter = warp & 3, g = warp >> 2, ng4 = GT2_CONV / 128;
       const int a = u.mb * MBLK + 32 * quarter + lane;
       const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
-      const int ea0 = Aexp[0][32 * quarter + lane] - 1022, ea1 = Aexp[1][32 * quarter + lane] - 1022;
+      const int ea0 = Aexp[u.ab][0][32 * quarter + lane] - 1022,
+                ea1 = Aexp[u.ab][1][32 * quarter + lane] - 1022;
 #pragma unroll 1
       for (int c = g; c < nj; c += ng4) {
         uint32_t f[2 * DIG];
@@ -838,9 +841,15 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
 
     Unit cur;
     cur.wb = 0;
+    cur.ab = 0;
     bool have_prev = false, fail = false;  // fail: uniform over the converting threads
     Unit prev = cur;
     int seq = 0;
+    // Per unit two barriers of the converting warps: B1 once every thread
+    // holds its values (the raw buffers may be refilled), B2 once the digits
+    // of both K halves, a new W block and the exponents are in place (both K
+    // halves are then posted).  The digit buffers are guarded per thread by
+    // the MMA completion barriers, the A exponents double-buffered by A block.
     if (claim(cur)) {
       load_w(cur);
       if (tid == 0) {
@@ -852,10 +861,6 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         // both K halves of cur to registers; the row's exponent
         bool ok = wait_raw(0);
         ok = wait_raw(1) && ok;
-        if (conv_sync_or(!ok)) {
-          fail = true;
-          break;
-        }
         double v[2][8];
         uint32_t emf = 0;  // largest exponent field (high-word bits 20..30) of the row segment
 #pragma unroll
@@ -874,7 +879,10 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         const int em = (int)(emf >> 20);
         const uint32_t em_sh = em < 64 ? 0xF0000000u : emf + (5u << 20);
         if (tid == 0) q_step();
-        conv_sync();  // both raw buffers consumed
+        if (conv_sync_or(!ok)) {  // B1: both raw buffers consumed
+          fail = true;
+          break;
+        }
         Unit next = cur;
         bool new_block = false;
         const bool has_next = advance(next, &new_block);  // may claim (uniform, syncs)
@@ -882,42 +890,32 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
           tma_issue(next, 0);
           tma_issue(next, 1);
         }
-        // K half 0's digits replace those prev's first MMAs read; the
-        // epilogue and a new W block need all of prev's MMAs
-        ok = wait_mma(0);
+        // each K half's digits replace those prev's MMAs of that half read
         uint4 d[DIG];
+        ok = wait_mma(0);
         digits8_u(v[0], em_sh, d);
         store_digits(d, 0);
-        if (have_prev && (prev.h == 1 || need_w)) ok = wait_mma(1) && ok;
-        if (conv_sync_or(!ok)) {
-          fail = true;
-          break;
-        }
+        ok = wait_mma(1) && ok;
+        digits8_u(v[1], em_sh, d);
+        store_digits(d, 1);
         tc_fence_after();
-        if (have_prev && prev.h == 1) {
-          epilogue(prev);
-          conv_sync();  // exponents and W read before they are replaced
+        if (have_prev && prev.h == 1) epilogue(prev);  // all of prev's MMAs are done
+        if (need_w) {
+          conv_sync();  // every epilogue has read W's exponents
+          load_w(cur);
         }
-        if (need_w) load_w(cur);
-        if (run == 0) Aexp[cur.h][row] = em;
+        if (run == 0) Aexp[cur.ab][cur.h][row] = em;
         cp_async_wait_all();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_fence_before();
-        conv_sync();  // digits of K half 0, W and exponents in place
-        post(seq, min(NBLK, cur.nJ - cur.jb), cur.h);
-        mma_pend[0] = true;
-        digits8_u(v[1], em_sh, d);
-        ok = wait_mma(1);  // prev's MMAs of K half 1
-        store_digits(d, 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        ++seq;
-        if (conv_sync_or(!ok)) {  // digits of K half 1 in place
+        if (conv_sync_or(!ok)) {  // B2: digits, W and exponents in place
           fail = true;
           break;
         }
+        post(seq, min(NBLK, cur.nJ - cur.jb), cur.h);
         if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(rb[1]) : "memory");
-        mma_pend[1] = true;
+        ++seq;
+        mma_pend[0] = mma_pend[1] = true;
         prev = cur;
         have_prev = true;
         if (!has_next) break;
