@@ -116,13 +116,15 @@ def job_value(steps, ws, t_ms_max):
     return ws * steps / (t_ms_max / 1e3)
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
-# ncu capture of the benchmark workload with the current kernels; see
-# profiles/dram_traffic_h2o64_96.md).  None: not captured.
+# DRAM traffic per launch at the benchmark size (dram__bytes_read.sum +
+# dram__bytes_write.sum): captured with the current kernels on the 48^3
+# profiling case and scaled by the units processed (each operand is read or
+# written once, so the traffic grows in proportion); see
+# profiles/dram_traffic_h2o64_96.md.  None: not captured.
 DRAM_BYTES_PER_LAUNCH = {
     "k_cg_mixed": 26.8e6,
-    "k_gram_tc": 2.025e9,
-    "k_expand_tc": 1.984e9,
+    "k_gram_tc": 2.08e9,
+    "k_expand_tc": 1.98e9,
 }
 
 
@@ -313,12 +315,12 @@ def run_ours(args, ws, rank, local):
                      "sampled SM clock; algorithmic bytes: the 37 stencil loads (4 B) per "
                      "unknown and inner FP32 iteration"))
         note_gt = ("HBM of measured (copy); algorithmic bytes: the A rows on the tiles where W is "
-                   "nonzero (8 B per point), W's BF16 digit planes (1536 B per tile slot and "
+                   "nonzero (8 B per point), W's FP16 digit planes (1536 B per tile slot and "
                    "128-row block), the FP64 partials written")
         slots = st["ace_support_points"] / 128  # total W list length over the tiles
         gram_bytes = (n * 128 * 8.0 * tiles_w + 1536.0 * slots * ((n + 127) // 128) +
                       8.0 * slots * n)
-        cand.append(("k_gram_tc (tensor-core M = Phi^T W and W^T psi, exact BF16 digits)",
+        cand.append(("k_gram_tc (tensor-core M = Phi^T W and W^T psi, exact FP16 digits)",
                      gram_ms, 2, gram_bytes, hbm, "hbm", note_gt))
         note_x = ("HBM of measured (copy); algorithmic bytes: the FP64 output (8 B per grid "
                   "point and vector) and W's per-tile BF16 digit image (24 KB per tile with "
