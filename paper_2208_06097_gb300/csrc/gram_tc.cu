@@ -670,7 +670,10 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
   } else {
     // ---- the converting warps ----
     const int nmb = (m + MBLK - 1) / MBLK;
-    bool tma_pending[2] = {false, false};  // meaningful in thread 0
+    // the thread that issues the A rows' TMA loads (lane 0 of the last
+    // converting warp: thread 0 already claims the tiles)
+    constexpr int TMA_TID = GT2_CONV - 32;
+    bool tma_pending[2] = {false, false};  // meaningful in TMA_TID
     // this thread's row and x-run, and the swizzled offset of its run
     const int row = tid >> 2, run = tid & 3;
     const uint32_t r_off = (uint32_t)(row * 256 + run * 64);
@@ -774,7 +777,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
     auto wait_raw = [&](int q) -> bool {
       const bool ok = mbar_wait(tb[q], tphase[q]);
       tphase[q] ^= 1;
-      if (tid == 0) tma_pending[q] = false;
+      if (tid == TMA_TID) tma_pending[q] = false;
       return ok;
     };
     auto wait_mma = [&](int q) -> bool {
@@ -852,7 +855,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
     // the MMA completion barriers, the A exponents double-buffered by A block.
     if (claim(cur)) {
       load_w(cur);
-      if (tid == 0) {
+      if (tid == TMA_TID) {
         tma_issue(cur, 0);
         tma_issue(cur, 1);
       }
@@ -886,7 +889,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         Unit next = cur;
         bool new_block = false;
         const bool has_next = advance(next, &new_block);  // may claim (uniform, syncs)
-        if (tid == 0 && has_next) {
+        if (tid == TMA_TID && has_next) {
           tma_issue(next, 0);
           tma_issue(next, 1);
         }
@@ -939,7 +942,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
       for (int q = 0; q < 2; ++q)
         if (mma_pend[q]) mbar_wait(mb[q], mphase[q]);
       // loads still in flight land before the CTA's shared memory is released
-      if (tid == 0)
+      if (tid == TMA_TID)
         for (int q = 0; q < 2; ++q)
           if (tma_pending[q]) mbar_wait(tb[q], tphase[q]);
     }
