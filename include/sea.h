@@ -72,8 +72,9 @@ typedef enum {
  * FP32 step lengths; the multipole moments, boundary values and far-field
  * products in double-float arithmetic (pairs of FP32 values, about 48
  * bits); the two contractions with W (M = Phi^T W dV, W^T psi, W H) on the
- * tensor cores from exact BF16 digit splits of FP64 values, truncated at
- * 2^-47 of each 64-point segment's largest value; the Cholesky diagonal
+ * tensor cores from exact digit splits of FP64 values (FP16 digits in the
+ * contraction, BF16 digits in the expansion), truncated at 2^-47 of each
+ * 64-point segment's largest value; the Cholesky diagonal
  * blocks in double-float, the rest of the Cholesky and L^-1 in FP64),
  * warm_start = 0
  * (1: every pair's CG starts from the attached learned model's guess and

@@ -376,6 +376,8 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   if (!c->have_phi) return sea_fail(c, SEA_ERR_STATE, "sea_set_orbitals first");
   if (!vxx_phi) return sea_fail(c, SEA_ERR_ARG, "vxx_phi is NULL");
   c->have_vxx = c->have_ace = false;
+  sea::Trace tr("sea_apply_vxx");
+  tr.stage("plan");
   SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
   SEA_CK(cudaEventRecord(c->ev[0], c->stream), "event");
   SEA_CK(sea::launch_plan_boxes(c), "domain boxes");
@@ -408,18 +410,22 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_ALLOC(Q, (size_t)std::max(c->P, 1) * SEA_NQ * sizeof(double));
   SEA_ALLOC(epair, (size_t)std::max(c->P, 1) * sizeof(double));
   SEA_ALLOC(iters, (size_t)std::max(c->P, 1) * sizeof(int));
+  tr.stage("pair setup");
   SEA_CK(sea::launch_pair_setup(c), "pair setup");
   c->cg_warm = false;
   if (c->prm.warm_start == 1) {  // learned initial guesses (the model's time counts as setup)
     if (!c->unet) return sea_fail(c, SEA_ERR_STATE, "warm_start = 1 needs sea_unet_attach");
+    tr.stage("warm start");
     const cudaError_t e = sea::launch_warm_start(c);
     if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "warm-start workspace");
     SEA_CK(e, "warm start");
     c->cg_warm = true;
   }
   SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
+  tr.stage("cg");
   SEA_CK(sea::launch_cg(c), "cg");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
+  tr.stage("far field and accumulation");
   double* vd = (double*)c->vxx_dev.p;
   if (on_device) {
     SEA_CK(sea::launch_accumulate(c, vd, vxx_phi), "accumulate");
@@ -495,6 +501,8 @@ static sea_status build_ace_common(sea_ctx* c) {
   c->stats.ace_eigen_sweeps = 0;
   c->stats.ace_negative_eigenvalues = 0;
   c->stats.ace_dropped_eigenvalues = 0;
+  sea::Trace tr("sea_build_ace");
+  tr.stage("M and Cholesky");
   SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
   SEA_CK(cudaEventRecord(c->ev[5], c->stream), "event");
   cudaError_t e = sea::launch_ace_build(c);
@@ -508,6 +516,7 @@ static sea_status build_ace_common(sea_ctx* c) {
     return sea_fail(c, SEA_ERR_CUDA, "a tensor-core completion wait timed out (M build)");
   const bool not_pd = (st & SEA_FLAG_NOT_PD) != 0;
   if ((not_pd && c->prm.ace_decomp == 0) || c->prm.ace_decomp == 2) {
+    tr.stage("eigen-decomposition");
     e = sea::launch_ace_eigen(c);
     if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE eigen workspace");
     SEA_CK(e, "ace eigen form");
@@ -562,6 +571,7 @@ sea_status sea_apply_ace(sea_ctx* c, const double* psi, int n_vec, double* out, 
   if (c->poisoned) return sea_fail(c, SEA_ERR_STATE, "context poisoned by an earlier CUDA error");
   if (!c->have_ace) return sea_fail(c, SEA_ERR_STATE, "sea_build_ace first");
   if (!psi || !out || n_vec < 1) return sea_fail(c, SEA_ERR_ARG, "bad psi/out");
+  sea::Trace tr("sea_apply_ace");
   const size_t bytes = (size_t)n_vec * c->ng * sizeof(double);
   if (on_device) {
     SEA_CK(cudaEventRecord(c->ev[7], c->stream), "event");

@@ -120,6 +120,8 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
   }
   sea_ctx* c0 = ctxs[0];
   cudaStream_t st = c0->stream;
+  sea::Trace tr("sea_apply_vxx_batch");
+  tr.stage("plans");
   // plans
   for (int k = 0; k < n; ++k) {
     sea_ctx* c = ctxs[k];
@@ -283,6 +285,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
   };
   c0->stats.batch_tune_ms = 0.0;
   if (!have_tuned && total > 0) {
+    tr.stage("autotuning");
     // every order x every grid size, one timed CG launch each (after one
     // warm-up launch), on the batch's own pairs; the pair setup runs once
     float t_tune = 0.f;
@@ -345,6 +348,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
                             cudaMemcpyHostToDevice, st),
             "items");
   }
+  tr.stage("post-plan phase");
   c0->stats.batch_order = tuned.order;
   c0->stats.batch_ctas_per_sm = tuned.per_sm_mixed;
   c0->stats.batch_ctas_per_sm_fp64 = tuned.per_sm_fp64;

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstddef>
@@ -33,6 +34,28 @@
 #define SEA_XCHUNKS_MAX 64
 
 namespace sea {
+
+// NVTX ranges of an entry point and its stages, for timeline tools (Nsight
+// Systems, or ncu's --nvtx filters); without an attached tool each push and
+// pop is a test of one function pointer.  The ranges mark where the host
+// enqueues each stage's launches; the stage times on the device are the
+// CUDA-event times in sea_stats.  stage() closes the previous stage's range
+// and opens the next; the destructor closes the open stage and the call.
+struct Trace {
+  explicit Trace(const char* call) { nvtxRangePushA(call); }
+  void stage(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~Trace() {
+    if (open) nvtxRangePop();
+    nvtxRangePop();
+  }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+  bool open = false;
+};
 
 __host__ __device__ inline int wrapi(int x, int n) {
   int r = x % n;
