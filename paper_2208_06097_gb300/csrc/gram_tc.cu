@@ -970,23 +970,22 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
 // E_j cancels and every D_d (at most 32 x 6 products of magnitude <= 2^14)
 // is an integer below 2^24, exact in the FP32 accumulator.  W's digits are
 // formed once per W into a per-tile image in the K-major layout (two K steps
-// of 16 list entries, six planes, 4 KB each); H's digits per tile, for 256
-// vectors at a time, into shared memory with the six planes of each chunk
-// of 32 vectors stacked along N, so one MMA of A plane k against planes
-// 0..5-k adds plane k's products to diagonals k..5 (TMEM columns 32 d).
-// Two accumulator buffers of 192 columns: the MMAs of chunk c + 1 run while
-// chunk c's epilogue reads its buffer back.
+// of 16 list entries, six planes, 4 KB each); H's digits per chunk of 32
+// vectors into a slot of a shared-memory ring with the six planes stacked
+// along N, so one MMA of A plane k against planes 0..5-k adds plane k's
+// products to diagonals k..5 (TMEM columns 32 d).  Two accumulator buffers
+// of 192 columns: the MMAs of chunk c + 1 run while chunk c's epilogue reads
+// its buffer back, and the digits of the following chunks are formed
+// meanwhile by warps of their own.
 // ---------------------------------------------------------------------------
-constexpr int XJ = 32, XKS = 16, XN = 32, XVB = 256;
+constexpr int XJ = 32, XKS = 16, XN = 32;
 constexpr uint32_t XA_BLOCK = MBLK * XKS * 2;          // 4 KB: one plane, one K step
 constexpr uint32_t XA_LBO = (MBLK / 8) * 128;          // 2048
 constexpr uint32_t XA_STEP = DIG * XA_BLOCK;           // 24 KB
 constexpr uint32_t XA_TILE = 2 * XA_STEP;              // 48 KB
 constexpr uint32_t XB_LBO = (DIG * XN / 8) * 128;      // 3072
 constexpr uint32_t XB_CHUNK = 2 * XB_LBO;              // 6 KB: 192 rows x 16 K
-constexpr uint32_t XB_STEP = (XVB / XN) * XB_CHUNK;    // 48 KB
 constexpr uint32_t XT_COLS = DIG * XN;                 // 192
-constexpr size_t XE_SMEM = 2 * XA_TILE + 2 * XB_STEP + 256;
 
 // W's digit image: CTA per tile (thread = point p), for tiles whose list has
 // 1..XJ entries.  wx[T][(q 6 + k) 4096 + (p / 8) 128 + (jq / 8) 2048 +
@@ -1047,17 +1046,37 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 }
 
 
-constexpr int XE_WARPS = 16;                       // digit and epilogue warps
-constexpr int XE_THREADS = 32 * (XE_WARPS + 1);    // and one MMA-issuing warp
+constexpr int XE_WARPS = 16;                 // epilogue warps (tensor-memory read-back, stores)
+constexpr int XP_WARPS = 8;                  // H-digit warps
+constexpr int XE_ISSUER = XE_WARPS + XP_WARPS;           // the MMA-issuing warp
+constexpr int XE_THREADS = 32 * (XE_ISSUER + 1);         // 800
+constexpr int XR = 4;                                    // ring slots (chunks of XN vectors)
+constexpr uint32_t XS_SLOT = 2 * XB_CHUNK;               // 12 KB: both K steps of one chunk
+constexpr size_t XE_SMEM = 2 * XA_TILE + XR * XS_SLOT + 128;
+constexpr int XF_FIRST = 1, XF_LAST = 2, XF_END = 4;    // slot flags
 
 // Persistent CTAs (one per SM) over the tiles whose list has at most XJ
-// entries.  Warps 0..15 form H's digits and read the accumulators back
-// (warp w: tensor-memory lanes 32 (w % 4), vectors 8 (w / 4) .. + 7 of a
-// chunk); warp 16 issues the MMAs.  Per accumulator buffer two mbarriers:
-// MMAs done (tcgen05.commit) and buffer read back (one arrival per
-// epilogue warp, right after its tensor-memory loads), so chunk c + 2's
-// MMAs start while chunk c's outputs are still being converted and
-// stored.  H(j, v) = H[j hj + v hv]; out[v ng + r].
+// entries, in three roles that run side by side.
+//  * H-digit warps (XP_WARPS): claim the tiles, bring each tile's W digit
+//    image in (bulk copy, two buffers), and for every chunk of XN = 32
+//    vectors of the tile form E_v and H's digits into the next slot of a
+//    ring of XR chunks, with the chunk's tile, first vector and E_v beside
+//    it; a slot is refilled once its MMAs are done and the epilogue warps
+//    have read its E_v.
+//  * The issuing warp: per chunk, once its slot is full (and, at a tile's
+//    first chunk, the tile's W image is in) and the accumulator buffer it
+//    takes is free, the chunk's MMAs into one of two buffers of 192
+//    tensor-memory columns, committed to that buffer's barrier, to the
+//    slot's and, at a tile's last chunk, to the W image's.
+//  * Epilogue warps (16): warp w reads tensor-memory lanes 32 (w % 4) back
+//    for vectors 8 (w / 4) .. + 7 of each chunk, combines the diagonal sums
+//    and stores the FP64 outputs; zero tiles (empty list) are stored as
+//    zeros without MMAs.
+// So the digits of the next chunks and the MMAs of the next chunk run while
+// a chunk's outputs are being converted and stored.  H(j, v) = H[j hj + v
+// hv]; out[v ng + r].  Every wait is bounded; on expiry the role stops, the
+// others see s_fail (or expire themselves) and the kernel reports
+// SEA_FLAG_WAIT after the MMAs and copies in flight are done.
 __global__ void __launch_bounds__(XE_THREADS, 1)
     k_expand_tc(const uint4* __restrict__ wx, const int* __restrict__ wxexp, TileGeom G, size_t ng,
                 int n_tiles, const int* __restrict__ tptr, const int* __restrict__ tlist,
@@ -1065,17 +1084,15 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
                 double* __restrict__ out, int* __restrict__ queue, unsigned* __restrict__ status) {
   extern __shared__ unsigned char xe_raw[];
   unsigned char* sA = xe_raw + ((128 - (smem_addr(xe_raw) & 127)) & 127);  // two tile images
-  unsigned char* sB = sA + 2 * XA_TILE;                                     // two K steps
-  __shared__ int lj[XJ], shj[XJ], emv2[2][XVB];
-  __shared__ __align__(16) int evx[XVB];
-  __shared__ __align__(8) unsigned long long abar[2], mdone[2], bfree[2];
+  unsigned char* sS = sA + 2 * XA_TILE;                                     // XR chunk slots
+  __shared__ int s_T[XR], s_nJ[XR], s_v0[XR], s_fl[XR], s_ab[XR];
+  __shared__ __align__(16) int s_ev[XR][XN];
+  __shared__ int p_lj[XJ], p_shj[XJ], p_em[2][XP_WARPS][XN], p_tile;
+  __shared__ __align__(8) unsigned long long bar_full[XR], bar_free[XR], bar_md[2], bar_tf[2],
+      bar_a[2], bar_af[2], bar_fin;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_next, s_fail;
+  __shared__ volatile int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool issuer = warp == XE_WARPS;
-  const uint32_t ab[2] = {smem_addr(&abar[0]), smem_addr(&abar[1])};
-  const uint32_t md[2] = {smem_addr(&mdone[0]), smem_addr(&mdone[1])};
-  const uint32_t bf[2] = {smem_addr(&bfree[0]), smem_addr(&bfree[1])};
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&tmem_base)),
@@ -1083,11 +1100,17 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ab[q]));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(md[q]));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bf[q]), "r"(XE_WARPS));
+    for (int q = 0; q < XR; ++q) {
+      mbar_init(smem_addr(&bar_full[q]), XP_WARPS);
+      mbar_init(smem_addr(&bar_free[q]), 1 + XE_WARPS);
     }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_addr(&bar_md[q]), 1);
+      mbar_init(smem_addr(&bar_tf[q]), XE_WARPS);
+      mbar_init(smem_addr(&bar_a[q]), 1);
+      mbar_init(smem_addr(&bar_af[q]), 1);
+    }
+    mbar_init(smem_addr(&bar_fin), 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_fail = 0;
   }
@@ -1095,200 +1118,276 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
-  const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
-  uint32_t aphase[2] = {0, 0};
-  bool a_pending[2] = {false, false};  // thread 0's bookkeeping
-  long long cg = 0;                    // chunks with MMAs so far (uniform)
-  auto list_len = [&](int T) { return tptr[T + 1] - tptr[T]; };
-  auto claim = [&]() -> int {
-    __syncthreads();
-    if (tid == 0) {
-      int t;
-      do {
-        t = atomicAdd(queue, 1);
-      } while (t < n_tiles && list_len(t) > XJ);
-      s_next = t;
-    }
-    __syncthreads();
-    return s_next;
-  };
-  auto prefetch = [&](int T, int b) {  // thread 0: W digit image of tile T into buffer b
-    const int nJ = list_len(T);
-    if (nJ == 0) return;
-    const uint32_t bytes = (uint32_t)((nJ + XKS - 1) / XKS) * XA_STEP;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(ab[b], bytes);
-    bulk_load(a_base + b * XA_TILE, reinterpret_cast<const unsigned char*>(wx) + (size_t)T * XA_TILE,
-              bytes, ab[b]);
-    a_pending[b] = true;
-  };
-  int T = claim(), buf = 0;
-  if (tid == 0 && T < n_tiles) prefetch(T, 0);
-  while (T < n_tiles) {
-    const int Tn = claim();
-    if (s_fail) break;
-    if (tid == 0 && Tn < n_tiles) prefetch(Tn, buf ^ 1);
-    const int j0 = tptr[T], nJ = list_len(T), nq = (nJ + XKS - 1) / XKS;
-    if (tid < XJ && tid < nJ) {
-      lj[tid] = tlist[j0 + tid];
-      shj[tid] = wxexp[j0 + tid] - 1022;
-    }
-    const int p = 32 * (warp & 3) + lane;  // epilogue point (tensor-memory lane)
-    const long long g = issuer ? -1 : tile_point(G, T, p);
-    bool a_ready = nJ == 0;
-    for (int vb = 0; vb < m; vb += XVB) {
-      __syncthreads();  // lj/shj visible; the previous block's MMAs and read-backs are done
-      if (s_fail) break;
-      const int vl = tid & (XVB - 1), q = tid >> 8;  // thread pair per vector: K step q
-      const int v = vb + vl;
-      if (nJ > 0) {
-        // E_v over the list (two partial maxima), then the digits of K step q
-        double hreg[XKS];
+  const uint32_t a_base = smem_addr(sA), s_base = smem_addr(sS);
+  const int nch = (m + XN - 1) / XN;  // chunks per tile
+
+  if (warp >= XE_WARPS && warp < XE_ISSUER) {
+    // ---- H-digit warps: lane = vector of the chunk, warp pw = list entries
+    // jp pw .. jp pw + jp - 1 with jp = 2 nq (so every warp has work) ----
+    const int pw = warp - XE_WARPS, ptid = tid - 32 * XE_WARPS;
+    auto pbar = [&]() { asm volatile("bar.sync 1, %0;" ::"n"(32 * XP_WARPS) : "memory"); };
+    auto pbar_or = [&](bool v) -> bool {
+      uint32_t r;
+      asm volatile(
+          "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, %2, p;\n"
+          "selp.u32 %0, 1, 0, q;\n}\n"
+          : "=r"(r)
+          : "r"((uint32_t)v), "n"(32 * XP_WARPS)
+          : "memory");
+      return r != 0;
+    };
+    int pseq = 0, tseq = 0;               // chunks published; tiles whose W image was loaded
+    uint32_t a_pend = 0, a_par = 0;       // ptid 0, bit b: a load into image buffer b was
+                                          // issued; the parity of its completion
+    bool fail = false;
+    for (;;) {
+      if (ptid == 0) {
+        int t;
+        do {
+          t = atomicAdd(queue, 1);
+        } while (t < n_tiles && tptr[t + 1] - tptr[t] > XJ);
+        p_tile = t;
+      }
+      pbar();
+      const int T = p_tile;
+      const bool end = T >= n_tiles;
+      const int j0 = end ? 0 : tptr[T], nJ = end ? 0 : tptr[T + 1] - j0;
+      const int nq = (nJ + XKS - 1) / XKS, ab = tseq & 1, jp = 2 * nq, jb = jp * pw;
+      if (ptid < nJ) {
+        p_lj[ptid] = tlist[j0 + ptid];
+        p_shj[ptid] = wxexp[j0 + ptid] - 1022;
+      }
+      bool ok = true;
+      if (ptid == 0 && nJ > 0) {
+        // the image buffer is free once the MMAs of the tile two back are done
+        if (tseq >= 2) ok = mbar_wait(smem_addr(&bar_af[ab]), (uint32_t)(((tseq - 2) >> 1) & 1));
+        if (ok) {
+          const uint32_t bytes = (uint32_t)nq * XA_STEP;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect_tx(smem_addr(&bar_a[ab]), bytes);
+          bulk_load(a_base + ab * XA_TILE,
+                    reinterpret_cast<const unsigned char*>(wx) + (size_t)T * XA_TILE, bytes,
+                    smem_addr(&bar_a[ab]));
+          a_pend |= 1u << ab;
+          a_par = (a_par & ~(1u << ab)) | ((uint32_t)((tseq >> 1) & 1) << ab);
+        }
+      }
+      if (pbar_or(!ok || s_fail)) {  // p_lj, p_shj visible
+        fail = true;
+        break;
+      }
+      // H(j, v) of this thread's entries for chunk c (sign folded in), zero
+      // beyond the list and the vectors
+      auto load_h = [&](int c, double (&h)[4]) {
+        const int v = c * XN + lane;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int jl = jb + i;
+          h[i] = (i < jp && v < m && jl < nJ) ? H[(long long)p_lj[jl] * hj + (long long)v * hv] : 0.0;
+          if (negate)  // the sign of y folded into H's digits (sign bit, exact)
+            h[i] = __longlong_as_double(__double_as_longlong(h[i]) ^ (long long)0x8000000000000000ULL);
+        }
+      };
+      double h[4];
+      if (nJ > 0) load_h(0, h);
+      for (int c = 0; c < (end ? 1 : nch); ++c, ++pseq) {
+        const int slot = pseq % XR, use = pseq / XR;
+        // the slot is free once its previous chunk's MMAs are done and its
+        // E_v was read
+        ok = true;
+        if (ptid == 0 && use >= 1) ok = mbar_wait(smem_addr(&bar_free[slot]), (uint32_t)((use - 1) & 1));
         int em = 0;
-        if (!issuer) {
+        if (nJ > 0) {
 #pragma unroll
-          for (int i = 0; i < XKS; ++i) {
-            const int jl = q * XKS + i;
-            hreg[i] = (v < m && jl < nJ) ? H[(long long)lj[jl] * hj + (long long)v * hv] : 0.0;
-            if (negate)  // the sign of y folded into H's digits (sign bit, exact)
-              hreg[i] = __longlong_as_double(__double_as_longlong(hreg[i]) ^ (long long)0x8000000000000000ULL);
+          for (int i = 0; i < 4; ++i) {
+            const int e = (int)((__double_as_longlong(h[i]) >> 52) & 0x7FF);
+            if (e) em = max(em, e + p_shj[jb + i]);
           }
-#pragma unroll
-          for (int i = 0; i < XKS; ++i) {
-            const int e = (int)((__double_as_longlong(hreg[i]) >> 52) & 0x7FF);
-            if (e) em = max(em, e + shj[q * XKS + i]);
-          }
-          emv2[q][vl] = em;
+          p_em[c & 1][pw][lane] = em;
         }
-        __syncthreads();
-        if (!issuer) {
-          em = max(emv2[0][vl], emv2[1][vl]);
-          if (q == 0) evx[vl] = em;  // E_v for the epilogue (read after the next barrier)
-          if (q < nq) {
-            const int c = vl / XN, vv = vl % XN;
-            unsigned char* dstc = sB + q * XB_STEP + c * XB_CHUNK;
-#pragma unroll
-            for (int jp = 0; jp < XKS; jp += 2) {
-              const int jl = q * XKS + jp;
-              float f0[DIG], f1[DIG];
-              digit_floats(jl < nJ ? fixed47(hreg[jp], em - shj[jl]) : 0, f0);
-              digit_floats(jl + 1 < nJ ? fixed47(hreg[jp + 1], em - shj[jl + 1]) : 0, f1);
-#pragma unroll
-              for (int l = 0; l < DIG; ++l) {
-                const int row = l * XN + vv;
-                *reinterpret_cast<uint32_t*>(dstc + (row >> 3) * 128 + (jp >> 3) * XB_LBO +
-                                             (row & 7) * 16 + (jp & 7) * 2) = pack_bf16(f0[l], f1[l]);
-              }
-            }
-          }
+        if (pbar_or(!ok || s_fail)) {  // the slot is free; the partial maxima are in place
+          fail = true;
+          break;
         }
-      }
-      if (!a_ready) {
-        if (!mbar_wait(ab[buf], aphase[buf])) s_fail = 1;
-        aphase[buf] ^= 1;
-        if (tid == 0) a_pending[buf] = false;
-        a_ready = true;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (s_fail) break;
-      const int nchunk = (min(XVB, m - vb) + XN - 1) / XN;
-      if (issuer) {
-        if (lane == 0 && nJ > 0) {
-          for (int c = 0; c < nchunk; ++c) {
-            const long long seq = cg + c;
-            const int tb = (int)(seq & 1);
-            const long long use = seq >> 1;
-            if (use >= 1 && !mbar_wait(bf[tb], (uint32_t)((use - 1) & 1))) {
-              s_fail = 1;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t dcol = tmem + (uint32_t)(tb * XT_COLS);
-            for (int qq = 0; qq < nq; ++qq)
+        if (nJ > 0) {
+          double hn[4];  // the next chunk's values, in flight while these digits are formed
+          if (c + 1 < nch) load_h(c + 1, hn);
 #pragma unroll
-              for (int k = 0; k < DIG; ++k) {
-                const uint64_t a =
-                    sdesc(a_base + buf * XA_TILE + qq * XA_STEP + k * XA_BLOCK, XA_LBO, 128);
-                const uint64_t b = sdesc(b_base + qq * XB_STEP + c * XB_CHUNK, XB_LBO, 128);
-                mma_kf16(dcol + (uint32_t)(k * XN), a, b, idesc_kf16((DIG - k) * XN, MBLK, true),
-                         (k > 0 || qq > 0) ? 1u : 0u);
-              }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    md[tb])
-                : "memory");
+          for (int w = 0; w < XP_WARPS; ++w) em = max(em, p_em[c & 1][w][lane]);
+          if (pw == 0) s_ev[slot][lane] = em;
+          uint32_t pk[DIG][2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int jl = jb + 2 * e;
+            float f0[DIG], f1[DIG];
+            digit_floats(jl < nJ ? fixed47(h[2 * e], em - p_shj[jl]) : 0, f0);
+            digit_floats(jl + 1 < nJ ? fixed47(h[2 * e + 1], em - p_shj[jl + 1]) : 0, f1);
+#pragma unroll
+            for (int l = 0; l < DIG; ++l) pk[l][e] = pack_bf16(f0[l], f1[l]);
           }
+          // entries jb.. of K step jb / 16: core matrix (jb / 8) % 2, bytes
+          // (jb % 8) 2 of its 16-byte rows
+          unsigned char* dst = sS + slot * XS_SLOT + (jb >> 4) * XB_CHUNK +
+                               ((jb >> 3) & 1) * XB_LBO + (jb & 7) * 2;
+#pragma unroll
+          for (int l = 0; l < DIG; ++l) {
+            const int row = l * XN + lane;
+            unsigned char* q = dst + (row >> 3) * 128 + (row & 7) * 16;
+            if (jp == 4)
+              *reinterpret_cast<uint2*>(q) = make_uint2(pk[l][0], pk[l][1]);
+            else
+              *reinterpret_cast<uint32_t*>(q) = pk[l][0];
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) h[i] = hn[i];
         }
+        if (ptid == 0) {
+          s_T[slot] = T;
+          s_nJ[slot] = nJ;
+          s_v0[slot] = c * XN;
+          s_fl[slot] = end ? XF_END : ((c == 0 ? XF_FIRST : 0) | (c == nch - 1 ? XF_LAST : 0));
+          s_ab[slot] = ab;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // digits -> tensor core
         __syncwarp();
-      } else {
-        const int vv0 = 8 * (warp >> 2);
-        for (int c = 0; c < nchunk; ++c) {
-          const int vbase = vb + c * XN + vv0;  // this warp's first vector of the chunk
-          double* o = out + (size_t)vbase * ng + (g >= 0 ? g : 0);
-          const bool full = vbase + 8 <= m;
-          if (nJ > 0) {
-            const long long seq = cg + c;
-            const int tb = (int)(seq & 1);
-            if (!mbar_wait(md[tb], (uint32_t)((seq >> 1) & 1))) {
-              s_fail = 1;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
-                                       (uint32_t)(tb * XT_COLS + vv0);
-            const int4 e4[2] = {*reinterpret_cast<const int4*>(evx + c * XN + vv0),
-                                *reinterpret_cast<const int4*>(evx + c * XN + vv0 + 4)};
-            const int ev[8] = {e4[0].x, e4[0].y, e4[0].z, e4[0].w, e4[1].x, e4[1].y, e4[1].z, e4[1].w};
-            // four vectors at a time: six diagonal sums each
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_full[slot])) : "memory");
+      }
+      if (fail || end) break;
+      if (nJ > 0) ++tseq;
+      pbar();  // every thread is done with this tile's p_lj, p_shj and p_tile
+    }
+    // image loads in flight land before the shared memory is released
+    if (ptid == 0)
+      for (int b = 0; b < 2; ++b)
+        if ((a_pend >> b) & 1u) mbar_wait(smem_addr(&bar_a[b]), (a_par >> b) & 1u);
+    if (fail) s_fail = 1;
+  } else if (warp == XE_ISSUER) {
+    // ---- the issuing warp ----
+    if (lane == 0) {
+      bool fail = false;
+      long long cgm = 0;  // chunks with MMAs so far
+      int tcount = 0;     // tiles with MMAs started
+      for (int seq = 0;; ++seq) {
+        const int slot = seq % XR, use = seq / XR;
+        if (s_fail || !mbar_wait(smem_addr(&bar_full[slot]), (uint32_t)(use & 1))) {
+          fail = true;
+          break;
+        }
+        const int fl = s_fl[slot], nJ = s_nJ[slot], ab = s_ab[slot];
+        if (fl & XF_END) break;
+        if (nJ == 0) {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_free[slot])) : "memory");
+          continue;
+        }
+        if (fl & XF_FIRST) {
+          if (!mbar_wait(smem_addr(&bar_a[ab]), (uint32_t)((tcount >> 1) & 1))) {
+            fail = true;
+            break;
+          }
+          ++tcount;
+        }
+        const int tb = (int)(cgm & 1);
+        const long long u = cgm >> 1;
+        if (u >= 1 && !mbar_wait(smem_addr(&bar_tf[tb]), (uint32_t)((u - 1) & 1))) {
+          fail = true;
+          break;
+        }
+        tc_fence_after();
+        const int nq = (nJ + XKS - 1) / XKS;
+        const uint32_t dcol = tmem + (uint32_t)(tb * XT_COLS);
+        for (int qq = 0; qq < nq; ++qq)
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              uint32_t f[DIG][4];
+          for (int k = 0; k < DIG; ++k) {
+            const uint64_t a = sdesc(a_base + ab * XA_TILE + qq * XA_STEP + k * XA_BLOCK, XA_LBO, 128);
+            const uint64_t b = sdesc(s_base + slot * XS_SLOT + qq * XB_CHUNK, XB_LBO, 128);
+            mma_kf16(dcol + (uint32_t)(k * XN), a, b, idesc_kf16((DIG - k) * XN, MBLK, true),
+                     (k > 0 || qq > 0) ? 1u : 0u);
+          }
+        mma_commit(smem_addr(&bar_md[tb]));
+        mma_commit(smem_addr(&bar_free[slot]));
+        if (fl & XF_LAST) mma_commit(smem_addr(&bar_af[ab]));
+        ++cgm;
+      }
+      // every MMA issued is done before the tensor memory is freed
+      mma_commit(smem_addr(&bar_fin));
+      mbar_wait(smem_addr(&bar_fin), 0);
+      if (fail) s_fail = 1;
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps ----
+    const int p = 32 * (warp & 3) + lane;  // tensor-memory lane = point of the tile
+    const int vv0 = 8 * (warp >> 2);
+    const uint32_t lane_q = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)vv0;
+    long long cgm = 0, g = -1;
+    int lastT = -1;
+    bool fail = false;
+    for (int seq = 0;; ++seq) {
+      const int slot = seq % XR, use = seq / XR;
+      bool ok = !s_fail && mbar_wait(smem_addr(&bar_full[slot]), (uint32_t)(use & 1));
+      if (!__all_sync(0xffffffffu, ok)) {
+        fail = true;
+        break;
+      }
+      const int fl = s_fl[slot], nJ = s_nJ[slot], T = s_T[slot], v0 = s_v0[slot];
+      const int4 e4[2] = {*reinterpret_cast<const int4*>(&s_ev[slot][vv0]),
+                          *reinterpret_cast<const int4*>(&s_ev[slot][vv0 + 4])};
+      __syncwarp();
+      if (fl & XF_END) break;
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_free[slot])) : "memory");
+      if (T != lastT) {
+        g = tile_point(G, T, p);
+        lastT = T;
+      }
+      const int vbase = v0 + vv0;  // this warp's first vector of the chunk
+      double* o = out + (size_t)vbase * ng + (g >= 0 ? g : 0);
+      const bool full = vbase + 8 <= m;
+      if (nJ > 0) {
+        const int tb = (int)(cgm & 1);
+        ok = mbar_wait(smem_addr(&bar_md[tb]), (uint32_t)((cgm >> 1) & 1));
+        if (!__all_sync(0xffffffffu, ok)) {
+          fail = true;
+          break;
+        }
+        ++cgm;
+        tc_fence_after();
+        const uint32_t la = lane_q + (uint32_t)(tb * XT_COLS);
+        const int ev[8] = {e4[0].x, e4[0].y, e4[0].z, e4[0].w, e4[1].x, e4[1].y, e4[1].z, e4[1].w};
+        // four vectors at a time: six diagonal sums each
 #pragma unroll
-              for (int d = 0; d < DIG; ++d) tmem_ld4(lane_addr + (uint32_t)(d * XN + 4 * hh), f[d]);
-              tmem_wait_ld();
-              if (hh == 1) {  // the buffer is read: the next MMAs may overwrite it
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bf[tb]) : "memory");
-              }
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t f[DIG][4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                // sum_d D_d 256^(5 - d), |D_d| < 2^22, in three 32-bit pairs
-                const int t01 = small_float_int(f[0][u]) * 256 + small_float_int(f[1][u]);
-                const int t23 = small_float_int(f[2][u]) * 256 + small_float_int(f[3][u]);
-                const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
-                const long long base = ((long long)t01 << 32) + (long long)t45;
-                const long long acc = base + (long long)t23 * 65536LL;
-                const double v = scaled_i64_rz(acc, ev[4 * hh + u] - 1022 - 54);
-                if (g >= 0 && (full || vbase + 4 * hh + u < m)) o[(size_t)(4 * hh + u) * ng] = v;
-              }
-            }
-          } else if (g >= 0) {
+          for (int d = 0; d < DIG; ++d) tmem_ld4(la + (uint32_t)(d * XN + 4 * hh), f[d]);
+          tmem_wait_ld();
+          if (hh == 1) {  // the buffer is read: the next MMAs may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_tf[tb])) : "memory");
+          }
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (full || vbase + u < m) o[(size_t)u * ng] = 0.0;
+          for (int u = 0; u < 4; ++u) {
+            // sum_d D_d 256^(5 - d), |D_d| < 2^22, in three 32-bit pairs
+            const int t01 = small_float_int(f[0][u]) * 256 + small_float_int(f[1][u]);
+            const int t23 = small_float_int(f[2][u]) * 256 + small_float_int(f[3][u]);
+            const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
+            const long long base = ((long long)t01 << 32) + (long long)t45;
+            const long long acc = base + (long long)t23 * 65536LL;
+            const double val = scaled_i64_rz(acc, ev[4 * hh + u] - 1022 - 54);
+            if (g >= 0 && (full || vbase + 4 * hh + u < m)) o[(size_t)(4 * hh + u) * ng] = val;
           }
         }
+      } else if (g >= 0) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (full || vbase + u < m) o[(size_t)u * ng] = 0.0;
       }
-      if (nJ > 0) cg += nchunk;
     }
-    T = Tn;
-    buf ^= 1;
-  }
-  __syncthreads();
-  if (s_fail && tid == 0) {
-    // bounded waits for work still in flight before the memory is released
-    for (int b = 0; b < 2; ++b) {
-      mbar_wait(md[b], (uint32_t)(((cg + b) >> 1) & 1));
-      if (a_pending[b]) mbar_wait(ab[b], aphase[b]);
-    }
-    atomicOr(status, SEA_FLAG_WAIT);
+    if (fail && lane == 0) s_fail = 1;
   }
   tc_fence_before();
   __syncthreads();
+  if (tid == 0 && s_fail) atomicOr(status, SEA_FLAG_WAIT);
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
