@@ -815,36 +815,43 @@ __global__ void __launch_bounds__(256)
 //   E = -sum_k d_k sum_i Y[k][i]^2,  Y[k][i] = sum_j A(k, j) M[i][j],
 // with A = L^-1, d = 1 (then Y[k][i] = <phi_i|xi_k>, the second form of
 // Eq. exx_ace), or A(k, j) = Q[j][k], d_k = 1/|lambda_k| (0 where dropped).
-// Block k forms row k of Y: warp w takes i = w, w + 8, ... (lanes over j,
-// coalesced rows of M), sums Y^2 in i order; warps' sums in warp order.
-__global__ void __launch_bounds__(256)
+// Warp w forms Y[k][i] for one block of 32 rows i (lane = i) and the two
+// rows k = kp and n - 1 - kp, so that with the triangular A = L^-1 (A(k, j)
+// = 0 for j > k, not read) every warp does n + 1 multiply-adds; A's entries
+// are the same for the warp's lanes (one broadcast load), each lane walks
+// its own row of M.  The warp's sum of d_k Y^2 (lane order, then a fixed
+// butterfly) goes to part[w]; k_exx_ace_sum adds the parts in order.
+__global__ void __launch_bounds__(64)
     k_exx_ace_rows(const double* __restrict__ M, const double* __restrict__ A, int transA,
                    const double* __restrict__ d, int n, double* __restrict__ part) {
-  extern __shared__ double a_row[];  // [n]
-  __shared__ double wsum[8];
-  const int k = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < n; j += blockDim.x)
-    a_row[j] = transA ? A[(size_t)j * n + k] : A[(size_t)k * n + j];
-  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * 2 + (threadIdx.x >> 5);
+  const int nib = (n + 31) / 32, npair = (n + 1) / 2;
+  if (gw >= nib * npair) return;
+  const int ib = gw % nib, kp = gw / nib;
+  const int i = ib * 32 + lane, k1 = kp, k2 = n - 1 - kp;
+  const bool tri = !transA;
+  const double* mi = M + (size_t)(i < n ? i : 0) * n;
+  auto a_at = [&](int k, int j) { return transA ? A[(size_t)j * n + k] : A[(size_t)k * n + j]; };
+  double y1 = 0.0, y2 = 0.0;
+  const int jboth = tri ? k1 + 1 : n, jend = tri ? k2 + 1 : n;
+  for (int j = 0; j < jboth; ++j) {
+    const double mv = mi[j];
+    y1 = fma(a_at(k1, j), mv, y1);
+    y2 = fma(a_at(k2, j), mv, y2);
+  }
+  for (int j = jboth; j < jend; ++j) y2 = fma(a_at(k2, j), mi[j], y2);
   double s = 0.0;
-  for (int i = warp; i < n; i += 8) {
-    const double* mi = M + (size_t)i * n;
-    double y = 0.0;
-    for (int j = lane; j < n; j += 32) y = fma(a_row[j], mi[j], y);
+  if (i < n) {
+    s = (d ? d[k1] : 1.0) * y1 * y1;
+    if (k2 != k1) s = fma((d ? d[k2] : 1.0) * y2, y2, s);
+  }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    s = fma(y, y, s);
-  }
-  if (lane == 0) wsum[warp] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += wsum[w];
-    part[k] = (d ? d[k] : 1.0) * t;
-  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) part[gw] = s;
 }
 
-// out = -sum_k part[k] (fixed order: thread strides, then the block sum).
+// out = -sum_w part[w] (fixed order: thread strides, then the block sum).
 __global__ void k_exx_ace_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
   __shared__ double red[32];
   double t = 0.0;
@@ -855,11 +862,12 @@ __global__ void k_exx_ace_sum(const double* __restrict__ part, int n, double* __
 
 static cudaError_t launch_exx_ace(sea_ctx* c, int transA, const double* d) {
   const int n = c->n_orb;
-  if (!sea_ensure(c, c->Gbuf, (size_t)n * sizeof(double))) return cudaErrorMemoryAllocation;
+  const int nparts = ((n + 31) / 32) * ((n + 1) / 2);
+  if (!sea_ensure(c, c->Gbuf, (size_t)nparts * sizeof(double))) return cudaErrorMemoryAllocation;
   double* part = (double*)c->Gbuf.p;
-  k_exx_ace_rows<<<n, 256, (size_t)n * sizeof(double), c->stream>>>(
+  k_exx_ace_rows<<<(nparts + 1) / 2, 64, 0, c->stream>>>(
       (const double*)c->Mbuf.p, (const double*)c->Linv.p, transA, d, n, part);
-  k_exx_ace_sum<<<1, 256, 0, c->stream>>>(part, n, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT);
+  k_exx_ace_sum<<<1, 256, 0, c->stream>>>(part, nparts, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT);
   c->launches += 2;
   return cudaGetLastError();
 }

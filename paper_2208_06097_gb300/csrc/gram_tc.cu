@@ -193,6 +193,16 @@ __device__ __forceinline__ int small_float_int(uint32_t f) {
   return __float_as_int(__uint_as_float(f) + 12582912.0f) - 0x4B400000;
 }
 
+// v 2^e2 truncated toward zero to FP64, 0 below the normal range: the same
+// value as scaled_i64_rz, with the 64-bit truncating conversion done by the
+// conversion instruction (on the FP64 pipe, which the integer epilogues
+// otherwise leave idle) and the scaling by 2^e2 added to the exponent field.
+__device__ __forceinline__ double scaled_i64_rz_cvt(long long v, int e2) {
+  const long long b = __double_as_longlong(__ll2double_rz(v));
+  const int ex = (int)((b >> 52) & 0x7FF) + e2;  // biased exponent of the result
+  return (v == 0 || ex <= 0) ? 0.0 : __longlong_as_double(b + ((long long)e2 << 52));
+}
+
 // Exact value of an integer-valued float below 2^24 in magnitude.
 __device__ __forceinline__ int float_int(float f) {
   const unsigned u = __float_as_uint(f);
@@ -590,7 +600,8 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
   unsigned char* sR = gt_raw + ((1024 - (smem_addr(gt_raw) & 1023)) & 1023);  // two K halves
   unsigned char* sA = sR + 2 * RAW_KHALF;
   unsigned char* sW = sA + SMEM_A2;
-  __shared__ int Aexp[2][2][MBLK], Wexp[2][NBLK];  // [A block parity][half][row], [half][slot]
+  __shared__ int Aexp[2][2][MBLK], Wexp[2][2][NBLK];  // [A block parity][half][row],
+                                                     // [W block parity][half][slot]
   __shared__ __align__(8) unsigned long long mbar[2], tbar[2], rbar[2];
   __shared__ int u_ring[2][2];  // per posted unit: W block width (0: end), half
   __shared__ uint32_t tmem_base;
@@ -728,7 +739,6 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
       u.jb = 0;
       u.mb = 0;
       u.h = 0;
-      u.wb = 0;
       return true;
     };
     auto advance = [&](Unit& u, bool* new_block) -> bool {
@@ -742,6 +752,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
       if (++u.mb < nmb) return true;
       u.mb = 0;
       *new_block = true;
+      u.wb ^= 1;
       u.jb += NBLK;
       if (u.jb < u.nJ) return true;
       return claim(u);
@@ -768,7 +779,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
       }
       if (tid < 2 * NBLK) {
         const int h = tid / NBLK, sl = tid % NBLK;
-        Wexp[h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
+        Wexp[u.wb][h][sl] = sl < nj ? wexp[(size_t)(u.j0 + u.jb + sl) * 2 + h] : 0;
       }
     };
     // bounded waits; false on expiry
@@ -800,38 +811,49 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
       const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
       const int ea0 = Aexp[u.ab][0][32 * quarter + lane] - 1022,
                 ea1 = Aexp[u.ab][1][32 * quarter + lane] - 1022;
+      // column pairs (c0, c0 + 1), c0 = 2 g, 2 g + 8, ...: one two-column
+      // tensor-memory load per diagonal and half
 #pragma unroll 1
-      for (int c = g; c < nj; c += ng4) {
-        uint32_t f[2 * DIG];
-#pragma unroll
-        for (int q = 0; q < 2 * DIG; ++q)
-          f[q] = tmem_ld1(lane_addr + (uint32_t)((q / DIG) * TMEM_HALF + (q % DIG) * P + c));
-        tmem_wait_ld();
+      for (int c0 = 2 * g; c0 < nj; c0 += 2 * ng4) {
         // |D_d| < (d + 1) 2^21 (A digits up to 255, W digits up to 128 in
         // magnitude, 64 points): D_0, D_1 (< 2^22) by the 2^22 conversion on
         // the FP32 pipe, the others by the conversion unit (exact: integer
         // values below 2^24); D_0 256 + D_1 and D_2 256 + D_3 stay below 2^31
-        long long acc[2];
+        long long acc[2][2];  // [half][column]
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint32_t* fh = f + h * DIG;
-          const int t01 = small_float_int(fh[0]) * 256 + small_float_int(fh[1]);
-          const int t23 = __float2int_rz(__uint_as_float(fh[2])) * 256 +
-                          __float2int_rz(__uint_as_float(fh[3]));
-          acc[h] = ((long long)t01 << 32) + ((long long)t23 << 16) +
-                   ((long long)__float2int_rz(__uint_as_float(fh[4])) << 8) +
-                   (long long)__float2int_rz(__uint_as_float(fh[5]));
+          uint32_t f[DIG][2];
+#pragma unroll
+          for (int d = 0; d < DIG; ++d)
+            tmem_ld2(lane_addr + (uint32_t)(h * TMEM_HALF + d * P + c0), f[d]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int t01 = small_float_int(f[0][cc]) * 256 + small_float_int(f[1][cc]);
+            const int t23 = __float2int_rz(__uint_as_float(f[2][cc])) * 256 +
+                            __float2int_rz(__uint_as_float(f[3][cc]));
+            acc[h][cc] = ((long long)t01 << 32) + ((long long)t23 << 16) +
+                         ((long long)__float2int_rz(__uint_as_float(f[4][cc])) << 8) +
+                         (long long)__float2int_rz(__uint_as_float(f[5][cc]));
+          }
         }
         // sum_r x w = 2^(E_x + E_w - 55) acc; the two halves on the larger
         // scale (the other truncated at its unit, 2^-55 of that segment's
         // scale), one truncation
-        const int e0 = ea0 + Wexp[0][c] - 1022 - 55, e1 = ea1 + Wexp[1][c] - 1022 - 55;
-        const bool b0 = e0 >= e1;
-        const int sh = min(b0 ? e0 - e1 : e1 - e0, 63);
-        const long long s2 = (b0 ? acc[0] : acc[1]) + ((b0 ? acc[1] : acc[0]) >> sh);
-        if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64_rz(s2, b0 ? e0 : e1);
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = c0 + cc;
+          if (c < nj) {
+            const int e0 = ea0 + Wexp[u.wb][0][c] - 1022 - 55, e1 = ea1 + Wexp[u.wb][1][c] - 1022 - 55;
+            const bool b0 = e0 >= e1;
+            const int sh = min(b0 ? e0 - e1 : e1 - e0, 63);
+            const long long s2 = (b0 ? acc[0][cc] : acc[1][cc]) + ((b0 ? acc[1][cc] : acc[0][cc]) >> sh);
+            if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64_rz(s2, b0 ? e0 : e1);
+          }
+        }
       }
     };
+
     // post unit u (or the end, nj = 0) to the issuing thread: ring entry
     // seq & 1, then ready[0] (thread 0, after a converting-warp barrier)
     auto post = [&](int seq, int nj, int h) {
@@ -903,10 +925,9 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
         store_digits(d, 1);
         tc_fence_after();
         if (have_prev && prev.h == 1) epilogue(prev);  // all of prev's MMAs are done
-        if (need_w) {
-          conv_sync();  // every epilogue has read W's exponents
-          load_w(cur);
-        }
+        // a new W block: the MMAs that read the old one are done (waited
+        // above) and its exponents sit in the other buffer
+        if (need_w) load_w(cur);
         if (run == 0) Aexp[cur.ab][cur.h][row] = em;
         cp_async_wait_all();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1188,13 +1209,14 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
             h[i] = __longlong_as_double(__double_as_longlong(h[i]) ^ (long long)0x8000000000000000ULL);
         }
       };
-      double h[4];
-      if (nJ > 0) load_h(0, h);
-      for (int c = 0; c < (end ? 1 : nch); ++c, ++pseq) {
+      // chunk c from the values in h; the next chunk's values are loaded
+      // into hn meanwhile (two register sets used in turn, so nothing waits
+      // on those loads before the next chunk); false on failure
+      auto chunk = [&](int c, double (&h)[4], double (&hn)[4]) -> bool {
         const int slot = pseq % XR, use = pseq / XR;
         // the slot is free once its previous chunk's MMAs are done and its
         // E_v was read
-        ok = true;
+        bool ok = true;
         if (ptid == 0 && use >= 1) ok = mbar_wait(smem_addr(&bar_free[slot]), (uint32_t)((use - 1) & 1));
         int em = 0;
         if (nJ > 0) {
@@ -1205,12 +1227,8 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
           }
           p_em[c & 1][pw][lane] = em;
         }
-        if (pbar_or(!ok || s_fail)) {  // the slot is free; the partial maxima are in place
-          fail = true;
-          break;
-        }
+        if (pbar_or(!ok || s_fail)) return false;  // the slot is free; the partial maxima are in place
         if (nJ > 0) {
-          double hn[4];  // the next chunk's values, in flight while these digits are formed
           if (c + 1 < nch) load_h(c + 1, hn);
 #pragma unroll
           for (int w = 0; w < XP_WARPS; ++w) em = max(em, p_em[c & 1][w][lane]);
@@ -1238,8 +1256,6 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
             else
               *reinterpret_cast<uint32_t*>(q) = pk[l][0];
           }
-#pragma unroll
-          for (int i = 0; i < 4; ++i) h[i] = hn[i];
         }
         if (ptid == 0) {
           s_T[slot] = T;
@@ -1251,6 +1267,15 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // digits -> tensor core
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_full[slot])) : "memory");
+        ++pseq;
+        return true;
+      };
+      double hA[4], hB[4];
+      if (nJ > 0) load_h(0, hA);
+      const int nc = end ? 1 : nch;
+      for (int c = 0; c < nc && !fail; c += 2) {
+        if (!chunk(c, hA, hB)) fail = true;
+        else if (c + 1 < nc && !chunk(c + 1, hB, hA)) fail = true;
       }
       if (fail || end) break;
       if (nJ > 0) ++tseq;
@@ -1373,7 +1398,7 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
             const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
             const long long base = ((long long)t01 << 32) + (long long)t45;
             const long long acc = base + (long long)t23 * 65536LL;
-            const double val = scaled_i64_rz(acc, ev[4 * hh + u] - 1022 - 54);
+            const double val = scaled_i64_rz_cvt(acc, ev[4 * hh + u] - 1022 - 54);
             if (g >= 0 && (full || vbase + 4 * hh + u < m)) o[(size_t)(4 * hh + u) * ng] = val;
           }
         }

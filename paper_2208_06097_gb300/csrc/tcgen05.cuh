@@ -95,6 +95,12 @@ __device__ __forceinline__ uint32_t tmem_ld1(uint32_t addr) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(addr));
   return r;
 }
+// Two consecutive columns (no wait).
+__device__ __forceinline__ void tmem_ld2(uint32_t addr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(addr));
+}
 // Four consecutive columns (no wait).
 __device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t* r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
