@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(SEA_ACC_THREADS)
     k_accumulate(int nx, int ny, int nz, int o_begin, const int* __restrict__ eptr,
                  const Entry* __restrict__ ent, const long long* __restrict__ coff,
                  const double* __restrict__ cbuf, double* __restrict__ out,
-                 double* __restrict__ out2) {
+                 double* __restrict__ out2, int bulk) {
   extern __shared__ double sp[];
   __shared__ int es[SEA_ACC_MAXE][5];  // x start, x length, y start, y length, meets the z tile
   const int o = o_begin + blockIdx.x;
@@ -374,21 +374,38 @@ __global__ void __launch_bounds__(SEA_ACC_THREADS)
       tmask[q] = hit ? 1 : 0;
     }
   }
-  __syncthreads();
   const size_t base = ((size_t)o * nz + z) * plane;
-  const int dy = blockDim.x / nx, dx = blockDim.x - dy * nx;  // (x, y) of g, without divisions
-  int y = threadIdx.x / nx, x = threadIdx.x - y * nx;
-  for (int g = threadIdx.x; g < plane; g += blockDim.x) {
-    const double v = sp[g];
-    if (out2) out2[base + g] = v;
-    if (all || tmask[(y / TY) * ntx + x / TX]) out[base + g] = v;
-    x += dx;
-    y += dy;
-    if (x >= nx) {
-      x -= nx;
-      ++y;
+  // The output stored in full (out2, else out when every tile is wanted) by
+  // one bulk copy of the plane from shared memory when `bulk` (the plane is
+  // a multiple of 16 bytes and the outputs 16-byte aligned): the generic
+  // writes are made visible to the copy engine, then thread 0 issues it and
+  // waits, before the CTA ends, until the plane has been read.
+  double* full = out2 ? out2 : (all ? out : nullptr);
+  const bool by_copy = bulk && full != nullptr;
+  if (by_copy) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (by_copy && threadIdx.x == 0) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(full + base),
+                 "r"((uint32_t)__cvta_generic_to_shared(sp)), "r"((uint32_t)plane * 8u)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+  if (!(by_copy && out2 == nullptr)) {  // else the copy stored everything
+    const int dy = blockDim.x / nx, dx = blockDim.x - dy * nx;  // (x, y) of g, without divisions
+    int y = threadIdx.x / nx, x = threadIdx.x - y * nx;
+    for (int g = threadIdx.x; g < plane; g += blockDim.x) {
+      const double v = sp[g];
+      if (out2 && !by_copy) out2[base + g] = v;
+      if (all || tmask[(y / TY) * ntx + x / TX]) out[base + g] = v;
+      x += dx;
+      y += dy;
+      if (x >= nx) {
+        x -= nx;
+        ++y;
+      }
     }
   }
+  if (by_copy && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 // E_xx = -sum_p (2 - delta_ij) e_p in pair order, plus CG statistics:
@@ -489,9 +506,14 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
       cudaError_t e = cudaFuncSetAttribute(k_accumulate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
       if (e != cudaSuccess) return e;
+      // bulk plane copies: whole planes of 16-byte multiples into 16-byte
+      // aligned outputs
+      const bool plane16 = ((size_t)c->N[0] * c->N[1] * sizeof(double)) % 16 == 0;
+      const bool al16 = ((uintptr_t)out % 16 == 0) && ((uintptr_t)out2 % 16 == 0);
       k_accumulate<<<dim3(o_end - o_begin, c->N[2]), SEA_ACC_THREADS, smem, c->stream>>>(
           c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p, (const Entry*)c->ewin.p,
-          (const long long*)c->coff.p, (const double*)c->cbuf.p, out, out2);
+          (const long long*)c->coff.p, (const double*)c->cbuf.p, out, out2,
+          plane16 && al16 ? 1 : 0);
     } else {
       k_accumulate_gmem<<<dim3(o_end - o_begin, (c->N[2] + SEA_SLAB - 1) / SEA_SLAB), 256, 0,
                           c->stream>>>(c->N[0], c->N[1], c->N[2], o_begin, (const int*)c->eptr.p,
