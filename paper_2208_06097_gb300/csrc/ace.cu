@@ -892,9 +892,12 @@ static cudaError_t launch_expand(sea_ctx* c, const TileGeom& G, const int* tptr,
   if (c->prm.precision == 1) {
     // tiles with at most expand_tc_max_list() W rows on the tensor cores,
     // longer lists (if any) by the FP32 kernel
+    if (!sea_ensure(c, c->xevb, (size_t)max(c->n_tiles, 1) * m * sizeof(int)))
+      return cudaErrorMemoryAllocation;
     const cudaError_t e = launch_expand_tc(c->stream, c->device, c->wx.p, G, c->ng, c->n_tiles,
-                                           tptr, tlist, H, hj, hv, m, sign < 0.0,
-                                           out, (int*)c->counts.p + 24, (unsigned*)c->status.p);
+                                           tptr, tlist, H, hj, hv, m, sign < 0.0, out,
+                                           (int*)c->xevb.p, (int*)c->counts.p + 24,
+                                           (unsigned*)c->status.p);
     if (e != cudaSuccess) return e;
     if (c->max_tile_list > expand_tc_max_list()) {
       const size_t smem = (size_t)c->max_tile_list * 32 * sizeof(float2);

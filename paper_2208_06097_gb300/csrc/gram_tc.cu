@@ -1067,6 +1067,27 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
 }
 
 
+// E_v of the expansion for every (tile, vector): the largest biased
+// exponent of H(j, v) 2^(E_j) over the tile's list (0 where all are zero);
+// thread = vector, grid y = tile.  Tiles with an empty list or more than XJ
+// entries are skipped (not read).
+__global__ void __launch_bounds__(128)
+    k_expand_ev(const int* __restrict__ tptr, const int* __restrict__ tlist,
+                const int* __restrict__ wxexp, const double* __restrict__ H, long long hj,
+                long long hv, int m, int* __restrict__ ev) {
+  const int T = blockIdx.y, v = blockIdx.x * 128 + threadIdx.x;
+  const int j0 = tptr[T], nJ = tptr[T + 1] - j0;
+  if (v >= m || nJ == 0 || nJ > XJ) return;
+  int em = 0;
+  for (int jl = 0; jl < nJ; ++jl) {
+    const int e =
+        (int)((__double_as_longlong(H[(long long)tlist[j0 + jl] * hj + (long long)v * hv]) >> 52) &
+              0x7FF);
+    if (e) em = max(em, e + wxexp[j0 + jl] - 1022);
+  }
+  ev[(size_t)T * m + v] = em;
+}
+
 constexpr int XE_WARPS = 16;                 // epilogue warps (tensor-memory read-back, stores)
 constexpr int XP_WARPS = 8;                  // H-digit warps
 constexpr int XE_ISSUER = XE_WARPS + XP_WARPS;           // the MMA-issuing warp
@@ -1102,13 +1123,14 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
     k_expand_tc(const uint4* __restrict__ wx, const int* __restrict__ wxexp, TileGeom G, size_t ng,
                 int n_tiles, const int* __restrict__ tptr, const int* __restrict__ tlist,
                 const double* __restrict__ H, long long hj, long long hv, int m, int negate,
-                double* __restrict__ out, int* __restrict__ queue, unsigned* __restrict__ status) {
+                double* __restrict__ out, const int* __restrict__ evp, int* __restrict__ queue,
+                unsigned* __restrict__ status) {
   extern __shared__ unsigned char xe_raw[];
   unsigned char* sA = xe_raw + ((128 - (smem_addr(xe_raw) & 127)) & 127);  // two tile images
   unsigned char* sS = sA + 2 * XA_TILE;                                     // XR chunk slots
   __shared__ int s_T[XR], s_nJ[XR], s_v0[XR], s_fl[XR], s_ab[XR];
   __shared__ __align__(16) int s_ev[XR][XN];
-  __shared__ int p_lj[XJ], p_shj[XJ], p_em[2][XP_WARPS][XN], p_tile;
+  __shared__ int p_lj[XJ], p_shj[XJ], p_tile;
   __shared__ __align__(8) unsigned long long bar_full[XR], bar_free[XR], bar_md[2], bar_tf[2],
       bar_a[2], bar_af[2], bar_fin;
   __shared__ uint32_t tmem_base;
@@ -1198,8 +1220,8 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
         break;
       }
       // H(j, v) of this thread's entries for chunk c (sign folded in), zero
-      // beyond the list and the vectors
-      auto load_h = [&](int c, double (&h)[4]) {
+      // beyond the list and the vectors, and E_v of the chunk's vector
+      auto load_h = [&](int c, double (&h)[4], int& ev) {
         const int v = c * XN + lane;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -1208,38 +1230,40 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
           if (negate)  // the sign of y folded into H's digits (sign bit, exact)
             h[i] = __longlong_as_double(__double_as_longlong(h[i]) ^ (long long)0x8000000000000000ULL);
         }
+        ev = v < m ? evp[(size_t)T * m + v] : 0;
       };
-      // chunk c from the values in h; the next chunk's values are loaded
-      // into hn meanwhile (two register sets used in turn, so nothing waits
-      // on those loads before the next chunk); false on failure
-      auto chunk = [&](int c, double (&h)[4], double (&hn)[4]) -> bool {
+      // chunk c from the values in h (the next chunk's values are loaded into
+      // hn meanwhile: two register sets used in turn, so nothing waits on
+      // those loads before the next chunk).  The warps of this role do not
+      // wait on one another here: each waits for the slot itself and
+      // arrives on its full barrier; a warp whose wait expired (wfail) skips
+      // the rest of the tile's chunks and the role stops at the tile's end.
+      bool wfail = false;
+      auto chunk = [&](int c, double (&h)[4], int ev, double (&hn)[4], int& evn) {
         const int slot = pseq % XR, use = pseq / XR;
+        ++pseq;
+        if (wfail) return;
         // the slot is free once its previous chunk's MMAs are done and its
         // E_v was read
         bool ok = true;
-        if (ptid == 0 && use >= 1) ok = mbar_wait(smem_addr(&bar_free[slot]), (uint32_t)((use - 1) & 1));
-        int em = 0;
-        if (nJ > 0) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int e = (int)((__double_as_longlong(h[i]) >> 52) & 0x7FF);
-            if (e) em = max(em, e + p_shj[jb + i]);
-          }
-          p_em[c & 1][pw][lane] = em;
+        if (lane == 0) {
+          if (use >= 1) ok = mbar_wait(smem_addr(&bar_free[slot]), (uint32_t)((use - 1) & 1));
+          ok = ok && !s_fail;
         }
-        if (pbar_or(!ok || s_fail)) return false;  // the slot is free; the partial maxima are in place
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {  // the same decision in every lane
+          wfail = true;
+          return;
+        }
         if (nJ > 0) {
-          if (c + 1 < nch) load_h(c + 1, hn);
-#pragma unroll
-          for (int w = 0; w < XP_WARPS; ++w) em = max(em, p_em[c & 1][w][lane]);
-          if (pw == 0) s_ev[slot][lane] = em;
+          if (c + 1 < nch) load_h(c + 1, hn, evn);
+          if (pw == 0) s_ev[slot][lane] = ev;
           uint32_t pk[DIG][2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int jl = jb + 2 * e;
             float f0[DIG], f1[DIG];
-            digit_floats(jl < nJ ? fixed47(h[2 * e], em - p_shj[jl]) : 0, f0);
-            digit_floats(jl + 1 < nJ ? fixed47(h[2 * e + 1], em - p_shj[jl + 1]) : 0, f1);
+            digit_floats(jl < nJ ? fixed47(h[2 * e], ev - p_shj[jl]) : 0, f0);
+            digit_floats(jl + 1 < nJ ? fixed47(h[2 * e + 1], ev - p_shj[jl + 1]) : 0, f1);
 #pragma unroll
             for (int l = 0; l < DIG; ++l) pk[l][e] = pack_bf16(f0[l], f1[l]);
           }
@@ -1267,19 +1291,18 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // digits -> tensor core
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar_full[slot])) : "memory");
-        ++pseq;
-        return true;
       };
       double hA[4], hB[4];
-      if (nJ > 0) load_h(0, hA);
+      int eA = 0, eB = 0;
+      if (nJ > 0) load_h(0, hA, eA);
       const int nc = end ? 1 : nch;
-      for (int c = 0; c < nc && !fail; c += 2) {
-        if (!chunk(c, hA, hB)) fail = true;
-        else if (c + 1 < nc && !chunk(c + 1, hB, hA)) fail = true;
+      for (int c = 0; c < nc; c += 2) {
+        chunk(c, hA, eA, hB, eB);
+        if (c + 1 < nc) chunk(c + 1, hB, eB, hA, eA);
       }
+      fail = pbar_or(wfail);  // every thread is done with this tile's lists
       if (fail || end) break;
       if (nJ > 0) ++tseq;
-      pbar();  // every thread is done with this tile's p_lj, p_shj and p_tile
     }
     // image loads in flight land before the shared memory is released
     if (ptid == 0)
@@ -1496,7 +1519,7 @@ cudaError_t launch_wx_digits(cudaStream_t st, const double* W, const TileGeom& G
 cudaError_t launch_expand_tc(cudaStream_t st, int device, const void* wxbuf, const TileGeom& G,
                              size_t ng, int n_tiles, const int* tptr, const int* tlist,
                              const double* H, long long hj, long long hv, int m, bool negate,
-                             double* out, int* queue, unsigned* status) {
+                             double* out, int* evbuf, int* queue, unsigned* status) {
   static bool attr_set[64] = {};
   if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
   if (!attr_set[device]) {
@@ -1512,8 +1535,11 @@ cudaError_t launch_expand_tc(cudaStream_t st, int device, const void* wxbuf, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
+  k_expand_ev<<<dim3((m + 127) / 128, n_tiles), 128, 0, st>>>(tptr, tlist, wxexp, H, hj, hv, m,
+                                                             evbuf);
   k_expand_tc<<<std::min(nsm, n_tiles), XE_THREADS, XE_SMEM, st>>>(
-      wx, wxexp, G, ng, n_tiles, tptr, tlist, H, hj, hv, m, negate ? 1 : 0, out, queue, status);
+      wx, wxexp, G, ng, n_tiles, tptr, tlist, H, hj, hv, m, negate ? 1 : 0, out, evbuf, queue,
+      status);
   return cudaGetLastError();
 }
 

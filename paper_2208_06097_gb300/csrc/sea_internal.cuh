@@ -502,6 +502,7 @@ struct sea_ctx {
   // ACE
   SeaBuf wdig;  // the mixed form's W digits (tensor-core contraction)
   SeaBuf wx;    // the mixed form's per-tile W digit images (tensor-core expansion)
+  SeaBuf xevb;  // the expansion's H exponents per (tile, vector)
   SeaBuf scdm_u, scdm_c;  // SCDM rotation and pivots
   SeaBuf tmask, tptr_o, tlist_o, tslot_o, tptr_t, tlist_t, partial, Mbuf, Abuf, Lbuf, Linv,
       Gbuf, Hbuf, Hbuf2;
@@ -580,7 +581,7 @@ cudaError_t launch_wx_digits(cudaStream_t st, const double* W, const TileGeom& G
 cudaError_t launch_expand_tc(cudaStream_t st, int device, const void* wxbuf, const TileGeom& G,
                              size_t ng, int n_tiles, const int* tptr, const int* tlist,
                              const double* H, long long hj, long long hv, int m, bool negate,
-                             double* out, int* queue, unsigned* status);
+                             double* out, int* evbuf, int* queue, unsigned* status);
 int expand_tc_max_list();
 cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const TileGeom& G,
                            size_t ng, int n_tiles, const int* tptr, long long slots,
