@@ -848,7 +848,7 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
             const bool b0 = e0 >= e1;
             const int sh = min(b0 ? e0 - e1 : e1 - e0, 63);
             const long long s2 = (b0 ? acc[0][cc] : acc[1][cc]) + ((b0 ? acc[1][cc] : acc[0][cc]) >> sh);
-            if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64_rz(s2, b0 ? e0 : e1);
+            if (a < m) partial[(size_t)(u.j0 + u.jb + c) * m + a] = scaled_i64_rz_cvt(s2, b0 ? e0 : e1);
           }
         }
       }
