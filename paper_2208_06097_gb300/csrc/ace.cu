@@ -999,15 +999,23 @@ cudaError_t launch_ace_build(sea_ctx* c) {
                           tptr, tlist, hinc, c->wdig.p);
     if (err != cudaSuccess) return err;
     if (!sea_ensure(c, c->wx, wx_digits_bytes(nt, hinc))) return cudaErrorMemoryAllocation;
-    err = launch_wx_digits(c->stream, (const double*)c->vxx_dev.p, G, c->ng, nt, tptr, tlist, tsub,
-                           c->wx.p);
-    if (err != cudaSuccess) return err;
     c->launches += 2;
   }
   cudaEventRecord(c->ev[10], c->stream);
   err = launch_gram(c, (const double*)c->phi.p, n, G, tptr, tlist, tsub);
   if (err != cudaSuccess) return err;
   cudaEventRecord(c->ev[11], c->stream);
+  if (c->prm.precision == 1) {
+    // W's per-tile images for the expansion (used by sea_apply_ace only) on
+    // a second stream, beside the latency-bound Cholesky chain below; the
+    // context stream waits for them before the build ends
+    err = cudaStreamWaitEvent(c->xfer[0], c->ev[11], 0);
+    if (err == cudaSuccess)
+      err = launch_wx_digits(c->xfer[0], (const double*)c->vxx_dev.p, G, c->ng, nt, tptr, tlist,
+                             tsub, c->wx.p);
+    if (err == cudaSuccess) err = cudaEventRecord(c->xev[0], c->xfer[0]);
+    if (err != cudaSuccess) return err;
+  }
   k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
       n, 1);
@@ -1044,7 +1052,9 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   c->launches += 10 + nchol;
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  return launch_exx_ace(c, 0, nullptr);  // Y = L^-1 M^T
+  err = launch_exx_ace(c, 0, nullptr);  // Y = L^-1 M^T
+  if (err == cudaSuccess && c->prm.precision == 1) err = cudaStreamWaitEvent(c->stream, c->xev[0], 0);
+  return err;
 }
 
 // Eigen form (App. A) after M is known: Q into Linv, S (eigenvalues on the

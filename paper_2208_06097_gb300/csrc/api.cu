@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 #include <algorithm>
 #include <new>
 
@@ -52,6 +53,43 @@ HarmCoef make_harmonic_coefficients() {
       h.gam_hi[l][k] = hi;
       h.gam_lo[l][k] = (float)(h.gam[l][k] - (double)hi);
     }
+  // D_lm as polynomials: coefficient arrays P[a][b][c] of x^a y^b z^c, the
+  // recurrence applied to them (multiplication by x, y, z, r^2 shifts them)
+  constexpr int E = SEA_LMAX + 1;
+  std::vector<double> P((size_t)SEA_NQ * E * E * E, 0.0);
+  auto at = [&](int q, int a, int b, int c) -> double& {
+    return P[(((size_t)q * E + a) * E + b) * E + c];
+  };
+  // dst += f * (x^dx y^dy z^dz) src
+  auto add_shift = [&](int dst, int src, double f, int dx, int dy, int dz) {
+    for (int a = 0; a + dx < E; ++a)
+      for (int b = 0; b + dy < E; ++b)
+        for (int c = 0; c + dz < E; ++c)
+          if (at(src, a, b, c) != 0.0) at(dst, a + dx, b + dy, c + dz) += f * at(src, a, b, c);
+  };
+  at(0, 0, 0, 0) = 1.0;
+  at(lmi(1, 1), 1, 0, 0) = 1.0;
+  at(lmi(1, -1), 0, 1, 0) = 1.0;
+  at(lmi(1, 0), 0, 0, 1) = 1.0;
+  for (int l = 1; l < SEA_LMAX; ++l) {
+    add_shift(lmi(l + 1, l + 1), lmi(l, l), 1.0, 1, 0, 0);
+    add_shift(lmi(l + 1, l + 1), lmi(l, -l), -1.0, 0, 1, 0);
+    add_shift(lmi(l + 1, -(l + 1)), lmi(l, l), 1.0, 0, 1, 0);
+    add_shift(lmi(l + 1, -(l + 1)), lmi(l, -l), 1.0, 1, 0, 0);
+    for (int m = -l; m <= l; ++m) {
+      add_shift(lmi(l + 1, m), lmi(l, m), 1.0, 0, 0, 1);
+      if (m >= -(l - 1) && m <= l - 1) {
+        const double g = h.gam[l][m + SEA_LMAX];
+        add_shift(lmi(l + 1, m), lmi(l - 1, m), -g, 2, 0, 0);
+        add_shift(lmi(l + 1, m), lmi(l - 1, m), -g, 0, 2, 0);
+        add_shift(lmi(l + 1, m), lmi(l - 1, m), -g, 0, 0, 2);
+      }
+    }
+  }
+  for (int l = 0; l <= SEA_LMAX; ++l)
+    for (int m = -l; m <= l; ++m)
+      for (int a = 0; a <= l; ++a)
+        for (int b = 0; a + b <= l; ++b) h.cart[lmi(l, m)][a][b] = at(lmi(l, m), a, b, l - a - b);
   return h;
 }
 

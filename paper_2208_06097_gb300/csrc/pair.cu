@@ -24,84 +24,188 @@ struct StencilW {
 };
 
 // Pair density and moments, one CTA per pair: b = 4 pi rho on the box,
-// Qs = rescaled multipole moments of rho about the box centre (Eq. mepole).
-// DFM: the moments in double-float arithmetic (mixed form).
+// Qs = rescaled multipole moments of rho about the box centre (Eq. mepole),
+//   Qs_lm = kappa_lm^2 dV sum_r rho(r) D_lm(r).
+// D_lm is a homogeneous polynomial of degree l (the coefficients cart[lm]
+// expanded from the harmonic recurrence), so the sum is a fixed combination
+// of the Cartesian moments M_abc = sum_r rho x^a y^b z^c, a + b + c <= 6,
+// which on the box grid separate.  With the point's offsets from the box
+// centre in half grid steps, u = 2 x - (ex - 1) (v, w likewise; x = u hx / 2),
+//   S_a(y, z) = sum_x rho u^a                (one thread per row),
+//   T_ab(z)   = sum_y v^b S_a(y, z)          (a + b <= 6, per slab of planes),
+//   M_abc     = (hx/2)^a (hy/2)^b (hz/2)^c sum_z w^c T_ab(z),
+// all sums in a fixed order.  Per point this is 7 products and sums instead
+// of the 49-term harmonic recurrence.  DFM: rho and S, T, M in double-float
+// arithmetic (mixed form), else FP64; the last combination in FP64.
+namespace {
 template <bool DFM>
-__global__ void __launch_bounds__(256, 1)
+struct MomR;  // the accumulation type and its operations
+template <>
+struct MomR<true> {
+  typedef DF T;
+  static __device__ __forceinline__ T zero() { return DF{0.f, 0.f}; }
+  static __device__ __forceinline__ T mul_i(T a, int k) { return df_mul_f(i2f_exact(k), a); }
+  static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+  static __device__ __forceinline__ T prod(double a, double c) {
+    const float2 as = split64(a), cs = split64(c);
+    return df_mul(DF{as.x, as.y}, DF{cs.x, cs.y});
+  }
+  static __device__ __forceinline__ T one() { return DF{1.f, 0.f}; }
+  static __device__ __forceinline__ double to_double(T a) { return df_to_double(a); }
+};
+template <>
+struct MomR<false> {
+  typedef double T;
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T mul_i(T a, int k) { return a * (double)k; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ T prod(double a, double c) { return a * c; }
+  static __device__ __forceinline__ T one() { return 1.0; }
+  static __device__ __forceinline__ double to_double(T a) { return a; }
+};
+constexpr int MOM_E = SEA_LMAX + 1;                       // powers 0..6
+constexpr int MOM_NAB = MOM_E * (MOM_E + 1) / 2;           // 28 pairs a + b <= 6
+constexpr int MOM_NABC = MOM_E * (MOM_E + 1) * (MOM_E + 2) / 6;  // 84 monomials
+constexpr int MOM_ZSLAB = 16;                             // planes per slab at most
+// (a, b) of pair index k (a + b <= 6, a-major)
+__device__ __forceinline__ void mom_ab(int k, int* a, int* b) {
+  int aa = 0;
+  while (k >= MOM_E - aa) {
+    k -= MOM_E - aa;
+    ++aa;
+  }
+  *a = aa;
+  *b = k;
+}
+__device__ __forceinline__ int mom_abi(int a, int b) { return a * MOM_E - a * (a - 1) / 2 + b; }
+}  // namespace
+
+// Dynamic shared memory of k_pair_moments for a grid with ny, nz points on
+// the y and z axes (box extents are at most those).
+size_t pair_moments_smem(int ny, int nz) {
+  const size_t rows = (size_t)std::max(256, ny);
+  return (rows * MOM_E + (size_t)MOM_ZSLAB * MOM_NAB + (size_t)(ny + nz) * MOM_E) * 8 +
+         (size_t)MOM_NABC * 8;
+}
+
+template <bool DFM>
+__global__ void __launch_bounds__(256)
     k_pair_moments(const double* __restrict__ phi, int nx, int ny, int nz,
                    const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
                    double hx, double hy, double hz, double dV, int lmax,
                    double* __restrict__ bbuf, double* __restrict__ Qout) {
+  typedef MomR<DFM> R;
+  typedef typename R::T T;
+  extern __shared__ double mom_sm[];
   const int p = blockIdx.x;
   const PairInfo P = pinfo[p];
-  const int ex = P.ext[0], ey = P.ext[1];
-  const int n = P.n;
+  const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
+  const int Z = min(MOM_ZSLAB, max(1, 256 / ey));  // planes per slab
+  T* S = reinterpret_cast<T*>(mom_sm);             // [rows of the slab][7]
+  T* Tz = S + (size_t)max(256, ey) * MOM_E;        // [Z][28]
+  T* vp = Tz + MOM_ZSLAB * MOM_NAB;                // [ey][7]: v^b
+  T* wp = vp + (size_t)ey * MOM_E;                 // [ez][7]: w^c
+  double* Mf = reinterpret_cast<double*>(wp + (size_t)ez * MOM_E);  // [84]
   const size_t ng = (size_t)nx * ny * nz;
   const double* fi = phi + (size_t)P.i * ng;
   const double* fj = phi + (size_t)P.j * ng;
   double* b = bbuf + voff[p];
-  const double cx = 0.5 * (ex - 1), cy = 0.5 * (ey - 1), cz = 0.5 * (P.ext[2] - 1);
   const double fourpi = 4.0 * 3.14159265358979323846;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-
-  __shared__ double red[8][SEA_NQ];
-  if (DFM) {
-    // positions as exact half-integers times h in double-float
-    const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
-    DF acc[SEA_NQ];
-#pragma unroll
-    for (int q = 0; q < SEA_NQ; ++q) acc[q] = DF{0.f, 0.f};
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
-      const size_t g = ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx +
-                       wrapi(P.lo[0] + x, nx);
-      const double a = fi[g], c = fj[g];
-      b[t] = fourpi * (a * c);
-      const float2 as = split64(a), cs = split64(c);
-      // offsets from the centre, (2 x - (ex - 1)) / 2 etc., exact in FP32
-      harm_accumulate_df(df_mul(DF{as.x, as.y}, DF{cs.x, cs.y}),
-                         df_mul_f(0.5f * i2f_exact(2 * x - (ex - 1)), Hx),
-                         df_mul_f(0.5f * i2f_exact(2 * y - (ey - 1)), Hy),
-                         df_mul_f(0.5f * i2f_exact(2 * z - (P.ext[2] - 1)), Hz), acc);
+  // powers of the half-step offsets along y and z
+  for (int k = threadIdx.x; k < ey + ez; k += blockDim.x) {
+    const bool isy = k < ey;
+    const int i = isy ? k : k - ey, e = isy ? ey : ez;
+    const int o = 2 * i - (e - 1);
+    T* dst = (isy ? vp : wp) + (size_t)i * MOM_E;
+    T pw = R::one();
+    for (int c = 0; c < MOM_E; ++c) {
+      dst[c] = pw;
+      pw = R::mul_i(pw, o);
     }
-    // warp sums in double-float, then the warps' sums in FP64 (fixed order)
+  }
+  // this thread's monomial of M (threads 0..83)
+  int ma = 0, mb = 0, mc = 0;
+  if (threadIdx.x < MOM_NABC) {
+    int k = threadIdx.x, l = 0;
+    while (k >= (l + 1) * (l + 2) / 2) {
+      k -= (l + 1) * (l + 2) / 2;
+      ++l;
+    }
+    ma = 0;  // degree l: (a, b) with a + b <= l in a-major order, c = l - a - b
+    while (k >= l - ma + 1) {
+      k -= l - ma + 1;
+      ++ma;
+    }
+    mb = k;
+    mc = l - ma - mb;
+  }
+  T macc = R::zero();
+  const int gx0 = wrapi(P.lo[0], nx);
+  for (int z0 = 0; z0 < ez; z0 += Z) {
+    const int zn = min(Z, ez - z0), rows = zn * ey;
+    __syncthreads();  // S, Tz of the previous slab are consumed; the powers are in place
+    // S_a(y, z): one thread per row; b = 4 pi rho on the way
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      const int y = r % ey, z = z0 + r / ey;
+      const size_t rowg =
+          ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx;
+      double* brow = b + ((size_t)z * ey + y) * ex;
+      T s[MOM_E];
 #pragma unroll
-    for (int q = 0; q < SEA_NQ; ++q) {
-      DF v = acc[q];
+      for (int a = 0; a < MOM_E; ++a) s[a] = R::zero();
+      int gx = gx0;
+      for (int x = 0; x < ex; ++x) {
+        const double av = fi[rowg + gx], cv = fj[rowg + gx];
+        brow[x] = fourpi * (av * cv);
+        T pk = R::prod(av, cv);
+        const int u = 2 * x - (ex - 1);
+        s[0] = R::add(s[0], pk);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const DF u = DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-        v = df_add(v, u);
+        for (int a = 1; a < MOM_E; ++a) {
+          pk = R::mul_i(pk, u);
+          s[a] = R::add(s[a], pk);
+        }
+        if (++gx == nx) gx = 0;
       }
-      if (lane == 0) red[w][q] = df_to_double(v);
-    }
-  } else {
-    double acc[SEA_NQ];
 #pragma unroll
-    for (int q = 0; q < SEA_NQ; ++q) acc[q] = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const int x = t % ex, y = (t / ex) % ey, z = t / (ex * ey);
-      const size_t g = ((size_t)wrapi(P.lo[2] + z, nz) * ny + wrapi(P.lo[1] + y, ny)) * nx +
-                       wrapi(P.lo[0] + x, nx);
-      const double rho = fi[g] * fj[g];
-      b[t] = fourpi * rho;
-      harm_accumulate(rho, (x - cx) * hx, (y - cy) * hy, (z - cz) * hz, acc);
+      for (int a = 0; a < MOM_E; ++a) S[(size_t)r * MOM_E + a] = s[a];
     }
-#pragma unroll
-    for (int q = 0; q < SEA_NQ; ++q) {
-      double v = acc[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[w][q] = v;
+    __syncthreads();
+    // T_ab(z) for the slab's planes
+    for (int it = threadIdx.x; it < zn * MOM_NAB; it += blockDim.x) {
+      const int zl = it / MOM_NAB;
+      int a, bb;
+      mom_ab(it - zl * MOM_NAB, &a, &bb);
+      T t = R::zero();
+      for (int y = 0; y < ey; ++y)
+        t = R::add(t, R::mul(vp[(size_t)y * MOM_E + bb], S[((size_t)zl * ey + y) * MOM_E + a]));
+      Tz[zl * MOM_NAB + mom_abi(a, bb)] = t;
     }
+    __syncthreads();
+    // M_abc += sum over the slab's planes of w^c T_ab(z)
+    if (threadIdx.x < MOM_NABC)
+      for (int zl = 0; zl < zn; ++zl)
+        macc = R::add(macc, R::mul(wp[(size_t)(z0 + zl) * MOM_E + mc], Tz[zl * MOM_NAB + mom_abi(ma, mb)]));
+  }
+  if (threadIdx.x < MOM_NABC) {
+    double sc = R::to_double(macc);
+    for (int k = 0; k < ma; ++k) sc *= 0.5 * hx;
+    for (int k = 0; k < mb; ++k) sc *= 0.5 * hy;
+    for (int k = 0; k < mc; ++k) sc *= 0.5 * hz;
+    Mf[threadIdx.x] = sc;
   }
   __syncthreads();
   if (threadIdx.x < SEA_NQ) {
     const int q = threadIdx.x;
-    double s = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][q];
     int l = 0;
     while ((l + 1) * (l + 1) <= q) ++l;
+    double s = 0.0;
+    const int base = l * (l + 1) * (l + 2) / 6;  // monomials of lower degree
+    int k = 0;
+    for (int a = 0; a <= l; ++a)
+      for (int bb = 0; a + bb <= l; ++bb, ++k) s = fma(c_harm.cart[q][a][bb], Mf[base + k], s);
     Qout[(size_t)p * SEA_NQ + q] = (l <= lmax) ? c_harm.kap2[q] * s * dV : 0.0;
   }
 }
@@ -912,7 +1016,13 @@ static StencilW make_weights(const sea_ctx* c) {
 cudaError_t launch_pair_setup(sea_ctx* c) {
   if (c->P == 0) return cudaSuccess;
   auto moments = c->prm.precision == 1 ? k_pair_moments<true> : k_pair_moments<false>;
-  moments<<<c->P, 256, 0, c->stream>>>(
+  const size_t msm = pair_moments_smem(c->N[1], c->N[2]);
+  if (msm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(moments, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)msm);
+    if (e != cudaSuccess) return e;
+  }
+  moments<<<c->P, 256, msm, c->stream>>>(
       (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const PairInfo*)c->pinfo.p,
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
       (double*)c->bbuf.p, (double*)c->Q.p);

@@ -82,6 +82,10 @@ __host__ __device__ inline int lmi(int l, int m) { return l * l + l + m; }
 struct HarmCoef {
   double gam[SEA_LMAX][2 * SEA_LMAX + 1];
   double kap2[SEA_NQ];
+  // D_lm as a homogeneous polynomial of degree l:
+  //   D_lm(x, y, z) = sum_{a + b <= l} cart[lm][a][b] x^a y^b z^(l - a - b)
+  // (the recurrence above carried out on coefficient arrays)
+  double cart[SEA_NQ][SEA_LMAX + 1][SEA_LMAX + 1];
   float gam_hi[SEA_LMAX][2 * SEA_LMAX + 1];  // gam = gam_hi + gam_lo (double-float)
   float gam_lo[SEA_LMAX][2 * SEA_LMAX + 1];
 };
