@@ -188,14 +188,14 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   const int t0 = blockIdx.x * SEA_CHUNK;
   if (t0 >= nw) return;
   const PairInfo P = pinfo[e.pair];
-  __shared__ double Qs[SEA_NQ];
-  __shared__ DF Qd[SEA_NQ];
-  if (threadIdx.x < SEA_NQ) {
-    const double q = Qg[(size_t)e.pair * SEA_NQ + threadIdx.x];
+  __shared__ double Ps[SEA_NMONO];
+  __shared__ DF Pd[SEA_NMONO];
+  if (threadIdx.x < SEA_NMONO) {
+    const double q = Qg[(size_t)e.pair * SEA_QSTRIDE + SEA_NQ + threadIdx.x];
     if (DFM)
-      Qd[threadIdx.x] = df_from_double(q);
+      Pd[threadIdx.x] = df_from_double(q);
     else
-      Qs[threadIdx.x] = q;
+      Ps[threadIdx.x] = q;
   }
   __syncthreads();
   const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
@@ -243,14 +243,14 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
         const float2 s = split64(v[(lz * P.ext[1] + ly) * P.ext[0] + lx]);
         val = DF{s.x, s.y};
       } else {  // lx - cx etc. are half-integers, exact in FP32
-        val = me_potential_df(Qd, df_mul_f(i2f_exact(lx) - cxf, Hx),
+        val = me_potential_cart_df(Pd, df_mul_f(i2f_exact(lx) - cxf, Hx),
                               df_mul_f(i2f_exact(ly) - cyf, Hy), df_mul_f(i2f_exact(lz) - czf, Hz));
       }
       const float2 f = split64(fp[g]);
       out[t] = df_to_double(df_mul(val, DF{f.x, f.y}));
     } else {
       const double val = inside ? v[(lz * P.ext[1] + ly) * P.ext[0] + lx]
-                                : me_potential(Qs, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
+                                : me_potential_cart(Ps, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
       out[t] = __dmul_rn(val, fp[g]);
     }
   }

@@ -445,7 +445,7 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_ALLOC(pbuf, U * sizeof(double));
   SEA_ALLOC(qbuf, U * sizeof(double));
   SEA_ALLOC(cbuf, (size_t)std::max<long long>(c->WC, 1) * sizeof(double));
-  SEA_ALLOC(Q, (size_t)std::max(c->P, 1) * SEA_NQ * sizeof(double));
+  SEA_ALLOC(Q, (size_t)std::max(c->P, 1) * SEA_QSTRIDE * sizeof(double));
   SEA_ALLOC(epair, (size_t)std::max(c->P, 1) * sizeof(double));
   SEA_ALLOC(iters, (size_t)std::max(c->P, 1) * sizeof(int));
   tr.stage("pair setup");

@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(256)
     Mf[threadIdx.x] = sc;
   }
   __syncthreads();
+  __shared__ double Qsm[SEA_NQ];
+  double* Qp = Qout + (size_t)p * SEA_QSTRIDE;
   if (threadIdx.x < SEA_NQ) {
     const int q = threadIdx.x;
     int l = 0;
@@ -206,7 +208,17 @@ __global__ void __launch_bounds__(256)
     int k = 0;
     for (int a = 0; a <= l; ++a)
       for (int bb = 0; a + bb <= l; ++bb, ++k) s = fma(c_harm.cart[q][a][bb], Mf[base + k], s);
-    Qout[(size_t)p * SEA_NQ + q] = (l <= lmax) ? c_harm.kap2[q] * s * dV : 0.0;
+    const double Q = (l <= lmax) ? c_harm.kap2[q] * s * dV : 0.0;
+    Qsm[q] = Q;
+    Qp[q] = Q;
+  }
+  __syncthreads();
+  // the potential's coefficients P_abc = sum_m Qs_lm cart[lm][a][b], l = a + b + c
+  if (threadIdx.x < MOM_NABC) {
+    const int l = ma + mb + mc;
+    double s = 0.0;
+    for (int m = -l; m <= l; ++m) s = fma(Qsm[lmi(l, m)], c_harm.cart[lmi(l, m)][ma][mb], s);
+    Qp[SEA_NQ + mono_k(ma, mb, mc)] = s;
   }
 }
 
@@ -233,14 +245,14 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
   const PairInfo P = pinfo[p];
   const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
   double* b = bbuf + voff[p];
-  __shared__ double Qs[SEA_NQ];
-  __shared__ DF Qd[SEA_NQ];
-  if (threadIdx.x < SEA_NQ) {
-    const double q = Qg[(size_t)p * SEA_NQ + threadIdx.x];
+  __shared__ double Ps[SEA_NMONO];
+  __shared__ DF Pd[SEA_NMONO];
+  if (threadIdx.x < SEA_NMONO) {
+    const double q = Qg[(size_t)p * SEA_QSTRIDE + SEA_NQ + threadIdx.x];
     if (DFM)
-      Qd[threadIdx.x] = df_from_double(q);
+      Pd[threadIdx.x] = df_from_double(q);
     else
-      Qs[threadIdx.x] = q;
+      Ps[threadIdx.x] = q;
   }
   __syncthreads();
   // me_potential at grid offsets (ox, oy, oz) from the box centre, in units
@@ -270,9 +282,9 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
         const float ox = a == 0 ? t : o1, oy = a == 0 ? o1 : (a == 1 ? t : o2);
         const float oz = a == 2 ? t : o2;
         if (DFM)
-          Gd[e] = me_potential_df(Qd, df_mul_f(ox, Hx), df_mul_f(oy, Hy), df_mul_f(oz, Hz));
+          Gd[e] = me_potential_cart_df(Pd, df_mul_f(ox, Hx), df_mul_f(oy, Hy), df_mul_f(oz, Hz));
         else
-          Gs[e] = me_potential(Qs, (double)ox * hx, (double)oy * hy, (double)oz * hz);
+          Gs[e] = me_potential_cart(Ps, (double)ox * hx, (double)oy * hy, (double)oz * hz);
       }
       __syncthreads();
       // moved into b with the stencil weights: thread per (line, boundary

@@ -15,6 +15,11 @@
 
 #define SEA_LMAX 6
 #define SEA_NQ ((SEA_LMAX + 1) * (SEA_LMAX + 1))
+// monomials x^a y^b z^c with a + b + c <= SEA_LMAX
+#define SEA_NMONO ((SEA_LMAX + 1) * (SEA_LMAX + 2) * (SEA_LMAX + 3) / 6)
+// per pair: the moments Qs (SEA_NQ), then the multipole potential's
+// coefficients in the Kelvin-inverted variables (SEA_NMONO)
+#define SEA_QSTRIDE (SEA_NQ + SEA_NMONO)
 #define SEA_FDP 6  // stencil half width: O(h^12) second difference (App. C)
 
 // Status bits written by kernels (device word, read back by the host).
@@ -63,6 +68,15 @@ __host__ __device__ inline int wrapi(int x, int n) {
 }
 
 __host__ __device__ inline int lmi(int l, int m) { return l * l + l + m; }
+
+// Position of x^a y^b z^c among the SEA_NMONO monomials (a-major, then b,
+// then c), the layout of the potential's coefficients.
+__host__ __device__ constexpr int mono_k(int a, int b, int c) {
+  int k = 0;
+  for (int i = 0; i < a; ++i) k += (SEA_LMAX - i + 1) * (SEA_LMAX - i + 2) / 2;
+  for (int j = 0; j < b; ++j) k += SEA_LMAX - a - j + 1;
+  return k + c;
+}
 
 // Real solid harmonics in a rescaled basis D_lm = C_lm / kappa_lm, where
 // C_lm are the Racah-normalized real regular solid harmonics
@@ -366,6 +380,51 @@ __device__ __forceinline__ DF me_potential_df(const DF* __restrict__ Q, DF x, DF
     }
   }
   return df_mul(v, df_sqrt(ir2));
+}
+
+// The multipole potential of Eq. me from its polynomial form: with u = r /
+// r^2, sum_lm Qs_lm D_lm(u) = sum_abc P_abc ux^a uy^b uz^c, P_abc = sum_m
+// Qs_lm cart[lm][a][b] (l = a + b + c; formed once per pair by
+// k_pair_moments, layout mono_k), so v = (1/r) sum P_abc ux^a uy^b uz^c,
+// evaluated by nested Horner steps (84 multiply-adds per point).  Double-float
+// (mixed form) and FP64 versions.
+__device__ __forceinline__ DF me_potential_cart_df(const DF* __restrict__ P, DF x, DF y, DF z) {
+  const DF r2 = df_fma(z, z, df_dot2(x, x, y, y));
+  const DF ir2 = df_rcp(r2);
+  const DF ux = df_mul(x, ir2), uy = df_mul(y, ir2), uz = df_mul(z, ir2);
+  DF pa{0.f, 0.f};
+#pragma unroll
+  for (int a = SEA_LMAX; a >= 0; --a) {
+    DF pb{0.f, 0.f};
+#pragma unroll
+    for (int b = SEA_LMAX - a; b >= 0; --b) {
+      DF pc = P[mono_k(a, b, SEA_LMAX - a - b)];
+#pragma unroll
+      for (int c = SEA_LMAX - a - b - 1; c >= 0; --c) pc = df_fma(pc, uz, P[mono_k(a, b, c)]);
+      pb = (b == SEA_LMAX - a) ? pc : df_fma(pb, uy, pc);
+    }
+    pa = (a == SEA_LMAX) ? pb : df_fma(pa, ux, pb);
+  }
+  return df_mul(pa, df_sqrt(ir2));
+}
+__device__ __forceinline__ double me_potential_cart(const double* __restrict__ P, double x,
+                                                    double y, double z) {
+  const double ir2 = 1.0 / (x * x + y * y + z * z);
+  const double ux = x * ir2, uy = y * ir2, uz = z * ir2;
+  double pa = 0.0;
+#pragma unroll
+  for (int a = SEA_LMAX; a >= 0; --a) {
+    double pb = 0.0;
+#pragma unroll
+    for (int b = SEA_LMAX - a; b >= 0; --b) {
+      double pc = P[mono_k(a, b, SEA_LMAX - a - b)];
+#pragma unroll
+      for (int c = SEA_LMAX - a - b - 1; c >= 0; --c) pc = fma(pc, uz, P[mono_k(a, b, c)]);
+      pb = (b == SEA_LMAX - a) ? pc : fma(pb, uy, pc);
+    }
+    pa = (a == SEA_LMAX) ? pb : fma(pa, ux, pb);
+  }
+  return pa * sqrt(ir2);
 }
 
 // harm_accumulate in double-float: acc[q] += w D_q(x, y, z), the same
