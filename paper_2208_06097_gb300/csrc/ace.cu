@@ -369,16 +369,16 @@ __global__ void k_gram_reduce(const double* __restrict__ partial, int m, int n_o
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)m * n_orb) return;
   const int a = (int)(t % m), o = (int)(t / m);
-  // in slot order; the loads of eight slots are issued before their adds
+  // in slot order; the loads of sixteen slots are issued before their adds
   double s = 0.0;
   int k = optr[o];
   const int k1 = optr[o + 1];
-  for (; k + 8 <= k1; k += 8) {
-    double p[8];
+  for (; k + 16 <= k1; k += 16) {
+    double p[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) p[u] = partial[(size_t)oslot[k + u] * m + a];
+    for (int u = 0; u < 16; ++u) p[u] = partial[(size_t)oslot[k + u] * m + a];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s += p[u];
+    for (int u = 0; u < 16; ++u) s += p[u];
   }
   for (; k < k1; ++k) s += partial[(size_t)oslot[k] * m + a];
   out[(size_t)a * sa + (size_t)o * so] = scale * s;
@@ -746,13 +746,19 @@ __global__ void k_scale_rows(double* __restrict__ B, const double* __restrict__ 
 }
 
 // C[n1][n2] = op(A) B, op(A)(i, k) = A[k][i] if transA else A[i][k]; A is
-// n1 x n1 (square), B is [n1][n2].  16 x 16 shared-memory tiles.
+// n1 x n1 (square), B is [n1][n2].  16 x 16 shared-memory tiles.  With
+// `lower`, A's zero upper triangle is not multiplied.
 __global__ void k_small_gemm(const double* __restrict__ A, int transA, const double* __restrict__ B,
-                             int n1, int n2, double* __restrict__ C) {
+                             int n1, int n2, double* __restrict__ C, int lower) {
   __shared__ double As[16][17], Bs[16][17];
   const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
   double acc = 0.0;
-  for (int k0 = 0; k0 < n1; k0 += 16) {
+  // lower: A is lower triangular (zeros above the diagonal, exactly), so
+  // op(A)(i, k) vanishes for k > i (A B) or k < i (A^T B); those tiles are
+  // skipped (their products would add exact zeros)
+  const int kbeg = (lower && transA) ? blockIdx.y * 16 : 0;
+  const int kend = (lower && !transA) ? min(n1, (int)(blockIdx.y + 1) * 16) : n1;
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
     double av = 0.0;
     if (i < n1 && ka < n1) av = transA ? A[(size_t)ka * n1 + i] : A[(size_t)i * n1 + ka];
@@ -1016,7 +1022,7 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     if (err == cudaSuccess) err = cudaEventRecord(c->xev[0], c->xfer[0]);
     if (err != cudaSuccess) return err;
   }
-  k_gram_reduce<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, c->stream>>>(
+  k_gram_reduce<<<(unsigned)(((long long)n * n + 63) / 64), 64, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
       n, 1);
   k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
@@ -1129,24 +1135,24 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
     if (e != cudaSuccess) return e;
   }
   cudaEventRecord(c->ev[13], c->stream);
-  k_gram_reduce<<<(unsigned)(((long long)n * nv + 255) / 256), 256, 0, c->stream>>>(
+  k_gram_reduce<<<(unsigned)(((long long)n * nv + 63) / 64), 64, 0, c->stream>>>(
       (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p,
       1, nv);
   // H = (-Mbar)^-1 G = L^-T (L^-1 G), or Q |Lambda|^-1 Q^T G in the eigen form
   dim3 gb((nv + 15) / 16, (n + 15) / 16), tb(16, 16);
   if (c->ace_eigen) {
     k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Gbuf.p,
-                                           n, nv, (double*)c->Hbuf2.p);
+                                           n, nv, (double*)c->Hbuf2.p, 0);
     k_scale_rows<<<(unsigned)(((size_t)n * nv + 255) / 256), 256, 0, c->stream>>>(
         (double*)c->Hbuf2.p, (const double*)c->Abuf.p, n, nv);
     k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Hbuf2.p,
-                                           n, nv, (double*)c->Hbuf.p);
+                                           n, nv, (double*)c->Hbuf.p, 0);
     c->launches += 1;
   } else {
     k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Gbuf.p,
-                                           n, nv, (double*)c->Hbuf2.p);
+                                           n, nv, (double*)c->Hbuf2.p, 1);
     k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Hbuf2.p,
-                                           n, nv, (double*)c->Hbuf.p);
+                                           n, nv, (double*)c->Hbuf.p, 1);
   }
   // out[v] = -sum_j W_j H[j][v]
   cudaEventRecord(c->ev[14], c->stream);
