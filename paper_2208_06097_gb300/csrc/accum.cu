@@ -173,20 +173,19 @@ __global__ void k_entry_offsets(const Entry* __restrict__ ent, const int* __rest
   }
 }
 
-#define SEA_CHUNK 1024
-
-// DFM: the multipole potential in double-float arithmetic (mixed form).
+// Window contributions of the entries (grid y) in chunks of SEA_CHUNK window
+// points (grid x); `part` as in contrib_range (2 when the mixed CG already
+// formed the far-field points).  DFM: double-float arithmetic (mixed form),
+// four CTAs per SM there (64 registers, no spills): the nested Horner steps
+// of the potential are one dependent chain per point, so the warps resident
+// per SM set the rate (measured 0.81 -> 0.77 ms per step against two CTAs).
 template <bool DFM>
-// Four CTAs per SM in the mixed form (64 registers, no spills): the nested
-// Horner steps of the potential are one dependent chain per point, so the
-// warps resident per SM set the rate (measured 0.81 -> 0.77 ms per step
-// against two CTAs).
 __global__ void __launch_bounds__(256, DFM ? 4 : 1)
     k_contrib(const double* __restrict__ phi, int nx, int ny, int nz, const Entry* __restrict__ ent,
               const long long* __restrict__ coff, const PairInfo* __restrict__ pinfo,
               const long long* __restrict__ voff, const double* __restrict__ vbuf,
               const double* __restrict__ Qg, double hx, double hy, double hz,
-              double* __restrict__ cbuf) {
+              double* __restrict__ cbuf, int part) {
   const Entry e = ent[blockIdx.y];
   const int nw = e.wl[0] * e.wl[1] * e.wl[2];
   const int t0 = blockIdx.x * SEA_CHUNK;
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(256, DFM ? 4 : 1)
   const PairInfo P = pinfo[e.pair];
   __shared__ double Ps[SEA_NMONO];
   __shared__ DF Pd[SEA_NMONO];
-  if (threadIdx.x < SEA_NMONO) {
+  if (part != 2 && threadIdx.x < SEA_NMONO) {
     const double q = Qg[(size_t)e.pair * SEA_QSTRIDE + SEA_NQ + threadIdx.x];
     if (DFM)
       Pd[threadIdx.x] = df_from_double(q);
@@ -202,62 +201,8 @@ __global__ void __launch_bounds__(256, DFM ? 4 : 1)
       Ps[threadIdx.x] = q;
   }
   __syncthreads();
-  const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
-  const double* v = vbuf + voff[e.pair];
-  const size_t ng = (size_t)nx * ny * nz;
-  const double* fp = phi + (size_t)e.partner * ng;
-  double* out = cbuf + coff[blockIdx.y];
-  const double cx = 0.5 * (P.ext[0] - 1), cy = 0.5 * (P.ext[1] - 1), cz = 0.5 * (P.ext[2] - 1);
-  const float cxf = 0.5f * i2f_exact(P.ext[0] - 1), cyf = 0.5f * i2f_exact(P.ext[1] - 1),
-              czf = 0.5f * i2f_exact(P.ext[2] - 1);
-  const int t1 = min(nw, t0 + SEA_CHUNK);
-  // window coordinates of t, advanced by the CTA stride without divisions;
-  // grid coordinates from the window start wrapped once
-  const int wx = e.wl[0], wy = e.wl[1], wxy = wx * wy;
-  const int S = blockDim.x;
-  const int dz = S / wxy, dy = (S - dz * wxy) / wx, dx = S - dz * wxy - dy * wx;
-  const int gx0 = wrapi(e.ws[0], nx), gy0 = wrapi(e.ws[1], ny), gz0 = wrapi(e.ws[2], nz);
-  int tz = (t0 + (int)threadIdx.x) / wxy;
-  int ty = (t0 + (int)threadIdx.x - tz * wxy) / wx;
-  int tx = t0 + (int)threadIdx.x - tz * wxy - ty * wx;
-  for (int t = t0 + threadIdx.x; t < t1; t += S) {
-    const int ux = e.ws[0] + tx, uy = e.ws[1] + ty, uz = e.ws[2] + tz;
-    const int lx = ux - P.lo[0], ly = uy - P.lo[1], lz = uz - P.lo[2];
-    const bool inside =
-        lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2];
-    int gx = gx0 + tx, gy = gy0 + ty, gz = gz0 + tz;  // window lengths are at most n
-    gx -= gx >= nx ? nx : 0;
-    gy -= gy >= ny ? ny : 0;
-    gz -= gz >= nz ? nz : 0;
-    const size_t g = ((size_t)gz * ny + gy) * nx + gx;
-    tx += dx;
-    ty += dy;
-    tz += dz;
-    if (tx >= wx) {
-      tx -= wx;
-      ++ty;
-    }
-    if (ty >= wy) {
-      ty -= wy;
-      ++tz;
-    }
-    if (DFM) {  // c = v phi in double-float, no FP64 instruction
-      DF val;
-      if (inside) {
-        const float2 s = split64(v[(lz * P.ext[1] + ly) * P.ext[0] + lx]);
-        val = DF{s.x, s.y};
-      } else {  // lx - cx etc. are half-integers, exact in FP32
-        val = me_potential_cart_df(Pd, df_mul_f(i2f_exact(lx) - cxf, Hx),
-                              df_mul_f(i2f_exact(ly) - cyf, Hy), df_mul_f(i2f_exact(lz) - czf, Hz));
-      }
-      const float2 f = split64(fp[g]);
-      out[t] = df_to_double(df_mul(val, DF{f.x, f.y}));
-    } else {
-      const double val = inside ? v[(lz * P.ext[1] + ly) * P.ext[0] + lx]
-                                : me_potential_cart(Ps, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
-      out[t] = __dmul_rn(val, fp[g]);
-    }
-  }
+  contrib_range<DFM>(part, e, P, phi, nx, ny, nz, vbuf + voff[e.pair], Pd, Ps, hx, hy, hz,
+                     cbuf + coff[blockIdx.y], t0, min(nw, t0 + SEA_CHUNK));
 }
 
 // Global-memory form: CTA per (orbital, slab of SLAB z-planes); out2, when
@@ -498,11 +443,15 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
           (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const Entry*)c->ewin.p + e0,
           (const long long*)c->coff.p + e0, (const PairInfo*)c->pinfo.p,
           (const long long*)c->voff.p, (const double*)c->vbuf.p, (const double*)c->Q.p, c->h[0],
-          c->h[1], c->h[2], (double*)c->cbuf.p);
+          c->h[1], c->h[2], (double*)c->cbuf.p, c->far_side ? 2 : 0);
       c->launches += 1;
     }
   }
   if (o_end > o_begin) {
+    if (c->far_side) {  // the contributions outside the pair boxes are in
+      const cudaError_t e = cudaStreamWaitEvent(c->stream, c->xev[1], 0);
+      if (e != cudaSuccess) return e;
+    }
     // the plane, then one tile-mask byte per (x tile, y tile)
     const size_t smem = (size_t)c->N[0] * c->N[1] * sizeof(double) +
                         (size_t)((c->N[0] + TX - 1) / TX) * ((c->N[1] + TY - 1) / TY);
@@ -526,6 +475,32 @@ cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_
     }
     c->launches += 1;
   }
+  return cudaGetLastError();
+}
+
+// The contributions outside each pair box (they need the moments alone) on
+// the context's first copy stream, beside the CG: submitted after the CG's
+// launch, whose persistent CTAs fill the GPU, they take the SMs that the CG's
+// last pairs leave idle.  The accumulation later forms the points inside
+// the boxes and waits for this launch.  Mixed form only.
+cudaError_t launch_contrib_far(sea_ctx* c, cudaEvent_t setup_done) {
+  c->far_side = false;
+  if (c->prm.precision != 1 || c->E == 0) return cudaSuccess;
+  cudaError_t e = cudaStreamWaitEvent(c->xfer[0], setup_done, 0);
+  if (e != cudaSuccess) return e;
+  const int chunks = (int)((c->max_window + SEA_CHUNK - 1) / SEA_CHUNK);
+  for (int e0 = 0; e0 < c->E; e0 += 65535) {
+    const int ne = std::min(65535, c->E - e0);
+    k_contrib<true><<<dim3(chunks, ne), 256, 0, c->xfer[0]>>>(
+        (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const Entry*)c->ewin.p + e0,
+        (const long long*)c->coff.p + e0, (const PairInfo*)c->pinfo.p,
+        (const long long*)c->voff.p, (const double*)c->vbuf.p, (const double*)c->Q.p, c->h[0],
+        c->h[1], c->h[2], (double*)c->cbuf.p, 1);
+    c->launches += 1;
+  }
+  e = cudaEventRecord(c->xev[1], c->xfer[0]);
+  if (e != cudaSuccess) return e;
+  c->far_side = true;
   return cudaGetLastError();
 }
 

@@ -462,6 +462,7 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
   tr.stage("cg");
   SEA_CK(sea::launch_cg(c), "cg");
+  SEA_CK(sea::launch_contrib_far(c, c->ev[2]), "far field");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
   tr.stage("far field and accumulation");
   double* vd = (double*)c->vxx_dev.p;

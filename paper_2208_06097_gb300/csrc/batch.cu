@@ -126,6 +126,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
   for (int k = 0; k < n; ++k) {
     sea_ctx* c = ctxs[k];
     c->have_vxx = c->have_ace = false;
+    c->far_side = false;  // the accumulation forms every contribution itself
     SEA_BCK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), st), "memset");
     SEA_BCK(sea::launch_plan_boxes(c), "domain boxes");
     SEA_BCK(sea::launch_plan_pairs(c), "pair selection");

@@ -579,6 +579,8 @@ struct sea_ctx {
   std::vector<int> h_eptr;  // entry offsets per orbital, host copy (last plan)
   struct sea_unet* unet = nullptr;  // learned warm start (attached model, not owned)
   bool cg_warm = false;             // the next CG starts from the guess in vbuf
+  bool far_side = false;            // the contributions outside the pair boxes were
+                                    // launched on xfer[0] (done at xev[1])
   cudaEvent_t xev[2 * SEA_XCHUNKS_MAX + 2] = {};
 };
 
@@ -601,12 +603,87 @@ struct Entry {
   int ws[3], wl[3];
 };
 
-// Launch wrappers (each file implements its own).
 namespace sea {
+// Window points per unit of the far-field work (k_contrib's CTAs and the
+// mixed CG's far-field items).
+#define SEA_CHUNK 1024
+
+// Window contributions c = v phi_partner (Eq. tDxx) of entry e at its window
+// points t = t0 + threadIdx.x, + blockDim.x, ... < t1 (window-compact
+// output out[t]): v is the pair's CG solution (v, box layout) inside the
+// pair box and the multipole potential (coefficients Pd, double-float, or
+// Ps, FP64) outside.  part 0: every point; 1: only the points outside the
+// box (they need the moments alone); 2: only those inside (they need the
+// solution).  DFM: double-float products (mixed form), else FP64.
+template <bool DFM>
+__device__ __forceinline__ void contrib_range(int part, const Entry& e, const PairInfo& P,
+                                              const double* __restrict__ phi, int nx, int ny,
+                                              int nz, const double* __restrict__ v, const DF* Pd,
+                                              const double* Ps, double hx, double hy, double hz,
+                                              double* __restrict__ out, int t0, int t1) {
+  const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
+  const size_t ng = (size_t)nx * ny * nz;
+  const double* fp = phi + (size_t)e.partner * ng;
+  const double cx = 0.5 * (P.ext[0] - 1), cy = 0.5 * (P.ext[1] - 1), cz = 0.5 * (P.ext[2] - 1);
+  const float cxf = 0.5f * i2f_exact(P.ext[0] - 1), cyf = 0.5f * i2f_exact(P.ext[1] - 1),
+              czf = 0.5f * i2f_exact(P.ext[2] - 1);
+  // window coordinates of t, advanced by the CTA stride without divisions;
+  // grid coordinates from the window start wrapped once
+  const int wx = e.wl[0], wy = e.wl[1], wxy = wx * wy;
+  const int S = blockDim.x;
+  const int dz = S / wxy, dy = (S - dz * wxy) / wx, dx = S - dz * wxy - dy * wx;
+  const int gx0 = wrapi(e.ws[0], nx), gy0 = wrapi(e.ws[1], ny), gz0 = wrapi(e.ws[2], nz);
+  int tz = (t0 + (int)threadIdx.x) / wxy;
+  int ty = (t0 + (int)threadIdx.x - tz * wxy) / wx;
+  int tx = t0 + (int)threadIdx.x - tz * wxy - ty * wx;
+  for (int t = t0 + threadIdx.x; t < t1; t += S) {
+    const int ux = e.ws[0] + tx, uy = e.ws[1] + ty, uz = e.ws[2] + tz;
+    const int lx = ux - P.lo[0], ly = uy - P.lo[1], lz = uz - P.lo[2];
+    const bool inside =
+        lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2];
+    int gx = gx0 + tx, gy = gy0 + ty, gz = gz0 + tz;  // window lengths are at most n
+    gx -= gx >= nx ? nx : 0;
+    gy -= gy >= ny ? ny : 0;
+    gz -= gz >= nz ? nz : 0;
+    const size_t g = ((size_t)gz * ny + gy) * nx + gx;
+    tx += dx;
+    ty += dy;
+    tz += dz;
+    if (tx >= wx) {
+      tx -= wx;
+      ++ty;
+    }
+    if (ty >= wy) {
+      ty -= wy;
+      ++tz;
+    }
+    if ((part == 1 && inside) || (part == 2 && !inside)) continue;
+    if (DFM) {  // c = v phi in double-float, no FP64 instruction
+      DF val;
+      if (inside) {
+        const float2 s = split64(v[(lz * P.ext[1] + ly) * P.ext[0] + lx]);
+        val = DF{s.x, s.y};
+      } else {  // lx - cx etc. are half-integers, exact in FP32
+        val = me_potential_cart_df(Pd, df_mul_f(i2f_exact(lx) - cxf, Hx),
+                                   df_mul_f(i2f_exact(ly) - cyf, Hy), df_mul_f(i2f_exact(lz) - czf, Hz));
+      }
+      const float2 f = split64(fp[g]);
+      out[t] = df_to_double(df_mul(val, DF{f.x, f.y}));
+    } else {
+      const double val = inside ? v[(lz * P.ext[1] + ly) * P.ext[0] + lx]
+                                : me_potential_cart(Ps, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
+      out[t] = __dmul_rn(val, fp[g]);
+    }
+  }
+}
+
+
+// Launch wrappers (each file implements its own).
 cudaError_t launch_plan_boxes(sea_ctx* c);
 cudaError_t launch_plan_pairs(sea_ctx* c);
 cudaError_t launch_pair_setup(sea_ctx* c);
 cudaError_t launch_cg(sea_ctx* c);
+cudaError_t launch_contrib_far(sea_ctx* c, cudaEvent_t setup_done);
 void make_batch_desc(sea_ctx* c, void* out);
 size_t batch_desc_bytes();
 // The persistent batched CG: ctas_per_sm CTAs per SM (0 or above the
