@@ -547,29 +547,36 @@ static sea_status build_ace_common(sea_ctx* c) {
   cudaError_t e = sea::launch_ace_build(c);
   if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE workspace");
   SEA_CK(e, "ace build");
-  unsigned st = 0;
-  SEA_CK(cudaMemcpyAsync(&st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+  // the status and, for the Cholesky form, E_xx^ACE in one read-back
+  struct {
+    double exx_ace;
+    unsigned st;
+  } rb = {0.0, 0u};
+  SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
+  SEA_CK(cudaMemcpyAsync(&rb.exx_ace, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT, sizeof(double),
+                         cudaMemcpyDeviceToHost, c->stream),
+         "exx_ace");
+  SEA_CK(cudaMemcpyAsync(&rb.st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
          "status");
   SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
-  if (st & SEA_FLAG_WAIT)
+  if (rb.st & SEA_FLAG_WAIT)
     return sea_fail(c, SEA_ERR_CUDA, "a tensor-core completion wait timed out (M build)");
-  const bool not_pd = (st & SEA_FLAG_NOT_PD) != 0;
+  const bool not_pd = (rb.st & SEA_FLAG_NOT_PD) != 0;
   if ((not_pd && c->prm.ace_decomp == 0) || c->prm.ace_decomp == 2) {
     tr.stage("eigen-decomposition");
     e = sea::launch_ace_eigen(c);
     if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE eigen workspace");
     SEA_CK(e, "ace eigen form");
     c->stats.ace_eigen = 1;
+    SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
+    SEA_CK(cudaMemcpyAsync(&rb.exx_ace, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT, sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream),
+           "exx_ace");
+    SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
   } else if (not_pd) {
     return sea_fail(c, SEA_ERR_NOT_PD, "-Mbar is not positive definite");
   }
-  SEA_CK(cudaEventRecord(c->ev[6], c->stream), "event");
-  double exx_ace = 0.0;
-  SEA_CK(cudaMemcpyAsync(&exx_ace, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT, sizeof(double),
-                         cudaMemcpyDeviceToHost, c->stream),
-         "exx_ace");
-  SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
-  c->stats.exx_ace = exx_ace;
+  c->stats.exx_ace = rb.exx_ace;
   float t = 0;
   cudaEventElapsedTime(&t, c->ev[5], c->ev[6]);
   c->stats.ms_ace_build = t;

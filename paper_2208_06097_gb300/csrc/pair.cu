@@ -95,11 +95,12 @@ __global__ void __launch_bounds__(256)
     k_pair_moments(const double* __restrict__ phi, int nx, int ny, int nz,
                    const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
                    double hx, double hy, double hz, double dV, int lmax,
-                   double* __restrict__ bbuf, double* __restrict__ Qout) {
+                   double* __restrict__ bbuf, double* __restrict__ Qout,
+                   const int* __restrict__ order) {
   typedef MomR<DFM> R;
   typedef typename R::T T;
   extern __shared__ double mom_sm[];
-  const int p = blockIdx.x;
+  const int p = order[blockIdx.x];  // the largest pairs first: the small ones fill the tail
   const PairInfo P = pinfo[p];
   const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
   const int Z = min(MOM_ZSLAB, max(1, 256 / ey));  // planes per slab
@@ -240,8 +241,9 @@ template <bool DFM>
 __global__ void __launch_bounds__(256, DFM ? 2 : 1)
     k_pair_boundary(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
                     double hx, double hy, double hz, StencilW W, StencilWd Wd,
-                    const double* __restrict__ Qg, double* __restrict__ bbuf) {
-  const int p = blockIdx.x;
+                    const double* __restrict__ Qg, double* __restrict__ bbuf,
+                    const int* __restrict__ order) {
+  const int p = order[blockIdx.x];  // the largest pairs first: the small ones fill the tail
   const PairInfo P = pinfo[p];
   const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
   double* b = bbuf + voff[p];
@@ -1037,7 +1039,7 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
   moments<<<c->P, 256, msm, c->stream>>>(
       (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const PairInfo*)c->pinfo.p,
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
-      (double*)c->bbuf.p, (double*)c->Q.p);
+      (double*)c->bbuf.p, (double*)c->Q.p, (const int*)c->order.p);
   auto boundary = c->prm.precision == 1 ? k_pair_boundary<true> : k_pair_boundary<false>;
   const StencilW W = make_weights(c);
   StencilWd Wd;
@@ -1048,7 +1050,7 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
     }
   boundary<<<c->P, 256, 0, c->stream>>>(
       (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], W, Wd,
-      (const double*)c->Q.p, (double*)c->bbuf.p);
+      (const double*)c->Q.p, (double*)c->bbuf.p, (const int*)c->order.p);
   c->launches += 2;
   return cudaGetLastError();
 }
