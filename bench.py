@@ -122,9 +122,9 @@ def job_value(steps, ws, t_ms_max):
 # written once, so the traffic grows in proportion); see
 # profiles/dram_traffic_h2o64_96.md.  None: not captured.
 DRAM_BYTES_PER_LAUNCH = {
-    "k_cg_mixed": 26.8e6,
-    "k_gram_tc": 2.08e9,
-    "k_expand_tc": 1.98e9,
+    "k_cg_mixed": 26.6e6,
+    "k_gram_tc": 2.026e9,
+    "k_expand_tc": 1.934e9,
 }
 
 
