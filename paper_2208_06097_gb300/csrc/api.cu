@@ -899,7 +899,7 @@ void sea_destroy(sea_ctx* c) {
                    &c->Q, &c->epair, &c->iters, &c->vbuf, &c->bbuf, &c->rbuf, &c->pbuf,
                    &c->qbuf, &c->eptr, &c->eent, &c->ewin, &c->coff, &c->cbuf, &c->status,
                    &c->exx_dev, &c->queue, &c->tmask, &c->tptr_o, &c->tlist_o, &c->tslot_o,
-                   &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf, &c->wdig, &c->wx, &c->xevb,
+                   &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf, &c->wdig, &c->wx, &c->xevb, &c->gbuf,
                    &c->scdm_u, &c->scdm_c,
                    &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2, &c->bdesc, &c->bitems,
                    &c->onorm};

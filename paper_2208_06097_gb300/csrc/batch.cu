@@ -157,6 +157,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
         !sea_ensure(c, c->qbuf, U * sizeof(double)) ||
         !sea_ensure(c, c->cbuf, (size_t)(c->WC > 1 ? c->WC : 1) * sizeof(double)) ||
         !sea_ensure(c, c->Q, P * SEA_QSTRIDE * sizeof(double)) ||
+        !sea_ensure(c, c->gbuf, 36 * U * sizeof(double)) ||
         !sea_ensure(c, c->epair, P * sizeof(double)) || !sea_ensure(c, c->iters, P * sizeof(int)))
       return sea_fail(c, SEA_ERR_OOM, "device allocation failed: batch buffers");
     total += c->P;

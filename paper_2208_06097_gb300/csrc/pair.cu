@@ -2,9 +2,10 @@
 //
 // k_pair_moments (one CTA per pair): rho_ij = phi_i phi_j on Omega_ij and
 //   its multipole moments about the box centre; b = 4 pi rho.
-// k_pair_boundary (one CTA per pair): the multipole potential at every
-//   point outside the box that the 37-point stencil reaches (one coordinate
-//   outside, by 1..6), added to b with the stencil weights.
+// k_ghost_eval (one CTA per pair and axis), k_boundary_apply (one CTA per
+//   pair): the multipole potential at every point outside the box that the
+//   37-point stencil reaches (one coordinate outside, by 1..6), added to b
+//   with the stencil weights.
 // k_cg (persistent, longest pairs first): conjugate gradients for
 //   -Lap_h v = b on the box with zero values outside, FP64, two block
 //   reductions per iteration (warp shuffles, then warps in fixed order),
@@ -224,29 +225,41 @@ __global__ void __launch_bounds__(256)
 }
 
 // Boundary values (Eq. me) at every point outside the box that the
-// 37-point stencil reaches, moved into b with the stencil weights; one CTA
-// per pair, the axes one after the other: the ghost values of up to
-// SEA_BND_LINES lines across the axis (one evaluation per thread) go to
-// shared memory, then one thread per line adds them into b (every b entry
-// is updated in a fixed order).
+// 37-point stencil reaches, moved into b with the stencil weights, in two
+// kernels.  k_ghost_eval (a CTA per pair and axis, the largest pairs first):
+// the ghost values of every line across the axis (one evaluation per
+// thread) into a global buffer, per pair at 36 voff (12 values per line;
+// the three faces, each at most the box's volume, fit in 36 times it).
+// k_boundary_apply (a CTA per pair): one thread per (line, boundary point)
+// adds the weighted ghost values into b, the axes one after the other, so
+// every b entry is updated in a fixed order.
 // The stencil's right-hand-side weights as double-float pairs (mixed form).
 struct StencilWd {
   float hi[3][SEA_FDP + 1], lo[3][SEA_FDP + 1];
 };
 
-// DFM: the potentials and their weighted sums in double-float arithmetic
-// (mixed form).
-#define SEA_BND_LINES 128
+// Line (u1, u2) across axis a: its coordinates on the other two axes, the
+// face extents and the ghost buffer offset of axis a within the pair.
+__device__ __forceinline__ void ghost_face(int a, int ex, int ey, int ez, int* e1, int* e2,
+                                           int* ea, int* sa, int* goff) {
+  *e1 = a == 0 ? ey : ex;
+  *e2 = a == 2 ? ey : ez;
+  *ea = a == 0 ? ex : (a == 1 ? ey : ez);
+  *sa = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
+  *goff = 2 * SEA_FDP * (a == 0 ? 0 : (a == 1 ? ey * ez : ey * ez + ex * ez));
+}
+
+// DFM: the potentials in double-float arithmetic (mixed form; four CTAs per
+// SM, the nested Horner steps being one dependent chain per point).
 template <bool DFM>
-__global__ void __launch_bounds__(256, DFM ? 2 : 1)
-    k_pair_boundary(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
-                    double hx, double hy, double hz, StencilW W, StencilWd Wd,
-                    const double* __restrict__ Qg, double* __restrict__ bbuf,
-                    const int* __restrict__ order) {
-  const int p = order[blockIdx.x];  // the largest pairs first: the small ones fill the tail
+__global__ void __launch_bounds__(256, DFM ? 4 : 1)
+    k_ghost_eval(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
+                 double hx, double hy, double hz, const double* __restrict__ Qg,
+                 double* __restrict__ gbuf, const int* __restrict__ order) {
+  const int a = blockIdx.x;
+  const int p = order[blockIdx.y];  // the largest pairs first: the small ones fill the tail
   const PairInfo P = pinfo[p];
   const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
-  double* b = bbuf + voff[p];
   __shared__ double Ps[SEA_NMONO];
   __shared__ DF Pd[SEA_NMONO];
   if (threadIdx.x < SEA_NMONO) {
@@ -257,75 +270,84 @@ __global__ void __launch_bounds__(256, DFM ? 2 : 1)
       Ps[threadIdx.x] = q;
   }
   __syncthreads();
-  // me_potential at grid offsets (ox, oy, oz) from the box centre, in units
-  // of h (half-integers, exact in FP32)
+  // the potential at grid offsets (ox, oy, oz) from the box centre, in
+  // units of h (half-integers, exact in FP32)
   const DF Hx = df_from_double(hx), Hy = df_from_double(hy), Hz = df_from_double(hz);
   const float cx = 0.5f * i2f_exact(ex - 1), cy = 0.5f * i2f_exact(ey - 1),
               cz = 0.5f * i2f_exact(ez - 1);
   constexpr int NG = 2 * SEA_FDP;  // ghost values per line: d = 1..FDP below, then above
-  __shared__ double Gs[SEA_BND_LINES * NG];  // plain form
-  __shared__ DF Gd[SEA_BND_LINES * NG];      // mixed form
-  for (int a = 0; a < 3; ++a) {
-    // line coordinates (u1, u2) across axis a; along-axis extent ea, stride sa
-    const int e1 = a == 0 ? ey : ex, e2 = a == 2 ? ey : ez;
-    const int ea = a == 0 ? ex : (a == 1 ? ey : ez);
-    const int sa = a == 0 ? 1 : (a == 1 ? ex : ex * ey);
-    const float ca = a == 0 ? cx : (a == 1 ? cy : cz);
-    const int nl = e1 * e2;
-    for (int l0 = 0; l0 < nl; l0 += SEA_BND_LINES) {
-      const int nb = min(SEA_BND_LINES, nl - l0);
-      // the ghost values of SEA_BND_LINES lines, one evaluation per thread
-      for (int e = threadIdx.x; e < nb * NG; e += blockDim.x) {
-        const int line = l0 + e / NG, k = e % NG;
-        const int u1 = line % e1, u2 = line / e1;
-        const float o1 = i2f_exact(u1) - (a == 0 ? cy : cx), o2 = i2f_exact(u2) - (a == 2 ? cy : cz);
-        const int d = k % SEA_FDP + 1;
-        const float t = i2f_exact(k < SEA_FDP ? -d : ea - 1 + d) - ca;
-        const float ox = a == 0 ? t : o1, oy = a == 0 ? o1 : (a == 1 ? t : o2);
-        const float oz = a == 2 ? t : o2;
-        if (DFM)
-          Gd[e] = me_potential_cart_df(Pd, df_mul_f(ox, Hx), df_mul_f(oy, Hy), df_mul_f(oz, Hz));
-        else
-          Gs[e] = me_potential_cart(Ps, (double)ox * hx, (double)oy * hy, (double)oz * hz);
-      }
-      __syncthreads();
-      // moved into b with the stencil weights: thread per (line, boundary
-      // point); the terms of each point in a fixed order
-      const int nbp = min(ea, NG);  // points of a line within FDP of either end
-      for (int e = threadIdx.x; e < nb * nbp; e += blockDim.x) {
-        const int li = e / nbp, idx = e % nbp;
-        const int ta = ea <= NG ? idx : (idx < SEA_FDP ? idx : ea - NG + idx);
-        const int line = l0 + li;
-        const int u1 = line % e1, u2 = line / e1;
-        int bx = 0, by = 0, bz = 0;
-        if (a == 0) { by = u1; bz = u2; }
-        else if (a == 1) { bx = u1; bz = u2; }
-        else { bx = u1; by = u2; }
-        const int base = (bz * ey + by) * ex + bx;
-        // ghost value d below: entry d - 1; above: entry FDP + d - 1
-        if (DFM) {
-          const DF* G = Gd + li * NG;
-          DF add{0.f, 0.f};
-#pragma unroll
-          for (int k = 1; k <= SEA_FDP; ++k) {
-            const DF w{Wd.hi[a][k], Wd.lo[a][k]};
-            if (ta - k < 0) add = df_add(add, df_mul(w, G[k - ta - 1]));
-            if (ta + k > ea - 1) add = df_add(add, df_mul(w, G[SEA_FDP + ta + k - (ea - 1) - 1]));
-          }
-          b[base + ta * sa] += df_to_double(add);
-        } else {
-          const double* G = Gs + li * NG;
-          double add = 0.0;
-#pragma unroll
-          for (int k = 1; k <= SEA_FDP; ++k) {
-            if (ta - k < 0) add += W.rhs[a][k] * G[k - ta - 1];
-            if (ta + k > ea - 1) add += W.rhs[a][k] * G[SEA_FDP + ta + k - (ea - 1) - 1];
-          }
-          b[base + ta * sa] += add;
-        }
-      }
-      __syncthreads();
+  int e1, e2, ea, sa, goff;
+  ghost_face(a, ex, ey, ez, &e1, &e2, &ea, &sa, &goff);
+  const float ca = a == 0 ? cx : (a == 1 ? cy : cz);
+  double* G = gbuf + 36 * voff[p] + goff;
+  const int nl = e1 * e2;
+  for (int e = threadIdx.x; e < nl * NG; e += blockDim.x) {
+    const int line = e / NG, k = e % NG;
+    const int u1 = line % e1, u2 = line / e1;
+    const float o1 = i2f_exact(u1) - (a == 0 ? cy : cx), o2 = i2f_exact(u2) - (a == 2 ? cy : cz);
+    const int d = k % SEA_FDP + 1;
+    const float t = i2f_exact(k < SEA_FDP ? -d : ea - 1 + d) - ca;
+    const float ox = a == 0 ? t : o1, oy = a == 0 ? o1 : (a == 1 ? t : o2);
+    const float oz = a == 2 ? t : o2;
+    if (DFM) {
+      const DF g = me_potential_cart_df(Pd, df_mul_f(ox, Hx), df_mul_f(oy, Hy), df_mul_f(oz, Hz));
+      reinterpret_cast<DF*>(G)[e] = g;
+    } else {
+      G[e] = me_potential_cart(Ps, (double)ox * hx, (double)oy * hy, (double)oz * hz);
     }
+  }
+}
+
+template <bool DFM>
+__global__ void __launch_bounds__(256)
+    k_boundary_apply(const PairInfo* __restrict__ pinfo, const long long* __restrict__ voff,
+                     StencilW W, StencilWd Wd, const double* __restrict__ gbuf,
+                     double* __restrict__ bbuf, const int* __restrict__ order) {
+  const int p = order[blockIdx.x];
+  const PairInfo P = pinfo[p];
+  const int ex = P.ext[0], ey = P.ext[1], ez = P.ext[2];
+  double* b = bbuf + voff[p];
+  constexpr int NG = 2 * SEA_FDP;
+  for (int a = 0; a < 3; ++a) {
+    int e1, e2, ea, sa, goff;
+    ghost_face(a, ex, ey, ez, &e1, &e2, &ea, &sa, &goff);
+    const double* Gp = gbuf + 36 * voff[p] + goff;
+    const int nl = e1 * e2;
+    const int nbp = min(ea, NG);  // points of a line within FDP of either end
+    // thread per (line, boundary point); the terms of each point in a fixed
+    // order, the axes one after the other
+    for (int e = threadIdx.x; e < nl * nbp; e += blockDim.x) {
+      const int line = e / nbp, idx = e % nbp;
+      const int ta = ea <= NG ? idx : (idx < SEA_FDP ? idx : ea - NG + idx);
+      const int u1 = line % e1, u2 = line / e1;
+      int bx = 0, by = 0, bz = 0;
+      if (a == 0) { by = u1; bz = u2; }
+      else if (a == 1) { bx = u1; bz = u2; }
+      else { bx = u1; by = u2; }
+      const int base = (bz * ey + by) * ex + bx;
+      // ghost value d below: entry d - 1; above: entry FDP + d - 1
+      if (DFM) {
+        const DF* G = reinterpret_cast<const DF*>(Gp) + (size_t)line * NG;
+        DF add{0.f, 0.f};
+#pragma unroll
+        for (int k = 1; k <= SEA_FDP; ++k) {
+          const DF w{Wd.hi[a][k], Wd.lo[a][k]};
+          if (ta - k < 0) add = df_add(add, df_mul(w, G[k - ta - 1]));
+          if (ta + k > ea - 1) add = df_add(add, df_mul(w, G[SEA_FDP + ta + k - (ea - 1) - 1]));
+        }
+        b[base + ta * sa] += df_to_double(add);
+      } else {
+        const double* G = Gp + (size_t)line * NG;
+        double add = 0.0;
+#pragma unroll
+        for (int k = 1; k <= SEA_FDP; ++k) {
+          if (ta - k < 0) add += W.rhs[a][k] * G[k - ta - 1];
+          if (ta + k > ea - 1) add += W.rhs[a][k] * G[SEA_FDP + ta + k - (ea - 1) - 1];
+        }
+        b[base + ta * sa] += add;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1040,7 +1062,10 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
       (const double*)c->phi.p, c->N[0], c->N[1], c->N[2], (const PairInfo*)c->pinfo.p,
       (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], c->dV, c->prm.lmax,
       (double*)c->bbuf.p, (double*)c->Q.p, (const int*)c->order.p);
-  auto boundary = c->prm.precision == 1 ? k_pair_boundary<true> : k_pair_boundary<false>;
+  if (!sea_ensure(c, c->gbuf, (size_t)36 * std::max<long long>(c->U, 1) * sizeof(double)))
+    return cudaErrorMemoryAllocation;
+  auto geval = c->prm.precision == 1 ? k_ghost_eval<true> : k_ghost_eval<false>;
+  auto gapply = c->prm.precision == 1 ? k_boundary_apply<true> : k_boundary_apply<false>;
   const StencilW W = make_weights(c);
   StencilWd Wd;
   for (int a = 0; a < 3; ++a)
@@ -1048,10 +1073,13 @@ cudaError_t launch_pair_setup(sea_ctx* c) {
       Wd.hi[a][k] = (float)W.rhs[a][k];
       Wd.lo[a][k] = (float)(W.rhs[a][k] - (double)Wd.hi[a][k]);
     }
-  boundary<<<c->P, 256, 0, c->stream>>>(
-      (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2], W, Wd,
-      (const double*)c->Q.p, (double*)c->bbuf.p, (const int*)c->order.p);
-  c->launches += 2;
+  geval<<<dim3(3, c->P), 256, 0, c->stream>>>(
+      (const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, c->h[0], c->h[1], c->h[2],
+      (const double*)c->Q.p, (double*)c->gbuf.p, (const int*)c->order.p);
+  gapply<<<c->P, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const long long*)c->voff.p, W,
+                                      Wd, (const double*)c->gbuf.p, (double*)c->bbuf.p,
+                                      (const int*)c->order.p);
+  c->launches += 3;
   return cudaGetLastError();
 }
 

@@ -566,6 +566,7 @@ struct sea_ctx {
   SeaBuf wdig;  // the mixed form's W digits (tensor-core contraction)
   SeaBuf wx;    // the mixed form's per-tile W digit images (tensor-core expansion)
   SeaBuf xevb;  // the expansion's H exponents per (tile, vector)
+  SeaBuf gbuf;  // ghost (boundary) values of the pair boxes, 36 voff per pair
   SeaBuf scdm_u, scdm_c;  // SCDM rotation and pivots
   SeaBuf tmask, tptr_o, tlist_o, tslot_o, tptr_t, tlist_t, partial, Mbuf, Abuf, Lbuf, Linv,
       Gbuf, Hbuf, Hbuf2;
