@@ -930,6 +930,84 @@ static size_t inv_scratch_doubles(int n) {
   return m;
 }
 
+// The Cholesky of -Mbar, L^-1 and E_xx^ACE: about 30 small launches whose
+// shapes depend on n alone.  On a stream that can be captured they are
+// recorded once into a CUDA graph (per context; again when a buffer moves or
+// n or the form changes) and replayed, which removes most of the gaps
+// between these latency-bound launches.
+static cudaError_t enqueue_chol_chain(sea_ctx* c) {
+  const int n = c->n_orb;
+  k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
+      (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
+  double* L = (double*)c->Lbuf.p;
+  double* Y = (double*)c->Abuf.p;  // Y_kk blocks, CB x CB each
+  unsigned* status = (unsigned*)c->status.p;
+  int nchol = 1;
+  for (int kb = 0, b = 0; kb < n; kb += CB, ++b) {
+    if (c->prm.precision == 1)
+      k_chol_diag_df<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
+    else
+      k_chol_diag<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
+    const int rows = n - kb - CB;
+    if (rows > 0) {
+      const int nt = (rows + 15) / 16;
+      k_chol_trsm<<<nt, 512, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
+      k_chol_syrk<<<nt * (nt + 1) / 2, 256, 0, c->stream>>>(L, n, kb, status);
+      nchol += 2;
+    }
+    nchol += 1;
+  }
+  double* Linv = (double*)c->Linv.p;
+  k_linv_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(Y, n, Linv);
+  for (int s = CB; s < n; s *= 2) {
+    const int pairs = (n - s + 2 * s - 1) / (2 * s);
+    const dim3 g((s + 15) / 16, (s + 15) / 16, pairs);
+    double* T = (double*)c->Hbuf2.p;
+    k_inv_pairs<<<g, 256, 0, c->stream>>>(n, s, 0, L, Linv, T);
+    k_inv_pairs<<<g, 256, 0, c->stream>>>(n, s, 1, L, Linv, T);
+    nchol += 2;
+  }
+  c->launches += 8 + nchol;
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  return launch_exx_ace(c, 0, nullptr);  // Y = L^-1 M^T
+}
+
+static cudaError_t launch_chol_chain(sea_ctx* c) {
+  if (!c->stream) return enqueue_chol_chain(c);  // the legacy stream: no capture
+  const int n = c->n_orb;
+  const int nparts = ((n + 31) / 32) * ((n + 1) / 2);
+  if (!sea_ensure(c, c->Gbuf, (size_t)nparts * sizeof(double))) return cudaErrorMemoryAllocation;
+  const void* sig[8] = {c->Mbuf.p, c->Lbuf.p, c->Abuf.p, c->Linv.p, c->Hbuf2.p, c->Gbuf.p,
+                        c->status.p, c->exx_dev.p};
+  bool same = c->chol_exec != nullptr && c->chol_n == n && c->chol_prec == c->prm.precision;
+  for (int k = 0; k < 8 && same; ++k) same = c->chol_sig[k] == sig[k];
+  if (!same) {
+    if (c->chol_exec) {
+      cudaGraphExecDestroy(c->chol_exec);
+      c->chol_exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const long long launches0 = c->launches;
+    e = enqueue_chol_chain(c);
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return e;
+    if (e2 != cudaSuccess) return e2;
+    e = cudaGraphInstantiate(&c->chol_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    c->chol_launches = c->launches - launches0;
+    c->launches = launches0;
+    c->chol_n = n;
+    c->chol_prec = c->prm.precision;
+    for (int k = 0; k < 8; ++k) c->chol_sig[k] = sig[k];
+  }
+  c->launches += c->chol_launches;
+  return cudaGraphLaunch(c->chol_exec, c->stream);
+}
+
 // Tile lists of W's support, M, Cholesky and L^-1.  Needs the incidence
 // count on the host to size the partial sums: one stream sync.
 cudaError_t launch_ace_build(sea_ctx* c) {
@@ -1025,40 +1103,8 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   k_gram_reduce<<<(unsigned)(((long long)n * n + 63) / 64), 64, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
       n, 1);
-  k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
-      (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
-  double* L = (double*)c->Lbuf.p;
-  double* Y = (double*)c->Abuf.p;  // Y_kk blocks, CB x CB each
-  unsigned* status = (unsigned*)c->status.p;
-  int nchol = 1;
-  for (int kb = 0, b = 0; kb < n; kb += CB, ++b) {
-    if (c->prm.precision == 1)
-      k_chol_diag_df<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
-    else
-      k_chol_diag<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
-    const int rows = n - kb - CB;
-    if (rows > 0) {
-      const int nt = (rows + 15) / 16;
-      k_chol_trsm<<<nt, 512, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
-      k_chol_syrk<<<nt * (nt + 1) / 2, 256, 0, c->stream>>>(L, n, kb, status);
-      nchol += 2;
-    }
-    nchol += 1;
-  }
-  double* Linv = (double*)c->Linv.p;
-  k_linv_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(Y, n, Linv);
-  for (int s = CB; s < n; s *= 2) {
-    const int pairs = (n - s + 2 * s - 1) / (2 * s);
-    const dim3 g((s + 15) / 16, (s + 15) / 16, pairs);
-    double* T = (double*)c->Hbuf2.p;
-    k_inv_pairs<<<g, 256, 0, c->stream>>>(n, s, 0, L, Linv, T);
-    k_inv_pairs<<<g, 256, 0, c->stream>>>(n, s, 1, L, Linv, T);
-    nchol += 2;
-  }
-  c->launches += 10 + nchol;
-  err = cudaGetLastError();
-  if (err != cudaSuccess) return err;
-  err = launch_exx_ace(c, 0, nullptr);  // Y = L^-1 M^T
+  c->launches += 2;
+  err = launch_chol_chain(c);
   if (err == cudaSuccess && c->prm.precision == 1) err = cudaStreamWaitEvent(c->stream, c->xev[0], 0);
   return err;
 }

@@ -893,6 +893,7 @@ void sea_destroy(sea_ctx* c) {
   for (cudaEvent_t e : c->xev)
     if (e) cudaEventDestroy(e);
   sea_batch_cache_free(c);
+  if (c->chol_exec) cudaGraphExecDestroy(c->chol_exec);
   SeaBuf* all[] = {&c->phi, &c->vxx_dev, &c->psi_dev, &c->out_dev, &c->rowsum, &c->colsum,
                    &c->marg, &c->box, &c->cand_flag, &c->cand_geom, &c->list_a, &c->list_b,
                    &c->cand_S, &c->counts, &c->pinfo, &c->pS, &c->psize, &c->voff, &c->order,

@@ -580,6 +580,10 @@ struct sea_ctx {
   std::vector<int> h_eptr;  // entry offsets per orbital, host copy (last plan)
   struct sea_unet* unet = nullptr;  // learned warm start (attached model, not owned)
   bool cg_warm = false;             // the next CG starts from the guess in vbuf
+  cudaGraphExec_t chol_exec = nullptr;  // the captured Cholesky / L^-1 / E_xx^ACE chain
+  const void* chol_sig[8] = {};         // the buffers it was captured with
+  int chol_n = 0, chol_prec = -1;
+  long long chol_launches = 0;
   bool far_side = false;            // the contributions outside the pair boxes were
                                     // launched on xfer[0] (done at xev[1])
   cudaEvent_t xev[2 * SEA_XCHUNKS_MAX + 2] = {};

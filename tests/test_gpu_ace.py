@@ -100,3 +100,32 @@ def test_exx_ace_closed_form(h2o8, precision):
 
 def F_of(s):
     return s.phi.reshape(s.n_orb, -1)
+
+
+@pytest.mark.parametrize("precision,own_stream", [(0, True), (1, True), (1, False)])
+def test_build_repeats_bit_for_bit(h2o8, precision, own_stream):
+    # On a context stream that can be captured, the Cholesky / L^-1 /
+    # E_xx^ACE chain is recorded once into a graph and replayed by later
+    # builds: every build gives the same M, L, E_xx^ACE and V^ACE psi, bit
+    # for bit, as does the legacy stream (no capture).
+    from paper_2208_06097_gb300 import sea
+    st = torch.cuda.Stream() if own_stream else None
+    kw = {"stream": st.cuda_stream} if own_stream else {}
+    ctx = sea.Context(h2o8.cell, h2o8.grid, precision=precision, **kw)
+    phi = torch.from_numpy(h2o8.phi).cuda()
+    out = torch.empty_like(phi)
+    ctx.set_orbitals(phi)
+    ctx.apply_vxx(out)
+    psi = torch.from_numpy(synth.random_trial_vectors(4, h2o8.grid, 7)).cuda()
+    runs = []
+    for _ in range(3):
+        ctx.build_ace()
+        M, L = ctx.ace_matrices()
+        y = torch.empty_like(psi)
+        ctx.apply_ace(psi, y)
+        torch.cuda.synchronize()
+        runs.append((M, L, ctx.stats()["exx_ace"], y.cpu().numpy()))
+    for M, L, e, y in runs[1:]:
+        assert np.array_equal(M, runs[0][0]) and np.array_equal(L, runs[0][1])
+        assert e == runs[0][2] and np.array_equal(y, runs[0][3])
+    ctx.close()
