@@ -931,10 +931,8 @@ static size_t inv_scratch_doubles(int n) {
 }
 
 // The Cholesky of -Mbar, L^-1 and E_xx^ACE: about 30 small launches whose
-// shapes depend on n alone.  On a stream that can be captured they are
-// recorded once into a CUDA graph (per context; again when a buffer moves or
-// n or the form changes) and replayed, which removes most of the gaps
-// between these latency-bound launches.
+// shapes depend on n alone, replayed from a graph (run_graph; recorded again
+// when a buffer moves or n or the form changes).
 static cudaError_t enqueue_chol_chain(sea_ctx* c) {
   const int n = c->n_orb;
   k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
@@ -974,38 +972,14 @@ static cudaError_t enqueue_chol_chain(sea_ctx* c) {
 }
 
 static cudaError_t launch_chol_chain(sea_ctx* c) {
-  if (!c->stream) return enqueue_chol_chain(c);  // the legacy stream: no capture
   const int n = c->n_orb;
   const int nparts = ((n + 31) / 32) * ((n + 1) / 2);
   if (!sea_ensure(c, c->Gbuf, (size_t)nparts * sizeof(double))) return cudaErrorMemoryAllocation;
-  const void* sig[8] = {c->Mbuf.p, c->Lbuf.p, c->Abuf.p, c->Linv.p, c->Hbuf2.p, c->Gbuf.p,
-                        c->status.p, c->exx_dev.p};
-  bool same = c->chol_exec != nullptr && c->chol_n == n && c->chol_prec == c->prm.precision;
-  for (int k = 0; k < 8 && same; ++k) same = c->chol_sig[k] == sig[k];
-  if (!same) {
-    if (c->chol_exec) {
-      cudaGraphExecDestroy(c->chol_exec);
-      c->chol_exec = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return e;
-    const long long launches0 = c->launches;
-    e = enqueue_chol_chain(c);
-    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess) return e;
-    if (e2 != cudaSuccess) return e2;
-    e = cudaGraphInstantiate(&c->chol_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return e;
-    c->chol_launches = c->launches - launches0;
-    c->launches = launches0;
-    c->chol_n = n;
-    c->chol_prec = c->prm.precision;
-    for (int k = 0; k < 8; ++k) c->chol_sig[k] = sig[k];
-  }
-  c->launches += c->chol_launches;
-  return cudaGraphLaunch(c->chol_exec, c->stream);
+  const std::vector<uintptr_t> sig = {
+      (uintptr_t)n, (uintptr_t)c->prm.precision, (uintptr_t)c->Mbuf.p, (uintptr_t)c->Lbuf.p,
+      (uintptr_t)c->Abuf.p, (uintptr_t)c->Linv.p, (uintptr_t)c->Hbuf2.p, (uintptr_t)c->Gbuf.p,
+      (uintptr_t)c->status.p, (uintptr_t)c->exx_dev.p};
+  return run_graph(c, c->g_chol, sig, [&]() { return enqueue_chol_chain(c); });
 }
 
 // Tile lists of W's support, M, Cholesky and L^-1.  Needs the incidence

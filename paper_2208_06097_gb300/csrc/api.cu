@@ -20,6 +20,13 @@ namespace sea {
 // the scaling kappa_lm = tau_|m| sigma_lm with tau_0 = 1, tau_{k+1} = t_k tau_k,
 // sigma_{|m|,m} = 1, sigma_{l+1,m} = b_lm sigma_lm removes t and b; then
 // gam_lm = c_lm sigma_{l-1,m} / sigma_{l+1,m}.
+// The bit pattern of a double, for graph signatures.
+uintptr_t bits_of(double v) {
+  uintptr_t u = 0;
+  memcpy(&u, &v, sizeof(double) < sizeof(u) ? sizeof(double) : sizeof(u));
+  return u;
+}
+
 HarmCoef make_harmonic_coefficients() {
   HarmCoef h;
   memset(&h, 0, sizeof(h));
@@ -418,9 +425,27 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   tr.stage("plan");
   SEA_CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream), "memset");
   SEA_CK(cudaEventRecord(c->ev[0], c->stream), "event");
-  SEA_CK(sea::launch_plan_boxes(c), "domain boxes");
-  SEA_CK(sea::launch_plan_pairs(c), "pair selection");
-  SEA_CK(sea::launch_entries(c), "accumulation entries");
+  {
+    // the plan: a fixed launch sequence for the context's sizes and buffers
+    const std::vector<uintptr_t> sig = {
+        (uintptr_t)c->n_orb, (uintptr_t)c->N[0], (uintptr_t)c->N[1], (uintptr_t)c->N[2],
+        (uintptr_t)c->device, sea::bits_of(c->prm.eps), sea::bits_of(c->prm.delta),
+        sea::bits_of(c->dV),
+        (uintptr_t)c->phi.p, (uintptr_t)c->rowsum.p, (uintptr_t)c->colsum.p, (uintptr_t)c->marg.p,
+        (uintptr_t)c->box.p, (uintptr_t)c->cand_flag.p, (uintptr_t)c->cand_geom.p,
+        (uintptr_t)c->list_a.p, (uintptr_t)c->list_b.p, (uintptr_t)c->cand_S.p,
+        (uintptr_t)c->counts.p, (uintptr_t)c->pinfo.p, (uintptr_t)c->pS.p, (uintptr_t)c->psize.p,
+        (uintptr_t)c->voff.p, (uintptr_t)c->order.p, (uintptr_t)c->eent.p, (uintptr_t)c->eptr.p,
+        (uintptr_t)c->ewin.p, (uintptr_t)c->coff.p};
+    SEA_CK(run_graph(c, c->g_plan, sig,
+                          [&]() {
+                            cudaError_t e = sea::launch_plan_boxes(c);
+                            if (e == cudaSuccess) e = sea::launch_plan_pairs(c);
+                            if (e == cudaSuccess) e = sea::launch_entries(c);
+                            return e;
+                          }),
+           "plan");
+  }
   int hc[16];
   SEA_CK(cudaMemcpyAsync(hc, c->counts.p, sizeof(hc), cudaMemcpyDeviceToHost, c->stream), "counts");
   if (!on_device) {  // entry offsets: the output is produced and copied out by orbital ranges
@@ -893,7 +918,8 @@ void sea_destroy(sea_ctx* c) {
   for (cudaEvent_t e : c->xev)
     if (e) cudaEventDestroy(e);
   sea_batch_cache_free(c);
-  if (c->chol_exec) cudaGraphExecDestroy(c->chol_exec);
+  for (LaunchGraph* g : {&c->g_chol, &c->g_plan})
+    if (g->exec) cudaGraphExecDestroy(g->exec);
   SeaBuf* all[] = {&c->phi, &c->vxx_dev, &c->psi_dev, &c->out_dev, &c->rowsum, &c->colsum,
                    &c->marg, &c->box, &c->cand_flag, &c->cand_geom, &c->list_a, &c->list_b,
                    &c->cand_S, &c->counts, &c->pinfo, &c->pS, &c->psize, &c->voff, &c->order,

@@ -427,50 +427,53 @@ __global__ void k_compact(const int* __restrict__ flag, long long n_host,
     if (flag[x]) out[pos++] = (int)x;
 }
 
-// One CTA per proto-pair: S_|ij| in the fixed row order, keep decision.
+// A CTA per proto-pair (CTA-stride loop over them): S_|ij| in the fixed row
+// order, keep decision.
 __global__ void k_screen(const double* __restrict__ phi, int n, int nx, int ny, int nz,
                          const int* __restrict__ proto_list, const int* __restrict__ nproto,
                          const int* __restrict__ geom, double dV, double delta,
                          int* __restrict__ keep, double* __restrict__ Sout) {
-  const int q = blockIdx.x;
-  if (q >= *nproto) return;
-  const long long c = proto_list[q];
-  int i, j;
-  decode_pair(c, n, &i, &j);
-  const int* g = geom + c * 9;
-  const int ex = g[3], ey = g[4], ez = g[5];
-  const size_t ng = (size_t)nx * ny * nz;
-  const double* fi = phi + (size_t)i * ng;
-  const double* fj = phi + (size_t)j * ng;
+  const int np = *nproto;
   __shared__ double rows[1024];
   __shared__ double tot;
-  if (threadIdx.x == 0) tot = 0.0;
-  const int nrows = ey * ez;
-  for (int r0 = 0; r0 < nrows; r0 += 1024) {
-    __syncthreads();
-    for (int r = r0 + threadIdx.x; r < min(nrows, r0 + 1024); r += blockDim.x) {
-      const int y = r % ey, z = r / ey;
-      const int gz = wrapi(g[2] + z, nz), gy = wrapi(g[1] + y, ny);
-      const size_t base = ((size_t)gz * ny + gy) * nx;
-      double row = 0.0;
-      for (int x = 0; x < ex; ++x) {
-        const int gx = wrapi(g[0] + x, nx);
-        row = __dadd_rn(row, fabs(__dmul_rn(fi[base + gx], fj[base + gx])));
+  for (int q = blockIdx.x; q < np; q += gridDim.x) {  // CTA-stride over the proto-pairs
+    __syncthreads();  // rows and tot of the previous proto-pair are consumed
+    const long long c = proto_list[q];
+    int i, j;
+    decode_pair(c, n, &i, &j);
+    const int* g = geom + c * 9;
+    const int ex = g[3], ey = g[4], ez = g[5];
+    const size_t ng = (size_t)nx * ny * nz;
+    const double* fi = phi + (size_t)i * ng;
+    const double* fj = phi + (size_t)j * ng;
+    if (threadIdx.x == 0) tot = 0.0;
+    const int nrows = ey * ez;
+    for (int r0 = 0; r0 < nrows; r0 += 1024) {
+      __syncthreads();
+      for (int r = r0 + threadIdx.x; r < min(nrows, r0 + 1024); r += blockDim.x) {
+        const int y = r % ey, z = r / ey;
+        const int gz = wrapi(g[2] + z, nz), gy = wrapi(g[1] + y, ny);
+        const size_t base = ((size_t)gz * ny + gy) * nx;
+        double row = 0.0;
+        for (int x = 0; x < ex; ++x) {
+          const int gx = wrapi(g[0] + x, nx);
+          row = __dadd_rn(row, fabs(__dmul_rn(fi[base + gx], fj[base + gx])));
+        }
+        rows[r - r0] = row;
       }
-      rows[r - r0] = row;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = tot;
+        for (int r = r0; r < min(nrows, r0 + 1024); ++r) t = __dadd_rn(t, rows[r - r0]);
+        tot = t;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = tot;
-      for (int r = r0; r < min(nrows, r0 + 1024); ++r) t = __dadd_rn(t, rows[r - r0]);
-      tot = t;
+      const double S = __dmul_rn(tot, dV);
+      Sout[q] = S;
+      keep[q] = (i == j || S >= delta) ? 1 : 0;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const double S = __dmul_rn(tot, dV);
-    Sout[q] = S;
-    keep[q] = (i == j || S >= delta) ? 1 : 0;
   }
 }
 
@@ -605,7 +608,9 @@ cudaError_t launch_plan_pairs(sea_ctx* c) {
                                            ncand, (int*)c->cand_flag.p, (int*)c->cand_geom.p);
   k_compact<<<1, 1024, 0, c->stream>>>((const int*)c->cand_flag.p, ncand, nullptr,
                                        (int*)c->list_a.p, counts + 0);
-  k_screen<<<(unsigned)ncand, 256, 0, c->stream>>>(
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  k_screen<<<(unsigned)std::min<long long>(ncand, 8LL * std::max(nsm, 1)), 256, 0, c->stream>>>(
       (const double*)c->phi.p, n, c->N[0], c->N[1], c->N[2], (const int*)c->list_a.p, counts + 0,
       (const int*)c->cand_geom.p, c->dV, c->prm.delta, (int*)c->cand_flag.p,
       (double*)c->cand_S.p);

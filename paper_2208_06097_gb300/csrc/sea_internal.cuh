@@ -525,6 +525,15 @@ inline TileGeom make_tile_geom(const int N[3]) {
 
 }  // namespace sea
 
+// A launch sequence recorded into a CUDA graph: the executable graph, the
+// signature (sizes, parameters, buffer addresses) it was recorded with, and
+// the number of kernels in it.
+struct LaunchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uintptr_t> sig;
+  long long launches = 0;
+};
+
 struct sea_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -580,14 +589,48 @@ struct sea_ctx {
   std::vector<int> h_eptr;  // entry offsets per orbital, host copy (last plan)
   struct sea_unet* unet = nullptr;  // learned warm start (attached model, not owned)
   bool cg_warm = false;             // the next CG starts from the guess in vbuf
-  cudaGraphExec_t chol_exec = nullptr;  // the captured Cholesky / L^-1 / E_xx^ACE chain
-  const void* chol_sig[8] = {};         // the buffers it was captured with
-  int chol_n = 0, chol_prec = -1;
-  long long chol_launches = 0;
+  LaunchGraph g_chol;  // the Cholesky / L^-1 / E_xx^ACE chain
+  LaunchGraph g_plan;  // the plan (boxes, pairs, accumulation entries)
   bool far_side = false;            // the contributions outside the pair boxes were
                                     // launched on xfer[0] (done at xev[1])
   cudaEvent_t xev[2 * SEA_XCHUNKS_MAX + 2] = {};
 };
+// enqueue() issues a fixed launch sequence on c->stream.  On a stream that
+// can be captured it is recorded once into gc (again whenever sig changes)
+// and the graph is replayed, which removes most of the gaps between short
+// dependent launches; on the legacy stream it runs directly.  enqueue()
+// must not allocate or synchronise.
+template <class F>
+inline cudaError_t run_graph(sea_ctx* c, LaunchGraph& gc, const std::vector<uintptr_t>& sig,
+                             F enqueue) {
+  if (!c->stream) return enqueue();
+  if (!gc.exec || gc.sig != sig) {
+    if (gc.exec) {
+      cudaGraphExecDestroy(gc.exec);
+      gc.exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const long long l0 = c->launches;
+    e = enqueue();
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    e = cudaGraphInstantiate(&gc.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    gc.launches = c->launches - l0;
+    c->launches = l0;
+    gc.sig = sig;
+  }
+  c->launches += gc.launches;
+  return cudaGraphLaunch(gc.exec, c->stream);
+}
+
 
 // Host-side helpers implemented in api.cu.
 sea_status sea_fail(sea_ctx* c, sea_status s, const char* msg);
