@@ -51,13 +51,19 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
 }
 
+// One bounded try: the thread may sleep until the phase completes, at most
+// about SEA_MBAR_SUSPEND_NS (so that waiting warps do not take issue slots
+// from working ones by polling).
+#ifndef SEA_MBAR_SUSPEND_NS
+#define SEA_MBAR_SUSPEND_NS 100000
+#endif
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
       "selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "n"(SEA_MBAR_SUSPEND_NS)
       : "memory");
   return done != 0;
 }
