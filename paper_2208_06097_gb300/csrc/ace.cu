@@ -361,27 +361,35 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// out[a * sa + o * so] = scale * sum over the tiles of o (ascending) of
-// partial[slot][a].
-__global__ void k_gram_reduce(const double* __restrict__ partial, int m, int n_orb,
-                              const int* __restrict__ optr, const int* __restrict__ oslot,
-                              double scale, double* __restrict__ out, int sa, int so) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)m * n_orb) return;
-  const int a = (int)(t % m), o = (int)(t / m);
-  // in slot order; the loads of sixteen slots are issued before their adds
+// out[a * sa + o * so] = scale * sum over the tiles of o of partial[slot][a].
+// A CTA per (orbital o, 64 values of a): its four thread groups z take the
+// slots z, z + 4, z + 8, ... of o's list (eight loads in flight each, added
+// in list order), and the four sums are added in the order z = 0, 1, 2, 3.
+constexpr int GR_A = 64, GR_Z = 4;
+__global__ void __launch_bounds__(GR_A * GR_Z)
+    k_gram_reduce(const double* __restrict__ partial, int m, int n_orb,
+                  const int* __restrict__ optr, const int* __restrict__ oslot, double scale,
+                  double* __restrict__ out, int sa, int so) {
+  __shared__ double red[GR_Z][GR_A];
+  const int o = blockIdx.y, x = threadIdx.x % GR_A, z = threadIdx.x / GR_A;
+  const int a = blockIdx.x * GR_A + x;
   double s = 0.0;
-  int k = optr[o];
-  const int k1 = optr[o + 1];
-  for (; k + 16 <= k1; k += 16) {
-    double p[16];
+  if (a < m) {
+    int k = optr[o] + z;
+    const int k1 = optr[o + 1];
+    for (; k + 7 * GR_Z < k1; k += 8 * GR_Z) {
+      double p[8];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) p[u] = partial[(size_t)oslot[k + u] * m + a];
+      for (int u = 0; u < 8; ++u) p[u] = partial[(size_t)oslot[k + u * GR_Z] * m + a];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) s += p[u];
+      for (int u = 0; u < 8; ++u) s += p[u];
+    }
+    for (; k < k1; k += GR_Z) s += partial[(size_t)oslot[k] * m + a];
   }
-  for (; k < k1; ++k) s += partial[(size_t)oslot[k] * m + a];
-  out[(size_t)a * sa + (size_t)o * so] = scale * s;
+  red[z][x] = s;
+  __syncthreads();
+  if (z == 0 && a < m)
+    out[(size_t)a * sa + (size_t)o * so] = scale * (((red[0][x] + red[1][x]) + red[2][x]) + red[3][x]);
 }
 
 // -Mbar = L L^T by a blocked right-looking Cholesky (block CB = 32), and
@@ -935,6 +943,12 @@ static size_t inv_scratch_doubles(int n) {
 // when a buffer moves or n or the form changes).
 static cudaError_t enqueue_chol_chain(sea_ctx* c) {
   const int n = c->n_orb;
+  if (c->prm.precision == 1) {  // one cooperative launch of block tasks, double-float
+    c->launches += 1;
+    return launch_chol_flow(c->stream, c->device, (const double*)c->Mbuf.p, n,
+                            (double*)c->Lbuf.p, (double*)c->Linv.p, c->flowbuf.p,
+                            (unsigned*)c->status.p, (double*)c->exx_dev.p + SEA_EXX_ACE_SLOT);
+  }
   k_chol_init<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, c->stream>>>(
       (const double*)c->Mbuf.p, n, (double*)c->Lbuf.p);
   double* L = (double*)c->Lbuf.p;
@@ -975,10 +989,12 @@ static cudaError_t launch_chol_chain(sea_ctx* c) {
   const int n = c->n_orb;
   const int nparts = ((n + 31) / 32) * ((n + 1) / 2);
   if (!sea_ensure(c, c->Gbuf, (size_t)nparts * sizeof(double))) return cudaErrorMemoryAllocation;
+  if (c->prm.precision == 1 && !sea_ensure(c, c->flowbuf, chol_flow_bytes(n)))
+    return cudaErrorMemoryAllocation;
   const std::vector<uintptr_t> sig = {
       (uintptr_t)n, (uintptr_t)c->prm.precision, (uintptr_t)c->Mbuf.p, (uintptr_t)c->Lbuf.p,
       (uintptr_t)c->Abuf.p, (uintptr_t)c->Linv.p, (uintptr_t)c->Hbuf2.p, (uintptr_t)c->Gbuf.p,
-      (uintptr_t)c->status.p, (uintptr_t)c->exx_dev.p};
+      (uintptr_t)c->status.p, (uintptr_t)c->exx_dev.p, (uintptr_t)c->flowbuf.p};
   return run_graph(c, c->g_chol, sig, [&]() { return enqueue_chol_chain(c); });
 }
 
@@ -1074,7 +1090,7 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     if (err == cudaSuccess) err = cudaEventRecord(c->xev[0], c->xfer[0]);
     if (err != cudaSuccess) return err;
   }
-  k_gram_reduce<<<(unsigned)(((long long)n * n + 63) / 64), 64, 0, c->stream>>>(
+  k_gram_reduce<<<dim3((n + GR_A - 1) / GR_A, n), GR_A * GR_Z, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
       n, 1);
   c->launches += 2;
@@ -1155,7 +1171,7 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
     if (e != cudaSuccess) return e;
   }
   cudaEventRecord(c->ev[13], c->stream);
-  k_gram_reduce<<<(unsigned)(((long long)n * nv + 63) / 64), 64, 0, c->stream>>>(
+  k_gram_reduce<<<dim3((nv + GR_A - 1) / GR_A, n), GR_A * GR_Z, 0, c->stream>>>(
       (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p,
       1, nv);
   // H = (-Mbar)^-1 G = L^-T (L^-1 G), or Q |Lambda|^-1 Q^T G in the eigen form

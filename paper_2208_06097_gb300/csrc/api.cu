@@ -585,7 +585,7 @@ static sea_status build_ace_common(sea_ctx* c) {
          "status");
   SEA_CK(cudaStreamSynchronize(c->stream), "build_ace");
   if (rb.st & SEA_FLAG_WAIT)
-    return sea_fail(c, SEA_ERR_CUDA, "a tensor-core completion wait timed out (M build)");
+    return sea_fail(c, SEA_ERR_CUDA, "a bounded completion wait timed out (ACE build)");
   const bool not_pd = (rb.st & SEA_FLAG_NOT_PD) != 0;
   if ((not_pd && c->prm.ace_decomp == 0) || c->prm.ace_decomp == 2) {
     tr.stage("eigen-decomposition");
@@ -926,7 +926,7 @@ void sea_destroy(sea_ctx* c) {
                    &c->Q, &c->epair, &c->iters, &c->vbuf, &c->bbuf, &c->rbuf, &c->pbuf,
                    &c->qbuf, &c->eptr, &c->eent, &c->ewin, &c->coff, &c->cbuf, &c->status,
                    &c->exx_dev, &c->queue, &c->tmask, &c->tptr_o, &c->tlist_o, &c->tslot_o,
-                   &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf, &c->wdig, &c->wx, &c->xevb, &c->gbuf,
+                   &c->tptr_t, &c->tlist_t, &c->partial, &c->Mbuf, &c->Abuf, &c->Lbuf, &c->wdig, &c->wx, &c->xevb, &c->gbuf, &c->flowbuf,
                    &c->scdm_u, &c->scdm_c,
                    &c->Linv, &c->Gbuf, &c->Hbuf, &c->Hbuf2, &c->bdesc, &c->bitems,
                    &c->onorm};

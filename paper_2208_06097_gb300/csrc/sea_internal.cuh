@@ -576,6 +576,7 @@ struct sea_ctx {
   SeaBuf wx;    // the mixed form's per-tile W digit images (tensor-core expansion)
   SeaBuf xevb;  // the expansion's H exponents per (tile, vector)
   SeaBuf gbuf;  // ghost (boundary) values of the pair boxes, 36 voff per pair
+  SeaBuf flowbuf;  // the mixed form's one-launch Cholesky chain: DF blocks and task flags
   SeaBuf scdm_u, scdm_c;  // SCDM rotation and pivots
   SeaBuf tmask, tptr_o, tlist_o, tslot_o, tptr_t, tlist_t, partial, Mbuf, Abuf, Lbuf, Linv,
       Gbuf, Hbuf, Hbuf2;
@@ -732,6 +733,11 @@ cudaError_t launch_plan_pairs(sea_ctx* c);
 cudaError_t launch_pair_setup(sea_ctx* c);
 cudaError_t launch_cg(sea_ctx* c);
 cudaError_t launch_contrib_far(sea_ctx* c, cudaEvent_t setup_done);
+// chol_flow.cu: the mixed form's Cholesky of -Mbar, L^-1 and E_xx^ACE in one
+// cooperative launch (scratch of chol_flow_bytes(n) bytes).
+size_t chol_flow_bytes(int n);
+cudaError_t launch_chol_flow(cudaStream_t st, int device, const double* M, int n, double* L,
+                             double* Linv, void* scratch, unsigned* status, double* exx);
 void make_batch_desc(sea_ctx* c, void* out);
 size_t batch_desc_bytes();
 // The persistent batched CG: ctas_per_sm CTAs per SM (0 or above the
