@@ -195,14 +195,14 @@ __device__ void solve_rows(SBlk& R, const SBlk& sL, const DF* rinv) {
   DF x[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) x[q] = sget(R, w + 8 * q, lane);
-#pragma unroll 1
+#pragma unroll 2
   for (int m = 0; m < FB - 1; ++m) {
-    const DF lt = sget(sL, lane, m);
-    const DF nl = df_neg(lt);
+    const DF nl = df_neg(sget(sL, lane, m));
+    const bool upd = lane > m;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const DF am = shfl_df(x[q], m);
-      if (lane > m) x[q] = df_fma(nl, am, x[q]);
+    for (int q = 0; q < 4; ++q) {  // selects, not branches: the four chains stay interleaved
+      const DF y = df_fma(nl, shfl_df(x[q], m), x[q]);
+      x[q] = upd ? y : x[q];
     }
   }
   const DF ri = rinv[lane];
@@ -211,19 +211,18 @@ __device__ void solve_rows(SBlk& R, const SBlk& sL, const DF* rinv) {
   __syncthreads();
 }
 
-// 1 / sqrt(d) for d > 0 in double-float: sqrt(d) from the rounded FP32
-// square root and one correction, its reciprocal from the rounded FP32
-// reciprocal and one Newton step (no division instruction sequence).
+// 1 / sqrt(d) for d > 0 in double-float, on the pivot chain: the FP32
+// reciprocal square root, one Newton step in FP32 (relative error about
+// 2^-23), one in double-float (about 2^-46): r + r (1 - d r^2) / 2 with
+// d r^2 formed from the exact square of r.
 __device__ __forceinline__ DF pivot_rsqrt(DF d) {
-  const float s = __fsqrt_rn(d.hi);
-  const float p = s * s;
-  const float pe = fmaf(s, s, -p);
-  const float dd = ((d.hi - p) - pe) + d.lo;  // d - s^2
-  const float y = __frcp_rn(s);
-  const DF sq = df_fast_two_sum(s, dd * (0.5f * y));
-  const DF t = df_mul_f(y, sq);  // sq y = 1 - e
+  float r = rsqrtf(d.hi);
+  r = r * fmaf(-0.5f * d.hi, r * r, 1.5f);
+  const float q = r * r;
+  const float qe = fmaf(r, r, -q);  // r^2 = q + qe exactly
+  const DF t = df_mul(d, DF{q, qe});
   const float e = (1.0f - t.hi) - t.lo;
-  return df_fast_two_sum(y, y * e);
+  return df_fast_two_sum(r, (0.5f * r) * e);
 }
 
 // Cholesky of the 32 x 32 block in sS by the CTA's 8 warps: warp w holds
