@@ -780,6 +780,37 @@ __global__ void k_small_gemm(const double* __restrict__ A, int transA, const dou
   if (i < n1 && j < n2) C[(size_t)i * n2 + j] = acc;
 }
 
+// The same product in double-float arithmetic for the mixed form (FP64
+// operands split exactly into FP32 pairs to about 2^-47, FP32 pipes instead
+// of the FP64 unit, one rounding to FP64 at the end).
+__global__ void __launch_bounds__(256)
+    k_small_gemm_df(const double* __restrict__ A, int transA, const double* __restrict__ B,
+                    int n1, int n2, double* __restrict__ C, int lower) {
+  __shared__ float Ah[16][17], Al[16][17], Bh[16][17], Bl[16][17];
+  const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+  DF acc{0.f, 0.f};
+  const int kbeg = (lower && transA) ? blockIdx.y * 16 : 0;
+  const int kend = (lower && !transA) ? min(n1, (int)(blockIdx.y + 1) * 16) : n1;
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    const int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+    double av = 0.0;
+    if (i < n1 && ka < n1) av = transA ? A[(size_t)ka * n1 + i] : A[(size_t)i * n1 + ka];
+    const double bv = (kb < n1 && j < n2) ? B[(size_t)kb * n2 + j] : 0.0;
+    const float2 as = split64(av), bs = split64(bv);
+    Ah[threadIdx.y][threadIdx.x] = as.x;
+    Al[threadIdx.y][threadIdx.x] = as.y;
+    Bh[threadIdx.y][threadIdx.x] = bs.x;
+    Bl[threadIdx.y][threadIdx.x] = bs.y;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      acc = df_fma(DF{Ah[threadIdx.y][k], Al[threadIdx.y][k]}, DF{Bh[k][threadIdx.x], Bl[k][threadIdx.x]},
+                   acc);
+    __syncthreads();
+  }
+  if (i < n1 && j < n2) C[(size_t)i * n2 + j] = df_to_double(acc);
+}
+
 // out[v][r] = sign * sum_{j in tile list} W[j][r] H(j, v), H(j, v) =
 // H[j * hj + v * hv], for every point r of the tile and v in a chunk of 32:
 // thread = (point, half of the chunk), 16 accumulators.
@@ -1176,18 +1207,20 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
       1, nv);
   // H = (-Mbar)^-1 G = L^-T (L^-1 G), or Q |Lambda|^-1 Q^T G in the eigen form
   dim3 gb((nv + 15) / 16, (n + 15) / 16), tb(16, 16);
+  // the mixed form's products in double-float (the FP64 unit is the bound of the FP64 ones)
+  auto small_gemm = c->prm.precision == 1 ? k_small_gemm_df : k_small_gemm;
   if (c->ace_eigen) {
-    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Gbuf.p,
+    small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Gbuf.p,
                                            n, nv, (double*)c->Hbuf2.p, 0);
     k_scale_rows<<<(unsigned)(((size_t)n * nv + 255) / 256), 256, 0, c->stream>>>(
         (double*)c->Hbuf2.p, (const double*)c->Abuf.p, n, nv);
-    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Hbuf2.p,
+    small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Hbuf2.p,
                                            n, nv, (double*)c->Hbuf.p, 0);
     c->launches += 1;
   } else {
-    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Gbuf.p,
+    small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 0, (const double*)c->Gbuf.p,
                                            n, nv, (double*)c->Hbuf2.p, 1);
-    k_small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Hbuf2.p,
+    small_gemm<<<gb, tb, 0, c->stream>>>((const double*)c->Linv.p, 1, (const double*)c->Hbuf2.p,
                                            n, nv, (double*)c->Hbuf.p, 1);
   }
   // out[v] = -sum_j W_j H[j][v]

@@ -226,39 +226,55 @@ __device__ __forceinline__ DF pivot_rsqrt(DF d) {
 }
 
 // Cholesky of the 32 x 32 block in sS by the CTA's 8 warps: warp w holds
-// columns w, w + 8, w + 16, w + 24 (lane = row).  Step k: the owner of
-// column k (complete) takes the pivot and writes L(:, k) to sL; after a
-// barrier every column c > k subtracts L(:, k) L(c, k).  1 / L(k, k) goes
-// to rinv.  Returns false on a non-positive pivot (that column is then 0).
+// the columns 4w .. 4w + 3 (lane = row).  In turn, warp b takes the pivots
+// of its four columns (each column then updates the warp's later columns
+// through shuffles, with no barrier), writes them to sL and, after a
+// barrier, every later warp subtracts their rank-4 product from its columns.
+// The pivot chain thus leaves the warp once per four columns.  1 / L(k, k)
+// goes to rinv.  Returns false on a non-positive pivot (its column is then 0).
 __device__ bool factor_block(const SBlk& sS, SBlk& sL, DF* rinv) {
   __shared__ int bad;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DF a[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) a[q] = sget(sS, lane, w + 8 * q);
+  for (int q = 0; q < 4; ++q) a[q] = sget(sS, lane, 4 * w + q);
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
 #pragma unroll 1
-  for (int k = 0; k < FB; ++k) {
-    if (w == (k & 7)) {
-      const int qk = k >> 3;
-      const DF ak = qk == 0 ? a[0] : (qk == 1 ? a[1] : (qk == 2 ? a[2] : a[3]));
-      const DF d = shfl_df(ak, k);
-      const bool pos = d.hi > 0.f;
-      const DF r = pos ? pivot_rsqrt(d) : DF{0.f, 0.f};
-      const DF l = (lane == k) ? df_mul(d, r) : (lane > k ? df_mul(ak, r) : DF{0.f, 0.f});
-      sput(sL, lane, k, l);
-      if (lane == k) {
-        rinv[k] = r;
-        if (!pos) bad = 1;
+  for (int b = 0; b < FB / 4; ++b) {
+    if (w == b) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * b + q;
+        const DF d = shfl_df(a[q], k);
+        const bool pos = d.hi > 0.f;
+        const DF r = pivot_rsqrt(pos ? d : DF{1.f, 0.f});
+        const DF rr = pos ? r : DF{0.f, 0.f};
+        const DF l = df_mul(lane == k ? d : a[q], rr);
+        a[q] = lane >= k ? l : DF{0.f, 0.f};
+        if (lane == k) {
+          rinv[k] = rr;
+          if (!pos) bad = 1;
+        }
+        const DF nl = df_neg(a[q]);
+#pragma unroll
+        for (int q2 = q + 1; q2 < 4; ++q2) a[q2] = df_fma(nl, shfl_df(a[q], 4 * b + q2), a[q2]);
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sput(sL, lane, 4 * b + q, a[q]);
     }
     __syncthreads();
-    const DF nlik = df_neg(sget(sL, lane, k));
+    if (w > b) {
+      DF li[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = w + 8 * q;
-      if (c > k) a[q] = df_fma(nlik, sget(sL, c, k), a[q]);
+      for (int q = 0; q < 4; ++q) li[q] = df_neg(sget(sL, lane, 4 * b + q));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = 4 * w + q;
+        const DF t = df_dot2(li[0], sget(sL, c, 4 * b), li[1], sget(sL, c, 4 * b + 1));
+        const DF u = df_dot2(li[2], sget(sL, c, 4 * b + 2), li[3], sget(sL, c, 4 * b + 3));
+        a[q] = df_add(a[q], df_add(t, u));
+      }
     }
   }
   __syncthreads();
