@@ -1029,23 +1029,25 @@ static cudaError_t launch_chol_chain(sea_ctx* c) {
   return run_graph(c, c->g_chol, sig, [&]() { return enqueue_chol_chain(c); });
 }
 
-// Tile lists of W's support, M, Cholesky and L^-1.  Needs the incidence
-// count on the host to size the partial sums: one stream sync.
-cudaError_t launch_ace_build(sea_ctx* c) {
+// The tile-major and orbital-major lists of W's support on stream st: the
+// (orbital, tile) incidences, per-tile counts and their scan, the lists.
+// The list arrays are sized for every (orbital, tile) pair (list_cap), so no
+// count has to reach the host before the lists are formed; the incidence
+// count and the longest tile list land in counts[10] and counts[12].
+cudaError_t launch_ace_lists(sea_ctx* c, cudaStream_t st) {
   const int n = c->n_orb;
   const TileGeom G = make_tile_geom(c->N);
   const int nt = G.ntx * G.nty * G.ntz;
-  c->n_tiles = nt;
   const long long ninc = (long long)n * nt;
+  const long long cap = std::max(ninc, 1LL);
   if (!sea_ensure(c, c->tmask, ninc * sizeof(int) * 3) ||
       !sea_ensure(c, c->tptr_t, (size_t)(nt + 1) * sizeof(int) * 2) ||
       !sea_ensure(c, c->tptr_o, (size_t)(n + 1) * sizeof(int) * 2) ||
-      !sea_ensure(c, c->Mbuf, (size_t)n * n * sizeof(double)) ||
-      !sea_ensure(c, c->Lbuf, (size_t)n * n * sizeof(double)) ||
-      !sea_ensure(c, c->Linv, (size_t)n * n * sizeof(double)) ||
-      !sea_ensure(c, c->Abuf, (size_t)((n + CB - 1) / CB) * CB * CB * sizeof(double)) ||
-      !sea_ensure(c, c->Hbuf2, inv_scratch_doubles(n) * sizeof(double)))
+      !sea_ensure(c, c->tlist_t, (size_t)cap * sizeof(int) * 2) ||
+      !sea_ensure(c, c->tlist_o, (size_t)cap * sizeof(int) * 2))
     return cudaErrorMemoryAllocation;
+  c->n_tiles = nt;
+  c->list_cap = cap;
   int* inc = (int*)c->tmask.p;
   int* gidx = inc + ninc;
   int* sub = inc + 2 * ninc;
@@ -1054,19 +1056,50 @@ cudaError_t launch_ace_build(sea_ctx* c) {
   int* ocnt = (int*)c->tptr_o.p;
   int* optr = ocnt + (n + 1);
   int* counts = (int*)c->counts.p;
-  k_tile_incidence<<<(unsigned)((ninc + 255) / 256), 256, 0, c->stream>>>(
+  int* tlist = (int*)c->tlist_t.p;
+  int* tsub = tlist + cap;
+  int* olist = (int*)c->tlist_o.p;
+  int* oslot = olist + cap;
+  k_tile_incidence<<<(unsigned)((ninc + 255) / 256), 256, 0, st>>>(
       (const Entry*)c->ewin.p, (const int*)c->eptr.p, n, G, nt, c->w_dense ? 1 : 0, inc, sub);
-  k_tile_lists<<<(nt + 7) / 8, 256, 0, c->stream>>>(inc, sub, n, nt, 0, tcnt, nullptr, nullptr,
-                                                    nullptr, nullptr);
-  k_scan_small<<<1, 1024, 0, c->stream>>>(tcnt, nt, tptr, counts + 10);
-  k_max_int<<<1, 1024, 0, c->stream>>>(tcnt, nt, counts + 12);
-  int hc[3] = {0, 0, 0};
-  cudaMemcpyAsync(hc, counts + 10, sizeof(hc), cudaMemcpyDeviceToHost, c->stream);
-  cudaError_t err = cudaStreamSynchronize(c->stream);
-  if (err != cudaSuccess) return err;
-  const int hinc = hc[0];
-  c->tile_inc = hinc;
-  c->max_tile_list = hc[2];
+  k_tile_lists<<<(nt + 7) / 8, 256, 0, st>>>(inc, sub, n, nt, 0, tcnt, nullptr, nullptr, nullptr,
+                                             nullptr);
+  k_scan_small<<<1, 1024, 0, st>>>(tcnt, nt, tptr, counts + 10);
+  k_max_int<<<1, 1024, 0, st>>>(tcnt, nt, counts + 12);
+  k_tile_lists<<<(nt + 7) / 8, 256, 0, st>>>(inc, sub, n, nt, 1, nullptr, tptr, tlist, tsub, gidx);
+  k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, st>>>(gidx, n, nt, 0, ocnt, nullptr, nullptr,
+                                                    nullptr);
+  k_scan_small<<<1, 1024, 0, st>>>(ocnt, n, optr, counts + 11);
+  k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, st>>>(gidx, n, nt, 1, nullptr, optr, olist, oslot);
+  c->launches += 8;
+  return cudaGetLastError();
+}
+
+// M, Cholesky and L^-1 (and the tile lists first, unless sea_apply_vxx
+// formed them with its plan: then their counts are already on the host).
+cudaError_t launch_ace_build(sea_ctx* c) {
+  const int n = c->n_orb;
+  const TileGeom G = make_tile_geom(c->N);
+  if (!sea_ensure(c, c->Mbuf, (size_t)n * n * sizeof(double)) ||
+      !sea_ensure(c, c->Lbuf, (size_t)n * n * sizeof(double)) ||
+      !sea_ensure(c, c->Linv, (size_t)n * n * sizeof(double)) ||
+      !sea_ensure(c, c->Abuf, (size_t)((n + CB - 1) / CB) * CB * CB * sizeof(double)) ||
+      !sea_ensure(c, c->Hbuf2, inv_scratch_doubles(n) * sizeof(double)))
+    return cudaErrorMemoryAllocation;
+  cudaError_t err = cudaSuccess;
+  if (c->w_dense || !c->lists_ready) {
+    c->lists_ready = false;
+    err = launch_ace_lists(c, c->stream);
+    if (err != cudaSuccess) return err;
+    int hc[3] = {0, 0, 0};
+    cudaMemcpyAsync(hc, (int*)c->counts.p + 10, sizeof(hc), cudaMemcpyDeviceToHost, c->stream);
+    err = cudaStreamSynchronize(c->stream);
+    if (err != cudaSuccess) return err;
+    c->tile_inc = hc[0];
+    c->max_tile_list = hc[2];
+  }
+  const int nt = c->n_tiles;
+  const int hinc = c->tile_inc;
   {
     const size_t smem = (size_t)c->max_tile_list * EV * sizeof(double);
     if (smem > 48 * 1024) {
@@ -1078,22 +1111,13 @@ cudaError_t launch_ace_build(sea_ctx* c) {
       if (err != cudaSuccess) return err;
     }
   }
-  // tlist_t holds the tile-major orbital list and, after it, the sub-boxes
-  if (!sea_ensure(c, c->tlist_t, (size_t)max(hinc, 1) * sizeof(int) * 2) ||
-      !sea_ensure(c, c->tlist_o, (size_t)max(hinc, 1) * sizeof(int) * 2) ||
-      !sea_ensure(c, c->partial, (size_t)max(hinc, 1) * n * sizeof(double)))
+  if (!sea_ensure(c, c->partial, (size_t)max(hinc, 1) * n * sizeof(double)))
     return cudaErrorMemoryAllocation;
-  int* tlist = (int*)c->tlist_t.p;
-  int* tsub = tlist + max(hinc, 1);
-  int* olist = (int*)c->tlist_o.p;
-  int* oslot = olist + max(hinc, 1);
-  k_tile_lists<<<(nt + 7) / 8, 256, 0, c->stream>>>(inc, sub, n, nt, 1, nullptr, tptr, tlist,
-                                                    tsub, gidx);
-  k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 0, ocnt, nullptr,
-                                                           nullptr, nullptr);
-  k_scan_small<<<1, 1024, 0, c->stream>>>(ocnt, n, optr, counts + 11);
-  k_orb_lists<<<(n * 32 + 127) / 128, 128, 0, c->stream>>>(gidx, n, nt, 1, nullptr, optr, olist,
-                                                           oslot);
+  const int* tptr = (const int*)c->tptr_t.p + (nt + 1);
+  const int* optr = (const int*)c->tptr_o.p + (n + 1);
+  const int* tlist = (const int*)c->tlist_t.p;
+  const int* tsub = tlist + c->list_cap;
+  const int* oslot = (const int*)c->tlist_o.p + c->list_cap;
   // M = Phi^T W dV
   err = cudaFuncSetAttribute(k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)GRAM_SMEM);
@@ -1191,10 +1215,10 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
     return cudaErrorMemoryAllocation;
   const int* tptr = (const int*)c->tptr_t.p + (nt + 1);
   const int* tlist = (const int*)c->tlist_t.p;
-  const int* tsub = tlist + max(hinc, 1);
+  const int* tsub = tlist + c->list_cap;
   const int* optr = (const int*)c->tptr_o.p + (n + 1);
   const int* olist = (const int*)c->tlist_o.p;
-  const int* oslot = olist + max(hinc, 1);
+  const int* oslot = olist + c->list_cap;
   // G[o][v] = <W_o|psi_v> dV
   cudaEventRecord(c->ev[12], c->stream);
   {
@@ -1239,7 +1263,7 @@ cudaError_t launch_ace_vectors(sea_ctx* c, double* xi) {
   const int nt = c->n_tiles;
   const int* tptr = (const int*)c->tptr_t.p + (nt + 1);
   const int* tlist = (const int*)c->tlist_t.p;
-  const int* tsub = tlist + max(c->tile_inc, 1);
+  const int* tsub = tlist + c->list_cap;
   // Xi[k][r] = sum_j W[j][r] (L^-1)[k][j]:  H(j, k) = Linv[k * n + j]
   cudaError_t ex = launch_expand(c, G, tptr, tlist, tsub, (const double*)c->Linv.p, 1, n, n, 1.0, xi);
   if (ex != cudaSuccess) return ex;

@@ -473,6 +473,7 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_ALLOC(Q, (size_t)std::max(c->P, 1) * SEA_QSTRIDE * sizeof(double));
   SEA_ALLOC(epair, (size_t)std::max(c->P, 1) * sizeof(double));
   SEA_ALLOC(iters, (size_t)std::max(c->P, 1) * sizeof(int));
+  c->lists_ready = false;
   tr.stage("pair setup");
   SEA_CK(sea::launch_pair_setup(c), "pair setup");
   c->cg_warm = false;
@@ -487,6 +488,15 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   SEA_CK(cudaEventRecord(c->ev[2], c->stream), "event");
   tr.stage("cg");
   SEA_CK(sea::launch_cg(c), "cg");
+  // W's tile lists for the ACE build follow from the plan alone: formed on
+  // the second side stream, on the SMs that the CG's last pairs leave idle
+  // (their counts come back with this call's results)
+  {
+    const cudaError_t e = sea::launch_ace_lists(c, c->xfer[1]);
+    if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE tile lists");
+    SEA_CK(e, "ACE tile lists");
+    SEA_CK(cudaEventRecord(c->xev[2], c->xfer[1]), "event");
+  }
   SEA_CK(sea::launch_contrib_far(c, c->ev[2]), "far field");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
   tr.stage("far field and accumulation");
@@ -522,12 +532,20 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
   struct {
     double res[5];
     unsigned st;
+    int lists[3];
   } r;
+  SEA_CK(cudaStreamWaitEvent(c->stream, c->xev[2], 0), "wait");
   SEA_CK(cudaMemcpyAsync(r.res, c->exx_dev.p, sizeof(r.res), cudaMemcpyDeviceToHost, c->stream),
          "exx");
   SEA_CK(cudaMemcpyAsync(&r.st, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
          "status");
+  SEA_CK(cudaMemcpyAsync(r.lists, (int*)c->counts.p + 10, sizeof(r.lists), cudaMemcpyDeviceToHost,
+                         c->stream),
+         "list counts");
   SEA_CK(cudaStreamSynchronize(c->stream), "apply_vxx");
+  c->tile_inc = r.lists[0];
+  c->max_tile_list = r.lists[2];
+  c->lists_ready = true;
   float t01 = 0, t12 = 0, t23 = 0, t34 = 0;
   cudaEventElapsedTime(&t01, c->ev[0], c->ev[1]);
   cudaEventElapsedTime(&t12, c->ev[1], c->ev[2]);

@@ -412,6 +412,7 @@ extern "C" sea_status sea_apply_vxx_batch(sea_ctx* const* ctxs, int n, double* c
     if (exx) exx[k] = r[k].res[0];
     c->w_dense = false;
     c->have_vxx = true;
+    c->lists_ready = false;  // the batch forms no ACE tile lists
     if (r[k].st & SEA_FLAG_CG_CAP) {
       sea_fail(c, SEA_ERR_CG_NOT_CONVERGED, "a pair's CG reached cg_max_iter");
       rs = SEA_ERR_CG_NOT_CONVERGED;

@@ -581,6 +581,9 @@ struct sea_ctx {
   SeaBuf tmask, tptr_o, tlist_o, tslot_o, tptr_t, tlist_t, partial, Mbuf, Abuf, Lbuf, Linv,
       Gbuf, Hbuf, Hbuf2;
   int n_tiles = 0, tile_inc = 0, max_tile_list = 0;
+  long long list_cap = 1;    // entries per list array (the second array's offset)
+  bool lists_ready = false;  // the tile lists of the last plan's W support are formed
+                             // and their counts on the host
 
   long long launches = 0;
   cudaEvent_t ev[16] = {};
@@ -780,6 +783,7 @@ int expand_tc_max_list();
 cudaError_t launch_gram_tc(cudaStream_t st, int device, const double* A, int m, const TileGeom& G,
                            size_t ng, int n_tiles, const int* tptr, long long slots,
                            const void* wbuf, double* partial, int* queue, unsigned* status);
+cudaError_t launch_ace_lists(sea_ctx* c, cudaStream_t st);
 cudaError_t launch_ace_build(sea_ctx* c);
 cudaError_t launch_ace_eigen(sea_ctx* c);
 cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int n_vec, double* out);

@@ -75,12 +75,14 @@ def test_cg_cap_reported_results_written(small):
         assert np.all(plan["iters"] == -2)
 
 
-def test_zero_orbital_makes_mbar_singular(small):
-    # Cholesky only (ace_decomp = 1): the zero pivot is reported
+@pytest.mark.parametrize("precision", [0, 1])
+def test_zero_orbital_makes_mbar_singular(small, precision):
+    # Cholesky only (ace_decomp = 1): the zero pivot is reported, by the
+    # FP64 kernel chain and by the mixed form's one-launch block tasks
     from paper_2208_06097_gb300 import sea
     phi = np.ascontiguousarray(small.phi.copy())
     phi[0] = 0.0
-    with _ctx(small, ace_decomp=1, orth_tol=0.0) as ctx:  # a zero orbital has norm 0
+    with _ctx(small, ace_decomp=1, orth_tol=0.0, precision=precision) as ctx:  # norm 0
         ctx.set_orbitals(phi)
         out = np.empty_like(phi)
         ctx.apply_vxx(out)

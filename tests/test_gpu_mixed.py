@@ -116,6 +116,14 @@ def test_mixed_ace_odd_grid():
     _mixed_ace_vs_oracle(s)
 
 
+def test_mixed_ace_partial_blocks():
+    # 40 orbitals: two 32 x 32 block columns in the Cholesky block tasks, the
+    # second padded (8 rows of M, the identity beyond them in -Mbar)
+    s = synth.make_waters(10, 8.5, 36, seed=77)
+    assert s.n_orb == 40
+    _mixed_ace_vs_oracle(s)
+
+
 def test_mixed_ace_long_tile_lists():
     # a coarse grid puts more than 32 W rows on some tiles: those tiles are
     # expanded by the FP32 kernel, the others on the tensor cores
