@@ -112,11 +112,13 @@ __device__ void wait_task(const FlowArgs& A, int t) {
   __syncthreads();
 }
 
-// Every thread's stores are made visible, then the flag of task t is set.
+// After a barrier (the CTA's stores precede it), thread 0 fences and sets
+// the flag of task t with a release store; a reader's acquire load of the
+// flag followed by its own barrier then orders its CTA's reads after them.
 __device__ void publish(const FlowArgs& A, int t) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     int* f = A.flag + t;
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(1) : "memory");
   }
@@ -342,8 +344,8 @@ __global__ void __launch_bounds__(FT) k_chol_flow(FlowArgs A) {
       if (!factor_block(sR, sL, rinv) && threadIdx.x == 0) atomicOr(A.status, SEA_FLAG_NOT_PD);
       store_df(A.Lb + ((size_t)s * nb + s) * FB * FB, sL, false);
       if (threadIdx.x < FB) A.Rb[s * FB + threadIdx.x] = make_float2(rinv[threadIdx.x].hi, rinv[threadIdx.x].lo);
+      publish(A, t);  // the FP64 outputs after the hand-over: only the caller reads them
       store_f64(A, A.L, s, s, &sL, true);
-      publish(A, t);
     } else if (r == 1) {
       // Y_s: L_ss Y = I, by rows of Y^T
       wait_task(A, T.D(s));
@@ -352,12 +354,12 @@ __global__ void __launch_bounds__(FT) k_chol_flow(FlowArgs A) {
       __syncthreads();
       solve_rows(sR, sL, rinv);  // sR = Y^T
       store_df(A.Xb + ((size_t)s * nb + s) * FB * FB, sR, true);
+      publish(A, t);
       for (int e = threadIdx.x; e < FB * FB; e += FT) {
         const int rr = e >> 5, c = e & 31;
         const int I = s * FB + rr, J = s * FB + c;
         if (I < A.n && J < A.n) A.Linv[(size_t)I * A.n + J] = c <= rr ? df_to_double(sget(sR, c, rr)) : 0.0;
       }
-      publish(A, t);
     } else if (r <= nb - s) {
       // P_is
       const int i = s + r - 1;
@@ -377,9 +379,9 @@ __global__ void __launch_bounds__(FT) k_chol_flow(FlowArgs A) {
       __syncthreads();
       solve_rows(sR, sL, rinv);  // rows of L_is
       store_df(A.Lb + ((size_t)i * nb + s) * FB * FB, sR, false);
+      publish(A, t);
       store_f64(A, A.L, i, s, &sR, false);
       store_f64(A, A.L, s, i, nullptr, false);
-      publish(A, t);
     } else if (r <= nb) {
       // X_sj
       const int j = r - (nb - s + 1);
@@ -398,6 +400,7 @@ __global__ void __launch_bounds__(FT) k_chol_flow(FlowArgs A) {
       __syncthreads();
       solve_rows(sR, sL, rinv);  // X_sj^T
       store_df(A.Xb + ((size_t)s * nb + j) * FB * FB, sR, true);
+      publish(A, t);
       for (int e = threadIdx.x; e < FB * FB; e += FT) {
         const int rr = e >> 5, c = e & 31;
         const int I = s * FB + rr, J = j * FB + c;
@@ -406,7 +409,6 @@ __global__ void __launch_bounds__(FT) k_chol_flow(FlowArgs A) {
           A.Linv[(size_t)J * A.n + I] = 0.0;
         }
       }
-      publish(A, t);
     } else {
       // Z_sq and E_sq
       const int q = r - nb - 1;
