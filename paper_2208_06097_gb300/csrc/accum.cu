@@ -271,7 +271,12 @@ __global__ void __launch_bounds__(SEA_ACC_THREADS)
   const int z = blockIdx.y;
   const int plane = nx * ny;
   unsigned char* tmask = reinterpret_cast<unsigned char*>(sp + plane);
-  for (int g = threadIdx.x; g < plane; g += blockDim.x) sp[g] = 0.0;
+  if ((plane & 1) == 0) {
+    double2* sp2 = reinterpret_cast<double2*>(sp);
+    for (int g = threadIdx.x; g < plane / 2; g += blockDim.x) sp2[g] = make_double2(0.0, 0.0);
+  } else {
+    for (int g = threadIdx.x; g < plane; g += blockDim.x) sp[g] = 0.0;
+  }
   const int e0 = eptr[o], e1 = eptr[o + 1];
   for (int k = e0; k < e1; ++k) {
     const Entry e = ent[k];
@@ -339,7 +344,27 @@ __global__ void __launch_bounds__(SEA_ACC_THREADS)
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   }
-  if (!(by_copy && out2 == nullptr)) {  // else the copy stored everything
+  const int nty = (ny + TY - 1) / TY;
+  if (by_copy && out2 != nullptr && !all) {
+    // the context's copy on the marked tiles only: a thread per tile, its
+    // rows as 16-byte pieces when rows and outputs allow it
+    const bool v2 = (nx & 1) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    for (int q = threadIdx.x; q < ntx * nty; q += blockDim.x) {
+      if (!tmask[q]) continue;
+      const int qy = q / ntx, qx = q - qy * ntx;
+      const int x0 = qx * TX, x1 = min(nx, x0 + TX), y1 = min(ny, qy * TY + TY);
+      for (int y = qy * TY; y < y1; ++y) {
+        const int g0 = y * nx;
+        if (v2) {
+          for (int x = x0; x < x1; x += 2)
+            *reinterpret_cast<double2*>(out + base + g0 + x) =
+                *reinterpret_cast<const double2*>(sp + g0 + x);
+        } else {
+          for (int x = x0; x < x1; ++x) out[base + g0 + x] = sp[g0 + x];
+        }
+      }
+    }
+  } else if (!(by_copy && out2 == nullptr)) {  // else the copy stored everything
     const int dy = blockDim.x / nx, dx = blockDim.x - dy * nx;  // (x, y) of g, without divisions
     int y = threadIdx.x / nx, x = threadIdx.x - y * nx;
     for (int g = threadIdx.x; g < plane; g += blockDim.x) {

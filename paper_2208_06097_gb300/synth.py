@@ -256,6 +256,10 @@ CONFIGS = {
     # profiling case with the benchmark's orbital count, small enough for
     # multi-pass kernel captures, its orbital array still larger than L2.
     "h2o64_48": dict(n_mol=64, L=12.42, grid=48, seed=1001),
+    # 16 waters in the benchmark's cell and grid (0.25 g/cm^3): the same grid
+    # spacing, box sizes and 96 x 96 planes with 64 orbitals, for multi-pass
+    # captures of the kernels whose shape follows the grid (outputs 0.45 GB).
+    "h2o16_96": dict(n_mol=16, L=12.42, grid=96, seed=1003),
 }
 
 
