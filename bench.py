@@ -370,7 +370,8 @@ def run_ours(args, ws, rank, local):
         "dtype": "f64" if chosen == "plain" else "f64+f32",
         "data": "synthetic (seeded water-like localized orbitals, see synth.py)",
         "config": {
-            "workload": WORKLOAD,
+            "workload": WORKLOAD if args.config == CONFIG else
+                        f"{args.config} (profiling case: {s.n_orb} orbitals, {s.grid} grid)",
             "form": FORMS[chosen],
             "forms_applications_per_s": {f: ws * K / (form_ms[f] / 1e3) for f in forms},
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",

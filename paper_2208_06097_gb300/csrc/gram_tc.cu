@@ -217,8 +217,9 @@ __device__ __forceinline__ int float_int(float f) {
 // wdig[((s * 2 + h) * DIG + k) * 8 + u] = the 8 BF16 digits (16 bytes) of
 // plane k, x-run u of W row list[s] on that half tile, and wexp[2 s + h]
 // the row segment's largest biased exponent.  Warp per (tile, half, group
-// of 8 slots).
-__global__ void __launch_bounds__(256)
+// of 8 slots).  Four CTAs per SM: the warps wait on their row loads, so
+// occupancy is what hides the latency.
+__global__ void __launch_bounds__(256, 4)
     k_w_digits(const double* __restrict__ W, TileGeom G, size_t ng, int n_tiles, int ngroups,
                const int* __restrict__ tptr, const int* __restrict__ tlist, uint4* __restrict__ wdig,
                int* __restrict__ wexp) {
