@@ -376,6 +376,33 @@ __device__ __forceinline__ double neg_lap(const double* __restrict__ pv, int t, 
   return (ax + ay) + az;
 }
 
+// The same operator in double-float on a double-float vector (the mixed
+// form's true residual, when the requested tolerance lies well above its
+// rounding floor): the FP32 pipes instead of the FP64 unit.
+struct StencilOpDF {
+  DF ax[3][SEA_FDP + 1];
+  DF center;
+};
+__device__ __forceinline__ DF lap_axis_df(const float2* __restrict__ pv, int t, int u, int e, int st,
+                                          const DF* __restrict__ w) {
+  DF a{0.f, 0.f};
+#pragma unroll
+  for (int k = 1; k <= SEA_FDP; ++k) {
+    const float2 L = (u - k >= 0) ? pv[t - k * st] : make_float2(0.f, 0.f);
+    const float2 R = (u + k < e) ? pv[t + k * st] : make_float2(0.f, 0.f);
+    a = df_fma(w[k], df_add(DF{L.x, L.y}, DF{R.x, R.y}), a);
+  }
+  return a;
+}
+__device__ __forceinline__ DF neg_lap_df(const float2* __restrict__ pv, int t, int x, int y, int z,
+                                         int ex, int ey, int ez, const StencilOpDF& W) {
+  const DF ax = lap_axis_df(pv, t, x, ex, 1, W.ax[0]);
+  const DF ay = lap_axis_df(pv, t, y, ey, ex, W.ax[1]);
+  const float2 c = pv[t];
+  const DF az = df_fma(W.center, DF{c.x, c.y}, lap_axis_df(pv, t, z, ez, ex * ey, W.ax[2]));
+  return df_add(df_add(ax, ay), az);
+}
+
 // Walks the points t = t0, t0 + S, t0 + 2S, ... of an ex x ey x ez box in
 // [z][y][x] order with their coordinates, without divisions in the loop.
 struct BoxWalk {
@@ -577,6 +604,9 @@ __global__ void __launch_bounds__(256, 3) k_cg(CgArgs A, StencilW W) {
 // CTA size of the mixed CG (one pair per CTA at a time)
 #define SEA_CG_THREADS 512
 #define SEA_MIXED_MAX_OUTER 30
+// smallest relative tolerance for which the true residual is formed in
+// double-float (below it, in FP64)
+#define SEA_DF_RESIDUAL_TOL 1e-10
 
 struct StencilWf {
   float ax[3][SEA_FDP + 1];
@@ -728,6 +758,7 @@ __device__ __forceinline__ float2 block_sum2_f(float a, float b, float2* slots) 
 // (r, r) <= SEA_MIXED_INNER^2 (r0, r0).  For pairs whose padded box fits the
 // shared buffer.  Ends with x += rnorm d (FP64).  Returns the new total of
 // inner iterations (stencil products followed by an update).
+template <bool DRES>
 __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, double rnorm,
                                              double* __restrict__ x, float* __restrict__ d,
                                              float* __restrict__ pf, float* __restrict__ sf,
@@ -742,10 +773,16 @@ __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, doubl
   for (int t = threadIdx.x; t < Vp; t += S) rS[t] = 0.f;
   __syncthreads();
   const double inv = 1.0 / rnorm;
+  const float invf = (float)inv;
   {
     BoxWalk w(threadIdx.x, S, ex, ey);
     for (; w.t < n; w.next(S)) {
-      rS[org + w.t + w.z * gap] = (float)(r[w.t] * inv);
+      if (DRES) {
+        const float2 rv = reinterpret_cast<const float2*>(r)[w.t];
+        rS[org + w.t + w.z * gap] = fmaf(rv.x, invf, rv.y * invf);
+      } else {
+        rS[org + w.t + w.z * gap] = (float)(r[w.t] * inv);
+      }
       pf[w.t] = 0.f;
       sf[w.t] = 0.f;
       d[w.t] = 0.f;
@@ -791,7 +828,17 @@ __device__ __forceinline__ int inner_cg_smem(const double* __restrict__ r, doubl
     ++inner_total;
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+  if (DRES) {
+    float2* xd = reinterpret_cast<float2*>(x);
+    const DF rn = df_from_double(rnorm);
+    for (int t = threadIdx.x; t < n; t += S) {
+      const float2 xv = xd[t];
+      const DF y = df_add(df_mul_f(d[t], rn), DF{xv.x, xv.y});
+      xd[t] = make_float2(y.hi, y.lo);
+    }
+  } else {
+    for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+  }
   __syncthreads();  // rS is free for the next pair
   return inner_total;
 }
@@ -853,18 +900,50 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
   float* pf = A.pf + off;
   float* qf = A.qf + off;
 
+  // The true residual in double-float (x and r held as FP32 pairs in their
+  // FP64 arrays until the end) when the tolerance is at least
+  // SEA_DF_RESIDUAL_TOL: its rounding floor, about 2^-47 of the stencil's
+  // largest terms (a few 10^-12 of ||b||), then stays far below the target.
+  const bool dres = A.tol_mode == 0 && A.tol >= SEA_DF_RESIDUAL_TOL;
+  __shared__ StencilOpDF Wo;
+  float2* xd = reinterpret_cast<float2*>(x);
+  float2* rd = reinterpret_cast<float2*>(r);
   double bb = 0.0, rr0 = 0.0;
-  for (int t = threadIdx.x; t < n; t += S) {
-    const double bt = b[t];
-    double rt = bt;
-    if (A.warm)  // r = b - A x0
-      rt = bt - neg_lap(x, t, t % ex, (t / ex) % ey, t / (ex * ey), ex, ey, ez, W);
-    r[t] = rt;
-    bb = fma(bt, bt, bb);
-    rr0 = fma(rt, rt, rr0);
+  if (dres) {
+    if (threadIdx.x < 3 * (SEA_FDP + 1))
+      Wo.ax[threadIdx.x / (SEA_FDP + 1)][threadIdx.x % (SEA_FDP + 1)] =
+          df_from_double(W.ax[threadIdx.x / (SEA_FDP + 1)][threadIdx.x % (SEA_FDP + 1)]);
+    if (threadIdx.x == 3 * (SEA_FDP + 1)) Wo.center = df_from_double(W.center);
+    for (int t = threadIdx.x; t < n; t += S) {
+      const float2 xv = A.warm ? split64(x[t]) : make_float2(0.f, 0.f);
+      xd[t] = xv;
+    }
+    __syncthreads();
+    float rr0f = 0.f;
+    BoxWalk w(threadIdx.x, S, ex, ey);
+    for (; w.t < n; w.next(S)) {
+      const double bt = b[w.t];
+      const float2 bs = split64(bt);
+      DF rt{bs.x, bs.y};
+      if (A.warm) rt = df_add(rt, df_neg(neg_lap_df(xd, w.t, w.x, w.y, w.z, ex, ey, ez, Wo)));
+      rd[w.t] = make_float2(rt.hi, rt.lo);
+      bb = fma(bt, bt, bb);
+      rr0f = fmaf(rt.hi, rt.hi, rr0f);
+    }
+    rr0 = (double)rr0f;
+  } else {
+    for (int t = threadIdx.x; t < n; t += S) {
+      const double bt = b[t];
+      double rt = bt;
+      if (A.warm)  // r = b - A x0
+        rt = bt - neg_lap(x, t, t % ex, (t / ex) % ey, t / (ex * ey), ex, ey, ez, W);
+      r[t] = rt;
+      bb = fma(bt, bt, bb);
+      rr0 = fma(rt, rt, rr0);
+    }
+    if (!A.warm)
+      for (int t = threadIdx.x; t < n; t += S) x[t] = 0.0;
   }
-  if (!A.warm)
-    for (int t = threadIdx.x; t < n; t += S) x[t] = 0.0;
   bb = block_sum_1w(bb, red[0], bc);
   rr0 = block_sum_1w(rr0, red[1], bc);
   __syncthreads();  // both slot arrays are read before their next use
@@ -884,13 +963,15 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
     float2* fs0 = reinterpret_cast<float2*>(red[0]);
     float2* fs1 = reinterpret_cast<float2*>(red[1]);
     if (cg_pad_volume(ex, ey, ez) <= A.pad_cap) {
-      inner_total = inner_cg_smem(r, rnorm, x, d, pf, rf, qf, pS, n, ex, ey, ez, Wf, fs0, fs1,
-                                  inner_total, A.max_iter);
+      inner_total = dres ? inner_cg_smem<true>(r, rnorm, x, d, pf, rf, qf, pS, n, ex, ey, ez, Wf,
+                                               fs0, fs1, inner_total, A.max_iter)
+                         : inner_cg_smem<false>(r, rnorm, x, d, pf, rf, qf, pS, n, ex, ey, ez, Wf,
+                                                fs0, fs1, inner_total, A.max_iter);
     } else {
     const double inv = 1.0 / rnorm;
     DotF rr0;
     for (int t = threadIdx.x; t < n; t += S) {
-      const float v = (float)(r[t] * inv);
+      const float v = dres ? fmaf(rd[t].x, (float)inv, rd[t].y * (float)inv) : (float)(r[t] * inv);
       rf[t] = v;
       pf[t] = v;
       d[t] = 0.f;
@@ -935,13 +1016,32 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
       for (int t = threadIdx.x; t < n; t += S) pf[t] = fmaf(beta, pf[t], rf[t]);
       __syncthreads();
     }
-    // FP64 correction
-    for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+    // correction of x (FP64, or double-float with dres)
+    if (dres) {
+      const DF rn = df_from_double(rnorm);
+      for (int t = threadIdx.x; t < n; t += S) {
+        const DF y = df_add(df_mul_f(d[t], rn), DF{xd[t].x, xd[t].y});
+        xd[t] = make_float2(y.hi, y.lo);
+      }
+    } else {
+      for (int t = threadIdx.x; t < n; t += S) x[t] = fma(rnorm, (double)d[t], x[t]);
+    }
     }
     __syncthreads();
     // true residual
     double r2 = 0.0;
-    {
+    if (dres) {
+      float r2f = 0.f;
+      BoxWalk w0(threadIdx.x, S, ex, ey);
+      for (; w0.t < n; w0.next(S)) {
+        const float2 bs = split64(b[w0.t]);
+        const DF rt = df_add(DF{bs.x, bs.y},
+                             df_neg(neg_lap_df(xd, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, Wo)));
+        rd[w0.t] = make_float2(rt.hi, rt.lo);
+        r2f = fmaf(rt.hi, rt.hi, r2f);
+      }
+      r2 = (double)r2f;
+    } else {
       BoxWalk w0(threadIdx.x, S, ex, ey);
       for (; w0.t < n; w0.next(S)) {
         const double rt = b[w0.t] - neg_lap(x, w0.t, w0.x, w0.y, w0.z, ex, ey, ez, W);
@@ -952,6 +1052,13 @@ __device__ __forceinline__ void cg_pair_mixed(const CgMixedArgs& A, const Stenci
     rnorm = sqrt(block_sum_1w(r2, red[0], bc));
     ++outer;
     done = rnorm <= target;
+  }
+  if (dres) {  // x back to FP64 (each thread converts the points it wrote)
+    for (int t = threadIdx.x; t < n; t += S) {
+      const float2 xv = xd[t];
+      x[t] = df_to_double(DF{xv.x, xv.y});
+    }
+    __syncthreads();
   }
   // pair integral of Eq. exxGen_mlwf over Omega_ij
   const double* fi = A.phi ? A.phi + (size_t)P.i * ng : nullptr;
