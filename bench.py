@@ -42,9 +42,10 @@ WORKLOAD = ("(H2O)64-like, 256 localized orbitals, L=12.42 A, 96^3 grid, eps=10^
             "delta=1e-3, CG tol 1e-8, l_max=6, O(h^12) stencil; ACE build + apply to "
             "256 trial vectors")
 FORMS = {"plain": "plain FP64",
-         "mixed": "mixed: FP32 CG sweeps/vectors inside FP64 iterative refinement (FP64 true "
-                  "residual and stopping rule, FP64 E_xx); double-float multipoles; ACE "
-                  "contractions on the tensor cores from exact digit splits of FP64 values"}
+         "mixed": "mixed: FP32 CG sweeps/vectors inside iterative refinement (true residual and "
+                  "solution in double-float at tol >= 1e-10, FP64 below; FP64 E_xx); "
+                  "double-float multipoles and Cholesky; ACE contractions on the tensor cores "
+                  "from exact digit splits of FP64 values"}
 
 # Algorithmic FP64 flops per CG unknown and iteration: the symmetric 37-point
 # stencil as 18 pair sums, 18 multiply-adds and the centre product (55), plus

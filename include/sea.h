@@ -66,16 +66,17 @@ typedef enum {
  * -W Q |Lambda|^-1 Q^T W^T (the complex zeta of App. A under a Hermitian
  * inner product), eigenvalues within 1e-13 max|lambda| of zero dropped --
  * when a Cholesky pivot is not positive), precision = 0 (FP64 everywhere; 1: the mixed form --
- * FP32 stencil sweeps and CG vectors inside an FP64 iterative refinement of
- * each pair's solve, whose true residual, its norm, the stopping rule and
- * E_xx stay FP64; the inner FP32 CG uses compensated FP32 dot products and
- * FP32 step lengths; the multipole moments, boundary values and far-field
- * products in double-float arithmetic (pairs of FP32 values, about 48
- * bits); the two contractions with W (M = Phi^T W dV, W^T psi, W H) on the
- * tensor cores from exact digit splits of FP64 values (FP16 digits in the
- * contraction, BF16 digits in the expansion), truncated at 2^-47 of each
- * 64-point segment's largest value; the Cholesky diagonal
- * blocks in double-float, the rest of the Cholesky and L^-1 in FP64),
+ * FP32 stencil sweeps and CG vectors inside an iterative refinement of
+ * each pair's solve, whose true residual and solution are FP64 for
+ * cg_tol < 1e-10 and double-float (pairs of FP32 values, about 48 bits)
+ * from 1e-10 up, the stopping rule on that true residual; E_xx FP64; the
+ * inner FP32 CG uses compensated FP32 dot products and FP32 step lengths;
+ * the multipole moments, boundary values and far-field products in
+ * double-float arithmetic; the two contractions with W (M = Phi^T W dV,
+ * W^T psi, W H) on the tensor cores from exact digit splits of FP64 values
+ * (FP16 digits in the contraction, BF16 digits in the expansion), truncated
+ * at 2^-47 of each 64-point segment's largest value; the Cholesky of -Mbar,
+ * L^-1, E_xx^ACE and the products with L^-1 in double-float),
  * warm_start = 0
  * (1: every pair's CG starts from the attached learned model's guess and
  * runs to the same tolerance; the batched form always starts from zero). */
