@@ -260,36 +260,76 @@ __device__ __forceinline__ double scaled_u128(unsigned long long hi, unsigned lo
   return __longlong_as_double((long long)(((unsigned long long)ex << 52) | (mnt & 0xFFFFFFFFFFFFFULL)));
 }
 
-// Thread per (orbital, axis, coordinate): the three marginals of |phi|^2 dV,
-// m = fl(fl(2^-64 S) dV) with S the exact sum of the plane's F values.
-// marg layout: [n][3][Nmax].
-__global__ void k_marginals(const ulonglong2* __restrict__ R, const ulonglong2* __restrict__ C,
-                            int n, int nx, int ny, int nz, int Nmax, double dV,
-                            double* __restrict__ marg) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int total = n * 3 * Nmax;
-  if (t >= total) return;
-  const int coord = t % Nmax, axis = (t / Nmax) % 3, i = t / (3 * Nmax);
-  unsigned long long hi = 0, lo = 0;
+// The three marginals of |phi|^2 dV, m = fl(fl(2^-64 S) dV) with S the exact
+// sum of the plane's F values (integer sums: any grouping gives the same S).
+// A CTA per (orbital, axis).  z (sum over y of the row sums R[i][z][y],
+// contiguous): a warp per z, lanes over y, a warp reduction.  y and x (sums
+// over z of R[i][z][y] and C[i][z][x]): a thread per (coordinate, part of
+// the z range), loads coalesced over the coordinate, the parts added in
+// shared memory.  marg layout: [n][3][Nmax].
+__device__ __forceinline__ void add_u128(unsigned long long& hi, unsigned long long& lo,
+                                         unsigned long long h2, unsigned long long l2) {
+  const unsigned long long t = lo + l2;
+  hi += h2 + (t < lo ? 1ULL : 0ULL);
+  lo = t;
+}
+constexpr int MG_THREADS = 256;
+__global__ void __launch_bounds__(MG_THREADS)
+    k_marginals(const ulonglong2* __restrict__ R, const ulonglong2* __restrict__ C, int n, int nx,
+                int ny, int nz, int Nmax, double dV, double* __restrict__ marg) {
+  extern __shared__ unsigned long long mg_part[];  // [parts][2 Nmax]
+  const int axis = blockIdx.x % 3, i = blockIdx.x / 3;
+  double* out = marg + ((size_t)i * 3 + axis) * Nmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (axis == 2) {
-    if (coord >= nz) return;
-    const ulonglong2* r = R + ((size_t)i * nz + coord) * ny;
-    for (int y = 0; y < ny; ++y) add_limbs(hi, lo, r[y]);
-  } else if (axis == 1) {
-    if (coord >= ny) return;
-    for (int z = 0; z < nz; ++z) add_limbs(hi, lo, R[((size_t)i * nz + z) * ny + coord]);
-  } else {
-    if (coord >= nx) return;
-    for (int z = 0; z < nz; ++z) add_limbs(hi, lo, C[((size_t)i * nz + z) * nx + coord]);
+    for (int z = warp; z < nz; z += MG_THREADS / 32) {
+      const ulonglong2* r = R + ((size_t)i * nz + z) * ny;
+      unsigned long long hi = 0, lo = 0;
+      for (int y = lane; y < ny; y += 32) add_limbs(hi, lo, r[y]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        add_u128(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+      if (lane == 0) out[z] = __dmul_rn(scaled_u128(hi, lo, -64), dV);
+    }
+    return;
   }
-  marg[t] = __dmul_rn(scaled_u128(hi, lo, -64), dV);
+  const int m = axis == 1 ? ny : nx;  // coordinates of this marginal
+  const ulonglong2* src = axis == 1 ? R : C;
+  const int parts = max(1, MG_THREADS / m);
+  for (int c = threadIdx.x; c < m * parts; c += MG_THREADS) {
+    const int coord = c % m, p = c / m;
+    const int z0 = (int)((long long)nz * p / parts), z1 = (int)((long long)nz * (p + 1) / parts);
+    unsigned long long hi = 0, lo = 0;
+    const ulonglong2* col = src + ((size_t)i * nz) * m + coord;
+    int z = z0;
+    for (; z + 4 <= z1; z += 4) {
+      const ulonglong2 v0 = col[(size_t)z * m], v1 = col[(size_t)(z + 1) * m];
+      const ulonglong2 v2 = col[(size_t)(z + 2) * m], v3 = col[(size_t)(z + 3) * m];
+      add_limbs(hi, lo, v0);
+      add_limbs(hi, lo, v1);
+      add_limbs(hi, lo, v2);
+      add_limbs(hi, lo, v3);
+    }
+    for (; z < z1; ++z) add_limbs(hi, lo, col[(size_t)z * m]);
+    mg_part[2 * ((size_t)p * Nmax + coord)] = hi;
+    mg_part[2 * ((size_t)p * Nmax + coord) + 1] = lo;
+  }
+  __syncthreads();
+  for (int coord = threadIdx.x; coord < m; coord += MG_THREADS) {
+    unsigned long long hi = 0, lo = 0;
+    for (int p = 0; p < parts; ++p)
+      add_u128(hi, lo, mg_part[2 * ((size_t)p * Nmax + coord)], mg_part[2 * ((size_t)p * Nmax + coord) + 1]);
+    out[coord] = __dmul_rn(scaled_u128(hi, lo, -64), dV);
+  }
 }
 
 // One CTA per (orbital, axis): shortest cyclic interval with outside mass
 // <= tail.  Thread per start s finds its shortest length (the condition is
 // monotone in the length: inside only grows); then the lexicographic
-// minimum of (length, start).  No interval at all (possible only for
-// tail = 0 under rounding): the whole axis from 0.
+// minimum of (length, start).  A start stops once its length reaches the
+// shortest one found so far by any start (it can no longer win), which
+// leaves every decision and sum as they were.  No interval at all
+// (possible only for tail = 0 under rounding): the whole axis from 0.
 __global__ void k_box_fit(const double* __restrict__ marg, int nx, int ny, int nz, int Nmax,
                           double tail, int* __restrict__ box) {
   extern __shared__ double sm[];
@@ -299,25 +339,30 @@ __global__ void k_box_fit(const double* __restrict__ marg, int nx, int ny, int n
   for (int x = threadIdx.x; x < n; x += blockDim.x) sm[x] = m[x];
   __shared__ double sT;
   __shared__ long long sbest[32];
+  __shared__ int sbestL;  // shortest length found so far (only decreases)
   __syncthreads();
   if (threadIdx.x == 0) {
     double T = 0.0;
     for (int x = 0; x < n; ++x) T = __dadd_rn(T, sm[x]);
     sT = T;
+    sbestL = n;
   }
   __syncthreads();
   const double T = sT;
+  const volatile int* vbest = &sbestL;
   long long best = 0x7fffffffffffffffLL;
   for (int s = threadIdx.x; s < n; s += blockDim.x) {
     double inside = 0.0;
     int L = 0, found = 0;
     while (L < n) {
+      if (L >= *vbest) break;  // its length would exceed the shortest found
       int x = s + L;
       if (x >= n) x -= n;
       inside = __dadd_rn(inside, sm[x]);
       ++L;
       if (__dsub_rn(T, inside) <= tail) {
         found = 1;
+        atomicMin(&sbestL, L);
         break;
       }
     }
@@ -585,10 +630,18 @@ cudaError_t launch_plan_boxes(sea_ctx* c) {
     if (e != cudaSuccess) return e;
     k_row_col_sums<<<rc_grid, 128, rc_smem, c->stream>>>(phi, nx, ny, nz, Rs, Cs);
   }
-  const int tot = n * 3 * Nmax;
-  k_marginals<<<(tot + 255) / 256, 256, 0, c->stream>>>(
-      (const ulonglong2*)c->rowsum.p, (const ulonglong2*)c->colsum.p, n, nx, ny, nz, Nmax, c->dV,
-      (double*)c->marg.p);
+  {
+    const int mmin = std::max(1, std::min(nx, ny));
+    const size_t mg_smem = (size_t)std::max(1, MG_THREADS / mmin) * Nmax * 2 * sizeof(unsigned long long);
+    if (mg_smem > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(k_marginals, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)mg_smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_marginals<<<n * 3, MG_THREADS, mg_smem, c->stream>>>(
+        (const ulonglong2*)c->rowsum.p, (const ulonglong2*)c->colsum.p, n, nx, ny, nz, Nmax,
+        c->dV, (double*)c->marg.p);
+  }
   k_box_fit<<<n * 3, 128, Nmax * sizeof(double), c->stream>>>(
       (const double*)c->marg.p, nx, ny, nz, Nmax, c->prm.eps / 3.0, (int*)c->box.p);
   c->launches += 3;
