@@ -111,24 +111,14 @@ __global__ void k_entries(const PairInfo* __restrict__ pinfo, const int* __restr
 // Single-CTA exclusive scan of n ints (n small); total into *tot.
 __global__ void k_scan_int(const int* __restrict__ in, int n, int* __restrict__ out,
                            int* __restrict__ tot) {
-  __shared__ long long part[1024];
+  __shared__ long long part[32];
   const int T = blockDim.x, chunk = (n + T - 1) / T;
   const int b = chunk * threadIdx.x, e = min(n, b + chunk);
   long long s = 0;
   for (int x = b; x < e; ++x) s += in[x];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long acc = 0;
-    for (int t = 0; t < T; ++t) {
-      long long v = part[t];
-      part[t] = acc;
-      acc += v;
-    }
-    *tot = (int)acc;
-  }
-  __syncthreads();
-  long long pos = part[threadIdx.x];
+  long long acc = 0;
+  long long pos = block_exscan_ll(s, part, &acc);
+  if (threadIdx.x == 0) *tot = (int)acc;
   for (int x = b; x < e; ++x) {
     out[x] = (int)pos;
     pos += in[x];
@@ -140,8 +130,7 @@ __global__ void k_scan_int(const int* __restrict__ in, int n, int* __restrict__ 
 __global__ void k_entry_offsets(const Entry* __restrict__ ent, const int* __restrict__ E_dev,
                                 long long* __restrict__ coff, long long* __restrict__ tot,
                                 long long* __restrict__ maxwin) {
-  __shared__ long long part[1024];
-  __shared__ long long pmax[1024];
+  __shared__ long long part[32];
   const int E = *E_dev;
   const int T = blockDim.x, chunk = (E + T - 1) / T;
   const int b = chunk * threadIdx.x, e = min(E, b + chunk);
@@ -151,22 +140,13 @@ __global__ void k_entry_offsets(const Entry* __restrict__ ent, const int* __rest
     s += w;
     mx = w > mx ? w : mx;
   }
-  part[threadIdx.x] = s;
-  pmax[threadIdx.x] = mx;
-  __syncthreads();
+  long long acc = 0;
+  long long pos = block_exscan_ll(s, part, &acc);
+  const long long m = block_max_ll(mx, part);
   if (threadIdx.x == 0) {
-    long long acc = 0, m = 0;
-    for (int t = 0; t < T; ++t) {
-      long long v = part[t];
-      part[t] = acc;
-      acc += v;
-      m = pmax[t] > m ? pmax[t] : m;
-    }
     *tot = acc;
     *maxwin = m;
   }
-  __syncthreads();
-  long long pos = part[threadIdx.x];
   for (int x = b; x < e; ++x) {
     coff[x] = pos;
     pos += (long long)ent[x].wl[0] * ent[x].wl[1] * ent[x].wl[2];

@@ -153,24 +153,14 @@ __global__ void k_orb_lists(const int* __restrict__ gidx, int n_orb, int n_tiles
 
 __global__ void k_scan_small(const int* __restrict__ in, int n, int* __restrict__ out,
                              int* __restrict__ tot) {
-  __shared__ long long part[1024];
+  __shared__ long long part[32];
   const int T = blockDim.x, chunk = (n + T - 1) / T;
   const int b = chunk * threadIdx.x, e = min(n, b + chunk);
   long long s = 0;
   for (int x = b; x < e; ++x) s += in[x];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long acc = 0;
-    for (int t = 0; t < T; ++t) {
-      long long v = part[t];
-      part[t] = acc;
-      acc += v;
-    }
-    *tot = (int)acc;
-  }
-  __syncthreads();
-  long long pos = part[threadIdx.x];
+  long long acc = 0;
+  long long pos = block_exscan_ll(s, part, &acc);
+  if (threadIdx.x == 0) *tot = (int)acc;
   for (int x = b; x < e; ++x) {
     out[x] = (int)pos;
     pos += in[x];

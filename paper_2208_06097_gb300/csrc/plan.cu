@@ -447,7 +447,7 @@ __global__ void k_proto_pairs(const int* __restrict__ box, int n, int nx, int ny
 __global__ void k_compact(const int* __restrict__ flag, long long n_host,
                           const int* __restrict__ n_dev, int* __restrict__ out,
                           int* __restrict__ count) {
-  __shared__ long long part[1024];
+  __shared__ long long part[32];
   const long long n = n_dev ? (long long)*n_dev : n_host;
   const int T = blockDim.x;
   const long long chunk = (n + T - 1) / T;
@@ -455,19 +455,9 @@ __global__ void k_compact(const int* __restrict__ flag, long long n_host,
   const long long e = min(n, b + chunk);
   long long s = 0;
   for (long long x = b; x < e; ++x) s += flag[x] != 0;
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long acc = 0;
-    for (int t = 0; t < T; ++t) {
-      long long v = part[t];
-      part[t] = acc;
-      acc += v;
-    }
-    *count = (int)acc;
-  }
-  __syncthreads();
-  long long pos = part[threadIdx.x];
+  long long acc = 0;
+  long long pos = block_exscan_ll(s, part, &acc);
+  if (threadIdx.x == 0) *count = (int)acc;
   for (long long x = b; x < e; ++x)
     if (flag[x]) out[pos++] = (int)x;
 }
@@ -554,8 +544,7 @@ __global__ void k_fill_pairs(const int* __restrict__ kept, const int* __restrict
 __global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__ count,
                              const PairInfo* __restrict__ pinfo, long long* __restrict__ off,
                              long long* __restrict__ tot, int* __restrict__ maxpad) {
-  __shared__ long long part[1024];
-  __shared__ int pmax[1024];
+  __shared__ long long part[32];
   const int n = *count;
   const int T = blockDim.x;
   const int chunk = (n + T - 1) / T;
@@ -567,23 +556,13 @@ __global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__
     const PairInfo P = pinfo[x];
     pm = max(pm, P.ext[0] * (P.ext[1] + SEA_FDP) * (P.ext[2] + 2 * SEA_FDP));
   }
-  part[threadIdx.x] = s;
-  pmax[threadIdx.x] = pm;
-  __syncthreads();
+  long long acc = 0;
+  long long pos = block_exscan_ll(s, part, &acc);
+  const int m = (int)block_max_ll(pm, part);
   if (threadIdx.x == 0) {
-    long long acc = 0;
-    int m = 0;
-    for (int t = 0; t < T; ++t) {
-      long long v = part[t];
-      part[t] = acc;
-      acc += v;
-      m = max(m, pmax[t]);
-    }
     *tot = acc;
     *maxpad = m;
   }
-  __syncthreads();
-  long long pos = part[threadIdx.x];
   for (int x = b; x < e; ++x) {
     off[x] = pos;
     pos += sz[x];
@@ -591,19 +570,28 @@ __global__ void k_scan_sizes(const int* __restrict__ sz, const int* __restrict__
 }
 
 // Longest-first processing order for the CG queue: rank by (size desc,
-// index asc).
-__global__ void k_lpt_order(const int* __restrict__ sz, const int* __restrict__ count,
-                            int* __restrict__ order) {
+// index asc).  The sizes pass through shared memory in chunks, read by all
+// threads at once (broadcast).
+__global__ void __launch_bounds__(256) k_lpt_order(const int* __restrict__ sz,
+                                                   const int* __restrict__ count,
+                                                   int* __restrict__ order) {
+  __shared__ int s_sz[2048];
   const int n = *count;
+  if ((int)(blockIdx.x * blockDim.x) >= n) return;  // uniform over the CTA
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int mine = sz[p];
+  const int mine = p < n ? sz[p] : 0;
   int rank = 0;
-  for (int q = 0; q < n; ++q) {
-    const int o = sz[q];
-    rank += (o > mine) || (o == mine && q < p);
+  for (int q0 = 0; q0 < n; q0 += 2048) {
+    const int m = min(2048, n - q0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < m; q += blockDim.x) s_sz[q] = sz[q0 + q];
+    __syncthreads();
+    for (int q = 0; q < m; ++q) {
+      const int o = s_sz[q];
+      rank += (o > mine) || (o == mine && q0 + q < p);
+    }
   }
-  order[rank] = p;
+  if (p < n) order[rank] = p;
 }
 
 cudaError_t launch_plan_boxes(sea_ctx* c) {

@@ -466,6 +466,52 @@ __device__ __forceinline__ void harm_accumulate_df(DF w, DF x, DF y, DF z, DF* a
   }
 }
 
+// Exclusive scan over the CTA of one 64-bit integer per thread (blockDim.x
+// a multiple of 32, at most 1024): warp shuffles, then the warp totals by
+// the first warp.  Returns this thread's exclusive prefix; *total = the
+// CTA's sum in every thread.  `ws` holds 32 values of shared memory.
+// Integer sums, so the results equal a serial scan's.
+__device__ __forceinline__ long long block_exscan_ll(long long v, long long* ws, long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    long long t = lane < nw ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    ws[lane] = t;
+  }
+  __syncthreads();
+  const long long before = (w ? ws[w - 1] : 0) + x - v;
+  *total = ws[nw - 1];
+  __syncthreads();  // ws may be reused
+  return before;
+}
+// Maximum over the CTA of one 64-bit integer per thread (same shape rules).
+__device__ __forceinline__ long long block_max_ll(long long v, long long* ws) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long y = __shfl_xor_sync(0xffffffffu, v, o);
+    v = y > v ? y : v;
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) ws[w] = v;
+  __syncthreads();
+  long long m = ws[0];
+  for (int k = 1; k < nw; ++k) m = ws[k] > m ? ws[k] : m;
+  __syncthreads();
+  return m;
+}
+
 // Sum over the block of one double; every thread gets the same total, added
 // in a fixed order (lane tree, then warps in index order).  `slots` holds
 // 32 doubles of shared memory, reused only after the next __syncthreads.
