@@ -122,7 +122,7 @@ def job_value(steps, ws, t_ms_max):
 # by a one-pass ncu run (the two counters and the duration only).  None: not
 # captured.
 DRAM_BYTES_PER_LAUNCH = {
-    "k_cg_mixed": 26.6e6,
+    "k_cg_mixed": 25.6e6,
     "k_gram_tc": 2.026e9,
     "k_expand_tc": 1.934e9,
 }
