@@ -129,3 +129,34 @@ def test_build_repeats_bit_for_bit(h2o8, precision, own_stream):
         assert np.array_equal(M, runs[0][0]) and np.array_equal(L, runs[0][1])
         assert e == runs[0][2] and np.array_equal(y, runs[0][3])
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ace_closed_form_many_orbitals(precision):
+    # 640 orthonormal orbitals (dense, 24^3 grid) and W = -G Phi: M = -G,
+    # -Mbar = G = L L^T, E_xx^ACE = -tr(G) and V^ACE psi = -Phi^T G Phi psi dV.
+    # With 20 block columns the mixed form's one-launch Cholesky has more
+    # block tasks (821) than resident CTAs, so CTAs take several in turn.
+    from paper_2208_06097_gb300 import sea
+    rng = np.random.default_rng(11)
+    n, grid, L = 640, (24, 24, 24), 10.0
+    N = grid[0] * grid[1] * grid[2]
+    dV = (L / grid[0]) ** 3
+    Q, _ = np.linalg.qr(rng.normal(size=(N, n)))
+    F = np.ascontiguousarray(Q.T / np.sqrt(dV))  # rows orthonormal under dV
+    B = rng.normal(size=(n, n))
+    G = B @ B.T / n + np.eye(n)
+    W = np.ascontiguousarray(-(G @ F))
+    psi = rng.normal(size=(3, N))
+    y = np.empty_like(psi)
+    with sea.Context((L, L, L), grid, precision=precision) as ctx:
+        ctx.set_orbitals(F.reshape((n,) + grid[::-1]))
+        ctx.build_ace_from(W.reshape((n,) + grid[::-1]))
+        e = ctx.stats()["exx_ace"]
+        M, Lc = ctx.ace_matrices()
+        ctx.apply_ace(psi.reshape((3,) + grid[::-1]), y.reshape((3,) + grid[::-1]))
+    assert np.abs(M + G).max() <= 1e-10 * np.abs(G).max()
+    assert np.abs(Lc - np.linalg.cholesky(G)).max() <= 1e-10 * np.abs(Lc).max()
+    assert abs(e + np.trace(G)) <= 1e-10 * np.trace(G)
+    yr = -(F.T @ (G @ (F @ psi.T))).T * dV
+    assert np.abs(y - yr).max() <= 1e-9 * np.abs(yr).max()
