@@ -111,6 +111,25 @@ def test_warm_start_same_solution_fewer_iterations(trained, h2o8, precision):
     ctx.close()
 
 
+def test_warm_start_mixed_production_tolerance(trained, h2o8):
+    # At cg_tol = 1e-8 the mixed form keeps x and the true residual in
+    # double-float: the guess enters split into FP32 pairs and r = b - A x0 is
+    # formed in double-float.  Same bound as the cold solve at that tolerance
+    # (the stopping rule), against the tight FP64 solution.
+    from paper_2208_06097_gb300 import sea
+    net = trained["net"]
+    ctx = sea.Context(h2o8.cell, h2o8.grid, cg_tol=1e-8, precision=1, warm_start=1)
+    net.attach(ctx)
+    ctx.set_orbitals(trained["phi"])
+    out = torch.empty_like(trained["phi"])
+    e = ctx.apply_vxx(out)
+    scale = np.abs(trained["cold"]).max()
+    assert np.abs(out.cpu().numpy() - trained["cold"]).max() <= 5e-8 * scale
+    assert abs(e - trained["ecold"]) <= 1e-8 * abs(trained["ecold"])
+    sea.WarmStartNet.detach(ctx)
+    ctx.close()
+
+
 def test_warm_start_needs_a_model(h2o8):
     from paper_2208_06097_gb300 import sea
     ctx = sea.Context(h2o8.cell, h2o8.grid, warm_start=1)
