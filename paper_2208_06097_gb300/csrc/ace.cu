@@ -458,65 +458,6 @@ __global__ void __launch_bounds__(1024)
   Y[lane * CB + w] = t * rinv[lane];
 }
 
-// The same block factorization in double-float arithmetic (the mixed form):
-// the FP32 pipe instead of FP64, whose per-warp instruction cost makes the
-// FP64 step chain of this one-CTA kernel long.  Inputs and outputs FP64.
-__global__ void __launch_bounds__(1024)
-    k_chol_diag_df(double* __restrict__ A, int n, int kb, unsigned* __restrict__ status,
-                   double* __restrict__ Y) {
-  if (*status & SEA_FLAG_NOT_PD) return;
-  __shared__ DF Lc[CB][CB + 1];
-  __shared__ DF Sc[CB][CB + 1];
-  __shared__ DF rinv[CB];
-  __shared__ int bad;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nb = min(CB, n - kb);
-  DF a{0.f, 0.f};
-  if (w < nb) {
-    if (lane < nb && lane >= w) {
-      const float2 v = split64(A[(size_t)(kb + lane) * n + kb + w]);
-      a = DF{v.x, v.y};
-    }
-  } else if (lane == w) {
-    a = DF{1.f, 0.f};
-  }
-  if (threadIdx.x == 0) bad = 0;
-  const DF zero{0.f, 0.f};
-  auto shfl = [&](DF v, int src) {
-    return DF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
-  };
-  auto pivot = [&]() {
-    const DF d = shfl(a, w);
-    const bool ok = d.hi > 0.f;
-    const DF r = ok ? df_rcp(df_sqrt(d)) : zero;
-    const DF l = (lane == w) ? df_mul(d, r) : (lane > w ? df_mul(a, r) : zero);
-    Lc[w][lane] = l;
-    Sc[w][lane] = (lane > w) ? df_mul(l, r) : zero;
-    if (lane == 0) {
-      rinv[w] = r;
-      if (!ok) bad = 1;
-    }
-  };
-  if (w == 0) pivot();
-  __syncthreads();
-  for (int k = 0; k < CB - 1; ++k) {
-    if (bad) break;
-    if (w > k) {
-      a = df_add(a, df_neg(df_mul(Lc[k][lane], Lc[k][w])));
-      if (w == k + 1) pivot();
-    }
-    __syncthreads();
-  }
-  if (bad) {
-    if (threadIdx.x == 0) atomicOr(status, SEA_FLAG_NOT_PD);
-    return;
-  }
-  if (w < nb && lane < nb && lane >= w) A[(size_t)(kb + lane) * n + kb + w] = df_to_double(Lc[w][lane]);
-  DF t = (lane == w) ? DF{1.f, 0.f} : zero;
-  for (int j = w; j < CB - 1; ++j) t = df_add(t, df_neg(df_mul(Sc[j][lane], shfl(t, j))));
-  Y[lane * CB + w] = df_to_double(df_mul(t, rinv[lane]));
-}
-
 // Rows [kb + CB, n) of the panel, 16 per CTA (thread = row, column):
 // L(i, j) = sum_{l <= j} A(i, l) Y(j, l), written in place.
 __global__ void __launch_bounds__(512)
@@ -977,10 +918,7 @@ static cudaError_t enqueue_chol_chain(sea_ctx* c) {
   unsigned* status = (unsigned*)c->status.p;
   int nchol = 1;
   for (int kb = 0, b = 0; kb < n; kb += CB, ++b) {
-    if (c->prm.precision == 1)
-      k_chol_diag_df<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
-    else
-      k_chol_diag<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
+    k_chol_diag<<<1, 1024, 0, c->stream>>>(L, n, kb, status, Y + (size_t)b * CB * CB);
     const int rows = n - kb - CB;
     if (rows > 0) {
       const int nt = (rows + 15) / 16;
