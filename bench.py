@@ -327,7 +327,7 @@ def run_ours(args, ws, rank, local):
                   "support and K step of 16 W rows)")
         ng = float(np.prod(s.grid))
         expand_bytes = 8.0 * N_TRIAL * ng + 24576.0 * tiles_w
-        cand.append(("k_expand_tc (tensor-core W H, exact BF16 digits)", sm["expand_apply"], 1,
+        cand.append(("k_expand_tc (tensor-core W H, exact FP16 digits)", sm["expand_apply"], 1,
                      expand_bytes, hbm, "hbm", note_x))
     def _rate(c):  # work per launch / time: flop -> TFLOP/s, bytes -> GB/s
         return c[3] / (c[1] / 1e3) / (1e9 if c[5] in ("hbm", "smem") else 1e12) if c[1] > 0 else 0.0

@@ -74,7 +74,7 @@ typedef enum {
  * the multipole moments, boundary values and far-field products in
  * double-float arithmetic; the two contractions with W (M = Phi^T W dV,
  * W^T psi, W H) on the tensor cores from exact digit splits of FP64 values
- * (FP16 digits in the contraction, BF16 digits in the expansion), truncated
+ * (FP16 digits in both, the contraction and the expansion), truncated
  * at 2^-47 of each 64-point segment's largest value; the Cholesky of -Mbar,
  * L^-1, E_xx^ACE and the products with L^-1 in double-float),
  * warm_start = 0

@@ -572,6 +572,35 @@ __device__ __forceinline__ void digits8_u(const double (&v)[8], uint32_t em_sh, 
   for (int k = 0; k < DIG; ++k) d[k] = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
 }
 
+// The same unsigned-byte FP16 digits for a pair of values with exponents of
+// their own (the expansion's H(j, v) 2^E_j against E_v): emax0, emax1 are
+// the largest biased exponents the two values are measured against (below 64:
+// the value counts as zero).  pk[k][e] = the pair's digits of plane k.
+__device__ __forceinline__ void digits2_u(double v0, double v1, int emax0, int emax1,
+                                          uint32_t (&pk)[DIG][2], int e) {
+  constexpr uint32_t K64 = 0x64646464u;
+  const uint32_t em0 = emax0 >= 64 ? (uint32_t)(emax0 + 5) << 20 : 0xF0000000u;
+  const uint32_t em1 = emax1 >= 64 ? (uint32_t)(emax1 + 5) << 20 : 0xF0000000u;
+  const unsigned long long b0 = (unsigned long long)__double_as_longlong(v0);
+  const unsigned long long b1 = (unsigned long long)__double_as_longlong(v1);
+  const uint32_t h0 = (uint32_t)(b0 >> 32), h1 = (uint32_t)(b1 >> 32);
+  const unsigned long long X0 = fixed48(h0, (uint32_t)b0, em0);
+  const unsigned long long X1 = fixed48(h1, (uint32_t)b1, em1);
+  const uint32_t x0h = (uint32_t)(X0 >> 32), x0l = (uint32_t)X0;
+  const uint32_t x1h = (uint32_t)(X1 >> 32), x1l = (uint32_t)X1;
+  const uint32_t tH = __byte_perm(x0h, x1h, 0x5140);
+  const uint32_t tB = __byte_perm(x0l, x1l, 0x7362);
+  const uint32_t tA = __byte_perm(x0l, x1l, 0x5140);
+  const uint32_t S = (__byte_perm(h0, h1, 0x7030) & 0x80008000u) | 0x3C003C00u;
+  const uint32_t C = S ^ 0xD800D800u;
+  pk[0][e] = hfma2_u(__byte_perm(tH, K64, 0x4342), S, C);
+  pk[1][e] = hfma2_u(__byte_perm(tH, K64, 0x4140), S, C);
+  pk[2][e] = hfma2_u(__byte_perm(tB, K64, 0x4342), S, C);
+  pk[3][e] = hfma2_u(__byte_perm(tB, K64, 0x4140), S, C);
+  pk[4][e] = hfma2_u(__byte_perm(tA, K64, 0x4342), S, C);
+  pk[5][e] = hfma2_u(__byte_perm(tA, K64, 0x4140), S, C);
+}
+
 // Converting warps 0..15 (named barrier 1) and the issuing warp 16.  Per
 // unit the converting warps post the unit's block width and half to a
 // two-entry ring and arrive on ready[0] once K half 0's digits are in place,
@@ -986,11 +1015,14 @@ __global__ void __launch_bounds__(GT2_THREADS, 1)
 // the tensor cores, per tile (M = the tile's 128 points, N = vectors, K =
 // the tile's W list, at most XJ = 32 entries; longer lists go to the FP32
 // kernel).  Scales: W's digits are taken per (tile, list entry j) with the
-// exponent E_j of that W row on the tile; H(j, v) is scaled exactly by 2^E_j
-// and split per (tile, vector v) with one exponent E_v over the list, so
-//   y = 2^(E_v) sum_d 2^(-14-8d) D_d,  D_d = sum_j sum_{k+l=d} a_k(j) b_l(j),
-// E_j cancels and every D_d (at most 32 x 6 products of magnitude <= 2^14)
-// is an integer below 2^24, exact in the FP32 accumulator.  W's digits are
+// exponent E_j of that W row on the tile (six balanced FP16 digits a_k,
+// |a_k| <= 128, on the 2^-47 grid); H(j, v) is scaled exactly by 2^E_j and
+// measured against one exponent E_v per (tile, vector v) over the list, its
+// digits the unsigned bytes b_l of |H| 2^(E_j - E_v) on the 2^-48 grid with
+// H's sign (as A's in the contraction), so
+//   y = 2^(E_v) sum_d 2^(-15-8d) D_d,  D_d = sum_j sum_{k+l=d} a_k(j) b_l(j),
+// E_j cancels and every D_d (at most 32 x 6 products of magnitude < 2^15)
+// is an integer below 2^23, exact in the FP32 accumulator.  W's digits are
 // formed once per W into a per-tile image in the K-major layout (two K steps
 // of 16 list entries, six planes, 4 KB each); H's digits per chunk of 32
 // vectors into a slot of a shared-memory ring with the six planes stacked
@@ -1048,7 +1080,7 @@ __global__ void __launch_bounds__(MBLK)
       digit_floats(jl < nJ ? fixed47(wval(jl), emx[jl]) : 0, f0);
       digit_floats(jl + 1 < nJ ? fixed47(wval(jl + 1), emx[jl + 1]) : 0, f1);
 #pragma unroll
-      for (int k = 0; k < DIG; ++k) pk[k][e / 2] = pack_bf16(f0[k], f1[k]);
+      for (int k = 0; k < DIG; ++k) pk[k][e / 2] = pack_f16(f0[k], f1[k]);
     }
     const int q = grp >> 1, jj = grp & 1;
 #pragma unroll
@@ -1262,11 +1294,8 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int jl = jb + 2 * e;
-            float f0[DIG], f1[DIG];
-            digit_floats(jl < nJ ? fixed47(h[2 * e], ev - p_shj[jl]) : 0, f0);
-            digit_floats(jl + 1 < nJ ? fixed47(h[2 * e + 1], ev - p_shj[jl + 1]) : 0, f1);
-#pragma unroll
-            for (int l = 0; l < DIG; ++l) pk[l][e] = pack_bf16(f0[l], f1[l]);
+            digits2_u(h[2 * e], h[2 * e + 1], jl < nJ ? ev - p_shj[jl] : 0,
+                      jl + 1 < nJ ? ev - p_shj[jl + 1] : 0, pk, e);
           }
           // entries jb.. of K step jb / 16: core matrix (jb / 8) % 2, bytes
           // (jb % 8) 2 of its 16-byte rows
@@ -1349,7 +1378,7 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
           for (int k = 0; k < DIG; ++k) {
             const uint64_t a = sdesc(a_base + ab * XA_TILE + qq * XA_STEP + k * XA_BLOCK, XA_LBO, 128);
             const uint64_t b = sdesc(s_base + slot * XS_SLOT + qq * XB_CHUNK, XB_LBO, 128);
-            mma_kf16(dcol + (uint32_t)(k * XN), a, b, idesc_kf16((DIG - k) * XN, MBLK, true),
+            mma_kf16(dcol + (uint32_t)(k * XN), a, b, idesc_kf16((DIG - k) * XN, MBLK, false),
                      (k > 0 || qq > 0) ? 1u : 0u);
           }
         mma_commit(smem_addr(&bar_md[tb]));
@@ -1402,6 +1431,7 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
         tc_fence_after();
         const uint32_t la = lane_q + (uint32_t)(tb * XT_COLS);
         const int ev[8] = {e4[0].x, e4[0].y, e4[0].z, e4[0].w, e4[1].x, e4[1].y, e4[1].z, e4[1].w};
+        const bool wide = nJ > XKS;
         // four vectors at a time: six diagonal sums each
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
@@ -1416,13 +1446,17 @@ __global__ void __launch_bounds__(XE_THREADS, 1)
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            // sum_d D_d 256^(5 - d), |D_d| < 2^22, in three 32-bit pairs
+            // sum_d D_d 256^(5 - d) in three 32-bit pairs; |D_d| < 2^22 except
+            // D_4 and D_5 of lists longer than 16 (below 2^23): those by the
+            // conversion instruction
             const int t01 = small_float_int(f[0][u]) * 256 + small_float_int(f[1][u]);
             const int t23 = small_float_int(f[2][u]) * 256 + small_float_int(f[3][u]);
-            const int t45 = small_float_int(f[4][u]) * 256 + small_float_int(f[5][u]);
+            const int d4 = wide ? __float2int_rz(__uint_as_float(f[4][u])) : small_float_int(f[4][u]);
+            const int d5 = wide ? __float2int_rz(__uint_as_float(f[5][u])) : small_float_int(f[5][u]);
+            const int t45 = d4 * 256 + d5;
             const long long base = ((long long)t01 << 32) + (long long)t45;
             const long long acc = base + (long long)t23 * 65536LL;
-            const double val = scaled_i64_rz_cvt(acc, ev[4 * hh + u] - 1022 - 54);
+            const double val = scaled_i64_rz_cvt(acc, ev[4 * hh + u] - 1022 - 55);
             if (g >= 0 && (full || vbase + 4 * hh + u < m)) o[(size_t)(4 * hh + u) * ng] = val;
           }
         }
