@@ -382,6 +382,36 @@ __global__ void __launch_bounds__(GR_A * GR_Z)
     out[(size_t)a * sa + (size_t)o * so] = scale * (((red[0][x] + red[1][x]) + red[2][x]) + red[3][x]);
 }
 
+// The same sums in double-float for the mixed form (the partials split
+// exactly to FP32 pairs, sums on the FP32 pipes; the FP64 adds of the form
+// above bound it there), one rounding to FP64 before the scaling.
+__global__ void __launch_bounds__(GR_A * GR_Z)
+    k_gram_reduce_df(const double* __restrict__ partial, int m, int n_orb,
+                     const int* __restrict__ optr, const int* __restrict__ oslot, double scale,
+                     double* __restrict__ out, int sa, int so) {
+  __shared__ DF red[GR_Z][GR_A];
+  const int o = blockIdx.y, x = threadIdx.x % GR_A, z = threadIdx.x / GR_A;
+  const int a = blockIdx.x * GR_A + x;
+  DF s{0.f, 0.f};
+  if (a < m) {
+    int k = optr[o] + z;
+    const int k1 = optr[o + 1];
+    for (; k + 7 * GR_Z < k1; k += 8 * GR_Z) {
+      double p[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) p[u] = partial[(size_t)oslot[k + u * GR_Z] * m + a];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s = df_add(s, df_from_double(p[u]));
+    }
+    for (; k < k1; k += GR_Z) s = df_add(s, df_from_double(partial[(size_t)oslot[k] * m + a]));
+  }
+  red[z][x] = s;
+  __syncthreads();
+  if (z == 0 && a < m)
+    out[(size_t)a * sa + (size_t)o * so] =
+        scale * df_to_double(df_add(df_add(df_add(red[0][x], red[1][x]), red[2][x]), red[3][x]));
+}
+
 // -Mbar = L L^T by a blocked right-looking Cholesky (block CB = 32), and
 // L^-1.  On this part a warp's FP64 instruction holds an SM sub-partition's
 // FP64 unit for about 64 cycles whatever its active lanes, so the kernels
@@ -1073,7 +1103,7 @@ cudaError_t launch_ace_build(sea_ctx* c) {
     if (err == cudaSuccess) err = cudaEventRecord(c->xev[0], c->xfer[0]);
     if (err != cudaSuccess) return err;
   }
-  k_gram_reduce<<<dim3((n + GR_A - 1) / GR_A, n), GR_A * GR_Z, 0, c->stream>>>(
+  (c->prm.precision == 1 ? k_gram_reduce_df : k_gram_reduce)<<<dim3((n + GR_A - 1) / GR_A, n), GR_A * GR_Z, 0, c->stream>>>(
       (const double*)c->partial.p, n, n, optr, oslot, c->dV, (double*)c->Mbuf.p,
       n, 1);
   c->launches += 2;
@@ -1154,7 +1184,7 @@ cudaError_t launch_ace_apply(sea_ctx* c, const double* psi, int nv, double* out)
     if (e != cudaSuccess) return e;
   }
   cudaEventRecord(c->ev[13], c->stream);
-  k_gram_reduce<<<dim3((nv + GR_A - 1) / GR_A, n), GR_A * GR_Z, 0, c->stream>>>(
+  (c->prm.precision == 1 ? k_gram_reduce_df : k_gram_reduce)<<<dim3((nv + GR_A - 1) / GR_A, n), GR_A * GR_Z, 0, c->stream>>>(
       (const double*)c->partial.p, nv, n, optr, oslot, c->dV, (double*)c->Gbuf.p,
       1, nv);
   // H = (-Mbar)^-1 G = L^-T (L^-1 G), or Q |Lambda|^-1 Q^T G in the eigen form
