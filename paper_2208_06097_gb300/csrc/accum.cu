@@ -509,18 +509,19 @@ cudaError_t launch_contrib_far(sea_ctx* c, cudaEvent_t setup_done) {
   return cudaGetLastError();
 }
 
-// E_xx and the CG statistics (after every pair energy is final).
-cudaError_t launch_exx(sea_ctx* c) {
-  k_exx<<<1, 256, 0, c->stream>>>((const PairInfo*)c->pinfo.p, (const int*)c->counts.p + 1,
+// E_xx and the CG statistics (after every pair energy is final), on
+// stream st.
+cudaError_t launch_exx(sea_ctx* c, cudaStream_t st) {
+  k_exx<<<1, 256, 0, st>>>((const PairInfo*)c->pinfo.p, (const int*)c->counts.p + 1,
                                  (const double*)c->epair.p, (const int*)c->iters.p,
                                  (double*)c->exx_dev.p);
   c->launches += 1;
   return cudaGetLastError();
 }
 
-cudaError_t launch_accumulate(sea_ctx* c, double* out, double* out2) {
+cudaError_t launch_accumulate(sea_ctx* c, double* out, double* out2, bool with_exx) {
   cudaError_t e = launch_accumulate_range(c, out, 0, c->n_orb, 0, c->E, out2);
-  return e != cudaSuccess ? e : launch_exx(c);
+  return e != cudaSuccess || !with_exx ? e : launch_exx(c, c->stream);
 }
 
 cudaError_t upload_harmonics_accum() { return upload_harmonics_here(); }

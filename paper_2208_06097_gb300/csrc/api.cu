@@ -495,14 +495,18 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
     const cudaError_t e = sea::launch_ace_lists(c, c->xfer[1]);
     if (e == cudaErrorMemoryAllocation) return sea_fail(c, SEA_ERR_OOM, "ACE tile lists");
     SEA_CK(e, "ACE tile lists");
-    SEA_CK(cudaEventRecord(c->xev[2], c->xfer[1]), "event");
   }
   SEA_CK(sea::launch_contrib_far(c, c->ev[2]), "far field");
   SEA_CK(cudaEventRecord(c->ev[3], c->stream), "event");
+  // E_xx and the CG statistics need the pair energies only: beside the far
+  // field and the accumulation, after the lists on the same side stream
+  SEA_CK(cudaStreamWaitEvent(c->xfer[1], c->ev[3], 0), "wait");
+  SEA_CK(sea::launch_exx(c, c->xfer[1]), "exx");
+  SEA_CK(cudaEventRecord(c->xev[2], c->xfer[1]), "event");
   tr.stage("far field and accumulation");
   double* vd = (double*)c->vxx_dev.p;
   if (on_device) {
-    SEA_CK(sea::launch_accumulate(c, vd, vxx_phi), "accumulate");
+    SEA_CK(sea::launch_accumulate(c, vd, vxx_phi, false), "accumulate");
     SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
   } else {
     // Host output: orbital ranges are finished and copied out one after
@@ -524,7 +528,6 @@ sea_status sea_apply_vxx(sea_ctx* c, double* vxx_phi, int on_device, double* exx
                              c->xfer[1]),
              "copy V_xx phi");
     }
-    SEA_CK(sea::launch_exx(c), "exx");
     SEA_CK(cudaEventRecord(c->ev[4], c->stream), "event");
     SEA_CK(cudaEventRecord(ev_out, c->xfer[1]), "event");
     SEA_CK(cudaStreamWaitEvent(c->stream, ev_out, 0), "wait");

@@ -798,10 +798,11 @@ int cg_pad_cap(const sea_ctx* c);
 cudaError_t launch_entries(sea_ctx* c);
 // V_xx phi into out (the context's W) and, when out2 is not null, also into
 // out2 (the caller's device buffer), both written by the same stores.
-cudaError_t launch_accumulate(sea_ctx* c, double* out, double* out2 = nullptr);
+cudaError_t launch_accumulate(sea_ctx* c, double* out, double* out2 = nullptr,
+                              bool with_exx = true);
 cudaError_t launch_accumulate_range(sea_ctx* c, double* out, int o_begin, int o_end, int e_begin,
                                     int e_end, double* out2 = nullptr);
-cudaError_t launch_exx(sea_ctx* c);
+cudaError_t launch_exx(sea_ctx* c, cudaStream_t st);
 // Learned warm start (unet.cu): x0 of every pair's CG from the attached model.
 cudaError_t launch_warm_start(sea_ctx* c);
 // SCDM localization of the orbitals in the context (scdm.cu): U and the
