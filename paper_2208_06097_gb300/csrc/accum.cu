@@ -154,8 +154,8 @@ __global__ void k_entry_offsets(const Entry* __restrict__ ent, const int* __rest
 }
 
 // Window contributions of the entries (grid y) in chunks of SEA_CHUNK window
-// points (grid x); `part` as in contrib_range (2 when the mixed CG already
-// formed the far-field points).  DFM: double-float arithmetic (mixed form),
+// points (grid x); `part` as in contrib_range (1: the far field on a side
+// stream beside the CG, 2: the points inside the pair boxes after it).  DFM: double-float arithmetic (mixed form),
 // four CTAs per SM there (64 registers, no spills): the nested Horner steps
 // of the potential are one dependent chain per point, so the warps resident
 // per SM set the rate (measured 0.81 -> 0.77 ms per step against two CTAs).
@@ -167,10 +167,14 @@ __global__ void __launch_bounds__(256, DFM ? 4 : 1)
               const double* __restrict__ Qg, double hx, double hy, double hz,
               double* __restrict__ cbuf, int part) {
   const Entry e = ent[blockIdx.y];
-  const int nw = e.wl[0] * e.wl[1] * e.wl[2];
-  const int t0 = blockIdx.x * SEA_CHUNK;
-  if (t0 >= nw) return;
   const PairInfo P = pinfo[e.pair];
+  const int nw = e.wl[0] * e.wl[1] * e.wl[2];
+  const WinSplit sp = window_split(e, P);
+  // parts 1 and 2 enumerate their own points (divisions exact below 2^24)
+  const bool compact = part != 0 && nw < (1 << 24);
+  const int cnt = !compact ? nw : part == 1 ? sp.n_out : sp.n_in;
+  const int t0 = blockIdx.x * SEA_CHUNK;
+  if (t0 >= cnt) return;
   __shared__ double Ps[SEA_NMONO];
   __shared__ DF Pd[SEA_NMONO];
   if (part != 2 && threadIdx.x < SEA_NMONO) {
@@ -181,8 +185,8 @@ __global__ void __launch_bounds__(256, DFM ? 4 : 1)
       Ps[threadIdx.x] = q;
   }
   __syncthreads();
-  contrib_range<DFM>(part, e, P, phi, nx, ny, nz, vbuf + voff[e.pair], Pd, Ps, hx, hy, hz,
-                     cbuf + coff[blockIdx.y], t0, min(nw, t0 + SEA_CHUNK));
+  contrib_range<DFM>(part, compact, sp, e, P, phi, nx, ny, nz, vbuf + voff[e.pair], Pd, Ps, hx, hy,
+                     hz, cbuf + coff[blockIdx.y], t0, min(cnt, t0 + SEA_CHUNK));
 }
 
 // Global-memory form: CTA per (orbital, slab of SLAB z-planes); out2, when

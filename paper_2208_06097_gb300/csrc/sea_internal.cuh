@@ -706,15 +706,104 @@ namespace sea {
 // mixed CG's far-field items).
 #define SEA_CHUNK 1024
 
-// Window contributions c = v phi_partner (Eq. tDxx) of entry e at its window
-// points t = t0 + threadIdx.x, + blockDim.x, ... < t1 (window-compact
-// output out[t]): v is the pair's CG solution (v, box layout) inside the
-// pair box and the multipole potential (coefficients Pd, double-float, or
-// Ps, FP64) outside.  part 0: every point; 1: only the points outside the
-// box (they need the moments alone); 2: only those inside (they need the
-// solution).  DFM: double-float products (mixed form), else FP64.
+// q = floor(a / d) and *r = a - q d for 0 <= a < 2^24, 1 <= d < 2^24: the
+// FP32 product a (1/d) is within (a/d) 2^-23 < 1 of a/d, so its truncation
+// is q or q +- 1, corrected once by the sign and size of the remainder.
+__host__ __device__ __forceinline__ int divmod_small(int a, int d, int* r) {
+  int q = (int)((float)a * (1.0f / (float)d));
+  int rr = a - q * d;
+  if (rr < 0) {
+    --q;
+    rr += d;
+  } else if (rr >= d) {
+    ++q;
+    rr -= d;
+  }
+  *r = rr;
+  return q;
+}
+
+// The pair box in the coordinates of an entry's window, clipped to it:
+// [b0[a], b1[a]) per axis, n_in points inside and n_out outside.  An empty
+// intersection is kept as the empty box [0, 0)^3, so that every window point
+// falls in the "z above" part of window_outside_point.
+struct WinSplit {
+  int b0[3], b1[3];
+  int n_in, n_out;
+};
+__host__ __device__ __forceinline__ WinSplit window_split(const Entry& e, const PairInfo& P) {
+  WinSplit s;
+  bool empty = false;
+  for (int a = 0; a < 3; ++a) {
+    const int lo = P.lo[a] - e.ws[a], hi = lo + P.ext[a];
+    s.b0[a] = lo < 0 ? 0 : (lo > e.wl[a] ? e.wl[a] : lo);
+    s.b1[a] = hi < 0 ? 0 : (hi > e.wl[a] ? e.wl[a] : hi);
+    empty = empty || s.b0[a] >= s.b1[a];
+  }
+  if (empty)
+    for (int a = 0; a < 3; ++a) s.b0[a] = s.b1[a] = 0;
+  s.n_in = (s.b1[0] - s.b0[0]) * (s.b1[1] - s.b0[1]) * (s.b1[2] - s.b0[2]);
+  s.n_out = e.wl[0] * e.wl[1] * e.wl[2] - s.n_in;
+  return s;
+}
+
+// Window coordinates of point u (0 <= u < n_out, n_out < 2^24) of the window
+// points outside the pair box, numbered through six disjoint boxes: the
+// planes below and above the box's z range, then within that z range the
+// rows below and above its y range, then within that y range the runs left
+// and right of its x range; x fastest inside each.
+__host__ __device__ __forceinline__ void window_outside_point(const WinSplit& s, const int wl[3],
+                                                              int u, int* tx, int* ty, int* tz) {
+  const int wx = wl[0], wy = wl[1], wz = wl[2];
+  const int zb = s.b1[2] - s.b0[2], yb = s.b1[1] - s.b0[1];
+  const int n1 = s.b0[2] * wx * wy, n2 = (wz - s.b1[2]) * wx * wy;
+  const int n3 = zb * s.b0[1] * wx, n4 = zb * (wy - s.b1[1]) * wx, n5 = zb * yb * s.b0[0];
+  int ox = 0, oy = 0, oz = 0, bx = wx, by = wy;
+  if (u < n1) {
+  } else if ((u -= n1) < n2) {
+    oz = s.b1[2];
+  } else if ((u -= n2) < n3) {
+    oz = s.b0[2];
+    by = s.b0[1];
+  } else if ((u -= n3) < n4) {
+    oz = s.b0[2];
+    oy = s.b1[1];
+    by = wy - s.b1[1];
+  } else if ((u -= n4) < n5) {
+    oz = s.b0[2];
+    oy = s.b0[1];
+    by = yb;
+    bx = s.b0[0];
+  } else {
+    u -= n5;
+    oz = s.b0[2];
+    oy = s.b0[1];
+    by = yb;
+    ox = s.b1[0];
+    bx = wx - s.b1[0];
+  }
+  int rx, ry;
+  const int q = divmod_small(u, bx, &rx);
+  const int qz = divmod_small(q, by, &ry);
+  *tx = ox + rx;
+  *ty = oy + ry;
+  *tz = oz + qz;
+}
+
+// Window contributions c = v phi_partner (Eq. tDxx) of entry e (window-
+// compact output out[t], t = (tz wy + ty) wx + tx): v is the pair's CG
+// solution (v, box layout) inside the pair box and the multipole potential
+// (coefficients Pd, double-float, or Ps, FP64) outside.  part 0: every
+// window point, t = t0 + threadIdx.x, + blockDim.x, ... < t1; 1: only the
+// points outside the box (they need the moments alone), 2: only those
+// inside (they need the solution); for parts 1 and 2 with compact set, t0
+// and t1 number the points of that part alone (window_outside_point; the
+// box's points in x-fastest order), so that no lane idles on a point of the
+// other part, else they are window points and the other part's are skipped.
+// DFM: double-float products (mixed form), else FP64.
 template <bool DFM>
-__device__ __forceinline__ void contrib_range(int part, const Entry& e, const PairInfo& P,
+__device__ __forceinline__ void contrib_range(int part, bool compact, const WinSplit& sp,
+                                              const Entry& e, const PairInfo& P,
                                               const double* __restrict__ phi, int nx, int ny,
                                               int nz, const double* __restrict__ v, const DF* Pd,
                                               const double* Ps, double hx, double hy, double hz,
@@ -725,37 +814,18 @@ __device__ __forceinline__ void contrib_range(int part, const Entry& e, const Pa
   const double cx = 0.5 * (P.ext[0] - 1), cy = 0.5 * (P.ext[1] - 1), cz = 0.5 * (P.ext[2] - 1);
   const float cxf = 0.5f * i2f_exact(P.ext[0] - 1), cyf = 0.5f * i2f_exact(P.ext[1] - 1),
               czf = 0.5f * i2f_exact(P.ext[2] - 1);
-  // window coordinates of t, advanced by the CTA stride without divisions;
-  // grid coordinates from the window start wrapped once
-  const int wx = e.wl[0], wy = e.wl[1], wxy = wx * wy;
-  const int S = blockDim.x;
-  const int dz = S / wxy, dy = (S - dz * wxy) / wx, dx = S - dz * wxy - dy * wx;
+  const int wx = e.wl[0], wy = e.wl[1];
   const int gx0 = wrapi(e.ws[0], nx), gy0 = wrapi(e.ws[1], ny), gz0 = wrapi(e.ws[2], nz);
-  int tz = (t0 + (int)threadIdx.x) / wxy;
-  int ty = (t0 + (int)threadIdx.x - tz * wxy) / wx;
-  int tx = t0 + (int)threadIdx.x - tz * wxy - ty * wx;
-  for (int t = t0 + threadIdx.x; t < t1; t += S) {
-    const int ux = e.ws[0] + tx, uy = e.ws[1] + ty, uz = e.ws[2] + tz;
-    const int lx = ux - P.lo[0], ly = uy - P.lo[1], lz = uz - P.lo[2];
-    const bool inside =
-        lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2];
+  const int S = blockDim.x;
+  // one window point (tx, ty, tz): its value into out[(tz wy + ty) wx + tx]
+  auto point = [&](int tx, int ty, int tz, bool inside) {
+    const int lx = e.ws[0] + tx - P.lo[0], ly = e.ws[1] + ty - P.lo[1], lz = e.ws[2] + tz - P.lo[2];
     int gx = gx0 + tx, gy = gy0 + ty, gz = gz0 + tz;  // window lengths are at most n
     gx -= gx >= nx ? nx : 0;
     gy -= gy >= ny ? ny : 0;
     gz -= gz >= nz ? nz : 0;
     const size_t g = ((size_t)gz * ny + gy) * nx + gx;
-    tx += dx;
-    ty += dy;
-    tz += dz;
-    if (tx >= wx) {
-      tx -= wx;
-      ++ty;
-    }
-    if (ty >= wy) {
-      ty -= wy;
-      ++tz;
-    }
-    if ((part == 1 && inside) || (part == 2 && !inside)) continue;
+    const int t = (tz * wy + ty) * wx + tx;
     if (DFM) {  // c = v phi in double-float, no FP64 instruction
       DF val;
       if (inside) {
@@ -772,6 +842,47 @@ __device__ __forceinline__ void contrib_range(int part, const Entry& e, const Pa
                                 : me_potential_cart(Ps, (lx - cx) * hx, (ly - cy) * hy, (lz - cz) * hz);
       out[t] = __dmul_rn(val, fp[g]);
     }
+  };
+  // parts 0 and 2, and part 1 without compact: a box [ox, ox + bx) x
+  // [oy, oy + by) x ... (the window, or with compact part 2 the pair box
+  // within it) walked with (kx, ky, kz) advanced by the CTA stride without
+  // divisions; compact part 1: window_outside_point
+  const bool outer = compact && part == 1, box = compact && part == 2;
+  const int ox = box ? sp.b0[0] : 0, oy = box ? sp.b0[1] : 0, oz = box ? sp.b0[2] : 0;
+  const int bx = box ? sp.b1[0] - sp.b0[0] : wx, by = box ? sp.b1[1] - sp.b0[1] : wy;
+  const int bxy = bx * by;
+  const int dz = S / bxy, dy = (S - dz * bxy) / bx, dx = S - dz * bxy - dy * bx;
+  int kz = (t0 + (int)threadIdx.x) / bxy;
+  int ky = (t0 + (int)threadIdx.x - kz * bxy) / bx;
+  int kx = t0 + (int)threadIdx.x - kz * bxy - ky * bx;
+  for (int t = t0 + threadIdx.x; t < t1; t += S) {
+    int tx, ty, tz;
+    bool inside = box;
+    if (outer) {
+      window_outside_point(sp, e.wl, t, &tx, &ty, &tz);
+    } else {
+      tx = ox + kx;
+      ty = oy + ky;
+      tz = oz + kz;
+      kx += dx;
+      ky += dy;
+      kz += dz;
+      if (kx >= bx) {
+        kx -= bx;
+        ++ky;
+      }
+      if (ky >= by) {
+        ky -= by;
+        ++kz;
+      }
+      if (!box) {
+        const int lx = e.ws[0] + tx - P.lo[0], ly = e.ws[1] + ty - P.lo[1],
+                  lz = e.ws[2] + tz - P.lo[2];
+        inside = lx >= 0 && lx < P.ext[0] && ly >= 0 && ly < P.ext[1] && lz >= 0 && lz < P.ext[2];
+        if ((part == 1 && inside) || (part == 2 && !inside)) continue;
+      }
+    }
+    point(tx, ty, tz, inside);
   }
 }
 
