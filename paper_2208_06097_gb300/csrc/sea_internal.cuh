@@ -855,6 +855,58 @@ __device__ __forceinline__ void contrib_range(int part, bool compact, const WinS
   int kz = (t0 + (int)threadIdx.x) / bxy;
   int ky = (t0 + (int)threadIdx.x - kz * bxy) / bx;
   int kx = t0 + (int)threadIdx.x - kz * bxy - ky * bx;
+  if (box) {
+    // in-box points: the loop is bound by the latency of its two loads per
+    // point, so each thread takes CU points (t, t + S, ...) with all their
+    // loads issued before the first product; the products are those of
+    // `point`, so the results are the same bits
+    constexpr int CU = 4;
+    const int l0 = e.ws[0] - P.lo[0], l1 = e.ws[1] - P.lo[1], l2 = e.ws[2] - P.lo[2];
+    for (int t = t0 + threadIdx.x; t < t1; t += CU * S) {
+      int lq[CU], tq[CU];
+      size_t gq[CU];
+#pragma unroll
+      for (int u = 0; u < CU; ++u) {
+        const int tx = ox + kx, ty = oy + ky, tz = oz + kz;
+        kx += dx;
+        ky += dy;
+        kz += dz;
+        if (kx >= bx) {
+          kx -= bx;
+          ++ky;
+        }
+        if (ky >= by) {
+          ky -= by;
+          ++kz;
+        }
+        int gx = gx0 + tx, gy = gy0 + ty, gz = gz0 + tz;
+        gx -= gx >= nx ? nx : 0;
+        gy -= gy >= ny ? ny : 0;
+        gz -= gz >= nz ? nz : 0;
+        gq[u] = ((size_t)gz * ny + gy) * nx + gx;
+        tq[u] = (tz * wy + ty) * wx + tx;
+        lq[u] = ((l2 + tz) * P.ext[1] + (l1 + ty)) * P.ext[0] + (l0 + tx);
+      }
+      double vq[CU], fq[CU];
+#pragma unroll
+      for (int u = 0; u < CU; ++u)
+        if (t + u * S < t1) {
+          vq[u] = v[lq[u]];
+          fq[u] = fp[gq[u]];
+        }
+#pragma unroll
+      for (int u = 0; u < CU; ++u)
+        if (t + u * S < t1) {
+          if (DFM) {
+            const float2 s = split64(vq[u]), f = split64(fq[u]);
+            out[tq[u]] = df_to_double(df_mul(DF{s.x, s.y}, DF{f.x, f.y}));
+          } else {
+            out[tq[u]] = __dmul_rn(vq[u], fq[u]);
+          }
+        }
+    }
+    return;
+  }
   for (int t = t0 + threadIdx.x; t < t1; t += S) {
     int tx, ty, tz;
     bool inside = box;
