@@ -1,8 +1,9 @@
 """Fixtures under tests/golden/ against the oracle and the library's defaults.
 
-`fd12_second_difference.txt` holds the published exact weights of the order-12
-centred second difference (the per-axis operator of the paper's O(h^12)
-Laplacian); the oracle derives its weights from a closed form, so the two are
+`fd12_second_difference.txt` holds the exact weights of the order-12 centred
+second difference, the per-axis operator of the paper's O(h^12) Laplacian.
+They are fixed by its moment conditions, which are checked here in rational
+arithmetic; the oracle derives its weights from a closed form, so the two are
 independent.  `paper_settings.txt` holds the settings the paper states for its
 calculations (l_max, stencil order, CG residual, the epsilon range).
 """
@@ -43,7 +44,7 @@ def test_fd12_fixture_is_consistent():
         assert sum(w[k] * k ** m for k in range(1, 7)) == 0
 
 
-def test_oracle_weights_match_published_table():
+def test_oracle_weights_match_exact_weights():
     w = _fd12()
     c = O.fd_coeffs(6)
     for k in range(7):
